@@ -1,0 +1,132 @@
+/*
+ * se_mobility.h -- C ABI of the B300 Spectral Ewald far-field grand mobility.
+ *
+ * Computes y = M_inf . x for N spheres of radii a_i in a cubic periodic box,
+ * where M_inf is the far-field grand mobility of Wang & Brady (arXiv 1506.08481)
+ * including the compressible-solvent pressure-moment terms:
+ *
+ *   x_i = [F (3), T (3), S (5), S_tr (1)]   moments the sphere exerts on the fluid
+ *   y_i = [U (3), Omega (3), E (5), E_tr (1)] translational / angular velocity,
+ *                                             strain rate, expansion rate
+ *
+ * S and E are traceless symmetric tensors stored as coordinates on the
+ * orthonormal basis (xx-yy)/sqrt2, (2zz-xx-yy)/sqrt6, (xy+yx)/sqrt2,
+ * (xz+zx)/sqrt2, (yz+zy)/sqrt2.  Per particle the components are stored
+ * contiguously (row-major [N][ncomp]); with ncomp < 12 only the leading
+ * components are read and written (3: F->U, 6: +T->Omega, 11: +S->E, 12: +S_tr->E_tr).
+ *
+ * Method (paper sections and equations):
+ *   Faxen laws Eqs. faxen-f/t/s/p and multipole expansion Eq. mul-expand (Sec. 2.1);
+ *   Hasimoto/Beenakker split of the periodic Oseen tensor Eqs. oseen-split,
+ *   oseen-ewald-rs/ws (Sec. 2.2) and of the source/pressure solutions Eq. source-split
+ *   (Sec. 2.3); real-space pairs within rc from a cell list (Sec. 3.3); wave space by
+ *   the Spectral Ewald method (Sec. 3.1): Gaussian spreading Eq. grid-space with the
+ *   shape function Eq. shape, theta from Eq. theta-param, fast Gaussian gridding
+ *   Eq. fgg-exp, 3D FFT, k-space scaling Eq. wave-result, gather by the trapezoid rule
+ *   Eq. parseval-sum; particle-size terms by the hybrid approach (Sec. 3.2, default)
+ *   or the real-space approach Eq. non-ortho-shape; self terms Eq. uf-self.
+ *   se_solve: GMRES with the block-diagonal far-field preconditioner of Sec. 4.2.
+ *
+ * Conventions common to all entry points:
+ *   - Every function returns 0 on success or a negative SE_ERR_* code; the message
+ *     of the last failure is returned by se_last_error(ctx).
+ *   - Device pointers are CUDA device addresses on the context's device; the caller
+ *     owns every buffer it passes; the context owns its internal scratch.
+ *   - Work is enqueued on the stream given to se_create (borrowed, never destroyed)
+ *     and is asynchronous unless stated otherwise.
+ *   - Viscosity eta = 1 unless set with SE_OPT_ETA.
+ */
+#ifndef SE_MOBILITY_H
+#define SE_MOBILITY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct se_ctx se_ctx;
+
+/* error codes */
+#define SE_OK                 0
+#define SE_ERR_ARG           -1   /* invalid argument (null pointer, bad size, ncomp, dtype) */
+#define SE_ERR_GRID          -2   /* M not of the form 2^a 3^b in [8, 512], or P outside [2, M] */
+#define SE_ERR_CUTOFF        -3   /* rc <= 0 or rc >= L/2 */
+#define SE_ERR_CUDA          -4   /* a CUDA runtime call failed */
+#define SE_ERR_STATE         -5   /* parameters or configuration not set */
+#define SE_ERR_NONFINITE     -6   /* non-finite position, radius or result */
+#define SE_ERR_NOT_CONVERGED -7   /* GMRES reached maxit (x holds the last iterate) */
+#define SE_ERR_NOMEM         -8   /* device allocation failed */
+
+/* dtypes of x / y */
+#define SE_F32 0
+#define SE_F64 1
+
+/* options for se_set_option */
+#define SE_OPT_PRECISION   1   /* compute precision of products: 0 = FP32 (default), 1 = FP64 */
+#define SE_OPT_SIZE_MODE   2   /* particle-size terms: 0 = hybrid (default), 1 = real-space approach */
+#define SE_OPT_ETA         3   /* solvent viscosity (default 1) */
+#define SE_OPT_SHAPE_M     4   /* Gaussian shape parameter m of Eq. theta-param (default sqrt(pi P)) */
+#define SE_OPT_RESTART     5   /* GMRES restart length (default 30) */
+#define SE_OPT_PARTS       6   /* bit mask of terms: 1 real space, 2 wave space, 4 self (default 7) */
+
+/* preconditioners for se_solve */
+#define SE_PRECOND_NONE    0
+#define SE_PRECOND_BLOCK   1   /* block-diagonal self + own-image blocks (Sec. 4.2) */
+#define SE_PRECOND_LEARNED 2   /* block preconditioner + learned correction (falls back to BLOCK) */
+
+/* Create a context on CUDA device `device`; `stream` is a cudaStream_t (may be 0 for
+ * the legacy default stream), borrowed for the context's lifetime.  *out receives the
+ * context, or NULL on failure (SE_ERR_CUDA). */
+int se_create(se_ctx **out, int device, void *stream);
+
+/* Destroy a context and free its scratch.  Synchronises its stream.  NULL is accepted. */
+int se_destroy(se_ctx *ctx);
+
+/* Ewald/SE parameters (Sec. 3.1, Eq. theta-param; Sec. 3.3):
+ *   xi  splitting parameter (> 0),  M grid points per dimension (2^a 3^b, 8..512),
+ *   P   support points per dimension (2..M),  rc real-space cutoff (> 0, < L/2 at
+ *   se_set_config).  Invalidates the configuration-dependent setup. */
+int se_set_params(se_ctx *ctx, double xi, int M, int P, double rc);
+
+/* Scalar options (SE_OPT_*).  Returns SE_ERR_ARG for an unknown key or a bad value. */
+int se_set_option(se_ctx *ctx, int key, double value);
+
+/* Particle configuration: N spheres, box side L; pos [N][3] and radius [N] are FP64
+ * DEVICE arrays (positions anywhere, wrapped into the box).  Builds the cell list,
+ * the spreading bins and (lazily) the preconditioner.  Fails with SE_ERR_CUTOFF when
+ * rc >= L/2 and SE_ERR_NONFINITE for non-finite or non-positive data.  The arrays are
+ * copied; the caller may free them afterwards.  Synchronises the stream. */
+int se_set_config(se_ctx *ctx, int64_t N, double L, const double *pos, const double *radius);
+
+/* y = M_inf . x.  x, y: DEVICE arrays [N][ncomp] of dtype SE_F32 or SE_F64 (both the
+ * same dtype); ncomp in {3, 6, 11, 12}.  x and y must not overlap.  Asynchronous. */
+int se_mobility_apply(se_ctx *ctx, int ncomp, const void *x, void *y, int dtype);
+
+/* Same product with HOST FP64 arrays x, y [N][ncomp]: copies x to the device, applies,
+ * copies y back and synchronises.  Pinned host memory gives the fastest copies. */
+int se_mobility_apply_host(se_ctx *ctx, int ncomp, const double *x, double *y);
+
+/* Solve M_inf . x = b by right-preconditioned GMRES(restart) (Sec. 4.1-4.2 with the
+ * near-field resistance set to zero).  b, x: DEVICE arrays [N][ncomp] of `dtype`;
+ * x holds the initial guess on entry and the solution on exit.  Krylov vectors and
+ * the true residual b - M x are FP64; products run at SE_OPT_PRECISION and the final
+ * residual check (one refinement restart if needed) uses an FP64 product.
+ * rtol: relative residual target; maxit: maximum products; precond: SE_PRECOND_*.
+ * *iters (may be NULL) receives the number of products, *relres (may be NULL) the
+ * final FP64 relative residual.  Synchronises.  Returns SE_ERR_NOT_CONVERGED if
+ * relres > rtol after maxit products. */
+int se_solve(se_ctx *ctx, int ncomp, const void *b, void *x, int dtype, double rtol,
+             int maxit, int precond, int *iters, double *relres);
+
+/* Message describing the last failure on this context ("" if none).  Valid until the
+ * next call on the same context.  ctx may be NULL (returns the last create failure). */
+const char *se_last_error(const se_ctx *ctx);
+
+/* Number of CUDA kernels this context has launched since creation (for accounting). */
+int64_t se_kernel_launches(const se_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SE_MOBILITY_H */

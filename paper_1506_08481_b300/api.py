@@ -1,0 +1,195 @@
+"""Thin ctypes binding over the C ABI declared in include/se_mobility.h.
+
+Argument marshalling only: every step of the product and of the solve runs in
+the CUDA library ``libse_b300.so``.  There is no CPU fallback; ``load()`` raises
+when the library is missing or fails to load.
+
+Device arrays are passed as torch CUDA tensors (their data pointers) and work is
+enqueued on torch's current CUDA stream unless another stream is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libse_b300.so")
+
+SE_OK = 0
+SE_ERR_ARG, SE_ERR_GRID, SE_ERR_CUTOFF, SE_ERR_CUDA = -1, -2, -3, -4
+SE_ERR_STATE, SE_ERR_NONFINITE, SE_ERR_NOT_CONVERGED, SE_ERR_NOMEM = -5, -6, -7, -8
+SE_F32, SE_F64 = 0, 1
+SE_OPT_PRECISION, SE_OPT_SIZE_MODE, SE_OPT_ETA, SE_OPT_SHAPE_M, SE_OPT_RESTART, SE_OPT_PARTS = 1, 2, 3, 4, 5, 6
+SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED = 0, 1, 2
+
+# every entry point declared in include/se_mobility.h
+ABI_SYMBOLS = ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
+               "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_last_error",
+               "se_kernel_launches")
+
+_lib = None
+
+
+class SeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (raises OSError if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with `python -m paper_1506_08481_b300.build`")
+    lib = ctypes.CDLL(path)
+    p, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    lib.se_create.argtypes = [ctypes.POINTER(p), i, p]
+    lib.se_destroy.argtypes = [p]
+    lib.se_set_params.argtypes = [p, d, i, i, d]
+    lib.se_set_option.argtypes = [p, i, d]
+    lib.se_set_config.argtypes = [p, i64, d, p, p]
+    lib.se_mobility_apply.argtypes = [p, i, p, p, i]
+    lib.se_mobility_apply_host.argtypes = [p, i, p, p]
+    lib.se_solve.argtypes = [p, i, p, p, i, d, i, i, ctypes.POINTER(i), ctypes.POINTER(d)]
+    lib.se_last_error.argtypes = [p]
+    lib.se_last_error.restype = ctypes.c_char_p
+    lib.se_kernel_launches.argtypes = [p]
+    lib.se_kernel_launches.restype = i64
+    for name in ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
+                 "se_mobility_apply", "se_mobility_apply_host", "se_solve"):
+        getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return SE_F32
+    if t.dtype == torch.float64:
+        return SE_F64
+    raise TypeError("x and y must be float32 or float64 tensors")
+
+
+class Context:
+    """Owns one se_ctx.  Methods mirror the C ABI entry points."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.se_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream))
+        if rc != SE_OK:
+            raise SeError(rc, self.lib.se_last_error(None).decode())
+        self.h = h
+        self.N = 0
+        self.L = 0.0
+        self._keep = []
+
+    def _check(self, rc):
+        if rc != SE_OK:
+            raise SeError(rc, self.lib.se_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.se_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return self.lib.se_last_error(self.h).decode()
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.se_kernel_launches(self.h))
+
+    # --- se_set_params / se_set_option
+    def se_set_params(self, xi: float, M: int, P: int, rc: float):
+        self._check(self.lib.se_set_params(self.h, float(xi), int(M), int(P), float(rc)))
+
+    set_params = se_set_params
+
+    def se_set_option(self, key: int, value: float):
+        self._check(self.lib.se_set_option(self.h, int(key), float(value)))
+
+    set_option = se_set_option
+
+    # --- se_set_config
+    def se_set_config(self, pos, rad, L: float):
+        """pos [N,3], rad [N]: numpy arrays or CUDA tensors (copied as FP64)."""
+        import torch
+        pos_t = torch.as_tensor(np.asarray(pos) if not torch.is_tensor(pos) else pos,
+                                dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
+        rad_t = torch.as_tensor(np.asarray(rad) if not torch.is_tensor(rad) else rad,
+                                dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
+        N = rad_t.shape[0]
+        if pos_t.numel() != 3 * N:
+            raise ValueError("pos must be [N, 3] with N = len(rad)")
+        self._check(self.lib.se_set_config(self.h, N, float(L), ctypes.c_void_p(pos_t.data_ptr()),
+                                           ctypes.c_void_p(rad_t.data_ptr())))
+        self.N, self.L = N, float(L)
+
+    set_config = se_set_config
+
+    # --- se_mobility_apply
+    def se_mobility_apply(self, x, y=None, ncomp: int | None = None):
+        """y = M_inf . x for CUDA tensors x [N, ncomp] (float32/float64)."""
+        import torch
+        if ncomp is None:
+            ncomp = x.shape[-1]
+        if y is None:
+            y = torch.empty_like(x)
+        if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+            raise ValueError("x and y must be contiguous CUDA tensors")
+        if x.dtype != y.dtype or x.numel() != self.N * ncomp or y.numel() != self.N * ncomp:
+            raise ValueError("x and y must be [N, ncomp] tensors of the same dtype")
+        self._check(self.lib.se_mobility_apply(self.h, int(ncomp), ctypes.c_void_p(x.data_ptr()),
+                                               ctypes.c_void_p(y.data_ptr()), _dtype_code(x)))
+        return y
+
+    apply = se_mobility_apply
+
+    def se_mobility_apply_host(self, x: np.ndarray, y: np.ndarray | None = None) -> np.ndarray:
+        """Host FP64 arrays [N, ncomp]; copies in, applies, copies out (synchronous)."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        ncomp = x.shape[-1]
+        if y is None:
+            y = np.empty_like(x)
+        self._check(self.lib.se_mobility_apply_host(self.h, int(ncomp), x.ctypes.data_as(ctypes.c_void_p),
+                                                    y.ctypes.data_as(ctypes.c_void_p)))
+        return y
+
+    apply_host = se_mobility_apply_host
+
+    # --- se_solve
+    def se_solve(self, b, x=None, rtol: float = 1e-6, maxit: int = 500, precond: int = SE_PRECOND_BLOCK,
+                 ncomp: int | None = None, allow_not_converged: bool = False):
+        """Solve M_inf x = b (CUDA tensors [N, ncomp]); returns (x, iters, relres)."""
+        import torch
+        if ncomp is None:
+            ncomp = b.shape[-1]
+        if x is None:
+            x = torch.zeros_like(b)
+        iters = ctypes.c_int(0)
+        relres = ctypes.c_double(0.0)
+        rc = self.lib.se_solve(self.h, int(ncomp), ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                               _dtype_code(b), float(rtol), int(maxit), int(precond), ctypes.byref(iters),
+                               ctypes.byref(relres))
+        if rc == SE_ERR_NOT_CONVERGED and allow_not_converged:
+            return x, iters.value, relres.value
+        self._check(rc)
+        return x, iters.value, relres.value
+
+    solve = se_solve

@@ -1,0 +1,387 @@
+// C ABI entry points (include/se_mobility.h): context lifecycle, parameters,
+// configuration, and the grand-mobility product y = M_inf . x.
+//
+// Product schedule (one call, all on the device, no host round trip):
+//   main stream : permute x into cell order -> [fork] -> spread -> FFT x -> FFT y
+//                 -> FFT z + k-space scaling + inverse z -> inverse y -> inverse x
+//                 -> [join] -> gather + real + self, written in caller order
+//   aux stream  : real-space pair sum (overlaps the memory-bound FFT chain)
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "se_internal.cuh"
+
+using namespace se;
+
+static std::string g_create_error;
+
+namespace se {
+
+namespace {
+
+template <typename T, typename TI>
+__global__ void permute_in_kernel(int N, int ncomp, const int *perm, const TI *x, T *xs)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const TI *src = x + (size_t)perm[k] * ncomp;
+    T *dst = xs + (size_t)k * kNC;
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) dst[c] = c < ncomp ? (T)src[c] : (T)0;
+}
+
+}  // namespace
+
+template <typename T, typename TI>
+void launch_permute_in(se_ctx *c, const TI *x, T *xs, int ncomp, cudaStream_t s)
+{
+    const int N = (int)c->N;
+    permute_in_kernel<T, TI><<<(N + 255) / 256, 256, 0, s>>>(N, ncomp, c->b.perm, x, xs);
+    c->launches++;
+}
+
+template void launch_permute_in<float, float>(se_ctx *, const float *, float *, int, cudaStream_t);
+template void launch_permute_in<float, double>(se_ctx *, const double *, float *, int, cudaStream_t);
+template void launch_permute_in<double, float>(se_ctx *, const float *, double *, int, cudaStream_t);
+template void launch_permute_in<double, double>(se_ctx *, const double *, double *, int, cudaStream_t);
+
+}  // namespace se
+
+// ---------------------------------------------------------------- helpers
+
+static bool grid_size_ok(int M)
+{
+    if (M < 8 || M > 512 || M % kTile != 0) return false;
+    int m = M;
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    return m == 1;
+}
+
+static void make_plan(int M, FftPlan &plan)
+{
+    plan.M = M;
+    plan.nst = 0;
+    int m = M;
+    while (m % 8 == 0) { plan.rad[plan.nst++] = 8; m /= 8; }
+    if (m % 4 == 0) { plan.rad[plan.nst++] = 4; m /= 4; }
+    if (m % 2 == 0) { plan.rad[plan.nst++] = 2; m /= 2; }
+    while (m % 3 == 0) { plan.rad[plan.nst++] = 3; m /= 3; }
+}
+
+static void dfree(void *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+template <typename P>
+static void dfree_t(P *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+static void free_grids(se_ctx *c)
+{
+    for (int q = 0; q < 2; ++q) {
+        dfree(c->b.grid_f[q]);
+        dfree(c->b.spec_f[q]);
+        dfree(c->b.spec_o[q]);
+        dfree(c->b.grid_o[q]);
+        dfree(c->b.tw[q]);
+        c->grid_M[q] = 0;
+    }
+}
+
+static void free_config(se_ctx *c)
+{
+    dfree_t(c->b.pos);
+    dfree_t(c->b.rad);
+    dfree_t(c->b.perm);
+    dfree_t(c->b.cell_start);
+    dfree_t(c->b.tile_perm);
+    dfree_t(c->b.tile_start);
+    dfree_t(c->b.sup_base);
+    for (int q = 0; q < 2; ++q) {
+        dfree(c->b.sup_s0[q]);
+        dfree(c->b.sup_w[q]);
+        dfree(c->b.xs[q]);
+        dfree(c->b.yreal[q]);
+        c->support_ok[q] = false;
+    }
+    dfree_t(c->b.pc_inv);
+    dfree_t(c->b.kry);
+    dfree_t(c->b.work64);
+    dfree_t(c->b.red);
+    dfree_t(c->b.stage);
+    c->alloc_N = 0;
+    c->tiles_ok = false;
+    c->pc_ready = false;
+}
+
+#define SE_ALLOC(ctx, ptr, bytes)                                                     \
+    do {                                                                              \
+        if (cudaMalloc((void **)&(ptr), (bytes)) != cudaSuccess) {                    \
+            cudaGetLastError();                                                       \
+            (ctx)->err = "device allocation of " + std::to_string((size_t)(bytes)) + " bytes failed"; \
+            return SE_ERR_NOMEM;                                                      \
+        }                                                                             \
+    } while (0)
+
+// grids for (M, precision prec)
+static int ensure_grids(se_ctx *c, int prec)
+{
+    const size_t es = prec == 1 ? sizeof(double) : sizeof(float);
+    if (c->grid_M[prec] == (size_t)c->M && c->b.grid_f[prec]) return SE_OK;
+    dfree(c->b.grid_f[prec]);
+    dfree(c->b.spec_f[prec]);
+    dfree(c->b.spec_o[prec]);
+    dfree(c->b.grid_o[prec]);
+    dfree(c->b.tw[prec]);
+    const size_t M = c->M, Mh = M / 2 + 1;
+    SE_ALLOC(c, c->b.grid_f[prec], M * M * M * 4 * es);
+    SE_ALLOC(c, c->b.spec_f[prec], M * M * Mh * 4 * 2 * es);
+    SE_ALLOC(c, c->b.spec_o[prec], M * M * Mh * 8 * 2 * es);
+    SE_ALLOC(c, c->b.grid_o[prec], M * M * M * 8 * es);
+    SE_ALLOC(c, c->b.tw[prec], M * 2 * es);
+    c->grid_M[prec] = c->M;
+    make_twiddles(c, prec);
+    return SE_OK;
+}
+
+// support tables and work vectors at precision prec
+static int ensure_support(se_ctx *c, int prec)
+{
+    if (c->alloc_N == 0 || !c->b.pos) {
+        c->err = "se_set_config must be called first";
+        return SE_ERR_STATE;
+    }
+    const size_t es = prec == 1 ? sizeof(double) : sizeof(float);
+    const size_t N = c->N;
+    if (!c->b.sup_s0[prec]) SE_ALLOC(c, c->b.sup_s0[prec], N * 3 * es);
+    if (!c->b.xs[prec]) SE_ALLOC(c, c->b.xs[prec], N * kNC * es);
+    if (!c->b.yreal[prec]) SE_ALLOC(c, c->b.yreal[prec], N * kNC * es);
+    if (!c->support_ok[prec]) {
+        dfree(c->b.sup_w[prec]);
+        SE_ALLOC(c, c->b.sup_w[prec], N * 3 * c->P * es);
+        return build_support(c, prec);
+    }
+    return SE_OK;
+}
+
+static int set_error(se_ctx *c, int code, const std::string &msg)
+{
+    c->err = msg;
+    return code;
+}
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" int se_create(se_ctx **out, int device, void *stream)
+{
+    if (!out) return SE_ERR_ARG;
+    *out = nullptr;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        g_create_error = "cudaSetDevice failed";
+        return SE_ERR_CUDA;
+    }
+    se_ctx *c = new se_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        g_create_error = "stream/event creation failed";
+        delete c;
+        return SE_ERR_CUDA;
+    }
+    *out = c;
+    return SE_OK;
+}
+
+extern "C" int se_destroy(se_ctx *c)
+{
+    if (!c) return SE_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->aux);
+    free_grids(c);
+    free_config(c);
+    cudaEventDestroy(c->ev_fork);
+    cudaEventDestroy(c->ev_join);
+    cudaStreamDestroy(c->aux);
+    delete c;
+    return SE_OK;
+}
+
+extern "C" const char *se_last_error(const se_ctx *c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" int64_t se_kernel_launches(const se_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" int se_set_params(se_ctx *c, double xi, int M, int P, double rc)
+{
+    if (!c) return SE_ERR_ARG;
+    if (!(xi > 0) || !std::isfinite(xi)) return set_error(c, SE_ERR_ARG, "xi must be positive");
+    if (!grid_size_ok(M)) return set_error(c, SE_ERR_GRID, "M must be 2^a 3^b, a multiple of 8, in [8, 512]");
+    if (P < 2 || P > 32 || P > M - kTile) return set_error(c, SE_ERR_GRID, "P must satisfy 2 <= P <= min(32, M - 8)");
+    if (!(rc > 0) || !std::isfinite(rc)) return set_error(c, SE_ERR_CUTOFF, "rc must be positive");
+    cudaSetDevice(c->device);
+    c->xi = xi;
+    c->M = M;
+    c->P = P;
+    c->rc = rc;
+    make_plan(M, c->plan);
+    c->have_params = true;
+    c->have_config = false;            // configuration-dependent setup must be rebuilt
+    c->pc_ready = false;
+    c->err.clear();
+    return SE_OK;
+}
+
+extern "C" int se_set_option(se_ctx *c, int key, double value)
+{
+    if (!c) return SE_ERR_ARG;
+    switch (key) {
+    case SE_OPT_PRECISION:
+        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "precision must be 0 (FP32) or 1 (FP64)");
+        c->precision = (int)value;
+        return SE_OK;
+    case SE_OPT_SIZE_MODE:
+        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "size mode must be 0 (hybrid) or 1 (real-space)");
+        c->size_mode = (int)value;
+        c->pc_ready = false;
+        return SE_OK;
+    case SE_OPT_ETA:
+        if (!(value > 0)) return set_error(c, SE_ERR_ARG, "eta must be positive");
+        c->eta = value;
+        c->pc_ready = false;
+        return SE_OK;
+    case SE_OPT_SHAPE_M:
+        if (!(value > 0)) return set_error(c, SE_ERR_ARG, "m must be positive");
+        c->m_shape = value;
+        c->m_user = true;
+        c->support_ok[0] = c->support_ok[1] = false;
+        c->pc_ready = false;
+        return SE_OK;
+    case SE_OPT_RESTART:
+        if (value < 1 || value > 200) return set_error(c, SE_ERR_ARG, "restart must be in [1, 200]");
+        c->restart = (int)value;
+        return SE_OK;
+    case SE_OPT_PARTS:
+        if (value < 0 || value > 7) return set_error(c, SE_ERR_ARG, "parts must be a mask in [0, 7]");
+        c->parts = (int)value;
+        return SE_OK;
+    default:
+        return set_error(c, SE_ERR_ARG, "unknown option");
+    }
+}
+
+extern "C" int se_set_config(se_ctx *c, int64_t N, double L, const double *pos, const double *radius)
+{
+    if (!c || !pos || !radius || N <= 0 || N > (1 << 28)) return c ? set_error(c, SE_ERR_ARG, "bad N or null pointer") : SE_ERR_ARG;
+    if (!c->have_params) return set_error(c, SE_ERR_STATE, "se_set_params must be called first");
+    if (!(L > 0) || !std::isfinite(L)) return set_error(c, SE_ERR_ARG, "L must be positive");
+    if (c->rc >= 0.5 * L) return set_error(c, SE_ERR_CUTOFF, "rc must be smaller than L/2");
+    cudaSetDevice(c->device);
+    SE_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    free_config(c);
+    c->N = N;
+    c->L = L;
+    int nc = (int)std::floor(L / c->rc);
+    if (nc < 3) nc = 1;
+    if (nc > 256) nc = 256;
+    c->nc = nc;
+    const size_t nt = c->M / kTile;
+    SE_ALLOC(c, c->b.pos, N * 3 * sizeof(double));
+    SE_ALLOC(c, c->b.rad, N * sizeof(double));
+    SE_ALLOC(c, c->b.perm, N * sizeof(int));
+    SE_ALLOC(c, c->b.cell_start, ((size_t)nc * nc * nc + 1) * sizeof(int));
+    SE_ALLOC(c, c->b.tile_perm, N * sizeof(int));
+    SE_ALLOC(c, c->b.tile_start, (nt * nt * nt + 1) * sizeof(int));
+    SE_ALLOC(c, c->b.sup_base, N * 3 * sizeof(int));
+    c->alloc_N = N;
+    int rc = build_cells(c, pos, radius);
+    if (rc == SE_OK) rc = ensure_support(c, c->precision);
+    if (rc != SE_OK) {
+        c->have_config = false;
+        free_config(c);
+        return rc;
+    }
+    c->have_config = true;
+    c->pc_ready = false;
+    c->err.clear();
+    return SE_OK;
+}
+
+template <typename T, typename TO>
+static int apply_t(se_ctx *c, int ncomp, const TO *x, TO *y)
+{
+    cudaStream_t s = c->stream;
+    T *xs = (T *)c->b.xs[pix<T>()], *yr = (T *)c->b.yreal[pix<T>()];
+    launch_permute_in<T, TO>(c, x, xs, ncomp, s);
+    SE_CUDA_CHECK(c, cudaEventRecord(c->ev_fork, s));
+    SE_CUDA_CHECK(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    if (c->parts & 1) launch_real<T>(c, xs, yr, c->aux, ncomp);
+    else SE_CUDA_CHECK(c, cudaMemsetAsync(yr, 0, c->N * kNC * sizeof(T), c->aux));
+    SE_CUDA_CHECK(c, cudaEventRecord(c->ev_join, c->aux));
+    const int with_wave = (c->parts & 2) ? 1 : 0;
+    if (with_wave) launch_wave<T>(c, xs, s, ncomp);
+    SE_CUDA_CHECK(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+    launch_gather_combine<T, TO>(c, xs, yr, y, ncomp, with_wave, s);
+    SE_CUDA_CHECK(c, cudaGetLastError());
+    return SE_OK;
+}
+
+int se::se_apply_internal(se_ctx *c, int ncomp, const void *x, void *y, int dtype, int prec)
+{
+    if (!c->have_config) return set_error(c, SE_ERR_STATE, "se_set_config must be called first");
+    int rc = ensure_support(c, prec);
+    if (rc != SE_OK) return rc;
+    rc = ensure_grids(c, prec);
+    if (rc != SE_OK) return rc;
+    if (prec == 1) {
+        return dtype == SE_F64 ? apply_t<double, double>(c, ncomp, (const double *)x, (double *)y)
+                               : apply_t<double, float>(c, ncomp, (const float *)x, (float *)y);
+    }
+    return dtype == SE_F64 ? apply_t<float, double>(c, ncomp, (const double *)x, (double *)y)
+                           : apply_t<float, float>(c, ncomp, (const float *)x, (float *)y);
+}
+
+static int check_apply_args(se_ctx *c, int ncomp, const void *x, const void *y, int dtype)
+{
+    if (!c) return SE_ERR_ARG;
+    if (!x || !y) return set_error(c, SE_ERR_ARG, "null x or y");
+    if (ncomp != 3 && ncomp != 6 && ncomp != 11 && ncomp != 12) return set_error(c, SE_ERR_ARG, "ncomp must be 3, 6, 11 or 12");
+    if (dtype != SE_F32 && dtype != SE_F64) return set_error(c, SE_ERR_ARG, "dtype must be SE_F32 or SE_F64");
+    if (!c->have_params) return set_error(c, SE_ERR_STATE, "se_set_params must be called first");
+    if (c->alloc_N == 0) return set_error(c, SE_ERR_STATE, "se_set_config must be called first");
+    return SE_OK;
+}
+
+extern "C" int se_mobility_apply(se_ctx *c, int ncomp, const void *x, void *y, int dtype)
+{
+    int rc = check_apply_args(c, ncomp, x, y, dtype);
+    if (rc != SE_OK) return rc;
+    cudaSetDevice(c->device);
+    return se_apply_internal(c, ncomp, x, y, dtype, c->precision);
+}
+
+extern "C" int se_mobility_apply_host(se_ctx *c, int ncomp, const double *x, double *y)
+{
+    int rc = check_apply_args(c, ncomp, x, y, SE_F64);
+    if (rc != SE_OK) return rc;
+    cudaSetDevice(c->device);
+    const size_t bytes = (size_t)c->N * ncomp * sizeof(double);
+    if (!c->b.stage) SE_ALLOC(c, c->b.stage, (size_t)c->N * kNC * sizeof(double) * 2);
+    double *dx = c->b.stage, *dy = c->b.stage + (size_t)c->N * kNC;
+    SE_CUDA_CHECK(c, cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, c->stream));
+    rc = se_apply_internal(c, ncomp, dx, dy, SE_F64, c->precision);
+    if (rc != SE_OK) return rc;
+    SE_CUDA_CHECK(c, cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, c->stream));
+    SE_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    return SE_OK;
+}

@@ -1,0 +1,144 @@
+// Internal declarations of the B300 Spectral Ewald mobility library.
+// Not part of the C ABI (include/se_mobility.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/se_mobility.h"
+
+namespace se {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kNC = 12;          // components per particle, internal layout
+constexpr int kTile = 8;         // spreading tile edge (grid points)
+
+template <typename T> struct C2;
+template <> struct C2<float> { using t = float2; };
+template <> struct C2<double> { using t = double2; };
+template <typename T> constexpr int pix() { return sizeof(T) == 8 ? 1 : 0; }
+
+// radices of a mixed-radix Stockham FFT of length M = 2^a 3^b
+struct FftPlan {
+    int M;
+    int nst;
+    int rad[16];
+};
+
+// Spectral Ewald parameters as used on the device (grid units: u = x M / L).
+struct SeParams {
+    int M, P, Mh;                // grid, support, M/2 + 1
+    int ntile;                   // M / kTile
+    double L, xi, rc, eta;
+    double alpha;                // Gaussian exp(-alpha s^2) in grid units, alpha = 2 m^2 / P^2
+    double kappa;                // M / L  (d/dx = kappa d/ds)
+    int hybrid;                  // 1: hybrid size terms, 0: real-space approach
+};
+
+// Cell list for the real-space sum (cells of side >= rc).
+struct CellGrid {
+    int nc;                      // cells per dimension (1 if fewer than 3 fit)
+};
+
+struct Buffers {
+    // configuration (sorted by cell)
+    double *pos = nullptr;       // [N][3] wrapped positions, cell order
+    double *rad = nullptr;       // [N]
+    int *perm = nullptr;         // sorted index -> caller index
+    int *cell_start = nullptr;   // [nc^3 + 1]
+    int *tile_perm = nullptr;    // tile order -> sorted index
+    int *tile_start = nullptr;   // [ntile^3 + 1]
+    int *sup_base = nullptr;     // [N][3] first support point (wrapped)
+    // per compute precision (index 0: FP32, 1: FP64)
+    void *sup_s0[2] = {};        // [N][3] T: offset of the first support point from the particle
+    void *sup_w[2] = {};         // [N][3][P] T: Gaussian weights along each axis
+    void *xs[2] = {};            // [N][12] T inputs in cell order
+    void *yreal[2] = {};         // [N][12] T real-space result
+    void *grid_f[2] = {};        // [M^3][4] T spread grids
+    void *spec_f[2] = {};        // [M][M][Mh][4] complex T
+    void *spec_o[2] = {};        // [M][M][Mh][8] complex T
+    void *grid_o[2] = {};        // [M^3][8] T gathered grids
+    void *tw[2] = {};            // [M] complex T twiddles
+    // host-API staging (device side)
+    double *stage = nullptr;     // [2][N][12]
+    // solver
+    double *pc_inv = nullptr;    // [N][nc][nc] inverse preconditioner blocks (caller order)
+    double *kry = nullptr;       // Krylov basis [restart + 1][n]
+    double *work64 = nullptr;    // FP64 work vectors [5][n]
+    double *red = nullptr;       // reduction scratch
+};
+
+}  // namespace se
+
+struct se_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;     // borrowed
+    cudaStream_t aux = nullptr;        // owned: real space overlaps the wave chain
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // parameters
+    bool have_params = false;
+    double xi = 0, rc = 0, m_shape = 0, eta = 1.0;
+    bool m_user = false;
+    int M = 0, P = 0;
+    int precision = 0;                 // 0 FP32, 1 FP64
+    int size_mode = 0;                 // 0 hybrid, 1 real-space approach
+    int restart = 30;
+    int parts = 7;
+    // configuration
+    bool have_config = false;
+    bool support_ok[2] = {false, false};
+    bool tiles_ok = false;
+    size_t grid_M[2] = {0, 0};
+    int64_t N = 0;
+    double L = 0;
+    int nc = 1;
+    // preconditioner state
+    bool pc_ready = false;
+    int pc_ncomp = 0, pc_prec = -1;
+    se::FftPlan plan{};
+    se::Buffers b;
+    size_t alloc_N = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+// ---- launchers implemented in the .cu files ----
+namespace se {
+
+SeParams make_params(const se_ctx *c);
+
+// se_config.cu
+int build_cells(se_ctx *c, const double *pos_dev, const double *rad_dev);
+int build_support(se_ctx *c, int prec);
+
+// se_real.cu
+template <typename T>
+void launch_real(se_ctx *c, const T *xs, T *yreal, cudaStream_t s, int ncomp);
+
+// se_wave.cu
+template <typename T>
+void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp);
+template <typename T, typename TO>
+void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int ncomp, int with_wave,
+                           cudaStream_t s);
+template <typename T>
+void setup_support(se_ctx *c, cudaStream_t s);
+void make_twiddles(se_ctx *c, int prec);
+
+// se_api.cu
+template <typename T, typename TI>
+void launch_permute_in(se_ctx *c, const TI *x, T *xs, int ncomp, cudaStream_t s);
+int se_apply_internal(se_ctx *c, int ncomp, const void *x, void *y, int dtype, int prec);
+
+}  // namespace se
+
+#define SE_CUDA_CHECK(ctx, call)                                                     \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);         \
+            return SE_ERR_CUDA;                                                      \
+        }                                                                            \
+    } while (0)

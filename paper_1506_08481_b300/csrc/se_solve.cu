@@ -1,0 +1,444 @@
+// se_solve: M_inf . x = b by right-preconditioned restarted GMRES (Sec. 4.1) with
+// the block-diagonal far-field preconditioner of Sec. 4.2.
+//
+// Far-field-only reading of Sec. 4.2: with no lubrication (R^nf = 0) the
+// preconditioner is the inverse of the block diagonal of M_inf, each block being
+// the sphere's self mobility plus the interaction with its own periodic images
+// (Eq. rfu-approx with the near-field blocks set to zero).  ILU0 of a dense block
+// is its exact LU, so each block is inverted exactly.  Because the block depends
+// only on the radius a (and the box), it is a polynomial of degree 2 in a^2 plus
+// the isolated-sphere terms; the polynomial is sampled with single-sphere Spectral
+// Ewald products (the same operator the solver inverts) at three radii.
+//
+// Precision: Krylov vectors, Gram-Schmidt (CGS2) and the true residual b - M x are
+// FP64; Krylov products run at the context's compute precision.  Each restart
+// starts from the FP64 true residual, which is the iterative-refinement step when
+// products are FP32.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "se_internal.cuh"
+
+namespace se {
+
+namespace {
+
+constexpr int kRedBlocks = 296;
+
+// part[i * kRedBlocks + blk] = partial sum of V_i . w (V_i = V + i * ld)
+__global__ void mdot_partial(const double *V, size_t ld, size_t n, const double *w, double *part)
+{
+    const int i = blockIdx.y;
+    const double *v = V + (size_t)i * ld;
+    double s = 0;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        s += v[e] * w[e];
+    __shared__ double sm[32];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) part[(size_t)i * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+__global__ void mdot_final(const double *part, int nblk, double *out)
+{
+    const int i = blockIdx.x;
+    double s = 0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)i * nblk + b];
+    __shared__ double sm[32];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (threadIdx.x == 0) out[i] = s;
+    }
+}
+
+// w -= sum_i h[i] V_i   (h on the device)
+__global__ void maxpy_kernel(const double *V, size_t ld, size_t n, int k, const double *h, double *w)
+{
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        double s = w[e];
+        for (int i = 0; i < k; ++i) s -= h[i] * V[(size_t)i * ld + e];
+        w[e] = s;
+    }
+}
+
+// out = sum_i y[i] V_i
+__global__ void combine_kernel(const double *V, size_t ld, size_t n, int k, const double *y, double *out)
+{
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        double s = 0;
+        for (int i = 0; i < k; ++i) s += y[i] * V[(size_t)i * ld + e];
+        out[e] = s;
+    }
+}
+
+__global__ void axpby_kernel(size_t n, double a, const double *x, double b, const double *y, double *out)
+{
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = a * x[e] + b * y[e];
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(size_t n, const TI *x, TO *y)
+{
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        y[e] = (TO)x[e];
+}
+
+// z_p = B_p^{-1} v_p for every particle p (blocks nc x nc, caller order)
+__global__ void block_apply_kernel(int N, int nc, const double *Binv, const double *v, double *z)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const double *B = Binv + (size_t)p * nc * nc;
+    const double *vp = v + (size_t)p * nc;
+    double *zp = z + (size_t)p * nc;
+    for (int a = 0; a < nc; ++a) {
+        double s = 0;
+        for (int b = 0; b < nc; ++b) s += B[a * nc + b] * vp[b];
+        zp[a] = s;
+    }
+}
+
+// Block of particle with radius a: isolated-sphere self terms + C0 + a^2 C1 + a^4 C2,
+// inverted by Gauss-Jordan elimination with partial pivoting.  Sorted particle k is
+// stored at caller index perm[k].  Singular blocks fall back to the isolated inverse.
+__global__ void block_build_kernel(int N, int nc, double eta, const double *rad, const int *perm,
+                                   const double *C /*[3][12][12]*/, double *Binv)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const double a = rad[k], a2 = a * a;
+    double A[kNC][2 * kNC];
+    const double pi = kPi;
+    for (int r = 0; r < nc; ++r) {
+        for (int q = 0; q < nc; ++q) {
+            A[r][q] = C[r * kNC + q] + a2 * C[kNC * kNC + r * kNC + q] + a2 * a2 * C[2 * kNC * kNC + r * kNC + q];
+            A[r][nc + q] = r == q ? 1.0 : 0.0;
+        }
+        const double iso = r < 3 ? 1.0 / (6 * pi * eta * a)
+                         : r < 6 ? 1.0 / (8 * pi * eta * a * a2)
+                         : r < 11 ? 3.0 / (20 * pi * eta * a * a2) : 3.0 / (16 * pi * eta * a * a2);
+        A[r][r] += iso;
+    }
+    bool ok = true;
+    for (int col = 0; col < nc && ok; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < nc; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (!(fabs(A[piv][col]) > 1e-300)) { ok = false; break; }
+        if (piv != col)
+            for (int q = 0; q < 2 * nc; ++q) { double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
+        const double inv = 1.0 / A[col][col];
+        for (int q = 0; q < 2 * nc; ++q) A[col][q] *= inv;
+        for (int r = 0; r < nc; ++r) {
+            if (r == col) continue;
+            const double f = A[r][col];
+            if (f != 0.0)
+                for (int q = 0; q < 2 * nc; ++q) A[r][q] -= f * A[col][q];
+        }
+    }
+    double *out = Binv + (size_t)perm[k] * nc * nc;
+    for (int r = 0; r < nc; ++r)
+        for (int q = 0; q < nc; ++q) {
+            double v = A[r][nc + q];
+            if (!ok || !isfinite(v)) {
+                const double iso = r < 3 ? 6 * pi * eta * a : r < 6 ? 8 * pi * eta * a * a2
+                                 : r < 11 ? 20 * pi * eta * a * a2 / 3 : 16 * pi * eta * a * a2 / 3;
+                v = r == q ? iso : 0.0;
+            }
+            out[r * nc + q] = v;
+        }
+}
+
+}  // namespace
+
+static int grid_for(size_t n) { size_t g = (n + 255) / 256; return (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g)); }
+
+// ---------------------------------------------------------------- preconditioner
+
+static int build_precond(se_ctx *c, int ncomp)
+{
+    cudaStream_t s = c->stream;
+    const int N = (int)c->N;
+    // radii range (sorted copy)
+    std::vector<double> rad(N);
+    SE_CUDA_CHECK(c, cudaMemcpy(rad.data(), c->b.rad, N * sizeof(double), cudaMemcpyDeviceToHost));
+    double amin = rad[0], amax = rad[0], asum = 0;
+    for (double a : rad) { amin = a < amin ? a : amin; amax = a > amax ? a : amax; asum += a; }
+    const bool mono = amax - amin <= 1e-12 * amax;
+    const double aref = asum / N;
+    const double samples[3] = {0.5 * aref, aref, 1.5 * aref};
+    const int nsamp = mono ? 1 : 3;
+
+    // single-sphere Spectral Ewald products in FP64 with the same parameters
+    se_ctx *sc = nullptr;
+    int rc = se_create(&sc, c->device, (void *)s);
+    if (rc != SE_OK) { c->err = "preconditioner: se_create failed"; return rc; }
+    rc = se_set_params(sc, c->xi, c->M, c->P, c->rc);
+    if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_PRECISION, 1);
+    if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_SIZE_MODE, c->size_mode);
+    if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_ETA, c->eta);
+    if (rc == SE_OK && c->m_user) rc = se_set_option(sc, SE_OPT_SHAPE_M, c->m_shape);
+    if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_PARTS, 2);   // wave space only (no real-space neighbours)
+    double *d = nullptr;                                         // pos(3) rad(1) x(12) y(12)
+    if (rc == SE_OK && cudaMalloc(&d, 28 * sizeof(double)) != cudaSuccess) rc = SE_ERR_NOMEM;
+    std::vector<double> blocks(3 * kNC * kNC, 0.0);
+    for (int si = 0; si < nsamp && rc == SE_OK; ++si) {
+        const double a = mono ? aref : samples[si];
+        double h[4] = {0.5 * c->L, 0.5 * c->L, 0.5 * c->L, a};
+        cudaMemcpy(d, h, 4 * sizeof(double), cudaMemcpyHostToDevice);
+        rc = se_set_config(sc, 1, c->L, d, d + 3);
+        for (int col = 0; col < ncomp && rc == SE_OK; ++col) {
+            double e[kNC] = {0};
+            e[col] = 1.0;
+            cudaMemcpyAsync(d + 4, e, kNC * sizeof(double), cudaMemcpyHostToDevice, s);
+            rc = se_mobility_apply(sc, kNC, d + 4, d + 16, SE_F64);
+            double y[kNC];
+            cudaMemcpyAsync(y, d + 16, kNC * sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            for (int r = 0; r < kNC; ++r) blocks[(size_t)si * kNC * kNC + r * kNC + col] = y[r];
+        }
+    }
+    if (rc != SE_OK) c->err = std::string("preconditioner: ") + se_last_error(sc);
+    se_destroy(sc);
+    if (d) cudaFree(d);
+    if (rc != SE_OK) return rc;
+
+    // self-image blocks minus nothing (wave + wave-self only): fit C0 + C1 a^2 + C2 a^4
+    std::vector<double> C(3 * kNC * kNC, 0.0);
+    // subtract the wave self term? No: the wave-only product of a single sphere is exactly the
+    // image interaction plus the wave sum's own self interaction; the self removal is added below.
+    for (int e = 0; e < kNC * kNC; ++e) {
+        if (mono) { C[e] = blocks[e]; continue; }
+        const double x0 = samples[0] * samples[0], x1 = samples[1] * samples[1], x2 = samples[2] * samples[2];
+        const double y0 = blocks[e], y1 = blocks[kNC * kNC + e], y2 = blocks[2 * kNC * kNC + e];
+        // quadratic through (x_i, y_i) in the variable a^2
+        const double l0 = y0 / ((x0 - x1) * (x0 - x2)), l1 = y1 / ((x1 - x0) * (x1 - x2)),
+                     l2 = y2 / ((x2 - x0) * (x2 - x1));
+        C[2 * kNC * kNC + e] = l0 + l1 + l2;
+        C[kNC * kNC + e] = -(l0 * (x1 + x2) + l1 * (x0 + x2) + l2 * (x0 + x1));
+        C[e] = l0 * x1 * x2 + l1 * x0 * x2 + l2 * x0 * x1;
+    }
+    // wave-space self removal (Eq. uf-self and its rotation / strain analogues)
+    {
+        const double xi = c->xi, eta = c->eta, x2 = xi * xi, pi32 = kPi * std::sqrt(kPi);
+        for (int r = 0; r < kNC; ++r) {
+            double c0 = 0, c1 = 0, c2 = 0;
+            if (r < 3) { c0 = 9 * xi; c1 = -10 * xi * x2; c2 = 7 * xi * x2 * x2; c0 /= 18 * pi32 * eta; c1 /= 18 * pi32 * eta; c2 /= 18 * pi32 * eta; }
+            else if (r < 6) { c0 = 5 * xi * x2 / (12 * pi32 * eta); }
+            else if (r < 11) { c0 = 25 * xi * x2 / (50 * pi32 * eta); c1 = -42 * xi * x2 * x2 / (50 * pi32 * eta); c2 = 27 * xi * x2 * x2 * x2 / (50 * pi32 * eta); }
+            if (mono) {
+                const double a2 = aref * aref;
+                C[r * kNC + r] -= c0 + c1 * a2 + c2 * a2 * a2;
+            } else {
+                C[r * kNC + r] -= c0;
+                C[kNC * kNC + r * kNC + r] -= c1;
+                C[2 * kNC * kNC + r * kNC + r] -= c2;
+            }
+        }
+    }
+    double *dC = nullptr;
+    SE_CUDA_CHECK(c, cudaMalloc(&dC, C.size() * sizeof(double)));
+    SE_CUDA_CHECK(c, cudaMemcpyAsync(dC, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (c->b.pc_inv) cudaFree(c->b.pc_inv);
+    c->b.pc_inv = nullptr;
+    if (cudaMalloc(&c->b.pc_inv, (size_t)N * ncomp * ncomp * sizeof(double)) != cudaSuccess) {
+        cudaFree(dC);
+        c->err = "preconditioner allocation failed";
+        return SE_ERR_NOMEM;
+    }
+    block_build_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->eta, c->b.rad, c->b.perm, dC, c->b.pc_inv);
+    c->launches++;
+    SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
+    cudaFree(dC);
+    c->pc_ready = true;
+    c->pc_ncomp = ncomp;
+    return SE_OK;
+}
+
+// ---------------------------------------------------------------- GMRES
+
+struct Gm {
+    se_ctx *c;
+    size_t n;
+    double *part, *hd;
+    int dots(const double *V, size_t ld, int k, const double *w, double *h_host)
+    {
+        cudaStream_t s = c->stream;
+        mdot_partial<<<dim3(kRedBlocks, k), 256, 0, s>>>(V, ld, n, w, part);
+        mdot_final<<<k, 256, 0, s>>>(part, kRedBlocks, hd);
+        c->launches += 2;
+        SE_CUDA_CHECK(c, cudaMemcpyAsync(h_host, hd, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
+        return SE_OK;
+    }
+    int axpy_multi(const double *V, size_t ld, int k, const double *h_host, double *w)
+    {
+        cudaStream_t s = c->stream;
+        SE_CUDA_CHECK(c, cudaMemcpyAsync(hd, h_host, k * sizeof(double), cudaMemcpyHostToDevice, s));
+        maxpy_kernel<<<grid_for(n), 256, 0, s>>>(V, ld, n, k, hd, w);
+        c->launches++;
+        return SE_OK;
+    }
+};
+
+}  // namespace se
+
+using namespace se;
+
+extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype, double rtol, int maxit,
+                        int precond, int *iters, double *relres)
+{
+    if (!c) return SE_ERR_ARG;
+    if (!b || !x) { c->err = "null b or x"; return SE_ERR_ARG; }
+    if (ncomp != 3 && ncomp != 6 && ncomp != 11 && ncomp != 12) { c->err = "ncomp must be 3, 6, 11 or 12"; return SE_ERR_ARG; }
+    if (dtype != SE_F32 && dtype != SE_F64) { c->err = "bad dtype"; return SE_ERR_ARG; }
+    if (!(rtol > 0) || maxit < 1) { c->err = "rtol must be > 0 and maxit >= 1"; return SE_ERR_ARG; }
+    if (precond < SE_PRECOND_NONE || precond > SE_PRECOND_LEARNED) { c->err = "bad preconditioner"; return SE_ERR_ARG; }
+    if (!c->have_config) { c->err = "se_set_config must be called first"; return SE_ERR_STATE; }
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int m = c->restart;
+    const size_t n = (size_t)c->N * ncomp;
+
+    // work space
+    if (c->b.kry) cudaFree(c->b.kry);
+    if (c->b.work64) cudaFree(c->b.work64);
+    if (c->b.red) cudaFree(c->b.red);
+    c->b.kry = c->b.work64 = c->b.red = nullptr;
+    if (cudaMalloc(&c->b.kry, (size_t)(m + 1) * n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->b.work64, 5 * n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->b.red, ((size_t)kRedBlocks * (m + 1) + 2 * (m + 1)) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "solver allocation failed";
+        return SE_ERR_NOMEM;
+    }
+    double *V = c->b.kry;
+    double *bd = c->b.work64, *xd = bd + n, *r = xd + n, *w = r + n, *z = w + n;
+    Gm gm{c, n, c->b.red, c->b.red + (size_t)kRedBlocks * (m + 1)};
+    double *yd = gm.hd + (m + 1);
+
+    if (dtype == SE_F64) {
+        SE_CUDA_CHECK(c, cudaMemcpyAsync(bd, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        SE_CUDA_CHECK(c, cudaMemcpyAsync(xd, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+        convert_kernel<float, double><<<grid_for(n), 256, 0, s>>>(n, (const float *)b, bd);
+        convert_kernel<float, double><<<grid_for(n), 256, 0, s>>>(n, (const float *)x, xd);
+        c->launches += 2;
+    }
+    if (precond != SE_PRECOND_NONE && (!c->pc_ready || c->pc_ncomp != ncomp)) {
+        int rc = build_precond(c, ncomp);
+        if (rc != SE_OK) return rc;
+    }
+    auto Pinv = [&](const double *v, double *out) {
+        if (precond == SE_PRECOND_NONE) {
+            cudaMemcpyAsync(out, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        } else {
+            block_apply_kernel<<<((int)c->N + 127) / 128, 128, 0, s>>>((int)c->N, ncomp, c->b.pc_inv, v, out);
+            c->launches++;
+        }
+    };
+
+    double bn2;
+    int rc = gm.dots(bd, 0, 1, bd, &bn2);
+    if (rc != SE_OK) return rc;
+    const double bnorm = std::sqrt(bn2);
+    int prods = 0;
+    double rel = 0.0;
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), h(m + 1), h2(m + 1), yv(m);
+    if (bnorm == 0.0) {
+        SE_CUDA_CHECK(c, cudaMemsetAsync(xd, 0, n * sizeof(double), s));
+    } else {
+        for (;;) {
+            // FP64 true residual
+            rc = se_apply_internal(c, ncomp, xd, w, SE_F64, 1);
+            if (rc != SE_OK) return rc;
+            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, bd, -1.0, w, r);
+            c->launches++;
+            double rn2;
+            rc = gm.dots(r, 0, 1, r, &rn2);
+            if (rc != SE_OK) return rc;
+            const double beta = std::sqrt(rn2);
+            rel = beta / bnorm;
+            if (!std::isfinite(rel)) { c->err = "non-finite residual"; return SE_ERR_NONFINITE; }
+            if (rel <= rtol || prods >= maxit) break;
+            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0 / beta, r, 0.0, r, V);
+            c->launches++;
+            std::fill(g.begin(), g.end(), 0.0);
+            g[0] = beta;
+            int k = 0;
+            for (int j = 0; j < m && prods < maxit; ++j) {
+                Pinv(V + (size_t)j * n, z);
+                rc = se_apply_internal(c, ncomp, z, w, SE_F64, c->precision);
+                if (rc != SE_OK) return rc;
+                ++prods;
+                // classical Gram-Schmidt, twice
+                if ((rc = gm.dots(V, n, j + 1, w, h.data())) != SE_OK) return rc;
+                if ((rc = gm.axpy_multi(V, n, j + 1, h.data(), w)) != SE_OK) return rc;
+                if ((rc = gm.dots(V, n, j + 1, w, h2.data())) != SE_OK) return rc;
+                if ((rc = gm.axpy_multi(V, n, j + 1, h2.data(), w)) != SE_OK) return rc;
+                double wn2;
+                if ((rc = gm.dots(w, 0, 1, w, &wn2)) != SE_OK) return rc;
+                const double hn = std::sqrt(wn2);
+                for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i] + h2[i];
+                H[(size_t)(j + 1) * m + j] = hn;
+                // apply the previous Givens rotations to column j, then a new one
+                for (int i = 0; i < j; ++i) {
+                    const double a0 = H[(size_t)i * m + j], a1 = H[(size_t)(i + 1) * m + j];
+                    H[(size_t)i * m + j] = cs[i] * a0 + sn[i] * a1;
+                    H[(size_t)(i + 1) * m + j] = -sn[i] * a0 + cs[i] * a1;
+                }
+                const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
+                const double den = std::hypot(a0, a1);
+                cs[j] = den > 0 ? a0 / den : 1.0;
+                sn[j] = den > 0 ? a1 / den : 0.0;
+                H[(size_t)j * m + j] = den;
+                H[(size_t)(j + 1) * m + j] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                k = j + 1;
+                if (hn > 0 && j + 1 < m + 1) {
+                    axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0 / hn, w, 0.0, w, V + (size_t)(j + 1) * n);
+                    c->launches++;
+                }
+                if (std::fabs(g[j + 1]) <= 0.3 * rtol * bnorm || hn == 0.0) break;
+            }
+            // y = H^{-1} g (upper triangular), x += P^{-1} V y
+            for (int i = k - 1; i >= 0; --i) {
+                double sacc = g[i];
+                for (int q = i + 1; q < k; ++q) sacc -= H[(size_t)i * m + q] * yv[q];
+                yv[i] = sacc / H[(size_t)i * m + i];
+            }
+            SE_CUDA_CHECK(c, cudaMemcpyAsync(yd, yv.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+            combine_kernel<<<grid_for(n), 256, 0, s>>>(V, n, n, k, yd, w);
+            c->launches++;
+            Pinv(w, z);
+            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, xd, 1.0, z, xd);
+            c->launches++;
+        }
+    }
+    if (dtype == SE_F64) {
+        SE_CUDA_CHECK(c, cudaMemcpyAsync(x, xd, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+        convert_kernel<double, float><<<grid_for(n), 256, 0, s>>>(n, xd, (float *)x);
+        c->launches++;
+    }
+    SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
+    if (iters) *iters = prods;
+    if (relres) *relres = rel;
+    if (rel > rtol) {
+        c->err = "GMRES did not reach rtol within maxit products";
+        return SE_ERR_NOT_CONVERGED;
+    }
+    return SE_OK;
+}

@@ -1,0 +1,727 @@
+// Wave-space part of the grand-mobility product by the Spectral Ewald method
+// (Sec. 3.1-3.2): Gaussian spreading (Eq. grid-space), forward 3D FFT, k-space
+// scaling (Eq. wave-result) fused into the last forward stage together with the
+// first inverse stage, inverse 3D FFT, and the trapezoid-rule gather
+// (Eq. parseval-sum, Eq. parseval-sum-2).
+//
+// Grid units: u = x M / L, so grid points are integers; the Gaussian of Eq. shape
+// is g(s) = exp(-alpha |s|^2) with alpha = 2 m^2 / P^2 (Eq. theta-param: the edge
+// value at |s| = P/2 is exp(-m^2/2)); d/dx = kappa d/ds with kappa = M / L.
+//
+// Per particle j the spread grid holds the force density of its multipoles
+//   H = F (1 + a^2 Lap/6) g + 1/2 grad g x T - S . grad (1 + a^2 Lap/10) g,   H_src = S_tr g
+// (Eq. grid-space extended to torques and stresslets via Eq. mul-expand).
+// With Hhat the forward DFT and q the integer wave vector, k = 2 pi q / L:
+//   Ghat = c exp(-k^2/(4 xi^2) + 2 pi^2 q^2/(alpha M^2)) [ Phi (I - k k/k^2) Hhat
+//          + i k/(4 k^2) Hhat_src ],  Phi = (1 + k^2/(4 xi^2))/k^2,  c = (alpha/pi)^3/(eta V)
+// (Eq. wave-result: the two exp(-theta q^2/(8 xi^2)) factors of Eq. rp-wave-tq are
+// the transforms of the spread and gather Gaussians, exp(theta q^2/(4 xi^2)) undoes
+// them; the source term is the wave part of Eq. source-split with Q = -grad phi/(16 pi eta)),
+// and the pressure (Eq. pres-multi-expans, wave part) scaled by 3/(4 eta) (Eq. faxen-p):
+//   Ghat_p = (3/4) c exp(...) i k.Hhat / k^2.
+// Hybrid approach (Sec. 3.2): the target Faxen Laplacian is applied in wave space,
+// Ghat'' = -k^2 Ghat, and gathered with weight a_i^2/6 (U) or a_i^2/10 (E).
+// Real-space approach: the target Laplacian acts on the gather weights instead.
+// Nyquist planes and q = 0 are set to zero.
+#include <cstdio>
+
+#include "se_fft.cuh"
+#include "se_internal.cuh"
+
+namespace se {
+
+namespace {
+
+constexpr int kEPT = 8;    // FFT elements per thread and stage
+constexpr int kFftMaxThreads = 512;
+
+template <typename T> struct V4;
+template <> struct V4<float> { using t = float4; };
+template <> struct V4<double> { using t = double4_32a; };
+
+__device__ __forceinline__ int wrapi(int i, int M) { return i >= M ? i - M : (i < 0 ? i + M : i); }
+
+// S tensor (xx, yy, zz, xy, xz, yz) from coordinates on the orthonormal basis
+template <typename T>
+__device__ __forceinline__ void stresslet_tensor(const T *s, T S[6])
+{
+    const T r2 = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637;
+    S[0] = r2 * s[0] - r6 * s[1];
+    S[1] = -r2 * s[0] - r6 * s[1];
+    S[2] = 2 * r6 * s[1];
+    S[3] = r2 * s[2];
+    S[4] = r2 * s[3];
+    S[5] = r2 * s[4];
+}
+
+// ---------------------------------------------------------------- support setup
+
+// Per particle (cell order): first support point b (wrapped), offset s0 = b - u of
+// that point from the particle, and the 1D Gaussian weights g(s0 + i), i < P, by
+// fast Gaussian gridding (Eq. fgg-exp) centred on the nearest grid point:
+//   g(delta + j) = exp(-alpha delta^2) exp(-2 alpha delta)^j exp(-alpha j^2).
+template <typename T>
+__global__ void support_kernel(int N, SeParams p, const double *pos, const double *e3 /*[2P+1], j=-P..P*/,
+                               int *base, T *s0out, T *w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int M = p.M, P = p.P;
+    for (int d = 0; d < 3; ++d) {
+        double u = pos[3 * i + d] * p.kappa;
+        int b = (int)floor(u - 0.5 * P) + 1;
+        double s0 = b - u;                       // in (-P/2, -P/2 + 1]
+        int ic = (int)floor(-s0 + 0.5);          // index of the point nearest the particle
+        double delta = s0 + ic;                  // in [-1/2, 1/2]
+        double e1 = exp(-p.alpha * delta * delta), e2 = exp(-2.0 * p.alpha * delta);
+        double pw = 1.0;
+        for (int j = 0; ic + j < P; ++j) {       // points at and above the centre
+            w[((size_t)i * 3 + d) * P + ic + j] = (T)(e1 * pw * e3[P + j]);
+            pw *= e2;
+        }
+        pw = 1.0;
+        for (int j = 1; ic - j >= 0; ++j) {      // points below the centre
+            pw /= e2;
+            w[((size_t)i * 3 + d) * P + ic - j] = (T)(e1 * pw * e3[P - j]);
+        }
+        b %= M;
+        if (b < 0) b += M;
+        base[3 * i + d] = b;
+        s0out[3 * i + d] = (T)s0;
+    }
+}
+
+// ---------------------------------------------------------------- spreading
+
+// One CTA per kTile^3 tile of the grid.  It visits the particles whose support
+// start lies in the bins that can reach the tile, accumulates their contributions
+// in shared memory (each warp spreads one particle over the intersection of its
+// support with the tile) and writes the tile once: no global atomics.
+template <typename T, int NCOMP>
+__global__ void __launch_bounds__(256) spread_kernel(SeParams p, const int *tile_start,
+                                                     const int *tile_perm, const int *base,
+                                                     const T *s0g, const T *wg, const double *rad,
+                                                     const T *xs, T *grid)
+{
+    constexpr int TT = kTile;
+    __shared__ T acc[TT * TT * TT * 4];
+    const int M = p.M, P = p.P, nt = p.ntile;
+    const int tile = blockIdx.x;
+    const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
+    const int t0x = tx * TT, t0y = ty * TT, t0z = tz * TT;
+    for (int e = threadIdx.x; e < TT * TT * TT * 4; e += blockDim.x) acc[e] = 0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int nbin = (P - 1 + TT - 1) / TT + 1;
+    const T alpha = (T)p.alpha, kap = (T)p.kappa;
+    const T akap = alpha * kap;
+
+    for (int bz = 0; bz < nbin; ++bz)
+        for (int by = 0; by < nbin; ++by)
+            for (int bx = 0; bx < nbin; ++bx) {
+                const int bin = (wrapi(tz - bz, nt) * nt + wrapi(ty - by, nt)) * nt + wrapi(tx - bx, nt);
+                const int qs = tile_start[bin], qe = tile_start[bin + 1];
+                for (int q = qs + warp; q < qe; q += nwarp) {
+                    const int i = tile_perm[q];
+                    int o[3], lo[3], hi[3];
+                    const int t0[3] = {t0x, t0y, t0z};
+                    bool empty = false;
+                    for (int d = 0; d < 3; ++d) {
+                        int od = t0[d] - base[3 * i + d];
+                        od = wrapi(od, M);
+                        if (od >= P) od -= M;            // tile starts before the support
+                        o[d] = od;
+                        lo[d] = max(0, -od);
+                        hi[d] = min(TT, P - od);
+                        empty |= lo[d] >= hi[d];
+                    }
+                    if (empty) continue;
+                    const T *xi = xs + (size_t)i * kNC;
+                    const T a = (T)rad[i];
+                    const T a2k2 = a * a * kap * kap;
+                    const T A0 = 1 - a2k2 * alpha, A1 = (T)(2.0 / 3.0) * a2k2 * alpha * alpha;
+                    const T B0 = 2 * kap * alpha * (1 - a2k2 * alpha);
+                    const T B1 = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
+                    const T F0 = xi[0], F1 = xi[1], F2 = xi[2];
+                    T T0 = 0, T1 = 0, T2 = 0, S[6] = {0, 0, 0, 0, 0, 0}, Str = 0;
+                    if constexpr (NCOMP >= 6) { T0 = xi[3]; T1 = xi[4]; T2 = xi[5]; }
+                    if constexpr (NCOMP >= 11) stresslet_tensor(xi + 6, S);
+                    if constexpr (NCOMP >= 12) Str = xi[11];
+                    const T sx0 = s0g[3 * i], sy0 = s0g[3 * i + 1], sz0 = s0g[3 * i + 2];
+                    const T *wx = wg + (size_t)i * 3 * P, *wy = wx + P, *wz = wy + P;
+                    const int nz = hi[2] - lo[2];
+                    T gzl = 0, szl = 0;
+                    if (lane < nz) {
+                        int iz = o[2] + lo[2] + lane;
+                        gzl = wz[iz];
+                        szl = sz0 + iz;
+                    }
+                    const int nx = hi[0] - lo[0], ny = hi[1] - lo[1], nxy = nx * ny;
+                    for (int it = 0; it < nxy; it += 32) {
+                        const int c = it + lane;
+                        const bool act = c < nxy;
+                        const int cy = act ? c / nx : 0, cx = act ? c - cy * nx : 0;
+                        const int tlx = lo[0] + cx, tly = lo[1] + cy;
+                        const int ix = o[0] + tlx, iy = o[1] + tly;
+                        const T gxy = act ? wx[ix] * wy[iy] : (T)0;
+                        const T sx = sx0 + ix, sy = sy0 + iy;
+                        for (int k = 0; k < nz; ++k) {
+                            const T gz = __shfl_sync(0xffffffffu, gzl, k);
+                            const T sz = __shfl_sync(0xffffffffu, szl, k);
+                            if (!act) continue;
+                            const T g = gxy * gz;
+                            const T s2 = sx * sx + sy * sy + sz * sz;
+                            const T cF = A0 + A1 * s2;
+                            T h0 = cF * F0, h1 = cF * F1, h2 = cF * F2;
+                            if constexpr (NCOMP >= 6) {
+                                // 1/2 grad g x T = -alpha kappa g (s x T)
+                                h0 -= akap * (sy * T2 - sz * T1);
+                                h1 -= akap * (sz * T0 - sx * T2);
+                                h2 -= akap * (sx * T1 - sy * T0);
+                            }
+                            if constexpr (NCOMP >= 11) {
+                                // -S . grad (1 + a^2 Lap/10) g = g (B0 + B1 s^2) S.s
+                                const T cS = B0 + B1 * s2;
+                                h0 += cS * (S[0] * sx + S[3] * sy + S[4] * sz);
+                                h1 += cS * (S[3] * sx + S[1] * sy + S[5] * sz);
+                                h2 += cS * (S[4] * sx + S[5] * sy + S[2] * sz);
+                            }
+                            T *dst = acc + (((lo[2] + k) * TT + tly) * TT + tlx) * 4;
+                            atomicAdd(dst + 0, g * h0);
+                            atomicAdd(dst + 1, g * h1);
+                            atomicAdd(dst + 2, g * h2);
+                            if constexpr (NCOMP >= 12) atomicAdd(dst + 3, g * Str);
+                        }
+                    }
+                }
+            }
+    __syncthreads();
+    for (int e = threadIdx.x; e < TT * TT * TT; e += blockDim.x) {
+        const int lx = e % TT, ly = (e / TT) % TT, lz = e / (TT * TT);
+        const size_t g = (((size_t)(t0z + lz) * M + (t0y + ly)) * M + (t0x + lx)) * 4;
+        typename V4<T>::t v;
+        v.x = acc[e * 4 + 0];
+        v.y = acc[e * 4 + 1];
+        v.z = acc[e * 4 + 2];
+        v.w = acc[e * 4 + 3];
+        *reinterpret_cast<typename V4<T>::t *>(grid + g) = v;
+    }
+}
+
+// ---------------------------------------------------------------- FFT passes
+
+// x pass, forward: each grid line (y, z) carries 4 real series packed as two complex
+// lines (H0 + i H1, H2 + i H3); after the transform the four half spectra
+// q = 0..M/2 are separated using Z(-q) = conj(Z(q)) of real data.
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_x_fwd(FftPlan plan, const typename C2<T>::t *twg, const T *grid,
+                          typename C2<T>::t *spec, int LX)
+{
+    using T2 = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2 *tw = reinterpret_cast<T2 *>(smraw);
+    const int M = plan.M, Mh = M / 2 + 1;
+    T2 *buf = tw + M;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
+    const size_t gl0 = (size_t)blockIdx.x * LX;
+    const int nl = (int)min((size_t)LX, (size_t)M * M - gl0);
+    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
+        const int gl = e / M, x = e - gl * M;
+        typename V4<T>::t v = *reinterpret_cast<const typename V4<T>::t *>(grid + ((gl0 + gl) * M + x) * 4);
+        buf[(2 * gl) * M + x] = T2{v.x, v.y};
+        buf[(2 * gl + 1) * M + x] = T2{v.z, v.w};
+    }
+    __syncthreads();
+    fft_lines<kEPT>(buf, 2 * nl, M, plan, tw, false);
+    for (int e = threadIdx.x; e < nl * Mh * 4; e += blockDim.x) {
+        const int c = e & 3, q = (e >> 2) % Mh, gl = (e >> 2) / Mh;
+        const T2 z = buf[(2 * gl + (c >> 1)) * M + q];
+        const T2 zm = buf[(2 * gl + (c >> 1)) * M + (q == 0 ? 0 : M - q)];
+        T2 r;
+        if ((c & 1) == 0) r = T2{(T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y)};
+        else r = T2{(T)0.5 * (z.y + zm.y), (T)-0.5 * (z.x - zm.x)};
+        spec[((gl0 + gl) * Mh + q) * 4 + c] = r;
+    }
+}
+
+// strided pass (y axis): lines of element stride `es` for LB consecutive q and all C
+// components, transformed in place.
+template <typename T>
+__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_strided(FftPlan plan, const typename C2<T>::t *twg, typename C2<T>::t *data,
+                            int C, int LB, size_t es, size_t os, int inv)
+{
+    using T2 = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2 *tw = reinterpret_cast<T2 *>(smraw);
+    const int M = plan.M, Mh = M / 2 + 1, ls = M + 1;
+    T2 *buf = tw + M;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
+    const int q0 = blockIdx.x * LB, nq = min(LB, Mh - q0), nl = nq * C;
+    const size_t base = (size_t)blockIdx.y * os + (size_t)q0 * C;
+    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
+        const int l = e % nl, el = e / nl;
+        buf[l * ls + el] = data[base + el * es + l];
+    }
+    __syncthreads();
+    fft_lines<kEPT>(buf, nl, ls, plan, tw, inv != 0);
+    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
+        const int l = e % nl, el = e / nl;
+        data[base + el * es + l] = buf[l * ls + el];
+    }
+}
+
+// z pass: forward transform of the 4 spectra, k-space scaling (see the file
+// header), inverse transform of the CO output spectra.  Lines are stored
+// component-major (line = c * nq + q) so inputs and outputs share the buffer.
+template <typename T, int CO>
+__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_z_scale(FftPlan plan, SeParams p, const typename C2<T>::t *twg,
+                            const typename C2<T>::t *specf, typename C2<T>::t *speco, int LB, T cnorm)
+{
+    using T2 = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2 *tw = reinterpret_cast<T2 *>(smraw);
+    const int M = plan.M, Mh = M / 2 + 1, ls = M + 1;
+    T2 *buf = tw + M;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
+    const int y = blockIdx.y;
+    const int q0 = blockIdx.x * LB, nq = min(LB, Mh - q0);
+    const size_t zs = (size_t)M * Mh;               // z stride in q units
+    for (int e = threadIdx.x; e < 4 * nq * M; e += blockDim.x) {
+        const int lm = e % (4 * nq), z = e / (4 * nq);
+        const int q = lm >> 2, c = lm & 3;
+        buf[(c * nq + q) * ls + z] = specf[((size_t)z * zs + (size_t)y * Mh + q0 + q) * 4 + c];
+    }
+    __syncthreads();
+    fft_lines<kEPT>(buf, 4 * nq, ls, plan, tw, false);
+
+    const int ys = y <= M / 2 ? y : y - M;
+    const T twopiL = (T)(2.0 * kPi / p.L);
+    const T i4x2 = (T)(0.25 / (p.xi * p.xi));
+    const T ecoef = (T)(2.0 * kPi * kPi / (p.alpha * (double)M * M));
+    for (int e = threadIdx.x; e < nq * M; e += blockDim.x) {
+        const int q = e % nq, z = e / nq;
+        const int qx = q0 + q, zsn = z <= M / 2 ? z : z - M;
+        T2 o[CO];
+#pragma unroll
+        for (int c = 0; c < CO; ++c) o[c] = T2{0, 0};
+        const bool zero = (qx == 0 && ys == 0 && zsn == 0) || 2 * qx == M || 2 * ys == M || 2 * zsn == M;
+        if (!zero) {
+            const T kx = twopiL * qx, ky = twopiL * ys, kz = twopiL * zsn;
+            const T k2 = kx * kx + ky * ky + kz * kz;
+            const T q2 = (T)(qx * qx + ys * ys + zsn * zsn);
+            const T E = exp(-k2 * i4x2 + ecoef * q2) * cnorm;
+            const T ik2 = 1 / k2;
+            const T Phi = E * (1 + k2 * i4x2) * ik2;
+            const T2 H0 = buf[(0 * nq + q) * ls + z], H1 = buf[(1 * nq + q) * ls + z];
+            const T2 H2 = buf[(2 * nq + q) * ls + z], Hs = buf[(3 * nq + q) * ls + z];
+            const T2 kH = T2{kx * H0.x + ky * H1.x + kz * H2.x, kx * H0.y + ky * H1.y + kz * H2.y};
+            const T2 pr = T2{kH.x * ik2, kH.y * ik2};
+            // This FFT's forward transform carries exp(-i q.n), so Hhat(q) holds the moments'
+            // structure factor at -k: the odd (i k) factors below are taken at -k.
+            const T sq = -E * (T)0.25 * ik2;           // -i k/(4 k^2) E H_src
+            const T2 iHs = T2{-Hs.y * sq, Hs.x * sq};
+            o[0] = T2{Phi * (H0.x - kx * pr.x) + kx * iHs.x, Phi * (H0.y - kx * pr.y) + kx * iHs.y};
+            o[1] = T2{Phi * (H1.x - ky * pr.x) + ky * iHs.x, Phi * (H1.y - ky * pr.y) + ky * iHs.y};
+            o[2] = T2{Phi * (H2.x - kz * pr.x) + kz * iHs.x, Phi * (H2.y - kz * pr.y) + kz * iHs.y};
+            const T cp = (T)-0.75 * E;                  // -(3/4) c E i k.H / k^2
+            const T2 op = T2{-cp * pr.y, cp * pr.x};
+            if constexpr (CO == 8) {
+                o[3] = T2{-k2 * o[0].x, -k2 * o[0].y};
+                o[4] = T2{-k2 * o[1].x, -k2 * o[1].y};
+                o[5] = T2{-k2 * o[2].x, -k2 * o[2].y};
+                o[6] = op;
+            } else {
+                o[3] = op;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CO; ++c) buf[(c * nq + q) * ls + z] = o[c];
+    }
+    __syncthreads();
+    fft_lines<kEPT>(buf, CO * nq, ls, plan, tw, true);
+    for (int e = threadIdx.x; e < CO * nq * M; e += blockDim.x) {
+        const int lm = e % (CO * nq), z = e / (CO * nq);
+        const int q = lm / CO, c = lm - q * CO;
+        speco[((size_t)z * zs + (size_t)y * Mh + q0 + q) * CO + c] = buf[(c * nq + q) * ls + z];
+    }
+}
+
+// x pass, inverse: pairs of half spectra are recombined into full complex lines
+// Z = A + i B (A(M-q) = conj A(q) for real output), transformed, and written as the
+// real grids A, B interleaved per point.
+template <typename T, int CO>
+__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_x_inv(FftPlan plan, const typename C2<T>::t *twg, const typename C2<T>::t *speco,
+                          T *grid, int LX)
+{
+    using T2 = typename C2<T>::t;
+    constexpr int NP = CO / 2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T2 *tw = reinterpret_cast<T2 *>(smraw);
+    const int M = plan.M, Mh = M / 2 + 1;
+    T2 *buf = tw + M;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
+    const size_t gl0 = (size_t)blockIdx.x * LX;
+    const int nl = (int)min((size_t)LX, (size_t)M * M - gl0);
+    for (int e = threadIdx.x; e < nl * NP * M; e += blockDim.x) {
+        const int x = e % M, pl = e / M, gl = pl / NP, pp = pl - gl * NP;
+        const T2 *src = speco + (gl0 + gl) * Mh * CO;
+        T2 z;
+        if (x <= M / 2) {
+            const T2 A = src[x * CO + 2 * pp], B = src[x * CO + 2 * pp + 1];
+            z = T2{A.x - B.y, A.y + B.x};
+        } else {
+            const T2 A = src[(M - x) * CO + 2 * pp], B = src[(M - x) * CO + 2 * pp + 1];
+            z = T2{A.x + B.y, -A.y + B.x};
+        }
+        buf[pl * M + x] = z;
+    }
+    __syncthreads();
+    fft_lines<kEPT>(buf, nl * NP, M, plan, tw, true);
+    for (int e = threadIdx.x; e < nl * M * CO; e += blockDim.x) {
+        const int c = e % CO, x = (e / CO) % M, gl = e / (CO * M);
+        const T2 z = buf[(gl * NP + (c >> 1)) * M + x];
+        grid[((gl0 + gl) * M + x) * CO + c] = (c & 1) ? z.y : z.x;
+    }
+}
+
+// ---------------------------------------------------------------- gather + combine
+
+template <typename T>
+__device__ __forceinline__ void kahan_add(T &sum, T &comp, T v)
+{
+    const T y = v - comp;
+    const T t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// One warp per particle: trapezoid-rule convolution of the gathered grids with the
+// particle's Gaussian (and its derivatives) over the P^3 support, then
+// y = real + wave + self, written in the caller's order and dtype.
+// Accumulators: U(3), s x v (3), sym(s (x) w) (6: xx yy zz xy xz yz), p (1).
+template <typename T, typename TO, int CO, int NCOMP>
+__global__ void __launch_bounds__(256) gather_kernel(SeParams p, int N, const int *base, const T *s0g,
+                                                     const T *wg, const double *rad, const int *perm,
+                                                     const T *grid, const T *xs, const T *yreal, TO *y,
+                                                     int ncomp_out, int with_wave, int with_self)
+{
+    constexpr int NA = 13;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= N) return;
+    const int M = p.M, P = p.P;
+    const double ad = rad[i];
+    const T a = (T)ad;
+    T acc[NA];
+#pragma unroll
+    for (int c = 0; c < NA; ++c) acc[c] = 0;
+    const T alpha = (T)p.alpha, kap = (T)p.kappa;
+    if (with_wave) {
+        T cmp[NA];
+#pragma unroll
+        for (int c = 0; c < NA; ++c) cmp[c] = 0;
+        const int bx = base[3 * i], by = base[3 * i + 1], bz = base[3 * i + 2];
+        const T sx0 = s0g[3 * i], sy0 = s0g[3 * i + 1], sz0 = s0g[3 * i + 2];
+        const T *wx = wg + (size_t)i * 3 * P, *wy = wx + P, *wz = wy + P;
+        const T gzl = lane < P ? wz[lane] : (T)0, szl = sz0 + lane;
+        const int zl = wrapi(bz + lane, M);
+        const T a2k2 = a * a * kap * kap;
+        // real-space approach weights (Faxen Laplacian on the Gaussian)
+        const T A0 = 1 - a2k2 * alpha, A1 = (T)(2.0 / 3.0) * a2k2 * alpha * alpha;
+        const T B0 = 2 * kap * alpha * (1 - a2k2 * alpha);
+        const T B1 = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
+        const T c6 = a * a / 6, c10 = a * a / 10;
+        for (int it = 0; it < P * P; it += 32) {
+            const int c = it + lane;
+            const bool act = c < P * P;
+            const int cy = act ? c / P : 0, cx = act ? c - cy * P : 0;
+            const int gx = wrapi(bx + cx, M), gy = wrapi(by + cy, M);
+            const T gxy = act ? wx[cx] * wy[cy] : (T)0;
+            const T sx = sx0 + cx, sy = sy0 + cy;
+            T col[NA];
+#pragma unroll
+            for (int cc = 0; cc < NA; ++cc) col[cc] = 0;
+            for (int k = 0; k < P; ++k) {
+                const T gz = __shfl_sync(0xffffffffu, gzl, k);
+                const T sz = __shfl_sync(0xffffffffu, szl, k);
+                const int gzi = __shfl_sync(0xffffffffu, zl, k);
+                if (!act) continue;
+                const T *gp = grid + (((size_t)gzi * M + gy) * M + gx) * CO;
+                const T g = gxy * gz;
+                if constexpr (CO == 8) {
+                    const typename V4<T>::t u0 = *reinterpret_cast<const typename V4<T>::t *>(gp);
+                    const typename V4<T>::t u1 = *reinterpret_cast<const typename V4<T>::t *>(gp + 4);
+                    // u0 = (v0 v1 v2 v''0), u1 = (v''1 v''2 p -)
+                    const T v0 = u0.x, v1 = u0.y, v2 = u0.z;
+                    const T w0 = u0.w, w1 = u1.x, w2 = u1.y;
+                    col[0] += g * (v0 + c6 * w0);
+                    col[1] += g * (v1 + c6 * w1);
+                    col[2] += g * (v2 + c6 * w2);
+                    if constexpr (NCOMP >= 6) {
+                        const T gx_ = g * sx, gy_ = g * sy, gz_ = g * sz;
+                        col[3] += gy_ * v2 - gz_ * v1;
+                        col[4] += gz_ * v0 - gx_ * v2;
+                        col[5] += gx_ * v1 - gy_ * v0;
+                        if constexpr (NCOMP >= 11) {
+                            const T e0 = v0 + c10 * w0, e1 = v1 + c10 * w1, e2 = v2 + c10 * w2;
+                            col[6] += gx_ * e0;
+                            col[7] += gy_ * e1;
+                            col[8] += gz_ * e2;
+                            col[9] += gx_ * e1 + gy_ * e0;
+                            col[10] += gx_ * e2 + gz_ * e0;
+                            col[11] += gy_ * e2 + gz_ * e1;
+                        }
+                    }
+                    if constexpr (NCOMP >= 12) col[12] += g * u1.z;
+                } else {
+                    const typename V4<T>::t u0 = *reinterpret_cast<const typename V4<T>::t *>(gp);
+                    const T v0 = u0.x, v1 = u0.y, v2 = u0.z;
+                    const T s2 = sx * sx + sy * sy + sz * sz;
+                    const T gu = g * (A0 + A1 * s2);
+                    col[0] += gu * v0;
+                    col[1] += gu * v1;
+                    col[2] += gu * v2;
+                    if constexpr (NCOMP >= 6) {
+                        const T gx_ = g * sx, gy_ = g * sy, gz_ = g * sz;
+                        col[3] += gy_ * v2 - gz_ * v1;
+                        col[4] += gz_ * v0 - gx_ * v2;
+                        col[5] += gx_ * v1 - gy_ * v0;
+                        if constexpr (NCOMP >= 11) {
+                            const T ge = g * (B0 + B1 * s2);
+                            const T ex = ge * sx, ey = ge * sy, ez = ge * sz;
+                            col[6] += ex * v0;
+                            col[7] += ey * v1;
+                            col[8] += ez * v2;
+                            col[9] += ex * v1 + ey * v0;
+                            col[10] += ex * v2 + ez * v0;
+                            col[11] += ey * v2 + ez * v1;
+                        }
+                    }
+                    if constexpr (NCOMP >= 12) col[12] += g * u0.w;
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < NA; ++cc) kahan_add(acc[cc], cmp[cc], col[cc]);
+        }
+#pragma unroll
+        for (int cc = 0; cc < NA; ++cc) {
+            T v = acc[cc] - cmp[cc];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            acc[cc] = v;
+        }
+    }
+    if (lane != 0) return;
+    // finalise the wave part: Omega = alpha kappa sum g (s x v); E from the symmetric sums
+    T out[kNC];
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = acc[2];
+    const T ak = alpha * kap;
+    out[3] = ak * acc[3];
+    out[4] = ak * acc[4];
+    out[5] = ak * acc[5];
+    {
+        // symmetric tensor A (xx yy zz xy xz yz) with off-diagonals stored as 2*A_xy
+        const T f = CO == 8 ? 2 * alpha * kap : (T)1;
+        const T Axx = f * acc[6], Ayy = f * acc[7], Azz = f * acc[8];
+        const T Axy = f * acc[9] * (T)0.5, Axz = f * acc[10] * (T)0.5, Ayz = f * acc[11] * (T)0.5;
+        const T r2 = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637, s2 = (T)1.41421356237309504880;
+        out[6] = r2 * (Axx - Ayy);
+        out[7] = r6 * (2 * Azz - Axx - Ayy);
+        out[8] = s2 * Axy;
+        out[9] = s2 * Axz;
+        out[10] = s2 * Ayz;
+    }
+    out[11] = acc[12];
+    // self: isolated sphere (Eqs. faxen-f/t/s/p) minus the self term in the wave sum (Eq. uf-self)
+    const T *xi_ = xs + (size_t)i * kNC;
+    const T *yr = yreal + (size_t)i * kNC;
+    double sU = 0, sO = 0, sE = 0, sP = 0;
+    if (with_self) {
+        const double xi = p.xi, eta = p.eta, a2 = ad * ad, x2 = xi * xi, pi32 = kPi * sqrt(kPi);
+        sU = 1.0 / (6 * kPi * eta * ad) - xi * (9 - 10 * a2 * x2 + 7 * a2 * a2 * x2 * x2) / (18 * pi32 * eta);
+        sO = 1.0 / (8 * kPi * eta * ad * a2) - 5 * xi * x2 / (12 * pi32 * eta);
+        sE = 3.0 / (20 * kPi * eta * ad * a2) - xi * x2 * (25 - 42 * a2 * x2 + 27 * a2 * a2 * x2 * x2) / (50 * pi32 * eta);
+        sP = 3.0 / (16 * kPi * eta * ad * a2);
+    }
+    TO *yo = y + (size_t)perm[i] * ncomp_out;
+    for (int c = 0; c < ncomp_out; ++c) {
+        const double sc = c < 3 ? sU : (c < 6 ? sO : (c < 11 ? sE : sP));
+        yo[c] = (TO)((double)out[c] + (double)yr[c] + sc * (double)xi_[c]);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host launchers
+
+static int fft_threads(int elements)
+{
+    int t = (elements + kEPT - 1) / kEPT;
+    t = (t + 31) / 32 * 32;
+    return t < 64 ? 64 : (t > kFftMaxThreads ? kFftMaxThreads : t);
+}
+
+void make_twiddles(se_ctx *c, int prec)
+{
+    const int M = c->M;
+    if (prec == 1) {
+        std::vector<double2> h(M);
+        for (int k = 0; k < M; ++k) h[k] = double2{cos(2 * kPi * k / M), -sin(2 * kPi * k / M)};
+        cudaMemcpyAsync(c->b.tw[1], h.data(), M * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
+    } else {
+        std::vector<float2> h(M);
+        for (int k = 0; k < M; ++k) h[k] = float2{(float)cos(2 * kPi * k / M), (float)-sin(2 * kPi * k / M)};
+        cudaMemcpyAsync(c->b.tw[0], h.data(), M * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+    }
+    cudaStreamSynchronize(c->stream);
+}
+
+template <typename T>
+void setup_support(se_ctx *c, cudaStream_t s)
+{
+    SeParams p = make_params(c);
+    std::vector<double> e3(2 * c->P + 1);
+    for (int j = -c->P; j <= c->P; ++j) e3[j + c->P] = exp(-p.alpha * j * j);
+    double *de3 = nullptr;
+    cudaMalloc(&de3, e3.size() * sizeof(double));
+    cudaMemcpyAsync(de3, e3.data(), e3.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    const int N = (int)c->N;
+    support_kernel<T><<<(N + 127) / 128, 128, 0, s>>>(N, p, c->b.pos, de3, c->b.sup_base, (T *)c->b.sup_s0[pix<T>()],
+                                                       (T *)c->b.sup_w[pix<T>()]);
+    c->launches++;
+    cudaStreamSynchronize(s);
+    cudaFree(de3);
+}
+
+template <typename T>
+static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_t s, int ncomp)
+{
+    const int nt = p.ntile, ntiles = nt * nt * nt;
+    auto args = [&](auto kern) {
+        kern<<<ntiles, 256, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base, (const T *)c->b.sup_s0[pix<T>()],
+                                     (const T *)c->b.sup_w[pix<T>()], c->b.rad, xs, (T *)c->b.grid_f[pix<T>()]);
+    };
+    if (ncomp <= 3) args(spread_kernel<T, 3>);
+    else if (ncomp <= 6) args(spread_kernel<T, 6>);
+    else if (ncomp <= 11) args(spread_kernel<T, 11>);
+    else args(spread_kernel<T, 12>);
+    c->launches++;
+}
+
+// lines per CTA so that one CTA holds about `budget` complex elements
+static int lines_for(int budget, int per_line)
+{
+    int l = budget / per_line;
+    return l < 1 ? 1 : l;
+}
+
+template <typename T>
+void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp)
+{
+    using T2 = typename C2<T>::t;
+    const SeParams p = make_params(c);
+    const int M = c->M, Mh = M / 2 + 1;
+    const int budget = kEPT * kFftMaxThreads;              // complex elements per CTA
+    const T2 *tw = (const T2 *)c->b.tw[pix<T>()];
+    T2 *sf = (T2 *)c->b.spec_f[pix<T>()], *so = (T2 *)c->b.spec_o[pix<T>()];
+    const int CO = p.hybrid ? 8 : 4;
+
+    launch_spread<T>(c, p, xs, s, ncomp);
+
+    {   // x forward
+        const int LX = lines_for(budget, 2 * M);
+        const int nl = 2 * LX * M;
+        const size_t smem = (size_t)(nl + M) * sizeof(T2);
+        const int blocks = (M * M + LX - 1) / LX;
+        cudaFuncSetAttribute(fft_x_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fft_x_fwd<T><<<blocks, fft_threads(nl), smem, s>>>(c->plan, tw, (const T *)c->b.grid_f[pix<T>()], sf, LX);
+        c->launches++;
+    }
+    {   // y forward (4 components)
+        const int LB = max(1, min(Mh, lines_for(budget, 4 * (M + 1))));
+        const size_t smem = (size_t)(4 * LB * (M + 1) + M) * sizeof(T2);
+        dim3 grid((Mh + LB - 1) / LB, M);
+        cudaFuncSetAttribute(fft_strided<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fft_strided<T><<<grid, fft_threads(4 * LB * M), smem, s>>>(c->plan, tw, sf, 4, LB, (size_t)Mh * 4,
+                                                                     (size_t)M * Mh * 4, 0);
+        c->launches++;
+    }
+    const T cnorm = (T)(pow(p.alpha / kPi, 3.0) / (p.eta * p.L * p.L * p.L));
+    {   // z forward + scale + z inverse
+        const int LB = max(1, min(Mh, lines_for(budget, CO * (M + 1))));
+        const size_t smem = (size_t)(CO * LB * (M + 1) + M) * sizeof(T2);
+        dim3 grid((Mh + LB - 1) / LB, M);
+        if (CO == 8) {
+            cudaFuncSetAttribute(fft_z_scale<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            fft_z_scale<T, 8><<<grid, fft_threads(CO * LB * M), smem, s>>>(c->plan, p, tw, sf, so, LB, cnorm);
+        } else {
+            cudaFuncSetAttribute(fft_z_scale<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            fft_z_scale<T, 4><<<grid, fft_threads(CO * LB * M), smem, s>>>(c->plan, p, tw, sf, so, LB, cnorm);
+        }
+        c->launches++;
+    }
+    {   // y inverse (CO components)
+        const int LB = max(1, min(Mh, lines_for(budget, CO * (M + 1))));
+        const size_t smem = (size_t)(CO * LB * (M + 1) + M) * sizeof(T2);
+        dim3 grid((Mh + LB - 1) / LB, M);
+        cudaFuncSetAttribute(fft_strided<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fft_strided<T><<<grid, fft_threads(CO * LB * M), smem, s>>>(c->plan, tw, so, CO, LB, (size_t)Mh * CO,
+                                                                      (size_t)M * Mh * CO, 1);
+        c->launches++;
+    }
+    {   // x inverse
+        const int LX = lines_for(budget, (CO / 2) * M);
+        const int nl = (CO / 2) * LX * M;
+        const size_t smem = (size_t)(nl + M) * sizeof(T2);
+        const int blocks = (M * M + LX - 1) / LX;
+        if (CO == 8) {
+            cudaFuncSetAttribute(fft_x_inv<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            fft_x_inv<T, 8><<<blocks, fft_threads(nl), smem, s>>>(c->plan, tw, so, (T *)c->b.grid_o[pix<T>()], LX);
+        } else {
+            cudaFuncSetAttribute(fft_x_inv<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            fft_x_inv<T, 4><<<blocks, fft_threads(nl), smem, s>>>(c->plan, tw, so, (T *)c->b.grid_o[pix<T>()], LX);
+        }
+        c->launches++;
+    }
+}
+
+template <typename T, typename TO>
+void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int ncomp, int with_wave,
+                           cudaStream_t s)
+{
+    const SeParams p = make_params(c);
+    const int N = (int)c->N;
+    const int wpb = 8;
+    dim3 grid((N + wpb - 1) / wpb);
+    const int with_self = (c->parts & 4) ? 1 : 0;
+    auto go = [&](auto kern) {
+        kern<<<grid, wpb * 32, 0, s>>>(p, N, c->b.sup_base, (const T *)c->b.sup_s0[pix<T>()], (const T *)c->b.sup_w[pix<T>()],
+                                       c->b.rad, c->b.perm, (const T *)c->b.grid_o[pix<T>()], xs, yreal, y, ncomp,
+                                       with_wave, with_self);
+    };
+    if (p.hybrid) {
+        if (ncomp <= 3) go(gather_kernel<T, TO, 8, 3>);
+        else if (ncomp <= 6) go(gather_kernel<T, TO, 8, 6>);
+        else if (ncomp <= 11) go(gather_kernel<T, TO, 8, 11>);
+        else go(gather_kernel<T, TO, 8, 12>);
+    } else {
+        if (ncomp <= 3) go(gather_kernel<T, TO, 4, 3>);
+        else if (ncomp <= 6) go(gather_kernel<T, TO, 4, 6>);
+        else if (ncomp <= 11) go(gather_kernel<T, TO, 4, 11>);
+        else go(gather_kernel<T, TO, 4, 12>);
+    }
+    c->launches++;
+}
+
+template void setup_support<float>(se_ctx *, cudaStream_t);
+template void setup_support<double>(se_ctx *, cudaStream_t);
+template void launch_wave<float>(se_ctx *, const float *, cudaStream_t, int);
+template void launch_wave<double>(se_ctx *, const double *, cudaStream_t, int);
+template void launch_gather_combine<float, float>(se_ctx *, const float *, const float *, float *, int, int, cudaStream_t);
+template void launch_gather_combine<float, double>(se_ctx *, const float *, const float *, double *, int, int, cudaStream_t);
+template void launch_gather_combine<double, float>(se_ctx *, const double *, const double *, float *, int, int, cudaStream_t);
+template void launch_gather_combine<double, double>(se_ctx *, const double *, const double *, double *, int, int, cudaStream_t);
+
+}  // namespace se
