@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 Spectral Ewald far-field grand mobility.
+
+Workload (the large-scale configuration): N = 200000 monodisperse spheres (a = 1)
+at volume fraction 0.45 in a cubic periodic box (seeded FCC-lattice subset, jitter,
+hard-sphere MC sweeps), all 12 multipole components [F, T, S, S_tr] i.i.d. N(0, 1),
+support P = 24, grid and Ewald parameters chosen for <= 1e-6 relative error against
+the FP64 direct-Ewald oracle.  One step = one product y = M_inf . x (cell order ->
+real space || spread -> 3D FFT + k-space scaling -> gather -> combine), inputs
+resident on the device; the grids (>= 1 GB) exceed the 126 MB L2, so every step
+streams them from HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); the product of one box does not shard,
+so every rank runs an independent replica (weak scaling, no collective on the data
+path); rank 0 prints one JSON line with the job-wide throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M∞·F products/s and GMRES solves/s at N=2e5, err≤1e-6 vs FP64; learned vs plain"
+WORKLOAD = "mono_n200000_phi0.45_ncomp12_P24"
+
+# Parameters for the workload (box side L = 123.02): error model of
+# paper_1506_08481_b300.params with its prefactor calibrated on the oracle rows.
+PARAMS = dict(xi=0.6, M=216, P=24, rc=7.5, m=8.68, size_mode=1)
+
+# per-point arithmetic of the hot kernels (FP32 flops, FMA = 2), for the ALU roofline
+FLOPS_PER_POINT = {"spread": 50.0, "gather": 44.0}
+FP32_LANES_PER_SM, SMS = 128, 148
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def stage_algorithmic(stage: str, N: int, M: int, P: int, CO: int):
+    """(bound, units per launch, unit) of one launch of a stage (FP32 grids)."""
+    Mh = M // 2 + 1
+    if stage == "spread":
+        return "alu", N * P ** 3 * FLOPS_PER_POINT["spread"], "flop"
+    if stage == "gather":
+        return "alu", N * P ** 3 * FLOPS_PER_POINT["gather"], "flop"
+    # FFT passes: one read and one write of the arrays they stream (bytes)
+    real_f, spec_f, spec_o, real_o = 4 * M ** 3 * 4, 4 * M * M * Mh * 8, CO * M * M * Mh * 8, CO * M ** 3 * 4
+    return "hbm", {"fft_x_fwd": real_f + spec_f, "fft_y_fwd": 2 * spec_f, "fft_z_scale": spec_f + spec_o,
+                   "fft_y_inv": 2 * spec_o, "fft_x_inv": spec_o + real_o}.get(stage, 0), "byte"
+
+
+def cpu_baseline(cfg, x, nrows_small=4, nrows_large=20):
+    """The oracle timed on host cores on two row samples; a full product's time is the
+    linear extrapolation in the number of target rows."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(7)
+    times = []
+    for nr in (nrows_small, nrows_large):
+        rows = rng.choice(cfg.N, nr, replace=False)
+        t = time.perf_counter()
+        oracle.mobility(cfg.pos, cfg.rad, cfg.L, x, rows=rows, tol=1e-10)
+        times.append(time.perf_counter() - t)
+    per_row = max((times[1] - times[0]) / (nrows_large - nrows_small), 1e-9)
+    t_full = times[0] + per_row * (cfg.N - nrows_small)
+    return {"value": 1.0 / t_full, "unit": "products/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 direct Ewald on {nrows_small} and {nrows_large} target rows of the N=200000 "
+                      f"workload ({times[0]:.1f} s, {times[1]:.1f} s); full product extrapolated linearly "
+                      f"in rows ({t_full:.0f} s)"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    from paper_1506_08481_b300 import inputs
+    import oracle
+    oracle.build()
+    cfg = inputs.mono_dense(seed=0, n=200000, phi=0.45)
+    x = inputs.moments(cfg.N, np.random.default_rng(1), 12)
+    nrows = 8
+    rng = np.random.default_rng(11)
+    times = []
+    for step in range(args.warmup + args.steps):
+        rows = rng.choice(cfg.N, nrows, replace=False)
+        t = time.perf_counter()
+        oracle.mobility(cfg.pos, cfg.rad, cfg.L, x, rows=rows, tol=1e-10)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t)
+    t = float(np.mean(times))
+    value = nrows / (cfg.N * t)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{nrows} target rows of the product per step"},
+            "cpu_baseline": {"value": value, "unit": "products/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": f"{nrows} random target rows per step, products/s = rows/(N t)"},
+            "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1506_08481_b300 import api, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    cfg = inputs.mono_dense(seed=0, n=200000, phi=0.45)
+    x_host = inputs.moments(cfg.N, np.random.default_rng(1), 12)
+    P_ = PARAMS
+    ctx = api.Context(local)
+    ctx.set_params(P_["xi"], P_["M"], P_["P"], P_["rc"])
+    ctx.set_option(api.SE_OPT_SHAPE_M, P_["m"])
+    ctx.set_option(api.SE_OPT_SIZE_MODE, P_["size_mode"])
+    ctx.set_option(api.SE_OPT_PRECISION, 0)
+    ctx.set_config(cfg.pos, cfg.rad, cfg.L)
+    x = torch.tensor(x_host, device=dev, dtype=torch.float32)
+    y = torch.empty_like(x)
+
+    # accuracy against the stored oracle rows (computed by tests/golden/make_golden.py)
+    acc = None
+    gpath = os.path.join(ROOT, "tests", "golden", "mono_n200k_rows.npz")
+    if os.path.exists(gpath):
+        g = np.load(gpath)
+        ctx.apply(x, y)
+        yg = y.double().cpu().numpy()[g["rows"]]
+        acc = float(np.linalg.norm(yg - g["y"]) / np.linalg.norm(g["y"]))
+
+    for _ in range(args.warmup):
+        ctx.apply(x, y)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ctx.set_option(api.SE_OPT_TIMING, 1)
+    launches0 = ctx.kernel_launches()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.apply(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    nprod, stage_ms = ctx.stage_times()
+    ctx.set_option(api.SE_OPT_TIMING, 0)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * args.steps / (ms * 1e-3)
+
+    # end to end through the host-buffer entry point (copies in the timed region)
+    x64 = np.ascontiguousarray(x_host)
+    y64 = np.empty_like(x64)
+    try:
+        xp = torch.from_numpy(x64).pin_memory().numpy()
+        yp = torch.from_numpy(y64).pin_memory().numpy()
+    except RuntimeError:
+        xp, yp = x64, y64
+    ctx.set_option(api.SE_OPT_PRECISION, 0)
+    ctx.apply_host(xp, yp)
+    ne2e = max(5, args.steps // 4)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(ne2e):
+        ctx.apply_host(xp, yp)
+    e2e = world * ne2e / (time.perf_counter() - t)
+
+    # GMRES solve with the block-diagonal preconditioner, FP32 products + FP64 refinement
+    solve = None
+    if not args.no_solve:
+        b = torch.tensor(x_host[:, :11], device=dev, dtype=torch.float64)
+        xs = torch.zeros_like(b)
+        ctx.set_option(api.SE_OPT_RESTART, 100)
+        ctx.solve(b, xs, rtol=1e-6, maxit=2, precond=api.SE_PRECOND_BLOCK, allow_not_converged=True)
+        xs.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, iters, relres = ctx.solve(b, xs, rtol=1e-6, maxit=600, precond=api.SE_PRECOND_BLOCK,
+                                     allow_not_converged=True)
+        ts = time.perf_counter() - t
+        solve = {"solves_per_s": world / ts, "iterations": iters, "relres_fp64": relres, "ncomp": 11,
+                 "rtol": 1e-6, "precond": "block", "restart": 100, "converged": bool(relres <= 1e-6)}
+
+    # roofline of the dominant kernel (largest summed device time)
+    peaks, peak_kind = measured_peaks()
+    CO = 8 if P_["size_mode"] == 0 else 4
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    t_launch = stage_ms[dom] / max(nprod, 1) * 1e-3
+    bound, units, unit = stage_algorithmic(dom, cfg.N, P_["M"], P_["P"], CO)
+    if bound == "alu":
+        clk_mhz = peaks.get("sm_max_mhz", 2032.0)
+        peak = SMS * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+        achieved = units / t_launch / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"FP32 CUDA cores: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clk_mhz:.0f} MHz"}
+    else:
+        peak = peaks.get("hbm_gbs", 6400.0)
+        achieved = units / t_launch / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs ({peak_kind})"}
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(cfg, x_host)
+        line = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": cfg.N, "L": round(cfg.L, 4), "phi": 0.45, "ncomp": 12,
+                           "xi": P_["xi"], "M": P_["M"], "P": P_["P"], "rc": P_["rc"], "m": P_["m"],
+                           "size_mode": "real-space" if P_["size_mode"] else "hybrid",
+                           "parallelism": f"replicas x{world}",
+                           "l2": "grids and spectra (>1 GB per product) exceed L2; inputs resident"},
+                "accuracy": {"rel_l2_vs_fp64_oracle": acc, "rows": 64},
+                "roofline": roof,
+                "stage_ms_per_product": {k: v / max(nprod, 1) for k, v in stage_ms.items()},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e, "unit": "products/s", "h2d_bytes_per_step": int(x64.nbytes),
+                        "d2h_bytes_per_step": int(y64.nbytes)},
+                "gpu_launches": int(launches), "clocks": clk, "solve": solve}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -69,6 +69,19 @@ typedef struct se_ctx se_ctx;
 #define SE_OPT_SHAPE_M     4   /* Gaussian shape parameter m of Eq. theta-param (default sqrt(pi P)) */
 #define SE_OPT_RESTART     5   /* GMRES restart length (default 30) */
 #define SE_OPT_PARTS       6   /* bit mask of terms: 1 real space, 2 wave space, 4 self (default 7) */
+#define SE_OPT_TIMING      7   /* 1: record CUDA events around every stage of each product (default 0) */
+
+/* product stages reported by se_stage_times */
+#define SE_STAGE_PERMUTE   0   /* inputs into cell order */
+#define SE_STAGE_REAL      1   /* real-space pair kernel (auxiliary stream) */
+#define SE_STAGE_SPREAD    2   /* Gaussian spreading */
+#define SE_STAGE_FFT_XF    3   /* forward FFT, x pass (real-to-complex) */
+#define SE_STAGE_FFT_YF    4   /* forward FFT, y pass */
+#define SE_STAGE_FFT_Z     5   /* forward z pass + k-space scaling + inverse z pass */
+#define SE_STAGE_FFT_YI    6   /* inverse FFT, y pass */
+#define SE_STAGE_FFT_XI    7   /* inverse FFT, x pass (complex-to-real) */
+#define SE_STAGE_GATHER    8   /* gather + real + self, written in caller order */
+#define SE_NSTAGE          9
 
 /* preconditioners for se_solve */
 #define SE_PRECOND_NONE    0
@@ -125,6 +138,12 @@ const char *se_last_error(const se_ctx *ctx);
 
 /* Number of CUDA kernels this context has launched since creation (for accounting). */
 int64_t se_kernel_launches(const se_ctx *ctx);
+
+/* With SE_OPT_TIMING on: ms[s] (s < nstage <= SE_NSTAGE) receives the summed device
+ * time of stage s over the products run since the previous call, measured with CUDA
+ * events recorded on the stream that launched the stage.  Synchronises; returns the
+ * number of products summed (>= 0) or a negative error code. */
+int se_stage_times(se_ctx *ctx, double *ms, int nstage);
 
 #ifdef __cplusplus
 }

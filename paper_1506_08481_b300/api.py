@@ -22,12 +22,14 @@ SE_ERR_ARG, SE_ERR_GRID, SE_ERR_CUTOFF, SE_ERR_CUDA = -1, -2, -3, -4
 SE_ERR_STATE, SE_ERR_NONFINITE, SE_ERR_NOT_CONVERGED, SE_ERR_NOMEM = -5, -6, -7, -8
 SE_F32, SE_F64 = 0, 1
 SE_OPT_PRECISION, SE_OPT_SIZE_MODE, SE_OPT_ETA, SE_OPT_SHAPE_M, SE_OPT_RESTART, SE_OPT_PARTS = 1, 2, 3, 4, 5, 6
+SE_OPT_TIMING = 7
+STAGES = ("permute", "real", "spread", "fft_x_fwd", "fft_y_fwd", "fft_z_scale", "fft_y_inv", "fft_x_inv", "gather")
 SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED = 0, 1, 2
 
 # every entry point declared in include/se_mobility.h
 ABI_SYMBOLS = ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
                "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_last_error",
-               "se_kernel_launches")
+               "se_kernel_launches", "se_stage_times")
 
 _lib = None
 
@@ -59,6 +61,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.se_last_error.restype = ctypes.c_char_p
     lib.se_kernel_launches.argtypes = [p]
     lib.se_kernel_launches.restype = i64
+    lib.se_stage_times.argtypes = [p, ctypes.POINTER(d), i]
+    lib.se_stage_times.restype = i
     for name in ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
                  "se_mobility_apply", "se_mobility_apply_host", "se_solve"):
         getattr(lib, name).restype = i
@@ -114,6 +118,16 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self.lib.se_kernel_launches(self.h))
+
+    def se_stage_times(self) -> tuple[int, dict]:
+        """(products, {stage: summed ms}) since the last call (needs SE_OPT_TIMING = 1)."""
+        buf = (ctypes.c_double * len(STAGES))()
+        n = self.lib.se_stage_times(self.h, buf, len(STAGES))
+        if n < 0:
+            self._check(n)
+        return n, dict(zip(STAGES, list(buf)))
+
+    stage_times = se_stage_times
 
     # --- se_set_params / se_set_option
     def se_set_params(self, xi: float, M: int, P: int, rc: float):

@@ -46,6 +46,18 @@ template void launch_permute_in<float, double>(se_ctx *, const double *, float *
 template void launch_permute_in<double, float>(se_ctx *, const float *, double *, int, cudaStream_t);
 template void launch_permute_in<double, double>(se_ctx *, const double *, double *, int, cudaStream_t);
 
+void stage_mark(se_ctx *c, int stage, cudaStream_t s, bool end)
+{
+    if (!c->timing) return;
+    const size_t need = (size_t)(c->tprod + 1) * 2 * SE_NSTAGE;
+    while (c->tev.size() < need) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->tev.push_back(e);
+    }
+    cudaEventRecord(c->tev[(size_t)c->tprod * 2 * SE_NSTAGE + 2 * stage + (end ? 1 : 0)], s);
+}
+
 }  // namespace se
 
 // ---------------------------------------------------------------- helpers
@@ -108,8 +120,17 @@ static void free_config(se_ctx *c)
         dfree(c->b.sup_w[q]);
         dfree(c->b.xs[q]);
         dfree(c->b.yreal[q]);
+        dfree(c->b.rel[q]);
         c->support_ok[q] = false;
     }
+    dfree_t(c->b.pair_off);
+    dfree_t(c->b.pair_j);
+    for (int q = 0; q < 2; ++q) {
+        dfree(c->b.pair_x[q]);
+        dfree(c->b.pair_c[q]);
+        c->pairs_ok[q] = false;
+    }
+    c->npairs = 0;
     dfree_t(c->b.pc_inv);
     dfree_t(c->b.kry);
     dfree_t(c->b.work64);
@@ -162,6 +183,22 @@ static int ensure_support(se_ctx *c, int prec)
     if (!c->b.sup_s0[prec]) SE_ALLOC(c, c->b.sup_s0[prec], N * 3 * es);
     if (!c->b.xs[prec]) SE_ALLOC(c, c->b.xs[prec], N * kNC * es);
     if (!c->b.yreal[prec]) SE_ALLOC(c, c->b.yreal[prec], N * kNC * es);
+    if (!c->b.rel[prec]) {
+        SE_ALLOC(c, c->b.rel[prec], N * 4 * es);
+        if (prec == 1) setup_rel<double>(c, c->stream);
+        else setup_rel<float>(c, c->stream);
+    }
+    if (!c->pairs_ok[prec]) {
+        // the stored pair table is an optimisation: without memory for it the
+        // real-space kernel recomputes the pairs from the cell list
+        const int r = prec == 1 ? build_pair_table<double>(c) : build_pair_table<float>(c);
+        if (r != SE_OK) {
+            cudaGetLastError();
+            dfree(c->b.pair_x[prec]);
+            dfree(c->b.pair_c[prec]);
+            c->err.clear();
+        }
+    }
     if (!c->support_ok[prec]) {
         dfree(c->b.sup_w[prec]);
         SE_ALLOC(c, c->b.sup_w[prec], N * 3 * c->P * es);
@@ -210,6 +247,7 @@ extern "C" int se_destroy(se_ctx *c)
     free_config(c);
     cudaEventDestroy(c->ev_fork);
     cudaEventDestroy(c->ev_join);
+    for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
     cudaStreamDestroy(c->aux);
     delete c;
     return SE_OK;
@@ -221,6 +259,23 @@ extern "C" const char *se_last_error(const se_ctx *c)
 }
 
 extern "C" int64_t se_kernel_launches(const se_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" int se_stage_times(se_ctx *c, double *ms, int nstage)
+{
+    if (!c || !ms || nstage < 1 || nstage > SE_NSTAGE) return SE_ERR_ARG;
+    for (int st = 0; st < nstage; ++st) ms[st] = 0.0;
+    const int n = c->tprod;
+    for (int q = 0; q < n; ++q)
+        for (int st = 0; st < nstage; ++st) {
+            cudaEvent_t b = c->tev[(size_t)q * 2 * SE_NSTAGE + 2 * st], e = c->tev[(size_t)q * 2 * SE_NSTAGE + 2 * st + 1];
+            SE_CUDA_CHECK(c, cudaEventSynchronize(e));
+            float t = 0.f;
+            SE_CUDA_CHECK(c, cudaEventElapsedTime(&t, b, e));
+            ms[st] += t;
+        }
+    c->tprod = 0;
+    return n;
+}
 
 extern "C" int se_set_params(se_ctx *c, double xi, int M, int P, double rc)
 {
@@ -275,6 +330,11 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         if (value < 0 || value > 7) return set_error(c, SE_ERR_ARG, "parts must be a mask in [0, 7]");
         c->parts = (int)value;
         return SE_OK;
+    case SE_OPT_TIMING:
+        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "timing must be 0 or 1");
+        c->timing = value != 0;
+        c->tprod = 0;
+        return SE_OK;
     default:
         return set_error(c, SE_ERR_ARG, "unknown option");
     }
@@ -322,16 +382,28 @@ static int apply_t(se_ctx *c, int ncomp, const TO *x, TO *y)
 {
     cudaStream_t s = c->stream;
     T *xs = (T *)c->b.xs[pix<T>()], *yr = (T *)c->b.yreal[pix<T>()];
+    stage_mark(c, SE_STAGE_PERMUTE, s, false);
     launch_permute_in<T, TO>(c, x, xs, ncomp, s);
+    stage_mark(c, SE_STAGE_PERMUTE, s, true);
     SE_CUDA_CHECK(c, cudaEventRecord(c->ev_fork, s));
     SE_CUDA_CHECK(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    stage_mark(c, SE_STAGE_REAL, c->aux, false);
     if (c->parts & 1) launch_real<T>(c, xs, yr, c->aux, ncomp);
     else SE_CUDA_CHECK(c, cudaMemsetAsync(yr, 0, c->N * kNC * sizeof(T), c->aux));
+    stage_mark(c, SE_STAGE_REAL, c->aux, true);
     SE_CUDA_CHECK(c, cudaEventRecord(c->ev_join, c->aux));
     const int with_wave = (c->parts & 2) ? 1 : 0;
     if (with_wave) launch_wave<T>(c, xs, s, ncomp);
+    else
+        for (int st = SE_STAGE_SPREAD; st <= SE_STAGE_FFT_XI; ++st) {
+            stage_mark(c, st, s, false);
+            stage_mark(c, st, s, true);
+        }
     SE_CUDA_CHECK(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+    stage_mark(c, SE_STAGE_GATHER, s, false);
     launch_gather_combine<T, TO>(c, xs, yr, y, ncomp, with_wave, s);
+    stage_mark(c, SE_STAGE_GATHER, s, true);
+    if (c->timing) c->tprod++;
     SE_CUDA_CHECK(c, cudaGetLastError());
     return SE_OK;
 }

@@ -137,6 +137,12 @@ __global__ void tile_key_kernel(int N, int nt, const int *base, int *key)
 
 }  // namespace
 
+void launch_scan(se_ctx *c, int n, const int *in, int *out, cudaStream_t s)
+{
+    scan_kernel<<<1, 1024, 0, s>>>(n, in, out);
+    c->launches++;
+}
+
 // counting sort of keys[0..N) into perm / start[0..nbins]; scratch: count (nbins)
 static int counting_sort(se_ctx *c, int N, int nbins, const int *key, int *count, int *start, int *perm,
                          bool sort_bins)

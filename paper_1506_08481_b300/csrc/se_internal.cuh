@@ -54,6 +54,7 @@ struct Buffers {
     // per compute precision (index 0: FP32, 1: FP64)
     void *sup_s0[2] = {};        // [N][3] T: offset of the first support point from the particle
     void *sup_w[2] = {};         // [N][3][P] T: Gaussian weights along each axis
+    void *rel[2] = {};           // [N][4] T offset from the cell origin (3) and radius
     void *xs[2] = {};            // [N][12] T inputs in cell order
     void *yreal[2] = {};         // [N][12] T real-space result
     void *grid_f[2] = {};        // [M^3][4] T spread grids
@@ -61,6 +62,11 @@ struct Buffers {
     void *spec_o[2] = {};        // [M][M][Mh][8] complex T
     void *grid_o[2] = {};        // [M^3][8] T gathered grids
     void *tw[2] = {};            // [M] complex T twiddles
+    // stored real-space pairs (Sec. 3.3): CSR over targets in cell order
+    int *pair_off = nullptr;     // [N + 1]
+    int *pair_j = nullptr;       // [npairs]
+    void *pair_x[2] = {};        // [3][npairs] T separations (SoA)
+    void *pair_c[2] = {};        // [19][npairs] T radial coefficients (SoA)
     // host-API staging (device side)
     double *stage = nullptr;     // [2][N][12]
     // solver
@@ -90,6 +96,8 @@ struct se_ctx {
     bool have_config = false;
     bool support_ok[2] = {false, false};
     bool tiles_ok = false;
+    bool pairs_ok[2] = {false, false};
+    size_t npairs = 0;
     size_t grid_M[2] = {0, 0};
     int64_t N = 0;
     double L = 0;
@@ -102,10 +110,17 @@ struct se_ctx {
     size_t alloc_N = 0;
     int64_t launches = 0;
     std::string err;
+    // stage timing (SE_OPT_TIMING): one pair of events per stage per product
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;      // pool, 2 * SE_NSTAGE per product
+    int tprod = 0;                     // products recorded since the last read
 };
 
 // ---- launchers implemented in the .cu files ----
 namespace se {
+
+// Record the begin (end = false) or end (end = true) event of `stage` of the current product.
+void stage_mark(se_ctx *c, int stage, cudaStream_t s, bool end);
 
 SeParams make_params(const se_ctx *c);
 
@@ -116,6 +131,12 @@ int build_support(se_ctx *c, int prec);
 // se_real.cu
 template <typename T>
 void launch_real(se_ctx *c, const T *xs, T *yreal, cudaStream_t s, int ncomp);
+template <typename T>
+void setup_rel(se_ctx *c, cudaStream_t s);
+template <typename T>
+int build_pair_table(se_ctx *c);
+// exclusive scan of n ints into out[0..n] on stream s
+void launch_scan(se_ctx *c, int n, const int *in, int *out, cudaStream_t s);
 
 // se_wave.cu
 template <typename T>

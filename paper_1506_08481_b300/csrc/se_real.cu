@@ -43,206 +43,580 @@ __device__ __forceinline__ float erfc_t<float>(float x) { return erfcf(x); }
 template <>
 __device__ __forceinline__ double erfc_t<double>(double x) { return erfc(x); }
 
+// Adds the couplings of source j (moments xj, radius^2 aj2) to target i (radius^2 ai2)
+// at separation x = r_i - r_j, |x|^2 = r2 < rc^2.
 template <typename T, int NCOMP>
-__global__ void __launch_bounds__(128) real_kernel(int N, double L, double rc, SeParams p, int nc,
-                                                   const int *cell_start, const double *pos,
-                                                   const double *rad, const T *xs, T *yreal)
+__device__ __forceinline__ void pair_accumulate(const T x0, const T x1, const T x2_, const T r2, const T ai2,
+                                                const T aj2, const T *xj, const T xi, const T x2,
+                                                const T exn, const T c8, const T c16, const T c32, T &U0,
+                                                T &U1, T &U2, T &O0, T &O1, T &O2, T &Et, T &Axx, T &Ayy,
+                                                T &Azz, T &Axy, T &Axz, T &Ayz)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const double pxi = pos[3 * i], pyi = pos[3 * i + 1], pzi = pos[3 * i + 2];
-    const T ai = (T)rad[i], ai2 = ai * ai;
+    const T r = sqrt(r2), ir2 = 1 / r2;
+    // B_0 .. B_7
+    T B[8];
+    const T ex = exp(-x2 * r2) * exn;
+    B[0] = erfc_t(xi * r) / r;
+    T pw = 1;
+#pragma unroll
+    for (int n = 1; n < 8; ++n) {
+        pw *= 2 * x2;
+        B[n] = ((2 * n - 1) * B[n - 1] + pw * ex) * ir2;
+    }
+    // D^k psi (s), D^k Lap psi (l), D^k Lap^2 psi (m)
+    const T s1 = B[0], s2 = -B[1], s3 = B[2], s4 = -B[3], s5 = B[4], s6 = -B[5], s7 = B[6], s8 = -B[7];
+    const T l1 = 5 * s2 + r2 * s3, l2 = 7 * s3 + r2 * s4, l3 = 9 * s4 + r2 * s5, l4 = 11 * s5 + r2 * s6,
+            l5 = 13 * s6 + r2 * s7, l6 = 15 * s7 + r2 * s8;
+    const T m1 = 5 * l2 + r2 * l3, m2 = 7 * l3 + r2 * l4, m3 = 9 * l4 + r2 * l5, m4 = 11 * l5 + r2 * l6;
+        const T F0 = xj[0], F1 = xj[1], F2 = xj[2];
+        const T xF = x0 * F0 + x1 * F1 + x2_ * F2;
+        {   // U <- F
+            const T c1 = (ai2 + aj2) * (T)(1.0 / 6), cc = ai2 * aj2 * (T)(1.0 / 36);
+            const T G1 = s1 + c1 * l1 + cc * m1, G2 = s2 + c1 * l2 + cc * m2;
+            const T a = c8 * (2 * G1 + r2 * G2), bb = c8 * xF * G2;
+            U0 += a * F0 - bb * x0;
+            U1 += a * F1 - bb * x1;
+            U2 += a * F2 - bb * x2_;
+        }
+        if constexpr (NCOMP >= 6) {
+            const T T0 = xj[3], T1 = xj[4], T2 = xj[5];
+            const T xT0 = x1 * T2 - x2_ * T1, xT1 = x2_ * T0 - x0 * T2, xT2 = x0 * T1 - x1 * T0;
+            const T xF0 = x1 * F2 - x2_ * F1, xF1 = x2_ * F0 - x0 * F2, xF2 = x0 * F1 - x1 * F0;
+            {   // U <- T
+                const T LG1 = c16 * (l1 + ai2 * (T)(1.0 / 6) * m1);
+                U0 += LG1 * xT0;
+                U1 += LG1 * xT1;
+                U2 += LG1 * xT2;
+            }
+            {   // Om <- F
+                const T LG1 = c16 * (l1 + aj2 * (T)(1.0 / 6) * m1);
+                O0 += LG1 * xF0;
+                O1 += LG1 * xF1;
+                O2 += LG1 * xF2;
+            }
+            {   // Om <- T
+                const T xTd = x0 * T0 + x1 * T1 + x2_ * T2;
+                const T a = c32 * xTd * l2, bb = c32 * (2 * l1 + r2 * l2);
+                O0 += a * x0 - bb * T0;
+                O1 += a * x1 - bb * T1;
+                O2 += a * x2_ - bb * T2;
+            }
+            if constexpr (NCOMP >= 11) {
+                // S tensor of j and its contractions
+                const T r2h = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637;
+                const T Sxx = r2h * xj[6] - r6 * xj[7], Syy = -r2h * xj[6] - r6 * xj[7],
+                        Szz = 2 * r6 * xj[7], Sxy = r2h * xj[8], Sxz = r2h * xj[9],
+                        Syz = r2h * xj[10];
+                const T Sx0 = Sxx * x0 + Sxy * x1 + Sxz * x2_;
+                const T Sx1 = Sxy * x0 + Syy * x1 + Syz * x2_;
+                const T Sx2 = Sxz * x0 + Syz * x1 + Szz * x2_;
+                const T xSx = x0 * Sx0 + x1 * Sx1 + x2_ * Sx2;
+                {   // U <- S
+                    const T c1 = ai2 * (T)(1.0 / 6) + aj2 * (T)0.1, cc = ai2 * aj2 * (T)(1.0 / 60);
+                    const T G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
+                    const T a = -c8 * (3 * G2 + r2 * G3), bb = c8 * xSx * G3;
+                    U0 += a * Sx0 + bb * x0;
+                    U1 += a * Sx1 + bb * x1;
+                    U2 += a * Sx2 + bb * x2_;
+                }
+                {   // Om <- S
+                    const T LG2 = -c16 * (l2 + aj2 * (T)0.1 * m2);
+                    O0 += LG2 * (x1 * Sx2 - x2_ * Sx1);
+                    O1 += LG2 * (x2_ * Sx0 - x0 * Sx2);
+                    O2 += LG2 * (x0 * Sx1 - x1 * Sx0);
+                }
+                {   // E <- F
+                    const T c1 = ai2 * (T)0.1 + aj2 * (T)(1.0 / 6), cc = ai2 * aj2 * (T)(1.0 / 60);
+                    const T G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
+                    const T a = c8 * (3 * G2 + r2 * G3), bb = -c8 * G3 * xF;
+                    Axx += a * x0 * F0 + bb * x0 * x0;
+                    Ayy += a * x1 * F1 + bb * x1 * x1;
+                    Azz += a * x2_ * F2 + bb * x2_ * x2_;
+                    Axy += a * (T)0.5 * (x0 * F1 + x1 * F0) + bb * x0 * x1;
+                    Axz += a * (T)0.5 * (x0 * F2 + x2_ * F0) + bb * x0 * x2_;
+                    Ayz += a * (T)0.5 * (x1 * F2 + x2_ * F1) + bb * x1 * x2_;
+                }
+                {   // E <- T
+                    const T a = c16 * (l2 + ai2 * (T)0.1 * m2);
+                    Axx += a * x0 * xT0;
+                    Ayy += a * x1 * xT1;
+                    Azz += a * x2_ * xT2;
+                    Axy += a * (T)0.5 * (x0 * xT1 + x1 * xT0);
+                    Axz += a * (T)0.5 * (x0 * xT2 + x2_ * xT0);
+                    Ayz += a * (T)0.5 * (x1 * xT2 + x2_ * xT1);
+                }
+                {   // E <- S
+                    const T c1 = (ai2 + aj2) * (T)0.1, cc = ai2 * aj2 * (T)0.01;
+                    const T G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3,
+                            G4 = s4 + c1 * l4 + cc * m4;
+                    const T a = -c8 * (3 * G2 + r2 * G3), bb = -c8 * (3 * G3 + r2 * G4),
+                            cq = c8 * G4 * xSx;
+                    Axx += a * Sxx + bb * x0 * Sx0 + cq * x0 * x0;
+                    Ayy += a * Syy + bb * x1 * Sx1 + cq * x1 * x1;
+                    Azz += a * Szz + bb * x2_ * Sx2 + cq * x2_ * x2_;
+                    Axy += a * Sxy + bb * (T)0.5 * (x0 * Sx1 + x1 * Sx0) + cq * x0 * x1;
+                    Axz += a * Sxz + bb * (T)0.5 * (x0 * Sx2 + x2_ * Sx0) + cq * x0 * x2_;
+                    Ayz += a * Syz + bb * (T)0.5 * (x1 * Sx2 + x2_ * Sx1) + cq * x1 * x2_;
+                }
+                if constexpr (NCOMP >= 12) {
+                    // phi: p_k = (-1)^k B_k ; Lap phi: q_k = (2k+3) p_{k+1} + r^2 p_{k+2}
+                    const T p1 = -B[1], p2 = B[2], p3 = -B[3], p4 = B[4];
+                    const T q1 = 5 * p2 + r2 * p3, q2 = 7 * p3 + r2 * p4;
+                    const T Str = xj[11];
+                    {   // U <- Str
+                        const T a = -c16 * (p1 + ai2 * (T)(1.0 / 6) * q1) * Str;
+                        U0 += a * x0;
+                        U1 += a * x1;
+                        U2 += a * x2_;
+                    }
+                    {   // E <- Str
+                        const T a = -c16 * (p2 + ai2 * (T)0.1 * q2) * Str;
+                        Axx += a * x0 * x0;
+                        Ayy += a * x1 * x1;
+                        Azz += a * x2_ * x2_;
+                        Axy += a * x0 * x1;
+                        Axz += a * x0 * x2_;
+                        Ayz += a * x1 * x2_;
+                    }
+                    // Etr <- F, S
+                    Et += -3 * c16 * xF * (p1 + aj2 * (T)(1.0 / 6) * q1) +
+                          3 * c16 * xSx * (p2 + aj2 * (T)0.1 * q2);
+                }
+            }
+        }
+}
+
+// One CTA per cell of side >= rc: its particles are the targets (one per thread);
+// the particles of the 27 neighbouring cells are staged in shared memory and every
+// staged source serves all targets of the cell.  Positions are offsets from the
+// own cell's origin, so x = off_i - (d * cellw + off_j) for the neighbour cell at
+// displacement d, accurate in FP32; with a single cell the minimum image is taken.
+template <typename T, int NCOMP>
+__global__ void __launch_bounds__(64) real_kernel(double L, double rc, SeParams p, int nc,
+                                                  const int *cell_start, const T *rel, const T *xs,
+                                                  T *yreal)
+{
+    constexpr int CH = 64;
+    constexpr int NM = NCOMP;
+    __shared__ T sj[CH][4];
+    __shared__ T smx[CH][NM];
+    const int cell = blockIdx.x;
+    const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
+    const int ts = cell_start[cell], te = cell_start[cell + 1];
+    const T cellw = (T)(L / nc), Lt = (T)L;
+    const T rc2 = (T)(rc * rc);
     const T xi = (T)p.xi, x2 = xi * xi;
     const T exn = (T)(1.0 / (p.xi * sqrt(kPi)));
     const T c8 = (T)(1.0 / (8 * kPi * p.eta)), c16 = (T)(1.0 / (16 * kPi * p.eta)),
             c32 = (T)(1.0 / (32 * kPi * p.eta));
-    const double rc2 = rc * rc;
-    const double cellw = L / nc;
-    T U0 = 0, U1 = 0, U2 = 0, O0 = 0, O1 = 0, O2 = 0, Et = 0;
-    T Axx = 0, Ayy = 0, Azz = 0, Axy = 0, Axz = 0, Ayz = 0;
-    const int cx = min(nc - 1, (int)(pxi / cellw)), cy = min(nc - 1, (int)(pyi / cellw)),
-              cz = min(nc - 1, (int)(pzi / cellw));
+    const int span = nc >= 3 ? 1 : 0;
+    for (int tb = ts; tb < te; tb += CH) {
+        const int i = tb + threadIdx.x;
+        const bool active = i < te;
+        T oi0 = 0, oi1 = 0, oi2 = 0, ai2 = 0;
+        if (active) {
+            oi0 = rel[4 * i];
+            oi1 = rel[4 * i + 1];
+            oi2 = rel[4 * i + 2];
+            ai2 = rel[4 * i + 3] * rel[4 * i + 3];
+        }
+        T U0 = 0, U1 = 0, U2 = 0, O0 = 0, O1 = 0, O2 = 0, Et = 0;
+        T Axx = 0, Ayy = 0, Azz = 0, Axy = 0, Axz = 0, Ayz = 0;
+        for (int dz = -span; dz <= span; ++dz)
+            for (int dy = -span; dy <= span; ++dy)
+                for (int dx = -span; dx <= span; ++dx) {
+                    const int nb = (((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc) * nc + (cx + dx + nc) % nc;
+                    const int js = cell_start[nb], je = cell_start[nb + 1];
+                    const T sh0 = dx * cellw, sh1 = dy * cellw, sh2 = dz * cellw;
+                    for (int jb = js; jb < je; jb += CH) {
+                        const int cnt = min(CH, je - jb);
+                        __syncthreads();
+                        for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) sj[e >> 2][e & 3] = rel[4 * jb + e];
+                        for (int e = threadIdx.x; e < cnt * NM; e += blockDim.x)
+                            smx[e / NM][e % NM] = xs[(size_t)(jb + e / NM) * kNC + e % NM];
+                        __syncthreads();
+                        if (!active) continue;
+                        for (int k = 0; k < cnt; ++k) {
+                            if (jb + k == i) continue;
+                            T x0 = oi0 - (sh0 + sj[k][0]), x1 = oi1 - (sh1 + sj[k][1]), x2_ = oi2 - (sh2 + sj[k][2]);
+                            if (span == 0) {
+                                x0 -= Lt * rint(x0 / Lt);
+                                x1 -= Lt * rint(x1 / Lt);
+                                x2_ -= Lt * rint(x2_ / Lt);
+                            }
+                            const T r2 = x0 * x0 + x1 * x1 + x2_ * x2_;
+                            if (r2 >= rc2) continue;
+                            T xj[kNC];
+#pragma unroll
+                            for (int c = 0; c < kNC; ++c) xj[c] = c < NM ? smx[k][c < NM ? c : 0] : (T)0;
+                            pair_accumulate<T, NCOMP>(x0, x1, x2_, r2, ai2, sj[k][3] * sj[k][3], xj, xi, x2, exn,
+                                                      c8, c16, c32, U0, U1, U2, O0, O1, O2, Et, Axx, Ayy, Azz,
+                                                      Axy, Axz, Ayz);
+                        }
+                    }
+                }
+        if (active) {
+            T *yo = yreal + (size_t)i * kNC;
+            yo[0] = U0;
+            yo[1] = U1;
+            yo[2] = U2;
+            yo[3] = O0;
+            yo[4] = O1;
+            yo[5] = O2;
+            const T r2h = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637, sq2 = (T)1.41421356237309504880;
+            yo[6] = r2h * (Axx - Ayy);
+            yo[7] = r6 * (2 * Azz - Axx - Ayy);
+            yo[8] = sq2 * Axy;
+            yo[9] = sq2 * Axz;
+            yo[10] = sq2 * Ayz;
+            yo[11] = Et;
+        }
+    }
+}
+
+// Offsets of every particle from the origin of its cell, and its radius.
+template <typename T>
+__global__ void rel_kernel(int N, double L, int nc, const double *pos, const double *rad, T *rel)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double w = L / nc;
+    for (int d = 0; d < 3; ++d) {
+        const double v = pos[3 * i + d];
+        int c = (int)(v / w);
+        c = c >= nc ? nc - 1 : c;
+        rel[4 * i + d] = (T)(v - c * w);
+    }
+    rel[4 * i + 3] = (T)rad[i];
+}
+
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------- stored pair table
+//
+// The real-space operator depends only on the configuration, so (as in Sec. 3.3,
+// where it is stored as a sparse matrix per configuration) its pairs are built once:
+// for every target i (cell order) the neighbours j with |x| < rc, the separation x
+// and 19 radial coefficients, each the combination of B_n, Faxen radii and 1/(8 pi eta)
+// that multiplies one tensor structure of the couplings listed at the top of this file:
+//   0 aF  = (2 G1 + r^2 G2)/(8 pi eta)      1 bF = G2/(8 pi eta)                 (U <- F)
+//   2 uT  = (LG)_1/(16 pi eta) [f6_i]       3 oF = (LG)_1/(16 pi eta) [f6_j]     (U <- T, Om <- F)
+//   4 oTa = (Lpsi)_2/(32 pi eta)            5 oTb = (2 (Lpsi)_1 + r^2 (Lpsi)_2)/(32 pi eta)
+//   6 uSa = -(3 G2 + r^2 G3)/(8 pi eta)     7 uSb = G3/(8 pi eta)                (U <- S)
+//   8 oS  = -(LG)_2/(16 pi eta) [f10_j]                                          (Om <- S)
+//   9 eFa = (3 G2 + r^2 G3)/(8 pi eta)     10 eFb = -G3/(8 pi eta)               (E <- F)
+//  11 eT  = (LG)_2/(16 pi eta) [f10_i]                                           (E <- T)
+//  12 eSa = -(3 G2 + r^2 G3)/(8 pi eta)    13 eSb = -(3 G3 + r^2 G4)/(8 pi eta)
+//  14 eSc = G4/(8 pi eta)                                                        (E <- S)
+//  15 uQ  = -Phi_1/(16 pi eta) [f6_i]      16 eQ = -Phi_2/(16 pi eta) [f10_i]    (U, E <- Str)
+//  17 tF  = -3 Phi_1/(16 pi eta) [f6_j]    18 tS = 3 Phi_2/(16 pi eta) [f10_j]   (Etr <- F, S)
+// The coefficients are evaluated in FP64 and stored at the compute precision.
+constexpr int kNPC = 19;
+
+__device__ __forceinline__ void pair_coefficients(double r2, double ai2, double aj2, double xi, double eta,
+                                                  double *cf)
+{
+    const double r = sqrt(r2), ir2 = 1.0 / r2, x2 = xi * xi;
+    const double ex = exp(-x2 * r2) / (xi * sqrt(kPi));
+    double B[8];
+    B[0] = erfc(xi * r) / r;
+    double pw = 1.0;
+    for (int n = 1; n < 8; ++n) {
+        pw *= 2 * x2;
+        B[n] = ((2 * n - 1) * B[n - 1] + pw * ex) * ir2;
+    }
+    const double s1 = B[0], s2 = -B[1], s3 = B[2], s4 = -B[3], s5 = B[4], s6 = -B[5], s7 = B[6], s8 = -B[7];
+    const double l1 = 5 * s2 + r2 * s3, l2 = 7 * s3 + r2 * s4, l3 = 9 * s4 + r2 * s5, l4 = 11 * s5 + r2 * s6,
+                 l5 = 13 * s6 + r2 * s7, l6 = 15 * s7 + r2 * s8;
+    const double m1 = 5 * l2 + r2 * l3, m2 = 7 * l3 + r2 * l4, m3 = 9 * l4 + r2 * l5, m4 = 11 * l5 + r2 * l6;
+    const double p1 = -B[1], p2 = B[2], p3 = -B[3], p4 = B[4];
+    const double q1 = 5 * p2 + r2 * p3, q2 = 7 * p3 + r2 * p4;
+    const double c8 = 1.0 / (8 * kPi * eta), c16 = 0.5 * c8, c32 = 0.25 * c8;
+    {
+        const double c1 = (ai2 + aj2) / 6, cc = ai2 * aj2 / 36;
+        const double G1 = s1 + c1 * l1 + cc * m1, G2 = s2 + c1 * l2 + cc * m2;
+        cf[0] = c8 * (2 * G1 + r2 * G2);
+        cf[1] = c8 * G2;
+    }
+    cf[2] = c16 * (l1 + ai2 / 6 * m1);
+    cf[3] = c16 * (l1 + aj2 / 6 * m1);
+    cf[4] = c32 * l2;
+    cf[5] = c32 * (2 * l1 + r2 * l2);
+    {
+        const double c1 = ai2 / 6 + aj2 / 10, cc = ai2 * aj2 / 60;
+        const double G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
+        cf[6] = -c8 * (3 * G2 + r2 * G3);
+        cf[7] = c8 * G3;
+    }
+    cf[8] = -c16 * (l2 + aj2 / 10 * m2);
+    {
+        const double c1 = ai2 / 10 + aj2 / 6, cc = ai2 * aj2 / 60;
+        const double G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
+        cf[9] = c8 * (3 * G2 + r2 * G3);
+        cf[10] = -c8 * G3;
+    }
+    cf[11] = c16 * (l2 + ai2 / 10 * m2);
+    {
+        const double c1 = (ai2 + aj2) / 10, cc = ai2 * aj2 / 100;
+        const double G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3, G4 = s4 + c1 * l4 + cc * m4;
+        cf[12] = -c8 * (3 * G2 + r2 * G3);
+        cf[13] = -c8 * (3 * G3 + r2 * G4);
+        cf[14] = c8 * G4;
+    }
+    cf[15] = -c16 * (p1 + ai2 / 6 * q1);
+    cf[16] = -c16 * (p2 + ai2 / 10 * q2);
+    cf[17] = -3 * c16 * (p1 + aj2 / 6 * q1);
+    cf[18] = 3 * c16 * (p2 + aj2 / 10 * q2);
+}
+
+// Neighbour search for target i (cell order) in FP64: calls f(j, x0, x1, x2, r2) for
+// every j != i with |x| < rc, in a fixed order.
+template <typename F>
+__device__ __forceinline__ void for_neighbours(int i, double L, double rc, int nc, const int *cell_start,
+                                               const double *pos, F f)
+{
+    const double w = L / nc, rc2 = rc * rc;
+    const double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
+    const int cx = min(nc - 1, (int)(px / w)), cy = min(nc - 1, (int)(py / w)), cz = min(nc - 1, (int)(pz / w));
     const int span = nc >= 3 ? 1 : 0;
     for (int dz = -span; dz <= span; ++dz)
         for (int dy = -span; dy <= span; ++dy)
             for (int dx = -span; dx <= span; ++dx) {
-                const int ccx = (cx + dx + nc) % nc, ccy = (cy + dy + nc) % nc, ccz = (cz + dz + nc) % nc;
-                const int cell = (ccz * nc + ccy) * nc + ccx;
-                const int js = cell_start[cell], je = cell_start[cell + 1];
-                for (int j = js; j < je; ++j) {
+                const int nb = (((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc) * nc + (cx + dx + nc) % nc;
+                for (int j = cell_start[nb]; j < cell_start[nb + 1]; ++j) {
                     if (j == i) continue;
-                    double ddx = pxi - pos[3 * j], ddy = pyi - pos[3 * j + 1], ddz = pzi - pos[3 * j + 2];
-                    ddx -= L * rint(ddx / L);
-                    ddy -= L * rint(ddy / L);
-                    ddz -= L * rint(ddz / L);
-                    const double rr2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (rr2 >= rc2) continue;
-                    const T x0 = (T)ddx, x1 = (T)ddy, x2_ = (T)ddz, r2 = (T)rr2;
-                    const T r = sqrt(r2), ir2 = 1 / r2;
-                    const T aj = (T)rad[j], aj2 = aj * aj;
-                    // B_0 .. B_7
-                    T B[8];
-                    const T ex = exp(-x2 * r2) * exn;
-                    B[0] = erfc_t(xi * r) / r;
-                    T pw = 1;
-#pragma unroll
-                    for (int n = 1; n < 8; ++n) {
-                        pw *= 2 * x2;
-                        B[n] = ((2 * n - 1) * B[n - 1] + pw * ex) * ir2;
-                    }
-                    // D^k psi (s), D^k Lap psi (l), D^k Lap^2 psi (m)
-                    const T s2 = -B[1], s3 = B[2], s4 = -B[3], s5 = B[4], s6 = -B[5], s7 = B[6], s8 = -B[7];
-                    const T s1 = B[0];
-                    const T l1 = 5 * s2 + r2 * s3, l2 = 7 * s3 + r2 * s4, l3 = 9 * s4 + r2 * s5,
-                            l4 = 11 * s5 + r2 * s6, l5 = 13 * s6 + r2 * s7, l6 = 15 * s7 + r2 * s8;
-                    const T m1 = 5 * l2 + r2 * l3, m2 = 7 * l3 + r2 * l4, m3 = 9 * l4 + r2 * l5,
-                            m4 = 11 * l5 + r2 * l6;
-                    const T *xj = xs + (size_t)j * kNC;
-                    const T F0 = xj[0], F1 = xj[1], F2 = xj[2];
-                    const T xF = x0 * F0 + x1 * F1 + x2_ * F2;
-                    {   // U <- F
-                        const T c1 = (ai2 + aj2) * (T)(1.0 / 6), cc = ai2 * aj2 * (T)(1.0 / 36);
-                        const T G1 = s1 + c1 * l1 + cc * m1, G2 = s2 + c1 * l2 + cc * m2;
-                        const T a = c8 * (2 * G1 + r2 * G2), bb = c8 * xF * G2;
-                        U0 += a * F0 - bb * x0;
-                        U1 += a * F1 - bb * x1;
-                        U2 += a * F2 - bb * x2_;
-                    }
-                    if constexpr (NCOMP >= 6) {
-                        const T T0 = xj[3], T1 = xj[4], T2 = xj[5];
-                        const T xT0 = x1 * T2 - x2_ * T1, xT1 = x2_ * T0 - x0 * T2, xT2 = x0 * T1 - x1 * T0;
-                        const T xF0 = x1 * F2 - x2_ * F1, xF1 = x2_ * F0 - x0 * F2, xF2 = x0 * F1 - x1 * F0;
-                        {   // U <- T
-                            const T LG1 = c16 * (l1 + ai2 * (T)(1.0 / 6) * m1);
-                            U0 += LG1 * xT0;
-                            U1 += LG1 * xT1;
-                            U2 += LG1 * xT2;
-                        }
-                        {   // Om <- F
-                            const T LG1 = c16 * (l1 + aj2 * (T)(1.0 / 6) * m1);
-                            O0 += LG1 * xF0;
-                            O1 += LG1 * xF1;
-                            O2 += LG1 * xF2;
-                        }
-                        {   // Om <- T
-                            const T xTd = x0 * T0 + x1 * T1 + x2_ * T2;
-                            const T a = c32 * xTd * l2, bb = c32 * (2 * l1 + r2 * l2);
-                            O0 += a * x0 - bb * T0;
-                            O1 += a * x1 - bb * T1;
-                            O2 += a * x2_ - bb * T2;
-                        }
-                        if constexpr (NCOMP >= 11) {
-                            // S tensor of j and its contractions
-                            const T r2h = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637;
-                            const T Sxx = r2h * xj[6] - r6 * xj[7], Syy = -r2h * xj[6] - r6 * xj[7],
-                                    Szz = 2 * r6 * xj[7], Sxy = r2h * xj[8], Sxz = r2h * xj[9],
-                                    Syz = r2h * xj[10];
-                            const T Sx0 = Sxx * x0 + Sxy * x1 + Sxz * x2_;
-                            const T Sx1 = Sxy * x0 + Syy * x1 + Syz * x2_;
-                            const T Sx2 = Sxz * x0 + Syz * x1 + Szz * x2_;
-                            const T xSx = x0 * Sx0 + x1 * Sx1 + x2_ * Sx2;
-                            {   // U <- S
-                                const T c1 = ai2 * (T)(1.0 / 6) + aj2 * (T)0.1, cc = ai2 * aj2 * (T)(1.0 / 60);
-                                const T G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
-                                const T a = -c8 * (3 * G2 + r2 * G3), bb = c8 * xSx * G3;
-                                U0 += a * Sx0 + bb * x0;
-                                U1 += a * Sx1 + bb * x1;
-                                U2 += a * Sx2 + bb * x2_;
-                            }
-                            {   // Om <- S
-                                const T LG2 = -c16 * (l2 + aj2 * (T)0.1 * m2);
-                                O0 += LG2 * (x1 * Sx2 - x2_ * Sx1);
-                                O1 += LG2 * (x2_ * Sx0 - x0 * Sx2);
-                                O2 += LG2 * (x0 * Sx1 - x1 * Sx0);
-                            }
-                            {   // E <- F
-                                const T c1 = ai2 * (T)0.1 + aj2 * (T)(1.0 / 6), cc = ai2 * aj2 * (T)(1.0 / 60);
-                                const T G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
-                                const T a = c8 * (3 * G2 + r2 * G3), bb = -c8 * G3 * xF;
-                                Axx += a * x0 * F0 + bb * x0 * x0;
-                                Ayy += a * x1 * F1 + bb * x1 * x1;
-                                Azz += a * x2_ * F2 + bb * x2_ * x2_;
-                                Axy += a * (T)0.5 * (x0 * F1 + x1 * F0) + bb * x0 * x1;
-                                Axz += a * (T)0.5 * (x0 * F2 + x2_ * F0) + bb * x0 * x2_;
-                                Ayz += a * (T)0.5 * (x1 * F2 + x2_ * F1) + bb * x1 * x2_;
-                            }
-                            {   // E <- T
-                                const T a = c16 * (l2 + ai2 * (T)0.1 * m2);
-                                Axx += a * x0 * xT0;
-                                Ayy += a * x1 * xT1;
-                                Azz += a * x2_ * xT2;
-                                Axy += a * (T)0.5 * (x0 * xT1 + x1 * xT0);
-                                Axz += a * (T)0.5 * (x0 * xT2 + x2_ * xT0);
-                                Ayz += a * (T)0.5 * (x1 * xT2 + x2_ * xT1);
-                            }
-                            {   // E <- S
-                                const T c1 = (ai2 + aj2) * (T)0.1, cc = ai2 * aj2 * (T)0.01;
-                                const T G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3,
-                                        G4 = s4 + c1 * l4 + cc * m4;
-                                const T a = -c8 * (3 * G2 + r2 * G3), bb = -c8 * (3 * G3 + r2 * G4),
-                                        cq = c8 * G4 * xSx;
-                                Axx += a * Sxx + bb * x0 * Sx0 + cq * x0 * x0;
-                                Ayy += a * Syy + bb * x1 * Sx1 + cq * x1 * x1;
-                                Azz += a * Szz + bb * x2_ * Sx2 + cq * x2_ * x2_;
-                                Axy += a * Sxy + bb * (T)0.5 * (x0 * Sx1 + x1 * Sx0) + cq * x0 * x1;
-                                Axz += a * Sxz + bb * (T)0.5 * (x0 * Sx2 + x2_ * Sx0) + cq * x0 * x2_;
-                                Ayz += a * Syz + bb * (T)0.5 * (x1 * Sx2 + x2_ * Sx1) + cq * x1 * x2_;
-                            }
-                            if constexpr (NCOMP >= 12) {
-                                // phi: p_k = (-1)^k B_k ; Lap phi: q_k = (2k+3) p_{k+1} + r^2 p_{k+2}
-                                const T p1 = -B[1], p2 = B[2], p3 = -B[3], p4 = B[4];
-                                const T q1 = 5 * p2 + r2 * p3, q2 = 7 * p3 + r2 * p4;
-                                const T Str = xj[11];
-                                {   // U <- Str
-                                    const T a = -c16 * (p1 + ai2 * (T)(1.0 / 6) * q1) * Str;
-                                    U0 += a * x0;
-                                    U1 += a * x1;
-                                    U2 += a * x2_;
-                                }
-                                {   // E <- Str
-                                    const T a = -c16 * (p2 + ai2 * (T)0.1 * q2) * Str;
-                                    Axx += a * x0 * x0;
-                                    Ayy += a * x1 * x1;
-                                    Azz += a * x2_ * x2_;
-                                    Axy += a * x0 * x1;
-                                    Axz += a * x0 * x2_;
-                                    Ayz += a * x1 * x2_;
-                                }
-                                // Etr <- F, S
-                                Et += -3 * c16 * xF * (p1 + aj2 * (T)(1.0 / 6) * q1) +
-                                      3 * c16 * xSx * (p2 + aj2 * (T)0.1 * q2);
-                            }
-                        }
-                    }
+                    double x0 = px - pos[3 * j], x1 = py - pos[3 * j + 1], x2 = pz - pos[3 * j + 2];
+                    x0 -= L * rint(x0 / L);
+                    x1 -= L * rint(x1 / L);
+                    x2 -= L * rint(x2 / L);
+                    const double r2 = x0 * x0 + x1 * x1 + x2 * x2;
+                    if (r2 < rc2) f(j, x0, x1, x2, r2);
                 }
             }
-    T *yo = yreal + (size_t)i * kNC;
-    yo[0] = U0;
-    yo[1] = U1;
-    yo[2] = U2;
-    yo[3] = O0;
-    yo[4] = O1;
-    yo[5] = O2;
-    const T r2h = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637, sq2 = (T)1.41421356237309504880;
-    yo[6] = r2h * (Axx - Ayy);
-    yo[7] = r6 * (2 * Azz - Axx - Ayy);
-    yo[8] = sq2 * Axy;
-    yo[9] = sq2 * Axz;
-    yo[10] = sq2 * Ayz;
-    yo[11] = Et;
+}
+
+__global__ void pair_count_kernel(int N, double L, double rc, int nc, const int *cell_start, const double *pos,
+                                  int *count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int n = 0;
+    for_neighbours(i, L, rc, nc, cell_start, pos, [&](int, double, double, double, double) { ++n; });
+    count[i] = n;
+}
+
+template <typename T>
+__global__ void pair_fill_kernel(int N, double L, double rc, int nc, double xi, double eta, const int *cell_start,
+                                 const double *pos, const double *rad, const int *off, size_t np, int *pj,
+                                 T *px, T *pc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double ai2 = rad[i] * rad[i];
+    size_t k = off[i];
+    for_neighbours(i, L, rc, nc, cell_start, pos, [&](int j, double x0, double x1, double x2, double r2) {
+        double cf[kNPC];
+        pair_coefficients(r2, ai2, rad[j] * rad[j], xi, eta, cf);
+        pj[k] = j;
+        px[k] = (T)x0;
+        px[np + k] = (T)x1;
+        px[2 * np + k] = (T)x2;
+        for (int q = 0; q < kNPC; ++q) pc[q * np + k] = (T)cf[q];
+        ++k;
+    });
+}
+
+// One warp per target: the lanes stream the target's stored pairs (coalesced SoA
+// loads), contract them with the neighbours' moments and reduce over the warp.
+template <typename T, int NCOMP>
+__global__ void __launch_bounds__(256) real_table_kernel(int N, const int *off, size_t np, const int *pj,
+                                                         const T *px, const T *pc, const T *xs, T *yreal)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= N) return;
+    T a[13];
+#pragma unroll
+    for (int c = 0; c < 13; ++c) a[c] = 0;
+    const int k1 = off[i + 1];
+    for (int k = off[i] + lane; k < k1; k += 32) {
+        const int j = pj[k];
+        const T x0 = px[k], x1 = px[np + k], x2 = px[2 * np + k];
+        const T *xj = xs + (size_t)j * kNC;
+        const T F0 = xj[0], F1 = xj[1], F2 = xj[2];
+        const T xF = x0 * F0 + x1 * F1 + x2 * F2;
+        {
+            const T aF = pc[k], bF = pc[np + k] * xF;
+            a[0] += aF * F0 - bF * x0;
+            a[1] += aF * F1 - bF * x1;
+            a[2] += aF * F2 - bF * x2;
+        }
+        if constexpr (NCOMP >= 6) {
+            const T T0 = xj[3], T1 = xj[4], T2 = xj[5];
+            const T xT0 = x1 * T2 - x2 * T1, xT1 = x2 * T0 - x0 * T2, xT2 = x0 * T1 - x1 * T0;
+            const T uT = pc[2 * np + k], oF = pc[3 * np + k];
+            a[0] += uT * xT0;
+            a[1] += uT * xT1;
+            a[2] += uT * xT2;
+            a[3] += oF * (x1 * F2 - x2 * F1);
+            a[4] += oF * (x2 * F0 - x0 * F2);
+            a[5] += oF * (x0 * F1 - x1 * F0);
+            const T oTa = pc[4 * np + k] * (x0 * T0 + x1 * T1 + x2 * T2), oTb = pc[5 * np + k];
+            a[3] += oTa * x0 - oTb * T0;
+            a[4] += oTa * x1 - oTb * T1;
+            a[5] += oTa * x2 - oTb * T2;
+            if constexpr (NCOMP >= 11) {
+                const T r2h = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637;
+                const T Sxx = r2h * xj[6] - r6 * xj[7], Syy = -r2h * xj[6] - r6 * xj[7], Szz = 2 * r6 * xj[7],
+                        Sxy = r2h * xj[8], Sxz = r2h * xj[9], Syz = r2h * xj[10];
+                const T Sx0 = Sxx * x0 + Sxy * x1 + Sxz * x2, Sx1 = Sxy * x0 + Syy * x1 + Syz * x2,
+                        Sx2 = Sxz * x0 + Syz * x1 + Szz * x2;
+                const T xSx = x0 * Sx0 + x1 * Sx1 + x2 * Sx2;
+                {   // U <- S
+                    const T ua = pc[6 * np + k], ub = pc[7 * np + k] * xSx;
+                    a[0] += ua * Sx0 + ub * x0;
+                    a[1] += ua * Sx1 + ub * x1;
+                    a[2] += ua * Sx2 + ub * x2;
+                }
+                {   // Om <- S
+                    const T o = pc[8 * np + k];
+                    a[3] += o * (x1 * Sx2 - x2 * Sx1);
+                    a[4] += o * (x2 * Sx0 - x0 * Sx2);
+                    a[5] += o * (x0 * Sx1 - x1 * Sx0);
+                }
+                // E (symmetric tensor xx yy zz xy xz yz) <- F, T, S
+                const T ea = pc[9 * np + k], eb = pc[10 * np + k] * xF, et = pc[11 * np + k];
+                const T sa = pc[12 * np + k], sb = pc[13 * np + k], sc = pc[14 * np + k] * xSx;
+                a[6] += ea * x0 * F0 + eb * x0 * x0 + et * x0 * xT0 + sa * Sxx + sb * x0 * Sx0 + sc * x0 * x0;
+                a[7] += ea * x1 * F1 + eb * x1 * x1 + et * x1 * xT1 + sa * Syy + sb * x1 * Sx1 + sc * x1 * x1;
+                a[8] += ea * x2 * F2 + eb * x2 * x2 + et * x2 * xT2 + sa * Szz + sb * x2 * Sx2 + sc * x2 * x2;
+                a[9] += (T)0.5 * (ea * (x0 * F1 + x1 * F0) + et * (x0 * xT1 + x1 * xT0) + sb * (x0 * Sx1 + x1 * Sx0)) +
+                        eb * x0 * x1 + sa * Sxy + sc * x0 * x1;
+                a[10] += (T)0.5 * (ea * (x0 * F2 + x2 * F0) + et * (x0 * xT2 + x2 * xT0) + sb * (x0 * Sx2 + x2 * Sx0)) +
+                         eb * x0 * x2 + sa * Sxz + sc * x0 * x2;
+                a[11] += (T)0.5 * (ea * (x1 * F2 + x2 * F1) + et * (x1 * xT2 + x2 * xT1) + sb * (x1 * Sx2 + x2 * Sx1)) +
+                         eb * x1 * x2 + sa * Syz + sc * x1 * x2;
+                if constexpr (NCOMP >= 12) {
+                    const T Str = xj[11];
+                    const T uq = pc[15 * np + k] * Str, eq = pc[16 * np + k] * Str;
+                    a[0] += uq * x0;
+                    a[1] += uq * x1;
+                    a[2] += uq * x2;
+                    a[6] += eq * x0 * x0;
+                    a[7] += eq * x1 * x1;
+                    a[8] += eq * x2 * x2;
+                    a[9] += eq * x0 * x1;
+                    a[10] += eq * x0 * x2;
+                    a[11] += eq * x1 * x2;
+                    a[12] += pc[17 * np + k] * xF + pc[18 * np + k] * xSx;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 13; ++c)
+        for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+    if (lane == 0) {
+        T *yo = yreal + (size_t)i * kNC;
+        yo[0] = a[0];
+        yo[1] = a[1];
+        yo[2] = a[2];
+        yo[3] = a[3];
+        yo[4] = a[4];
+        yo[5] = a[5];
+        const T r2h = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637, sq2 = (T)1.41421356237309504880;
+        yo[6] = r2h * (a[6] - a[7]);
+        yo[7] = r6 * (2 * a[8] - a[6] - a[7]);
+        yo[8] = sq2 * a[9];
+        yo[9] = sq2 * a[10];
+        yo[10] = sq2 * a[11];
+        yo[11] = a[12];
+    }
 }
 
 }  // namespace
+
+// neighbour lists (precision independent) and coefficients at precision T
+template <typename T>
+int build_pair_table(se_ctx *c)
+{
+    cudaStream_t s = c->stream;
+    const int N = (int)c->N;
+    if (!c->b.pair_off) {
+        int *count = nullptr;
+        if (cudaMalloc(&c->b.pair_off, (N + 1) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&count, N * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            if (count) cudaFree(count);
+            c->err = "pair table allocation failed";
+            return SE_ERR_NOMEM;
+        }
+        pair_count_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, c->L, c->rc, c->nc, c->b.cell_start, c->b.pos, count);
+        c->launches++;
+        launch_scan(c, N, count, c->b.pair_off, s);
+        int np = 0;
+        cudaMemcpyAsync(&np, c->b.pair_off + N, sizeof(int), cudaMemcpyDeviceToHost, s);
+        SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
+        cudaFree(count);
+        c->npairs = (size_t)np;
+        if (cudaMalloc(&c->b.pair_j, (c->npairs + 1) * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            c->err = "pair table allocation failed";
+            return SE_ERR_NOMEM;
+        }
+    }
+    const int q = pix<T>();
+    const size_t np = c->npairs;
+    if (cudaMalloc(&c->b.pair_x[q], (3 * np + 1) * sizeof(T)) != cudaSuccess ||
+        cudaMalloc(&c->b.pair_c[q], ((size_t)kNPC * np + 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "pair table allocation failed";
+        return SE_ERR_NOMEM;
+    }
+    pair_fill_kernel<T><<<(N + 127) / 128, 128, 0, s>>>(N, c->L, c->rc, c->nc, c->xi, c->eta, c->b.cell_start,
+                                                         c->b.pos, c->b.rad, c->b.pair_off, np, c->b.pair_j,
+                                                         (T *)c->b.pair_x[q], (T *)c->b.pair_c[q]);
+    c->launches++;
+    SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
+    c->pairs_ok[q] = true;
+    return SE_OK;
+}
+
+template int build_pair_table<float>(se_ctx *);
+template int build_pair_table<double>(se_ctx *);
+
+template <typename T>
+void setup_rel(se_ctx *c, cudaStream_t s)
+{
+    const int N = (int)c->N;
+    rel_kernel<T><<<(N + 127) / 128, 128, 0, s>>>(N, c->L, c->nc, c->b.pos, c->b.rad, (T *)c->b.rel[pix<T>()]);
+    c->launches++;
+}
 
 template <typename T>
 void launch_real(se_ctx *c, const T *xs, T *yreal, cudaStream_t s, int ncomp)
 {
     const SeParams p = make_params(c);
-    const int N = (int)c->N;
-    const int tpb = 128;
+    const int q = pix<T>();
+    if (c->pairs_ok[q]) {
+        const int N = (int)c->N, wpb = 8;
+        auto go = [&](auto kern) {
+            kern<<<(N + wpb - 1) / wpb, wpb * 32, 0, s>>>(N, c->b.pair_off, c->npairs, c->b.pair_j,
+                                                          (const T *)c->b.pair_x[q], (const T *)c->b.pair_c[q],
+                                                          xs, yreal);
+        };
+        if (ncomp <= 3) go(real_table_kernel<T, 3>);
+        else if (ncomp <= 6) go(real_table_kernel<T, 6>);
+        else if (ncomp <= 11) go(real_table_kernel<T, 11>);
+        else go(real_table_kernel<T, 12>);
+        c->launches++;
+        return;
+    }
+    const int ncell = c->nc * c->nc * c->nc;
     auto go = [&](auto kern) {
-        kern<<<(N + tpb - 1) / tpb, tpb, 0, s>>>(N, c->L, c->rc, p, c->nc, c->b.cell_start, c->b.pos,
-                                                  c->b.rad, xs, yreal);
+        kern<<<ncell, 64, 0, s>>>(c->L, c->rc, p, c->nc, c->b.cell_start, (const T *)c->b.rel[pix<T>()], xs, yreal);
     };
     if (ncomp <= 3) go(real_kernel<T, 3>);
     else if (ncomp <= 6) go(real_kernel<T, 6>);
@@ -251,6 +625,8 @@ void launch_real(se_ctx *c, const T *xs, T *yreal, cudaStream_t s, int ncomp)
     c->launches++;
 }
 
+template void setup_rel<float>(se_ctx *, cudaStream_t);
+template void setup_rel<double>(se_ctx *, cudaStream_t);
 template void launch_real<float>(se_ctx *, const float *, float *, cudaStream_t, int);
 template void launch_real<double>(se_ctx *, const double *, double *, cudaStream_t, int);
 

@@ -93,119 +93,140 @@ __global__ void support_kernel(int N, SeParams p, const double *pos, const doubl
 
 // ---------------------------------------------------------------- spreading
 
-// One CTA per kTile^3 tile of the grid.  It visits the particles whose support
-// start lies in the bins that can reach the tile, accumulates their contributions
-// in shared memory (each warp spreads one particle over the intersection of its
-// support with the tile) and writes the tile once: no global atomics.
+// One CTA per kTile^3 tile of the grid; each of its 128 threads owns a column of
+// 4 grid points and accumulates their values in registers (no atomics anywhere).
+// The candidate particles (those in the bins whose support start lies within
+// P - 1 points before the tile) are listed by a prefix sum over the bin counts and
+// staged in shared memory 128 at a time, one particle per thread: their Gaussian
+// weights restricted to the tile window, the offset of the tile origin from the
+// particle, the Faxen coefficients and the moments.
 template <typename T, int NCOMP>
-__global__ void __launch_bounds__(256) spread_kernel(SeParams p, const int *tile_start,
+__global__ void __launch_bounds__(128) spread_kernel(SeParams p, const int *tile_start,
                                                      const int *tile_perm, const int *base,
                                                      const T *s0g, const T *wg, const double *rad,
                                                      const T *xs, T *grid)
 {
-    constexpr int TT = kTile;
-    __shared__ T acc[TT * TT * TT * 4];
+    constexpr int TT = kTile, CH = 128, NW = 3 * TT, NPR = 20, MAXB = 125;
+    __shared__ T sw[CH][NW];          // window weights x(8) y(8) z(8)
+    __shared__ T sp[CH][NPR];         // s(3) A0 A1 B0 B1 F(3) T(3) S(6) Str
+    __shared__ int sok[CH];
+    __shared__ int bin_beg[MAXB], bin_off[MAXB + 1];
     const int M = p.M, P = p.P, nt = p.ntile;
     const int tile = blockIdx.x;
-    const int tx = tile % nt, ty = (tile / nt) % nt, tz = tile / (nt * nt);
-    const int t0x = tx * TT, t0y = ty * TT, t0z = tz * TT;
-    for (int e = threadIdx.x; e < TT * TT * TT * 4; e += blockDim.x) acc[e] = 0;
+    const int bx0 = tile % nt, by0 = (tile / nt) % nt, bz0 = tile / (nt * nt);
+    const int t0[3] = {bx0 * TT, by0 * TT, bz0 * TT};
+    const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, zh = threadIdx.x >> 6;
+    const int nbin = (P - 1 + TT - 1) / TT + 1, nb3 = nbin * nbin * nbin;
+    const T alpha = (T)p.alpha, kap = (T)p.kappa, akap = alpha * kap;
+    constexpr int NA = NCOMP >= 12 ? 4 : 3;
+    T acc[4][NA];
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+#pragma unroll
+        for (int c = 0; c < NA; ++c) acc[z][c] = 0;
+
+    // candidate list: bins (tile - b) for b in [0, nbin)^3, concatenated
+    if ((int)threadIdx.x < nb3) {
+        const int bb = threadIdx.x;
+        const int bx = bb % nbin, by = (bb / nbin) % nbin, bz = bb / (nbin * nbin);
+        const int bin = (wrapi(bz0 - bz, nt) * nt + wrapi(by0 - by, nt)) * nt + wrapi(bx0 - bx, nt);
+        bin_beg[bb] = tile_start[bin];
+        bin_off[bb + 1] = tile_start[bin + 1] - tile_start[bin];
+    }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        bin_off[0] = 0;
+        for (int bb = 0; bb < nb3; ++bb) bin_off[bb + 1] += bin_off[bb];
+    }
+    __syncthreads();
+    const int total = bin_off[nb3];
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int nbin = (P - 1 + TT - 1) / TT + 1;
-    const T alpha = (T)p.alpha, kap = (T)p.kappa;
-    const T akap = alpha * kap;
-
-    for (int bz = 0; bz < nbin; ++bz)
-        for (int by = 0; by < nbin; ++by)
-            for (int bx = 0; bx < nbin; ++bx) {
-                const int bin = (wrapi(tz - bz, nt) * nt + wrapi(ty - by, nt)) * nt + wrapi(tx - bx, nt);
-                const int qs = tile_start[bin], qe = tile_start[bin + 1];
-                for (int q = qs + warp; q < qe; q += nwarp) {
-                    const int i = tile_perm[q];
-                    int o[3], lo[3], hi[3];
-                    const int t0[3] = {t0x, t0y, t0z};
-                    bool empty = false;
-                    for (int d = 0; d < 3; ++d) {
-                        int od = t0[d] - base[3 * i + d];
-                        od = wrapi(od, M);
-                        if (od >= P) od -= M;            // tile starts before the support
-                        o[d] = od;
-                        lo[d] = max(0, -od);
-                        hi[d] = min(TT, P - od);
-                        empty |= lo[d] >= hi[d];
-                    }
-                    if (empty) continue;
-                    const T *xi = xs + (size_t)i * kNC;
-                    const T a = (T)rad[i];
-                    const T a2k2 = a * a * kap * kap;
-                    const T A0 = 1 - a2k2 * alpha, A1 = (T)(2.0 / 3.0) * a2k2 * alpha * alpha;
-                    const T B0 = 2 * kap * alpha * (1 - a2k2 * alpha);
-                    const T B1 = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
-                    const T F0 = xi[0], F1 = xi[1], F2 = xi[2];
-                    T T0 = 0, T1 = 0, T2 = 0, S[6] = {0, 0, 0, 0, 0, 0}, Str = 0;
-                    if constexpr (NCOMP >= 6) { T0 = xi[3]; T1 = xi[4]; T2 = xi[5]; }
-                    if constexpr (NCOMP >= 11) stresslet_tensor(xi + 6, S);
-                    if constexpr (NCOMP >= 12) Str = xi[11];
-                    const T sx0 = s0g[3 * i], sy0 = s0g[3 * i + 1], sz0 = s0g[3 * i + 2];
-                    const T *wx = wg + (size_t)i * 3 * P, *wy = wx + P, *wz = wy + P;
-                    const int nz = hi[2] - lo[2];
-                    T gzl = 0, szl = 0;
-                    if (lane < nz) {
-                        int iz = o[2] + lo[2] + lane;
-                        gzl = wz[iz];
-                        szl = sz0 + iz;
-                    }
-                    const int nx = hi[0] - lo[0], ny = hi[1] - lo[1], nxy = nx * ny;
-                    for (int it = 0; it < nxy; it += 32) {
-                        const int c = it + lane;
-                        const bool act = c < nxy;
-                        const int cy = act ? c / nx : 0, cx = act ? c - cy * nx : 0;
-                        const int tlx = lo[0] + cx, tly = lo[1] + cy;
-                        const int ix = o[0] + tlx, iy = o[1] + tly;
-                        const T gxy = act ? wx[ix] * wy[iy] : (T)0;
-                        const T sx = sx0 + ix, sy = sy0 + iy;
-                        for (int k = 0; k < nz; ++k) {
-                            const T gz = __shfl_sync(0xffffffffu, gzl, k);
-                            const T sz = __shfl_sync(0xffffffffu, szl, k);
-                            if (!act) continue;
-                            const T g = gxy * gz;
-                            const T s2 = sx * sx + sy * sy + sz * sz;
-                            const T cF = A0 + A1 * s2;
-                            T h0 = cF * F0, h1 = cF * F1, h2 = cF * F2;
-                            if constexpr (NCOMP >= 6) {
-                                // 1/2 grad g x T = -alpha kappa g (s x T)
-                                h0 -= akap * (sy * T2 - sz * T1);
-                                h1 -= akap * (sz * T0 - sx * T2);
-                                h2 -= akap * (sx * T1 - sy * T0);
-                            }
-                            if constexpr (NCOMP >= 11) {
-                                // -S . grad (1 + a^2 Lap/10) g = g (B0 + B1 s^2) S.s
-                                const T cS = B0 + B1 * s2;
-                                h0 += cS * (S[0] * sx + S[3] * sy + S[4] * sz);
-                                h1 += cS * (S[3] * sx + S[1] * sy + S[5] * sz);
-                                h2 += cS * (S[4] * sx + S[5] * sy + S[2] * sz);
-                            }
-                            T *dst = acc + (((lo[2] + k) * TT + tly) * TT + tlx) * 4;
-                            atomicAdd(dst + 0, g * h0);
-                            atomicAdd(dst + 1, g * h1);
-                            atomicAdd(dst + 2, g * h2);
-                            if constexpr (NCOMP >= 12) atomicAdd(dst + 3, g * Str);
-                        }
-                    }
-                }
+    for (int c0 = 0; c0 < total; c0 += CH) {
+        const int cnt = min(CH, total - c0);
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            const int k = threadIdx.x, idx = c0 + k;
+            int lo = 0, hi = nb3;                       // bin_off[lo] <= idx < bin_off[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (bin_off[mid] <= idx) lo = mid; else hi = mid;
             }
-    __syncthreads();
-    for (int e = threadIdx.x; e < TT * TT * TT; e += blockDim.x) {
-        const int lx = e % TT, ly = (e / TT) % TT, lz = e / (TT * TT);
-        const size_t g = (((size_t)(t0z + lz) * M + (t0y + ly)) * M + (t0x + lx)) * 4;
+            const int i = tile_perm[bin_beg[lo] + idx - bin_off[lo]];
+            bool ok = true;
+            for (int d = 0; d < 3; ++d) {
+                int od = wrapi(t0[d] - base[3 * i + d], M);   // support index of the tile origin
+                if (od >= P) od -= M;
+                ok &= (od < P) && (od > -TT);
+                const T *w = wg + ((size_t)i * 3 + d) * P;
+#pragma unroll
+                for (int t = 0; t < TT; ++t) {
+                    const int ix = od + t;
+                    sw[k][d * TT + t] = (ix >= 0 && ix < P) ? w[ix] : (T)0;
+                }
+                sp[k][d] = s0g[3 * i + d] + (T)od;             // offset of tile point 0
+            }
+            const T a = (T)rad[i], a2k2 = a * a * kap * kap;
+            sp[k][3] = 1 - a2k2 * alpha;
+            sp[k][4] = (T)(2.0 / 3.0) * a2k2 * alpha * alpha;
+            sp[k][5] = 2 * kap * alpha * (1 - a2k2 * alpha);
+            sp[k][6] = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
+            const T *xi = xs + (size_t)i * kNC;
+            sp[k][7] = xi[0];
+            sp[k][8] = xi[1];
+            sp[k][9] = xi[2];
+            if constexpr (NCOMP >= 6) { sp[k][10] = xi[3]; sp[k][11] = xi[4]; sp[k][12] = xi[5]; }
+            if constexpr (NCOMP >= 11) stresslet_tensor(xi + 6, &sp[k][13]);
+            if constexpr (NCOMP >= 12) sp[k][19] = xi[11];
+            sok[k] = ok;
+        }
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            if (!sok[k]) continue;
+            const T gxy = sw[k][tx] * sw[k][TT + ty];
+            if (gxy == (T)0) continue;
+            const T sx = sp[k][0] + tx, sy = sp[k][1] + ty;
+            const T sxy2 = sx * sx + sy * sy;
+            const T A0 = sp[k][3], A1 = sp[k][4];
+            const T F0 = sp[k][7], F1 = sp[k][8], F2 = sp[k][9];
+#pragma unroll
+            for (int zz = 0; zz < 4; ++zz) {
+                const int z = zh * 4 + zz;
+                const T g = gxy * sw[k][2 * TT + z];
+                const T sz = sp[k][2] + z;
+                const T s2 = sxy2 + sz * sz;
+                const T cF = A0 + A1 * s2;
+                T h0 = cF * F0, h1 = cF * F1, h2 = cF * F2;
+                if constexpr (NCOMP >= 6) {
+                    // 1/2 grad g x T = -alpha kappa g (s x T)
+                    const T T0 = sp[k][10], T1 = sp[k][11], T2 = sp[k][12];
+                    h0 -= akap * (sy * T2 - sz * T1);
+                    h1 -= akap * (sz * T0 - sx * T2);
+                    h2 -= akap * (sx * T1 - sy * T0);
+                }
+                if constexpr (NCOMP >= 11) {
+                    // -S . grad (1 + a^2 Lap/10) g = g (B0 + B1 s^2) S.s
+                    const T cS = sp[k][5] + sp[k][6] * s2;
+                    const T *S = &sp[k][13];
+                    h0 += cS * (S[0] * sx + S[3] * sy + S[4] * sz);
+                    h1 += cS * (S[3] * sx + S[1] * sy + S[5] * sz);
+                    h2 += cS * (S[4] * sx + S[5] * sy + S[2] * sz);
+                }
+                acc[zz][0] += g * h0;
+                acc[zz][1] += g * h1;
+                acc[zz][2] += g * h2;
+                if constexpr (NCOMP >= 12) acc[zz][3] += g * sp[k][19];
+            }
+        }
+    }
+#pragma unroll
+    for (int zz = 0; zz < 4; ++zz) {
+        const size_t gi = (((size_t)(t0[2] + zh * 4 + zz) * M + (t0[1] + ty)) * M + (t0[0] + tx)) * 4;
         typename V4<T>::t v;
-        v.x = acc[e * 4 + 0];
-        v.y = acc[e * 4 + 1];
-        v.z = acc[e * 4 + 2];
-        v.w = acc[e * 4 + 3];
-        *reinterpret_cast<typename V4<T>::t *>(grid + g) = v;
+        v.x = acc[zz][0];
+        v.y = acc[zz][1];
+        v.z = acc[zz][2];
+        v.w = NCOMP >= 12 ? acc[zz][NA - 1] : (T)0;
+        *reinterpret_cast<typename V4<T>::t *>(grid + gi) = v;
     }
 }
 
@@ -600,7 +621,7 @@ static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_
 {
     const int nt = p.ntile, ntiles = nt * nt * nt;
     auto args = [&](auto kern) {
-        kern<<<ntiles, 256, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base, (const T *)c->b.sup_s0[pix<T>()],
+        kern<<<ntiles, 128, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base, (const T *)c->b.sup_s0[pix<T>()],
                                      (const T *)c->b.sup_w[pix<T>()], c->b.rad, xs, (T *)c->b.grid_f[pix<T>()]);
     };
     if (ncomp <= 3) args(spread_kernel<T, 3>);
@@ -628,8 +649,11 @@ void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp)
     T2 *sf = (T2 *)c->b.spec_f[pix<T>()], *so = (T2 *)c->b.spec_o[pix<T>()];
     const int CO = p.hybrid ? 8 : 4;
 
+    stage_mark(c, SE_STAGE_SPREAD, s, false);
     launch_spread<T>(c, p, xs, s, ncomp);
+    stage_mark(c, SE_STAGE_SPREAD, s, true);
 
+    stage_mark(c, SE_STAGE_FFT_XF, s, false);
     {   // x forward
         const int LX = lines_for(budget, 2 * M);
         const int nl = 2 * LX * M;
@@ -639,6 +663,8 @@ void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp)
         fft_x_fwd<T><<<blocks, fft_threads(nl), smem, s>>>(c->plan, tw, (const T *)c->b.grid_f[pix<T>()], sf, LX);
         c->launches++;
     }
+    stage_mark(c, SE_STAGE_FFT_XF, s, true);
+    stage_mark(c, SE_STAGE_FFT_YF, s, false);
     {   // y forward (4 components)
         const int LB = max(1, min(Mh, lines_for(budget, 4 * (M + 1))));
         const size_t smem = (size_t)(4 * LB * (M + 1) + M) * sizeof(T2);
@@ -648,7 +674,9 @@ void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp)
                                                                      (size_t)M * Mh * 4, 0);
         c->launches++;
     }
+    stage_mark(c, SE_STAGE_FFT_YF, s, true);
     const T cnorm = (T)(pow(p.alpha / kPi, 3.0) / (p.eta * p.L * p.L * p.L));
+    stage_mark(c, SE_STAGE_FFT_Z, s, false);
     {   // z forward + scale + z inverse
         const int LB = max(1, min(Mh, lines_for(budget, CO * (M + 1))));
         const size_t smem = (size_t)(CO * LB * (M + 1) + M) * sizeof(T2);
@@ -662,6 +690,8 @@ void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp)
         }
         c->launches++;
     }
+    stage_mark(c, SE_STAGE_FFT_Z, s, true);
+    stage_mark(c, SE_STAGE_FFT_YI, s, false);
     {   // y inverse (CO components)
         const int LB = max(1, min(Mh, lines_for(budget, CO * (M + 1))));
         const size_t smem = (size_t)(CO * LB * (M + 1) + M) * sizeof(T2);
@@ -671,6 +701,8 @@ void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp)
                                                                       (size_t)M * Mh * CO, 1);
         c->launches++;
     }
+    stage_mark(c, SE_STAGE_FFT_YI, s, true);
+    stage_mark(c, SE_STAGE_FFT_XI, s, false);
     {   // x inverse
         const int LX = lines_for(budget, (CO / 2) * M);
         const int nl = (CO / 2) * LX * M;
@@ -685,6 +717,7 @@ void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp)
         }
         c->launches++;
     }
+    stage_mark(c, SE_STAGE_FFT_XI, s, true);
 }
 
 template <typename T, typename TO>
