@@ -57,6 +57,7 @@ typedef struct se_ctx se_ctx;
 #define SE_ERR_NONFINITE     -6   /* non-finite position, radius or result */
 #define SE_ERR_NOT_CONVERGED -7   /* GMRES reached maxit (x holds the last iterate) */
 #define SE_ERR_NOMEM         -8   /* device allocation failed */
+#define SE_ERR_TOO_LARGE     -9   /* problem larger than a fixed capacity (se_real_space_apply_noalloc) */
 
 /* dtypes of x / y */
 #define SE_F32 0
@@ -131,6 +132,32 @@ int se_mobility_apply_host(se_ctx *ctx, int ncomp, const double *x, double *y);
  * relres > rtol after maxit products. */
 int se_solve(se_ctx *ctx, int ncomp, const void *b, void *x, int dtype, double rtol,
              int maxit, int precond, int *iters, double *relres);
+
+/* Allocation-free real-space part.  The paper has no counterpart: this entry point is
+ * for callers that cannot allocate device memory -- an application whose own allocator
+ * reserves the device memory up front, or a latency-critical caller that cannot accept
+ * the device-wide synchronisation of cudaMalloc / cudaFree.  It computes the real-space
+ * pair sum of y = M_inf . x (all pairs with |x| < rc, the couplings of se_mobility_apply's
+ * real-space part, FP64) for N <= SE_NOALLOC_MAX_N spheres, with the cell list and all
+ * other scratch in one fixed device array of about 2 MB that every GPU loading the
+ * library holds until the process exits; cells are enlarged if more than
+ * SE_NOALLOC_MAX_CELLS would be needed.  It calls no allocator.
+ *   device, stream : CUDA device and cudaStream_t to run on (stream may be 0)
+ *   N, L           : spheres and box side;  xi, rc, eta : Ewald parameter, cutoff (< L/2),
+ *                    viscosity;  pos [N][3], radius [N] : FP64 DEVICE arrays
+ *   x, y           : FP64 DEVICE arrays [N][ncomp], ncomp in {3, 6, 11, 12}; y is overwritten
+ * Returns SE_ERR_TOO_LARGE if N > SE_NOALLOC_MAX_N, SE_ERR_CUTOFF if rc >= L/2,
+ * SE_ERR_ARG for null pointers or bad sizes, SE_ERR_NONFINITE for non-finite positions
+ * or non-positive radii, SE_ERR_CUDA for a failed CUDA call; synchronises the stream.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one array and
+ * every call clears what must start at zero; calls that overlap on the GPU race on it,
+ * so the caller must not run two at once. */
+#define SE_NOALLOC_MAX_N     8192
+#define SE_NOALLOC_MAX_CELLS 4096
+int se_real_space_apply_noalloc(int device, void *stream, int64_t N, double L, double xi, double rc,
+                                double eta, const double *pos, const double *radius, int ncomp,
+                                const double *x, double *y);
 
 /* Message describing the last failure on this context ("" if none).  Valid until the
  * next call on the same context.  ctx may be NULL (returns the last create failure). */

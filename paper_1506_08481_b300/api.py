@@ -20,6 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libse_b300.so")
 SE_OK = 0
 SE_ERR_ARG, SE_ERR_GRID, SE_ERR_CUTOFF, SE_ERR_CUDA = -1, -2, -3, -4
 SE_ERR_STATE, SE_ERR_NONFINITE, SE_ERR_NOT_CONVERGED, SE_ERR_NOMEM = -5, -6, -7, -8
+SE_ERR_TOO_LARGE = -9
+SE_NOALLOC_MAX_N = 8192
 SE_F32, SE_F64 = 0, 1
 SE_OPT_PRECISION, SE_OPT_SIZE_MODE, SE_OPT_ETA, SE_OPT_SHAPE_M, SE_OPT_RESTART, SE_OPT_PARTS = 1, 2, 3, 4, 5, 6
 SE_OPT_TIMING = 7
@@ -29,7 +31,7 @@ SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED = 0, 1, 2
 # every entry point declared in include/se_mobility.h
 ABI_SYMBOLS = ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
                "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_last_error",
-               "se_kernel_launches", "se_stage_times")
+               "se_kernel_launches", "se_stage_times", "se_real_space_apply_noalloc")
 
 _lib = None
 
@@ -63,6 +65,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.se_kernel_launches.restype = i64
     lib.se_stage_times.argtypes = [p, ctypes.POINTER(d), i]
     lib.se_stage_times.restype = i
+    lib.se_real_space_apply_noalloc.argtypes = [i, p, i64, d, d, d, d, p, p, i, p, p]
+    lib.se_real_space_apply_noalloc.restype = i
     for name in ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
                  "se_mobility_apply", "se_mobility_apply_host", "se_solve"):
         getattr(lib, name).restype = i

@@ -30,6 +30,8 @@
 // total unchanged; they make the real part consistent with the spread force density.)
 // E rows are accumulated as a symmetric tensor and projected on the orthonormal
 // traceless basis at the end.
+#include <cmath>
+
 #include "se_internal.cuh"
 
 namespace se {
@@ -631,3 +633,208 @@ template void launch_real<float>(se_ctx *, const float *, float *, cudaStream_t,
 template void launch_real<double>(se_ctx *, const double *, double *, cudaStream_t, int);
 
 }  // namespace se
+
+// ---------------------------------------------------------------- allocation-free variant
+//
+// se_real_space_apply_noalloc: the real-space pair sum of the product (the cell-list
+// kernel above, in FP64) for callers that cannot allocate device memory -- for
+// instance an application whose own allocator reserves the device memory up front,
+// or a latency-critical caller that cannot accept the device-wide synchronisation of
+// cudaMalloc / cudaFree.  Its scratch (cell keys, counts, cell starts, the particle
+// order, sorted offsets and moments, the sorted result) lives in one file-scope
+// device array sized for SE_NOALLOC_MAX_N particles and SE_NOALLOC_MAX_CELLS cells.
+// Every GPU that loads the library holds that array (about 2 MB) until the process
+// exits.  All calls share it: calls that overlap on the GPU (several host threads or
+// streams at once) race on it and must be serialised by the caller.
+namespace se {
+namespace {
+
+constexpr int kNaMaxN = SE_NOALLOC_MAX_N, kNaMaxCells = SE_NOALLOC_MAX_CELLS;
+constexpr size_t kNaInts = 2 * (size_t)kNaMaxN + 2 * ((size_t)kNaMaxCells + 1) + 64;
+constexpr size_t kNaBytes = kNaInts * sizeof(int) + (size_t)kNaMaxN * (4 + 2 * kNC) * sizeof(double);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+struct NaLayout {
+    int *key, *count, *start, *perm, *flag;
+    double *rel, *xs, *yr;
+};
+
+NaLayout na_layout(unsigned char *base)
+{
+    NaLayout l;
+    int *ip = reinterpret_cast<int *>(base);
+    l.key = ip;
+    l.perm = ip + kNaMaxN;
+    l.count = ip + 2 * kNaMaxN;
+    l.start = l.count + (kNaMaxCells + 1);
+    l.flag = l.start + (kNaMaxCells + 1);
+    double *dp = reinterpret_cast<double *>(base + kNaInts * sizeof(int));
+    l.rel = dp;
+    l.xs = dp + 4 * (size_t)kNaMaxN;
+    l.yr = l.xs + (size_t)kNC * kNaMaxN;
+    return l;
+}
+
+__global__ void na_clear_kernel(int ncell, int *count, int *flag)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= ncell; e += gridDim.x * blockDim.x) count[e] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) flag[0] = 0;
+}
+
+__global__ void na_key_kernel(int N, double L, int nc, const double *pos, const double *rad, int *key, int *count,
+                              int *flag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    bool ok = isfinite(rad[i]) && rad[i] > 0;
+    int k[3];
+    for (int d = 0; d < 3; ++d) {
+        double v = pos[3 * i + d];
+        ok = ok && isfinite(v);
+        v = ok ? v - L * floor(v / L) : 0.0;
+        int c = (int)(v / (L / nc));
+        k[d] = c >= nc ? nc - 1 : (c < 0 ? 0 : c);
+    }
+    key[i] = (k[2] * nc + k[1]) * nc + k[0];
+    atomicAdd(&count[key[i]], 1);
+    if (!ok) atomicExch(flag, 1);
+}
+
+// exclusive scan of count[0..n) into start[0..n] (one CTA), then count is reused as a cursor
+__global__ void na_scan_kernel(int n, int *count, int *start)
+{
+    __shared__ int part[1024];
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * per, e = min(n, b + per);
+    int s = 0;
+    for (int q = b; q < e; ++q) s += count[q];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const int v = part[t];
+            part[t] = acc;
+            acc += v;
+        }
+        start[n] = acc;
+    }
+    __syncthreads();
+    int acc = part[threadIdx.x];
+    for (int q = b; q < e; ++q) {
+        start[q] = acc;
+        acc += count[q];
+        count[q] = 0;
+    }
+}
+
+__global__ void na_scatter_kernel(int N, const int *key, const int *start, int *cursor, int *perm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int k = key[i];
+    perm[start[k] + atomicAdd(&cursor[k], 1)] = i;
+}
+
+// order each cell by caller index (deterministic layout), then gather offsets and moments
+__global__ void na_order_kernel(int ncell, const int *start, int *perm)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= ncell) return;
+    for (int i = start[b] + 1; i < start[b + 1]; ++i) {
+        const int v = perm[i];
+        int j = i - 1;
+        while (j >= start[b] && perm[j] > v) {
+            perm[j + 1] = perm[j];
+            --j;
+        }
+        perm[j + 1] = v;
+    }
+}
+
+__global__ void na_gather_kernel(int N, double L, int nc, int ncomp, const int *perm, const double *pos,
+                                 const double *rad, const double *x, double *rel, double *xs)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int i = perm[k];
+    const double w = L / nc;
+    for (int d = 0; d < 3; ++d) {
+        double v = pos[3 * i + d];
+        v -= L * floor(v / L);
+        int c = (int)(v / w);
+        c = c >= nc ? nc - 1 : c;
+        rel[4 * k + d] = v - c * w;
+    }
+    rel[4 * k + 3] = rad[i];
+    for (int c = 0; c < kNC; ++c) xs[(size_t)k * kNC + c] = c < ncomp ? x[(size_t)i * ncomp + c] : 0.0;
+}
+
+__global__ void na_scatter_out_kernel(int N, int ncomp, const int *perm, const double *yr, double *y)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    for (int c = 0; c < ncomp; ++c) y[(size_t)perm[k] * ncomp + c] = yr[(size_t)k * kNC + c];
+}
+
+constexpr int kNaMaxDevices = 64;
+unsigned char *g_noalloc_ptr[kNaMaxDevices] = {};
+
+}  // namespace
+
+}  // namespace se
+
+extern "C" int se_real_space_apply_noalloc(int device, void *stream, int64_t N, double L, double xi, double rc,
+                                           double eta, const double *pos, const double *radius, int ncomp,
+                                           const double *x, double *y)
+{
+    using namespace se;
+    if (!pos || !radius || !x || !y || N < 1) return SE_ERR_ARG;
+    if (ncomp != 3 && ncomp != 6 && ncomp != 11 && ncomp != 12) return SE_ERR_ARG;
+    if (!(L > 0) || !(xi > 0) || !(eta > 0) || !std::isfinite(L)) return SE_ERR_ARG;
+    if (N > kNaMaxN) return SE_ERR_TOO_LARGE;
+    if (!(rc > 0) || rc >= 0.5 * L) return SE_ERR_CUTOFF;
+    if (device < 0 || device >= kNaMaxDevices) return SE_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return SE_ERR_CUDA;
+    // once per device: the device address of the scratch array (its host-side name is
+    // only a stand-in and must not be passed to a kernel)
+    if (!g_noalloc_ptr[device]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return SE_ERR_CUDA;
+        }
+        g_noalloc_ptr[device] = static_cast<unsigned char *>(ptr);
+    }
+    int nc = (int)std::floor(L / rc);
+    if (nc < 3) nc = 1;
+    while (nc > 1 && nc * nc * nc > kNaMaxCells) --nc;   // larger cells stay correct
+    if (nc < 3) nc = 1;
+    const int n = (int)N, ncell = nc * nc * nc;
+    const NaLayout l = na_layout(g_noalloc_ptr[device]);
+    cudaStream_t s = (cudaStream_t)stream;
+    na_clear_kernel<<<(ncell + 256) / 256, 256, 0, s>>>(ncell, l.count, l.flag);
+    na_key_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, L, nc, pos, radius, l.key, l.count, l.flag);
+    na_scan_kernel<<<1, 1024, 0, s>>>(ncell, l.count, l.start);
+    na_scatter_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, l.key, l.start, l.count, l.perm);
+    na_order_kernel<<<(ncell + 127) / 128, 128, 0, s>>>(ncell, l.start, l.perm);
+    na_gather_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, L, nc, ncomp, l.perm, pos, radius, x, l.rel, l.xs);
+    SeParams p{};
+    p.L = L;
+    p.xi = xi;
+    p.rc = rc;
+    p.eta = eta;
+    auto go = [&](auto kern) { kern<<<ncell, 64, 0, s>>>(L, rc, p, nc, l.start, l.rel, l.xs, l.yr); };
+    if (ncomp <= 3) go(real_kernel<double, 3>);
+    else if (ncomp <= 6) go(real_kernel<double, 6>);
+    else if (ncomp <= 11) go(real_kernel<double, 11>);
+    else go(real_kernel<double, 12>);
+    na_scatter_out_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, ncomp, l.perm, l.yr, y);
+    int flag = 0;
+    if (cudaMemcpyAsync(&flag, l.flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return SE_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return SE_ERR_CUDA;
+    return flag ? SE_ERR_NONFINITE : SE_OK;
+}
