@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=200000,
+                    help="spheres (N-sweep of the large-scale configuration at the same phi and grid density)")
     return ap.parse_args()
 
 
@@ -196,9 +198,13 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    cfg = inputs.mono_dense(seed=0, n=200000, phi=0.45)
+    cfg = inputs.mono_dense(seed=0, n=args.n, phi=0.45)
     x_host = inputs.moments(cfg.N, np.random.default_rng(1), 12)
-    P_ = PARAMS
+    P_ = dict(PARAMS)
+    if args.n != 200000:
+        from paper_1506_08481_b300 import params as prm
+        need = P_["M"] * cfg.L / 123.018      # same grid spacing (same accuracy)
+        P_["M"] = min(v for v in prm.fft_sizes() if v >= need)
     ctx = api.Context(local)
     ctx.set_params(P_["xi"], P_["M"], P_["P"], P_["rc"])
     ctx.set_option(api.SE_OPT_SHAPE_M, P_["m"])
@@ -211,7 +217,7 @@ def run_ours(args, rank, world, local):
     # accuracy against the stored oracle rows (computed by tests/golden/make_golden.py)
     acc = None
     gpath = os.path.join(ROOT, "tests", "golden", "mono_n200k_rows.npz")
-    if os.path.exists(gpath):
+    if os.path.exists(gpath) and args.n == 200000:
         g = np.load(gpath)
         ctx.apply(x, y)
         yg = y.double().cpu().numpy()[g["rows"]]
@@ -299,6 +305,7 @@ def run_ours(args, rank, world, local):
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs ({peak_kind})"}
 
+    workload = WORKLOAD if args.n == 200000 else WORKLOAD.replace("n200000", f"n{args.n}")
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
@@ -306,7 +313,7 @@ def run_ours(args, rank, world, local):
         line = {"metric": METRIC, "value": value, "unit": "products/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": cfg.N, "L": round(cfg.L, 4), "phi": 0.45, "ncomp": 12,
+                "config": {"workload": workload, "N": cfg.N, "L": round(cfg.L, 4), "phi": 0.45, "ncomp": 12,
                            "xi": P_["xi"], "M": P_["M"], "P": P_["P"], "rc": P_["rc"], "m": P_["m"],
                            "size_mode": "real-space" if P_["size_mode"] else "hybrid",
                            "parallelism": f"replicas x{world}",

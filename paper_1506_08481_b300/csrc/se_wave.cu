@@ -93,41 +93,45 @@ __global__ void support_kernel(int N, SeParams p, const double *pos, const doubl
 
 // ---------------------------------------------------------------- spreading
 
-// One CTA per kTile^3 tile of the grid; each of its 128 threads owns a column of
-// 4 grid points and accumulates their values in registers (no atomics anywhere).
-// The candidate particles (those in the bins whose support start lies within
-// P - 1 points before the tile) are listed by a prefix sum over the bin counts and
-// staged in shared memory 128 at a time, one particle per thread: their Gaussian
-// weights restricted to the tile window, the offset of the tile origin from the
-// particle, the Faxen coefficients and the moments.
+// One CTA per kTile^3 tile of the grid; each of its 64 threads owns one (x, y)
+// column of 8 grid points and accumulates their values in registers (no atomics
+// anywhere).  The candidate particles (those in the bins whose support start lies
+// within P - 1 points before the tile) are listed by a prefix sum over the bin counts
+// and staged in shared memory 64 at a time, one particle per thread: the x and y
+// Gaussian weights in the tile window, the table W_z = g_z (1, s_z, s_z^2, s_z^3) of the
+// 8 tile planes, the offsets of the tile origin, the Faxen coefficients and moments.
+// Along a column the force density is a cubic polynomial in s_z times g_z
+// (Eq. grid-space with the torque and stresslet terms):
+//   H = g [ (A0 + A1 s^2) F - alpha kappa (s x T) + (B0 + B1 s^2) S.s ],  H_src = g S_tr,
+// so a thread forms 13 column coefficients per particle and spends 13 FMAs per point.
 template <typename T, int NCOMP>
-__global__ void __launch_bounds__(128) spread_kernel(SeParams p, const int *tile_start,
-                                                     const int *tile_perm, const int *base,
-                                                     const T *s0g, const T *wg, const double *rad,
-                                                     const T *xs, T *grid)
+__global__ void __launch_bounds__(64) spread_kernel(SeParams p, const int *tile_start,
+                                                    const int *tile_perm, const int *base,
+                                                    const T *s0g, const T *wg, const double *rad,
+                                                    const T *xs, T *grid)
 {
-    constexpr int TT = kTile, CH = 128, NW = 3 * TT, NPR = 20, MAXB = 125;
-    __shared__ T sw[CH][NW];          // window weights x(8) y(8) z(8)
-    __shared__ T sp[CH][NPR];         // s(3) A0 A1 B0 B1 F(3) T(3) S(6) Str
-    __shared__ int sok[CH];
+    constexpr int TT = kTile, CH = 64, NPR = 22, MAXB = 125;
+    using T4 = typename V4<T>::t;
+    __shared__ T sxy[CH][2 * TT];     // window weights x(8) y(8)
+    __shared__ T4 swz[CH][TT];        // g_z (1, s_z, s_z^2, s_z^3) per tile plane
+    __shared__ T sp[CH][NPR];         // sx0 sy0 A0 A1 B0 B1 F(3) T(3) S(6) Str ok
     __shared__ int bin_beg[MAXB], bin_off[MAXB + 1];
     const int M = p.M, P = p.P, nt = p.ntile;
     const int tile = blockIdx.x;
     const int bx0 = tile % nt, by0 = (tile / nt) % nt, bz0 = tile / (nt * nt);
     const int t0[3] = {bx0 * TT, by0 * TT, bz0 * TT};
-    const int tx = threadIdx.x & 7, ty = (threadIdx.x >> 3) & 7, zh = threadIdx.x >> 6;
+    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
     const int nbin = (P - 1 + TT - 1) / TT + 1, nb3 = nbin * nbin * nbin;
     const T alpha = (T)p.alpha, kap = (T)p.kappa, akap = alpha * kap;
     constexpr int NA = NCOMP >= 12 ? 4 : 3;
-    T acc[4][NA];
+    T acc[TT][NA];
 #pragma unroll
-    for (int z = 0; z < 4; ++z)
+    for (int z = 0; z < TT; ++z)
 #pragma unroll
         for (int c = 0; c < NA; ++c) acc[z][c] = 0;
 
     // candidate list: bins (tile - b) for b in [0, nbin)^3, concatenated
-    if ((int)threadIdx.x < nb3) {
-        const int bb = threadIdx.x;
+    for (int bb = threadIdx.x; bb < nb3; bb += blockDim.x) {
         const int bx = bb % nbin, by = (bb / nbin) % nbin, bz = bb / (nbin * nbin);
         const int bin = (wrapi(bz0 - bz, nt) * nt + wrapi(by0 - by, nt)) * nt + wrapi(bx0 - bx, nt);
         bin_beg[bb] = tile_start[bin];
@@ -153,80 +157,106 @@ __global__ void __launch_bounds__(128) spread_kernel(SeParams p, const int *tile
             }
             const int i = tile_perm[bin_beg[lo] + idx - bin_off[lo]];
             bool ok = true;
+            int od[3];
             for (int d = 0; d < 3; ++d) {
-                int od = wrapi(t0[d] - base[3 * i + d], M);   // support index of the tile origin
-                if (od >= P) od -= M;
-                ok &= (od < P) && (od > -TT);
-                const T *w = wg + ((size_t)i * 3 + d) * P;
-#pragma unroll
-                for (int t = 0; t < TT; ++t) {
-                    const int ix = od + t;
-                    sw[k][d * TT + t] = (ix >= 0 && ix < P) ? w[ix] : (T)0;
-                }
-                sp[k][d] = s0g[3 * i + d] + (T)od;             // offset of tile point 0
+                int o = wrapi(t0[d] - base[3 * i + d], M);   // support index of the tile origin
+                if (o >= P) o -= M;
+                ok &= (o < P) && (o > -TT);
+                od[d] = o;
             }
+            const T *w = wg + (size_t)i * 3 * P;
+#pragma unroll
+            for (int t = 0; t < TT; ++t) {
+                const int ix = od[0] + t, iy = od[1] + t, iz = od[2] + t;
+                sxy[k][t] = (ix >= 0 && ix < P) ? w[ix] : (T)0;
+                sxy[k][TT + t] = (iy >= 0 && iy < P) ? w[P + iy] : (T)0;
+                const T g = (iz >= 0 && iz < P) ? w[2 * P + iz] : (T)0;
+                const T sz = s0g[3 * i + 2] + (T)iz;
+                swz[k][t] = T4{g, g * sz, g * sz * sz, g * sz * sz * sz};
+            }
+            sp[k][0] = s0g[3 * i] + (T)od[0];                 // offsets of the tile origin
+            sp[k][1] = s0g[3 * i + 1] + (T)od[1];
             const T a = (T)rad[i], a2k2 = a * a * kap * kap;
-            sp[k][3] = 1 - a2k2 * alpha;
-            sp[k][4] = (T)(2.0 / 3.0) * a2k2 * alpha * alpha;
-            sp[k][5] = 2 * kap * alpha * (1 - a2k2 * alpha);
-            sp[k][6] = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
+            sp[k][2] = 1 - a2k2 * alpha;
+            sp[k][3] = (T)(2.0 / 3.0) * a2k2 * alpha * alpha;
+            sp[k][4] = 2 * kap * alpha * (1 - a2k2 * alpha);
+            sp[k][5] = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
             const T *xi = xs + (size_t)i * kNC;
-            sp[k][7] = xi[0];
-            sp[k][8] = xi[1];
-            sp[k][9] = xi[2];
-            if constexpr (NCOMP >= 6) { sp[k][10] = xi[3]; sp[k][11] = xi[4]; sp[k][12] = xi[5]; }
-            if constexpr (NCOMP >= 11) stresslet_tensor(xi + 6, &sp[k][13]);
-            if constexpr (NCOMP >= 12) sp[k][19] = xi[11];
-            sok[k] = ok;
+            sp[k][6] = xi[0];
+            sp[k][7] = xi[1];
+            sp[k][8] = xi[2];
+            if constexpr (NCOMP >= 6) { sp[k][9] = xi[3]; sp[k][10] = xi[4]; sp[k][11] = xi[5]; }
+            if constexpr (NCOMP >= 11) stresslet_tensor(xi + 6, &sp[k][12]);
+            if constexpr (NCOMP >= 12) sp[k][18] = xi[11];
+            sp[k][21] = ok ? (T)1 : (T)0;
         }
         __syncthreads();
         for (int k = 0; k < cnt; ++k) {
-            if (!sok[k]) continue;
-            const T gxy = sw[k][tx] * sw[k][TT + ty];
-            if (gxy == (T)0) continue;
+            const T gxy = sxy[k][tx] * sxy[k][TT + ty];
+            if (gxy == (T)0 || sp[k][21] == (T)0) continue;
             const T sx = sp[k][0] + tx, sy = sp[k][1] + ty;
             const T sxy2 = sx * sx + sy * sy;
-            const T A0 = sp[k][3], A1 = sp[k][4];
-            const T F0 = sp[k][7], F1 = sp[k][8], F2 = sp[k][9];
+            const T A1 = sp[k][3], a0 = sp[k][2] + A1 * sxy2;
+            // column coefficients c[alpha][p] of s_z^p (times g_xy)
+            T c[3][4];
 #pragma unroll
-            for (int zz = 0; zz < 4; ++zz) {
-                const int z = zh * 4 + zz;
-                const T g = gxy * sw[k][2 * TT + z];
-                const T sz = sp[k][2] + z;
-                const T s2 = sxy2 + sz * sz;
-                const T cF = A0 + A1 * s2;
-                T h0 = cF * F0, h1 = cF * F1, h2 = cF * F2;
-                if constexpr (NCOMP >= 6) {
-                    // 1/2 grad g x T = -alpha kappa g (s x T)
-                    const T T0 = sp[k][10], T1 = sp[k][11], T2 = sp[k][12];
-                    h0 -= akap * (sy * T2 - sz * T1);
-                    h1 -= akap * (sz * T0 - sx * T2);
-                    h2 -= akap * (sx * T1 - sy * T0);
+            for (int q = 0; q < 3; ++q) {
+                const T F = sp[k][6 + q];
+                c[q][0] = a0 * F;
+                c[q][1] = 0;
+                c[q][2] = A1 * F;
+                c[q][3] = 0;
+            }
+            if constexpr (NCOMP >= 6) {
+                // -alpha kappa (s x T), s x T = c0 + s_z c1
+                const T T0 = sp[k][9], T1 = sp[k][10], T2 = sp[k][11];
+                c[0][0] -= akap * sy * T2;
+                c[1][0] += akap * sx * T2;
+                c[2][0] -= akap * (sx * T1 - sy * T0);
+                c[0][1] += akap * T1;
+                c[1][1] -= akap * T0;
+            }
+            if constexpr (NCOMP >= 11) {
+                // (B0 + B1 s^2) S.s with S.s = d0 + s_z d1
+                const T *S = &sp[k][12];
+                const T B1 = sp[k][5], b0 = sp[k][4] + B1 * sxy2;
+                const T d00 = S[0] * sx + S[3] * sy, d01 = S[3] * sx + S[1] * sy, d02 = S[4] * sx + S[5] * sy;
+                const T d10 = S[4], d11 = S[5], d12 = S[2];
+                c[0][0] += b0 * d00; c[1][0] += b0 * d01; c[2][0] += b0 * d02;
+                c[0][1] += b0 * d10; c[1][1] += b0 * d11; c[2][1] += b0 * d12;
+                c[0][2] += B1 * d00; c[1][2] += B1 * d01; c[2][2] += B1 * d02;
+                c[0][3] = B1 * d10; c[1][3] = B1 * d11; c[2][3] = B1 * d12;
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) c[q][e] *= gxy;
+            const T cs = NCOMP >= 12 ? gxy * sp[k][18] : (T)0;
+#pragma unroll
+            for (int z = 0; z < TT; ++z) {
+                const T4 W = swz[k][z];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if constexpr (NCOMP >= 11)
+                        acc[z][q] += c[q][0] * W.x + c[q][1] * W.y + c[q][2] * W.z + c[q][3] * W.w;
+                    else if constexpr (NCOMP >= 6)
+                        acc[z][q] += c[q][0] * W.x + c[q][1] * W.y + c[q][2] * W.z;
+                    else
+                        acc[z][q] += c[q][0] * W.x + c[q][2] * W.z;
                 }
-                if constexpr (NCOMP >= 11) {
-                    // -S . grad (1 + a^2 Lap/10) g = g (B0 + B1 s^2) S.s
-                    const T cS = sp[k][5] + sp[k][6] * s2;
-                    const T *S = &sp[k][13];
-                    h0 += cS * (S[0] * sx + S[3] * sy + S[4] * sz);
-                    h1 += cS * (S[3] * sx + S[1] * sy + S[5] * sz);
-                    h2 += cS * (S[4] * sx + S[5] * sy + S[2] * sz);
-                }
-                acc[zz][0] += g * h0;
-                acc[zz][1] += g * h1;
-                acc[zz][2] += g * h2;
-                if constexpr (NCOMP >= 12) acc[zz][3] += g * sp[k][19];
+                if constexpr (NCOMP >= 12) acc[z][NA - 1] += cs * W.x;
             }
         }
     }
 #pragma unroll
-    for (int zz = 0; zz < 4; ++zz) {
-        const size_t gi = (((size_t)(t0[2] + zh * 4 + zz) * M + (t0[1] + ty)) * M + (t0[0] + tx)) * 4;
-        typename V4<T>::t v;
-        v.x = acc[zz][0];
-        v.y = acc[zz][1];
-        v.z = acc[zz][2];
-        v.w = NCOMP >= 12 ? acc[zz][NA - 1] : (T)0;
-        *reinterpret_cast<typename V4<T>::t *>(grid + gi) = v;
+    for (int z = 0; z < TT; ++z) {
+        const size_t gi = (((size_t)(t0[2] + z) * M + (t0[1] + ty)) * M + (t0[0] + tx)) * 4;
+        T4 v;
+        v.x = acc[z][0];
+        v.y = acc[z][1];
+        v.z = acc[z][2];
+        v.w = NCOMP >= 12 ? acc[z][NA - 1] : (T)0;
+        *reinterpret_cast<T4 *>(grid + gi) = v;
     }
 }
 
@@ -420,16 +450,24 @@ __device__ __forceinline__ void kahan_add(T &sum, T &comp, T v)
 // One warp per particle: trapezoid-rule convolution of the gathered grids with the
 // particle's Gaussian (and its derivatives) over the P^3 support, then
 // y = real + wave + self, written in the caller's order and dtype.
-// Accumulators: U(3), s x v (3), sym(s (x) w) (6: xx yy zz xy xz yz), p (1).
+// The Gaussian is separable and every target weight is a polynomial of degree <= 3
+// in s_z times g_z, so each lane (one (x, y) column of the support) sums the column
+// against the per-warp table W_k = g_z (1, s_z, s_z^2, s_z^3) held in shared memory
+// (13 FMAs per grid point) and converts the column moments into the 13 outputs
+// U(3), s x v (3), sym(s (x) w) (6: xx yy zz, xy xz yz doubled), p (1) once per column.
+// Column contributions are Kahan-compensated across the P^2 / 32 columns of a lane.
 template <typename T, typename TO, int CO, int NCOMP>
-__global__ void __launch_bounds__(256) gather_kernel(SeParams p, int N, const int *base, const T *s0g,
+__global__ void __launch_bounds__(256, 4) gather_kernel(SeParams p, int N, const int *base, const T *s0g,
                                                      const T *wg, const double *rad, const int *perm,
                                                      const T *grid, const T *xs, const T *yreal, TO *y,
                                                      int ncomp_out, int with_wave, int with_self)
 {
     constexpr int NA = 13;
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    using T4 = typename V4<T>::t;
+    __shared__ T4 Wz[8][32];
+    __shared__ int Zi[8][32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int i = blockIdx.x * (blockDim.x >> 5) + wl;
     if (i >= N) return;
     const int M = p.M, P = p.P;
     const double ad = rad[i];
@@ -445,83 +483,91 @@ __global__ void __launch_bounds__(256) gather_kernel(SeParams p, int N, const in
         const int bx = base[3 * i], by = base[3 * i + 1], bz = base[3 * i + 2];
         const T sx0 = s0g[3 * i], sy0 = s0g[3 * i + 1], sz0 = s0g[3 * i + 2];
         const T *wx = wg + (size_t)i * 3 * P, *wy = wx + P, *wz = wy + P;
-        const T gzl = lane < P ? wz[lane] : (T)0, szl = sz0 + lane;
-        const int zl = wrapi(bz + lane, M);
+        if (lane < P) {
+            const T g = wz[lane], sz = sz0 + lane;
+            Wz[wl][lane] = T4{g, g * sz, g * sz * sz, g * sz * sz * sz};
+            Zi[wl][lane] = wrapi(bz + lane, M);
+        }
+        __syncwarp();
         const T a2k2 = a * a * kap * kap;
         // real-space approach weights (Faxen Laplacian on the Gaussian)
         const T A0 = 1 - a2k2 * alpha, A1 = (T)(2.0 / 3.0) * a2k2 * alpha * alpha;
         const T B0 = 2 * kap * alpha * (1 - a2k2 * alpha);
         const T B1 = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
         const T c6 = a * a / 6, c10 = a * a / 10;
+        const size_t zs = (size_t)M * M * CO;
         for (int it = 0; it < P * P; it += 32) {
             const int c = it + lane;
             const bool act = c < P * P;
             const int cy = act ? c / P : 0, cx = act ? c - cy * P : 0;
-            const int gx = wrapi(bx + cx, M), gy = wrapi(by + cy, M);
-            const T gxy = act ? wx[cx] * wy[cy] : (T)0;
-            const T sx = sx0 + cx, sy = sy0 + cy;
-            T col[NA];
-#pragma unroll
-            for (int cc = 0; cc < NA; ++cc) col[cc] = 0;
-            for (int k = 0; k < P; ++k) {
-                const T gz = __shfl_sync(0xffffffffu, gzl, k);
-                const T sz = __shfl_sync(0xffffffffu, szl, k);
-                const int gzi = __shfl_sync(0xffffffffu, zl, k);
-                if (!act) continue;
-                const T *gp = grid + (((size_t)gzi * M + gy) * M + gx) * CO;
-                const T g = gxy * gz;
-                if constexpr (CO == 8) {
-                    const typename V4<T>::t u0 = *reinterpret_cast<const typename V4<T>::t *>(gp);
-                    const typename V4<T>::t u1 = *reinterpret_cast<const typename V4<T>::t *>(gp + 4);
-                    // u0 = (v0 v1 v2 v''0), u1 = (v''1 v''2 p -)
-                    const T v0 = u0.x, v1 = u0.y, v2 = u0.z;
-                    const T w0 = u0.w, w1 = u1.x, w2 = u1.y;
-                    col[0] += g * (v0 + c6 * w0);
-                    col[1] += g * (v1 + c6 * w1);
-                    col[2] += g * (v2 + c6 * w2);
-                    if constexpr (NCOMP >= 6) {
-                        const T gx_ = g * sx, gy_ = g * sy, gz_ = g * sz;
-                        col[3] += gy_ * v2 - gz_ * v1;
-                        col[4] += gz_ * v0 - gx_ * v2;
-                        col[5] += gx_ * v1 - gy_ * v0;
-                        if constexpr (NCOMP >= 11) {
-                            const T e0 = v0 + c10 * w0, e1 = v1 + c10 * w1, e2 = v2 + c10 * w2;
-                            col[6] += gx_ * e0;
-                            col[7] += gy_ * e1;
-                            col[8] += gz_ * e2;
-                            col[9] += gx_ * e1 + gy_ * e0;
-                            col[10] += gx_ * e2 + gz_ * e0;
-                            col[11] += gy_ * e2 + gz_ * e1;
+            const T *gp = grid + ((size_t)wrapi(by + cy, M) * M + wrapi(bx + cx, M)) * CO;
+            // column moments: Z0..Z3 of v (and of v'' in the hybrid mode), Zp of p
+            T z0[3] = {0, 0, 0}, z1[3] = {0, 0, 0}, z2[3] = {0, 0, 0}, z3[3] = {0, 0, 0}, zp = 0;
+            if (act) {
+#pragma unroll 4
+                for (int k = 0; k < P; ++k) {
+                    const T4 w = Wz[wl][k];
+                    const T4 u0 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[wl][k] * zs);
+                    if constexpr (CO == 8) {
+                        const T4 u1 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[wl][k] * zs + 4);
+                        // u0 = (v0 v1 v2 v''0), u1 = (v''1 v''2 p -): z0 = sum g v, z1 = sum g v'',
+                        // z2 = sum g s_z v, z3 = sum g s_z v''
+                        z0[0] += w.x * u0.x; z0[1] += w.x * u0.y; z0[2] += w.x * u0.z;
+                        z1[0] += w.x * u0.w; z1[1] += w.x * u1.x; z1[2] += w.x * u1.y;
+                        if constexpr (NCOMP >= 6) {
+                            z2[0] += w.y * u0.x; z2[1] += w.y * u0.y; z2[2] += w.y * u0.z;
+                            if constexpr (NCOMP >= 11) { z3[0] += w.y * u0.w; z3[1] += w.y * u1.x; z3[2] += w.y * u1.y; }
                         }
-                    }
-                    if constexpr (NCOMP >= 12) col[12] += g * u1.z;
-                } else {
-                    const typename V4<T>::t u0 = *reinterpret_cast<const typename V4<T>::t *>(gp);
-                    const T v0 = u0.x, v1 = u0.y, v2 = u0.z;
-                    const T s2 = sx * sx + sy * sy + sz * sz;
-                    const T gu = g * (A0 + A1 * s2);
-                    col[0] += gu * v0;
-                    col[1] += gu * v1;
-                    col[2] += gu * v2;
-                    if constexpr (NCOMP >= 6) {
-                        const T gx_ = g * sx, gy_ = g * sy, gz_ = g * sz;
-                        col[3] += gy_ * v2 - gz_ * v1;
-                        col[4] += gz_ * v0 - gx_ * v2;
-                        col[5] += gx_ * v1 - gy_ * v0;
-                        if constexpr (NCOMP >= 11) {
-                            const T ge = g * (B0 + B1 * s2);
-                            const T ex = ge * sx, ey = ge * sy, ez = ge * sz;
-                            col[6] += ex * v0;
-                            col[7] += ey * v1;
-                            col[8] += ez * v2;
-                            col[9] += ex * v1 + ey * v0;
-                            col[10] += ex * v2 + ez * v0;
-                            col[11] += ey * v2 + ez * v1;
+                        if constexpr (NCOMP >= 12) zp += w.x * u1.z;
+                    } else {
+                        z0[0] += w.x * u0.x; z0[1] += w.x * u0.y; z0[2] += w.x * u0.z;
+                        z2[0] += w.z * u0.x; z2[1] += w.z * u0.y; z2[2] += w.z * u0.z;
+                        if constexpr (NCOMP >= 6) {
+                            z1[0] += w.y * u0.x; z1[1] += w.y * u0.y; z1[2] += w.y * u0.z;
+                            if constexpr (NCOMP >= 11) { z3[0] += w.w * u0.x; z3[1] += w.w * u0.y; z3[2] += w.w * u0.z; }
                         }
+                        if constexpr (NCOMP >= 12) zp += w.x * u0.w;
                     }
-                    if constexpr (NCOMP >= 12) col[12] += g * u0.w;
                 }
             }
+            const T gxy = act ? wx[cx] * wy[cy] : (T)0;
+            const T sx = sx0 + cx, sy = sy0 + cy, sxy2 = sx * sx + sy * sy;
+            T col[NA];
+            if constexpr (CO == 8) {
+                // U = sum g (v + a^2/6 v''); Omega ~ sum g s x v; E ~ sum g sym(s (x) (v + a^2/10 v''))
+                col[0] = gxy * (z0[0] + c6 * z1[0]);
+                col[1] = gxy * (z0[1] + c6 * z1[1]);
+                col[2] = gxy * (z0[2] + c6 * z1[2]);
+                col[3] = gxy * (sy * z0[2] - z2[1]);
+                col[4] = gxy * (z2[0] - sx * z0[2]);
+                col[5] = gxy * (sx * z0[1] - sy * z0[0]);
+                const T Q0 = z0[0] + c10 * z1[0], Q1 = z0[1] + c10 * z1[1], Q2 = z0[2] + c10 * z1[2];
+                const T R0 = z2[0] + c10 * z3[0], R1 = z2[1] + c10 * z3[1], R2 = z2[2] + c10 * z3[2];
+                col[6] = gxy * sx * Q0;
+                col[7] = gxy * sy * Q1;
+                col[8] = gxy * R2;
+                col[9] = gxy * (sx * Q1 + sy * Q0);
+                col[10] = gxy * (sx * Q2 + R0);
+                col[11] = gxy * (sy * Q2 + R1);
+            } else {
+                // z0 = sum g v, z1 = sum g s_z v, z2 = sum g s_z^2 v, z3 = sum g s_z^3 v
+                const T a0 = A0 + A1 * sxy2, b0 = B0 + B1 * sxy2;
+                col[0] = gxy * (a0 * z0[0] + A1 * z2[0]);
+                col[1] = gxy * (a0 * z0[1] + A1 * z2[1]);
+                col[2] = gxy * (a0 * z0[2] + A1 * z2[2]);
+                col[3] = gxy * (sy * z0[2] - z1[1]);
+                col[4] = gxy * (z1[0] - sx * z0[2]);
+                col[5] = gxy * (sx * z0[1] - sy * z0[0]);
+                const T Q0 = b0 * z0[0] + B1 * z2[0], Q1 = b0 * z0[1] + B1 * z2[1], Q2 = b0 * z0[2] + B1 * z2[2];
+                const T R0 = b0 * z1[0] + B1 * z3[0], R1 = b0 * z1[1] + B1 * z3[1], R2 = b0 * z1[2] + B1 * z3[2];
+                col[6] = gxy * sx * Q0;
+                col[7] = gxy * sy * Q1;
+                col[8] = gxy * R2;
+                col[9] = gxy * (sx * Q1 + sy * Q0);
+                col[10] = gxy * (sx * Q2 + R0);
+                col[11] = gxy * (sy * Q2 + R1);
+            }
+            col[12] = gxy * zp;
 #pragma unroll
             for (int cc = 0; cc < NA; ++cc) kahan_add(acc[cc], cmp[cc], col[cc]);
         }
@@ -621,7 +667,7 @@ static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_
 {
     const int nt = p.ntile, ntiles = nt * nt * nt;
     auto args = [&](auto kern) {
-        kern<<<ntiles, 128, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base, (const T *)c->b.sup_s0[pix<T>()],
+        kern<<<ntiles, 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base, (const T *)c->b.sup_s0[pix<T>()],
                                      (const T *)c->b.sup_w[pix<T>()], c->b.rad, xs, (T *)c->b.grid_f[pix<T>()]);
     };
     if (ncomp <= 3) args(spread_kernel<T, 3>);
