@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["mono_n200k", "batch64"], default="mono_n200k")
+    ap.add_argument("--autotune", action="store_true", help="batch64: time candidate parameters per box")
     ap.add_argument("--n", type=int, default=200000,
                     help="spheres (N-sweep of the large-scale configuration at the same phi and grid density)")
     return ap.parse_args()
@@ -331,11 +333,78 @@ def run_ours(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args, rank, world, local):
+    """64 independent boxes (N ~ U[500, 8000], radii 1 and 1.5, phi ~ U[0.1, 0.45]),
+    forces only, FP32, per-box parameters for 1e-6; one step = one product of every box.
+    The captured graph (boxes concurrent on 8 streams) against a per-box launch loop."""
+    import torch
+    from paper_1506_08481_b300 import api, inputs, params
+
+    torch.cuda.set_device(local)
+    boxes = inputs.batch_boxes(seed=0)
+    rng = np.random.default_rng(1)
+    ctxs, xs, ys, chosen = [], [], [], []
+    for cfg in boxes:
+        if args.autotune:
+            sp, mode, _ = params.autotune(cfg, 1e-6, ncomp=3)
+        else:
+            sp, mode = params.choose(cfg.L, cfg.N, 1e-6, M_max=128), 1
+        c = api.Context(local)
+        c.set_params(sp.xi, sp.M, sp.P, sp.rc)
+        c.set_option(api.SE_OPT_SHAPE_M, sp.m)
+        c.set_option(api.SE_OPT_SIZE_MODE, mode)
+        c.set_config(cfg.pos, cfg.rad, cfg.L)
+        xs.append(torch.tensor(rng.standard_normal((cfg.N, 3)), device=f"cuda:{local}", dtype=torch.float32))
+        ys.append(torch.empty_like(xs[-1]))
+        ctxs.append(c)
+        chosen.append((sp.M, sp.P))
+    stream = torch.cuda.current_stream()
+
+    def timed(batch, use_graph):
+        for _ in range(args.warmup):
+            batch.apply(xs, ys, use_graph=use_graph)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            batch.apply(xs, ys, use_graph=use_graph)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    launches0 = sum(c.kernel_launches() for c in ctxs)
+    b = api.Batch(ctxs, nstreams=1)
+    ms_loop = timed(b, False)
+    b.close()
+    b = api.Batch(ctxs, nstreams=8)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_graph = timed(b, True)
+    clk = clocks.stop()
+    b.close()
+    ntot = sum(c.N for c in boxes)
+    if rank == 0:
+        line = {"metric": "aggregate box products/s, 64 uneven boxes (forces only)", "value": world * 64 / (ms_graph * 1e-3),
+                "unit": "box products/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "batch64", "boxes": 64, "N_total": ntot, "ncomp": 3,
+                           "params": "autotuned" if args.autotune else "error-model choice for 1e-6",
+                           "M_P_per_box": chosen, "streams": 8},
+                "per_box_launch_loop": {"value": world * 64 / (ms_loop * 1e-3), "ms_per_step": ms_loop},
+                "graph_speedup": ms_loop / ms_graph,
+                "gpu_launches_setup_and_eager": sum(c.kernel_launches() for c in ctxs) - launches0,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch64":
+        run_batch(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

@@ -87,7 +87,7 @@ typedef struct se_ctx se_ctx;
 /* preconditioners for se_solve */
 #define SE_PRECOND_NONE    0
 #define SE_PRECOND_BLOCK   1   /* block-diagonal self + own-image blocks (Sec. 4.2) */
-#define SE_PRECOND_LEARNED 2   /* block preconditioner + learned correction (falls back to BLOCK) */
+#define SE_PRECOND_LEARNED 2   /* block preconditioner + learned correction (BLOCK without weights) */
 
 /* Create a context on CUDA device `device`; `stream` is a cudaStream_t (may be 0 for
  * the legacy default stream), borrowed for the context's lifetime.  *out receives the
@@ -158,6 +158,45 @@ int se_solve(se_ctx *ctx, int ncomp, const void *b, void *x, int dtype, double r
 int se_real_space_apply_noalloc(int device, void *stream, int64_t N, double L, double xi, double rc,
                                 double eta, const double *pos, const double *radius, int ncomp,
                                 const double *x, double *y);
+
+/* Learned preconditioner correction (SE_PRECOND_LEARNED).  A small network (16 -> 64 ->
+ * 64 -> 4, tanh, FP32) maps rotation- and permutation-invariant features of a sphere's
+ * radius and of its neighbours inside rc to corrections of the isotropic parts of its
+ * block of the Sec. 4.2 preconditioner; blocks that would not be invertible fall back
+ * to the plain block.  Weights are SE_MLP_NW packed floats (layout in se_learned.cu),
+ * produced by paper_1506_08481_b300/train_pc.py.
+ *   se_set_learned_weights: copies the HOST array w; SE_ERR_NONFINITE on NaN/Inf.
+ *   se_learned_features   : DEVICE feat [N][16] in caller order for the configuration.
+ *   se_mlp_forward        : DEVICE w, X [n][16] -> Y [n][4] (dimensionless corrections).
+ *   se_mlp_grad           : gradient DEVICE grad [SE_MLP_NTRAIN] and loss [1] of the mean
+ *                           squared error of the standardised outputs against Yt [n][4];
+ *                           scratch >= n * 276 floats (SE_ERR_TOO_LARGE otherwise).
+ *   se_mlp_adam_step      : one Adam update (beta 0.9, 0.999) of the trained parameters.
+ * The network's kernels are asynchronous on `stream` except se_learned_features. */
+#define SE_MLP_NW     5544
+#define SE_MLP_NTRAIN 5508
+int se_set_learned_weights(se_ctx *ctx, const float *w, int nw);
+int se_learned_features(se_ctx *ctx, float *feat);
+int se_mlp_forward(const float *w, const float *X, int n, float *Y, void *stream);
+int se_mlp_grad(const float *w, const float *X, const float *Yt, int n, float *grad, float *loss,
+                float *scratch, size_t scratch_floats, void *stream);
+int se_mlp_adam_step(float *w, float *m, float *v, const float *grad, int step, float lr, void *stream);
+
+/* Batches of independent boxes (uneven N, each with its own context and parameters).
+ * se_batch_create borrows nbox configured contexts (they must outlive the batch) and
+ * runs box i on the i-th (mod nstreams) of nstreams streams it creates, forked from
+ * and joined back to `stream`.
+ * se_batch_apply enqueues y[i] = M_inf(box i) . x[i] for every box (DEVICE arrays
+ * [N_i][ncomp] of `dtype`).  With use_graph = 1 the first call (and any call with other
+ * pointers, ncomp or dtype) runs the batch once eagerly, captures it into one CUDA graph
+ * and launches it; later calls only launch the graph.  With use_graph = 0 every box's
+ * kernels are launched one by one.  Asynchronous on `stream`; errors as for
+ * se_mobility_apply, described by se_batch_last_error. */
+typedef struct se_batch se_batch;
+int se_batch_create(se_batch **out, se_ctx *const *ctx, int nbox, int nstreams, void *stream);
+int se_batch_apply(se_batch *b, int ncomp, const void *const *x, void *const *y, int dtype, int use_graph);
+int se_batch_destroy(se_batch *b);
+const char *se_batch_last_error(const se_batch *b);
 
 /* Message describing the last failure on this context ("" if none).  Valid until the
  * next call on the same context.  ctx may be NULL (returns the last create failure). */

@@ -31,7 +31,11 @@ SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED = 0, 1, 2
 # every entry point declared in include/se_mobility.h
 ABI_SYMBOLS = ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
                "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_last_error",
-               "se_kernel_launches", "se_stage_times", "se_real_space_apply_noalloc")
+               "se_kernel_launches", "se_stage_times", "se_real_space_apply_noalloc",
+               "se_set_learned_weights", "se_learned_features", "se_mlp_forward", "se_mlp_grad",
+               "se_mlp_adam_step", "se_batch_create", "se_batch_apply", "se_batch_destroy",
+               "se_batch_last_error")
+SE_MLP_NW, SE_MLP_NTRAIN, SE_MLP_SAMPLE = 5544, 5508, 276
 
 _lib = None
 
@@ -67,6 +71,21 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.se_stage_times.restype = i
     lib.se_real_space_apply_noalloc.argtypes = [i, p, i64, d, d, d, d, p, p, i, p, p]
     lib.se_real_space_apply_noalloc.restype = i
+    lib.se_set_learned_weights.argtypes = [p, p, i]
+    lib.se_learned_features.argtypes = [p, p]
+    lib.se_mlp_forward.argtypes = [p, p, i, p, p]
+    lib.se_mlp_grad.argtypes = [p, p, p, i, p, p, p, ctypes.c_size_t, p]
+    lib.se_mlp_adam_step.argtypes = [p, p, p, p, i, ctypes.c_float, p]
+    for name in ("se_set_learned_weights", "se_learned_features", "se_mlp_forward", "se_mlp_grad",
+                 "se_mlp_adam_step"):
+        getattr(lib, name).restype = i
+    lib.se_batch_create.argtypes = [ctypes.POINTER(p), ctypes.POINTER(p), i, i, p]
+    lib.se_batch_apply.argtypes = [p, i, ctypes.POINTER(p), ctypes.POINTER(p), i, i]
+    lib.se_batch_destroy.argtypes = [p]
+    lib.se_batch_last_error.argtypes = [p]
+    lib.se_batch_last_error.restype = ctypes.c_char_p
+    for name in ("se_batch_create", "se_batch_apply", "se_batch_destroy"):
+        getattr(lib, name).restype = i
     for name in ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
                  "se_mobility_apply", "se_mobility_apply_host", "se_solve"):
         getattr(lib, name).restype = i
@@ -191,6 +210,21 @@ class Context:
 
     apply_host = se_mobility_apply_host
 
+    # --- learned preconditioner correction
+    def se_set_learned_weights(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32).reshape(-1)
+        self._check(self.lib.se_set_learned_weights(self.h, w.ctypes.data_as(ctypes.c_void_p), w.size))
+
+    set_learned_weights = se_set_learned_weights
+
+    def se_learned_features(self):
+        import torch
+        f = torch.empty(self.N, 16, device=f"cuda:{self.device}", dtype=torch.float32)
+        self._check(self.lib.se_learned_features(self.h, ctypes.c_void_p(f.data_ptr())))
+        return f
+
+    learned_features = se_learned_features
+
     # --- se_solve
     def se_solve(self, b, x=None, rtol: float = 1e-6, maxit: int = 500, precond: int = SE_PRECOND_BLOCK,
                  ncomp: int | None = None, allow_not_converged: bool = False):
@@ -211,3 +245,77 @@ class Context:
         return x, iters.value, relres.value
 
     solve = se_solve
+
+
+# --- network kernels (stand-alone; device tensors)
+def mlp_forward(w, X):
+    import torch
+    Y = torch.empty(X.shape[0], 4, device=X.device, dtype=torch.float32)
+    rc = load().se_mlp_forward(ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                               ctypes.c_void_p(Y.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != SE_OK:
+        raise SeError(rc, "se_mlp_forward failed")
+    return Y
+
+
+def mlp_grad(w, X, Yt, scratch=None):
+    import torch
+    n = X.shape[0]
+    if scratch is None or scratch.numel() < n * SE_MLP_SAMPLE:
+        scratch = torch.empty(n * SE_MLP_SAMPLE, device=X.device, dtype=torch.float32)
+    g = torch.empty(SE_MLP_NTRAIN, device=X.device, dtype=torch.float32)
+    loss = torch.empty(1, device=X.device, dtype=torch.float32)
+    rc = load().se_mlp_grad(ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                            ctypes.c_void_p(Yt.data_ptr()), n, ctypes.c_void_p(g.data_ptr()),
+                            ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(scratch.data_ptr()),
+                            scratch.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != SE_OK:
+        raise SeError(rc, "se_mlp_grad failed")
+    return g, loss, scratch
+
+
+def mlp_adam_step(w, m, v, g, step, lr):
+    import torch
+    rc = load().se_mlp_adam_step(ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(m.data_ptr()),
+                                 ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(g.data_ptr()), int(step),
+                                 float(lr), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != SE_OK:
+        raise SeError(rc, "se_mlp_adam_step failed")
+
+
+class Batch:
+    """Independent boxes applied together (se_batch_*); contexts must be configured."""
+
+    def __init__(self, contexts, nstreams: int = 8, stream=None):
+        import torch
+        self.lib = load()
+        self.ctxs = list(contexts)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.ctxs[0].device)
+        self.stream = stream
+        arr = (ctypes.c_void_p * len(self.ctxs))(*[c.h for c in self.ctxs])
+        h = ctypes.c_void_p()
+        rc = self.lib.se_batch_create(ctypes.byref(h), arr, len(self.ctxs), int(nstreams),
+                                      ctypes.c_void_p(stream.cuda_stream))
+        if rc != SE_OK:
+            raise SeError(rc, "se_batch_create failed")
+        self.h = h
+
+    def apply(self, xs, ys, use_graph: bool = True):
+        ncomp = xs[0].shape[-1]
+        xa = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        ya = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+        rc = self.lib.se_batch_apply(self.h, int(ncomp), xa, ya, _dtype_code(xs[0]), int(bool(use_graph)))
+        if rc != SE_OK:
+            raise SeError(rc, self.lib.se_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.se_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -245,6 +245,7 @@ extern "C" int se_destroy(se_ctx *c)
     cudaStreamSynchronize(c->aux);
     free_grids(c);
     free_config(c);
+    dfree_t(c->b.mlp_w);
     cudaEventDestroy(c->ev_fork);
     cudaEventDestroy(c->ev_join);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);

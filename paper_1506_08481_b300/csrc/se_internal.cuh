@@ -71,6 +71,7 @@ struct Buffers {
     double *stage = nullptr;     // [2][N][12]
     // solver
     double *pc_inv = nullptr;    // [N][nc][nc] inverse preconditioner blocks (caller order)
+    float *mlp_w = nullptr;      // learned correction network (packed parameters)
     double *kry = nullptr;       // Krylov basis [restart + 1][n]
     double *work64 = nullptr;    // FP64 work vectors [5][n]
     double *red = nullptr;       // reduction scratch
@@ -104,7 +105,9 @@ struct se_ctx {
     int nc = 1;
     // preconditioner state
     bool pc_ready = false;
-    int pc_ncomp = 0, pc_prec = -1;
+    int pc_ncomp = 0, pc_prec = -1, pc_kind = -1;
+    bool have_mlp = false;
+    int pc_fallbacks = 0;              // particles whose learned block fell back to the plain one
     se::FftPlan plan{};
     se::Buffers b;
     size_t alloc_N = 0;
@@ -135,6 +138,10 @@ template <typename T>
 void setup_rel(se_ctx *c, cudaStream_t s);
 template <typename T>
 int build_pair_table(se_ctx *c);
+// se_learned.cu: per-particle learned corrections [N][4] (caller order)
+int learned_corrections(se_ctx *c, double *d_dev);
+// se_solve.cu
+void convert_f2d(int n, const float *x, double *y, cudaStream_t s);
 // exclusive scan of n ints into out[0..n] on stream s
 void launch_scan(se_ctx *c, int n, const int *in, int *out, cudaStream_t s);
 

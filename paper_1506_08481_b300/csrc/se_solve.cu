@@ -112,14 +112,24 @@ __global__ void block_apply_kernel(int N, int nc, const double *Binv, const doub
 // Block of particle with radius a: isolated-sphere self terms + C0 + a^2 C1 + a^4 C2,
 // inverted by Gauss-Jordan elimination with partial pivoting.  Sorted particle k is
 // stored at caller index perm[k].  Singular blocks fall back to the isolated inverse.
+// `corr` (may be null, caller order [N][4]): learned dimensionless corrections of the
+// isotropic parts, each scaled by the isolated-sphere mobility of its block.  A learned
+// block that cannot be inverted falls back to the plain block (counted in *fallbacks).
 __global__ void block_build_kernel(int N, int nc, double eta, const double *rad, const int *perm,
-                                   const double *C /*[3][12][12]*/, double *Binv)
+                                   const double *C /*[3][12][12]*/, const double *corr, double *Binv,
+                                   int *fallbacks)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     const double a = rad[k], a2 = a * a;
     double A[kNC][2 * kNC];
     const double pi = kPi;
+    const double *d = corr ? corr + (size_t)perm[k] * 4 : nullptr;
+    bool use_corr = d != nullptr;
+    if (use_corr)
+        for (int q = 0; q < 4; ++q) use_corr &= isfinite(d[q]) != 0;
+    if (d && !use_corr) atomicAdd(fallbacks, 1);
+retry:
     for (int r = 0; r < nc; ++r) {
         for (int q = 0; q < nc; ++q) {
             A[r][q] = C[r * kNC + q] + a2 * C[kNC * kNC + r * kNC + q] + a2 * a2 * C[2 * kNC * kNC + r * kNC + q];
@@ -128,7 +138,8 @@ __global__ void block_build_kernel(int N, int nc, double eta, const double *rad,
         const double iso = r < 3 ? 1.0 / (6 * pi * eta * a)
                          : r < 6 ? 1.0 / (8 * pi * eta * a * a2)
                          : r < 11 ? 3.0 / (20 * pi * eta * a * a2) : 3.0 / (16 * pi * eta * a * a2);
-        A[r][r] += iso;
+        const double dc = use_corr ? d[r < 3 ? 0 : r < 6 ? 1 : r < 11 ? 2 : 3] : 0.0;
+        A[r][r] += iso * (1.0 + dc);
     }
     bool ok = true;
     for (int col = 0; col < nc && ok; ++col) {
@@ -147,6 +158,19 @@ __global__ void block_build_kernel(int N, int nc, double eta, const double *rad,
                 for (int q = 0; q < 2 * nc; ++q) A[r][q] -= f * A[col][q];
         }
     }
+    if (use_corr) {
+        bool fin = ok;
+        for (int r = 0; r < nc && fin; ++r)
+            for (int q = 0; q < nc; ++q) fin &= isfinite(A[r][nc + q]) != 0;
+        // the corrected block must stay positive on its diagonal (a mobility)
+        for (int r = 0; r < nc && fin; ++r) fin &= A[r][nc + r] > 0;
+        if (!fin) {
+            atomicAdd(fallbacks, 1);
+            use_corr = false;
+            ok = true;
+            goto retry;
+        }
+    }
     double *out = Binv + (size_t)perm[k] * nc * nc;
     for (int r = 0; r < nc; ++r)
         for (int q = 0; q < nc; ++q) {
@@ -162,11 +186,16 @@ __global__ void block_build_kernel(int N, int nc, double eta, const double *rad,
 
 }  // namespace
 
+void convert_f2d(int n, const float *x, double *y, cudaStream_t s)
+{
+    convert_kernel<float, double><<<(n + 255) / 256, 256, 0, s>>>((size_t)n, x, y);
+}
+
 static int grid_for(size_t n) { size_t g = (n + 255) / 256; return (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g)); }
 
 // ---------------------------------------------------------------- preconditioner
 
-static int build_precond(se_ctx *c, int ncomp)
+static int build_precond(se_ctx *c, int ncomp, bool learned)
 {
     cudaStream_t s = c->stream;
     const int N = (int)c->N;
@@ -257,12 +286,37 @@ static int build_precond(se_ctx *c, int ncomp)
         c->err = "preconditioner allocation failed";
         return SE_ERR_NOMEM;
     }
-    block_build_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->eta, c->b.rad, c->b.perm, dC, c->b.pc_inv);
+    double *corr = nullptr;
+    int *dfb = nullptr;
+    if (cudaMalloc(&dfb, sizeof(int)) != cudaSuccess) { cudaFree(dC); return SE_ERR_NOMEM; }
+    cudaMemsetAsync(dfb, 0, sizeof(int), s);
+    if (learned) {
+        if (cudaMalloc(&corr, (size_t)N * 4 * sizeof(double)) != cudaSuccess) {
+            cudaFree(dC);
+            cudaFree(dfb);
+            return SE_ERR_NOMEM;
+        }
+        const int r = learned_corrections(c, corr);
+        if (r != SE_OK) {
+            cudaFree(dC);
+            cudaFree(dfb);
+            cudaFree(corr);
+            return r;
+        }
+    }
+    block_build_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->eta, c->b.rad, c->b.perm, dC, corr, c->b.pc_inv,
+                                                       dfb);
     c->launches++;
+    int fb = 0;
+    cudaMemcpyAsync(&fb, dfb, sizeof(int), cudaMemcpyDeviceToHost, s);
     SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
     cudaFree(dC);
+    cudaFree(dfb);
+    if (corr) cudaFree(corr);
+    c->pc_fallbacks = fb;
     c->pc_ready = true;
     c->pc_ncomp = ncomp;
+    c->pc_kind = learned ? SE_PRECOND_LEARNED : SE_PRECOND_BLOCK;
     return SE_OK;
 }
 
@@ -336,8 +390,10 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
         convert_kernel<float, double><<<grid_for(n), 256, 0, s>>>(n, (const float *)x, xd);
         c->launches += 2;
     }
-    if (precond != SE_PRECOND_NONE && (!c->pc_ready || c->pc_ncomp != ncomp)) {
-        int rc = build_precond(c, ncomp);
+    // the learned correction needs trained weights; without them it is the plain block
+    const int kind = precond == SE_PRECOND_LEARNED && c->have_mlp ? SE_PRECOND_LEARNED : SE_PRECOND_BLOCK;
+    if (precond != SE_PRECOND_NONE && (!c->pc_ready || c->pc_ncomp != ncomp || c->pc_kind != kind)) {
+        int rc = build_precond(c, ncomp, kind == SE_PRECOND_LEARNED);
         if (rc != SE_OK) return rc;
     }
     auto Pinv = [&](const double *v, double *out) {

@@ -104,3 +104,55 @@ def choose(L: float, N: int, tol: float, P: int | None = None, M_max: int = 384,
     if best is None:
         raise ValueError("no grid up to M_max meets the accuracy with rc < L/2")
     return best[1]
+
+
+def candidates(L: float, N: int, tol: float, M_max: int = 384, supports=None) -> list[SeParams]:
+    """Distinct parameter sets meeting the error model at tol: the cheapest per grid size
+    for each support."""
+    out, seen = [], set()
+    for P in (supports or [None]):
+        for M in fft_sizes(16, M_max):
+            try:
+                sp = choose(L, N, tol, P=P, M_max=M, M_min=M)
+            except ValueError:
+                continue
+            key = (sp.M, sp.P)
+            if key not in seen:
+                seen.add(key)
+                out.append(sp)
+    return out
+
+
+def autotune(cfg, tol: float, ncomp: int = 3, precision: int = 0, max_candidates: int = 4, reps: int = 3,
+             supports=None):
+    """Time the cheapest few candidate parameter sets (and both particle-size modes) for a
+    configuration on the GPU and return (SeParams, size_mode, ms per product) of the fastest."""
+    import torch
+    from . import api
+    cands = sorted(candidates(cfg.L, cfg.N, tol, supports=supports),
+                   key=lambda s: s.M ** 3 * math.log2(s.M) * 0.5 + 0.1 * cfg.N * s.P ** 3
+                   + cfg.N ** 2 / cfg.L ** 3 * 4.19 * s.rc ** 3)[:max_candidates]
+    x = torch.randn(cfg.N, ncomp, device="cuda", dtype=torch.float32 if precision == 0 else torch.float64)
+    y = torch.empty_like(x)
+    best = None
+    for sp in cands:
+        for mode in (1, 0):
+            ctx = api.Context()
+            ctx.set_params(sp.xi, sp.M, sp.P, sp.rc)
+            ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
+            ctx.set_option(api.SE_OPT_SIZE_MODE, mode)
+            ctx.set_option(api.SE_OPT_PRECISION, precision)
+            ctx.set_config(cfg.pos, cfg.rad, cfg.L)
+            ctx.apply(x, y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                ctx.apply(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            ctx.close()
+            if best is None or ms < best[2]:
+                best = (sp, mode, ms)
+    return best

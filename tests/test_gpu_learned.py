@@ -1,0 +1,118 @@
+"""Learned correction of the block-diagonal preconditioner: the hand-written network
+kernels against the FP64 reference network (oracle/mlp.py), training, fallbacks, and
+what the trained network gains over the plain block preconditioner."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import mlp as ref  # noqa: E402
+from paper_1506_08481_b300 import api, inputs, params  # noqa: E402
+
+WEIGHTS = os.path.join(os.path.dirname(api.__file__), "learned_pc_weights.npy")
+
+
+def random_weights(rng, scale=0.3):
+    w = rng.standard_normal(ref.NW) * scale
+    w[ref.NTRAIN:ref.NTRAIN + 16] = rng.standard_normal(16) * 0.2            # mu
+    w[ref.NTRAIN + 16:ref.NTRAIN + 32] = rng.uniform(0.5, 2.0, 16)            # sd
+    w[ref.NTRAIN + 32:] = rng.uniform(0.5, 2.0, 4)                            # os
+    return w.astype(np.float32)
+
+
+def test_forward_and_gradient_match_reference_network():
+    rng = np.random.default_rng(0)
+    w = random_weights(rng)
+    X = rng.standard_normal((777, 16)).astype(np.float32)
+    Yt = rng.standard_normal((777, 4)).astype(np.float32)
+    wt, Xt, Yt_t = (torch.tensor(a, device="cuda") for a in (w, X, Yt))
+    Y = api.mlp_forward(wt, Xt).double().cpu().numpy()
+    Yr = ref.forward(w.astype(np.float64), X.astype(np.float64))
+    assert np.linalg.norm(Y - Yr) / np.linalg.norm(Yr) <= 1e-5
+    g, loss, _ = api.mlp_grad(wt, Xt, Yt_t)
+    lr, gr = ref.loss_and_grad(w.astype(np.float64), X.astype(np.float64), Yt.astype(np.float64))
+    assert abs(float(loss.item()) - lr) <= 1e-5 * lr
+    g = g.double().cpu().numpy()
+    assert np.linalg.norm(g - gr) / np.linalg.norm(gr) <= 1e-4
+
+
+def test_adam_training_reduces_the_loss():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((4096, 16)).astype(np.float32)
+    Yt = np.stack([np.tanh(X[:, 0] - X[:, 3]), X[:, 1] * X[:, 2] * 0.3, np.sin(X[:, 5]), 0 * X[:, 0]], 1)
+    w = random_weights(rng, 0.2)
+    w[ref.NTRAIN:ref.NTRAIN + 16] = 0.0
+    w[ref.NTRAIN + 16:ref.NTRAIN + 32] = 1.0
+    w[ref.NTRAIN + 32:] = 1.0
+    wt, Xt, Yt_t = torch.tensor(w, device="cuda"), torch.tensor(X, device="cuda"), torch.tensor(Yt.astype(np.float32), device="cuda")
+    m, v = torch.zeros(api.SE_MLP_NTRAIN, device="cuda"), torch.zeros(api.SE_MLP_NTRAIN, device="cuda")
+    g, l0, scratch = api.mlp_grad(wt, Xt, Yt_t)
+    l0 = float(l0.item())
+    for step in range(1, 301):
+        g, loss, scratch = api.mlp_grad(wt, Xt, Yt_t, scratch)
+        api.mlp_adam_step(wt, m, v, g, step, 3e-3)
+    assert float(loss.item()) < 0.2 * l0
+
+
+def _solve_ctx(cfg):
+    sp = params.choose(cfg.L, cfg.N, 1e-8, M_max=96)
+    ctx = api.Context()
+    ctx.set_params(sp.xi, sp.M, sp.P, sp.rc)
+    ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
+    ctx.set_option(api.SE_OPT_PRECISION, 1)
+    ctx.set_option(api.SE_OPT_RESTART, 100)
+    ctx.set_config(cfg.pos, cfg.rad, cfg.L)
+    return ctx
+
+
+def test_without_weights_learned_is_the_block_preconditioner():
+    cfg = inputs.lognormal(seed=7, n=300, phi=0.3)
+    ctx = _solve_ctx(cfg)
+    b = torch.tensor(np.random.default_rng(2).standard_normal((cfg.N, 11)), device="cuda")
+    x1, i1, r1 = ctx.solve(b, rtol=1e-8, maxit=400, precond=api.SE_PRECOND_BLOCK)
+    x2, i2, r2 = ctx.solve(b, rtol=1e-8, maxit=400, precond=api.SE_PRECOND_LEARNED)
+    assert i1 == i2 and torch.equal(x1, x2)
+
+
+def test_bad_weights_are_rejected_or_fall_back():
+    cfg = inputs.lognormal(seed=8, n=300, phi=0.3)
+    ctx = _solve_ctx(cfg)
+    w = random_weights(np.random.default_rng(3))
+    bad = w.copy()
+    bad[5] = np.nan
+    with pytest.raises(api.SeError) as e:
+        ctx.set_learned_weights(bad)
+    assert e.value.code == api.SE_ERR_NONFINITE
+    # corrections that would make every block negative fall back to the plain block
+    w[ref.NTRAIN - 4:ref.NTRAIN] = -50.0          # b3
+    w[:ref.NTRAIN - 4] *= 0.0
+    ctx.set_learned_weights(w)
+    b = torch.tensor(np.random.default_rng(4).standard_normal((cfg.N, 11)), device="cuda")
+    x1, i1, _ = ctx.solve(b, rtol=1e-8, maxit=400, precond=api.SE_PRECOND_BLOCK)
+    x2, i2, r2 = ctx.solve(b, rtol=1e-8, maxit=400, precond=api.SE_PRECOND_LEARNED)
+    assert r2 <= 1e-8 and i1 == i2
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained weights in the package")
+def test_trained_network_gain_on_held_out_configurations():
+    """Held-out log-normal configurations (seeds disjoint from training): the learned
+    preconditioner needs no more products than the plain block one, and both solutions
+    agree (the network only changes the iteration count)."""
+    w = np.load(WEIGHTS)
+    gains = []
+    for seed in (5001, 5002, 5003):
+        cfg = inputs.lognormal(seed=seed, n=600, phi=0.4)
+        ctx = _solve_ctx(cfg)
+        b = torch.tensor(np.random.default_rng(seed).standard_normal((cfg.N, 11)), device="cuda")
+        xb, ib, rb = ctx.solve(b, rtol=1e-8, maxit=800, precond=api.SE_PRECOND_BLOCK)
+        ctx.set_learned_weights(w)
+        xl, il, rl = ctx.solve(b, rtol=1e-8, maxit=800, precond=api.SE_PRECOND_LEARNED)
+        assert rb <= 1e-8 and rl <= 1e-8
+        assert float(torch.linalg.norm(xl - xb) / torch.linalg.norm(xb)) <= 1e-6
+        gains.append(ib / il)
+    print("iterations block/learned:", gains)
+    assert np.mean(gains) >= 1.0
