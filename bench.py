@@ -39,9 +39,15 @@ WORKLOAD = "mono_n200000_phi0.45_ncomp12_P24"
 # paper_1506_08481_b300.params with its prefactor calibrated on the oracle rows.
 PARAMS = dict(xi=0.6, M=216, P=24, rc=7.5, m=8.68, size_mode=1)
 
-# per-point arithmetic of the hot kernels (FP32 flops, FMA = 2), for the ALU roofline
-FLOPS_PER_POINT = {"spread": 50.0, "gather": 44.0}
+# arithmetic of the ALU-bound kernels (FP32 flop, FMA = 2): 13 FMAs per support point
+# (the z-moment / column-coefficient form) plus the per-column work amortised over the
+# P points of a column (spread: 13 column coefficients; gather: moment-to-output
+# conversion and the compensated column sums)
+FLOPS_PER_POINT = {"spread": 26.0, "gather": 26.0}
+FLOPS_PER_COLUMN = {"spread": 75.0, "gather": 72.0}
 FP32_LANES_PER_SM, SMS = 128, 148
+# bytes of one stored real-space pair in FP32 (index 4 + separation 12 + 19 coefficients)
+PAIR_BYTES = 92
 
 
 def parse():
@@ -52,6 +58,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU product and solve")
+    ap.add_argument("--solve-maxit", type=int, default=800)
+    ap.add_argument("--no-tuned", action="store_true", help="skip the error-model-tuned product")
+    ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2],
+                    help="real-space sum beside the spread (0), beside the FFT chain (1), in line (2)")
+    ap.add_argument("--fp64-solve-maxit", type=int, default=100,
+                    help="iterations of the plain FP64 solve that are timed (it runs ~20x slower)")
     ap.add_argument("--workload", choices=["mono_n200k", "batch64"], default="mono_n200k")
     ap.add_argument("--autotune", action="store_true", help="batch64: time candidate parameters per box")
     ap.add_argument("--n", type=int, default=200000,
@@ -127,17 +140,44 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def stage_algorithmic(stage: str, N: int, M: int, P: int, CO: int):
+def stage_algorithmic(stage: str, N: int, M: int, P: int, CO: int, npairs: int = 0):
     """(bound, units per launch, unit) of one launch of a stage (FP32 grids)."""
     Mh = M // 2 + 1
-    if stage == "spread":
-        return "alu", N * P ** 3 * FLOPS_PER_POINT["spread"], "flop"
-    if stage == "gather":
-        return "alu", N * P ** 3 * FLOPS_PER_POINT["gather"], "flop"
+    if stage in ("spread", "gather"):
+        return "alu", N * P ** 3 * FLOPS_PER_POINT[stage] + N * P ** 2 * FLOPS_PER_COLUMN[stage], "flop"
+    if stage == "real":
+        # the stored pair table streamed once, moments read and results written once
+        return "hbm", npairs * PAIR_BYTES + N * 12 * 4 * 2, "byte"
+    if stage == "permute":
+        return "hbm", N * 12 * 4 * 2, "byte"
     # FFT passes: one read and one write of the arrays they stream (bytes)
     real_f, spec_f, spec_o, real_o = 4 * M ** 3 * 4, 4 * M * M * Mh * 8, CO * M * M * Mh * 8, CO * M ** 3 * 4
     return "hbm", {"fft_x_fwd": real_f + spec_f, "fft_y_fwd": 2 * spec_f, "fft_z_scale": spec_f + spec_o,
                    "fft_y_inv": 2 * spec_o, "fft_x_inv": spec_o + real_o}.get(stage, 0), "byte"
+
+
+def count_pairs(cfg, rc):
+    """Ordered pairs i != j closer than rc (periodic), the rows of the real-space table."""
+    from scipy.spatial import cKDTree
+    pos = np.mod(cfg.pos, cfg.L)
+    t = cKDTree(pos, boxsize=cfg.L)
+    return int(t.count_neighbors(t, rc)) - cfg.N
+
+
+def roofline_entry(stage, ms, N, M, P, CO, npairs, peaks, peak_kind):
+    bound, units, unit = stage_algorithmic(stage, N, M, P, CO, npairs)
+    t = ms * 1e-3
+    if bound == "alu":
+        clk_mhz = peaks.get("sm_max_mhz", 2032.0)
+        peak = SMS * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
+        achieved = units / t / 1e12
+        return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "ms": ms,
+                "peak_source": f"FP32 CUDA cores: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clk_mhz:.0f} MHz"}
+    peak = peaks.get("hbm_gbs", 6400.0)
+    achieved = units / t / 1e9
+    return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "ms": ms, "peak_source": f"hbm_gbs ({peak_kind})"}
 
 
 def cpu_baseline(cfg, x, nrows_small=4, nrows_large=20):
@@ -212,6 +252,7 @@ def run_ours(args, rank, world, local):
     ctx.set_option(api.SE_OPT_SHAPE_M, P_["m"])
     ctx.set_option(api.SE_OPT_SIZE_MODE, P_["size_mode"])
     ctx.set_option(api.SE_OPT_PRECISION, 0)
+    ctx.set_option(api.SE_OPT_OVERLAP, args.overlap)
     ctx.set_config(cfg.pos, cfg.rad, cfg.L)
     x = torch.tensor(x_host, device=dev, dtype=torch.float32)
     y = torch.empty_like(x)
@@ -272,40 +313,128 @@ def run_ours(args, rank, world, local):
         ctx.apply_host(xp, yp)
     e2e = world * ne2e / (time.perf_counter() - t)
 
-    # GMRES solve with the block-diagonal preconditioner, FP32 products + FP64 refinement
+    # the plain FP64 GPU path on the same workload: products/s and accuracy
+    fp64 = None
+    if not args.no_fp64:
+        ctx.set_option(api.SE_OPT_PRECISION, 1)
+        xd = x.double()
+        yd = torch.empty_like(xd)
+        for _ in range(3):
+            ctx.apply(xd, yd)
+        n64 = max(3, args.steps // 4)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n64):
+            ctx.apply(xd, yd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / n64
+        acc64 = None
+        if acc is not None:
+            acc64 = float(np.linalg.norm(yd.cpu().numpy()[g["rows"]] - g["y"]) / np.linalg.norm(g["y"]))
+        fp64 = {"value": world * 1e3 / ms64, "unit": "products/s", "ms_per_product": ms64,
+                "rel_l2_vs_fp64_oracle": acc64, "fp32_speedup": ms64 / ms_step}
+        del xd, yd
+        ctx.set_option(api.SE_OPT_PRECISION, 0)
+
+    # the same product at the parameters the error model picks for this box at 5e-7 in
+    # FP32 (method error plus FP32 rounding floor), so the product still meets 1e-6; the
+    # support P is then the model's choice instead of the configuration's P = 24
+    tuned = None
+    if not args.no_tuned and args.n == 200000:
+        from paper_1506_08481_b300 import params as prm
+        sp = prm.choose(cfg.L, cfg.N, 5e-7, M_max=384, precision=0)
+        ct = api.Context(local)
+        ct.set_params(sp.xi, sp.M, sp.P, sp.rc)
+        ct.set_option(api.SE_OPT_SHAPE_M, sp.m)
+        ct.set_option(api.SE_OPT_SIZE_MODE, 1)
+        ct.set_option(api.SE_OPT_PRECISION, 0)
+        ct.set_config(cfg.pos, cfg.rad, cfg.L)
+        yt = torch.empty_like(x)
+        for _ in range(3):
+            ct.apply(x, yt)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ct.apply(x, yt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mst = e0.elapsed_time(e1) / args.steps
+        acct = None
+        if acc is not None:
+            acct = float(np.linalg.norm(yt.double().cpu().numpy()[g["rows"]] - g["y"]) / np.linalg.norm(g["y"]))
+        tuned = {"value": world * 1e3 / mst, "unit": "products/s", "ms_per_product": mst,
+                 "rel_l2_vs_fp64_oracle": acct,
+                 "params": {"xi": sp.xi, "M": sp.M, "P": sp.P, "rc": sp.rc, "m": sp.m, "model_tol": 5e-7}}
+        ct.close()
+        del yt
+
+    # GMRES solves of M x = b (F, T, S; b = the first 11 input components) to 1e-6:
+    # FP32 products + FP64 true residual and refinement, with the plain block-diagonal
+    # and the learned preconditioner, and the plain FP64 GPU path with the block one
     solve = None
     if not args.no_solve:
         b = torch.tensor(x_host[:, :11], device=dev, dtype=torch.float64)
         xs = torch.zeros_like(b)
         ctx.set_option(api.SE_OPT_RESTART, 100)
-        ctx.solve(b, xs, rtol=1e-6, maxit=2, precond=api.SE_PRECOND_BLOCK, allow_not_converged=True)
-        xs.zero_()
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        _, iters, relres = ctx.solve(b, xs, rtol=1e-6, maxit=600, precond=api.SE_PRECOND_BLOCK,
-                                     allow_not_converged=True)
-        ts = time.perf_counter() - t
-        solve = {"solves_per_s": world / ts, "iterations": iters, "relres_fp64": relres, "ncomp": 11,
-                 "rtol": 1e-6, "precond": "block", "restart": 100, "converged": bool(relres <= 1e-6)}
+        wpath = os.path.join(ROOT, "paper_1506_08481_b300", "learned_pc_weights.npy")
+        if os.path.exists(wpath):
+            ctx.set_learned_weights(np.load(wpath))
+        runs = [("fp32_block", 0, api.SE_PRECOND_BLOCK, args.solve_maxit),
+                ("fp32_learned", 0, api.SE_PRECOND_LEARNED, args.solve_maxit)]
+        if not args.no_fp64:
+            runs.append(("fp64_block", 1, api.SE_PRECOND_BLOCK, args.fp64_solve_maxit))
+        solve = {"ncomp": 11, "rtol": 1e-6, "restart": 100, "maxit": args.solve_maxit,
+                 "learned_weights": os.path.exists(wpath)}
+        for name, prec, pc, maxit in runs:
+            ctx.set_option(api.SE_OPT_PRECISION, prec)
+            ctx.solve(b, xs, rtol=1e-6, maxit=2, precond=pc, allow_not_converged=True)   # setup
+            xs.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, iters, relres = ctx.solve(b, xs, rtol=1e-6, maxit=maxit, precond=pc, allow_not_converged=True)
+            ts = time.perf_counter() - t
+            solve[name] = {"solves_per_s": world / ts, "seconds": ts, "iterations": iters,
+                           "relres_fp64": relres, "converged": bool(relres <= 1e-6)}
+        if "fp64_block" in solve and not solve["fp64_block"]["converged"]:
+            # the FP64 path timed over its first maxit iterations; the time of a whole solve
+            # is projected at the iteration count of the FP32 block-preconditioned solve
+            r = solve["fp64_block"]
+            r["seconds_per_iteration"] = r["seconds"] / max(r["iterations"], 1)
+            r["projected_seconds"] = r["seconds_per_iteration"] * solve["fp32_block"]["iterations"]
+            r["solves_per_s"] = world / r["projected_seconds"]
+            r["note"] = (f"timed over {r['iterations']} iterations; solves/s projected at the FP32 "
+                         f"solve's {solve['fp32_block']['iterations']} iterations")
+        ctx.set_option(api.SE_OPT_PRECISION, 0)
+        solve["solves_per_s"] = solve["fp32_learned"]["solves_per_s"]
 
-    # roofline of the dominant kernel (largest summed device time)
+    # the real-space kernel alone (in the product it runs on a second stream beside the
+    # spread and FFT, so its in-product event time includes the overlap)
+    ctx.set_option(api.SE_OPT_PARTS, 1)
+    ctx.set_option(api.SE_OPT_TIMING, 0)
+    ctx.apply(x, y)
+    ctx.set_option(api.SE_OPT_TIMING, 1)
+    nprod0, st0 = ctx.stage_times()
+    for _ in range(5):
+        ctx.apply(x, y)
+    nprod1, st1 = ctx.stage_times()
+    ctx.set_option(api.SE_OPT_TIMING, 0)
+    ctx.set_option(api.SE_OPT_PARTS, 7)
+    real_alone_ms = (st1["real"] - st0["real"]) / max(nprod1 - nprod0, 1)
+
+    # roofline of every kernel; the dominant one is the serial stage with the largest time
     peaks, peak_kind = measured_peaks()
     CO = 8 if P_["size_mode"] == 0 else 4
-    dom = max(stage_ms, key=lambda k: stage_ms[k])
-    t_launch = stage_ms[dom] / max(nprod, 1) * 1e-3
-    bound, units, unit = stage_algorithmic(dom, cfg.N, P_["M"], P_["P"], CO)
-    if bound == "alu":
-        clk_mhz = peaks.get("sm_max_mhz", 2032.0)
-        peak = SMS * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
-        achieved = units / t_launch / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"FP32 CUDA cores: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clk_mhz:.0f} MHz"}
-    else:
-        peak = peaks.get("hbm_gbs", 6400.0)
-        achieved = units / t_launch / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs ({peak_kind})"}
+    npairs = count_pairs(cfg, P_["rc"])
+    per_prod = {k: v / max(nprod, 1) for k, v in stage_ms.items()}
+    kernels = {}
+    for k, v in per_prod.items():
+        kernels[k] = roofline_entry(k, real_alone_ms if k == "real" else v, cfg.N, P_["M"], P_["P"], CO, npairs,
+                                    peaks, peak_kind)
+    kernels["real"]["note"] = "timed alone (real-space part only); overlapped with spread/FFT in the product"
+    dom = max((k for k in per_prod if k not in ("real", "permute")), key=lambda k: per_prod[k])
+    roof = dict(kernels[dom])
+    roof["traffic"] = None
 
     workload = WORKLOAD if args.n == 200000 else WORKLOAD.replace("n200000", f"n{args.n}")
     if rank == 0:
@@ -318,15 +447,17 @@ def run_ours(args, rank, world, local):
                 "config": {"workload": workload, "N": cfg.N, "L": round(cfg.L, 4), "phi": 0.45, "ncomp": 12,
                            "xi": P_["xi"], "M": P_["M"], "P": P_["P"], "rc": P_["rc"], "m": P_["m"],
                            "size_mode": "real-space" if P_["size_mode"] else "hybrid",
+                           "real_space_overlap": ["beside spread", "beside FFT", "in line"][args.overlap],
                            "parallelism": f"replicas x{world}",
                            "l2": "grids and spectra (>1 GB per product) exceed L2; inputs resident"},
                 "accuracy": {"rel_l2_vs_fp64_oracle": acc, "rows": 64},
                 "roofline": roof,
-                "stage_ms_per_product": {k: v / max(nprod, 1) for k, v in stage_ms.items()},
+                "stage_ms_per_product": per_prod,
+                "kernels": kernels, "npairs_real_space": npairs,
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e, "unit": "products/s", "h2d_bytes_per_step": int(x64.nbytes),
                         "d2h_bytes_per_step": int(y64.nbytes)},
-                "gpu_launches": int(launches), "clocks": clk, "solve": solve}
+                "gpu_launches": int(launches), "clocks": clk, "fp64_product": fp64, "tuned_product": tuned, "solve": solve}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -348,7 +479,8 @@ def run_batch(args, rank, world, local):
         if args.autotune:
             sp, mode, _ = params.autotune(cfg, 1e-6, ncomp=3)
         else:
-            sp, mode = params.choose(cfg.L, cfg.N, 1e-6, M_max=128), 1
+            sp, mode = params.choose(cfg.L, cfg.N, 1e-6, M_max=128, a_eff=params.effective_radius(cfg.rad),
+                                     precision=0), 1
         c = api.Context(local)
         c.set_params(sp.xi, sp.M, sp.P, sp.rc)
         c.set_option(api.SE_OPT_SHAPE_M, sp.m)

@@ -71,6 +71,10 @@ typedef struct se_ctx se_ctx;
 #define SE_OPT_RESTART     5   /* GMRES restart length (default 30) */
 #define SE_OPT_PARTS       6   /* bit mask of terms: 1 real space, 2 wave space, 4 self (default 7) */
 #define SE_OPT_TIMING      7   /* 1: record CUDA events around every stage of each product (default 0) */
+#define SE_OPT_OVERLAP     8   /* where the real-space sum runs: 0 = on a second, high-priority stream
+                                  beside the spread, 1 = beside the FFT chain, 2 = in line before the
+                                  spread (default: the spread and gather fill every SM, so running
+                                  beside them only slows them); results are identical */
 
 /* product stages reported by se_stage_times */
 #define SE_STAGE_PERMUTE   0   /* inputs into cell order */

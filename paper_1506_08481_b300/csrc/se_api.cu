@@ -2,10 +2,11 @@
 // configuration, and the grand-mobility product y = M_inf . x.
 //
 // Product schedule (one call, all on the device, no host round trip):
-//   main stream : permute x into cell order -> [fork] -> spread -> FFT x -> FFT y
-//                 -> FFT z + k-space scaling + inverse z -> inverse y -> inverse x
-//                 -> [join] -> gather + real + self, written in caller order
-//   aux stream  : real-space pair sum (overlaps the memory-bound FFT chain)
+//   permute x into cell order -> real-space pair sum -> spread -> FFT x -> FFT y
+//   -> FFT z + k-space scaling + inverse z -> inverse y -> inverse x
+//   -> gather + real + self, written in caller order.
+// SE_OPT_OVERLAP can move the real-space sum onto a second, high-priority stream
+// beside the spread or the FFT chain (forked and joined with events).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -76,10 +77,14 @@ static void make_plan(int M, FftPlan &plan)
     plan.M = M;
     plan.nst = 0;
     int m = M;
+    // radix 8 and 9 first, then at most two of 6, 4, 3, 2 (M = 2^a 3^b, 8 | M):
+    // every admissible M up to 512 takes at most three passes
     while (m % 8 == 0) { plan.rad[plan.nst++] = 8; m /= 8; }
+    while (m % 9 == 0) { plan.rad[plan.nst++] = 9; m /= 9; }
+    if (m == 6) { plan.rad[plan.nst++] = 6; m = 1; }
     if (m % 4 == 0) { plan.rad[plan.nst++] = 4; m /= 4; }
     if (m % 2 == 0) { plan.rad[plan.nst++] = 2; m /= 2; }
-    while (m % 3 == 0) { plan.rad[plan.nst++] = 3; m /= 3; }
+    if (m % 3 == 0) { plan.rad[plan.nst++] = 3; m /= 3; }
 }
 
 static void dfree(void *&p)
@@ -226,7 +231,9 @@ extern "C" int se_create(se_ctx **out, int device, void *stream)
     se_ctx *c = new se_ctx();
     c->device = device;
     c->stream = (cudaStream_t)stream;
-    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         g_create_error = "stream/event creation failed";
@@ -331,6 +338,10 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         if (value < 0 || value > 7) return set_error(c, SE_ERR_ARG, "parts must be a mask in [0, 7]");
         c->parts = (int)value;
         return SE_OK;
+    case SE_OPT_OVERLAP:
+        if (value != 0 && value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "overlap must be 0, 1 or 2");
+        c->overlap = (int)value;
+        return SE_OK;
     case SE_OPT_TIMING:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "timing must be 0 or 1");
         c->timing = value != 0;
@@ -386,21 +397,40 @@ static int apply_t(se_ctx *c, int ncomp, const TO *x, TO *y)
     stage_mark(c, SE_STAGE_PERMUTE, s, false);
     launch_permute_in<T, TO>(c, x, xs, ncomp, s);
     stage_mark(c, SE_STAGE_PERMUTE, s, true);
-    SE_CUDA_CHECK(c, cudaEventRecord(c->ev_fork, s));
-    SE_CUDA_CHECK(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
-    stage_mark(c, SE_STAGE_REAL, c->aux, false);
-    if (c->parts & 1) launch_real<T>(c, xs, yr, c->aux, ncomp);
-    else SE_CUDA_CHECK(c, cudaMemsetAsync(yr, 0, c->N * kNC * sizeof(T), c->aux));
-    stage_mark(c, SE_STAGE_REAL, c->aux, true);
-    SE_CUDA_CHECK(c, cudaEventRecord(c->ev_join, c->aux));
     const int with_wave = (c->parts & 2) ? 1 : 0;
-    if (with_wave) launch_wave<T>(c, xs, s, ncomp);
+    // the real-space sum runs in line before the spread (overlap 2, the default), or on
+    // the auxiliary high-priority stream beside the spread (0) or the FFT chain (1)
+    auto real_part = [&](cudaStream_t rs) -> int {
+        stage_mark(c, SE_STAGE_REAL, rs, false);
+        if (c->parts & 1) launch_real<T>(c, xs, yr, rs, ncomp);
+        else SE_CUDA_CHECK(c, cudaMemsetAsync(yr, 0, c->N * kNC * sizeof(T), rs));
+        stage_mark(c, SE_STAGE_REAL, rs, true);
+        return SE_OK;
+    };
+    auto fork_real = [&]() -> int {
+        SE_CUDA_CHECK(c, cudaEventRecord(c->ev_fork, s));
+        SE_CUDA_CHECK(c, cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+        const int r = real_part(c->aux);
+        if (r != SE_OK) return r;
+        SE_CUDA_CHECK(c, cudaEventRecord(c->ev_join, c->aux));
+        return SE_OK;
+    };
+    int rc;
+    if (c->overlap == 2 && (rc = real_part(s)) != SE_OK) return rc;
+    if (c->overlap == 0 && (rc = fork_real()) != SE_OK) return rc;
+    if (with_wave) launch_wave_spread<T>(c, xs, s, ncomp);
+    else {
+        stage_mark(c, SE_STAGE_SPREAD, s, false);
+        stage_mark(c, SE_STAGE_SPREAD, s, true);
+    }
+    if (c->overlap == 1 && (rc = fork_real()) != SE_OK) return rc;
+    if (with_wave) launch_wave_fft<T>(c, s);
     else
-        for (int st = SE_STAGE_SPREAD; st <= SE_STAGE_FFT_XI; ++st) {
+        for (int st = SE_STAGE_FFT_XF; st <= SE_STAGE_FFT_XI; ++st) {
             stage_mark(c, st, s, false);
             stage_mark(c, st, s, true);
         }
-    SE_CUDA_CHECK(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+    if (c->overlap != 2) SE_CUDA_CHECK(c, cudaStreamWaitEvent(s, c->ev_join, 0));
     stage_mark(c, SE_STAGE_GATHER, s, false);
     launch_gather_combine<T, TO>(c, xs, yr, y, ncomp, with_wave, s);
     stage_mark(c, SE_STAGE_GATHER, s, true);

@@ -1,13 +1,18 @@
-// Mixed-radix (2, 3, 4, 8) Stockham FFT of many lines held in shared memory.
+// Mixed-radix (2, 3, 4, 6, 8, 9) Stockham FFT of a batch of NL lines held in shared
+// memory in element-major order (element e of line l at index e * NL + l), computed
+// out of place between two buffers so that a thread takes its butterflies one at a
+// time (few registers, several CTAs per SM to overlap the global traffic of one CTA
+// with the arithmetic of the others).
 //
-// Each stage of radix R over a line of length M performs M/R butterflies
-//   v_r = x[j + r M/R] * W_{Ns R}^{r (j mod Ns)},  X = DFT_R(v),
+// A stage of radix R over lines of length M performs M/R butterflies per line:
+//   v_r = x[j + r M/R] W_{Ns R}^{r (j mod Ns)},  X = DFT_R(v),
 //   y[(j div Ns) Ns R + (j mod Ns) + r Ns] = X_r,
 // with Ns the product of the radices already applied (the self-sorting Stockham
-// ordering, so no bit reversal pass is needed).  A CTA transforms `nlines` lines
-// of `lstride`-strided storage in place: every thread first loads the inputs of
-// its butterflies into registers, the block synchronises, then the outputs are
-// written back.  Twiddles come from a table tw[t] = exp(-2 pi i t / M).
+// ordering: no digit-reversal pass).  Twiddles come from tw[t] = exp(-2 pi i t / M);
+// the inverse transform conjugates them and is unnormalised.  Consecutive threads
+// take consecutive lines at one butterfly position, so with NL >= 16 (8-byte complex)
+// or NL >= 8 (16-byte complex) every warp access is a contiguous run of words.
+// Radices 6 and 9 are two-level Cooley-Tukey butterflies (inner radix 3).
 #pragma once
 
 #include "se_internal.cuh"
@@ -26,43 +31,67 @@ __device__ __forceinline__ T2 csub(T2 a, T2 b) { return T2{a.x - b.x, a.y - b.y}
 // multiply by -i (forward transform) or +i (inverse transform)
 template <typename T2>
 __device__ __forceinline__ T2 mul_mi(T2 a, bool inv) { return inv ? T2{-a.y, a.x} : T2{a.y, -a.x}; }
+// multiply by exp(-+ i theta) given c = cos(theta), s = sin(theta)
+template <typename T2, typename T>
+__device__ __forceinline__ T2 rot(T2 a, T c, T s, bool inv)
+{
+    return inv ? T2{a.x * c - a.y * s, a.y * c + a.x * s} : T2{a.x * c + a.y * s, a.y * c - a.x * s};
+}
+
+template <typename T2>
+__device__ __forceinline__ void dft3(T2 &v0, T2 &v1, T2 &v2, bool inv)
+{
+    using T = decltype(v0.x);
+    const T s3 = (T)0.86602540378443864676;
+    const T2 t1 = cadd(v1, v2);
+    const T2 t2 = T2{v0.x - (T)0.5 * t1.x, v0.y - (T)0.5 * t1.y};
+    const T2 d = csub(v1, v2);
+    const T2 t3 = mul_mi(T2{s3 * d.x, s3 * d.y}, inv);
+    v0 = cadd(v0, t1);
+    v1 = cadd(t2, t3);
+    v2 = csub(t2, t3);
+}
 
 template <int R, typename T2>
 __device__ __forceinline__ void dft_generic(T2 (&v)[R], bool inv)
 {
     using T = decltype(v[0].x);
     if constexpr (R == 2) {
-        T2 a = v[0];
+        const T2 a = v[0];
         v[0] = cadd(a, v[1]);
         v[1] = csub(a, v[1]);
     } else if constexpr (R == 3) {
-        const T s3 = (T)0.86602540378443864676;
-        T2 t1 = cadd(v[1], v[2]);
-        T2 t2 = T2{v[0].x - (T)0.5 * t1.x, v[0].y - (T)0.5 * t1.y};
-        T2 d = csub(v[1], v[2]);
-        T2 t3 = mul_mi(T2{s3 * d.x, s3 * d.y}, inv);
-        v[0] = cadd(v[0], t1);
-        v[1] = cadd(t2, t3);
-        v[2] = csub(t2, t3);
+        dft3(v[0], v[1], v[2], inv);
     } else if constexpr (R == 4) {
-        T2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        T2 t2 = cadd(v[1], v[3]), t3 = mul_mi(csub(v[1], v[3]), inv);
+        const T2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const T2 t2 = cadd(v[1], v[3]), t3 = mul_mi(csub(v[1], v[3]), inv);
         v[0] = cadd(t0, t2);
         v[2] = csub(t0, t2);
         v[1] = cadd(t1, t3);
         v[3] = csub(t1, t3);
+    } else if constexpr (R == 6) {
+        // n = n1 + 2 n2, k = k1 + 3 k2: radix-3 over n2, twiddle W6^(n1 k1), radix-2 over n1
+        dft3(v[0], v[2], v[4], inv);
+        dft3(v[1], v[3], v[5], inv);
+        const T h = (T)0.5, s3 = (T)0.86602540378443864676;
+        const T2 b1 = rot(v[3], h, s3, inv);       // W6^1
+        const T2 b2 = rot(v[5], -h, s3, inv);      // W6^2
+        const T2 a0 = v[0], a1 = v[2], a2 = v[4];
+        v[0] = cadd(a0, v[1]);
+        v[3] = csub(a0, v[1]);
+        v[1] = cadd(a1, b1);
+        v[4] = csub(a1, b1);
+        v[2] = cadd(a2, b2);
+        v[5] = csub(a2, b2);
     } else if constexpr (R == 8) {
         const T h = (T)0.70710678118654752440;
         T2 e[4] = {v[0], v[2], v[4], v[6]};
         T2 o[4] = {v[1], v[3], v[5], v[7]};
         dft_generic<4>(e, inv);
         dft_generic<4>(o, inv);
-        // W8^k o_k, W8 = exp(-+ i pi/4)
-        T2 w1 = inv ? T2{h * (o[1].x - o[1].y), h * (o[1].x + o[1].y)}
-                    : T2{h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};
-        T2 w2 = mul_mi(o[2], inv);
-        T2 w3 = inv ? T2{-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y)}
-                    : T2{h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};
+        const T2 w1 = rot(o[1], h, h, inv);
+        const T2 w2 = mul_mi(o[2], inv);
+        const T2 w3 = rot(o[3], -h, h, inv);
         v[0] = cadd(e[0], o[0]);
         v[4] = csub(e[0], o[0]);
         v[1] = cadd(e[1], w1);
@@ -71,66 +100,100 @@ __device__ __forceinline__ void dft_generic(T2 (&v)[R], bool inv)
         v[6] = csub(e[2], w2);
         v[3] = cadd(e[3], w3);
         v[7] = csub(e[3], w3);
+    } else if constexpr (R == 9) {
+        // n = n1 + 3 n2, k = k1 + 3 k2: radix-3 over n2, twiddle W9^(n1 k1), radix-3 over n1
+        dft3(v[0], v[3], v[6], inv);
+        dft3(v[1], v[4], v[7], inv);
+        dft3(v[2], v[5], v[8], inv);
+        const T c1 = (T)0.76604444311897803520, s1 = (T)0.64278760968653932632;    // 2 pi / 9
+        const T c2 = (T)0.17364817766693034885, s2 = (T)0.98480775301220805936;    // 4 pi / 9
+        const T c4 = (T)-0.93969262078590838405, s4 = (T)0.34202014332566873304;   // 8 pi / 9
+        // inner results a[n1][k1] sit at v[n1 + 3 k1]
+        v[4] = rot(v[4], c1, s1, inv);
+        v[7] = rot(v[7], c2, s2, inv);
+        v[5] = rot(v[5], c2, s2, inv);
+        v[8] = rot(v[8], c4, s4, inv);
+        T2 x0 = v[0], x1 = v[1], x2 = v[2];
+        dft3(x0, x1, x2, inv);
+        T2 y0 = v[3], y1 = v[4], y2 = v[5];
+        dft3(y0, y1, y2, inv);
+        T2 z0 = v[6], z1 = v[7], z2 = v[8];
+        dft3(z0, z1, z2, inv);
+        // X[k1 + 3 k2] = (k1-th group)[k2]
+        v[0] = x0; v[3] = x1; v[6] = x2;
+        v[1] = y0; v[4] = y1; v[7] = y2;
+        v[2] = z0; v[5] = z1; v[8] = z2;
     }
 }
 
-// One radix-R stage over `nlines` lines (elements per thread bounded by EPT).
-template <int R, int EPT, typename T2>
-__device__ __forceinline__ void fft_stage(T2 *buf, int M, int nlines, int lstride, int Ns,
-                                          const T2 *tw, bool inv)
+// One out-of-place radix-R stage over NL element-major lines of length M.
+// inv_ns = 1/Ns: j mod Ns is formed as j - Ns floor((j + 1/2)/Ns), exact for the
+// j < 512, Ns <= 256 that occur (the fraction stays >= 1/(2 Ns) away from an integer).
+template <int R, int NL, typename T2>
+__device__ __forceinline__ void fft_stage(const T2 *__restrict__ src, T2 *__restrict__ dst, int M, int Ns,
+                                          float inv_ns, const T2 *__restrict__ tw, bool inv)
 {
-    constexpr int K = (EPT + R - 1) / R;
     const int nbl = M / R;
-    const int nb = nbl * nlines;
     const int tstep = M / (Ns * R);
-    T2 v[K][R];
+    const int nb = nbl * NL;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int l = b % NL, j = b / NL;
+        T2 v[R];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        int b = threadIdx.x + k * blockDim.x;
-        if (b < nb) {
-            int line = b / nbl, j = b - line * nbl;
-            const T2 *src = buf + line * lstride + j;
+        for (int r = 0; r < R; ++r) v[r] = src[(j + r * nbl) * NL + l];
+        int kk = 0;
+        if (Ns > 1) {
+            const int q = __float2int_rz(((float)j + 0.5f) * inv_ns);
+            kk = j - q * Ns;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[k][r] = src[r * nbl];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        int b = threadIdx.x + k * blockDim.x;
-        if (b < nb) {
-            int line = b / nbl, j = b - line * nbl;
-            int kk = j % Ns;
-            if (Ns > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    T2 w = tw[r * kk * tstep];
-                    if (inv) w.y = -w.y;
-                    v[k][r] = cmul(v[k][r], w);
-                }
+            for (int r = 1; r < R; ++r) {
+                T2 w = tw[r * kk * tstep];
+                if (inv) w.y = -w.y;
+                v[r] = cmul(v[r], w);
             }
-            dft_generic<R>(v[k], inv);
-            T2 *dst = buf + line * lstride + (j - kk) * R + kk;
-#pragma unroll
-            for (int r = 0; r < R; ++r) dst[r * Ns] = v[k][r];
         }
+        dft_generic<R>(v, inv);
+        T2 *d = dst + ((j - kk) * R + kk) * NL + l;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[r * Ns * NL] = v[r];
     }
     __syncthreads();
 }
 
-// Full transform of nlines lines (unnormalised; inv selects exp(+2 pi i ...)).
-template <int EPT, typename T2>
-__device__ void fft_lines(T2 *buf, int nlines, int lstride, const FftPlan &plan, const T2 *tw, bool inv)
+// Full transform of NL lines starting in buffer a (b is scratch of the same size);
+// returns the buffer that holds the result.
+template <int NL, typename T2>
+__device__ T2 *fft_run(T2 *a, T2 *b, const FftPlan &plan, const T2 *tw, bool inv)
 {
     int Ns = 1;
     for (int s = 0; s < plan.nst; ++s) {
         const int R = plan.rad[s];
-        if (R == 8) fft_stage<8, EPT>(buf, plan.M, nlines, lstride, Ns, tw, inv);
-        else if (R == 4) fft_stage<4, EPT>(buf, plan.M, nlines, lstride, Ns, tw, inv);
-        else if (R == 3) fft_stage<3, EPT>(buf, plan.M, nlines, lstride, Ns, tw, inv);
-        else fft_stage<2, EPT>(buf, plan.M, nlines, lstride, Ns, tw, inv);
+        const float inv_ns = 1.0f / (float)Ns;
+        switch (R) {
+        case 8: fft_stage<8, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
+        case 9: fft_stage<9, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
+        case 6: fft_stage<6, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
+        case 4: fft_stage<4, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
+        case 3: fft_stage<3, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
+        default: fft_stage<2, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
+        }
         Ns *= R;
+        T2 *t = a;
+        a = b;
+        b = t;
     }
+    return a;
+}
+
+// 16-byte asynchronous global -> shared copies (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;\n" ::: "memory");
 }
 
 }  // namespace se

@@ -93,6 +93,7 @@ struct se_ctx {
     int size_mode = 0;                 // 0 hybrid, 1 real-space approach
     int restart = 30;
     int parts = 7;
+    int overlap = 2;             // SE_OPT_OVERLAP
     // configuration
     bool have_config = false;
     bool support_ok[2] = {false, false};
@@ -147,7 +148,9 @@ void launch_scan(se_ctx *c, int n, const int *in, int *out, cudaStream_t s);
 
 // se_wave.cu
 template <typename T>
-void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp);
+void launch_wave_spread(se_ctx *c, const T *xs, cudaStream_t s, int ncomp);
+template <typename T>
+void launch_wave_fft(se_ctx *c, cudaStream_t s);
 template <typename T, typename TO>
 void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int ncomp, int with_wave,
                            cudaStream_t s);

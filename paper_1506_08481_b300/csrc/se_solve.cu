@@ -405,10 +405,12 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
         }
     };
 
-    double bn2;
+    double bn2, xn2;
     int rc = gm.dots(bd, 0, 1, bd, &bn2);
     if (rc != SE_OK) return rc;
+    if ((rc = gm.dots(xd, 0, 1, xd, &xn2)) != SE_OK) return rc;
     const double bnorm = std::sqrt(bn2);
+    bool x_zero = xn2 == 0.0;          // a zero initial guess: the first residual is b itself
     int prods = 0;
     double rel = 0.0;
     std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), h(m + 1), h2(m + 1), yv(m);
@@ -417,10 +419,15 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
     } else {
         for (;;) {
             // FP64 true residual
-            rc = se_apply_internal(c, ncomp, xd, w, SE_F64, 1);
-            if (rc != SE_OK) return rc;
-            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, bd, -1.0, w, r);
-            c->launches++;
+            if (x_zero) {
+                SE_CUDA_CHECK(c, cudaMemcpyAsync(r, bd, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                x_zero = false;
+            } else {
+                rc = se_apply_internal(c, ncomp, xd, w, SE_F64, 1);
+                if (rc != SE_OK) return rc;
+                axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, bd, -1.0, w, r);
+                c->launches++;
+            }
             double rn2;
             rc = gm.dots(r, 0, 1, r, &rn2);
             if (rc != SE_OK) return rc;

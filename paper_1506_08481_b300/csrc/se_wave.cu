@@ -24,6 +24,7 @@
 // Real-space approach: the target Laplacian acts on the gather weights instead.
 // Nyquist planes and q = 0 are set to zero.
 #include <cstdio>
+#include <type_traits>
 
 #include "se_fft.cuh"
 #include "se_internal.cuh"
@@ -32,8 +33,6 @@ namespace se {
 
 namespace {
 
-constexpr int kEPT = 8;    // FFT elements per thread and stage
-constexpr int kFftMaxThreads = 512;
 
 template <typename T> struct V4;
 template <> struct V4<float> { using t = float4; };
@@ -105,15 +104,17 @@ __global__ void support_kernel(int N, SeParams p, const double *pos, const doubl
 //   H = g [ (A0 + A1 s^2) F - alpha kappa (s x T) + (B0 + B1 s^2) S.s ],  H_src = g S_tr,
 // so a thread forms 13 column coefficients per particle and spends 13 FMAs per point.
 template <typename T, int NCOMP>
-__global__ void __launch_bounds__(64) spread_kernel(SeParams p, const int *tile_start,
+__global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeParams p, const int *tile_start,
                                                     const int *tile_perm, const int *base,
                                                     const T *s0g, const T *wg, const double *rad,
                                                     const T *xs, T *grid)
 {
     constexpr int TT = kTile, CH = 64, NPR = 22, MAXB = 125;
     using T4 = typename V4<T>::t;
-    __shared__ T sxy[CH][2 * TT];     // window weights x(8) y(8)
-    __shared__ T4 swz[CH][TT];        // g_z (1, s_z, s_z^2, s_z^3) per tile plane
+    // rows are XOR-swizzled by the particle slot so that the staging writes (one
+    // particle per thread) spread over all banks; reads broadcast one particle's row
+    __shared__ T sxy[CH][2 * TT];     // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
+    __shared__ T4 swz[CH][TT];        // g_z (1, s_z, s_z^2, s_z^3) of plane t at t ^ (k & 7)
     __shared__ T sp[CH][NPR];         // sx0 sy0 A0 A1 B0 B1 F(3) T(3) S(6) Str ok
     __shared__ int bin_beg[MAXB], bin_off[MAXB + 1];
     const int M = p.M, P = p.P, nt = p.ntile;
@@ -165,14 +166,15 @@ __global__ void __launch_bounds__(64) spread_kernel(SeParams p, const int *tile_
                 od[d] = o;
             }
             const T *w = wg + (size_t)i * 3 * P;
+            const int sw_xy = (k >> 1) & 15, sw_z = k & 7;
 #pragma unroll
             for (int t = 0; t < TT; ++t) {
                 const int ix = od[0] + t, iy = od[1] + t, iz = od[2] + t;
-                sxy[k][t] = (ix >= 0 && ix < P) ? w[ix] : (T)0;
-                sxy[k][TT + t] = (iy >= 0 && iy < P) ? w[P + iy] : (T)0;
+                sxy[k][t ^ sw_xy] = (ix >= 0 && ix < P) ? w[ix] : (T)0;
+                sxy[k][(TT + t) ^ sw_xy] = (iy >= 0 && iy < P) ? w[P + iy] : (T)0;
                 const T g = (iz >= 0 && iz < P) ? w[2 * P + iz] : (T)0;
                 const T sz = s0g[3 * i + 2] + (T)iz;
-                swz[k][t] = T4{g, g * sz, g * sz * sz, g * sz * sz * sz};
+                swz[k][t ^ sw_z] = T4{g, g * sz, g * sz * sz, g * sz * sz * sz};
             }
             sp[k][0] = s0g[3 * i] + (T)od[0];                 // offsets of the tile origin
             sp[k][1] = s0g[3 * i + 1] + (T)od[1];
@@ -188,12 +190,18 @@ __global__ void __launch_bounds__(64) spread_kernel(SeParams p, const int *tile_
             if constexpr (NCOMP >= 6) { sp[k][9] = xi[3]; sp[k][10] = xi[4]; sp[k][11] = xi[5]; }
             if constexpr (NCOMP >= 11) stresslet_tensor(xi + 6, &sp[k][12]);
             if constexpr (NCOMP >= 12) sp[k][18] = xi[11];
-            sp[k][21] = ok ? (T)1 : (T)0;
+            // which halves of the tile's 8 planes the support reaches (planes t with
+            // 0 <= od_z + t < P); bit 0: planes 0-3, bit 1: planes 4-7
+            const int zlo = max(0, -od[2]), zhi = min(TT, P - od[2]);
+            const int halves = (zlo < TT / 2 && zhi > 0 ? 1 : 0) | (zhi > TT / 2 && zlo < TT ? 2 : 0);
+            sp[k][21] = ok ? (T)halves : (T)0;
         }
         __syncthreads();
         for (int k = 0; k < cnt; ++k) {
-            const T gxy = sxy[k][tx] * sxy[k][TT + ty];
-            if (gxy == (T)0 || sp[k][21] == (T)0) continue;
+            const int sw_xy = (k >> 1) & 15, sw_z = k & 7;
+            const T gxy = sxy[k][tx ^ sw_xy] * sxy[k][(TT + ty) ^ sw_xy];
+            const int halves = (int)sp[k][21];
+            if (gxy == (T)0 || halves == 0) continue;
             const T sx = sp[k][0] + tx, sy = sp[k][1] + ty;
             const T sxy2 = sx * sx + sy * sy;
             const T A1 = sp[k][3], a0 = sp[k][2] + A1 * sxy2;
@@ -232,20 +240,26 @@ __global__ void __launch_bounds__(64) spread_kernel(SeParams p, const int *tile_
 #pragma unroll
                 for (int e = 0; e < 4; ++e) c[q][e] *= gxy;
             const T cs = NCOMP >= 12 ? gxy * sp[k][18] : (T)0;
+            auto planes = [&](auto z0c) {
+                constexpr int z0 = decltype(z0c)::value;
 #pragma unroll
-            for (int z = 0; z < TT; ++z) {
-                const T4 W = swz[k][z];
+                for (int z = z0; z < z0 + TT / 2; ++z) {
+                    const T4 W = swz[k][z ^ sw_z];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    if constexpr (NCOMP >= 11)
-                        acc[z][q] += c[q][0] * W.x + c[q][1] * W.y + c[q][2] * W.z + c[q][3] * W.w;
-                    else if constexpr (NCOMP >= 6)
-                        acc[z][q] += c[q][0] * W.x + c[q][1] * W.y + c[q][2] * W.z;
-                    else
-                        acc[z][q] += c[q][0] * W.x + c[q][2] * W.z;
+                    for (int q = 0; q < 3; ++q) {
+                        if constexpr (NCOMP >= 11)
+                            acc[z][q] += c[q][0] * W.x + c[q][1] * W.y + c[q][2] * W.z + c[q][3] * W.w;
+                        else if constexpr (NCOMP >= 6)
+                            acc[z][q] += c[q][0] * W.x + c[q][1] * W.y + c[q][2] * W.z;
+                        else
+                            acc[z][q] += c[q][0] * W.x + c[q][2] * W.z;
+                    }
+                    if constexpr (NCOMP >= 12) acc[z][NA - 1] += cs * W.x;
                 }
-                if constexpr (NCOMP >= 12) acc[z][NA - 1] += cs * W.x;
-            }
+            };
+            // planes outside the support carry zero weight: skip a half the support misses
+            if (halves & 1) planes(std::integral_constant<int, 0>{});
+            if (halves & 2) planes(std::integral_constant<int, TT / 2>{});
         }
     }
 #pragma unroll
@@ -261,102 +275,138 @@ __global__ void __launch_bounds__(64) spread_kernel(SeParams p, const int *tile_
 }
 
 // ---------------------------------------------------------------- FFT passes
+//
+// Each pass moves a chunk of lines into shared memory with 16-byte asynchronous
+// copies (the whole chunk in flight at once), transforms it there (se_fft.cuh) and
+// writes it back with coalesced stores; four CTAs of 256 threads per SM at the usual
+// grid sizes, so the copies of one CTA overlap the arithmetic of the others.  The
+// shared buffers hold NL element-major lines of up to M + 2 elements.
 
-// x pass, forward: each grid line (y, z) carries 4 real series packed as two complex
+template <typename T> constexpr int fft_nl() { return sizeof(T) == 4 ? 16 : 8; }
+constexpr int kFftThreads = 256;
+
+// shared layout of a pass: twiddles [M], two line buffers [NLB (M + 2)]
+template <typename T2>
+__device__ __forceinline__ void fft_smem(int M, int NLB, T2 *&tw, T2 *&A, T2 *&B)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    tw = reinterpret_cast<T2 *>(smraw);
+    A = tw + ((M + 1) & ~1);
+    B = A + (size_t)NLB * (M + 2);
+}
+
+// x pass, forward: each grid row (y, z) carries 4 real series packed as two complex
 // lines (H0 + i H1, H2 + i H3); after the transform the four half spectra
 // q = 0..M/2 are separated using Z(-q) = conj(Z(q)) of real data.
 template <typename T>
-__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_x_fwd(FftPlan plan, const typename C2<T>::t *twg, const T *grid,
-                          typename C2<T>::t *spec, int LX)
+__global__ void __launch_bounds__(kFftThreads, 4) fft_x_fwd(FftPlan plan, const typename C2<T>::t *twg,
+                                                            const T *grid, typename C2<T>::t *spec)
 {
     using T2 = typename C2<T>::t;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T2 *tw = reinterpret_cast<T2 *>(smraw);
+    constexpr int NL = fft_nl<T>(), NR = NL / 2;          // complex lines, grid rows
     const int M = plan.M, Mh = M / 2 + 1;
-    T2 *buf = tw + M;
+    T2 *tw, *A, *B;
+    fft_smem(M, NL, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
-    const size_t gl0 = (size_t)blockIdx.x * LX;
-    const int nl = (int)min((size_t)LX, (size_t)M * M - gl0);
-    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
-        const int gl = e / M, x = e - gl * M;
-        typename V4<T>::t v = *reinterpret_cast<const typename V4<T>::t *>(grid + ((gl0 + gl) * M + x) * 4);
-        buf[(2 * gl) * M + x] = T2{v.x, v.y};
-        buf[(2 * gl + 1) * M + x] = T2{v.z, v.w};
+    const size_t row0 = (size_t)blockIdx.x * NR;
+    if constexpr (sizeof(T) == 4) {
+        // one float4 (H0..H3) of row r at x -> lines 2r, 2r + 1 at element x
+        for (int e = threadIdx.x; e < NR * M; e += blockDim.x) {
+            const int r = e % NR, x = e / NR;
+            cp_async16(A + x * NL + 2 * r, grid + ((row0 + r) * M + x) * 4);
+        }
+    } else {
+        for (int e = threadIdx.x; e < 2 * NR * M; e += blockDim.x) {
+            const int h = e & 1, r = (e >> 1) % NR, x = (e >> 1) / NR;
+            cp_async16(A + x * NL + 2 * r + h, grid + ((row0 + r) * M + x) * 4 + 2 * h);
+        }
     }
+    cp_async_wait_all();
     __syncthreads();
-    fft_lines<kEPT>(buf, 2 * nl, M, plan, tw, false);
-    for (int e = threadIdx.x; e < nl * Mh * 4; e += blockDim.x) {
-        const int c = e & 3, q = (e >> 2) % Mh, gl = (e >> 2) / Mh;
-        const T2 z = buf[(2 * gl + (c >> 1)) * M + q];
-        const T2 zm = buf[(2 * gl + (c >> 1)) * M + (q == 0 ? 0 : M - q)];
-        T2 r;
-        if ((c & 1) == 0) r = T2{(T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y)};
-        else r = T2{(T)0.5 * (z.y + zm.y), (T)-0.5 * (z.x - zm.x)};
-        spec[((gl0 + gl) * Mh + q) * 4 + c] = r;
+    const T2 *Z = fft_run<NL>(A, B, plan, tw, false);
+    for (int e = threadIdx.x; e < NR * Mh * 2; e += blockDim.x) {
+        const int h = e & 1, r = (e >> 1) % NR, q = (e >> 1) / NR;
+        const T2 z = Z[q * NL + 2 * r + h];
+        const T2 zm = Z[(q == 0 ? 0 : M - q) * NL + 2 * r + h];
+        T2 *o = spec + ((row0 + r) * Mh + q) * 4 + 2 * h;
+        o[0] = T2{(T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y)};
+        o[1] = T2{(T)0.5 * (z.y + zm.y), (T)-0.5 * (z.x - zm.x)};
     }
 }
 
-// strided pass (y axis): lines of element stride `es` for LB consecutive q and all C
-// components, transformed in place.
-template <typename T>
-__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_strided(FftPlan plan, const typename C2<T>::t *twg, typename C2<T>::t *data,
-                            int C, int LB, size_t es, size_t os, int inv)
+// y pass (forward or inverse) in place on half spectra [z][y][q][C]: a CTA takes the
+// NL / C wave numbers q0.. of one z plane, all C components, lines along y.
+template <typename T, int C>
+__global__ void __launch_bounds__(kFftThreads, 4) fft_y(FftPlan plan, const typename C2<T>::t *twg,
+                                                        typename C2<T>::t *data, int inv)
 {
     using T2 = typename C2<T>::t;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T2 *tw = reinterpret_cast<T2 *>(smraw);
-    const int M = plan.M, Mh = M / 2 + 1, ls = M + 1;
-    T2 *buf = tw + M;
+    constexpr int NL = fft_nl<T>(), LB = NL / C, CPE = sizeof(T) == 4 ? 2 : 1;   // complex per copy
+    const int M = plan.M, Mh = M / 2 + 1;
+    T2 *tw, *A, *B;
+    fft_smem(M, NL, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
-    const int q0 = blockIdx.x * LB, nq = min(LB, Mh - q0), nl = nq * C;
-    const size_t base = (size_t)blockIdx.y * os + (size_t)q0 * C;
-    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
-        const int l = e % nl, el = e / nl;
-        buf[l * ls + el] = data[base + el * es + l];
+    const int q0 = blockIdx.x * LB, nv = min(LB, Mh - q0) * C;     // valid lines
+    const size_t base = ((size_t)blockIdx.y * M * Mh + q0) * C, es = (size_t)Mh * C;
+    for (int e = threadIdx.x; e < (NL / CPE) * M; e += blockDim.x) {
+        const int k = e % (NL / CPE), y = e / (NL / CPE);
+        T2 *d = A + y * NL + k * CPE;
+        if (k * CPE < nv) cp_async16(d, data + base + y * es + k * CPE);
+        else
+            for (int u = 0; u < CPE; ++u) d[u] = T2{0, 0};
     }
+    cp_async_wait_all();
     __syncthreads();
-    fft_lines<kEPT>(buf, nl, ls, plan, tw, inv != 0);
-    for (int e = threadIdx.x; e < nl * M; e += blockDim.x) {
-        const int l = e % nl, el = e / nl;
-        data[base + el * es + l] = buf[l * ls + el];
+    const T2 *Z = fft_run<NL>(A, B, plan, tw, inv != 0);
+    for (int e = threadIdx.x; e < NL * M; e += blockDim.x) {
+        const int l = e % NL, y = e / NL;
+        if (l < nv) data[base + y * es + l] = Z[y * NL + l];
     }
 }
 
 // z pass: forward transform of the 4 spectra, k-space scaling (see the file
-// header), inverse transform of the CO output spectra.  Lines are stored
-// component-major (line = c * nq + q) so inputs and outputs share the buffer.
-template <typename T, int CO>
-__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_z_scale(FftPlan plan, SeParams p, const typename C2<T>::t *twg,
-                            const typename C2<T>::t *specf, typename C2<T>::t *speco, int LB, T cnorm)
+// header), inverse transform of the CO output spectra.  A CTA takes LB wave numbers
+// q0.. of one y row (LB = 4 for FP32 and 2 for FP64 while the buffers fit in shared
+// memory); input lines q * 4 + c, output lines q * CO + c (the component order of the
+// arrays in HBM).
+template <typename T, int CO, int LB>
+__global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, SeParams p, const typename C2<T>::t *twg,
+                                                              const typename C2<T>::t *specf,
+                                                              typename C2<T>::t *speco, T cnorm)
 {
     using T2 = typename C2<T>::t;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T2 *tw = reinterpret_cast<T2 *>(smraw);
-    const int M = plan.M, Mh = M / 2 + 1, ls = M + 1;
-    T2 *buf = tw + M;
+    constexpr int NLI = 4 * LB, NLO = LB * CO, CPE = sizeof(T) == 4 ? 2 : 1;
+    const int M = plan.M, Mh = M / 2 + 1;
+    T2 *tw, *A, *B;
+    fft_smem(M, NLO, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
     const int y = blockIdx.y;
     const int q0 = blockIdx.x * LB, nq = min(LB, Mh - q0);
-    const size_t zs = (size_t)M * Mh;               // z stride in q units
-    for (int e = threadIdx.x; e < 4 * nq * M; e += blockDim.x) {
-        const int lm = e % (4 * nq), z = e / (4 * nq);
-        const int q = lm >> 2, c = lm & 3;
-        buf[(c * nq + q) * ls + z] = specf[((size_t)z * zs + (size_t)y * Mh + q0 + q) * 4 + c];
+    const size_t zs = (size_t)M * Mh;                      // z stride in q units
+    for (int e = threadIdx.x; e < (NLI / CPE) * M; e += blockDim.x) {
+        const int k = e % (NLI / CPE), z = e / (NLI / CPE);
+        T2 *d = A + z * NLI + k * CPE;
+        if (k * CPE < nq * 4) cp_async16(d, specf + ((size_t)z * zs + (size_t)y * Mh + q0) * 4 + k * CPE);
+        else
+            for (int u = 0; u < CPE; ++u) d[u] = T2{0, 0};
     }
+    cp_async_wait_all();
     __syncthreads();
-    fft_lines<kEPT>(buf, 4 * nq, ls, plan, tw, false);
+    T2 *X = fft_run<NLI>(A, B, plan, tw, false);
+    T2 *Y = X == A ? B : A;
 
     const int ys = y <= M / 2 ? y : y - M;
     const T twopiL = (T)(2.0 * kPi / p.L);
     const T i4x2 = (T)(0.25 / (p.xi * p.xi));
     const T ecoef = (T)(2.0 * kPi * kPi / (p.alpha * (double)M * M));
-    for (int e = threadIdx.x; e < nq * M; e += blockDim.x) {
-        const int q = e % nq, z = e / nq;
+    for (int e = threadIdx.x; e < LB * M; e += blockDim.x) {
+        const int q = e % LB, z = e / LB;
         const int qx = q0 + q, zsn = z <= M / 2 ? z : z - M;
         T2 o[CO];
 #pragma unroll
         for (int c = 0; c < CO; ++c) o[c] = T2{0, 0};
-        const bool zero = (qx == 0 && ys == 0 && zsn == 0) || 2 * qx == M || 2 * ys == M || 2 * zsn == M;
+        const bool zero = q >= nq || (qx == 0 && ys == 0 && zsn == 0) || 2 * qx == M || 2 * ys == M ||
+                          2 * zsn == M;
         if (!zero) {
             const T kx = twopiL * qx, ky = twopiL * ys, kz = twopiL * zsn;
             const T k2 = kx * kx + ky * ky + kz * kz;
@@ -364,8 +414,8 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_z_scale(FftPlan plan, S
             const T E = exp(-k2 * i4x2 + ecoef * q2) * cnorm;
             const T ik2 = 1 / k2;
             const T Phi = E * (1 + k2 * i4x2) * ik2;
-            const T2 H0 = buf[(0 * nq + q) * ls + z], H1 = buf[(1 * nq + q) * ls + z];
-            const T2 H2 = buf[(2 * nq + q) * ls + z], Hs = buf[(3 * nq + q) * ls + z];
+            const T2 *h = X + z * NLI + q * 4;
+            const T2 H0 = h[0], H1 = h[1], H2 = h[2], Hs = h[3];
             const T2 kH = T2{kx * H0.x + ky * H1.x + kz * H2.x, kx * H0.y + ky * H1.y + kz * H2.y};
             const T2 pr = T2{kH.x * ik2, kH.y * ik2};
             // This FFT's forward transform carries exp(-i q.n), so Hhat(q) holds the moments'
@@ -386,15 +436,15 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_z_scale(FftPlan plan, S
                 o[3] = op;
             }
         }
+        T2 *w = Y + z * NLO + q * CO;
 #pragma unroll
-        for (int c = 0; c < CO; ++c) buf[(c * nq + q) * ls + z] = o[c];
+        for (int c = 0; c < CO; ++c) w[c] = o[c];
     }
     __syncthreads();
-    fft_lines<kEPT>(buf, CO * nq, ls, plan, tw, true);
-    for (int e = threadIdx.x; e < CO * nq * M; e += blockDim.x) {
-        const int lm = e % (CO * nq), z = e / (CO * nq);
-        const int q = lm / CO, c = lm - q * CO;
-        speco[((size_t)z * zs + (size_t)y * Mh + q0 + q) * CO + c] = buf[(c * nq + q) * ls + z];
+    const T2 *Z = fft_run<NLO>(Y, X, plan, tw, true);
+    for (int e = threadIdx.x; e < NLO * M; e += blockDim.x) {
+        const int l = e % NLO, z = e / NLO;
+        if (l < nq * CO) speco[((size_t)z * zs + (size_t)y * Mh + q0) * CO + l] = Z[z * NLO + l];
     }
 }
 
@@ -402,37 +452,46 @@ __global__ void __launch_bounds__(kFftMaxThreads, 1) fft_z_scale(FftPlan plan, S
 // Z = A + i B (A(M-q) = conj A(q) for real output), transformed, and written as the
 // real grids A, B interleaved per point.
 template <typename T, int CO>
-__global__ void __launch_bounds__(kFftMaxThreads, 1) fft_x_inv(FftPlan plan, const typename C2<T>::t *twg, const typename C2<T>::t *speco,
-                          T *grid, int LX)
+__global__ void __launch_bounds__(kFftThreads, 4) fft_x_inv(FftPlan plan, const typename C2<T>::t *twg,
+                                                            const typename C2<T>::t *speco, T *grid)
 {
     using T2 = typename C2<T>::t;
-    constexpr int NP = CO / 2;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T2 *tw = reinterpret_cast<T2 *>(smraw);
+    constexpr int NL = fft_nl<T>(), NP = CO / 2, NR = NL / NP, CPE = sizeof(T) == 4 ? 2 : 1;
     const int M = plan.M, Mh = M / 2 + 1;
-    T2 *buf = tw + M;
+    T2 *tw, *A, *B;
+    fft_smem(M, NL, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
-    const size_t gl0 = (size_t)blockIdx.x * LX;
-    const int nl = (int)min((size_t)LX, (size_t)M * M - gl0);
-    for (int e = threadIdx.x; e < nl * NP * M; e += blockDim.x) {
-        const int x = e % M, pl = e / M, gl = pl / NP, pp = pl - gl * NP;
-        const T2 *src = speco + (gl0 + gl) * Mh * CO;
+    const size_t row0 = (size_t)blockIdx.x * NR;
+    // the NR rows of half spectra are contiguous in HBM: stage them raw in B
+    const int nraw = NR * Mh * CO;
+    const T2 *src = speco + row0 * Mh * CO;
+    for (int e = threadIdx.x; e < nraw / CPE; e += blockDim.x) cp_async16(B + e * CPE, src + e * CPE);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int e = threadIdx.x; e < NL * M; e += blockDim.x) {
+        const int l = e % NL, x = e / NL, r = l / NP, pp = l - r * NP;
+        const T2 *s = B + (size_t)r * Mh * CO + 2 * pp;
         T2 z;
         if (x <= M / 2) {
-            const T2 A = src[x * CO + 2 * pp], B = src[x * CO + 2 * pp + 1];
-            z = T2{A.x - B.y, A.y + B.x};
+            const T2 a = s[x * CO], b = s[x * CO + 1];
+            z = T2{a.x - b.y, a.y + b.x};
         } else {
-            const T2 A = src[(M - x) * CO + 2 * pp], B = src[(M - x) * CO + 2 * pp + 1];
-            z = T2{A.x + B.y, -A.y + B.x};
+            const T2 a = s[(M - x) * CO], b = s[(M - x) * CO + 1];
+            z = T2{a.x + b.y, -a.y + b.x};
         }
-        buf[pl * M + x] = z;
+        A[x * NL + l] = z;
     }
     __syncthreads();
-    fft_lines<kEPT>(buf, nl * NP, M, plan, tw, true);
-    for (int e = threadIdx.x; e < nl * M * CO; e += blockDim.x) {
-        const int c = e % CO, x = (e / CO) % M, gl = e / (CO * M);
-        const T2 z = buf[(gl * NP + (c >> 1)) * M + x];
-        grid[((gl0 + gl) * M + x) * CO + c] = (c & 1) ? z.y : z.x;
+    const T2 *Z = fft_run<NL>(A, B, plan, tw, true);
+    for (int e = threadIdx.x; e < NR * M; e += blockDim.x) {
+        const int r = e % NR, x = e / NR;
+        const T2 *s = Z + x * NL + r * NP;
+        T *g = grid + ((row0 + r) * M + x) * CO;
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+            g[2 * pp] = s[pp].x;
+            g[2 * pp + 1] = s[pp].y;
+        }
     }
 }
 
@@ -623,12 +682,12 @@ __global__ void __launch_bounds__(256, 4) gather_kernel(SeParams p, int N, const
 
 // ---------------------------------------------------------------- host launchers
 
-static int fft_threads(int elements)
+template <typename T2>
+static size_t fft_smem_bytes(int M, int nlb)
 {
-    int t = (elements + kEPT - 1) / kEPT;
-    t = (t + 31) / 32 * 32;
-    return t < 64 ? 64 : (t > kFftMaxThreads ? kFftMaxThreads : t);
+    return ((size_t)((M + 1) & ~1) + 2 * (size_t)nlb * (M + 2)) * sizeof(T2);
 }
+constexpr size_t kSmemMax = 227 * 1024;
 
 void make_twiddles(se_ctx *c, int prec)
 {
@@ -677,92 +736,93 @@ static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_
     c->launches++;
 }
 
-// lines per CTA so that one CTA holds about `budget` complex elements
-static int lines_for(int budget, int per_line)
+template <typename T, int CO, int LB>
+static void launch_z(se_ctx *c, const SeParams &p, const typename C2<T>::t *tw, const typename C2<T>::t *sf,
+                     typename C2<T>::t *so, T cnorm, cudaStream_t s)
 {
-    int l = budget / per_line;
-    return l < 1 ? 1 : l;
+    using T2 = typename C2<T>::t;
+    const int M = c->M, Mh = M / 2 + 1;
+    const size_t smem = fft_smem_bytes<T2>(M, CO * LB);
+    cudaFuncSetAttribute(fft_z_scale<T, CO, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fft_z_scale<T, CO, LB><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, smem, s>>>(c->plan, p, tw, sf, so, cnorm);
+}
+
+template <typename T, int CO>
+static void launch_z_fit(se_ctx *c, const SeParams &p, const typename C2<T>::t *tw, const typename C2<T>::t *sf,
+                         typename C2<T>::t *so, T cnorm, cudaStream_t s)
+{
+    using T2 = typename C2<T>::t;
+    constexpr int LB0 = fft_nl<T>() / 4;
+    if (fft_smem_bytes<T2>(c->M, CO * LB0) <= kSmemMax) launch_z<T, CO, LB0>(c, p, tw, sf, so, cnorm, s);
+    else if (fft_smem_bytes<T2>(c->M, CO * 2) <= kSmemMax) launch_z<T, CO, 2>(c, p, tw, sf, so, cnorm, s);
+    else launch_z<T, CO, 1>(c, p, tw, sf, so, cnorm, s);
+}
+
+template <typename T, int C>
+static void launch_y(se_ctx *c, const typename C2<T>::t *tw, typename C2<T>::t *data, int inv, cudaStream_t s)
+{
+    using T2 = typename C2<T>::t;
+    constexpr int NL = fft_nl<T>(), LB = NL / C;
+    const int M = c->M, Mh = M / 2 + 1;
+    const size_t smem = fft_smem_bytes<T2>(M, NL);
+    cudaFuncSetAttribute(fft_y<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fft_y<T, C><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, smem, s>>>(c->plan, tw, data, inv);
 }
 
 template <typename T>
-void launch_wave(se_ctx *c, const T *xs, cudaStream_t s, int ncomp)
+void launch_wave_spread(se_ctx *c, const T *xs, cudaStream_t s, int ncomp)
 {
-    using T2 = typename C2<T>::t;
     const SeParams p = make_params(c);
-    const int M = c->M, Mh = M / 2 + 1;
-    const int budget = kEPT * kFftMaxThreads;              // complex elements per CTA
-    const T2 *tw = (const T2 *)c->b.tw[pix<T>()];
-    T2 *sf = (T2 *)c->b.spec_f[pix<T>()], *so = (T2 *)c->b.spec_o[pix<T>()];
-    const int CO = p.hybrid ? 8 : 4;
-
     stage_mark(c, SE_STAGE_SPREAD, s, false);
     launch_spread<T>(c, p, xs, s, ncomp);
     stage_mark(c, SE_STAGE_SPREAD, s, true);
+}
+
+template <typename T>
+void launch_wave_fft(se_ctx *c, cudaStream_t s)
+{
+    using T2 = typename C2<T>::t;
+    constexpr int NL = fft_nl<T>();
+    const SeParams p = make_params(c);
+    const int M = c->M;
+    const T2 *tw = (const T2 *)c->b.tw[pix<T>()];
+    T2 *sf = (T2 *)c->b.spec_f[pix<T>()], *so = (T2 *)c->b.spec_o[pix<T>()];
+    const int CO = p.hybrid ? 8 : 4;
+    const size_t smem = fft_smem_bytes<T2>(M, NL);
 
     stage_mark(c, SE_STAGE_FFT_XF, s, false);
-    {   // x forward
-        const int LX = lines_for(budget, 2 * M);
-        const int nl = 2 * LX * M;
-        const size_t smem = (size_t)(nl + M) * sizeof(T2);
-        const int blocks = (M * M + LX - 1) / LX;
-        cudaFuncSetAttribute(fft_x_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        fft_x_fwd<T><<<blocks, fft_threads(nl), smem, s>>>(c->plan, tw, (const T *)c->b.grid_f[pix<T>()], sf, LX);
-        c->launches++;
-    }
+    cudaFuncSetAttribute(fft_x_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fft_x_fwd<T><<<M * M / (NL / 2), kFftThreads, smem, s>>>(c->plan, tw, (const T *)c->b.grid_f[pix<T>()], sf);
+    c->launches++;
     stage_mark(c, SE_STAGE_FFT_XF, s, true);
+
     stage_mark(c, SE_STAGE_FFT_YF, s, false);
-    {   // y forward (4 components)
-        const int LB = max(1, min(Mh, lines_for(budget, 4 * (M + 1))));
-        const size_t smem = (size_t)(4 * LB * (M + 1) + M) * sizeof(T2);
-        dim3 grid((Mh + LB - 1) / LB, M);
-        cudaFuncSetAttribute(fft_strided<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        fft_strided<T><<<grid, fft_threads(4 * LB * M), smem, s>>>(c->plan, tw, sf, 4, LB, (size_t)Mh * 4,
-                                                                     (size_t)M * Mh * 4, 0);
-        c->launches++;
-    }
+    launch_y<T, 4>(c, tw, sf, 0, s);
+    c->launches++;
     stage_mark(c, SE_STAGE_FFT_YF, s, true);
+
     const T cnorm = (T)(pow(p.alpha / kPi, 3.0) / (p.eta * p.L * p.L * p.L));
     stage_mark(c, SE_STAGE_FFT_Z, s, false);
-    {   // z forward + scale + z inverse
-        const int LB = max(1, min(Mh, lines_for(budget, CO * (M + 1))));
-        const size_t smem = (size_t)(CO * LB * (M + 1) + M) * sizeof(T2);
-        dim3 grid((Mh + LB - 1) / LB, M);
-        if (CO == 8) {
-            cudaFuncSetAttribute(fft_z_scale<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            fft_z_scale<T, 8><<<grid, fft_threads(CO * LB * M), smem, s>>>(c->plan, p, tw, sf, so, LB, cnorm);
-        } else {
-            cudaFuncSetAttribute(fft_z_scale<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            fft_z_scale<T, 4><<<grid, fft_threads(CO * LB * M), smem, s>>>(c->plan, p, tw, sf, so, LB, cnorm);
-        }
-        c->launches++;
-    }
+    if (CO == 8) launch_z_fit<T, 8>(c, p, tw, sf, so, cnorm, s);
+    else launch_z_fit<T, 4>(c, p, tw, sf, so, cnorm, s);
+    c->launches++;
     stage_mark(c, SE_STAGE_FFT_Z, s, true);
+
     stage_mark(c, SE_STAGE_FFT_YI, s, false);
-    {   // y inverse (CO components)
-        const int LB = max(1, min(Mh, lines_for(budget, CO * (M + 1))));
-        const size_t smem = (size_t)(CO * LB * (M + 1) + M) * sizeof(T2);
-        dim3 grid((Mh + LB - 1) / LB, M);
-        cudaFuncSetAttribute(fft_strided<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        fft_strided<T><<<grid, fft_threads(CO * LB * M), smem, s>>>(c->plan, tw, so, CO, LB, (size_t)Mh * CO,
-                                                                      (size_t)M * Mh * CO, 1);
-        c->launches++;
-    }
+    if (CO == 8) launch_y<T, 8>(c, tw, so, 1, s);
+    else launch_y<T, 4>(c, tw, so, 1, s);
+    c->launches++;
     stage_mark(c, SE_STAGE_FFT_YI, s, true);
+
     stage_mark(c, SE_STAGE_FFT_XI, s, false);
-    {   // x inverse
-        const int LX = lines_for(budget, (CO / 2) * M);
-        const int nl = (CO / 2) * LX * M;
-        const size_t smem = (size_t)(nl + M) * sizeof(T2);
-        const int blocks = (M * M + LX - 1) / LX;
-        if (CO == 8) {
-            cudaFuncSetAttribute(fft_x_inv<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            fft_x_inv<T, 8><<<blocks, fft_threads(nl), smem, s>>>(c->plan, tw, so, (T *)c->b.grid_o[pix<T>()], LX);
-        } else {
-            cudaFuncSetAttribute(fft_x_inv<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            fft_x_inv<T, 4><<<blocks, fft_threads(nl), smem, s>>>(c->plan, tw, so, (T *)c->b.grid_o[pix<T>()], LX);
-        }
-        c->launches++;
+    if (CO == 8) {
+        cudaFuncSetAttribute(fft_x_inv<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fft_x_inv<T, 8><<<M * M / (NL / 4), kFftThreads, smem, s>>>(c->plan, tw, so, (T *)c->b.grid_o[pix<T>()]);
+    } else {
+        cudaFuncSetAttribute(fft_x_inv<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fft_x_inv<T, 4><<<M * M / (NL / 2), kFftThreads, smem, s>>>(c->plan, tw, so, (T *)c->b.grid_o[pix<T>()]);
     }
+    c->launches++;
     stage_mark(c, SE_STAGE_FFT_XI, s, true);
 }
 
@@ -796,8 +856,10 @@ void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int nc
 
 template void setup_support<float>(se_ctx *, cudaStream_t);
 template void setup_support<double>(se_ctx *, cudaStream_t);
-template void launch_wave<float>(se_ctx *, const float *, cudaStream_t, int);
-template void launch_wave<double>(se_ctx *, const double *, cudaStream_t, int);
+template void launch_wave_spread<float>(se_ctx *, const float *, cudaStream_t, int);
+template void launch_wave_spread<double>(se_ctx *, const double *, cudaStream_t, int);
+template void launch_wave_fft<float>(se_ctx *, cudaStream_t);
+template void launch_wave_fft<double>(se_ctx *, cudaStream_t);
 template void launch_gather_combine<float, float>(se_ctx *, const float *, const float *, float *, int, int, cudaStream_t);
 template void launch_gather_combine<float, double>(se_ctx *, const float *, const float *, double *, int, int, cudaStream_t);
 template void launch_gather_combine<double, float>(se_ctx *, const double *, const double *, float *, int, int, cudaStream_t);

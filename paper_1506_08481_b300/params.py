@@ -1,13 +1,24 @@
 """Host-side choice of the Ewald / Spectral Ewald parameters (xi, M, P, rc, m).
 
-Error model (relative, up to a prefactor C calibrated against the oracle):
-  real space   pairs beyond rc dropped:        exp(-(xi rc)^2)                (Eq. oseen-ewald-rs)
-  truncation   Gaussian cut at |s| = P/2:       exp(-m^2/2)                   (Eq. theta-param)
+Error model (relative 2-norm of the product, conservative by a factor 2-10 against the
+FP64 oracle on the measured configurations):
+  real space   pairs beyond rc dropped:        exp(-(xi rc)^2) f_r            (Eq. oseen-ewald-rs)
+  truncation   Gaussian cut at |s| = P/2:       exp(-m^2/2) f_w                (Eq. theta-param)
   resolution   the grid aliases of the Gaussian, ghat(nu -+ 1)/ghat(nu) = exp(-A (1 - 2|nu|)),
                weighted by the kernel decay exp(-B nu^2) of the mode nu = q/M:
-                 max_nu exp(-A (1 - 2 nu) - B nu^2),  A = pi^2 P^2/(2 m^2),  B = (pi M/(xi L))^2
+                 max_nu exp(-A (1 - 2 nu) - B nu^2) f_w,  A = pi^2 P^2/(2 m^2),  B = (pi M/(xi L))^2
                (its nu = 1/2 value exp(-B/4) is the wave-space truncation of Eq. oseen-ewald-ws)
-With m = sqrt(pi P) the truncation is exp(-P pi/2), the minimum error of Eq. error-scale.
+The factors carry the derivatives that the torque, stresslet and Faxen terms put on
+the kernels (Eq. mul-expand: up to two Laplacians and two gradients of J), which
+multiply each truncated tail by powers of the wave number or of 1/r:
+  f_r = 1 + 0.1 (a xi)^4 (xi rc)^6,    f_w = 1 + 0.25 (a xi)^8 E_w^6,   E_w = pi M/(2 xi L),
+with a the effective radius <a^8>^(1/8) (fitted to the oracle's real- and wave-space
+truncation errors of mono-, bi- and polydisperse suspensions, 12 components).
+FP32 products add a rounding floor 3e-7 (1 + R): the wave grids carry each particle's
+own wave-space self term, which the FP64 self correction cancels (Eq. uf-self and its
+torque/stresslet analogues); R = (20/3) (a xi)^3 (25 - 42 (a xi)^2 + 27 (a xi)^4) / (50 pi^(1/2))
+is the ratio of that stresslet self term to the isolated-sphere stresslet mobility
+3/(20 pi eta a^3), so the FP32 error grows with a xi and the choice keeps a xi near 1.
 The net k-space factor exp(theta q^2/(4 xi^2) - k^2/(4 xi^2)) of Eq. wave-result never
 amplifies (rounding noise stays at working precision) iff P xi L <= M m.
 Cost model (relative device time of this library's kernels): real-space pairs
@@ -18,8 +29,10 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass
 
-# prefactor between the exponential model and the measured relative 2-norm error
-ERROR_PREFACTOR = 100.0
+import numpy as np
+
+# prefactor between the model and the measured relative 2-norm error
+ERROR_PREFACTOR = 1.0
 
 
 @dataclass
@@ -51,19 +64,57 @@ def fft_sizes(lo: int = 8, hi: int = 512) -> list[int]:
     return sorted(out)
 
 
-def resolution_exponent(P: int, m: float, M: int, xi: float, L: float) -> float:
+def effective_radius(rad) -> float:
+    """<a^8>^(1/8), the radius that sets the size factors of the error model."""
+    r = np.asarray(rad, dtype=np.float64)
+    return float(np.mean(r ** 8) ** 0.125)
+
+
+def resolution_exponent(P: int, m, M: int, xi, L: float):
     """min over modes of A (1 - 2 nu) + B nu^2 (the resolution error is exp(-this))."""
-    A = math.pi ** 2 * P ** 2 / (2.0 * m * m)
-    B = (math.pi * M / (xi * L)) ** 2
-    nu = A / B
-    return B / 4.0 if nu >= 0.5 else A - A * A / B
+    A = math.pi ** 2 * P ** 2 / (2.0 * np.asarray(m) ** 2)
+    B = (math.pi * M / (np.asarray(xi) * L)) ** 2
+    return np.where(A / B >= 0.5, B / 4.0, A - A * A / B)
 
 
-def error_estimate(L: float, xi: float, M: int, P: int, rc: float, m: float) -> float:
+def _f_real(a, xi, Er):
+    return 1.0 + 0.1 * (a * xi) ** 4 * Er ** 6
+
+
+def _f_wave(a, xi, M, L):
+    Ew = math.pi * M / (2.0 * xi * L)
+    return 1.0 + 0.25 * (a * xi) ** 8 * Ew ** 6
+
+
+FP32_FLOOR = 3e-7
+
+
+def self_ratio(axi):
+    """Wave-space stresslet self term over the isolated-sphere stresslet mobility at a xi."""
+    axi = np.asarray(axi, dtype=np.float64)
+    return axi ** 3 * (25.0 - 42.0 * axi ** 2 + 27.0 * axi ** 4) * (20.0 / 3.0) / (50.0 * math.sqrt(math.pi))
+
+
+def _e32(a, xi):
+    return FP32_FLOOR * (1.0 + self_ratio(a * xi))
+
+
+def error_terms(L: float, xi: float, M: int, P: int, rc: float, m: float, a_eff: float = 1.0,
+                precision: int = 1) -> dict:
+    """The modelled error terms (relative); precision 0 adds the FP32 rounding floor."""
+    fw = _f_wave(a_eff, xi, M, L)
+    t = {"real": ERROR_PREFACTOR * math.exp(-(xi * rc) ** 2) * _f_real(a_eff, xi, xi * rc),
+         "truncation": ERROR_PREFACTOR * math.exp(-m * m / 2.0) * fw,
+         "resolution": ERROR_PREFACTOR * float(np.exp(-resolution_exponent(P, m, M, xi, L))) * fw}
+    if precision == 0:
+        t["fp32"] = float(_e32(a_eff, xi))
+    return t
+
+
+def error_estimate(L: float, xi: float, M: int, P: int, rc: float, m: float, a_eff: float = 1.0,
+                   precision: int = 1) -> float:
     """Model of the relative error of the product."""
-    e = max(math.exp(-(xi * rc) ** 2), math.exp(-m * m / 2.0),
-            math.exp(-resolution_exponent(P, m, M, xi, L)))
-    return ERROR_PREFACTOR * e
+    return max(error_terms(L, xi, M, P, rc, m, a_eff, precision).values())
 
 
 def support_for(tol: float) -> int:
@@ -72,48 +123,77 @@ def support_for(tol: float) -> int:
     return max(4, P + (P % 2))
 
 
+def _rc_for(tol: float, a: float, xi: float) -> float:
+    """Smallest rc with the real-space term <= tol (bisection on xi rc)."""
+    lo, hi = 0.0, 12.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if ERROR_PREFACTOR * math.exp(-mid * mid) * _f_real(a, xi, mid) <= tol:
+            hi = mid
+        else:
+            lo = mid
+    return hi / xi
+
+
 def choose(L: float, N: int, tol: float, P: int | None = None, M_max: int = 384,
-           rc_max: float | None = None, M_min: int = 16) -> SeParams:
-    """Cheapest (xi, M, m, rc) whose modelled error is <= tol."""
-    E = math.log(ERROR_PREFACTOR / tol)
+           rc_max: float | None = None, M_min: int = 16, a_eff: float = 1.0,
+           precision: int = 1, fp32_tol: float | None = None) -> SeParams:
+    """Cheapest (xi, M, P, m, rc) whose modelled error is <= tol; a_eff is the effective
+    radius of the suspension (effective_radius), precision 0 for FP32 products.  fp32_tol
+    bounds the FP32 rounding floor separately (a solve whose Krylov products run in FP32
+    and whose residual runs in FP64 needs tol for the method and fp32_tol for FP32)."""
+    if precision == 0 and fp32_tol is None:
+        fp32_tol = tol
     supports = [P] if P is not None else list(range(support_for(tol), 33, 2))
     n = N / L ** 3
     rc_lim = 0.499 * L if rc_max is None else min(rc_max, 0.499 * L)
+    ms = 3.0 + 0.075 * np.arange(121)
     best = None
-    for P, M, i in ((P, M, i) for P in supports for M in fft_sizes(M_min, M_max) for i in range(121)):
-        if P > M - 8:
-            continue
-        if True:
-            m = 3.0 + 0.075 * i
-            if m * m / 2.0 < E:
+    for P in supports:
+        for M in fft_sizes(M_min, M_max):
+            if P > M - 8:
                 continue
-            A = math.pi ** 2 * P ** 2 / (2.0 * m * m)
-            if A <= E:
-                continue
-            # largest xi meeting the resolution bound (both branches of the minimum)
-            xi_res = math.pi * M * math.sqrt(A - E) / (L * A)
-            if A >= (math.pi * M / (xi_res * L)) ** 2 / 2.0:
-                xi_res = math.pi * M / (2.0 * L * math.sqrt(E))
-            xi = min(xi_res, M * m / (P * L))          # no k-space amplification
-            rc = math.sqrt(E) / xi
-            if rc > rc_lim or resolution_exponent(P, m, M, xi, L) < E * (1 - 1e-9):
-                continue
-            cost = N * n * 4.0 / 3.0 * math.pi * rc ** 3 + 0.5 * M ** 3 * math.log2(M) + 0.1 * N * P ** 3
-            if best is None or cost < best[0]:
-                best = (cost, SeParams(xi=xi, M=M, P=P, rc=rc, m=m))
+            # largest xi per m meeting the wave-space terms (all grow with xi): bisection
+            lo = np.full_like(ms, 1e-3)
+            hi = M * ms / (P * L)                   # no k-space amplification
+            def ok(xi):
+                fw = _f_wave(a_eff, xi, M, L)
+                e = np.maximum(np.exp(-ms * ms / 2.0), np.exp(-resolution_exponent(P, ms, M, xi, L)))
+                good = ERROR_PREFACTOR * e * fw <= tol
+                if fp32_tol is not None:
+                    good &= _e32(a_eff, xi) <= fp32_tol
+                return good
+            good_hi = ok(hi)
+            for _ in range(50):
+                mid = 0.5 * (lo + hi)
+                g = ok(mid)
+                lo = np.where(g, mid, lo)
+                hi = np.where(g, hi, mid)
+            xi_m = np.where(good_hi, M * ms / (P * L), lo)
+            feasible = ok(xi_m)
+            for xi, m, f in zip(xi_m, ms, feasible):
+                if not f:
+                    continue
+                rc = _rc_for(tol, a_eff, float(xi))
+                if rc > rc_lim:
+                    continue
+                cost = N * n * 4.0 / 3.0 * math.pi * rc ** 3 + 0.5 * M ** 3 * math.log2(M) + 0.1 * N * P ** 3
+                if best is None or cost < best[0]:
+                    best = (cost, SeParams(xi=float(xi), M=M, P=P, rc=rc, m=float(m)))
     if best is None:
         raise ValueError("no grid up to M_max meets the accuracy with rc < L/2")
     return best[1]
 
 
-def candidates(L: float, N: int, tol: float, M_max: int = 384, supports=None) -> list[SeParams]:
+def candidates(L: float, N: int, tol: float, M_max: int = 384, supports=None, a_eff: float = 1.0,
+               precision: int = 1) -> list[SeParams]:
     """Distinct parameter sets meeting the error model at tol: the cheapest per grid size
     for each support."""
     out, seen = [], set()
     for P in (supports or [None]):
         for M in fft_sizes(16, M_max):
             try:
-                sp = choose(L, N, tol, P=P, M_max=M, M_min=M)
+                sp = choose(L, N, tol, P=P, M_max=M, M_min=M, a_eff=a_eff, precision=precision)
             except ValueError:
                 continue
             key = (sp.M, sp.P)
@@ -129,7 +209,8 @@ def autotune(cfg, tol: float, ncomp: int = 3, precision: int = 0, max_candidates
     configuration on the GPU and return (SeParams, size_mode, ms per product) of the fastest."""
     import torch
     from . import api
-    cands = sorted(candidates(cfg.L, cfg.N, tol, supports=supports),
+    cands = sorted(candidates(cfg.L, cfg.N, tol, supports=supports, a_eff=effective_radius(cfg.rad),
+                              precision=precision),
                    key=lambda s: s.M ** 3 * math.log2(s.M) * 0.5 + 0.1 * cfg.N * s.P ** 3
                    + cfg.N ** 2 / cfg.L ** 3 * 4.19 * s.rc ** 3)[:max_candidates]
     x = torch.randn(cfg.N, ncomp, device="cuda", dtype=torch.float32 if precision == 0 else torch.float64)

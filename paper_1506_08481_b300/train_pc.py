@@ -62,7 +62,7 @@ def targets_for(ctx, cfg):
 
 
 def make_context(cfg, tol=1e-7, M_max=64):
-    sp = params.choose(cfg.L, cfg.N, tol, M_max=M_max)
+    sp = params.choose(cfg.L, cfg.N, tol, M_max=M_max, a_eff=params.effective_radius(cfg.rad))
     ctx = api.Context()
     ctx.set_params(sp.xi, sp.M, sp.P, sp.rc)
     ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)

@@ -15,7 +15,7 @@ def test_batch_graph_matches_per_box_products(oracle_mod):
     ctxs, xs, refs = [], [], []
     rng = np.random.default_rng(0)
     for cfg in boxes:
-        sp = params.choose(cfg.L, cfg.N, 1e-6, M_max=64)
+        sp = params.choose(cfg.L, cfg.N, 1e-6, M_max=64, a_eff=params.effective_radius(cfg.rad), precision=0)
         c = api.Context()
         c.set_params(sp.xi, sp.M, sp.P, sp.rc)
         c.set_option(api.SE_OPT_SHAPE_M, sp.m)

@@ -149,7 +149,7 @@ def test_ragged_sizes_and_grids(oracle_mod, N, M):
     from paper_1506_08481_b300 import params
     ref = oracle_mod.mobility(pos, rad, L, x, tol=1e-14)
     tol = 1e-11 if M > 24 else 1e-5
-    sp = params.choose(L, N, tol, M_max=M, M_min=M)
+    sp = params.choose(L, N, tol, M_max=M, M_min=M, a_eff=params.effective_radius(rad))
     ctx = make_ctx(sp.xi, M, sp.P, sp.rc, cfg, precision=1)
     ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
     y = gpu_apply(ctx, x)
@@ -198,7 +198,8 @@ def test_bidisperse_n2000_precision_ladder(oracle_mod):
     ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x, tol=1e-12)[:, :11]
     from paper_1506_08481_b300 import params
     for tol, prec in ((1e-4, 0), (1e-6, 0), (1e-8, 1)):
-        sp = params.choose(cfg.L, cfg.N, tol / 10, M_max=192)
+        sp = params.choose(cfg.L, cfg.N, tol / 3, M_max=192, a_eff=params.effective_radius(cfg.rad),
+                           precision=prec)
         ctx = make_ctx(sp.xi, sp.M, sp.P, sp.rc, cfg, precision=prec)
         ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
         y = gpu_apply(ctx, x[:, :11].copy())
