@@ -49,6 +49,14 @@ FP32_LANES_PER_SM, SMS = 128, 148
 # bytes of one stored real-space pair in FP32 (index 4 + separation 12 + 19 coefficients)
 PAIR_BYTES = 92
 
+# DRAM bytes (read + write) per launch from one ncu capture of the half-size case
+# (N = 100000, M = 192, the command in profiles/kernels_mono_n100000_P24.md), scaled to a
+# launch of the measured workload by grid points (M^3) or stored pairs.  A kernel changed
+# since that capture has no entry (its traffic is reported as null).
+NCU_CAPTURE = {"N": 100000, "M": 192, "npairs": 18740004}
+NCU_DRAM_BYTES = {"spread": 105e6, "gather": 183e6, "fft_x_fwd": 187e6, "fft_y_fwd": 184e6,
+                  "fft_z_scale": 195e6, "fft_y_inv": 184e6, "fft_x_inv": 187e6, "real": 1811e6}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -164,6 +172,16 @@ def count_pairs(cfg, rc):
     return int(t.count_neighbors(t, rc)) - cfg.N
 
 
+def ncu_traffic(stage, M, npairs):
+    """Scaled DRAM bytes per launch from the ncu capture, or None."""
+    b = NCU_DRAM_BYTES.get(stage)
+    if b is None:
+        return None
+    if stage == "real":
+        return b * npairs / NCU_CAPTURE["npairs"]
+    return b * (M / NCU_CAPTURE["M"]) ** 3
+
+
 def roofline_entry(stage, ms, N, M, P, CO, npairs, peaks, peak_kind):
     bound, units, unit = stage_algorithmic(stage, N, M, P, CO, npairs)
     t = ms * 1e-3
@@ -172,12 +190,13 @@ def roofline_entry(stage, ms, N, M, P, CO, npairs, peaks, peak_kind):
         peak = SMS * FP32_LANES_PER_SM * 2 * clk_mhz * 1e6 / 1e12
         achieved = units / t / 1e12
         return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "ms": ms,
+                "frac": achieved / peak, "ms": ms, "traffic": ncu_traffic(stage, M, npairs),
                 "peak_source": f"FP32 CUDA cores: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clk_mhz:.0f} MHz"}
     peak = peaks.get("hbm_gbs", 6400.0)
     achieved = units / t / 1e9
     return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "ms": ms, "peak_source": f"hbm_gbs ({peak_kind})"}
+            "frac": achieved / peak, "ms": ms, "traffic": ncu_traffic(stage, M, npairs),
+            "algorithmic_bytes": units, "peak_source": f"hbm_gbs ({peak_kind})"}
 
 
 def cpu_baseline(cfg, x, nrows_small=4, nrows_large=20):
@@ -434,7 +453,8 @@ def run_ours(args, rank, world, local):
     kernels["real"]["note"] = "timed alone (real-space part only); overlapped with spread/FFT in the product"
     dom = max((k for k in per_prod if k not in ("real", "permute")), key=lambda k: per_prod[k])
     roof = dict(kernels[dom])
-    roof["traffic"] = None
+    roof["traffic_source"] = ("ncu DRAM bytes of the N=100000 capture scaled by grid points or pairs"
+                              if roof["traffic"] is not None else "kernel changed since the last capture")
 
     workload = WORKLOAD if args.n == 200000 else WORKLOAD.replace("n200000", f"n{args.n}")
     if rank == 0:

@@ -30,3 +30,25 @@ def test_forward_consistent_with_loss():
     Y = mlp.forward(w, X)
     loss, _ = mlp.loss_and_grad(w, X, Y)
     assert loss < 1e-24
+
+
+def test_closed_forms_of_degenerate_networks():
+    """Zero hidden weights and biases: every hidden unit is tanh(0) = 0, so the output is
+    b3 * os whatever the input.  One hidden path (single nonzero weights): the output is
+    os * w3 * tanh(w2 * tanh(w1 (x - mu)/sd + b1))."""
+    rng = np.random.default_rng(2)
+    w = np.zeros(mlp.NW)
+    p = mlp.unpack(w)                       # views into w
+    p["b3"][:] = rng.standard_normal(mlp.O)
+    p["mu"][:] = rng.standard_normal(mlp.F)
+    p["sd"][:] = rng.uniform(0.5, 2.0, mlp.F)
+    p["os"][:] = rng.uniform(0.5, 2.0, mlp.O)
+    X = rng.standard_normal((7, mlp.F))
+    np.testing.assert_array_equal(mlp.forward(w, X), np.tile(p["b3"] * p["os"], (7, 1)))
+    p["b3"][:] = 0.0
+    p["W1"][5, 3], p["b1"][5], p["W2"][9, 5], p["W3"][2, 9] = 0.7, -0.2, 1.3, -0.9
+    y = mlp.forward(w, X)
+    xs = (X[:, 3] - p["mu"][3]) / p["sd"][3]
+    expect = p["os"][2] * -0.9 * np.tanh(1.3 * np.tanh(0.7 * xs - 0.2))
+    np.testing.assert_allclose(y[:, 2], expect, rtol=1e-14, atol=0)
+    assert np.all(y[:, [0, 1, 3]] == 0.0)
