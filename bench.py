@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU product and solve")
     ap.add_argument("--solve-maxit", type=int, default=800)
     ap.add_argument("--no-tuned", action="store_true", help="skip the error-model-tuned product")
+    ap.add_argument("--gather", type=int, default=0, choices=[0, 1, 2],
+                    help="gather kernel: by support size (0), warp per particle (1), staged bins (2)")
     ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2],
                     help="real-space sum beside the spread (0), beside the FFT chain (1), in line (2)")
     ap.add_argument("--fp64-solve-maxit", type=int, default=100,
@@ -272,6 +274,7 @@ def run_ours(args, rank, world, local):
     ctx.set_option(api.SE_OPT_SIZE_MODE, P_["size_mode"])
     ctx.set_option(api.SE_OPT_PRECISION, 0)
     ctx.set_option(api.SE_OPT_OVERLAP, args.overlap)
+    ctx.set_option(api.SE_OPT_GATHER, args.gather)
     ctx.set_config(cfg.pos, cfg.rad, cfg.L)
     x = torch.tensor(x_host, device=dev, dtype=torch.float32)
     y = torch.empty_like(x)
@@ -368,6 +371,7 @@ def run_ours(args, rank, world, local):
         ct.set_option(api.SE_OPT_SHAPE_M, sp.m)
         ct.set_option(api.SE_OPT_SIZE_MODE, 1)
         ct.set_option(api.SE_OPT_PRECISION, 0)
+        ct.set_option(api.SE_OPT_GATHER, args.gather)
         ct.set_config(cfg.pos, cfg.rad, cfg.L)
         yt = torch.empty_like(x)
         for _ in range(3):

@@ -75,6 +75,10 @@ typedef struct se_ctx se_ctx;
                                   beside the spread, 1 = beside the FFT chain, 2 = in line before the
                                   spread (default: the spread and gather fill every SM, so running
                                   beside them only slows them); results are identical */
+#define SE_OPT_GATHER      9   /* gather kernel: 0 = default (currently 1), 1 = one warp per particle
+                                  reading the grid through L2, 2 = one CTA per spreading bin staging
+                                  the bin's support window in shared memory (slower on B300 at P = 14
+                                  and 24); results agree to rounding */
 
 /* product stages reported by se_stage_times */
 #define SE_STAGE_PERMUTE   0   /* inputs into cell order */

@@ -26,6 +26,7 @@ SE_F32, SE_F64 = 0, 1
 SE_OPT_PRECISION, SE_OPT_SIZE_MODE, SE_OPT_ETA, SE_OPT_SHAPE_M, SE_OPT_RESTART, SE_OPT_PARTS = 1, 2, 3, 4, 5, 6
 SE_OPT_TIMING = 7
 SE_OPT_OVERLAP = 8
+SE_OPT_GATHER = 9
 STAGES = ("permute", "real", "spread", "fft_x_fwd", "fft_y_fwd", "fft_z_scale", "fft_y_inv", "fft_x_inv", "gather")
 SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED = 0, 1, 2
 

@@ -123,6 +123,7 @@ static void free_config(se_ctx *c)
     for (int q = 0; q < 2; ++q) {
         dfree(c->b.sup_s0[q]);
         dfree(c->b.sup_w[q]);
+        dfree(c->b.self_c[q]);
         dfree(c->b.xs[q]);
         dfree(c->b.yreal[q]);
         dfree(c->b.rel[q]);
@@ -207,6 +208,7 @@ static int ensure_support(se_ctx *c, int prec)
     if (!c->support_ok[prec]) {
         dfree(c->b.sup_w[prec]);
         SE_ALLOC(c, c->b.sup_w[prec], N * 3 * c->P * es);
+        if (!c->b.self_c[prec]) SE_ALLOC(c, c->b.self_c[prec], N * 4 * es);
         return build_support(c, prec);
     }
     return SE_OK;
@@ -320,7 +322,16 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         return SE_OK;
     case SE_OPT_ETA:
         if (!(value > 0)) return set_error(c, SE_ERR_ARG, "eta must be positive");
-        c->eta = value;
+        if (value != c->eta) {
+            // the stored pair coefficients and the self coefficients carry 1/eta
+            c->eta = value;
+            for (int q = 0; q < 2; ++q) {
+                dfree(c->b.pair_x[q]);
+                dfree(c->b.pair_c[q]);
+                c->pairs_ok[q] = false;
+                c->support_ok[q] = false;
+            }
+        }
         c->pc_ready = false;
         return SE_OK;
     case SE_OPT_SHAPE_M:
@@ -341,6 +352,10 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
     case SE_OPT_OVERLAP:
         if (value != 0 && value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "overlap must be 0, 1 or 2");
         c->overlap = (int)value;
+        return SE_OK;
+    case SE_OPT_GATHER:
+        if (value != 0 && value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "gather must be 0, 1 or 2");
+        c->gather = (int)value;
         return SE_OK;
     case SE_OPT_TIMING:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "timing must be 0 or 1");

@@ -215,7 +215,7 @@ int build_support(se_ctx *c, int prec)
         SE_CUDA_CHECK(c, cudaMalloc(&count, sizeof(int) * (ntile + 1)));
         tile_key_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, nt, c->b.sup_base, key);
         c->launches++;
-        int rc = counting_sort(c, N, ntile, key, count, c->b.tile_start, c->b.tile_perm, false);
+        int rc = counting_sort(c, N, ntile, key, count, c->b.tile_start, c->b.tile_perm, true);
         cudaError_t e = cudaStreamSynchronize(s);
         cudaFree(key);
         cudaFree(count);

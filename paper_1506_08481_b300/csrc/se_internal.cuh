@@ -54,6 +54,7 @@ struct Buffers {
     // per compute precision (index 0: FP32, 1: FP64)
     void *sup_s0[2] = {};        // [N][3] T: offset of the first support point from the particle
     void *sup_w[2] = {};         // [N][3][P] T: Gaussian weights along each axis
+    void *self_c[2] = {};        // [N][4] T: self coefficients of U, Omega, E, E_tr (computed in FP64)
     void *rel[2] = {};           // [N][4] T offset from the cell origin (3) and radius
     void *xs[2] = {};            // [N][12] T inputs in cell order
     void *yreal[2] = {};         // [N][12] T real-space result
@@ -94,6 +95,7 @@ struct se_ctx {
     int restart = 30;
     int parts = 7;
     int overlap = 2;             // SE_OPT_OVERLAP
+    int gather = 0;              // SE_OPT_GATHER
     // configuration
     bool have_config = false;
     bool support_ok[2] = {false, false};

@@ -350,6 +350,9 @@ struct Gm {
 
 using namespace se;
 
+// working-precision restart residuals are used while rel > kFp64Switch * rtol
+constexpr double kFp64Switch = 30.0;
+
 extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype, double rtol, int maxit,
                         int precond, int *iters, double *relres)
 {
@@ -417,13 +420,21 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
     if (bnorm == 0.0) {
         SE_CUDA_CHECK(c, cudaMemsetAsync(xd, 0, n * sizeof(double), s));
     } else {
+        // Residuals at the restarts: while the working-precision residual b - M x is well
+        // above rtol (kFp64Switch rtol) it is formed with working-precision products
+        // (accumulated in FP64): its FP32 rounding, a few 1e-7 of |M| |x|, is then small
+        // against the residual itself.  Below that every restart uses the FP64 residual
+        // (an FP64 product), so each further cycle is a step of iterative refinement on
+        // the FP64 residual, and convergence is decided by it.
+        bool fp64_res = c->precision == 1;
         for (;;) {
-            // FP64 true residual
+            bool exact = fp64_res;            // r is the FP64 residual (or b itself)
             if (x_zero) {
                 SE_CUDA_CHECK(c, cudaMemcpyAsync(r, bd, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
                 x_zero = false;
+                exact = true;
             } else {
-                rc = se_apply_internal(c, ncomp, xd, w, SE_F64, 1);
+                rc = se_apply_internal(c, ncomp, xd, w, SE_F64, fp64_res ? 1 : c->precision);
                 if (rc != SE_OK) return rc;
                 axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, bd, -1.0, w, r);
                 c->launches++;
@@ -434,6 +445,10 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
             const double beta = std::sqrt(rn2);
             rel = beta / bnorm;
             if (!std::isfinite(rel)) { c->err = "non-finite residual"; return SE_ERR_NONFINITE; }
+            if (!exact && (rel <= kFp64Switch * rtol || prods >= maxit)) {
+                fp64_res = true;              // from here on the FP64 residual decides
+                continue;
+            }
             if (rel <= rtol || prods >= maxit) break;
             axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0 / beta, r, 0.0, r, V);
             c->launches++;

@@ -23,6 +23,7 @@
 // Ghat'' = -k^2 Ghat, and gathered with weight a_i^2/6 (U) or a_i^2/10 (E).
 // Real-space approach: the target Laplacian acts on the gather weights instead.
 // Nyquist planes and q = 0 are set to zero.
+#include <algorithm>
 #include <cstdio>
 #include <type_traits>
 
@@ -274,6 +275,23 @@ __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeP
     }
 }
 
+// Self coefficients of particle i (FP64, once per configuration): the isolated sphere
+// (Eqs. faxen-f/t/s/p: 1/(6 pi eta a), 1/(8 pi eta a^3), 3/(20 pi eta a^3),
+// 3/(16 pi eta a^3)) minus the self term that the wave-space sum contains (Eq. uf-self
+// for U and its torque and stresslet analogues; the source-pressure coupling has none).
+template <typename T>
+__global__ void self_coef_kernel(int N, double xi, double eta, const double *rad, T *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double a = rad[i], a2 = a * a, x2 = xi * xi, pi32 = kPi * sqrt(kPi);
+    out[4 * i] = (T)(1.0 / (6 * kPi * eta * a) - xi * (9 - 10 * a2 * x2 + 7 * a2 * a2 * x2 * x2) / (18 * pi32 * eta));
+    out[4 * i + 1] = (T)(1.0 / (8 * kPi * eta * a * a2) - 5 * xi * x2 / (12 * pi32 * eta));
+    out[4 * i + 2] = (T)(3.0 / (20 * kPi * eta * a * a2) -
+                         xi * x2 * (25 - 42 * a2 * x2 + 27 * a2 * a2 * x2 * x2) / (50 * pi32 * eta));
+    out[4 * i + 3] = (T)(3.0 / (16 * kPi * eta * a * a2));
+}
+
 // ---------------------------------------------------------------- FFT passes
 //
 // Each pass moves a chunk of lines into shared memory with 16-byte asynchronous
@@ -370,9 +388,10 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_y(FftPlan plan, const type
 // memory); input lines q * 4 + c, output lines q * CO + c (the component order of the
 // arrays in HBM).
 template <typename T, int CO, int LB>
-__global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, SeParams p, const typename C2<T>::t *twg,
+__global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, const typename C2<T>::t *twg,
                                                               const typename C2<T>::t *specf,
-                                                              typename C2<T>::t *speco, T cnorm)
+                                                              typename C2<T>::t *speco, T cnorm, T twopiL, T i4x2,
+                                                              T ecoef)
 {
     using T2 = typename C2<T>::t;
     constexpr int NLI = 4 * LB, NLO = LB * CO, CPE = sizeof(T) == 4 ? 2 : 1;
@@ -396,9 +415,6 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, SePa
     T2 *Y = X == A ? B : A;
 
     const int ys = y <= M / 2 ? y : y - M;
-    const T twopiL = (T)(2.0 * kPi / p.L);
-    const T i4x2 = (T)(0.25 / (p.xi * p.xi));
-    const T ecoef = (T)(2.0 * kPi * kPi / (p.alpha * (double)M * M));
     for (int e = threadIdx.x; e < LB * M; e += blockDim.x) {
         const int q = e % LB, z = e / LB;
         const int qx = q0 + q, zsn = z <= M / 2 ? z : z - M;
@@ -411,7 +427,10 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, SePa
             const T kx = twopiL * qx, ky = twopiL * ys, kz = twopiL * zsn;
             const T k2 = kx * kx + ky * ky + kz * kz;
             const T q2 = (T)(qx * qx + ys * ys + zsn * zsn);
-            const T E = exp(-k2 * i4x2 + ecoef * q2) * cnorm;
+            const T ex = -k2 * i4x2 + ecoef * q2;
+            T E;
+            if constexpr (sizeof(T) == 4) E = expf(ex) * cnorm;
+            else E = exp(ex) * cnorm;
             const T ik2 = 1 / k2;
             const T Phi = E * (1 + k2 * i4x2) * ik2;
             const T2 *h = X + z * NLI + q * 4;
@@ -506,6 +525,52 @@ __device__ __forceinline__ void kahan_add(T &sum, T &comp, T v)
     sum = t;
 }
 
+// Wave sums acc[13] of particle i (internal order) -> outputs in the caller's order:
+// Omega = alpha kappa sum g (s x v), E on the orthonormal basis from the symmetric sums,
+// plus the real-space part and the self terms: isolated sphere (Eqs. faxen-f/t/s/p)
+// minus the self term in the wave sum (Eq. uf-self and its torque/stresslet analogues).
+template <typename T, typename TO, int CO>
+__device__ __forceinline__ void combine_write(const SeParams &p, const T (&acc)[13], int i, const T *selfc,
+                                              const int *perm, const T *xs, const T *yreal, TO *y,
+                                              int ncomp_out, int with_self)
+{
+    const T alpha = (T)p.alpha, kap = (T)p.kappa;
+    T out[kNC];
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = acc[2];
+    const T ak = alpha * kap;
+    out[3] = ak * acc[3];
+    out[4] = ak * acc[4];
+    out[5] = ak * acc[5];
+    {
+        // symmetric tensor A (xx yy zz xy xz yz) with off-diagonals stored as 2*A_xy
+        const T f = CO == 8 ? 2 * alpha * kap : (T)1;
+        const T Axx = f * acc[6], Ayy = f * acc[7], Azz = f * acc[8];
+        const T Axy = f * acc[9] * (T)0.5, Axz = f * acc[10] * (T)0.5, Ayz = f * acc[11] * (T)0.5;
+        const T r2 = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637, s2 = (T)1.41421356237309504880;
+        out[6] = r2 * (Axx - Ayy);
+        out[7] = r6 * (2 * Azz - Axx - Ayy);
+        out[8] = s2 * Axy;
+        out[9] = s2 * Axz;
+        out[10] = s2 * Ayz;
+    }
+    out[11] = acc[12];
+    const T *xi_ = xs + (size_t)i * kNC;
+    const T *yr = yreal + (size_t)i * kNC;
+    T sc[4] = {0, 0, 0, 0};
+    if (with_self) {
+        sc[0] = selfc[4 * i];
+        sc[1] = selfc[4 * i + 1];
+        sc[2] = selfc[4 * i + 2];
+        sc[3] = selfc[4 * i + 3];
+    }
+    TO *yo = y + (size_t)perm[i] * ncomp_out;
+#pragma unroll
+    for (int c = 0; c < kNC; ++c)
+        if (c < ncomp_out) yo[c] = (TO)(out[c] + yr[c] + sc[c < 3 ? 0 : (c < 6 ? 1 : (c < 11 ? 2 : 3))] * xi_[c]);
+}
+
 // One warp per particle: trapezoid-rule convolution of the gathered grids with the
 // particle's Gaussian (and its derivatives) over the P^3 support, then
 // y = real + wave + self, written in the caller's order and dtype.
@@ -517,7 +582,7 @@ __device__ __forceinline__ void kahan_add(T &sum, T &comp, T v)
 // Column contributions are Kahan-compensated across the P^2 / 32 columns of a lane.
 template <typename T, typename TO, int CO, int NCOMP>
 __global__ void __launch_bounds__(256, 4) gather_kernel(SeParams p, int N, const int *base, const T *s0g,
-                                                     const T *wg, const double *rad, const int *perm,
+                                                     const T *wg, const double *rad, const T *selfc, const int *perm,
                                                      const T *grid, const T *xs, const T *yreal, TO *y,
                                                      int ncomp_out, int with_wave, int with_self)
 {
@@ -638,43 +703,240 @@ __global__ void __launch_bounds__(256, 4) gather_kernel(SeParams p, int N, const
         }
     }
     if (lane != 0) return;
-    // finalise the wave part: Omega = alpha kappa sum g (s x v); E from the symmetric sums
-    T out[kNC];
-    out[0] = acc[0];
-    out[1] = acc[1];
-    out[2] = acc[2];
-    const T ak = alpha * kap;
-    out[3] = ak * acc[3];
-    out[4] = ak * acc[4];
-    out[5] = ak * acc[5];
-    {
-        // symmetric tensor A (xx yy zz xy xz yz) with off-diagonals stored as 2*A_xy
-        const T f = CO == 8 ? 2 * alpha * kap : (T)1;
-        const T Axx = f * acc[6], Ayy = f * acc[7], Azz = f * acc[8];
-        const T Axy = f * acc[9] * (T)0.5, Axz = f * acc[10] * (T)0.5, Ayz = f * acc[11] * (T)0.5;
-        const T r2 = (T)0.70710678118654752440, r6 = (T)0.40824829046386301637, s2 = (T)1.41421356237309504880;
-        out[6] = r2 * (Axx - Ayy);
-        out[7] = r6 * (2 * Azz - Axx - Ayy);
-        out[8] = s2 * Axy;
-        out[9] = s2 * Axz;
-        out[10] = s2 * Ayz;
-    }
-    out[11] = acc[12];
-    // self: isolated sphere (Eqs. faxen-f/t/s/p) minus the self term in the wave sum (Eq. uf-self)
-    const T *xi_ = xs + (size_t)i * kNC;
-    const T *yr = yreal + (size_t)i * kNC;
-    double sU = 0, sO = 0, sE = 0, sP = 0;
-    if (with_self) {
-        const double xi = p.xi, eta = p.eta, a2 = ad * ad, x2 = xi * xi, pi32 = kPi * sqrt(kPi);
-        sU = 1.0 / (6 * kPi * eta * ad) - xi * (9 - 10 * a2 * x2 + 7 * a2 * a2 * x2 * x2) / (18 * pi32 * eta);
-        sO = 1.0 / (8 * kPi * eta * ad * a2) - 5 * xi * x2 / (12 * pi32 * eta);
-        sE = 3.0 / (20 * kPi * eta * ad * a2) - xi * x2 * (25 - 42 * a2 * x2 + 27 * a2 * a2 * x2 * x2) / (50 * pi32 * eta);
-        sP = 3.0 / (16 * kPi * eta * ad * a2);
-    }
-    TO *yo = y + (size_t)perm[i] * ncomp_out;
-    for (int c = 0; c < ncomp_out; ++c) {
-        const double sc = c < 3 ? sU : (c < 6 ? sO : (c < 11 ? sE : sP));
-        yo[c] = (TO)((double)out[c] + (double)yr[c] + sc * (double)xi_[c]);
+    combine_write<T, TO, CO>(p, acc, i, selfc, perm, xs, yreal, y, ncomp_out, with_self);
+}
+
+// ---------------------------------------------------------------- staged gather
+//
+// The particles whose support starts in one kTile^3 tile (a spreading bin) share a
+// window of U = kTile + P - 1 grid points per dimension.  A CTA takes one bin and
+// stages the window in shared memory Z planes at a time (16-byte asynchronous copies,
+// periodic wrap per point); every support row (y, z) of every particle of the bin is
+// summed along x against the particle's table W_x = g_x (1, s_x, s_x^2, s_x^3): 13 FMAs
+// per grid point, operands from shared memory.  The row moments become the 13 wave
+// sums with the (y, z) polynomial weights (the transpose of the column form above).
+// Rows of a slab are dealt to the warps in contiguous ranges of 32-row chunks; a warp
+// reduces its row sums per particle into its own shared slot (Kahan-compensated) and
+// the slots are added in warp order at the end, so the result does not depend on
+// scheduling.
+template <typename T>
+struct StagedLayout {
+    static constexpr int W = 8, NA = 13;
+    int U, Z, G;
+    __host__ __device__ size_t slab_bytes(int CO) const { return (size_t)Z * U * U * CO * sizeof(T); }
+    __host__ __device__ size_t wx_off(int CO) const { return slab_bytes(CO); }
+    __host__ __device__ size_t wyz_off(int CO, int P) const { return wx_off(CO) + (size_t)G * P * 4 * sizeof(T); }
+    __host__ __device__ size_t slot_off(int CO, int P) const { return wyz_off(CO, P) + (size_t)G * 2 * P * sizeof(T); }
+    __host__ __device__ size_t pf_off(int CO, int P) const { return slot_off(CO, P) + 2 * (size_t)W * G * NA * sizeof(T); }
+    __host__ __device__ size_t pinf_off(int CO, int P) const { return pf_off(CO, P) + (size_t)G * 2 * sizeof(T); }
+    __host__ __device__ size_t bytes(int CO, int P) const { return pinf_off(CO, P) + (size_t)(5 * G + 1) * sizeof(int); }
+};
+
+template <typename T, typename TO, int CO, int NCOMP>
+__global__ void __launch_bounds__(256, 2) gather_staged_kernel(SeParams p, StagedLayout<T> lay, const int *tile_start,
+                                                            const int *tile_perm, const int *base, const T *s0g,
+                                                            const T *wg, const double *rad, const T *selfc,
+                                                            const int *perm, const T *grid, const T *xs,
+                                                            const T *yreal, TO *y, int ncomp_out, int with_self)
+{
+    constexpr int NA = 13, W = StagedLayout<T>::W, NV = CO / 4, CPP = CO * (int)sizeof(T) / 16;
+    using T4 = typename V4<T>::t;
+    const int P = p.P, M = p.M, nt = p.ntile, U = lay.U, Z = lay.Z, G = lay.G;
+    const int bin = blockIdx.x;
+    const int b0 = tile_start[bin], nb = tile_start[bin + 1] - b0;
+    if (nb == 0) return;
+    const int tx0 = (bin % nt) * kTile, ty0 = ((bin / nt) % nt) * kTile, tz0 = (bin / (nt * nt)) * kTile;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+    extern __shared__ __align__(32) unsigned char smstage[];
+    T4 *slab = reinterpret_cast<T4 *>(smstage);                       // [Z][U][U][NV]
+    T4 *Wx = reinterpret_cast<T4 *>(smstage + lay.wx_off(CO));        // [G][P]
+    T *wyz = reinterpret_cast<T *>(smstage + lay.wyz_off(CO, P));     // [G][2][P]: g_y, g_z
+    T *slot = reinterpret_cast<T *>(smstage + lay.slot_off(CO, P));   // [W][G][NA] sums, then compensations
+    T *scomp = slot + (size_t)W * G * NA;
+    T *pf = reinterpret_cast<T *>(smstage + lay.pf_off(CO, P));       // [G][2]: s_y0, s_z0
+    int *pinf = reinterpret_cast<int *>(smstage + lay.pinf_off(CO, P));  // [G][4]: ox, oy, oz, i
+    int *cpre = pinf + 4 * G;                                        // [G + 1] chunk prefix of a slab
+
+    const T alpha = (T)p.alpha, kap = (T)p.kappa;
+
+    for (int g0 = 0; g0 < nb; g0 += G) {
+        const int ng = min(G, nb - g0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < ng * P; e += blockDim.x) {
+            const int q = e / P, t = e - q * P;
+            const int i = tile_perm[b0 + g0 + q];
+            const T *w = wg + (size_t)i * 3 * P;
+            const T sx = s0g[3 * i] + (T)t, g = w[t];
+            Wx[q * P + t] = T4{g, g * sx, g * sx * sx, g * sx * sx * sx};
+            wyz[(2 * q) * P + t] = w[P + t];
+            wyz[(2 * q + 1) * P + t] = w[2 * P + t];
+        }
+        for (int q = threadIdx.x; q < ng; q += blockDim.x) {
+            const int i = tile_perm[b0 + g0 + q];
+            pinf[4 * q] = base[3 * i] - tx0;
+            pinf[4 * q + 1] = base[3 * i + 1] - ty0;
+            pinf[4 * q + 2] = base[3 * i + 2] - tz0;
+            pinf[4 * q + 3] = i;
+            pf[2 * q] = s0g[3 * i + 1];
+            pf[2 * q + 1] = s0g[3 * i + 2];
+        }
+        for (int e = threadIdx.x; e < 2 * W * G * NA; e += blockDim.x) slot[e] = 0;
+
+        for (int zs = 0; zs < U; zs += Z) {
+            const int nzs = min(Z, U - zs);
+            __syncthreads();                       // tables staged, previous slab consumed
+            // one warp per window row (uy, uz): lanes copy its points, wrapping in x
+            for (int r = wid; r < nzs * U; r += W) {
+                const int uy = r % U, uz = r / U;
+                const T *rowp = grid + ((size_t)wrapi(tz0 + zs + uz, M) * M + wrapi(ty0 + uy, M)) * M * CO;
+                for (int e = lane; e < U * CPP; e += 32) {
+                    const int ux = e / CPP, h = e - ux * CPP;
+                    cp_async16(smstage + ((size_t)r * U * CPP + e) * 16,
+                               rowp + (size_t)wrapi(tx0 + ux, M) * CO + h * (16 / sizeof(T)));
+                }
+            }
+            if (threadIdx.x == 0) {
+                int acc = 0;
+                for (int q = 0; q < ng; ++q) {
+                    const int oz = pinf[4 * q + 2];
+                    const int lo = max(oz, zs), hi = min(oz + P, zs + nzs);
+                    cpre[q] = acc;
+                    acc += hi > lo ? ((hi - lo) * P + 31) >> 5 : 0;
+                }
+                cpre[ng] = acc;
+            }
+            cp_async_wait_all();
+            __syncthreads();
+            const int nch = cpre[ng];
+            const int c_lo = (int)((long long)nch * wid / W), c_hi = (int)((long long)nch * (wid + 1) / W);
+            T o[NA];
+#pragma unroll
+            for (int c = 0; c < NA; ++c) o[c] = 0;
+            int cur = -1, q = 0;
+            auto flush = [&](int qq) {
+#pragma unroll
+                for (int c = 0; c < NA; ++c)
+                    for (int off = 16; off > 0; off >>= 1) o[c] += __shfl_xor_sync(0xffffffffu, o[c], off);
+                // lane c keeps component c: a Kahan step into this warp's slot
+                T v = 0;
+#pragma unroll
+                for (int c = 0; c < NA; ++c)
+                    if (lane == c) v = o[c];
+                if (lane < NA) {
+                    T *sm = slot + ((size_t)wid * G + qq) * NA + lane, *cm = scomp + ((size_t)wid * G + qq) * NA + lane;
+                    T s = *sm, cc = *cm;
+                    kahan_add(s, cc, v);
+                    *sm = s;
+                    *cm = cc;
+                }
+#pragma unroll
+                for (int c = 0; c < NA; ++c) o[c] = 0;
+            };
+            for (int ci = c_lo; ci < c_hi; ++ci) {
+                while (cpre[q + 1] <= ci) ++q;
+                if (q != cur) {
+                    if (cur >= 0) flush(cur);
+                    cur = q;
+                }
+                const int ox = pinf[4 * q], oy = pinf[4 * q + 1], oz = pinf[4 * q + 2];
+                const int lo = max(oz, zs), hi = min(oz + P, zs + nzs);
+                const int j = (ci - cpre[q]) * 32 + lane;
+                if (j >= (hi - lo) * P) continue;
+                const int yr = j % P, zr = lo - oz + j / P;
+                const T4 *g = slab + ((size_t)((oz + zr - zs) * U + oy + yr) * U + ox) * NV;
+                const T4 *wx = Wx + q * P;
+                T x0[3] = {0, 0, 0}, x1[3] = {0, 0, 0}, x2[3] = {0, 0, 0}, x3[3] = {0, 0, 0}, xp = 0;
+#pragma unroll 4
+                for (int t = 0; t < P; ++t) {
+                    const T4 wv = wx[t];
+                    const T4 u0 = g[t * NV];
+                    if constexpr (CO == 8) {
+                        const T4 u1 = g[t * NV + 1];
+                        // x0 = sum g v, x1 = sum g v'', x2 = sum g s_x v, x3 = sum g s_x v''
+                        x0[0] += wv.x * u0.x; x0[1] += wv.x * u0.y; x0[2] += wv.x * u0.z;
+                        x1[0] += wv.x * u0.w; x1[1] += wv.x * u1.x; x1[2] += wv.x * u1.y;
+                        if constexpr (NCOMP >= 6) {
+                            x2[0] += wv.y * u0.x; x2[1] += wv.y * u0.y; x2[2] += wv.y * u0.z;
+                            if constexpr (NCOMP >= 11) { x3[0] += wv.y * u0.w; x3[1] += wv.y * u1.x; x3[2] += wv.y * u1.y; }
+                        }
+                        if constexpr (NCOMP >= 12) xp += wv.x * u1.z;
+                    } else {
+                        // x0..x3 = sum g s_x^k v, k = 0..3
+                        x0[0] += wv.x * u0.x; x0[1] += wv.x * u0.y; x0[2] += wv.x * u0.z;
+                        x2[0] += wv.z * u0.x; x2[1] += wv.z * u0.y; x2[2] += wv.z * u0.z;
+                        if constexpr (NCOMP >= 6) {
+                            x1[0] += wv.y * u0.x; x1[1] += wv.y * u0.y; x1[2] += wv.y * u0.z;
+                            if constexpr (NCOMP >= 11) { x3[0] += wv.w * u0.x; x3[1] += wv.w * u0.y; x3[2] += wv.w * u0.z; }
+                        }
+                        if constexpr (NCOMP >= 12) xp += wv.x * u0.w;
+                    }
+                }
+                const T gyz = wyz[(2 * q) * P + yr] * wyz[(2 * q + 1) * P + zr];
+                const T sy = pf[2 * q] + (T)yr, sz = pf[2 * q + 1] + (T)zr;
+                T r[NA];
+                if constexpr (CO == 8) {
+                    const T ad = (T)rad[pinf[4 * q + 3]];
+                    const T c6 = ad * ad / 6, c10 = ad * ad / 10;
+                    r[0] = x0[0] + c6 * x1[0];
+                    r[1] = x0[1] + c6 * x1[1];
+                    r[2] = x0[2] + c6 * x1[2];
+                    r[3] = sy * x0[2] - sz * x0[1];
+                    r[4] = sz * x0[0] - x2[2];
+                    r[5] = x2[1] - sy * x0[0];
+                    const T Q0 = x0[0] + c10 * x1[0], Q1 = x0[1] + c10 * x1[1], Q2 = x0[2] + c10 * x1[2];
+                    const T R0 = x2[0] + c10 * x3[0], R1 = x2[1] + c10 * x3[1], R2 = x2[2] + c10 * x3[2];
+                    r[6] = R0;
+                    r[7] = sy * Q1;
+                    r[8] = sz * Q2;
+                    r[9] = R1 + sy * Q0;
+                    r[10] = R2 + sz * Q0;
+                    r[11] = sy * Q2 + sz * Q1;
+                } else {
+                    const T ad = (T)rad[pinf[4 * q + 3]];
+                    const T a2k2 = ad * ad * kap * kap;
+                    const T A0 = 1 - a2k2 * alpha, A1 = (T)(2.0 / 3.0) * a2k2 * alpha * alpha;
+                    const T B0 = 2 * kap * alpha * (1 - a2k2 * alpha);
+                    const T B1 = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
+                    const T syz2 = sy * sy + sz * sz, a0 = A0 + A1 * syz2, b0 = B0 + B1 * syz2;
+                    r[0] = a0 * x0[0] + A1 * x2[0];
+                    r[1] = a0 * x0[1] + A1 * x2[1];
+                    r[2] = a0 * x0[2] + A1 * x2[2];
+                    r[3] = sy * x0[2] - sz * x0[1];
+                    r[4] = sz * x0[0] - x1[2];
+                    r[5] = x1[1] - sy * x0[0];
+                    const T Q0 = b0 * x0[0] + B1 * x2[0], Q1 = b0 * x0[1] + B1 * x2[1], Q2 = b0 * x0[2] + B1 * x2[2];
+                    const T R0 = b0 * x1[0] + B1 * x3[0], R1 = b0 * x1[1] + B1 * x3[1], R2 = b0 * x1[2] + B1 * x3[2];
+                    r[6] = R0;
+                    r[7] = sy * Q1;
+                    r[8] = sz * Q2;
+                    r[9] = R1 + sy * Q0;
+                    r[10] = R2 + sz * Q0;
+                    r[11] = sy * Q2 + sz * Q1;
+                }
+                r[12] = xp;
+#pragma unroll
+                for (int c = 0; c < NA; ++c) o[c] += gyz * r[c];
+            }
+            if (cur >= 0) flush(cur);
+        }
+        __syncthreads();
+        // the W slots of a particle, added in warp order, then combined and written
+        for (int qq = wid; qq < ng; qq += W) {
+            T v = 0;
+            if (lane < NA)
+                for (int ww = 0; ww < W; ++ww) {
+                    const size_t k = ((size_t)ww * G + qq) * NA + lane;
+                    v += slot[k] - scomp[k];
+                }
+            T acc[NA];
+#pragma unroll
+            for (int c = 0; c < NA; ++c) acc[c] = __shfl_sync(0xffffffffu, v, c);
+            if (lane == 0) {
+                const int i = pinf[4 * qq + 3];
+                combine_write<T, TO, CO>(p, acc, i, selfc, perm, xs, yreal, y, ncomp_out, with_self);
+            }
+        }
     }
 }
 
@@ -688,6 +950,8 @@ static size_t fft_smem_bytes(int M, int nlb)
     return ((size_t)((M + 1) & ~1) + 2 * (size_t)nlb * (M + 2)) * sizeof(T2);
 }
 constexpr size_t kSmemMax = 227 * 1024;
+constexpr size_t kStagedBudget = 110 * 1024;   // staged gather: two CTAs per SM
+constexpr int kStagedMaxP = 0;                 // default: staged gather up to this support (measured slower at P = 14 and 24)
 
 void make_twiddles(se_ctx *c, int prec)
 {
@@ -716,7 +980,8 @@ void setup_support(se_ctx *c, cudaStream_t s)
     const int N = (int)c->N;
     support_kernel<T><<<(N + 127) / 128, 128, 0, s>>>(N, p, c->b.pos, de3, c->b.sup_base, (T *)c->b.sup_s0[pix<T>()],
                                                        (T *)c->b.sup_w[pix<T>()]);
-    c->launches++;
+    self_coef_kernel<T><<<(N + 127) / 128, 128, 0, s>>>(N, c->xi, c->eta, c->b.rad, (T *)c->b.self_c[pix<T>()]);
+    c->launches += 2;
     cudaStreamSynchronize(s);
     cudaFree(de3);
 }
@@ -743,8 +1008,12 @@ static void launch_z(se_ctx *c, const SeParams &p, const typename C2<T>::t *tw, 
     using T2 = typename C2<T>::t;
     const int M = c->M, Mh = M / 2 + 1;
     const size_t smem = fft_smem_bytes<T2>(M, CO * LB);
+    // k = 2 pi q / L; net exponent -k^2/(4 xi^2) + 2 pi^2 q^2/(alpha M^2) (see the file header)
+    const T twopiL = (T)(2.0 * kPi / p.L), i4x2 = (T)(0.25 / (p.xi * p.xi));
+    const T ecoef = (T)(2.0 * kPi * kPi / (p.alpha * (double)M * M));
     cudaFuncSetAttribute(fft_z_scale<T, CO, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fft_z_scale<T, CO, LB><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, smem, s>>>(c->plan, p, tw, sf, so, cnorm);
+    fft_z_scale<T, CO, LB><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, smem, s>>>(c->plan, tw, sf, so, cnorm, twopiL,
+                                                                                 i4x2, ecoef);
 }
 
 template <typename T, int CO>
@@ -837,9 +1106,42 @@ void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int nc
     const int with_self = (c->parts & 4) ? 1 : 0;
     auto go = [&](auto kern) {
         kern<<<grid, wpb * 32, 0, s>>>(p, N, c->b.sup_base, (const T *)c->b.sup_s0[pix<T>()], (const T *)c->b.sup_w[pix<T>()],
-                                       c->b.rad, c->b.perm, (const T *)c->b.grid_o[pix<T>()], xs, yreal, y, ncomp,
-                                       with_wave, with_self);
+                                       c->b.rad, (const T *)c->b.self_c[pix<T>()], c->b.perm,
+                                       (const T *)c->b.grid_o[pix<T>()], xs, yreal, y, ncomp, with_wave, with_self);
     };
+    const bool staged = c->gather == 2 || (c->gather == 0 && c->P <= kStagedMaxP);
+    if (with_wave && staged) {
+        // staged gather: one CTA per spreading bin (see gather_staged_kernel)
+        const int CO = p.hybrid ? 8 : 4;
+        StagedLayout<T> lay;
+        lay.U = kTile + c->P - 1;
+        lay.G = sizeof(T) == 4 ? 32 : 16;
+        lay.Z = 1;
+        lay.Z = (int)std::max<size_t>(1, std::min<size_t>(8, (kStagedBudget - (lay.bytes(CO, c->P) - lay.slab_bytes(CO))) /
+                                                            ((size_t)lay.U * lay.U * CO * sizeof(T))));
+        const size_t smem = lay.bytes(CO, c->P);
+        const int ntiles = p.ntile * p.ntile * p.ntile;
+        auto st = [&](auto kern) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<ntiles, 256, smem, s>>>(p, lay, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
+                                           (const T *)c->b.sup_s0[pix<T>()], (const T *)c->b.sup_w[pix<T>()], c->b.rad,
+                                           (const T *)c->b.self_c[pix<T>()], c->b.perm,
+                                           (const T *)c->b.grid_o[pix<T>()], xs, yreal, y, ncomp, with_self);
+        };
+        if (p.hybrid) {
+            if (ncomp <= 3) st(gather_staged_kernel<T, TO, 8, 3>);
+            else if (ncomp <= 6) st(gather_staged_kernel<T, TO, 8, 6>);
+            else if (ncomp <= 11) st(gather_staged_kernel<T, TO, 8, 11>);
+            else st(gather_staged_kernel<T, TO, 8, 12>);
+        } else {
+            if (ncomp <= 3) st(gather_staged_kernel<T, TO, 4, 3>);
+            else if (ncomp <= 6) st(gather_staged_kernel<T, TO, 4, 6>);
+            else if (ncomp <= 11) st(gather_staged_kernel<T, TO, 4, 11>);
+            else st(gather_staged_kernel<T, TO, 4, 12>);
+        }
+        c->launches++;
+        return;
+    }
     if (p.hybrid) {
         if (ncomp <= 3) go(gather_kernel<T, TO, 8, 3>);
         else if (ncomp <= 6) go(gather_kernel<T, TO, 8, 6>);
