@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU product and solve")
     ap.add_argument("--solve-maxit", type=int, default=800)
+    ap.add_argument("--restart", type=int, default=100, help="GMRES restart length of the solves")
     ap.add_argument("--no-tuned", action="store_true", help="skip the error-model-tuned product")
     ap.add_argument("--gather", type=int, default=0, choices=[0, 1, 2],
                     help="gather kernel: by support size (0), warp per particle (1), staged bins (2)")
@@ -399,7 +400,7 @@ def run_ours(args, rank, world, local):
     if not args.no_solve:
         b = torch.tensor(x_host[:, :11], device=dev, dtype=torch.float64)
         xs = torch.zeros_like(b)
-        ctx.set_option(api.SE_OPT_RESTART, 100)
+        ctx.set_option(api.SE_OPT_RESTART, args.restart)
         wpath = os.path.join(ROOT, "paper_1506_08481_b300", "learned_pc_weights.npy")
         if os.path.exists(wpath):
             ctx.set_learned_weights(np.load(wpath))
@@ -407,7 +408,7 @@ def run_ours(args, rank, world, local):
                 ("fp32_learned", 0, api.SE_PRECOND_LEARNED, args.solve_maxit)]
         if not args.no_fp64:
             runs.append(("fp64_block", 1, api.SE_PRECOND_BLOCK, args.fp64_solve_maxit))
-        solve = {"ncomp": 11, "rtol": 1e-6, "restart": 100, "maxit": args.solve_maxit,
+        solve = {"ncomp": 11, "rtol": 1e-6, "restart": args.restart, "maxit": args.solve_maxit,
                  "learned_weights": os.path.exists(wpath)}
         for name, prec, pc, maxit in runs:
             ctx.set_option(api.SE_OPT_PRECISION, prec)

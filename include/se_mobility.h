@@ -68,7 +68,7 @@ typedef struct se_ctx se_ctx;
 #define SE_OPT_SIZE_MODE   2   /* particle-size terms: 0 = hybrid (default), 1 = real-space approach */
 #define SE_OPT_ETA         3   /* solvent viscosity (default 1) */
 #define SE_OPT_SHAPE_M     4   /* Gaussian shape parameter m of Eq. theta-param (default sqrt(pi P)) */
-#define SE_OPT_RESTART     5   /* GMRES restart length (default 30) */
+#define SE_OPT_RESTART     5   /* GMRES restart length, 1..1000 (default 30; the basis takes (restart + 1) N ncomp doubles) */
 #define SE_OPT_PARTS       6   /* bit mask of terms: 1 real space, 2 wave space, 4 self (default 7) */
 #define SE_OPT_TIMING      7   /* 1: record CUDA events around every stage of each product (default 0) */
 #define SE_OPT_OVERLAP     8   /* where the real-space sum runs: 0 = on a second, high-priority stream

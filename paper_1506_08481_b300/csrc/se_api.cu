@@ -342,7 +342,7 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         c->pc_ready = false;
         return SE_OK;
     case SE_OPT_RESTART:
-        if (value < 1 || value > 200) return set_error(c, SE_ERR_ARG, "restart must be in [1, 200]");
+        if (value < 1 || value > 1000) return set_error(c, SE_ERR_ARG, "restart must be in [1, 1000]");
         c->restart = (int)value;
         return SE_OK;
     case SE_OPT_PARTS:

@@ -110,13 +110,15 @@ __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeP
                                                     const T *s0g, const T *wg, const double *rad,
                                                     const T *xs, T *grid)
 {
-    constexpr int TT = kTile, CH = 64, NPR = 22, MAXB = 125;
+    constexpr int TT = kTile, CH = 64, MAXB = 125;
     using T4 = typename V4<T>::t;
     // rows are XOR-swizzled by the particle slot so that the staging writes (one
     // particle per thread) spread over all banks; reads broadcast one particle's row
     __shared__ T sxy[CH][2 * TT];     // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
     __shared__ T4 swz[CH][TT];        // g_z (1, s_z, s_z^2, s_z^3) of plane t at t ^ (k & 7)
-    __shared__ T sp[CH][NPR];         // sx0 sy0 A0 A1 B0 B1 F(3) T(3) S(6) Str ok
+    // per particle, read as broadcast vectors: (sx0 sy0 A0 A1) (B0 B1 halves Str)
+    // (F0 F1 F2 T0) (T1 T2 Sxx Syy) (Szz Sxy Sxz Syz)
+    __shared__ T4 sp[CH][5];
     __shared__ int bin_beg[MAXB], bin_off[MAXB + 1];
     const int M = p.M, P = p.P, nt = p.ntile;
     const int tile = blockIdx.x;
@@ -177,70 +179,72 @@ __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeP
                 const T sz = s0g[3 * i + 2] + (T)iz;
                 swz[k][t ^ sw_z] = T4{g, g * sz, g * sz * sz, g * sz * sz * sz};
             }
-            sp[k][0] = s0g[3 * i] + (T)od[0];                 // offsets of the tile origin
-            sp[k][1] = s0g[3 * i + 1] + (T)od[1];
             const T a = (T)rad[i], a2k2 = a * a * kap * kap;
-            sp[k][2] = 1 - a2k2 * alpha;
-            sp[k][3] = (T)(2.0 / 3.0) * a2k2 * alpha * alpha;
-            sp[k][4] = 2 * kap * alpha * (1 - a2k2 * alpha);
-            sp[k][5] = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
             const T *xi = xs + (size_t)i * kNC;
-            sp[k][6] = xi[0];
-            sp[k][7] = xi[1];
-            sp[k][8] = xi[2];
-            if constexpr (NCOMP >= 6) { sp[k][9] = xi[3]; sp[k][10] = xi[4]; sp[k][11] = xi[5]; }
-            if constexpr (NCOMP >= 11) stresslet_tensor(xi + 6, &sp[k][12]);
-            if constexpr (NCOMP >= 12) sp[k][18] = xi[11];
+            T S[6] = {0, 0, 0, 0, 0, 0}, Tq[3] = {0, 0, 0};
+            if constexpr (NCOMP >= 6) { Tq[0] = xi[3]; Tq[1] = xi[4]; Tq[2] = xi[5]; }
+            if constexpr (NCOMP >= 11) stresslet_tensor(xi + 6, S);
             // which halves of the tile's 8 planes the support reaches (planes t with
             // 0 <= od_z + t < P); bit 0: planes 0-3, bit 1: planes 4-7
             const int zlo = max(0, -od[2]), zhi = min(TT, P - od[2]);
             const int halves = (zlo < TT / 2 && zhi > 0 ? 1 : 0) | (zhi > TT / 2 && zlo < TT ? 2 : 0);
-            sp[k][21] = ok ? (T)halves : (T)0;
+            // offsets of the tile origin, Faxen coefficients, moments
+            sp[k][0] = T4{s0g[3 * i] + (T)od[0], s0g[3 * i + 1] + (T)od[1], 1 - a2k2 * alpha,
+                          (T)(2.0 / 3.0) * a2k2 * alpha * alpha};
+            sp[k][1] = T4{2 * kap * alpha * (1 - a2k2 * alpha), (T)0.8 * kap * a2k2 * alpha * alpha * alpha,
+                          ok ? (T)halves : (T)0, NCOMP >= 12 ? xi[11] : (T)0};
+            sp[k][2] = T4{xi[0], xi[1], xi[2], Tq[0]};
+            sp[k][3] = T4{Tq[1], Tq[2], S[0], S[1]};
+            sp[k][4] = T4{S[2], S[3], S[4], S[5]};
         }
         __syncthreads();
         for (int k = 0; k < cnt; ++k) {
             const int sw_xy = (k >> 1) & 15, sw_z = k & 7;
             const T gxy = sxy[k][tx ^ sw_xy] * sxy[k][(TT + ty) ^ sw_xy];
-            const int halves = (int)sp[k][21];
+            const T4 v1 = sp[k][1];
+            const int halves = (int)v1.z;
             if (gxy == (T)0 || halves == 0) continue;
-            const T sx = sp[k][0] + tx, sy = sp[k][1] + ty;
+            const T4 v0 = sp[k][0], v2 = sp[k][2];
+            const T sx = v0.x + tx, sy = v0.y + ty;
             const T sxy2 = sx * sx + sy * sy;
-            const T A1 = sp[k][3], a0 = sp[k][2] + A1 * sxy2;
+            const T A1 = v0.w, a0 = v0.z + A1 * sxy2;
             // column coefficients c[alpha][p] of s_z^p (times g_xy)
             T c[3][4];
+            const T F[3] = {v2.x, v2.y, v2.z};
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                const T F = sp[k][6 + q];
-                c[q][0] = a0 * F;
+                c[q][0] = a0 * F[q];
                 c[q][1] = 0;
-                c[q][2] = A1 * F;
+                c[q][2] = A1 * F[q];
                 c[q][3] = 0;
             }
             if constexpr (NCOMP >= 6) {
                 // -alpha kappa (s x T), s x T = c0 + s_z c1
-                const T T0 = sp[k][9], T1 = sp[k][10], T2 = sp[k][11];
+                const T4 v3 = sp[k][3];
+                const T T0 = v2.w, T1 = v3.x, T2 = v3.y;
                 c[0][0] -= akap * sy * T2;
                 c[1][0] += akap * sx * T2;
                 c[2][0] -= akap * (sx * T1 - sy * T0);
                 c[0][1] += akap * T1;
                 c[1][1] -= akap * T0;
-            }
-            if constexpr (NCOMP >= 11) {
-                // (B0 + B1 s^2) S.s with S.s = d0 + s_z d1
-                const T *S = &sp[k][12];
-                const T B1 = sp[k][5], b0 = sp[k][4] + B1 * sxy2;
-                const T d00 = S[0] * sx + S[3] * sy, d01 = S[3] * sx + S[1] * sy, d02 = S[4] * sx + S[5] * sy;
-                const T d10 = S[4], d11 = S[5], d12 = S[2];
-                c[0][0] += b0 * d00; c[1][0] += b0 * d01; c[2][0] += b0 * d02;
-                c[0][1] += b0 * d10; c[1][1] += b0 * d11; c[2][1] += b0 * d12;
-                c[0][2] += B1 * d00; c[1][2] += B1 * d01; c[2][2] += B1 * d02;
-                c[0][3] = B1 * d10; c[1][3] = B1 * d11; c[2][3] = B1 * d12;
+                if constexpr (NCOMP >= 11) {
+                    // (B0 + B1 s^2) S.s with S.s = d0 + s_z d1
+                    const T4 v4 = sp[k][4];
+                    const T S[6] = {v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
+                    const T B1 = v1.y, b0 = v1.x + B1 * sxy2;
+                    const T d00 = S[0] * sx + S[3] * sy, d01 = S[3] * sx + S[1] * sy, d02 = S[4] * sx + S[5] * sy;
+                    const T d10 = S[4], d11 = S[5], d12 = S[2];
+                    c[0][0] += b0 * d00; c[1][0] += b0 * d01; c[2][0] += b0 * d02;
+                    c[0][1] += b0 * d10; c[1][1] += b0 * d11; c[2][1] += b0 * d12;
+                    c[0][2] += B1 * d00; c[1][2] += B1 * d01; c[2][2] += B1 * d02;
+                    c[0][3] = B1 * d10; c[1][3] = B1 * d11; c[2][3] = B1 * d12;
+                }
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) c[q][e] *= gxy;
-            const T cs = NCOMP >= 12 ? gxy * sp[k][18] : (T)0;
+            const T cs = NCOMP >= 12 ? gxy * v1.w : (T)0;
             auto planes = [&](auto z0c) {
                 constexpr int z0 = decltype(z0c)::value;
 #pragma unroll
