@@ -126,56 +126,67 @@ __device__ __forceinline__ void dft_generic(T2 (&v)[R], bool inv)
     }
 }
 
-// One out-of-place radix-R stage over NL element-major lines of length M.
-// inv_ns = 1/Ns: j mod Ns is formed as j - Ns floor((j + 1/2)/Ns), exact for the
-// j < 512, Ns <= 256 that occur (the fraction stays >= 1/(2 Ns) away from an integer).
-template <int R, int NL, typename T2>
+// One out-of-place radix-R stage over NL element-major lines of length M (INV selects
+// the inverse transform at compile time).  inv_ns = 1/Ns: j mod Ns is formed as
+// j - Ns floor((j + 1/2)/Ns), exact for the j < 512, Ns <= 256 that occur (the fraction
+// stays >= 1/(2 Ns) away from an integer).
+template <int R, int NL, bool INV, typename T2>
 __device__ __forceinline__ void fft_stage(const T2 *__restrict__ src, T2 *__restrict__ dst, int M, int Ns,
-                                          float inv_ns, const T2 *__restrict__ tw, bool inv)
+                                          float inv_ns, const T2 *__restrict__ tw)
 {
     const int nbl = M / R;
     const int tstep = M / (Ns * R);
     const int nb = nbl * NL;
+    const int sstride = nbl * NL, dstride = Ns * NL;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         const int l = b % NL, j = b / NL;
         T2 v[R];
+        const T2 *s = src + b;                 // = src + j NL + l
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[(j + r * nbl) * NL + l];
+        for (int r = 0; r < R; ++r) v[r] = s[r * sstride];
         int kk = 0;
         if (Ns > 1) {
             const int q = __float2int_rz(((float)j + 0.5f) * inv_ns);
             kk = j - q * Ns;
+            const int step = kk * tstep;
+            int t = step;
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                T2 w = tw[r * kk * tstep];
-                if (inv) w.y = -w.y;
+            for (int r = 1; r < R; ++r, t += step) {
+                T2 w = tw[t];
+                if constexpr (INV) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
         }
-        dft_generic<R>(v, inv);
+        dft_generic<R>(v, INV);
         T2 *d = dst + ((j - kk) * R + kk) * NL + l;
 #pragma unroll
-        for (int r = 0; r < R; ++r) d[r * Ns * NL] = v[r];
+        for (int r = 0; r < R; ++r) d[r * dstride] = v[r];
     }
     __syncthreads();
 }
 
 // Full transform of NL lines starting in buffer a (b is scratch of the same size);
 // returns the buffer that holds the result.
-template <int NL, typename T2>
-__device__ T2 *fft_run(T2 *a, T2 *b, const FftPlan &plan, const T2 *tw, bool inv)
+template <int NL, bool INV, typename T2>
+__device__ T2 *fft_run_dir(T2 *a, T2 *b, const FftPlan &plan, const T2 *tw)
 {
     int Ns = 1;
-    for (int s = 0; s < plan.nst; ++s) {
-        const int R = plan.rad[s];
+    // at most four radix passes for every admissible M (the plan puts 8 and 9 first);
+    // the radices are read with constant indices so the plan stays in registers
+    const int rads[4] = {plan.rad[0], plan.nst > 1 ? plan.rad[1] : 1, plan.nst > 2 ? plan.rad[2] : 1,
+                         plan.nst > 3 ? plan.rad[3] : 1};
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (s >= plan.nst) break;
+        const int R = rads[s];
         const float inv_ns = 1.0f / (float)Ns;
         switch (R) {
-        case 8: fft_stage<8, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
-        case 9: fft_stage<9, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
-        case 6: fft_stage<6, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
-        case 4: fft_stage<4, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
-        case 3: fft_stage<3, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
-        default: fft_stage<2, NL>(a, b, plan.M, Ns, inv_ns, tw, inv); break;
+        case 8: fft_stage<8, NL, INV>(a, b, plan.M, Ns, inv_ns, tw); break;
+        case 9: fft_stage<9, NL, INV>(a, b, plan.M, Ns, inv_ns, tw); break;
+        case 6: fft_stage<6, NL, INV>(a, b, plan.M, Ns, inv_ns, tw); break;
+        case 4: fft_stage<4, NL, INV>(a, b, plan.M, Ns, inv_ns, tw); break;
+        case 3: fft_stage<3, NL, INV>(a, b, plan.M, Ns, inv_ns, tw); break;
+        default: fft_stage<2, NL, INV>(a, b, plan.M, Ns, inv_ns, tw); break;
         }
         Ns *= R;
         T2 *t = a;
@@ -183,6 +194,12 @@ __device__ T2 *fft_run(T2 *a, T2 *b, const FftPlan &plan, const T2 *tw, bool inv
         b = t;
     }
     return a;
+}
+
+template <int NL, typename T2>
+__device__ T2 *fft_run(T2 *a, T2 *b, const FftPlan &plan, const T2 *tw, bool inv)
+{
+    return inv ? fft_run_dir<NL, true>(a, b, plan, tw) : fft_run_dir<NL, false>(a, b, plan, tw);
 }
 
 // 16-byte asynchronous global -> shared copies (both addresses 16-byte aligned)

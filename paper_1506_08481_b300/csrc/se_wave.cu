@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_x_fwd(FftPlan plan, const 
     }
     cp_async_wait_all();
     __syncthreads();
-    const T2 *Z = fft_run<NL>(A, B, plan, tw, false);
+    const T2 *Z = fft_run_dir<NL, false>(A, B, plan, tw);
     for (int e = threadIdx.x; e < NR * Mh * 2; e += blockDim.x) {
         const int h = e & 1, r = (e >> 1) % NR, q = (e >> 1) / NR;
         const T2 z = Z[q * NL + 2 * r + h];
@@ -358,9 +358,9 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_x_fwd(FftPlan plan, const 
 
 // y pass (forward or inverse) in place on half spectra [z][y][q][C]: a CTA takes the
 // NL / C wave numbers q0.. of one z plane, all C components, lines along y.
-template <typename T, int C>
+template <typename T, int C, bool INV>
 __global__ void __launch_bounds__(kFftThreads, 4) fft_y(FftPlan plan, const typename C2<T>::t *twg,
-                                                        typename C2<T>::t *data, int inv)
+                                                        typename C2<T>::t *data)
 {
     using T2 = typename C2<T>::t;
     constexpr int NL = fft_nl<T>(), LB = NL / C, CPE = sizeof(T) == 4 ? 2 : 1;   // complex per copy
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_y(FftPlan plan, const type
     }
     cp_async_wait_all();
     __syncthreads();
-    const T2 *Z = fft_run<NL>(A, B, plan, tw, inv != 0);
+    const T2 *Z = fft_run_dir<NL, INV>(A, B, plan, tw);
     for (int e = threadIdx.x; e < NL * M; e += blockDim.x) {
         const int l = e % NL, y = e / NL;
         if (l < nv) data[base + y * es + l] = Z[y * NL + l];
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, cons
     }
     cp_async_wait_all();
     __syncthreads();
-    T2 *X = fft_run<NLI>(A, B, plan, tw, false);
+    T2 *X = fft_run_dir<NLI, false>(A, B, plan, tw);
     T2 *Y = X == A ? B : A;
 
     const int ys = y <= M / 2 ? y : y - M;
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, cons
         for (int c = 0; c < CO; ++c) w[c] = o[c];
     }
     __syncthreads();
-    const T2 *Z = fft_run<NLO>(Y, X, plan, tw, true);
+    const T2 *Z = fft_run_dir<NLO, true>(Y, X, plan, tw);
     for (int e = threadIdx.x; e < NLO * M; e += blockDim.x) {
         const int l = e % NLO, z = e / NLO;
         if (l < nq * CO) speco[((size_t)z * zs + (size_t)y * Mh + q0) * CO + l] = Z[z * NLO + l];
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_x_inv(FftPlan plan, const 
         A[x * NL + l] = z;
     }
     __syncthreads();
-    const T2 *Z = fft_run<NL>(A, B, plan, tw, true);
+    const T2 *Z = fft_run_dir<NL, true>(A, B, plan, tw);
     for (int e = threadIdx.x; e < NR * M; e += blockDim.x) {
         const int r = e % NR, x = e / NR;
         const T2 *s = Z + x * NL + r * NP;
@@ -585,18 +585,21 @@ __device__ __forceinline__ void combine_write(const SeParams &p, const T (&acc)[
 // U(3), s x v (3), sym(s (x) w) (6: xx yy zz, xy xz yz doubled), p (1) once per column.
 // Column contributions are Kahan-compensated across the P^2 / 32 columns of a lane.
 template <typename T, typename TO, int CO, int NCOMP>
-__global__ void __launch_bounds__(256, 4) gather_kernel(SeParams p, int N, const int *base, const T *s0g,
-                                                     const T *wg, const double *rad, const T *selfc, const int *perm,
-                                                     const T *grid, const T *xs, const T *yreal, TO *y,
-                                                     int ncomp_out, int with_wave, int with_self)
+__global__ void __launch_bounds__(256, 4) gather_kernel(SeParams p, int N, const int *order, const int *base,
+                                                     const T *s0g, const T *wg, const double *rad, const T *selfc,
+                                                     const int *perm, const T *grid, const T *xs, const T *yreal,
+                                                     TO *y, int ncomp_out, int with_wave, int with_self)
 {
     constexpr int NA = 13;
     using T4 = typename V4<T>::t;
     __shared__ T4 Wz[8][32];
     __shared__ int Zi[8][32];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int i = blockIdx.x * (blockDim.x >> 5) + wl;
-    if (i >= N) return;
+    // particles in spreading-bin order (supports starting in the same 8^3 tile are
+    // taken by neighbouring warps, so their grid reads share L1 lines)
+    const int w_ = blockIdx.x * (blockDim.x >> 5) + wl;
+    if (w_ >= N) return;
+    const int i = order ? order[w_] : w_;
     const int M = p.M, P = p.P;
     const double ad = rad[i];
     const T a = (T)ad;
@@ -1031,15 +1034,15 @@ static void launch_z_fit(se_ctx *c, const SeParams &p, const typename C2<T>::t *
     else launch_z<T, CO, 1>(c, p, tw, sf, so, cnorm, s);
 }
 
-template <typename T, int C>
-static void launch_y(se_ctx *c, const typename C2<T>::t *tw, typename C2<T>::t *data, int inv, cudaStream_t s)
+template <typename T, int C, bool INV>
+static void launch_y(se_ctx *c, const typename C2<T>::t *tw, typename C2<T>::t *data, cudaStream_t s)
 {
     using T2 = typename C2<T>::t;
     constexpr int NL = fft_nl<T>(), LB = NL / C;
     const int M = c->M, Mh = M / 2 + 1;
     const size_t smem = fft_smem_bytes<T2>(M, NL);
-    cudaFuncSetAttribute(fft_y<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fft_y<T, C><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, smem, s>>>(c->plan, tw, data, inv);
+    cudaFuncSetAttribute(fft_y<T, C, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fft_y<T, C, INV><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, smem, s>>>(c->plan, tw, data);
 }
 
 template <typename T>
@@ -1070,7 +1073,7 @@ void launch_wave_fft(se_ctx *c, cudaStream_t s)
     stage_mark(c, SE_STAGE_FFT_XF, s, true);
 
     stage_mark(c, SE_STAGE_FFT_YF, s, false);
-    launch_y<T, 4>(c, tw, sf, 0, s);
+    launch_y<T, 4, false>(c, tw, sf, s);
     c->launches++;
     stage_mark(c, SE_STAGE_FFT_YF, s, true);
 
@@ -1082,8 +1085,8 @@ void launch_wave_fft(se_ctx *c, cudaStream_t s)
     stage_mark(c, SE_STAGE_FFT_Z, s, true);
 
     stage_mark(c, SE_STAGE_FFT_YI, s, false);
-    if (CO == 8) launch_y<T, 8>(c, tw, so, 1, s);
-    else launch_y<T, 4>(c, tw, so, 1, s);
+    if (CO == 8) launch_y<T, 8, true>(c, tw, so, s);
+    else launch_y<T, 4, true>(c, tw, so, s);
     c->launches++;
     stage_mark(c, SE_STAGE_FFT_YI, s, true);
 
@@ -1109,7 +1112,8 @@ void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int nc
     dim3 grid((N + wpb - 1) / wpb);
     const int with_self = (c->parts & 4) ? 1 : 0;
     auto go = [&](auto kern) {
-        kern<<<grid, wpb * 32, 0, s>>>(p, N, c->b.sup_base, (const T *)c->b.sup_s0[pix<T>()], (const T *)c->b.sup_w[pix<T>()],
+        kern<<<grid, wpb * 32, 0, s>>>(p, N, with_wave ? c->b.tile_perm : nullptr, c->b.sup_base,
+                                       (const T *)c->b.sup_s0[pix<T>()], (const T *)c->b.sup_w[pix<T>()],
                                        c->b.rad, (const T *)c->b.self_c[pix<T>()], c->b.perm,
                                        (const T *)c->b.grid_o[pix<T>()], xs, yreal, y, ncomp, with_wave, with_self);
     };
