@@ -96,6 +96,10 @@ typedef struct se_ctx se_ctx;
 #define SE_PRECOND_NONE    0
 #define SE_PRECOND_BLOCK   1   /* block-diagonal self + own-image blocks (Sec. 4.2) */
 #define SE_PRECOND_LEARNED 2   /* block preconditioner + learned correction (BLOCK without weights) */
+#define SE_PRECOND_SPECTRAL 3  /* block preconditioner minus a correction of the long-wavelength
+                                  transverse force modes (their eigenvalues n/(eta k^2) set the
+                                  iteration count), applied as a forces-only product on a coarse
+                                  grid; built with three extra products.  Not in the paper. */
 
 /* Create a context on CUDA device `device`; `stream` is a cudaStream_t (may be 0 for
  * the legacy default stream), borrowed for the context's lifetime.  *out receives the

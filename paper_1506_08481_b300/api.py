@@ -28,7 +28,7 @@ SE_OPT_TIMING = 7
 SE_OPT_OVERLAP = 8
 SE_OPT_GATHER = 9
 STAGES = ("permute", "real", "spread", "fft_x_fwd", "fft_y_fwd", "fft_z_scale", "fft_y_inv", "fft_x_inv", "gather")
-SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED = 0, 1, 2
+SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED, SE_PRECOND_SPECTRAL = 0, 1, 2, 3
 
 # every entry point declared in include/se_mobility.h
 ABI_SYMBOLS = ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",

@@ -113,6 +113,7 @@ static void free_grids(se_ctx *c)
 
 static void free_config(se_ctx *c)
 {
+    free_spectral(c);
     dfree_t(c->b.pos);
     dfree_t(c->b.rad);
     dfree_t(c->b.perm);
@@ -255,6 +256,7 @@ extern "C" int se_destroy(se_ctx *c)
     free_grids(c);
     free_config(c);
     dfree_t(c->b.mlp_w);
+    for (int q = 0; q < 2; ++q) dfree(c->ktab[q]);
     cudaEventDestroy(c->ev_fork);
     cudaEventDestroy(c->ev_join);
     for (cudaEvent_t e : c->tev) cudaEventDestroy(e);

@@ -111,6 +111,16 @@ struct se_ctx {
     int pc_ncomp = 0, pc_prec = -1, pc_kind = -1;
     bool have_mlp = false;
     int pc_fallbacks = 0;              // particles whose learned block fell back to the plain one
+    // spectral correction (SE_PRECOND_SPECTRAL): a coarse forces-only context whose
+    // k-space kernel is the radial table ktab (transverse modes, |k| <= ktab_kmax)
+    se_ctx *spc = nullptr;
+    double *sp_f = nullptr, *sp_u = nullptr;   // [N][3] FP64 force part of a vector / correction
+    double sp_theta = 0.8;
+    bool ktab_on = false;
+    void *ktab[2] = {};                 // [ktab_n] T: h(k) at k = i ktab_kmax / (ktab_n - 1)
+    int ktab_n = 0;
+    double ktab_kmax = 0;
+    double sp_fit[3] = {0, 0, 0};       // fitted lambda_T(k) = A / k^2 + l0, and lambda_B
     se::FftPlan plan{};
     se::Buffers b;
     size_t alloc_N = 0;
@@ -153,6 +163,8 @@ template <typename T>
 void launch_wave_spread(se_ctx *c, const T *xs, cudaStream_t s, int ncomp);
 template <typename T>
 void launch_wave_fft(se_ctx *c, cudaStream_t s);
+// releases the spectral-correction sub-context (se_solve.cu)
+void free_spectral(se_ctx *c);
 template <typename T, typename TO>
 void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int ncomp, int with_wave,
                            cudaStream_t s);

@@ -14,6 +14,7 @@
 // FP64; Krylov products run at the context's compute precision.  Each restart
 // starts from the FP64 true residual, which is the iterative-refinement step when
 // products are FP32.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -346,6 +347,227 @@ struct Gm {
     }
 };
 
+
+// ---------------------------------------------------------------- spectral correction
+//
+// SE_PRECOND_SPECTRAL = block preconditioner minus a correction of the long-wavelength
+// force modes.  For a transverse plane wave of the forces, f_j = e^{i k.r_j} u (u . k = 0),
+// M f is close to lambda(k) f with lambda(k) = A/k^2 + l0: the collective Stokes mobility
+// n/(eta k^2) of the suspension (A comes out near n/eta) plus a bulk term.  These modes
+// carry the largest eigenvalues of the preconditioned operator (cond(M) grows like L^2).
+// The correction C = sum over 0 < |k| <= k_c of (1/N) e^{i k.r_i} h(k) P_T(k) e^{-i k.r_j}
+// with h(k) = theta (lambda_B - 1/lambda(k))^+ maps such a mode to f / lambda(k) (times a
+// damping theta), lambda_B being the block preconditioner's value on the mode.  It is
+// evaluated as a forces-only wave-space product on a coarse grid whose k-space kernel
+// is the table h(|k|)/N.  A and l0 come from Rayleigh quotients of three probe shells
+// (one product each); k_c a = 0.9 stays below the structure peak of the suspension.
+
+__global__ void unpermute_pos_kernel(int N, const double *pos_cell, const int *perm, double *pos_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int j = perm[i];
+    for (int d = 0; d < 3; ++d) pos_out[3 * j + d] = pos_cell[3 * i + d];
+}
+
+__global__ void fill_kernel(int n, double v, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = v;
+}
+
+// z[i][0..2] = Re sum_m (ar_m + i ai_m) e^{i k_m . r_i}, other components 0
+__global__ void probe_kernel(int N, int ncomp, int nmode, const double *pos, const double *modes /*[nmode][9]*/,
+                             double *z)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double f[3] = {0, 0, 0};
+    for (int m = 0; m < nmode; ++m) {
+        const double *md = modes + 9 * m;
+        const double ph = md[0] * pos[3 * i] + md[1] * pos[3 * i + 1] + md[2] * pos[3 * i + 2];
+        const double cs = cos(ph), sn = sin(ph);
+        for (int d = 0; d < 3; ++d) f[d] += md[3 + d] * cs - md[6 + d] * sn;
+    }
+    for (int c = 0; c < ncomp; ++c) z[(size_t)i * ncomp + c] = c < 3 ? f[c] : 0.0;
+}
+
+__global__ void take_forces_kernel(int N, int ncomp, const double *v, double *f)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int d = 0; d < 3; ++d) f[3 * i + d] = v[(size_t)i * ncomp + d];
+}
+
+__global__ void sub_forces_kernel(int N, int ncomp, const double *u, double *z)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int d = 0; d < 3; ++d) z[(size_t)i * ncomp + d] -= u[3 * i + d];
+}
+
+void free_spectral(se_ctx *c)
+{
+    if (c->spc) se_destroy(c->spc);
+    c->spc = nullptr;
+    if (c->sp_f) cudaFree(c->sp_f);
+    if (c->sp_u) cudaFree(c->sp_u);
+    c->sp_f = c->sp_u = nullptr;
+}
+
+static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
+{
+    cudaStream_t s = c->stream;
+    const int N = (int)c->N;
+    free_spectral(c);
+    std::vector<double> rad(N);
+    SE_CUDA_CHECK(c, cudaMemcpy(rad.data(), c->b.rad, N * sizeof(double), cudaMemcpyDeviceToHost));
+    double asum = 0;
+    for (double a : rad) asum += a;
+    const double aref = asum / N, L = c->L, kc = 0.9 / aref, k1 = 2 * kPi / L;
+    if (kc <= 1.5 * k1) return SE_OK;                       // box too small: no long waves to correct
+    // coarse grid with Nyquist wave number >= 2.5 k_c
+    int Mc = 16;
+    const int sizes[] = {16, 24, 32, 48, 64, 72, 96, 128, 144, 192, 216, 256};
+    for (int q : sizes) { Mc = q; if (kPi * q / L >= 2.5 * kc) break; }
+    // probe shells: |n|^2 = 1, about (n_c/2)^2 and n_c^2 (n_c = k_c / k1)
+    const double nc = kc / k1;
+    const int targets[3] = {1, std::max(2, (int)std::lround(0.25 * nc * nc)), std::max(3, (int)std::floor(nc * nc))};
+    double lamT[3], lamB[3], kk[3];
+    double *modes_d = nullptr;
+    SE_CUDA_CHECK(c, cudaMalloc(&modes_d, 9 * 64 * sizeof(double)));
+    unsigned long long rng = 0x9e3779b97f4a7c15ull;
+    auto urand = [&]() { rng ^= rng << 13; rng ^= rng >> 7; rng ^= rng << 17; return (double)(rng >> 11) / 9007199254740992.0; };
+    auto gauss = [&]() { const double u1 = std::max(urand(), 1e-300), u2 = urand(); return std::sqrt(-2 * std::log(u1)) * std::cos(2 * kPi * u2); };
+    double *posc = nullptr;
+    SE_CUDA_CHECK(c, cudaMalloc(&posc, 3 * (size_t)N * sizeof(double)));
+    unpermute_pos_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, c->b.pos, c->b.perm, posc);
+    int rc = SE_OK;
+    for (int t = 0; t < 3 && rc == SE_OK; ++t) {
+        // modes with |n|^2 = target (nearest populated shell above it), at most 64
+        std::vector<double> md;
+        int r2 = targets[t];
+        for (; md.empty() && r2 < targets[t] + 64; ++r2) {
+            const int R = (int)std::ceil(std::sqrt((double)r2));
+            for (int a = -R; a <= R && md.size() < 9 * 64; ++a)
+                for (int b2 = -R; b2 <= R && md.size() < 9 * 64; ++b2)
+                    for (int cc = -R; cc <= R && md.size() < 9 * 64; ++cc) {
+                        if (a * a + b2 * b2 + cc * cc != r2) continue;
+                        const double kv[3] = {k1 * a, k1 * b2, k1 * cc};
+                        const double kn = std::sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
+                        double ar[3], ai[3];
+                        for (int d = 0; d < 3; ++d) { ar[d] = gauss(); ai[d] = gauss(); }
+                        double pr = 0, pi_ = 0;
+                        for (int d = 0; d < 3; ++d) { pr += ar[d] * kv[d] / kn; pi_ += ai[d] * kv[d] / kn; }
+                        for (int d = 0; d < 3; ++d) { ar[d] -= pr * kv[d] / kn; ai[d] -= pi_ * kv[d] / kn; }
+                        md.insert(md.end(), {kv[0], kv[1], kv[2], ar[0], ar[1], ar[2], ai[0], ai[1], ai[2]});
+                    }
+        }
+        kk[t] = k1 * std::sqrt((double)(r2 - 1));
+        const int nm = (int)(md.size() / 9);
+        cudaMemcpyAsync(modes_d, md.data(), md.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+        probe_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, nm, posc, modes_d, z);
+        c->launches++;
+        rc = se_apply_internal(c, ncomp, z, w, SE_F64, c->precision);
+        if (rc != SE_OK) break;
+        double zz, zMz, zBz;
+        if ((rc = gm.dots(z, 0, 1, z, &zz)) != SE_OK) break;
+        if ((rc = gm.dots(z, 0, 1, w, &zMz)) != SE_OK) break;
+        block_apply_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->b.pc_inv, z, w);
+        c->launches++;
+        if ((rc = gm.dots(z, 0, 1, w, &zBz)) != SE_OK) break;
+        lamT[t] = zMz / zz;
+        lamB[t] = zBz / zz;
+    }
+    cudaFree(modes_d);
+    if (rc != SE_OK) { cudaFree(posc); return rc; }
+    // least squares lambda = A / k^2 + l0 over the three shells
+    double sxx = 0, sx = 0, sy = 0, sxy = 0;
+    for (int t = 0; t < 3; ++t) {
+        const double xk = 1.0 / (kk[t] * kk[t]);
+        sxx += xk * xk; sx += xk; sy += lamT[t]; sxy += xk * lamT[t];
+    }
+    const double A = (3 * sxy - sx * sy) / (3 * sxx - sx * sx), l0 = (sy - A * sx) / 3;
+    const double lB = (lamB[0] + lamB[1] + lamB[2]) / 3;
+    c->sp_fit[0] = A;
+    c->sp_fit[1] = l0;
+    c->sp_fit[2] = lB;
+    // table h(k)/N on [0, k_c]
+    const int ntab = 512;
+    std::vector<float> tab(ntab);
+    for (int i = 0; i < ntab; ++i) {
+        const double k = kc * i / (ntab - 1);
+        double h = 0;
+        if (i > 0) {
+            const double lam = A / (k * k) + l0;
+            if (lam > 1.0 / lB) h = c->sp_theta * (lB - 1.0 / lam);
+        } else {
+            h = c->sp_theta * lB;
+        }
+        tab[i] = (float)(h / N);
+    }
+    // coarse forces-only context with a tabulated kernel (wave part only, point forces)
+    se_ctx *sc = nullptr;
+    rc = se_create(&sc, c->device, (void *)s);
+    if (rc != SE_OK) { cudaFree(posc); c->err = "spectral preconditioner: se_create failed"; return rc; }
+    c->spc = sc;
+    const int Pc = 8;
+    if (rc == SE_OK) rc = se_set_params(sc, 1.0, Mc, Pc, std::min(0.25 * L, 1.0));
+    if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_PRECISION, 0);
+    if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_SIZE_MODE, 1);
+    if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_PARTS, 2);
+    double *rtiny = nullptr;
+    if (rc == SE_OK && cudaMalloc(&rtiny, (size_t)N * sizeof(double)) != cudaSuccess) rc = SE_ERR_NOMEM;
+    if (rc == SE_OK) {
+        fill_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, 1e-6 * aref, rtiny);
+        rc = se_set_config(sc, N, L, posc, rtiny);
+    }
+    if (rtiny) cudaFree(rtiny);
+    cudaFree(posc);
+    if (rc == SE_OK) {
+        if (cudaMalloc(&sc->ktab[0], ntab * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&c->sp_f, 3 * (size_t)N * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&c->sp_u, 3 * (size_t)N * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            rc = SE_ERR_NOMEM;
+        }
+    }
+    if (rc == SE_OK) {
+        cudaMemcpyAsync(sc->ktab[0], tab.data(), ntab * sizeof(float), cudaMemcpyHostToDevice, s);
+        sc->ktab_n = ntab;
+        sc->ktab_kmax = kc;
+        sc->ktab_on = true;
+        SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
+    }
+    if (rc != SE_OK) {
+        if (c->err.empty()) c->err = std::string("spectral preconditioner: ") + se_last_error(sc);
+        free_spectral(c);
+    }
+    return rc;
+}
+
+// z = P^-1 v for the spectral preconditioner: block part, then minus the correction
+static int spectral_apply(se_ctx *c, int ncomp, const double *v, double *z)
+{
+    cudaStream_t s = c->stream;
+    const int N = (int)c->N;
+    block_apply_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->b.pc_inv, v, z);
+    c->launches++;
+    if (!c->spc) return SE_OK;
+    take_forces_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, v, c->sp_f);
+    c->launches++;
+    const int rc = se_apply_internal(c->spc, 3, c->sp_f, c->sp_u, SE_F64, 0);
+    if (rc != SE_OK) {
+        c->err = std::string("spectral preconditioner: ") + c->spc->err;
+        return rc;
+    }
+    c->launches += c->spc->launches;
+    c->spc->launches = 0;
+    sub_forces_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->sp_u, z);
+    c->launches++;
+    return SE_OK;
+}
+
 }  // namespace se
 
 using namespace se;
@@ -361,7 +583,7 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
     if (ncomp != 3 && ncomp != 6 && ncomp != 11 && ncomp != 12) { c->err = "ncomp must be 3, 6, 11 or 12"; return SE_ERR_ARG; }
     if (dtype != SE_F32 && dtype != SE_F64) { c->err = "bad dtype"; return SE_ERR_ARG; }
     if (!(rtol > 0) || maxit < 1) { c->err = "rtol must be > 0 and maxit >= 1"; return SE_ERR_ARG; }
-    if (precond < SE_PRECOND_NONE || precond > SE_PRECOND_LEARNED) { c->err = "bad preconditioner"; return SE_ERR_ARG; }
+    if (precond < SE_PRECOND_NONE || precond > SE_PRECOND_SPECTRAL) { c->err = "bad preconditioner"; return SE_ERR_ARG; }
     if (!c->have_config) { c->err = "se_set_config must be called first"; return SE_ERR_STATE; }
     cudaSetDevice(c->device);
     cudaStream_t s = c->stream;
@@ -398,14 +620,22 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
     if (precond != SE_PRECOND_NONE && (!c->pc_ready || c->pc_ncomp != ncomp || c->pc_kind != kind)) {
         int rc = build_precond(c, ncomp, kind == SE_PRECOND_LEARNED);
         if (rc != SE_OK) return rc;
+        free_spectral(c);
     }
-    auto Pinv = [&](const double *v, double *out) {
+    if (precond == SE_PRECOND_SPECTRAL && !c->spc) {
+        int rc = build_spectral(c, ncomp, gm, z, w);
+        if (rc != SE_OK) return rc;
+    }
+    auto Pinv = [&](const double *v, double *out) -> int {
         if (precond == SE_PRECOND_NONE) {
-            cudaMemcpyAsync(out, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+            SE_CUDA_CHECK(c, cudaMemcpyAsync(out, v, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        } else if (precond == SE_PRECOND_SPECTRAL) {
+            return spectral_apply(c, ncomp, v, out);
         } else {
             block_apply_kernel<<<((int)c->N + 127) / 128, 128, 0, s>>>((int)c->N, ncomp, c->b.pc_inv, v, out);
             c->launches++;
         }
+        return SE_OK;
     };
 
     double bn2, xn2;
@@ -456,7 +686,7 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
             g[0] = beta;
             int k = 0;
             for (int j = 0; j < m && prods < maxit; ++j) {
-                Pinv(V + (size_t)j * n, z);
+                if ((rc = Pinv(V + (size_t)j * n, z)) != SE_OK) return rc;
                 rc = se_apply_internal(c, ncomp, z, w, SE_F64, c->precision);
                 if (rc != SE_OK) return rc;
                 ++prods;
@@ -500,7 +730,7 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
             SE_CUDA_CHECK(c, cudaMemcpyAsync(yd, yv.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
             combine_kernel<<<grid_for(n), 256, 0, s>>>(V, n, n, k, yd, w);
             c->launches++;
-            Pinv(w, z);
+            if ((rc = Pinv(w, z)) != SE_OK) return rc;
             axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, xd, 1.0, z, xd);
             c->launches++;
         }

@@ -471,6 +471,79 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, cons
     }
 }
 
+// z pass with a tabulated radial kernel in place of the Ewald one (the coarse spectral
+// correction of SE_PRECOND_SPECTRAL): forward z transform of the force spectra, the
+// transverse projection times h(|k|) for |k| <= kmax (zero beyond), the window
+// compensation exp(2 pi^2 q^2/(alpha M^2)) (alpha/pi)^3 of the spread and gather
+// Gaussians, inverse z transform.  The source and pressure outputs are zero.
+template <typename T, int LB>
+__global__ void __launch_bounds__(kFftThreads, 4) fft_z_table(FftPlan plan, const typename C2<T>::t *twg,
+                                                              const typename C2<T>::t *specf,
+                                                              typename C2<T>::t *speco, const T *tab, int ntab,
+                                                              T kmax, T cnorm, T twopiL, T ecoef)
+{
+    using T2 = typename C2<T>::t;
+    constexpr int NLI = 4 * LB, CO = 4, NLO = LB * CO, CPE = sizeof(T) == 4 ? 2 : 1;
+    const int M = plan.M, Mh = M / 2 + 1;
+    T2 *tw, *A, *B;
+    fft_smem(M, NLO, tw, A, B);
+    for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
+    const int y = blockIdx.y;
+    const int q0 = blockIdx.x * LB, nq = min(LB, Mh - q0);
+    const size_t zs = (size_t)M * Mh;
+    for (int e = threadIdx.x; e < (NLI / CPE) * M; e += blockDim.x) {
+        const int k = e % (NLI / CPE), z = e / (NLI / CPE);
+        T2 *d = A + z * NLI + k * CPE;
+        if (k * CPE < nq * 4) cp_async16(d, specf + ((size_t)z * zs + (size_t)y * Mh + q0) * 4 + k * CPE);
+        else
+            for (int u = 0; u < CPE; ++u) d[u] = T2{0, 0};
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    T2 *X = fft_run_dir<NLI, false>(A, B, plan, tw);
+    T2 *Y = X == A ? B : A;
+    const int ys = y <= M / 2 ? y : y - M;
+    const T dk = kmax / (T)(ntab - 1);
+    for (int e = threadIdx.x; e < LB * M; e += blockDim.x) {
+        const int q = e % LB, z = e / LB;
+        const int qx = q0 + q, zsn = z <= M / 2 ? z : z - M;
+        T2 o[CO];
+#pragma unroll
+        for (int c = 0; c < CO; ++c) o[c] = T2{0, 0};
+        const T kx = twopiL * qx, ky = twopiL * ys, kz = twopiL * zsn;
+        const T k2 = kx * kx + ky * ky + kz * kz;
+        const bool zero = q >= nq || (qx == 0 && ys == 0 && zsn == 0) || 2 * qx == M || 2 * ys == M ||
+                          2 * zsn == M || k2 > kmax * kmax;
+        if (!zero) {
+            const T kk = sqrt(k2), u = kk / dk;
+            const int i0 = min((int)u, ntab - 2);
+            const T f = u - (T)i0;
+            const T hk = tab[i0] + f * (tab[i0 + 1] - tab[i0]);
+            const T q2 = (T)(qx * qx + ys * ys + zsn * zsn);
+            T E;
+            if constexpr (sizeof(T) == 4) E = expf(ecoef * q2) * cnorm * hk;
+            else E = exp(ecoef * q2) * cnorm * hk;
+            const T ik2 = 1 / k2;
+            const T2 *hh = X + z * NLI + q * 4;
+            const T2 H0 = hh[0], H1 = hh[1], H2 = hh[2];
+            const T2 kH = T2{kx * H0.x + ky * H1.x + kz * H2.x, kx * H0.y + ky * H1.y + kz * H2.y};
+            const T2 pr = T2{kH.x * ik2, kH.y * ik2};
+            o[0] = T2{E * (H0.x - kx * pr.x), E * (H0.y - kx * pr.y)};
+            o[1] = T2{E * (H1.x - ky * pr.x), E * (H1.y - ky * pr.y)};
+            o[2] = T2{E * (H2.x - kz * pr.x), E * (H2.y - kz * pr.y)};
+        }
+        T2 *wv = Y + z * NLO + q * CO;
+#pragma unroll
+        for (int c = 0; c < CO; ++c) wv[c] = o[c];
+    }
+    __syncthreads();
+    const T2 *Z = fft_run_dir<NLO, true>(Y, X, plan, tw);
+    for (int e = threadIdx.x; e < NLO * M; e += blockDim.x) {
+        const int l = e % NLO, z = e / NLO;
+        if (l < nq * CO) speco[((size_t)z * zs + (size_t)y * Mh + q0) * CO + l] = Z[z * NLO + l];
+    }
+}
+
 // x pass, inverse: pairs of half spectra are recombined into full complex lines
 // Z = A + i B (A(M-q) = conj A(q) for real output), transformed, and written as the
 // real grids A, B interleaved per point.
@@ -1079,7 +1152,16 @@ void launch_wave_fft(se_ctx *c, cudaStream_t s)
 
     const T cnorm = (T)(pow(p.alpha / kPi, 3.0) / (p.eta * p.L * p.L * p.L));
     stage_mark(c, SE_STAGE_FFT_Z, s, false);
-    if (CO == 8) launch_z_fit<T, 8>(c, p, tw, sf, so, cnorm, s);
+    if (c->ktab_on && CO == 4) {
+        constexpr int LB = fft_nl<T>() / 4;
+        const int Mh = M / 2 + 1;
+        const size_t zsm = fft_smem_bytes<T2>(M, 4 * LB);
+        const T twopiL = (T)(2.0 * kPi / p.L), ecoef = (T)(2.0 * kPi * kPi / (p.alpha * (double)M * M));
+        const T cn = (T)pow(p.alpha / kPi, 3.0);
+        cudaFuncSetAttribute(fft_z_table<T, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm);
+        fft_z_table<T, LB><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, zsm, s>>>(
+            c->plan, tw, sf, so, (const T *)c->ktab[pix<T>()], c->ktab_n, (T)c->ktab_kmax, cn, twopiL, ecoef);
+    } else if (CO == 8) launch_z_fit<T, 8>(c, p, tw, sf, so, cnorm, s);
     else launch_z_fit<T, 4>(c, p, tw, sf, so, cnorm, s);
     c->launches++;
     stage_mark(c, SE_STAGE_FFT_Z, s, true);
