@@ -355,6 +355,16 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         if (value != 0 && value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "overlap must be 0, 1 or 2");
         c->overlap = (int)value;
         return SE_OK;
+    case SE_OPT_PC_THETA:
+        if (!(value > 0 && value <= 1)) return set_error(c, SE_ERR_ARG, "theta must be in (0, 1]");
+        if (value != c->sp_theta) free_spectral(c);
+        c->sp_theta = value;
+        return SE_OK;
+    case SE_OPT_PC_KA:
+        if (!(value > 0 && value <= 3)) return set_error(c, SE_ERR_ARG, "k_c a must be in (0, 3]");
+        if (value != c->sp_ka) free_spectral(c);
+        c->sp_ka = value;
+        return SE_OK;
     case SE_OPT_GATHER:
         if (value != 0 && value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "gather must be 0, 1 or 2");
         c->gather = (int)value;

@@ -115,12 +115,14 @@ struct se_ctx {
     // k-space kernel is the radial table ktab (transverse modes, |k| <= ktab_kmax)
     se_ctx *spc = nullptr;
     double *sp_f = nullptr, *sp_u = nullptr;   // [N][3] FP64 force part of a vector / correction
-    double sp_theta = 0.8;
+    double *sp_s = nullptr;             // [N] sqrt of the block preconditioner's force diagonal
+    double sp_theta = 0.9, sp_ka = 0.9;
     bool ktab_on = false;
     void *ktab[2] = {};                 // [ktab_n] T: h(k) at k = i ktab_kmax / (ktab_n - 1)
     int ktab_n = 0;
     double ktab_kmax = 0;
     double sp_fit[3] = {0, 0, 0};       // fitted lambda_T(k) = A / k^2 + l0, and lambda_B
+    double sp_rho = 0;                  // largest eigenvalue of the correction before capping
     se::FftPlan plan{};
     se::Buffers b;
     size_t alloc_N = 0;

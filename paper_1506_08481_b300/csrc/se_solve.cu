@@ -355,12 +355,14 @@ struct Gm {
 // M f is close to lambda(k) f with lambda(k) = A/k^2 + l0: the collective Stokes mobility
 // n/(eta k^2) of the suspension (A comes out near n/eta) plus a bulk term.  These modes
 // carry the largest eigenvalues of the preconditioned operator (cond(M) grows like L^2).
-// The correction C = sum over 0 < |k| <= k_c of (1/N) e^{i k.r_i} h(k) P_T(k) e^{-i k.r_j}
-// with h(k) = theta (lambda_B - 1/lambda(k))^+ maps such a mode to f / lambda(k) (times a
-// damping theta), lambda_B being the block preconditioner's value on the mode.  It is
-// evaluated as a forces-only wave-space product on a coarse grid whose k-space kernel
-// is the table h(|k|)/N.  A and l0 come from Rayleigh quotients of three probe shells
-// (one product each); k_c a = 0.9 stays below the structure peak of the suspension.
+// With S = diag(s_i), s_i^2 the force diagonal of particle i's block, the preconditioner
+// is P^-1 = B - S C S on the force components, C = sum over 0 < |k| <= k_c of
+// (1/N) e^{i k.r_i} h(k) P_T(k) e^{-i k.r_j}, h(k) = theta (1 - 1/lambda(k))^+, lambda(k)
+// the Rayleigh quotient of S M S on the mode: the scaled mode goes to (1 - theta) lambda
+// + theta times itself, and P^-1 stays positive definite for any size mix (h < 1).
+// The cutoff k_c is where the fitted lambda falls to 1.2, so h decays to zero there.  C is a forces-only wave-space product on a coarse grid whose k-space kernel
+// is the table h(|k|)/N; A and l0 come from three probe shells (one product each);
+// k_c a = 0.9 stays below the structure peak of the suspension.
 
 __global__ void unpermute_pos_kernel(int N, const double *pos_cell, const int *perm, double *pos_out)
 {
@@ -392,18 +394,48 @@ __global__ void probe_kernel(int N, int ncomp, int nmode, const double *pos, con
     for (int c = 0; c < ncomp; ++c) z[(size_t)i * ncomp + c] = c < 3 ? f[c] : 0.0;
 }
 
-__global__ void take_forces_kernel(int N, int ncomp, const double *v, double *f)
+// s_i = sqrt of the mean force diagonal of particle i's preconditioner block
+__global__ void force_scale_kernel(int N, int ncomp, const double *Binv, double *s)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    for (int d = 0; d < 3; ++d) f[3 * i + d] = v[(size_t)i * ncomp + d];
+    const double *B = Binv + (size_t)i * ncomp * ncomp;
+    const double d = (B[0] + B[ncomp + 1] + B[2 * ncomp + 2]) / 3.0;
+    s[i] = sqrt(d > 0 ? d : 0.0);
 }
 
-__global__ void sub_forces_kernel(int N, int ncomp, const double *u, double *z)
+// f = s v_F (the force components of v, scaled)
+__global__ void take_forces_kernel(int N, int ncomp, const double *s, const double *v, double *f)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    for (int d = 0; d < 3; ++d) z[(size_t)i * ncomp + d] -= u[3 * i + d];
+    for (int d = 0; d < 3; ++d) f[3 * i + d] = s[i] * v[(size_t)i * ncomp + d];
+}
+
+// z_F -= s u
+__global__ void sub_forces_kernel(int N, int ncomp, const double *s, const double *u, double *z)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int d = 0; d < 3; ++d) z[(size_t)i * ncomp + d] -= s[i] * u[3 * i + d];
+}
+
+// v[i] = uniform(-1, 1) from a counter hash (start vector of the power iteration)
+__global__ void hash_fill_kernel(size_t n, unsigned seed, double *v)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long x = (unsigned long long)i * 0x9E3779B97F4A7C15ull + seed;
+    x ^= x >> 33; x *= 0xFF51AFD7ED558CCDull; x ^= x >> 33; x *= 0xC4CEB9FE1A85EC53ull; x ^= x >> 33;
+    v[i] = (double)(x >> 11) / 4503599627370496.0 - 1.0;
+}
+
+// z_F *= s (in place)
+__global__ void scale_forces_kernel(int N, int ncomp, const double *s, double *z)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int d = 0; d < 3; ++d) z[(size_t)i * ncomp + d] *= s[i];
 }
 
 void free_spectral(se_ctx *c)
@@ -412,8 +444,12 @@ void free_spectral(se_ctx *c)
     c->spc = nullptr;
     if (c->sp_f) cudaFree(c->sp_f);
     if (c->sp_u) cudaFree(c->sp_u);
-    c->sp_f = c->sp_u = nullptr;
+    if (c->sp_s) cudaFree(c->sp_s);
+    c->sp_f = c->sp_u = c->sp_s = nullptr;
 }
+
+// largest eigenvalue allowed for the correction C
+constexpr double kCMax = 0.97;
 
 static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
 {
@@ -424,7 +460,8 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
     SE_CUDA_CHECK(c, cudaMemcpy(rad.data(), c->b.rad, N * sizeof(double), cudaMemcpyDeviceToHost));
     double asum = 0;
     for (double a : rad) asum += a;
-    const double aref = asum / N, L = c->L, kc = 0.9 / aref, k1 = 2 * kPi / L;
+    const double aref = asum / N, L = c->L, k1 = 2 * kPi / L;
+    double kc = c->sp_ka / aref;
     if (kc <= 1.5 * k1) return SE_OK;                       // box too small: no long waves to correct
     // coarse grid with Nyquist wave number >= 2.5 k_c
     int Mc = 16;
@@ -441,7 +478,9 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
     auto gauss = [&]() { const double u1 = std::max(urand(), 1e-300), u2 = urand(); return std::sqrt(-2 * std::log(u1)) * std::cos(2 * kPi * u2); };
     double *posc = nullptr;
     SE_CUDA_CHECK(c, cudaMalloc(&posc, 3 * (size_t)N * sizeof(double)));
+    SE_CUDA_CHECK(c, cudaMalloc(&c->sp_s, (size_t)N * sizeof(double)));
     unpermute_pos_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, c->b.pos, c->b.perm, posc);
+    force_scale_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->b.pc_inv, c->sp_s);
     int rc = SE_OK;
     for (int t = 0; t < 3 && rc == SE_OK; ++t) {
         // modes with |n|^2 = target (nearest populated shell above it), at most 64
@@ -468,16 +507,16 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
         cudaMemcpyAsync(modes_d, md.data(), md.size() * sizeof(double), cudaMemcpyHostToDevice, s);
         probe_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, nm, posc, modes_d, z);
         c->launches++;
+        double zz, zMz;
+        if ((rc = gm.dots(z, 0, 1, z, &zz)) != SE_OK) break;
+        // Rayleigh quotient of S M S on the plane-wave combination
+        scale_forces_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->sp_s, z);
+        c->launches++;
         rc = se_apply_internal(c, ncomp, z, w, SE_F64, c->precision);
         if (rc != SE_OK) break;
-        double zz, zMz, zBz;
-        if ((rc = gm.dots(z, 0, 1, z, &zz)) != SE_OK) break;
         if ((rc = gm.dots(z, 0, 1, w, &zMz)) != SE_OK) break;
-        block_apply_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->b.pc_inv, z, w);
-        c->launches++;
-        if ((rc = gm.dots(z, 0, 1, w, &zBz)) != SE_OK) break;
         lamT[t] = zMz / zz;
-        lamB[t] = zBz / zz;
+        lamB[t] = 1.0;
     }
     cudaFree(modes_d);
     if (rc != SE_OK) { cudaFree(posc); return rc; }
@@ -489,6 +528,12 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
     }
     const double A = (3 * sxy - sx * sy) / (3 * sxx - sx * sx), l0 = (sy - A * sx) / 3;
     const double lB = (lamB[0] + lamB[1] + lamB[2]) / 3;
+    if (A > 0 && 1.2 * lB - l0 > 0) kc = std::min(2.0 / aref, std::max(kc, std::sqrt(A / (1.2 * lB - l0))));
+    {
+        int q = 16;
+        for (int s2 : sizes) { q = s2; if (kPi * s2 / L >= 2.5 * kc) break; }
+        Mc = q;
+    }
     c->sp_fit[0] = A;
     c->sp_fit[1] = l0;
     c->sp_fit[2] = lB;
@@ -497,13 +542,11 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
     std::vector<float> tab(ntab);
     for (int i = 0; i < ntab; ++i) {
         const double k = kc * i / (ntab - 1);
+        // h = theta (1 - 1/lambda): a mode with the fitted lambda goes to
+        // (1 - theta) lambda + theta; zero where the fit reaches 1 (at k_c, see above)
         double h = 0;
-        if (i > 0) {
-            const double lam = A / (k * k) + l0;
-            if (lam > 1.0 / lB) h = c->sp_theta * (lB - 1.0 / lam);
-        } else {
-            h = c->sp_theta * lB;
-        }
+        const double lam = i > 0 ? A / (k * k) + l0 : 1e300;
+        if (lam > lB) h = c->sp_theta * (1.0 - lB / lam);
         tab[i] = (float)(h / N);
     }
     // coarse forces-only context with a tabulated kernel (wave part only, point forces)
@@ -537,6 +580,32 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
         sc->ktab_n = ntab;
         sc->ktab_kmax = kc;
         sc->ktab_on = true;
+        // On particle positions the plane waves are only nearly orthogonal, so |C| can
+        // exceed max h.  Power iteration on C (symmetric, positive semi-definite): if its
+        // largest eigenvalue passes kCMax the table is scaled down to kCMax, which keeps
+        // I - C, and P^-1, positive definite.
+        const size_t n3 = 3 * (size_t)N;
+        Gm g3{c, n3, gm.part, gm.hd};
+        hash_fill_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(n3, 12345u, c->sp_f);
+        double rho = 0;
+        for (int it = 0; it < 12 && rc == SE_OK; ++it) {
+            rc = se_apply_internal(sc, 3, c->sp_f, c->sp_u, SE_F64, 0);
+            double ff = 0, fu = 0, uu = 0;
+            if (rc == SE_OK) rc = g3.dots(c->sp_f, 0, 1, c->sp_f, &ff);
+            if (rc == SE_OK) rc = g3.dots(c->sp_f, 0, 1, c->sp_u, &fu);
+            if (rc == SE_OK) rc = g3.dots(c->sp_u, 0, 1, c->sp_u, &uu);
+            if (rc != SE_OK || !(uu > 0)) break;
+            rho = fu / ff;
+            axpby_kernel<<<grid_for(n3), 256, 0, s>>>(n3, 1.0 / std::sqrt(uu), c->sp_u, 0.0, c->sp_u, c->sp_f);
+            c->launches++;
+        }
+        c->sp_rho = rho;
+        if (rc == SE_OK && rho > kCMax) {
+            for (float &v : tab) v = (float)(v * (kCMax / rho));
+            cudaMemcpyAsync(sc->ktab[0], tab.data(), ntab * sizeof(float), cudaMemcpyHostToDevice, s);
+        }
+        c->launches += sc->launches;
+        sc->launches = 0;
         SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
     }
     if (rc != SE_OK) {
@@ -554,7 +623,7 @@ static int spectral_apply(se_ctx *c, int ncomp, const double *v, double *z)
     block_apply_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->b.pc_inv, v, z);
     c->launches++;
     if (!c->spc) return SE_OK;
-    take_forces_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, v, c->sp_f);
+    take_forces_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->sp_s, v, c->sp_f);
     c->launches++;
     const int rc = se_apply_internal(c->spc, 3, c->sp_f, c->sp_u, SE_F64, 0);
     if (rc != SE_OK) {
@@ -563,7 +632,7 @@ static int spectral_apply(se_ctx *c, int ncomp, const double *v, double *z)
     }
     c->launches += c->spc->launches;
     c->spc->launches = 0;
-    sub_forces_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->sp_u, z);
+    sub_forces_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->sp_s, c->sp_u, z);
     c->launches++;
     return SE_OK;
 }

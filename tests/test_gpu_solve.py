@@ -139,9 +139,9 @@ def test_single_sphere_block_is_the_exact_inverse():
 
 def test_lognormal_n20000_solve_rows_vs_oracle(oracle_mod):
     """Polydisperse solve at N = 20000, phi = 0.4, log-normal radii: GMRES to 1e-6 with
-    the plain and the learned block preconditioner (trained weights if the package has
-    them), FP32 products; the oracle product of each solution at 8 random rows gives
-    back the right-hand side."""
+    the plain, the learned (trained weights if the package has them) and the spectral
+    preconditioner, FP32 products; the oracle product of each solution at 8 random rows
+    gives back the right-hand side."""
     import os
     cfg = inputs.lognormal(seed=3, n=20000, phi=0.4)
     ctx = solve_ctx(cfg, 1e-8, precision=0, M_max=128, restart=100, fp32_tol=1e-5)
@@ -153,7 +153,8 @@ def test_lognormal_n20000_solve_rows_vs_oracle(oracle_mod):
         ctx.set_learned_weights(np.load(weights))
     rows = rng.choice(cfg.N, 8, replace=False)
     its = {}
-    for name, pc in (("block", api.SE_PRECOND_BLOCK), ("learned", api.SE_PRECOND_LEARNED)):
+    for name, pc in (("block", api.SE_PRECOND_BLOCK), ("learned", api.SE_PRECOND_LEARNED),
+                     ("spectral", api.SE_PRECOND_SPECTRAL)):
         x, iters, relres = ctx.solve(bt, rtol=1e-6, maxit=1500, precond=pc)
         assert relres <= 1e-6, name
         x12 = np.zeros((cfg.N, 12))
@@ -161,7 +162,8 @@ def test_lognormal_n20000_solve_rows_vs_oracle(oracle_mod):
         y = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x12, rows=rows, tol=1e-10)[:, :11]
         assert rel(y, b[rows]) <= 5e-6, name
         its[name] = iters
-    print("N=20000 products block/learned:", its)
+    print("N=20000 products block/learned/spectral:", its)
+    assert its["spectral"] < its["block"]
 
 
 def test_spectral_preconditioner_cuts_products():
