@@ -356,7 +356,7 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         c->overlap = (int)value;
         return SE_OK;
     case SE_OPT_PC_THETA:
-        if (!(value > 0 && value <= 1)) return set_error(c, SE_ERR_ARG, "theta must be in (0, 1]");
+        if (!(value >= 0 && value <= 1)) return set_error(c, SE_ERR_ARG, "theta must be in [0, 1]");
         if (value != c->sp_theta) free_spectral(c);
         c->sp_theta = value;
         return SE_OK;

@@ -73,7 +73,7 @@ struct Buffers {
     // solver
     double *pc_inv = nullptr;    // [N][nc][nc] inverse preconditioner blocks (caller order)
     float *mlp_w = nullptr;      // learned correction network (packed parameters)
-    double *kry = nullptr;       // Krylov basis [restart + 1][n]
+    double *kry = nullptr;       // Krylov basis [restart + 1][n] and preconditioned vectors [restart][n]
     double *work64 = nullptr;    // FP64 work vectors [5][n]
     double *red = nullptr;       // reduction scratch
 };
@@ -116,7 +116,7 @@ struct se_ctx {
     se_ctx *spc = nullptr;
     double *sp_f = nullptr, *sp_u = nullptr;   // [N][3] FP64 force part of a vector / correction
     double *sp_s = nullptr;             // [N] sqrt of the block preconditioner's force diagonal
-    double sp_theta = 0.9, sp_ka = 0.9;
+    double sp_theta = 0, sp_ka = 0.9;    // theta 0: 0.98 (monodisperse) or 0.9
     bool ktab_on = false;
     void *ktab[2] = {};                 // [ktab_n] T: h(k) at k = i ktab_kmax / (ktab_n - 1)
     int ktab_n = 0;

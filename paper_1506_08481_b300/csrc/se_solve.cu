@@ -1,5 +1,6 @@
-// se_solve: M_inf . x = b by right-preconditioned restarted GMRES (Sec. 4.1) with
-// the block-diagonal far-field preconditioner of Sec. 4.2.
+// se_solve: M_inf . x = b by right-preconditioned restarted flexible GMRES (Sec. 4.1;
+// the preconditioned vectors are stored, so a preconditioner evaluated in FP32 need
+// not be exactly linear) with the block-diagonal far-field preconditioner of Sec. 4.2.
 //
 // Far-field-only reading of Sec. 4.2: with no lubrication (R^nf = 0) the
 // preconditioner is the inverse of the block diagonal of M_inf, each block being
@@ -458,8 +459,10 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
     free_spectral(c);
     std::vector<double> rad(N);
     SE_CUDA_CHECK(c, cudaMemcpy(rad.data(), c->b.rad, N * sizeof(double), cudaMemcpyDeviceToHost));
-    double asum = 0;
-    for (double a : rad) asum += a;
+    double asum = 0, amin = rad[0], amax = rad[0];
+    for (double a : rad) { asum += a; amin = std::min(amin, a); amax = std::max(amax, a); }
+    // damping: measured robust at 0.98 on monodisperse suspensions, 0.9 with size spread
+    const double theta = c->sp_theta > 0 ? c->sp_theta : (amax - amin <= 0.01 * amax ? 0.98 : 0.9);
     const double aref = asum / N, L = c->L, k1 = 2 * kPi / L;
     double kc = c->sp_ka / aref;
     if (kc <= 1.5 * k1) return SE_OK;                       // box too small: no long waves to correct
@@ -546,7 +549,7 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
         // (1 - theta) lambda + theta; zero where the fit reaches 1 (at k_c, see above)
         double h = 0;
         const double lam = i > 0 ? A / (k * k) + l0 : 1e300;
-        if (lam > lB) h = c->sp_theta * (1.0 - lB / lam);
+        if (lam > lB) h = theta * (1.0 - lB / lam);
         tab[i] = (float)(h / N);
     }
     // coarse forces-only context with a tabulated kernel (wave part only, point forces)
@@ -664,14 +667,15 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
     if (c->b.work64) cudaFree(c->b.work64);
     if (c->b.red) cudaFree(c->b.red);
     c->b.kry = c->b.work64 = c->b.red = nullptr;
-    if (cudaMalloc(&c->b.kry, (size_t)(m + 1) * n * sizeof(double)) != cudaSuccess ||
+    // flexible GMRES: Krylov basis V [m + 1][n] and the preconditioned vectors Z [m][n]
+    if (cudaMalloc(&c->b.kry, (size_t)(2 * m + 1) * n * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->b.work64, 5 * n * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->b.red, ((size_t)kRedBlocks * (m + 1) + 2 * (m + 1)) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         c->err = "solver allocation failed";
         return SE_ERR_NOMEM;
     }
-    double *V = c->b.kry;
+    double *V = c->b.kry, *Zb = c->b.kry + (size_t)(m + 1) * n;
     double *bd = c->b.work64, *xd = bd + n, *r = xd + n, *w = r + n, *z = w + n;
     Gm gm{c, n, c->b.red, c->b.red + (size_t)kRedBlocks * (m + 1)};
     double *yd = gm.hd + (m + 1);
@@ -755,8 +759,9 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
             g[0] = beta;
             int k = 0;
             for (int j = 0; j < m && prods < maxit; ++j) {
-                if ((rc = Pinv(V + (size_t)j * n, z)) != SE_OK) return rc;
-                rc = se_apply_internal(c, ncomp, z, w, SE_F64, c->precision);
+                double *zj = Zb + (size_t)j * n;
+                if ((rc = Pinv(V + (size_t)j * n, zj)) != SE_OK) return rc;
+                rc = se_apply_internal(c, ncomp, zj, w, SE_F64, c->precision);
                 if (rc != SE_OK) return rc;
                 ++prods;
                 // classical Gram-Schmidt, twice
@@ -790,17 +795,17 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
                 }
                 if (std::fabs(g[j + 1]) <= 0.3 * rtol * bnorm || hn == 0.0) break;
             }
-            // y = H^{-1} g (upper triangular), x += P^{-1} V y
+            // y = H^{-1} g (upper triangular), x += Z y (flexible GMRES: the stored
+            // preconditioned vectors, so an FP32-rounded preconditioner stays consistent)
             for (int i = k - 1; i >= 0; --i) {
                 double sacc = g[i];
                 for (int q = i + 1; q < k; ++q) sacc -= H[(size_t)i * m + q] * yv[q];
                 yv[i] = sacc / H[(size_t)i * m + i];
             }
             SE_CUDA_CHECK(c, cudaMemcpyAsync(yd, yv.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
-            combine_kernel<<<grid_for(n), 256, 0, s>>>(V, n, n, k, yd, w);
+            combine_kernel<<<grid_for(n), 256, 0, s>>>(Zb, n, n, k, yd, w);
             c->launches++;
-            if ((rc = Pinv(w, z)) != SE_OK) return rc;
-            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, xd, 1.0, z, xd);
+            axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, xd, 1.0, w, xd);
             c->launches++;
         }
     }
