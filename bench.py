@@ -90,6 +90,23 @@ def dist_setup(args):
     return rank, world, local
 
 
+def job_time_ms(ms_local: float, world: int, device=None) -> float:
+    """The job's time: the maximum over ranks of a locally measured time (the ranks
+    run independent replicas; this reduction of one number is the only collective)."""
+    if world <= 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ms_job: float, world: int) -> float:
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return world * units_per_rank / (ms_job * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -312,12 +329,9 @@ def run_ours(args, rank, world, local):
     nprod, stage_ms = ctx.stage_times()
     ctx.set_option(api.SE_OPT_TIMING, 0)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time_ms(ms, world, dev)
     ms_step = ms / args.steps
-    value = world * args.steps / (ms * 1e-3)
+    value = job_rate(args.steps, ms, world)
 
     # end to end through the host-buffer entry point (copies in the timed region)
     x64 = np.ascontiguousarray(x_host)
@@ -331,10 +345,12 @@ def run_ours(args, rank, world, local):
     ctx.apply_host(xp, yp)
     ne2e = max(5, args.steps // 4)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t = time.perf_counter()
     for _ in range(ne2e):
         ctx.apply_host(xp, yp)
-    e2e = world * ne2e / (time.perf_counter() - t)
+    e2e = job_rate(ne2e, job_time_ms(1e3 * (time.perf_counter() - t), world, dev), world)
 
     # the plain FP64 GPU path on the same workload: products/s and accuracy
     fp64 = None
@@ -503,6 +519,10 @@ def run_batch(args, rank, world, local):
     from paper_1506_08481_b300 import api, inputs, params
 
     torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     boxes = inputs.batch_boxes(seed=0)
     rng = np.random.default_rng(1)
     ctxs, xs, ys, chosen = [], [], [], []
@@ -527,13 +547,15 @@ def run_batch(args, rank, world, local):
         for _ in range(args.warmup):
             batch.apply(xs, ys, use_graph=use_graph)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
             batch.apply(xs, ys, use_graph=use_graph)
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps
+        return job_time_ms(e0.elapsed_time(e1), world, dev) / args.steps
 
     launches0 = sum(c.kernel_launches() for c in ctxs)
     b = api.Batch(ctxs, nstreams=1)
@@ -547,18 +569,22 @@ def run_batch(args, rank, world, local):
     b.close()
     ntot = sum(c.N for c in boxes)
     if rank == 0:
-        line = {"metric": "aggregate box products/s, 64 uneven boxes (forces only)", "value": world * 64 / (ms_graph * 1e-3),
+        line = {"metric": "aggregate box products/s, 64 uneven boxes (forces only)", "value": job_rate(64, ms_graph, world),
                 "unit": "box products/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "batch64", "boxes": 64, "N_total": ntot, "ncomp": 3,
                            "params": "autotuned" if args.autotune else "error-model choice for 1e-6",
                            "M_P_per_box": chosen, "streams": 8},
-                "per_box_launch_loop": {"value": world * 64 / (ms_loop * 1e-3), "ms_per_step": ms_loop},
+                "per_box_launch_loop": {"value": job_rate(64, ms_loop, world), "ms_per_step": ms_loop},
                 "graph_speedup": ms_loop / ms_graph,
                 "gpu_launches_setup_and_eager": sum(c.kernel_launches() for c in ctxs) - launches0,
                 "clocks": clk}
         print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def main():
