@@ -78,6 +78,7 @@ def parse():
                     help="iterations of the plain FP64 solve that are timed (it runs ~20x slower)")
     ap.add_argument("--workload", choices=["mono_n200k", "batch64"], default="mono_n200k")
     ap.add_argument("--autotune", action="store_true", help="batch64: time candidate parameters per box")
+    ap.add_argument("--streams", type=int, default=8, help="batch64: streams of the captured graph")
     ap.add_argument("--n", type=int, default=200000,
                     help="spheres (N-sweep of the large-scale configuration at the same phi and grid density)")
     return ap.parse_args()
@@ -561,7 +562,7 @@ def run_batch(args, rank, world, local):
     b = api.Batch(ctxs, nstreams=1)
     ms_loop = timed(b, False)
     b.close()
-    b = api.Batch(ctxs, nstreams=8)
+    b = api.Batch(ctxs, nstreams=args.streams)
     clocks = ClockSampler(local)
     clocks.start()
     ms_graph = timed(b, True)
@@ -575,7 +576,7 @@ def run_batch(args, rank, world, local):
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "batch64", "boxes": 64, "N_total": ntot, "ncomp": 3,
                            "params": "autotuned" if args.autotune else "error-model choice for 1e-6",
-                           "M_P_per_box": chosen, "streams": 8},
+                           "M_P_per_box": chosen, "streams": args.streams},
                 "per_box_launch_loop": {"value": job_rate(64, ms_loop, world), "ms_per_step": ms_loop},
                 "graph_speedup": ms_loop / ms_graph,
                 "gpu_launches_setup_and_eager": sum(c.kernel_launches() for c in ctxs) - launches0,

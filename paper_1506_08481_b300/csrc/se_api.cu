@@ -103,6 +103,7 @@ static void free_grids(se_ctx *c)
 {
     for (int q = 0; q < 2; ++q) {
         dfree(c->b.grid_f[q]);
+        dfree(c->b.grid_part[q]);
         dfree(c->b.spec_f[q]);
         dfree(c->b.spec_o[q]);
         dfree(c->b.grid_o[q]);
@@ -163,12 +164,20 @@ static int ensure_grids(se_ctx *c, int prec)
     const size_t es = prec == 1 ? sizeof(double) : sizeof(float);
     if (c->grid_M[prec] == (size_t)c->M && c->b.grid_f[prec]) return SE_OK;
     dfree(c->b.grid_f[prec]);
+    dfree(c->b.grid_part[prec]);
     dfree(c->b.spec_f[prec]);
     dfree(c->b.spec_o[prec]);
     dfree(c->b.grid_o[prec]);
     dfree(c->b.tw[prec]);
     const size_t M = c->M, Mh = M / 2 + 1;
     SE_ALLOC(c, c->b.grid_f[prec], M * M * M * 4 * es);
+    // With few spreading tiles (small M) several CTAs share a tile, each summing part
+    // of its particles into its own partial grid: about two waves of CTAs on 148 SMs.
+    {
+        const size_t ntiles = (M / kTile) * (M / kTile) * (M / kTile);
+        c->nsplit = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * 148 * 11 + ntiles - 1) / ntiles));
+        if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[prec], (size_t)c->nsplit * M * M * M * 4 * es);
+    }
     SE_ALLOC(c, c->b.spec_f[prec], M * M * Mh * 4 * 2 * es);
     SE_ALLOC(c, c->b.spec_o[prec], M * M * Mh * 8 * 2 * es);
     SE_ALLOC(c, c->b.grid_o[prec], M * M * M * 8 * es);

@@ -59,6 +59,7 @@ struct Buffers {
     void *xs[2] = {};            // [N][12] T inputs in cell order
     void *yreal[2] = {};         // [N][12] T real-space result
     void *grid_f[2] = {};        // [M^3][4] T spread grids
+    void *grid_part[2] = {};     // [nsplit][M^3][4] T partial spread grids (small grids only)
     void *spec_f[2] = {};        // [M][M][Mh][4] complex T
     void *spec_o[2] = {};        // [M][M][Mh][8] complex T
     void *grid_o[2] = {};        // [M^3][8] T gathered grids
@@ -96,6 +97,7 @@ struct se_ctx {
     int parts = 7;
     int overlap = 2;             // SE_OPT_OVERLAP
     int gather = 0;              // SE_OPT_GATHER
+    int nsplit = 1;              // CTAs sharing a spreading tile (few tiles: small M)
     // configuration
     bool have_config = false;
     bool support_ok[2] = {false, false};

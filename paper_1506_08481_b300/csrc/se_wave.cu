@@ -104,11 +104,11 @@ __global__ void support_kernel(int N, SeParams p, const double *pos, const doubl
 // (Eq. grid-space with the torque and stresslet terms):
 //   H = g [ (A0 + A1 s^2) F - alpha kappa (s x T) + (B0 + B1 s^2) S.s ],  H_src = g S_tr,
 // so a thread forms 13 column coefficients per particle and spends 13 FMAs per point.
-template <typename T, int NCOMP>
+template <typename T, int NCOMP, bool SPLIT>
 __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeParams p, const int *tile_start,
                                                     const int *tile_perm, const int *base,
                                                     const T *s0g, const T *wg, const double *rad,
-                                                    const T *xs, T *grid)
+                                                    const T *xs, T *grid, int nsplit)
 {
     constexpr int TT = kTile, CH = 64, MAXB = 125;
     using T4 = typename V4<T>::t;
@@ -149,7 +149,15 @@ __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeP
     __syncthreads();
     const int total = bin_off[nb3];
 
-    for (int c0 = 0; c0 < total; c0 += CH) {
+    // SPLIT: part blockIdx.y of nsplit takes every nsplit-th chunk of the candidates
+    // and writes the partial grid blockIdx.y
+    int cbeg = 0, cstep = CH;
+    if constexpr (SPLIT) {
+        grid += (size_t)blockIdx.y * M * M * M * 4;
+        cbeg = blockIdx.y * CH;
+        cstep = nsplit * CH;
+    }
+    for (int c0 = cbeg; c0 < total; c0 += cstep) {
         const int cnt = min(CH, total - c0);
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
@@ -294,6 +302,25 @@ __global__ void self_coef_kernel(int N, double xi, double eta, const double *rad
     out[4 * i + 2] = (T)(3.0 / (20 * kPi * eta * a * a2) -
                          xi * x2 * (25 - 42 * a2 * x2 + 27 * a2 * a2 * x2 * x2) / (50 * pi32 * eta));
     out[4 * i + 3] = (T)(3.0 / (16 * kPi * eta * a * a2));
+}
+
+// grid = sum over the nsplit partial grids, in part order
+template <typename T>
+__global__ void sum_parts_kernel(size_t n4, int nsplit, const T *parts, T *grid)
+{
+    using T4 = typename V4<T>::t;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n4) return;
+    const T4 *p = reinterpret_cast<const T4 *>(parts) + e;
+    T4 s = p[0];
+    for (int q = 1; q < nsplit; ++q) {
+        const T4 v = p[(size_t)q * n4];
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+    }
+    reinterpret_cast<T4 *>(grid)[e] = s;
 }
 
 // ---------------------------------------------------------------- FFT passes
@@ -658,7 +685,7 @@ __device__ __forceinline__ void combine_write(const SeParams &p, const T (&acc)[
 // U(3), s x v (3), sym(s (x) w) (6: xx yy zz, xy xz yz doubled), p (1) once per column.
 // Column contributions are Kahan-compensated across the P^2 / 32 columns of a lane.
 template <typename T, typename TO, int CO, int NCOMP>
-__global__ void __launch_bounds__(256, 4) gather_kernel(SeParams p, int N, const int *order, const int *base,
+__global__ void __launch_bounds__(256, 2) gather_kernel(SeParams p, int N, const int *order, const int *base,
                                                      const T *s0g, const T *wg, const double *rad, const T *selfc,
                                                      const int *perm, const T *grid, const T *xs, const T *yreal,
                                                      TO *y, int ncomp_out, int with_wave, int with_self)
@@ -708,7 +735,7 @@ __global__ void __launch_bounds__(256, 4) gather_kernel(SeParams p, int N, const
             // column moments: Z0..Z3 of v (and of v'' in the hybrid mode), Zp of p
             T z0[3] = {0, 0, 0}, z1[3] = {0, 0, 0}, z2[3] = {0, 0, 0}, z3[3] = {0, 0, 0}, zp = 0;
             if (act) {
-#pragma unroll 4
+#pragma unroll 12
                 for (int k = 0; k < P; ++k) {
                     const T4 w = Wz[wl][k];
                     const T4 u0 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[wl][k] * zs);
@@ -1069,16 +1096,30 @@ void setup_support(se_ctx *c, cudaStream_t s)
 template <typename T>
 static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_t s, int ncomp)
 {
-    const int nt = p.ntile, ntiles = nt * nt * nt;
+    const int nt = p.ntile, ntiles = nt * nt * nt, ns = c->nsplit;
+    T *out = ns > 1 ? (T *)c->b.grid_part[pix<T>()] : (T *)c->b.grid_f[pix<T>()];
     auto args = [&](auto kern) {
-        kern<<<ntiles, 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base, (const T *)c->b.sup_s0[pix<T>()],
-                                     (const T *)c->b.sup_w[pix<T>()], c->b.rad, xs, (T *)c->b.grid_f[pix<T>()]);
+        kern<<<dim3(ntiles, ns), 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
+                                              (const T *)c->b.sup_s0[pix<T>()], (const T *)c->b.sup_w[pix<T>()],
+                                              c->b.rad, xs, out, ns);
     };
-    if (ncomp <= 3) args(spread_kernel<T, 3>);
-    else if (ncomp <= 6) args(spread_kernel<T, 6>);
-    else if (ncomp <= 11) args(spread_kernel<T, 11>);
-    else args(spread_kernel<T, 12>);
+    if (ns > 1) {
+        if (ncomp <= 3) args(spread_kernel<T, 3, true>);
+        else if (ncomp <= 6) args(spread_kernel<T, 6, true>);
+        else if (ncomp <= 11) args(spread_kernel<T, 11, true>);
+        else args(spread_kernel<T, 12, true>);
+    } else {
+        if (ncomp <= 3) args(spread_kernel<T, 3, false>);
+        else if (ncomp <= 6) args(spread_kernel<T, 6, false>);
+        else if (ncomp <= 11) args(spread_kernel<T, 11, false>);
+        else args(spread_kernel<T, 12, false>);
+    }
     c->launches++;
+    if (ns > 1) {
+        const size_t n4 = (size_t)p.M * p.M * p.M;
+        sum_parts_kernel<T><<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(n4, ns, out, (T *)c->b.grid_f[pix<T>()]);
+        c->launches++;
+    }
 }
 
 template <typename T, int CO, int LB>

@@ -1,5 +1,6 @@
 """Batches of uneven boxes: the captured CUDA graph and the eager per-box launches give
-the same products as each box's own se_mobility_apply, and graph replays stay correct."""
+the same products (bitwise), equal to each box's own se_mobility_apply to FP32 rounding,
+and graph replays stay correct."""
 import numpy as np
 import pytest
 
@@ -27,13 +28,22 @@ def test_batch_graph_matches_per_box_products(oracle_mod):
     torch.cuda.synchronize()
     ys = [torch.empty_like(x) for x in xs]
     b = api.Batch(ctxs, nstreams=4)
+    first = None
     for use_graph in (False, True, True):           # eager, capture + launch, replay
         for y in ys:
             y.fill_(float("nan"))
         b.apply(xs, ys, use_graph=use_graph)
         torch.cuda.synchronize()
+        # a box alone may split its spreading tiles over CTAs (small grids) and so sum in
+        # another order than inside a batch: equal to FP32 rounding; the batch's own
+        # eager and graph launches are bitwise equal
         for y, r in zip(ys, refs):
-            assert torch.equal(y, r)
+            assert float(torch.linalg.norm(y - r) / torch.linalg.norm(r)) <= 1e-6
+        if first is None:
+            first = [y.clone() for y in ys]
+        else:
+            for y, f in zip(ys, first):
+                assert torch.equal(y, f)
     # new inputs in the same buffers: the replayed graph reads them
     for x in xs:
         x.mul_(-2.0)
