@@ -373,61 +373,108 @@ __device__ __forceinline__ void pair_coefficients(double r2, double ai2, double 
     cf[18] = 3 * c16 * (p2 + aj2 / 10 * q2);
 }
 
-// Neighbour search for target i (cell order) in FP64: calls f(j, x0, x1, x2, r2) for
-// every j != i with |x| < rc, in a fixed order.
-template <typename F>
-__device__ __forceinline__ void for_neighbours(int i, double L, double rc, int nc, const int *cell_start,
-                                               const double *pos, F f)
+// Neighbour search for target i (cell order): calls f(j) for every j != i with
+// |x_ij| < rc (minimum image), in a fixed order (cells dz, dy, dx, then cell order).
+// The decision is the FP64 one, |x|^2 < rc^2 with x = p_i - p_j wrapped by +-L; it is
+// taken in FP32 where that is safe: with positions in [0, L) rounded to FP32, each
+// component of the FP32 separation is within 5 * 2^-24 L of the exact one and the FP32
+// |x|^2 within 2^-22 |x|^2 of its value, so |x_f32| differs from |x| by less than
+// mrg = 2^-20 (L + rc).  Below (rc - mrg)^2 the pair is surely inside, at or above
+// (rc + mrg)^2 surely outside; only the thin band between repeats the FP64 test.
+__device__ __forceinline__ double min_image(double d, double L)
 {
-    const double w = L / nc, rc2 = rc * rc;
+    return d > 0.5 * L ? d - L : (d < -0.5 * L ? d + L : d);
+}
+__device__ __forceinline__ float min_image_f(float d, float L)
+{
+    return d > 0.5f * L ? d - L : (d < -0.5f * L ? d + L : d);
+}
+
+struct PairSearch {
+    double L, rc2;
+    float Lf, lo, hi;          // FP32 box and the band (rc -+ mrg)^2
+    int nc;
+};
+
+template <typename F>
+__device__ __forceinline__ void for_neighbours(int i, const PairSearch &ps, const int *cell_start,
+                                               const double *pos, const float4 *pf, F f)
+{
+    const int nc = ps.nc;
+    const double w = ps.L / nc;
     const double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
     const int cx = min(nc - 1, (int)(px / w)), cy = min(nc - 1, (int)(py / w)), cz = min(nc - 1, (int)(pz / w));
+    const float4 pi = pf[i];
     const int span = nc >= 3 ? 1 : 0;
     for (int dz = -span; dz <= span; ++dz)
         for (int dy = -span; dy <= span; ++dy)
             for (int dx = -span; dx <= span; ++dx) {
                 const int nb = (((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc) * nc + (cx + dx + nc) % nc;
                 for (int j = cell_start[nb]; j < cell_start[nb + 1]; ++j) {
-                    if (j == i) continue;
-                    double x0 = px - pos[3 * j], x1 = py - pos[3 * j + 1], x2 = pz - pos[3 * j + 2];
-                    x0 -= L * rint(x0 / L);
-                    x1 -= L * rint(x1 / L);
-                    x2 -= L * rint(x2 / L);
-                    const double r2 = x0 * x0 + x1 * x1 + x2 * x2;
-                    if (r2 < rc2) f(j, x0, x1, x2, r2);
+                    const float4 pj = pf[j];
+                    const float x0 = min_image_f(pi.x - pj.x, ps.Lf), x1 = min_image_f(pi.y - pj.y, ps.Lf),
+                                x2 = min_image_f(pi.z - pj.z, ps.Lf);
+                    const float r2f = x0 * x0 + x1 * x1 + x2 * x2;
+                    if (r2f >= ps.hi || j == i) continue;
+                    if (r2f >= ps.lo) {
+                        const double y0 = min_image(px - pos[3 * j], ps.L), y1 = min_image(py - pos[3 * j + 1], ps.L),
+                                     y2 = min_image(pz - pos[3 * j + 2], ps.L);
+                        if (!(y0 * y0 + y1 * y1 + y2 * y2 < ps.rc2)) continue;
+                    }
+                    f(j);
                 }
             }
 }
 
-__global__ void pair_count_kernel(int N, double L, double rc, int nc, const int *cell_start, const double *pos,
+__global__ void pos_f32_kernel(int N, const double *pos, float4 *pf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) pf[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], 0.f);
+}
+
+__global__ void pair_count_kernel(int N, PairSearch ps, const int *cell_start, const double *pos, const float4 *pf,
                                   int *count)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int n = 0;
-    for_neighbours(i, L, rc, nc, cell_start, pos, [&](int, double, double, double, double) { ++n; });
+    for_neighbours(i, ps, cell_start, pos, pf, [&](int) { ++n; });
     count[i] = n;
 }
 
-template <typename T>
-__global__ void pair_fill_kernel(int N, double L, double rc, int nc, double xi, double eta, const int *cell_start,
-                                 const double *pos, const double *rad, const int *off, size_t np, int *pj,
-                                 T *px, T *pc)
+__global__ void pair_list_kernel(int N, PairSearch ps, const int *cell_start, const double *pos, const float4 *pf,
+                                 const int *off, int *pj)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const double ai2 = rad[i] * rad[i];
-    size_t k = off[i];
-    for_neighbours(i, L, rc, nc, cell_start, pos, [&](int j, double x0, double x1, double x2, double r2) {
+    int k = off[i];
+    for_neighbours(i, ps, cell_start, pos, pf, [&](int j) { pj[k++] = j; });
+}
+
+// One warp per target: the lanes take the target's pairs in turn, form the FP64
+// separation and the radial coefficients and store them (coalesced SoA rows).
+template <typename T>
+__global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double xi, double eta, const double *pos,
+                                                        const double *rad, const int *off, size_t np, const int *pj,
+                                                        T *px, T *pc)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= N) return;
+    const double p0 = pos[3 * i], p1 = pos[3 * i + 1], p2 = pos[3 * i + 2], ai2 = rad[i] * rad[i];
+    const int ke = off[i + 1];
+    for (int k = off[i] + lane; k < ke; k += 32) {
+        const int j = pj[k];
+        const double x0 = min_image(p0 - pos[3 * j], L), x1 = min_image(p1 - pos[3 * j + 1], L),
+                     x2 = min_image(p2 - pos[3 * j + 2], L);
         double cf[kNPC];
-        pair_coefficients(r2, ai2, rad[j] * rad[j], xi, eta, cf);
-        pj[k] = j;
+        pair_coefficients(x0 * x0 + x1 * x1 + x2 * x2, ai2, rad[j] * rad[j], xi, eta, cf);
         px[k] = (T)x0;
         px[np + k] = (T)x1;
         px[2 * np + k] = (T)x2;
+#pragma unroll
         for (int q = 0; q < kNPC; ++q) pc[q * np + k] = (T)cf[q];
-        ++k;
-    });
+    }
 }
 
 // One warp per target: the lanes stream the target's stored pairs (coalesced SoA
@@ -548,38 +595,70 @@ int build_pair_table(se_ctx *c)
     const int N = (int)c->N;
     if (!c->b.pair_off) {
         int *count = nullptr;
-        if (cudaMalloc(&c->b.pair_off, (N + 1) * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&count, N * sizeof(int)) != cudaSuccess) {
-            cudaGetLastError();
+        float4 *pf = nullptr;
+        auto release = [&]() {
             if (count) cudaFree(count);
+            if (pf) cudaFree(pf);
+        };
+        auto drop_lists = [&]() {          // leave no half-built list behind
+            if (c->b.pair_off) cudaFree(c->b.pair_off);
+            if (c->b.pair_j) cudaFree(c->b.pair_j);
+            c->b.pair_off = nullptr;
+            c->b.pair_j = nullptr;
+        };
+        auto fail = [&]() {
+            cudaGetLastError();
+            release();
+            drop_lists();
             c->err = "pair table allocation failed";
             return SE_ERR_NOMEM;
-        }
-        pair_count_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, c->L, c->rc, c->nc, c->b.cell_start, c->b.pos, count);
-        c->launches++;
+        };
+        auto sync = [&]() {
+            const cudaError_t e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) return SE_OK;
+            release();
+            drop_lists();
+            c->err = std::string("pair table build: ") + cudaGetErrorString(e);
+            return SE_ERR_CUDA;
+        };
+        if (cudaMalloc(&c->b.pair_off, (N + 1) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&count, N * sizeof(int)) != cudaSuccess || cudaMalloc(&pf, N * sizeof(float4)) != cudaSuccess)
+            return fail();
+        PairSearch ps;
+        ps.L = c->L;
+        ps.rc2 = c->rc * c->rc;
+        ps.nc = c->nc;
+        ps.Lf = (float)c->L;
+        const double mrg = std::ldexp(c->L + c->rc, -20);
+        ps.lo = (float)((c->rc - mrg) * (c->rc - mrg));
+        ps.hi = (float)((c->rc + mrg) * (c->rc + mrg));
+        pos_f32_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, c->b.pos, pf);
+        pair_count_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ps, c->b.cell_start, c->b.pos, pf, count);
+        c->launches += 2;
         launch_scan(c, N, count, c->b.pair_off, s);
         int np = 0;
         cudaMemcpyAsync(&np, c->b.pair_off + N, sizeof(int), cudaMemcpyDeviceToHost, s);
-        SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
-        cudaFree(count);
+        if (int rc = sync()) return rc;
         c->npairs = (size_t)np;
-        if (cudaMalloc(&c->b.pair_j, (c->npairs + 1) * sizeof(int)) != cudaSuccess) {
-            cudaGetLastError();
-            c->err = "pair table allocation failed";
-            return SE_ERR_NOMEM;
-        }
+        if (cudaMalloc(&c->b.pair_j, (c->npairs + 1) * sizeof(int)) != cudaSuccess) return fail();
+        pair_list_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ps, c->b.cell_start, c->b.pos, pf, c->b.pair_off,
+                                                         c->b.pair_j);
+        c->launches++;
+        if (int rc = sync()) return rc;
+        release();
     }
     const int q = pix<T>();
     const size_t np = c->npairs;
     if (cudaMalloc(&c->b.pair_x[q], (3 * np + 1) * sizeof(T)) != cudaSuccess ||
         cudaMalloc(&c->b.pair_c[q], ((size_t)kNPC * np + 1) * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
+        if (c->b.pair_x[q]) cudaFree(c->b.pair_x[q]);
+        c->b.pair_x[q] = nullptr;
         c->err = "pair table allocation failed";
         return SE_ERR_NOMEM;
     }
-    pair_fill_kernel<T><<<(N + 127) / 128, 128, 0, s>>>(N, c->L, c->rc, c->nc, c->xi, c->eta, c->b.cell_start,
-                                                         c->b.pos, c->b.rad, c->b.pair_off, np, c->b.pair_j,
-                                                         (T *)c->b.pair_x[q], (T *)c->b.pair_c[q]);
+    pair_fill_kernel<T><<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->xi, c->eta, c->b.pos, c->b.rad, c->b.pair_off, np,
+                                                    c->b.pair_j, (T *)c->b.pair_x[q], (T *)c->b.pair_c[q]);
     c->launches++;
     SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
     c->pairs_ok[q] = true;

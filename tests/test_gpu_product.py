@@ -232,3 +232,38 @@ def test_gather_variants_agree(small_poly, small_poly_ref, size_mode):
         out[g] = gpu_apply(ctx, x)
         assert rel(out[g], small_poly_ref) <= 1e-9
     assert rel(out[2], out[1]) <= 1e-13
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_cutoff_boundary_pairs(oracle_mod, precision):
+    """Pairs at |x| = rc (1 +- delta), delta from 1e-13 to 1e-2, along axes, diagonals and
+    random directions, some across the periodic boundary, each pair further than rc from
+    every other sphere: the real-space sum keeps exactly the pairs with |x| < rc (the
+    FP64 decision of the oracle's image loop), including those decided in the thin band
+    where FP32 separations cannot tell."""
+    rng = np.random.default_rng(29)
+    L, rc, xi = 40.0, 4.0, 0.5
+    deltas = [s * d for d in (1e-13, 1e-9, 3e-7, 3e-6, 1e-4, 1e-2) for s in (1, -1)]
+    dirs = [np.array([1.0, 0, 0]), np.array([0, -1.0, 0]), np.ones(3) / np.sqrt(3)]
+    dirs += [v / np.linalg.norm(v) for v in rng.standard_normal((3, 3))]
+    pos = []
+    slots = [(8.0 + 10 * a, 8.0 + 10 * b, 8.0 + 10 * c) for a in range(4) for b in range(4) for c in range(4)]
+    k = 0
+    for d in deltas:
+        for u in dirs[:4] if abs(d) > 1e-5 else dirs:
+            p = np.array(slots[k])
+            k += 1
+            pos += [p, np.mod(p + rc * (1 + d) * u, L)]
+    pos = np.array(pos)
+    rad = np.full(len(pos), 0.5)
+    cfg = inputs.Config("cutoff", L, pos, rad)
+    x = rng.standard_normal((len(pos), 12))
+    ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x, xi=xi, rc=rc, kc=1.0, parts=1)
+    inside = np.array([d < 0 for d in deltas for _ in (dirs[:4] if abs(d) > 1e-5 else dirs)])
+    # every pair inside rc is felt, every pair outside is not
+    assert np.all(np.abs(ref[0::2][inside]).max(axis=1) > 1e-6)
+    assert np.all(ref[0::2][~inside] == 0)
+    ctx = make_ctx(xi, 32, 8, rc, cfg, precision=precision, parts=1)
+    y = gpu_apply(ctx, x, dtype=torch.float64 if precision else torch.float32)
+    assert np.all(y[0::2][~inside] == 0) and np.all(y[1::2][~inside] == 0)
+    assert rel(y[:, :11], ref[:, :11]) <= (1e-12 if precision else 2e-6)
