@@ -379,18 +379,24 @@ def run_ours(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1) / n64
+        ctx.set_option(api.SE_OPT_TIMING, 1)
+        ctx.stage_times()
+        ctx.apply(xd, yd)
+        n1, st64 = ctx.stage_times()
+        ctx.set_option(api.SE_OPT_TIMING, 0)
         acc64 = None
         if acc is not None:
             acc64 = float(np.linalg.norm(yd.cpu().numpy()[g["rows"]] - g["y"]) / np.linalg.norm(g["y"]))
         fp64 = {"value": world * 1e3 / ms64, "unit": "products/s", "ms_per_product": ms64,
-                "rel_l2_vs_fp64_oracle": acc64, "fp32_speedup": ms64 / ms_step}
+                "rel_l2_vs_fp64_oracle": acc64, "fp32_speedup": ms64 / ms_step,
+                "stage_ms_per_product": {k: v / max(n1, 1) for k, v in st64.items()}}
         del xd, yd
         ctx.set_option(api.SE_OPT_PRECISION, 0)
 
     # the same product at the parameters the error model picks for this box at 5e-7 in
     # FP32 (method error plus FP32 rounding floor), so the product still meets 1e-6; the
     # support P is then the model's choice instead of the configuration's P = 24
-    tuned = None
+    tuned, ct = None, None
     if not args.no_tuned and args.n == 200000:
         from paper_1506_08481_b300 import params as prm
         sp = prm.choose(cfg.L, cfg.N, 5e-7, M_max=384, precision=0)
@@ -417,37 +423,48 @@ def run_ours(args, rank, world, local):
         tuned = {"value": world * 1e3 / mst, "unit": "products/s", "ms_per_product": mst,
                  "rel_l2_vs_fp64_oracle": acct,
                  "params": {"xi": sp.xi, "M": sp.M, "P": sp.P, "rc": sp.rc, "m": sp.m, "model_tol": 5e-7}}
-        ct.close()
         del yt
 
     # GMRES solves of M x = b (F, T, S; b = the first 11 input components) to 1e-6:
-    # FP32 products + FP64 true residual and refinement, with the plain block-diagonal
-    # and the learned preconditioner, and the plain FP64 GPU path with the block one
+    # FP32 products + FP64 true residual and refinement, with the plain block-diagonal,
+    # the learned and the spectral preconditioner, and the plain FP64 GPU path with the
+    # block one; then the block and spectral solves again at the error model's parameters
     solve = None
     if not args.no_solve:
         b = torch.tensor(x_host[:, :11], device=dev, dtype=torch.float64)
         xs = torch.zeros_like(b)
-        ctx.set_option(api.SE_OPT_RESTART, args.restart)
         wpath = os.path.join(ROOT, "paper_1506_08481_b300", "learned_pc_weights.npy")
-        if os.path.exists(wpath):
-            ctx.set_learned_weights(np.load(wpath))
+
+        def solves(c, runs):
+            out = {}
+            c.set_option(api.SE_OPT_RESTART, args.restart)
+            if os.path.exists(wpath):
+                c.set_learned_weights(np.load(wpath))
+            for name, prec, pc, maxit in runs:
+                c.set_option(api.SE_OPT_PRECISION, prec)
+                c.solve(b, xs, rtol=1e-6, maxit=2, precond=pc, allow_not_converged=True)   # setup
+                xs.zero_()
+                torch.cuda.synchronize()
+                if world > 1:
+                    torch.distributed.barrier()
+                t = time.perf_counter()
+                _, iters, relres = c.solve(b, xs, rtol=1e-6, maxit=maxit, precond=pc, allow_not_converged=True)
+                torch.cuda.synchronize()
+                ts = job_time_ms(1e3 * (time.perf_counter() - t), world, dev) / 1e3
+                out[name] = {"solves_per_s": world / ts, "seconds": ts, "iterations": iters,
+                             "relres_fp64": relres, "converged": bool(relres <= 1e-6)}
+            c.set_option(api.SE_OPT_PRECISION, 0)
+            return out
+
         runs = [("fp32_block", 0, api.SE_PRECOND_BLOCK, args.solve_maxit),
                 ("fp32_learned", 0, api.SE_PRECOND_LEARNED, args.solve_maxit),
                 ("fp32_spectral", 0, api.SE_PRECOND_SPECTRAL, args.solve_maxit)]
         if not args.no_fp64:
             runs.append(("fp64_block", 1, api.SE_PRECOND_BLOCK, args.fp64_solve_maxit))
         solve = {"ncomp": 11, "rtol": 1e-6, "restart": args.restart, "maxit": args.solve_maxit,
-                 "learned_weights": os.path.exists(wpath)}
-        for name, prec, pc, maxit in runs:
-            ctx.set_option(api.SE_OPT_PRECISION, prec)
-            ctx.solve(b, xs, rtol=1e-6, maxit=2, precond=pc, allow_not_converged=True)   # setup
-            xs.zero_()
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            _, iters, relres = ctx.solve(b, xs, rtol=1e-6, maxit=maxit, precond=pc, allow_not_converged=True)
-            ts = time.perf_counter() - t
-            solve[name] = {"solves_per_s": world / ts, "seconds": ts, "iterations": iters,
-                           "relres_fp64": relres, "converged": bool(relres <= 1e-6)}
+                 "learned_weights": os.path.exists(wpath),
+                 "params": {k: P_[k] for k in ("xi", "M", "P", "rc")}}
+        solve.update(solves(ctx, runs))
         if "fp64_block" in solve and not solve["fp64_block"]["converged"]:
             # the FP64 path timed over its first maxit iterations; the time of a whole solve
             # is projected at the iteration count of the FP32 block-preconditioned solve
@@ -457,13 +474,19 @@ def run_ours(args, rank, world, local):
             r["solves_per_s"] = world / r["projected_seconds"]
             r["note"] = (f"timed over {r['iterations']} iterations; solves/s projected at the FP32 "
                          f"solve's {solve['fp32_block']['iterations']} iterations")
-        ctx.set_option(api.SE_OPT_PRECISION, 0)
         # headline: the spectral preconditioner (block + long-wavelength correction);
         # the plain block and the learned block correction beside it
         solve["solves_per_s"] = solve["fp32_spectral"]["solves_per_s"]
         solve["headline"] = "fp32_spectral"
         solve["speedup_vs_block"] = solve["fp32_spectral"]["solves_per_s"] / solve["fp32_block"]["solves_per_s"]
         solve["learned_vs_block"] = solve["fp32_learned"]["solves_per_s"] / solve["fp32_block"]["solves_per_s"]
+        if ct is not None:
+            tuned_solves = solves(ct, [("fp32_block", 0, api.SE_PRECOND_BLOCK, args.solve_maxit),
+                                       ("fp32_spectral", 0, api.SE_PRECOND_SPECTRAL, args.solve_maxit)])
+            tuned_solves["params"] = tuned["params"]
+            solve["tuned_params"] = tuned_solves
+    if ct is not None:
+        ct.close()
 
     # the real-space kernel alone (in the product it runs on a second stream beside the
     # spread and FFT, so its in-product event time includes the overlap)

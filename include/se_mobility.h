@@ -84,6 +84,10 @@ typedef struct se_ctx se_ctx;
                                   the bin's support window in shared memory (slower on B300 at P = 14
                                   and 24); results agree to rounding */
 
+#define SE_OPT_SPREAD     12   /* spreading kernel: 0 = default (FP32: 8 x 8 x 16 tiles with packed FP32
+                                  FMAs where the grid has room for them, else 8^3 tiles), 1 = 8^3
+                                  tiles always; results agree to rounding */
+
 /* product stages reported by se_stage_times */
 #define SE_STAGE_PERMUTE   0   /* inputs into cell order */
 #define SE_STAGE_REAL      1   /* real-space pair kernel (auxiliary stream) */

@@ -172,10 +172,10 @@ static int ensure_grids(se_ctx *c, int prec)
     const size_t M = c->M, Mh = M / 2 + 1;
     SE_ALLOC(c, c->b.grid_f[prec], M * M * M * 4 * es);
     // With few spreading tiles (small M) several CTAs share a tile, each summing part
-    // of its particles into its own partial grid: about two waves of CTAs on 148 SMs.
+    // of its particles into its own partial grid: about two waves of CTAs on the SMs.
     {
         const size_t ntiles = (M / kTile) * (M / kTile) * (M / kTile);
-        c->nsplit = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * 148 * 11 + ntiles - 1) / ntiles));
+        c->nsplit = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * kSMs * 11 + ntiles - 1) / ntiles));
         if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[prec], (size_t)c->nsplit * M * M * M * 4 * es);
     }
     SE_ALLOC(c, c->b.spec_f[prec], M * M * Mh * 4 * 2 * es);
@@ -377,6 +377,10 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
     case SE_OPT_GATHER:
         if (value != 0 && value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "gather must be 0, 1 or 2");
         c->gather = (int)value;
+        return SE_OK;
+    case SE_OPT_SPREAD:
+        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "spread must be 0 or 1");
+        c->spread = (int)value;
         return SE_OK;
     case SE_OPT_TIMING:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "timing must be 0 or 1");

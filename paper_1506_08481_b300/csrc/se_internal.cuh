@@ -14,6 +14,7 @@ namespace se {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kNC = 12;          // components per particle, internal layout
 constexpr int kTile = 8;         // spreading tile edge (grid points)
+constexpr int kSMs = 148;        // streaming multiprocessors of a B300 (grid sizing)
 
 template <typename T> struct C2;
 template <> struct C2<float> { using t = float2; };
@@ -97,6 +98,7 @@ struct se_ctx {
     int parts = 7;
     int overlap = 2;             // SE_OPT_OVERLAP
     int gather = 0;              // SE_OPT_GATHER
+    int spread = 0;              // SE_OPT_SPREAD
     int nsplit = 1;              // CTAs sharing a spreading tile (few tiles: small M)
     // configuration
     bool have_config = false;

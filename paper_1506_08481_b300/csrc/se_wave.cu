@@ -287,6 +287,232 @@ __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeP
     }
 }
 
+// ---- FP32 spreading over 8 x 8 x 16 tiles with packed FMAs
+//
+// The same column scheme as spread_kernel with tiles of 16 planes: a thread's column
+// coefficients (the per-particle overhead) serve 16 planes instead of 8, and the
+// plane updates pair planes (2 zp, 2 zp + 1) in packed FP32 FMAs (fma.rn.f32x2: two
+// lanes' worth of FMAs per issue slot), acc2[zp][q] = (value at plane 2 zp, value at
+// plane 2 zp + 1) of component q.  The staged table holds, per particle and plane pair,
+// (W_2zp.e, W_2zp+1.e) for e = 0..3 (W = g_z (1, s_z, s_z^2, s_z^3)).  Quarters of the
+// tile (4 planes) that the support misses are skipped.  The grid's last tile is only 8
+// planes deep when M / 8 is odd; its planes beyond M are computed and not written.
+using u64 = unsigned long long;
+__device__ __forceinline__ u64 pack2(float lo, float hi)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(u64 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
+{
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+constexpr int kTz = 16;    // planes per tile of spread16_kernel
+
+template <int NCOMP, bool SPLIT>
+__global__ void __launch_bounds__(64, 8) spread16_kernel(SeParams p, const int *tile_start, const int *tile_perm,
+                                                         const int *base, const float *s0g, const float *wg,
+                                                         const double *rad, const float *xs, float *grid, int nsplit)
+{
+    constexpr int TT = kTile, TZ = kTz, CH = 64, MAXB = 6 * 6 * 7;
+    __shared__ float sxy[CH][2 * TT];   // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
+    __shared__ float4 swz[CH][TZ];      // unit 2 zp + h: (W_2zp, W_2zp+1) of e = 2h, 2h + 1; at unit ^ (k & 7)
+    __shared__ float4 sp[CH][5];
+    __shared__ int bin_beg[MAXB], bin_off[MAXB + 1];
+    const int M = p.M, P = p.P, nt = p.ntile;
+    const int ntz = (nt + 1) / 2;
+    const int tile = blockIdx.x;
+    const int bx0 = tile % nt, by0 = (tile / nt) % nt, bzp = tile / (nt * nt);
+    const int t0[3] = {bx0 * TT, by0 * TT, bzp * TZ};
+    const int tz_planes = min(TZ, M - t0[2]);           // 16, or 8 for the last tile of an odd nt
+    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+    const int nbin = (P - 1 + TT - 1) / TT + 1;
+    const int nbz = nbin + (tz_planes > TT ? 1 : 0);    // z-bins: the top bin of the tile and nbz - 1 below
+    const int bztop = 2 * bzp + (tz_planes > TT ? 1 : 0);
+    const int nb3 = nbin * nbin * nbz;
+    const float alpha = (float)p.alpha, kap = (float)p.kappa, akap = alpha * kap;
+    (void)ntz;
+    u64 acc2[TZ / 2][4];
+#pragma unroll
+    for (int z = 0; z < TZ / 2; ++z)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc2[z][c] = 0ull;
+
+    for (int bb = threadIdx.x; bb < nb3; bb += blockDim.x) {
+        const int bx = bb % nbin, by = (bb / nbin) % nbin, bz = bb / (nbin * nbin);
+        const int bin = (wrapi(bztop - bz, nt) * nt + wrapi(by0 - by, nt)) * nt + wrapi(bx0 - bx, nt);
+        bin_beg[bb] = tile_start[bin];
+        bin_off[bb + 1] = tile_start[bin + 1] - tile_start[bin];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bin_off[0] = 0;
+        for (int bb = 0; bb < nb3; ++bb) bin_off[bb + 1] += bin_off[bb];
+    }
+    __syncthreads();
+    const int total = bin_off[nb3];
+
+    int cbeg = 0, cstep = CH;
+    if constexpr (SPLIT) {
+        grid += (size_t)blockIdx.y * M * M * M * 4;
+        cbeg = blockIdx.y * CH;
+        cstep = nsplit * CH;
+    }
+    for (int c0 = cbeg; c0 < total; c0 += cstep) {
+        const int cnt = min(CH, total - c0);
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            const int k = threadIdx.x, idx = c0 + k;
+            int lo = 0, hi = nb3;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (bin_off[mid] <= idx) lo = mid; else hi = mid;
+            }
+            const int i = tile_perm[bin_beg[lo] + idx - bin_off[lo]];
+            bool ok = true;
+            int od[3];
+            for (int d = 0; d < 3; ++d) {
+                int o = wrapi(t0[d] - base[3 * i + d], M);
+                if (o >= P) o -= M;
+                ok &= (o < P) && (o > -(d == 2 ? TZ : TT));
+                od[d] = o;
+            }
+            const float *w = wg + (size_t)i * 3 * P;
+            const int sw_xy = (k >> 1) & 15, sw_z = k & 7;
+#pragma unroll
+            for (int t = 0; t < TT; ++t) {
+                const int ix = od[0] + t, iy = od[1] + t;
+                sxy[k][t ^ sw_xy] = (ix >= 0 && ix < P) ? w[ix] : 0.f;
+                sxy[k][(TT + t) ^ sw_xy] = (iy >= 0 && iy < P) ? w[P + iy] : 0.f;
+            }
+            const float s0z = s0g[3 * i + 2];
+#pragma unroll
+            for (int zp = 0; zp < TZ / 2; ++zp) {
+                float4 W[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int iz = od[2] + 2 * zp + h;
+                    const float g = (iz >= 0 && iz < P) ? w[2 * P + iz] : 0.f;
+                    const float sz = s0z + (float)iz;
+                    W[h] = make_float4(g, g * sz, g * sz * sz, g * sz * sz * sz);
+                }
+                swz[k][(2 * zp) ^ sw_z] = make_float4(W[0].x, W[1].x, W[0].y, W[1].y);
+                swz[k][(2 * zp + 1) ^ sw_z] = make_float4(W[0].z, W[1].z, W[0].w, W[1].w);
+            }
+            const float a = (float)rad[i], a2k2 = a * a * kap * kap;
+            const float *xi = xs + (size_t)i * kNC;
+            float S[6] = {0, 0, 0, 0, 0, 0}, Tq[3] = {0, 0, 0};
+            if constexpr (NCOMP >= 6) { Tq[0] = xi[3]; Tq[1] = xi[4]; Tq[2] = xi[5]; }
+            if constexpr (NCOMP >= 11) stresslet_tensor(xi + 6, S);
+            // quarters (4 planes each) of the tile that the support reaches
+            const int zlo = max(0, -od[2]), zhi = min(tz_planes, P - od[2]);
+            int quarters = 0;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq)
+                if (zlo < 4 * qq + 4 && zhi > 4 * qq) quarters |= 1 << qq;
+            sp[k][0] = make_float4(s0g[3 * i] + (float)od[0], s0g[3 * i + 1] + (float)od[1], 1 - a2k2 * alpha,
+                                   (2.0f / 3.0f) * a2k2 * alpha * alpha);
+            sp[k][1] = make_float4(2 * kap * alpha * (1 - a2k2 * alpha), 0.8f * kap * a2k2 * alpha * alpha * alpha,
+                                   ok ? (float)quarters : 0.f, NCOMP >= 12 ? xi[11] : 0.f);
+            sp[k][2] = make_float4(xi[0], xi[1], xi[2], Tq[0]);
+            sp[k][3] = make_float4(Tq[1], Tq[2], S[0], S[1]);
+            sp[k][4] = make_float4(S[2], S[3], S[4], S[5]);
+        }
+        __syncthreads();
+        for (int k = 0; k < cnt; ++k) {
+            const int sw_xy = (k >> 1) & 15, sw_z = k & 7;
+            const float gxy = sxy[k][tx ^ sw_xy] * sxy[k][(TT + ty) ^ sw_xy];
+            const float4 v1 = sp[k][1];
+            const int quarters = (int)v1.z;
+            if (gxy == 0.f || quarters == 0) continue;
+            const float4 v0 = sp[k][0], v2 = sp[k][2];
+            const float sx = v0.x + tx, sy = v0.y + ty;
+            const float sxy2 = sx * sx + sy * sy;
+            const float A1 = v0.w, a0 = v0.z + A1 * sxy2;
+            float c[3][4];
+            const float F[3] = {v2.x, v2.y, v2.z};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                c[q][0] = a0 * F[q];
+                c[q][1] = 0;
+                c[q][2] = A1 * F[q];
+                c[q][3] = 0;
+            }
+            if constexpr (NCOMP >= 6) {
+                const float4 v3 = sp[k][3];
+                const float T0 = v2.w, T1 = v3.x, T2 = v3.y;
+                c[0][0] -= akap * sy * T2;
+                c[1][0] += akap * sx * T2;
+                c[2][0] -= akap * (sx * T1 - sy * T0);
+                c[0][1] += akap * T1;
+                c[1][1] -= akap * T0;
+                if constexpr (NCOMP >= 11) {
+                    const float4 v4 = sp[k][4];
+                    const float S[6] = {v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
+                    const float B1 = v1.y, b0 = v1.x + B1 * sxy2;
+                    const float d00 = S[0] * sx + S[3] * sy, d01 = S[3] * sx + S[1] * sy, d02 = S[4] * sx + S[5] * sy;
+                    const float d10 = S[4], d11 = S[5], d12 = S[2];
+                    c[0][0] += b0 * d00; c[1][0] += b0 * d01; c[2][0] += b0 * d02;
+                    c[0][1] += b0 * d10; c[1][1] += b0 * d11; c[2][1] += b0 * d12;
+                    c[0][2] += B1 * d00; c[1][2] += B1 * d01; c[2][2] += B1 * d02;
+                    c[0][3] = B1 * d10; c[1][3] = B1 * d11; c[2][3] = B1 * d12;
+                }
+            }
+            constexpr int NE = NCOMP >= 11 ? 4 : (NCOMP >= 6 ? 3 : 2);
+            constexpr int ES[4] = {0, 2, 1, 3};       // the terms present: 0, 2 (F); 1 (T); 3 (S)
+            u64 cc[3][4];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float v = c[q][e] * gxy;
+                    cc[q][e] = pack2(v, v);
+                }
+            const float csv = NCOMP >= 12 ? gxy * v1.w : 0.f;
+            const u64 cs = pack2(csv, csv);
+            auto quarter = [&](auto q0c) {
+                constexpr int zq = decltype(q0c)::value;
+#pragma unroll
+                for (int zp = 2 * zq; zp < 2 * zq + 2; ++zp) {
+                    const ulonglong2 wa = *reinterpret_cast<const ulonglong2 *>(&swz[k][(2 * zp) ^ sw_z]);
+                    const ulonglong2 wb = *reinterpret_cast<const ulonglong2 *>(&swz[k][(2 * zp + 1) ^ sw_z]);
+                    const u64 Wp[4] = {wa.x, wa.y, wb.x, wb.y};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int j = 0; j < NE; ++j) acc2[zp][q] = ffma2(cc[q][ES[j]], Wp[ES[j]], acc2[zp][q]);
+                    if constexpr (NCOMP >= 12) acc2[zp][3] = ffma2(cs, Wp[0], acc2[zp][3]);
+                }
+            };
+            if (quarters & 1) quarter(std::integral_constant<int, 0>{});
+            if (quarters & 2) quarter(std::integral_constant<int, 1>{});
+            if (quarters & 4) quarter(std::integral_constant<int, 2>{});
+            if (quarters & 8) quarter(std::integral_constant<int, 3>{});
+        }
+    }
+#pragma unroll
+    for (int zp = 0; zp < TZ / 2; ++zp) {
+        float lo[4], hi[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) unpack2(acc2[zp][q], lo[q], hi[q]);
+        const int z = 2 * zp;
+        if (z < tz_planes) {
+            const size_t gi = (((size_t)(t0[2] + z) * M + (t0[1] + ty)) * M + (t0[0] + tx)) * 4;
+            *reinterpret_cast<float4 *>(grid + gi) = make_float4(lo[0], lo[1], lo[2], NCOMP >= 12 ? lo[3] : 0.f);
+            *reinterpret_cast<float4 *>(grid + gi + (size_t)M * M * 4) =
+                make_float4(hi[0], hi[1], hi[2], NCOMP >= 12 ? hi[3] : 0.f);
+        }
+    }
+}
+
 // Self coefficients of particle i (FP64, once per configuration): the isolated sphere
 // (Eqs. faxen-f/t/s/p: 1/(6 pi eta a), 1/(8 pi eta a^3), 3/(20 pi eta a^3),
 // 3/(16 pi eta a^3)) minus the self term that the wave-space sum contains (Eq. uf-self
@@ -1093,9 +1319,53 @@ void setup_support(se_ctx *c, cudaStream_t s)
     cudaFree(de3);
 }
 
+// whether spread16_kernel applies: FP32, and the nbin + 1 z-bins of a 16-plane tile
+// are distinct bins of the grid
+static bool use_spread16(const se_ctx *c, const SeParams &p, bool fp32)
+{
+    const int nbin = (p.P - 1 + kTile - 1) / kTile + 1;
+    return fp32 && c->spread == 0 && nbin + 1 <= p.ntile;
+}
+
+static void launch_spread16(se_ctx *c, const SeParams &p, const float *xs, cudaStream_t s, int ncomp)
+{
+    const int nt = p.ntile, ntiles = nt * nt * ((nt + 1) / 2);
+    // partial grids only where the tiles alone leave SMs idle (at most the allocated parts)
+    const int ns = std::min(c->nsplit, std::max(1, (2 * kSMs * 8 + ntiles - 1) / ntiles));
+    float *out = ns > 1 ? (float *)c->b.grid_part[0] : (float *)c->b.grid_f[0];
+    auto args = [&](auto kern) {
+        kern<<<dim3(ntiles, ns), 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
+                                              (const float *)c->b.sup_s0[0], (const float *)c->b.sup_w[0], c->b.rad,
+                                              xs, out, ns);
+    };
+    if (ns > 1) {
+        if (ncomp <= 3) args(spread16_kernel<3, true>);
+        else if (ncomp <= 6) args(spread16_kernel<6, true>);
+        else if (ncomp <= 11) args(spread16_kernel<11, true>);
+        else args(spread16_kernel<12, true>);
+    } else {
+        if (ncomp <= 3) args(spread16_kernel<3, false>);
+        else if (ncomp <= 6) args(spread16_kernel<6, false>);
+        else if (ncomp <= 11) args(spread16_kernel<11, false>);
+        else args(spread16_kernel<12, false>);
+    }
+    c->launches++;
+    if (ns > 1) {
+        const size_t n4 = (size_t)p.M * p.M * p.M;
+        sum_parts_kernel<float><<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(n4, ns, out, (float *)c->b.grid_f[0]);
+        c->launches++;
+    }
+}
+
 template <typename T>
 static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_t s, int ncomp)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_spread16(c, p, true)) {
+            launch_spread16(c, p, xs, s, ncomp);
+            return;
+        }
+    }
     const int nt = p.ntile, ntiles = nt * nt * nt, ns = c->nsplit;
     T *out = ns > 1 ? (T *)c->b.grid_part[pix<T>()] : (T *)c->b.grid_f[pix<T>()];
     auto args = [&](auto kern) {

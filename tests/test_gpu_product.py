@@ -267,3 +267,22 @@ def test_cutoff_boundary_pairs(oracle_mod, precision):
     y = gpu_apply(ctx, x, dtype=torch.float64 if precision else torch.float32)
     assert np.all(y[0::2][~inside] == 0) and np.all(y[1::2][~inside] == 0)
     assert rel(y[:, :11], ref[:, :11]) <= (1e-12 if precision else 2e-6)
+
+
+@pytest.mark.parametrize("M,P", [(216, 24), (72, 24), (48, 16), (48, 32), (24, 8), (24, 12)])
+@pytest.mark.parametrize("ncomp", [3, 6, 11, 12])
+def test_spread_variants_agree(small_poly, small_poly_ref, M, P, ncomp):
+    """FP32 spreading over 8 x 8 x 16 tiles with packed FMAs (the default where the grid
+    has room for it: M = 72 and 216 leave a last tile of 8 planes, M = 48 and 24 split the
+    tiles' particles over partial grids, M = 24 with P = 12 falls back) against 8^3 tiles
+    (SE_OPT_SPREAD 1): the same terms in another order, so they agree to FP32 rounding."""
+    cfg, x = small_poly
+    x = x[:, :ncomp].copy()
+    out = {}
+    for s in (0, 1):
+        ctx = make_ctx(0.9, M, P, 5.4, cfg, precision=0)
+        ctx.set_option(api.SE_OPT_SPREAD, s)
+        out[s] = gpu_apply(ctx, x, dtype=torch.float32)
+    assert rel(out[0], out[1]) <= 2e-6
+    if M == 72 and ncomp == 12:
+        assert rel(out[0], small_poly_ref) <= 1e-5
