@@ -207,15 +207,28 @@ int se_mlp_adam_step(float *w, float *m, float *v, const float *grad, int step, 
  * runs box i on the i-th (mod nstreams) of nstreams streams it creates, forked from
  * and joined back to `stream`.
  * se_batch_apply enqueues y[i] = M_inf(box i) . x[i] for every box (DEVICE arrays
- * [N_i][ncomp] of `dtype`).  With use_graph = 1 the first call (and any call with other
- * pointers, ncomp or dtype) runs the batch once eagerly, captures it into one CUDA graph
- * and launches it; later calls only launch the graph.  With use_graph = 0 every box's
- * kernels are launched one by one.  Asynchronous on `stream`; errors as for
- * se_mobility_apply, described by se_batch_last_error. */
+ * [N_i][ncomp] of `dtype`).  use_graph selects how:
+ *   0  every box's kernels are launched one by one (box i on stream i mod nstreams);
+ *   1  the first call (and any call with other pointers, ncomp or dtype) runs the batch
+ *      once eagerly, captures it into one CUDA graph and launches it; later calls only
+ *      launch the graph;
+ *   2  ONE persistent cooperative launch computes every box (FP32 boxes with their
+ *      stored pair tables): eight phases (inputs, real space + spreading, five FFT
+ *      passes with the k-space scaling, gather), each a list of work items over all
+ *      boxes claimed by the CTAs through a counter, separated by grid barriers.  The
+ *      first call runs the batch eagerly and prepares the launch (captured into a graph
+ *      when the runtime allows); later calls make the one launch.  A CTA that waits
+ *      more than about two seconds at a barrier aborts the launch; se_batch_status
+ *      reports it.
+ * Asynchronous on `stream`; errors as for se_mobility_apply (SE_ERR_STATE when a box
+ * does not meet mode 2's conditions), described by se_batch_last_error.
+ * se_batch_status synchronises `stream` and returns SE_ERR_CUDA if a persistent launch
+ * since the previous call was aborted, else SE_OK. */
 typedef struct se_batch se_batch;
 int se_batch_create(se_batch **out, se_ctx *const *ctx, int nbox, int nstreams, void *stream);
 int se_batch_apply(se_batch *b, int ncomp, const void *const *x, void *const *y, int dtype, int use_graph);
 int se_batch_destroy(se_batch *b);
+int se_batch_status(se_batch *b);
 const char *se_batch_last_error(const se_batch *b);
 
 /* Message describing the last failure on this context ("" if none).  Valid until the

@@ -39,7 +39,7 @@ ABI_SYMBOLS = ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_
                "se_kernel_launches", "se_stage_times", "se_real_space_apply_noalloc",
                "se_set_learned_weights", "se_learned_features", "se_mlp_forward", "se_mlp_grad",
                "se_mlp_adam_step", "se_batch_create", "se_batch_apply", "se_batch_destroy",
-               "se_batch_last_error")
+               "se_batch_last_error", "se_batch_status")
 SE_MLP_NW, SE_MLP_NTRAIN, SE_MLP_SAMPLE = 5544, 5508, 276
 
 _lib = None
@@ -89,7 +89,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.se_batch_destroy.argtypes = [p]
     lib.se_batch_last_error.argtypes = [p]
     lib.se_batch_last_error.restype = ctypes.c_char_p
-    for name in ("se_batch_create", "se_batch_apply", "se_batch_destroy"):
+    lib.se_batch_status.argtypes = [p]
+    for name in ("se_batch_create", "se_batch_apply", "se_batch_destroy", "se_batch_status"):
         getattr(lib, name).restype = i
     for name in ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
                  "se_mobility_apply", "se_mobility_apply_host", "se_solve"):
@@ -306,11 +307,23 @@ class Batch:
             raise SeError(rc, "se_batch_create failed")
         self.h = h
 
-    def apply(self, xs, ys, use_graph: bool = True):
+    # se_batch_apply modes
+    PER_BOX, GRAPH, PERSISTENT = 0, 1, 2
+
+    def apply(self, xs, ys, use_graph=True):
+        """use_graph: False/0 per-box launches, True/1 one CUDA graph of the boxes' kernels,
+        2 one persistent launch for every box (Batch.PERSISTENT)."""
         ncomp = xs[0].shape[-1]
         xa = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
         ya = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
-        rc = self.lib.se_batch_apply(self.h, int(ncomp), xa, ya, _dtype_code(xs[0]), int(bool(use_graph)))
+        mode = int(use_graph) if not isinstance(use_graph, bool) else int(use_graph)
+        rc = self.lib.se_batch_apply(self.h, int(ncomp), xa, ya, _dtype_code(xs[0]), mode)
+        if rc != SE_OK:
+            raise SeError(rc, self.lib.se_batch_last_error(self.h).decode())
+
+    def status(self):
+        """Synchronises; raises if a persistent launch since the last call was aborted."""
+        rc = self.lib.se_batch_status(self.h)
         if rc != SE_OK:
             raise SeError(rc, self.lib.se_batch_last_error(self.h).decode())
 

@@ -18,8 +18,11 @@ struct se_batch {
     cudaStream_t cap = nullptr;                  // owned: the graph is captured on it
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    // what the graph was captured for
-    int g_ncomp = 0, g_dtype = -1;
+    // the persistent launch (mode 2): its plan, and whether the graph holds it
+    se::PersistPlan pp;
+    bool pp_ok = false;
+    // what the graph was captured for (mode 1 or 2)
+    int g_mode = 0, g_ncomp = 0, g_dtype = -1;
     std::vector<const void *> g_x;
     std::vector<void *> g_y;
     std::string err;
@@ -65,7 +68,9 @@ extern "C" int se_batch_destroy(se_batch *b)
     if (!b) return SE_OK;
     cudaSetDevice(b->device);
     for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
+    if (b->main) cudaStreamSynchronize(b->main);
     batch_drop_graph(b);
+    se::persist_free(b->pp);
     for (size_t q = 0; q < b->streams.size(); ++q) {
         if (b->join[q]) cudaEventDestroy(b->join[q]);
         if (b->streams[q]) cudaStreamDestroy(b->streams[q]);
@@ -105,20 +110,68 @@ static int batch_enqueue(se_batch *b, cudaStream_t root, int ncomp, const void *
     return SE_OK;
 }
 
+// mode 2: one persistent launch for all boxes, captured into the batch's graph when the
+// runtime accepts the capture of a cooperative launch, else launched directly
+static int batch_persistent(se_batch *b, int ncomp, const void *const *x, void *const *y, int dtype)
+{
+    const size_t n = b->box.size();
+    bool same = b->pp_ok && b->pp.ncomp == ncomp && b->pp.dtype == dtype;
+    for (size_t i = 0; same && i < n; ++i) same = b->g_x[i] == x[i] && b->g_y[i] == y[i];
+    if (!same) {
+        batch_drop_graph(b);
+        b->pp_ok = false;
+        // one eager pass sets up every box's tables and grids (and computes this step)
+        int rc = batch_enqueue(b, b->main, ncomp, x, y, dtype);
+        if (rc != SE_OK) return rc;
+        SE_CUDA_CHECK(b, cudaStreamSynchronize(b->main));
+        rc = se::persist_prepare(b->box.data(), (int)n, ncomp, x, y, dtype, b->pp, b->err);
+        if (rc != SE_OK) return rc;
+        b->pp_ok = true;
+        b->g_mode = 2;
+        b->g_ncomp = ncomp;
+        b->g_dtype = dtype;
+        b->g_x.assign(x, x + n);
+        b->g_y.assign(y, y + n);
+        if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+            std::string e;
+            const int lr = se::persist_launch(b->pp, b->cap, e);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(b->cap, &g);
+            if (lr == SE_OK && ec == cudaSuccess && g && cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess) {
+                b->graph = g;
+            } else {
+                if (g) cudaGraphDestroy(g);
+                b->exec = nullptr;
+            }
+        }
+        cudaGetLastError();
+        return SE_OK;                 // this step was computed by the eager pass
+    }
+    b->box[0]->launches++;
+    if (b->exec) {
+        SE_CUDA_CHECK(b, cudaGraphLaunch(b->exec, b->main));
+        return SE_OK;
+    }
+    return se::persist_launch(b->pp, b->main, b->err);
+}
+
 extern "C" int se_batch_apply(se_batch *b, int ncomp, const void *const *x, void *const *y, int dtype,
                               int use_graph)
 {
     if (!b || !x || !y) return SE_ERR_ARG;
     if (ncomp != 3 && ncomp != 6 && ncomp != 11 && ncomp != 12) return SE_ERR_ARG;
     if (dtype != SE_F32 && dtype != SE_F64) return SE_ERR_ARG;
+    if (use_graph < 0 || use_graph > 2) return SE_ERR_ARG;
     const size_t n = b->box.size();
     for (size_t i = 0; i < n; ++i)
         if (!x[i] || !y[i]) return SE_ERR_ARG;
     cudaSetDevice(b->device);
     if (!use_graph) return batch_enqueue(b, b->main, ncomp, x, y, dtype);
-    bool same = b->exec && b->g_ncomp == ncomp && b->g_dtype == dtype;
+    if (use_graph == 2) return batch_persistent(b, ncomp, x, y, dtype);
+    bool same = b->exec && b->g_mode == 1 && b->g_ncomp == ncomp && b->g_dtype == dtype;
     for (size_t i = 0; same && i < n; ++i) same = b->g_x[i] == x[i] && b->g_y[i] == y[i];
     if (!same) {
+        b->pp_ok = false;
         batch_drop_graph(b);
         // one eager pass sets up every box's tables and grids outside the capture; the
         // capture runs on the batch's own stream (the caller's may be the legacy stream)
@@ -137,12 +190,25 @@ extern "C" int se_batch_apply(se_batch *b, int ncomp, const void *const *x, void
         }
         b->graph = g;
         SE_CUDA_CHECK(b, cudaGraphInstantiate(&b->exec, b->graph, 0));
+        b->g_mode = 1;
         b->g_ncomp = ncomp;
         b->g_dtype = dtype;
         b->g_x.assign(x, x + n);
         b->g_y.assign(y, y + n);
     }
     SE_CUDA_CHECK(b, cudaGraphLaunch(b->exec, b->main));
+    return SE_OK;
+}
+
+extern "C" int se_batch_status(se_batch *b)
+{
+    if (!b) return SE_ERR_ARG;
+    cudaSetDevice(b->device);
+    SE_CUDA_CHECK(b, cudaStreamSynchronize(b->main));
+    if (b->pp.ctl && se::persist_failed(b->pp, b->main)) {
+        b->err = "a persistent batch launch gave up waiting at a grid barrier";
+        return SE_ERR_CUDA;
+    }
     return SE_OK;
 }
 

@@ -178,6 +178,22 @@ template <typename T>
 void setup_support(se_ctx *c, cudaStream_t s);
 void make_twiddles(se_ctx *c, int prec);
 
+// se_wave.cu: one persistent launch for the products of a batch of boxes (FP32)
+struct PersistPlan {
+    void *desc = nullptr;        // device BoxDesc[nbox]
+    int *pref = nullptr;         // device [kPersistPhases][nbox + 1] work-item prefix sums
+    unsigned *ctl = nullptr;     // device: barrier count, generation, work counters, status (2)
+    int nbox = 0, ncomp = 0, dtype = -1, grid = 0;
+    size_t smem = 0;
+    const void *kernel = nullptr;
+};
+int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *x, void *const *y, int dtype,
+                    PersistPlan &pl, std::string &err);
+int persist_launch(const PersistPlan &pl, cudaStream_t s, std::string &err);
+// 1 if a persistent launch since the last call gave up at a grid barrier (synchronises)
+int persist_failed(const PersistPlan &pl, cudaStream_t s);
+void persist_free(PersistPlan &pl);
+
 // se_api.cu
 template <typename T, typename TI>
 void launch_permute_in(se_ctx *c, const TI *x, T *xs, int ncomp, cudaStream_t s);

@@ -104,27 +104,35 @@ __global__ void support_kernel(int N, SeParams p, const double *pos, const doubl
 // (Eq. grid-space with the torque and stresslet terms):
 //   H = g [ (A0 + A1 s^2) F - alpha kappa (s x T) + (B0 + B1 s^2) S.s ],  H_src = g S_tr,
 // so a thread forms 13 column coefficients per particle and spends 13 FMAs per point.
-template <typename T, int NCOMP, bool SPLIT>
-__global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeParams p, const int *tile_start,
-                                                    const int *tile_perm, const int *base,
-                                                    const T *s0g, const T *wg, const double *rad,
-                                                    const T *xs, T *grid, int nsplit)
+// Shared staging of spread_body (rows are XOR-swizzled by the particle slot so that the
+// staging writes, one particle per thread, spread over all banks; reads broadcast one
+// particle's row; per particle sp holds (sx0 sy0 A0 A1) (B0 B1 halves Str)
+// (F0 F1 F2 T0) (T1 T2 Sxx Syy) (Szz Sxy Sxz Syz) as broadcast vectors)
+template <typename T> struct Spread8Smem {
+    T sxy[64][2 * kTile];                  // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
+    typename V4<T>::t swz[64][kTile];      // g_z (1, s_z, s_z^2, s_z^3) of plane t at t ^ (k & 7)
+    typename V4<T>::t sp[64][5];
+    int bin_beg[125], bin_off[126];
+};
+
+// The tile's work for 64 threads (tid 0..63, sync() a barrier of those 64 threads).
+template <typename T, int NCOMP, bool SPLIT, typename Sync>
+__device__ __forceinline__ void spread_body(int tile, int part, int tid, Sync sync, Spread8Smem<T> &sm, SeParams p,
+                                            const int *tile_start, const int *tile_perm, const int *base,
+                                            const T *s0g, const T *wg, const double *rad, const T *xs, T *grid,
+                                            int nsplit)
 {
-    constexpr int TT = kTile, CH = 64, MAXB = 125;
+    constexpr int TT = kTile, CH = 64;
     using T4 = typename V4<T>::t;
-    // rows are XOR-swizzled by the particle slot so that the staging writes (one
-    // particle per thread) spread over all banks; reads broadcast one particle's row
-    __shared__ T sxy[CH][2 * TT];     // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
-    __shared__ T4 swz[CH][TT];        // g_z (1, s_z, s_z^2, s_z^3) of plane t at t ^ (k & 7)
-    // per particle, read as broadcast vectors: (sx0 sy0 A0 A1) (B0 B1 halves Str)
-    // (F0 F1 F2 T0) (T1 T2 Sxx Syy) (Szz Sxy Sxz Syz)
-    __shared__ T4 sp[CH][5];
-    __shared__ int bin_beg[MAXB], bin_off[MAXB + 1];
+    auto &sxy = sm.sxy;
+    auto &swz = sm.swz;
+    auto &sp = sm.sp;
+    auto &bin_beg = sm.bin_beg;
+    auto &bin_off = sm.bin_off;
     const int M = p.M, P = p.P, nt = p.ntile;
-    const int tile = blockIdx.x;
     const int bx0 = tile % nt, by0 = (tile / nt) % nt, bz0 = tile / (nt * nt);
     const int t0[3] = {bx0 * TT, by0 * TT, bz0 * TT};
-    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+    const int tx = tid & 7, ty = tid >> 3;
     const int nbin = (P - 1 + TT - 1) / TT + 1, nb3 = nbin * nbin * nbin;
     const T alpha = (T)p.alpha, kap = (T)p.kappa, akap = alpha * kap;
     constexpr int NA = NCOMP >= 12 ? 4 : 3;
@@ -135,33 +143,33 @@ __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeP
         for (int c = 0; c < NA; ++c) acc[z][c] = 0;
 
     // candidate list: bins (tile - b) for b in [0, nbin)^3, concatenated
-    for (int bb = threadIdx.x; bb < nb3; bb += blockDim.x) {
+    for (int bb = tid; bb < nb3; bb += CH) {
         const int bx = bb % nbin, by = (bb / nbin) % nbin, bz = bb / (nbin * nbin);
         const int bin = (wrapi(bz0 - bz, nt) * nt + wrapi(by0 - by, nt)) * nt + wrapi(bx0 - bx, nt);
         bin_beg[bb] = tile_start[bin];
         bin_off[bb + 1] = tile_start[bin + 1] - tile_start[bin];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    sync();
+    if (tid == 0) {
         bin_off[0] = 0;
         for (int bb = 0; bb < nb3; ++bb) bin_off[bb + 1] += bin_off[bb];
     }
-    __syncthreads();
+    sync();
     const int total = bin_off[nb3];
 
-    // SPLIT: part blockIdx.y of nsplit takes every nsplit-th chunk of the candidates
-    // and writes the partial grid blockIdx.y
+    // SPLIT: part `part` of nsplit takes every nsplit-th chunk of the candidates
+    // and writes the partial grid part
     int cbeg = 0, cstep = CH;
     if constexpr (SPLIT) {
-        grid += (size_t)blockIdx.y * M * M * M * 4;
-        cbeg = blockIdx.y * CH;
+        grid += (size_t)part * M * M * M * 4;
+        cbeg = part * CH;
         cstep = nsplit * CH;
     }
     for (int c0 = cbeg; c0 < total; c0 += cstep) {
         const int cnt = min(CH, total - c0);
-        __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const int k = threadIdx.x, idx = c0 + k;
+        sync();
+        if ((int)tid < cnt) {
+            const int k = tid, idx = c0 + k;
             int lo = 0, hi = nb3;                       // bin_off[lo] <= idx < bin_off[lo + 1]
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
@@ -205,7 +213,7 @@ __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeP
             sp[k][3] = T4{Tq[1], Tq[2], S[0], S[1]};
             sp[k][4] = T4{S[2], S[3], S[4], S[5]};
         }
-        __syncthreads();
+        sync();
         for (int k = 0; k < cnt; ++k) {
             const int sw_xy = (k >> 1) & 15, sw_z = k & 7;
             const T gxy = sxy[k][tx ^ sw_xy] * sxy[k][(TT + ty) ^ sw_xy];
@@ -287,6 +295,17 @@ __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeP
     }
 }
 
+template <typename T, int NCOMP, bool SPLIT>
+__global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeParams p, const int *tile_start,
+                                                    const int *tile_perm, const int *base,
+                                                    const T *s0g, const T *wg, const double *rad,
+                                                    const T *xs, T *grid, int nsplit)
+{
+    __shared__ Spread8Smem<T> sm;
+    spread_body<T, NCOMP, SPLIT>(blockIdx.x, blockIdx.y, threadIdx.x, [] { __syncthreads(); }, sm, p, tile_start,
+                                 tile_perm, base, s0g, wg, rad, xs, grid, nsplit);
+}
+
 // ---- FP32 spreading over 8 x 8 x 16 tiles with packed FMAs
 //
 // The same column scheme as spread_kernel with tiles of 16 planes: a thread's column
@@ -317,60 +336,66 @@ __device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
 
 constexpr int kTz = 16;    // planes per tile of spread16_kernel
 
-template <int NCOMP, bool SPLIT>
-__global__ void __launch_bounds__(64, 8) spread16_kernel(SeParams p, const int *tile_start, const int *tile_perm,
-                                                         const int *base, const float *s0g, const float *wg,
-                                                         const double *rad, const float *xs, float *grid, int nsplit)
+struct Spread16Smem {
+    float sxy[64][2 * kTile];   // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
+    float4 swz[64][kTz];        // unit 2 zp + h: (W_2zp, W_2zp+1) of e = 2h, 2h + 1; at unit ^ (k & 7)
+    float4 sp[64][5];
+    int bin_beg[6 * 6 * 7], bin_off[6 * 6 * 7 + 1];
+};
+
+template <int NCOMP, bool SPLIT, typename Sync>
+__device__ __forceinline__ void spread16_body(int tile, int part, int tid, Sync sync, Spread16Smem &sm, SeParams p,
+                                              const int *tile_start, const int *tile_perm, const int *base,
+                                              const float *s0g, const float *wg, const double *rad, const float *xs,
+                                              float *grid, int nsplit)
 {
-    constexpr int TT = kTile, TZ = kTz, CH = 64, MAXB = 6 * 6 * 7;
-    __shared__ float sxy[CH][2 * TT];   // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
-    __shared__ float4 swz[CH][TZ];      // unit 2 zp + h: (W_2zp, W_2zp+1) of e = 2h, 2h + 1; at unit ^ (k & 7)
-    __shared__ float4 sp[CH][5];
-    __shared__ int bin_beg[MAXB], bin_off[MAXB + 1];
+    constexpr int TT = kTile, TZ = kTz, CH = 64;
+    auto &sxy = sm.sxy;
+    auto &swz = sm.swz;
+    auto &sp = sm.sp;
+    auto &bin_beg = sm.bin_beg;
+    auto &bin_off = sm.bin_off;
     const int M = p.M, P = p.P, nt = p.ntile;
-    const int ntz = (nt + 1) / 2;
-    const int tile = blockIdx.x;
     const int bx0 = tile % nt, by0 = (tile / nt) % nt, bzp = tile / (nt * nt);
     const int t0[3] = {bx0 * TT, by0 * TT, bzp * TZ};
     const int tz_planes = min(TZ, M - t0[2]);           // 16, or 8 for the last tile of an odd nt
-    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+    const int tx = tid & 7, ty = tid >> 3;
     const int nbin = (P - 1 + TT - 1) / TT + 1;
     const int nbz = nbin + (tz_planes > TT ? 1 : 0);    // z-bins: the top bin of the tile and nbz - 1 below
     const int bztop = 2 * bzp + (tz_planes > TT ? 1 : 0);
     const int nb3 = nbin * nbin * nbz;
     const float alpha = (float)p.alpha, kap = (float)p.kappa, akap = alpha * kap;
-    (void)ntz;
     u64 acc2[TZ / 2][4];
 #pragma unroll
     for (int z = 0; z < TZ / 2; ++z)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc2[z][c] = 0ull;
 
-    for (int bb = threadIdx.x; bb < nb3; bb += blockDim.x) {
+    for (int bb = tid; bb < nb3; bb += CH) {
         const int bx = bb % nbin, by = (bb / nbin) % nbin, bz = bb / (nbin * nbin);
         const int bin = (wrapi(bztop - bz, nt) * nt + wrapi(by0 - by, nt)) * nt + wrapi(bx0 - bx, nt);
         bin_beg[bb] = tile_start[bin];
         bin_off[bb + 1] = tile_start[bin + 1] - tile_start[bin];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    sync();
+    if (tid == 0) {
         bin_off[0] = 0;
         for (int bb = 0; bb < nb3; ++bb) bin_off[bb + 1] += bin_off[bb];
     }
-    __syncthreads();
+    sync();
     const int total = bin_off[nb3];
 
     int cbeg = 0, cstep = CH;
     if constexpr (SPLIT) {
-        grid += (size_t)blockIdx.y * M * M * M * 4;
-        cbeg = blockIdx.y * CH;
+        grid += (size_t)part * M * M * M * 4;
+        cbeg = part * CH;
         cstep = nsplit * CH;
     }
     for (int c0 = cbeg; c0 < total; c0 += cstep) {
         const int cnt = min(CH, total - c0);
-        __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const int k = threadIdx.x, idx = c0 + k;
+        sync();
+        if ((int)tid < cnt) {
+            const int k = tid, idx = c0 + k;
             int lo = 0, hi = nb3;
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
@@ -426,7 +451,7 @@ __global__ void __launch_bounds__(64, 8) spread16_kernel(SeParams p, const int *
             sp[k][3] = make_float4(Tq[1], Tq[2], S[0], S[1]);
             sp[k][4] = make_float4(S[2], S[3], S[4], S[5]);
         }
-        __syncthreads();
+        sync();
         for (int k = 0; k < cnt; ++k) {
             const int sw_xy = (k >> 1) & 15, sw_z = k & 7;
             const float gxy = sxy[k][tx ^ sw_xy] * sxy[k][(TT + ty) ^ sw_xy];
@@ -513,6 +538,16 @@ __global__ void __launch_bounds__(64, 8) spread16_kernel(SeParams p, const int *
     }
 }
 
+template <int NCOMP, bool SPLIT>
+__global__ void __launch_bounds__(64, 8) spread16_kernel(SeParams p, const int *tile_start, const int *tile_perm,
+                                                         const int *base, const float *s0g, const float *wg,
+                                                         const double *rad, const float *xs, float *grid, int nsplit)
+{
+    __shared__ Spread16Smem sm;
+    spread16_body<NCOMP, SPLIT>(blockIdx.x, blockIdx.y, threadIdx.x, [] { __syncthreads(); }, sm, p, tile_start,
+                                tile_perm, base, s0g, wg, rad, xs, grid, nsplit);
+}
+
 // Self coefficients of particle i (FP64, once per configuration): the isolated sphere
 // (Eqs. faxen-f/t/s/p: 1/(6 pi eta a), 1/(8 pi eta a^3), 3/(20 pi eta a^3),
 // 3/(16 pi eta a^3)) minus the self term that the wave-space sum contains (Eq. uf-self
@@ -562,28 +597,31 @@ constexpr int kFftThreads = 256;
 
 // shared layout of a pass: twiddles [M], two line buffers [NLB (M + 2)]
 template <typename T2>
-__device__ __forceinline__ void fft_smem(int M, int NLB, T2 *&tw, T2 *&A, T2 *&B)
+__device__ __forceinline__ void fft_smem(unsigned char *sm, int M, int NLB, T2 *&tw, T2 *&A, T2 *&B)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    tw = reinterpret_cast<T2 *>(smraw);
+    tw = reinterpret_cast<T2 *>(sm);
     A = tw + ((M + 1) & ~1);
     B = A + (size_t)NLB * (M + 2);
 }
+
+// The passes below are device functions of (CTA index, shared buffer) so that the
+// persistent batched kernel runs the same code; each __global__ wrapper passes its
+// blockIdx and dynamic shared memory.
 
 // x pass, forward: each grid row (y, z) carries 4 real series packed as two complex
 // lines (H0 + i H1, H2 + i H3); after the transform the four half spectra
 // q = 0..M/2 are separated using Z(-q) = conj(Z(q)) of real data.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads, 4) fft_x_fwd(FftPlan plan, const typename C2<T>::t *twg,
-                                                            const T *grid, typename C2<T>::t *spec)
+__device__ __forceinline__ void fft_x_fwd_body(int bx, unsigned char *sm, const FftPlan &plan,
+                                               const typename C2<T>::t *twg, const T *grid, typename C2<T>::t *spec)
 {
     using T2 = typename C2<T>::t;
     constexpr int NL = fft_nl<T>(), NR = NL / 2;          // complex lines, grid rows
     const int M = plan.M, Mh = M / 2 + 1;
     T2 *tw, *A, *B;
-    fft_smem(M, NL, tw, A, B);
+    fft_smem(sm, M, NL, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
-    const size_t row0 = (size_t)blockIdx.x * NR;
+    const size_t row0 = (size_t)bx * NR;
     if constexpr (sizeof(T) == 4) {
         // one float4 (H0..H3) of row r at x -> lines 2r, 2r + 1 at element x
         for (int e = threadIdx.x; e < NR * M; e += blockDim.x) {
@@ -609,20 +647,28 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_x_fwd(FftPlan plan, const 
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, 4) fft_x_fwd(FftPlan plan, const typename C2<T>::t *twg,
+                                                            const T *grid, typename C2<T>::t *spec)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    fft_x_fwd_body<T>(blockIdx.x, smraw, plan, twg, grid, spec);
+}
+
 // y pass (forward or inverse) in place on half spectra [z][y][q][C]: a CTA takes the
 // NL / C wave numbers q0.. of one z plane, all C components, lines along y.
 template <typename T, int C, bool INV>
-__global__ void __launch_bounds__(kFftThreads, 4) fft_y(FftPlan plan, const typename C2<T>::t *twg,
-                                                        typename C2<T>::t *data)
+__device__ __forceinline__ void fft_y_body(int bx, int by, unsigned char *sm, const FftPlan &plan,
+                                           const typename C2<T>::t *twg, typename C2<T>::t *data)
 {
     using T2 = typename C2<T>::t;
     constexpr int NL = fft_nl<T>(), LB = NL / C, CPE = sizeof(T) == 4 ? 2 : 1;   // complex per copy
     const int M = plan.M, Mh = M / 2 + 1;
     T2 *tw, *A, *B;
-    fft_smem(M, NL, tw, A, B);
+    fft_smem(sm, M, NL, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
-    const int q0 = blockIdx.x * LB, nv = min(LB, Mh - q0) * C;     // valid lines
-    const size_t base = ((size_t)blockIdx.y * M * Mh + q0) * C, es = (size_t)Mh * C;
+    const int q0 = bx * LB, nv = min(LB, Mh - q0) * C;     // valid lines
+    const size_t base = ((size_t)by * M * Mh + q0) * C, es = (size_t)Mh * C;
     for (int e = threadIdx.x; e < (NL / CPE) * M; e += blockDim.x) {
         const int k = e % (NL / CPE), y = e / (NL / CPE);
         T2 *d = A + y * NL + k * CPE;
@@ -639,25 +685,32 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_y(FftPlan plan, const type
     }
 }
 
+template <typename T, int C, bool INV>
+__global__ void __launch_bounds__(kFftThreads, 4) fft_y(FftPlan plan, const typename C2<T>::t *twg,
+                                                        typename C2<T>::t *data)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    fft_y_body<T, C, INV>(blockIdx.x, blockIdx.y, smraw, plan, twg, data);
+}
+
 // z pass: forward transform of the 4 spectra, k-space scaling (see the file
 // header), inverse transform of the CO output spectra.  A CTA takes LB wave numbers
 // q0.. of one y row (LB = 4 for FP32 and 2 for FP64 while the buffers fit in shared
 // memory); input lines q * 4 + c, output lines q * CO + c (the component order of the
 // arrays in HBM).
 template <typename T, int CO, int LB>
-__global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, const typename C2<T>::t *twg,
-                                                              const typename C2<T>::t *specf,
-                                                              typename C2<T>::t *speco, T cnorm, T twopiL, T i4x2,
-                                                              T ecoef)
+__device__ __forceinline__ void fft_z_scale_body(int bx, int by, unsigned char *sm, const FftPlan &plan,
+                                                 const typename C2<T>::t *twg, const typename C2<T>::t *specf,
+                                                 typename C2<T>::t *speco, T cnorm, T twopiL, T i4x2, T ecoef)
 {
     using T2 = typename C2<T>::t;
     constexpr int NLI = 4 * LB, NLO = LB * CO, CPE = sizeof(T) == 4 ? 2 : 1;
     const int M = plan.M, Mh = M / 2 + 1;
     T2 *tw, *A, *B;
-    fft_smem(M, NLO, tw, A, B);
+    fft_smem(sm, M, NLO, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
-    const int y = blockIdx.y;
-    const int q0 = blockIdx.x * LB, nq = min(LB, Mh - q0);
+    const int y = by;
+    const int q0 = bx * LB, nq = min(LB, Mh - q0);
     const size_t zs = (size_t)M * Mh;                      // z stride in q units
     for (int e = threadIdx.x; e < (NLI / CPE) * M; e += blockDim.x) {
         const int k = e % (NLI / CPE), z = e / (NLI / CPE);
@@ -724,6 +777,16 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, cons
     }
 }
 
+template <typename T, int CO, int LB>
+__global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, const typename C2<T>::t *twg,
+                                                              const typename C2<T>::t *specf,
+                                                              typename C2<T>::t *speco, T cnorm, T twopiL, T i4x2,
+                                                              T ecoef)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    fft_z_scale_body<T, CO, LB>(blockIdx.x, blockIdx.y, smraw, plan, twg, specf, speco, cnorm, twopiL, i4x2, ecoef);
+}
+
 // z pass with a tabulated radial kernel in place of the Ewald one (the coarse spectral
 // correction of SE_PRECOND_SPECTRAL): forward z transform of the force spectra, the
 // transverse projection times h(|k|) for |k| <= kmax (zero beyond), the window
@@ -738,8 +801,9 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_z_table(FftPlan plan, cons
     using T2 = typename C2<T>::t;
     constexpr int NLI = 4 * LB, CO = 4, NLO = LB * CO, CPE = sizeof(T) == 4 ? 2 : 1;
     const int M = plan.M, Mh = M / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
     T2 *tw, *A, *B;
-    fft_smem(M, NLO, tw, A, B);
+    fft_smem(smraw, M, NLO, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
     const int y = blockIdx.y;
     const int q0 = blockIdx.x * LB, nq = min(LB, Mh - q0);
@@ -801,16 +865,16 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_z_table(FftPlan plan, cons
 // Z = A + i B (A(M-q) = conj A(q) for real output), transformed, and written as the
 // real grids A, B interleaved per point.
 template <typename T, int CO>
-__global__ void __launch_bounds__(kFftThreads, 4) fft_x_inv(FftPlan plan, const typename C2<T>::t *twg,
-                                                            const typename C2<T>::t *speco, T *grid)
+__device__ __forceinline__ void fft_x_inv_body(int bx, unsigned char *sm, const FftPlan &plan,
+                                               const typename C2<T>::t *twg, const typename C2<T>::t *speco, T *grid)
 {
     using T2 = typename C2<T>::t;
     constexpr int NL = fft_nl<T>(), NP = CO / 2, NR = NL / NP, CPE = sizeof(T) == 4 ? 2 : 1;
     const int M = plan.M, Mh = M / 2 + 1;
     T2 *tw, *A, *B;
-    fft_smem(M, NL, tw, A, B);
+    fft_smem(sm, M, NL, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
-    const size_t row0 = (size_t)blockIdx.x * NR;
+    const size_t row0 = (size_t)bx * NR;
     // the NR rows of half spectra are contiguous in HBM: stage them raw in B
     const int nraw = NR * Mh * CO;
     const T2 *src = speco + row0 * Mh * CO;
@@ -842,6 +906,14 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_x_inv(FftPlan plan, const 
             g[2 * pp + 1] = s[pp].y;
         }
     }
+}
+
+template <typename T, int CO>
+__global__ void __launch_bounds__(kFftThreads, 4) fft_x_inv(FftPlan plan, const typename C2<T>::t *twg,
+                                                            const typename C2<T>::t *speco, T *grid)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    fft_x_inv_body<T, CO>(blockIdx.x, smraw, plan, twg, speco, grid);
 }
 
 // ---------------------------------------------------------------- gather + combine
@@ -910,20 +982,16 @@ __device__ __forceinline__ void combine_write(const SeParams &p, const T (&acc)[
 // (13 FMAs per grid point) and converts the column moments into the 13 outputs
 // U(3), s x v (3), sym(s (x) w) (6: xx yy zz, xy xz yz doubled), p (1) once per column.
 // Column contributions are Kahan-compensated across the P^2 / 32 columns of a lane.
+// The work of warp w_ (particle order[w_]); Wz and Zi: the warp's 32-entry tables.
 template <typename T, typename TO, int CO, int NCOMP>
-__global__ void __launch_bounds__(256, 2) gather_kernel(SeParams p, int N, const int *order, const int *base,
-                                                     const T *s0g, const T *wg, const double *rad, const T *selfc,
-                                                     const int *perm, const T *grid, const T *xs, const T *yreal,
-                                                     TO *y, int ncomp_out, int with_wave, int with_self)
+__device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t *Wz, int *Zi, const SeParams &p,
+                                            int N, const int *order, const int *base, const T *s0g, const T *wg,
+                                            const double *rad, const T *selfc, const int *perm, const T *grid,
+                                            const T *xs, const T *yreal, TO *y, int ncomp_out, int with_wave,
+                                            int with_self)
 {
     constexpr int NA = 13;
     using T4 = typename V4<T>::t;
-    __shared__ T4 Wz[8][32];
-    __shared__ int Zi[8][32];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    // particles in spreading-bin order (supports starting in the same 8^3 tile are
-    // taken by neighbouring warps, so their grid reads share L1 lines)
-    const int w_ = blockIdx.x * (blockDim.x >> 5) + wl;
     if (w_ >= N) return;
     const int i = order ? order[w_] : w_;
     const int M = p.M, P = p.P;
@@ -942,8 +1010,8 @@ __global__ void __launch_bounds__(256, 2) gather_kernel(SeParams p, int N, const
         const T *wx = wg + (size_t)i * 3 * P, *wy = wx + P, *wz = wy + P;
         if (lane < P) {
             const T g = wz[lane], sz = sz0 + lane;
-            Wz[wl][lane] = T4{g, g * sz, g * sz * sz, g * sz * sz * sz};
-            Zi[wl][lane] = wrapi(bz + lane, M);
+            Wz[lane] = T4{g, g * sz, g * sz * sz, g * sz * sz * sz};
+            Zi[lane] = wrapi(bz + lane, M);
         }
         __syncwarp();
         const T a2k2 = a * a * kap * kap;
@@ -963,10 +1031,10 @@ __global__ void __launch_bounds__(256, 2) gather_kernel(SeParams p, int N, const
             if (act) {
 #pragma unroll 12
                 for (int k = 0; k < P; ++k) {
-                    const T4 w = Wz[wl][k];
-                    const T4 u0 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[wl][k] * zs);
+                    const T4 w = Wz[k];
+                    const T4 u0 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[k] * zs);
                     if constexpr (CO == 8) {
-                        const T4 u1 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[wl][k] * zs + 4);
+                        const T4 u1 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[k] * zs + 4);
                         // u0 = (v0 v1 v2 v''0), u1 = (v''1 v''2 p -): z0 = sum g v, z1 = sum g v'',
                         // z2 = sum g s_z v, z3 = sum g s_z v''
                         z0[0] += w.x * u0.x; z0[1] += w.x * u0.y; z0[2] += w.x * u0.z;
@@ -1037,6 +1105,21 @@ __global__ void __launch_bounds__(256, 2) gather_kernel(SeParams p, int N, const
     }
     if (lane != 0) return;
     combine_write<T, TO, CO>(p, acc, i, selfc, perm, xs, yreal, y, ncomp_out, with_self);
+}
+
+template <typename T, typename TO, int CO, int NCOMP>
+__global__ void __launch_bounds__(256, 2) gather_kernel(SeParams p, int N, const int *order, const int *base,
+                                                     const T *s0g, const T *wg, const double *rad, const T *selfc,
+                                                     const int *perm, const T *grid, const T *xs, const T *yreal,
+                                                     TO *y, int ncomp_out, int with_wave, int with_self)
+{
+    __shared__ typename V4<T>::t Wz[8][32];
+    __shared__ int Zi[8][32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    // particles in spreading-bin order (supports starting in the same 8^3 tile are
+    // taken by neighbouring warps, so their grid reads share L1 lines)
+    gather_body<T, TO, CO, NCOMP>(blockIdx.x * (blockDim.x >> 5) + wl, lane, Wz[wl], Zi[wl], p, N, order, base, s0g,
+                                  wg, rad, selfc, perm, grid, xs, yreal, y, ncomp_out, with_wave, with_self);
 }
 
 // ---------------------------------------------------------------- staged gather
@@ -1567,5 +1650,390 @@ template void launch_gather_combine<float, float>(se_ctx *, const float *, const
 template void launch_gather_combine<float, double>(se_ctx *, const float *, const float *, double *, int, int, cudaStream_t);
 template void launch_gather_combine<double, float>(se_ctx *, const double *, const double *, float *, int, int, cudaStream_t);
 template void launch_gather_combine<double, double>(se_ctx *, const double *, const double *, double *, int, int, cudaStream_t);
+
+}  // namespace se
+
+// ---------------------------------------------------------------- persistent batched product
+//
+// The products of a batch of independent boxes (own N, M, P, xi, rc each) in ONE
+// cooperative launch of 2 CTAs per SM: eight phases, each a list of work items over
+// every box (prefix sums per phase), separated by a grid barrier:
+//   0 inputs into cell order   1 real-space pair sum and spreading (4 tiles per CTA,
+//   64 threads each)   2 x pass   3 y pass   4 z pass with the k-space scaling
+//   5 inverse y pass   6 inverse x pass   7 gather + combine.
+// Items are claimed with an atomic counter per phase (boxes of very different size
+// share the SMs in proportion to their work).  The stage code is that of the
+// per-box kernels (the *_body functions).  Every wait at a grid barrier is bounded:
+// after about two seconds the CTA raises the launch's abort flag (and the sticky
+// failure flag the host reads) and returns; the other CTAs see the flag and return.
+#include "se_real_table.cuh"
+
+namespace se {
+
+namespace {
+
+constexpr int kPersistPhases = 8;
+constexpr int kPersistThreads = 256;
+constexpr long long kBarrierSpins = 20000000;    // x ~100 ns sleeps
+
+struct BoxDesc {
+    SeParams p;
+    FftPlan plan;
+    int N, co, s16, with_wave, with_real, with_self;
+    int nreal_items;                  // phase-1 items of the real-space sum (8 targets each)
+    float cnorm, twopiL, i4x2, ecoef;
+    const void *x;
+    void *y;
+    float *xs, *yreal;
+    const int *perm, *tile_start, *tile_perm, *sup_base;
+    const float *sup_s0, *sup_w, *selfc;
+    const double *rad;
+    float *grid_f, *grid_o;
+    float2 *spec_f, *spec_o;
+    const float2 *tw;
+    const int *pair_off, *pair_j;
+    const float *pair_x, *pair_c;
+    size_t npairs;
+};
+
+// ctl: [0] arrivals, [1] generation, [2 .. 2 + phases) work counters, then the abort
+// flag and the sticky failure flag
+constexpr int kCtlAbort = 2 + kPersistPhases, kCtlFailed = kCtlAbort + 1, kCtlWords = kCtlFailed + 1;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *a)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ bool grid_barrier(unsigned *ctl)
+{
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        const unsigned g = ld_acquire(ctl + 1);
+        __threadfence();
+        if (atomicAdd(ctl, 1u) == gridDim.x - 1) {
+            atomicExch(ctl, 0u);
+            __threadfence();
+            atomicAdd(ctl + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (ld_acquire(ctl + 1) == g) {
+                if (ld_acquire(ctl + kCtlAbort)) break;
+                if (++spins > kBarrierSpins) {
+                    atomicExch(ctl + kCtlAbort, 1u);
+                    atomicExch(ctl + kCtlFailed, 1u);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok = ld_acquire(ctl + kCtlAbort) == 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bar_named(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+template <int NCOMP, typename TO>
+__global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(const BoxDesc *__restrict__ bd, int nbox,
+                                                                              const int *__restrict__ pref,
+                                                                              unsigned *ctl)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int ph = 0; ph < kPersistPhases; ++ph) {
+        if (ph > 0 && !grid_barrier(ctl)) return;
+        const int *pr = pref + ph * (nbox + 1);
+        const int total = pr[nbox];
+        for (;;) {
+            __syncthreads();                          // the previous item's shared buffers are free
+            if (threadIdx.x == 0) s_item = (int)atomicAdd(ctl + 2 + ph, 1u);
+            __syncthreads();
+            const int item = s_item;
+            if (item >= total) break;
+            int lo = 0, hi = nbox;                    // pr[lo] <= item < pr[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pr[mid] <= item) lo = mid; else hi = mid;
+            }
+            const BoxDesc &d = bd[lo];
+            const int it = item - pr[lo];
+            const int Mh = d.p.M / 2 + 1;
+            switch (ph) {
+            case 0: {
+                const int k = it * kPersistThreads + threadIdx.x;
+                if (k < d.N) {
+                    const TO *src = (const TO *)d.x + (size_t)d.perm[k] * NCOMP;
+                    float *dst = d.xs + (size_t)k * kNC;
+#pragma unroll
+                    for (int c = 0; c < kNC; ++c) dst[c] = c < NCOMP ? (float)src[c] : 0.f;
+                }
+                break;
+            }
+            case 1:
+                if (it < d.nreal_items) {
+                    const int i = it * (kPersistThreads / 32) + warp;
+                    if (d.with_real) {
+                        real_table_body<float, NCOMP>(i, lane, d.N, d.pair_off, d.npairs, d.pair_j, d.pair_x,
+                                                      d.pair_c, d.xs, d.yreal);
+                    } else if (i < d.N && lane < kNC) {
+                        d.yreal[(size_t)i * kNC + lane] = 0.f;
+                    }
+                } else {
+                    const int grp = threadIdx.x >> 6, tid = threadIdx.x & 63;
+                    const int nt = d.p.ntile;
+                    const int ntiles = d.s16 ? nt * nt * ((nt + 1) / 2) : nt * nt * nt;
+                    const int tile = (it - d.nreal_items) * 4 + grp;
+                    if (tile < ntiles) {
+                        auto sync = [grp] { bar_named(1 + grp, 64); };
+                        if (d.s16) {
+                            Spread16Smem &sm = reinterpret_cast<Spread16Smem *>(smraw)[grp];
+                            spread16_body<NCOMP, false>(tile, 0, tid, sync, sm, d.p, d.tile_start, d.tile_perm,
+                                                        d.sup_base, d.sup_s0, d.sup_w, d.rad, d.xs, d.grid_f, 1);
+                        } else {
+                            Spread8Smem<float> &sm = *reinterpret_cast<Spread8Smem<float> *>(
+                                smraw + (size_t)grp * sizeof(Spread16Smem));
+                            spread_body<float, NCOMP, false>(tile, 0, tid, sync, sm, d.p, d.tile_start, d.tile_perm,
+                                                             d.sup_base, d.sup_s0, d.sup_w, d.rad, d.xs, d.grid_f,
+                                                             1);
+                        }
+                    }
+                }
+                break;
+            case 2:
+                fft_x_fwd_body<float>(it, smraw, d.plan, d.tw, d.grid_f, d.spec_f);
+                break;
+            case 3: {
+                const int nbx = (Mh + 3) / 4;
+                fft_y_body<float, 4, false>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_f);
+                break;
+            }
+            case 4: {
+                const int nbx = (Mh + 3) / 4;
+                if (d.co == 8)
+                    fft_z_scale_body<float, 8, 4>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_f, d.spec_o,
+                                                  d.cnorm, d.twopiL, d.i4x2, d.ecoef);
+                else
+                    fft_z_scale_body<float, 4, 4>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_f, d.spec_o,
+                                                  d.cnorm, d.twopiL, d.i4x2, d.ecoef);
+                break;
+            }
+            case 5: {
+                if (d.co == 8) {
+                    const int nbx = (Mh + 1) / 2;
+                    fft_y_body<float, 8, true>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_o);
+                } else {
+                    const int nbx = (Mh + 3) / 4;
+                    fft_y_body<float, 4, true>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_o);
+                }
+                break;
+            }
+            case 6:
+                if (d.co == 8) fft_x_inv_body<float, 8>(it, smraw, d.plan, d.tw, d.spec_o, d.grid_o);
+                else fft_x_inv_body<float, 4>(it, smraw, d.plan, d.tw, d.spec_o, d.grid_o);
+                break;
+            default: {
+                float4 *Wz = reinterpret_cast<float4 *>(smraw) + warp * 32;
+                int *Zi = reinterpret_cast<int *>(smraw + (kPersistThreads / 32) * 32 * sizeof(float4)) + warp * 32;
+                const int w_ = it * (kPersistThreads / 32) + warp;
+                const int *order = d.with_wave ? d.tile_perm : nullptr;
+                if (d.co == 8)
+                    gather_body<float, TO, 8, NCOMP>(w_, lane, Wz, Zi, d.p, d.N, order, d.sup_base, d.sup_s0, d.sup_w,
+                                                     d.rad, d.selfc, d.perm, d.grid_o, d.xs, d.yreal, (TO *)d.y,
+                                                     NCOMP, d.with_wave, d.with_self);
+                else
+                    gather_body<float, TO, 4, NCOMP>(w_, lane, Wz, Zi, d.p, d.N, order, d.sup_base, d.sup_s0, d.sup_w,
+                                                     d.rad, d.selfc, d.perm, d.grid_o, d.xs, d.yreal, (TO *)d.y,
+                                                     NCOMP, d.with_wave, d.with_self);
+                break;
+            }
+            }
+        }
+    }
+}
+
+template <int NCOMP, typename TO>
+const void *persist_kernel_for() { return (const void *)batch_persistent_kernel<NCOMP, TO>; }
+
+const void *persist_kernel(int ncomp, int dtype)
+{
+    if (dtype == SE_F64) {
+        if (ncomp <= 3) return persist_kernel_for<3, double>();
+        if (ncomp <= 6) return persist_kernel_for<6, double>();
+        if (ncomp <= 11) return persist_kernel_for<11, double>();
+        return persist_kernel_for<12, double>();
+    }
+    if (ncomp <= 3) return persist_kernel_for<3, float>();
+    if (ncomp <= 6) return persist_kernel_for<6, float>();
+    if (ncomp <= 11) return persist_kernel_for<11, float>();
+    return persist_kernel_for<12, float>();
+}
+
+}  // namespace
+
+void persist_free(PersistPlan &pl)
+{
+    if (pl.desc) cudaFree(pl.desc);
+    if (pl.pref) cudaFree(pl.pref);
+    if (pl.ctl) cudaFree(pl.ctl);
+    pl = PersistPlan();
+}
+
+int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *x, void *const *y, int dtype,
+                    PersistPlan &pl, std::string &err)
+{
+    persist_free(pl);
+    std::vector<BoxDesc> h(nbox);
+    std::vector<int> pref((size_t)kPersistPhases * (nbox + 1), 0);
+    size_t smem = (size_t)4 * sizeof(Spread16Smem);
+    for (int b = 0; b < nbox; ++b) {
+        se_ctx *c = box[b];
+        const int with_real = (c->parts & 1) ? 1 : 0, with_wave = (c->parts & 2) ? 1 : 0;
+        if (c->precision != 0 || !c->support_ok[0] || !c->b.grid_f[0] || (with_real && !c->pairs_ok[0]) ||
+            c->ktab_on) {
+            err = "box " + std::to_string(b) + ": the persistent batch needs FP32 products with the stored pair "
+                  "table (run the batch once without it first)";
+            return SE_ERR_STATE;
+        }
+        const SeParams p = make_params(c);
+        BoxDesc &d = h[b];
+        d.p = p;
+        d.plan = c->plan;
+        d.N = (int)c->N;
+        d.co = p.hybrid ? 8 : 4;
+        d.s16 = use_spread16(c, p, true) ? 1 : 0;
+        d.with_wave = with_wave;
+        d.with_real = with_real;
+        d.with_self = (c->parts & 4) ? 1 : 0;
+        d.nreal_items = (d.N + kPersistThreads / 32 - 1) / (kPersistThreads / 32);
+        d.cnorm = (float)(pow(p.alpha / kPi, 3.0) / (p.eta * p.L * p.L * p.L));
+        d.twopiL = (float)(2.0 * kPi / p.L);
+        d.i4x2 = (float)(0.25 / (p.xi * p.xi));
+        d.ecoef = (float)(2.0 * kPi * kPi / (p.alpha * (double)p.M * p.M));
+        d.x = x[b];
+        d.y = y[b];
+        d.xs = (float *)c->b.xs[0];
+        d.yreal = (float *)c->b.yreal[0];
+        d.perm = c->b.perm;
+        d.tile_start = c->b.tile_start;
+        d.tile_perm = c->b.tile_perm;
+        d.sup_base = c->b.sup_base;
+        d.sup_s0 = (const float *)c->b.sup_s0[0];
+        d.sup_w = (const float *)c->b.sup_w[0];
+        d.selfc = (const float *)c->b.self_c[0];
+        d.rad = c->b.rad;
+        d.grid_f = (float *)c->b.grid_f[0];
+        d.grid_o = (float *)c->b.grid_o[0];
+        d.spec_f = (float2 *)c->b.spec_f[0];
+        d.spec_o = (float2 *)c->b.spec_o[0];
+        d.tw = (const float2 *)c->b.tw[0];
+        d.pair_off = c->b.pair_off;
+        d.pair_j = c->b.pair_j;
+        d.pair_x = (const float *)c->b.pair_x[0];
+        d.pair_c = (const float *)c->b.pair_c[0];
+        d.npairs = c->npairs;
+        const int M = p.M, Mh = M / 2 + 1, nt = p.ntile;
+        const int ntiles = d.s16 ? nt * nt * ((nt + 1) / 2) : nt * nt * nt;
+        const int nw = with_wave;
+        const int items[kPersistPhases] = {
+            (d.N + kPersistThreads - 1) / kPersistThreads,
+            d.nreal_items + nw * (ntiles + 3) / 4,
+            nw * M * M / 8,
+            nw * ((Mh + 3) / 4) * M,
+            nw * ((Mh + 3) / 4) * M,
+            nw * (d.co == 8 ? (Mh + 1) / 2 : (Mh + 3) / 4) * M,
+            nw * M * M / (d.co == 8 ? 4 : 8),
+            d.nreal_items};
+        for (int ph = 0; ph < kPersistPhases; ++ph)
+            pref[(size_t)ph * (nbox + 1) + b + 1] = pref[(size_t)ph * (nbox + 1) + b] + items[ph];
+        smem = std::max(smem, fft_smem_bytes<float2>(M, fft_nl<float>()));
+        smem = std::max(smem, fft_smem_bytes<float2>(M, 4 * d.co));
+    }
+    if (smem > kSmemMax) {
+        err = "a box's grid is too large for the persistent batch";
+        return SE_ERR_GRID;
+    }
+    const void *kern = persist_kernel(ncomp, dtype);
+    int dev = 0, nsm = 0, occ = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPersistThreads, smem) != cudaSuccess ||
+        occ < 1 || !coop) {
+        cudaGetLastError();
+        err = "the persistent batch kernel cannot be launched cooperatively on this device";
+        return SE_ERR_CUDA;
+    }
+    if (cudaMalloc(&pl.desc, nbox * sizeof(BoxDesc)) != cudaSuccess ||
+        cudaMalloc(&pl.pref, pref.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&pl.ctl, kCtlWords * sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        persist_free(pl);
+        err = "persistent batch allocation failed";
+        return SE_ERR_NOMEM;
+    }
+    if (cudaMemcpy(pl.desc, h.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pl.pref, pref.data(), pref.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(pl.ctl, 0, kCtlWords * sizeof(unsigned)) != cudaSuccess) {
+        persist_free(pl);
+        err = "persistent batch upload failed";
+        return SE_ERR_CUDA;
+    }
+    pl.nbox = nbox;
+    pl.ncomp = ncomp;
+    pl.dtype = dtype;
+    pl.grid = occ * nsm;
+    pl.smem = smem;
+    pl.kernel = kern;
+    return SE_OK;
+}
+
+int persist_launch(const PersistPlan &pl, cudaStream_t s, std::string &err)
+{
+    // fresh barrier, work counters and abort flag; the sticky failure flag stays
+    cudaError_t e = cudaMemsetAsync(pl.ctl, 0, kCtlFailed * sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        const BoxDesc *bd = (const BoxDesc *)pl.desc;
+        int nbox = pl.nbox;
+        const int *pref = pl.pref;
+        unsigned *ctl = pl.ctl;
+        void *args[] = {(void *)&bd, (void *)&nbox, (void *)&pref, (void *)&ctl};
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.gridDim = dim3(pl.grid);
+        cfg.blockDim = dim3(kPersistThreads);
+        cfg.dynamicSmemBytes = pl.smem;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, pl.kernel, args);
+    }
+    if (e != cudaSuccess) {
+        err = std::string("persistent batch launch: ") + cudaGetErrorString(e);
+        return SE_ERR_CUDA;
+    }
+    return SE_OK;
+}
+
+int persist_failed(const PersistPlan &pl, cudaStream_t s)
+{
+    unsigned f = 0;
+    cudaMemcpyAsync(&f, pl.ctl + kCtlFailed, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    cudaMemsetAsync(pl.ctl + kCtlFailed, 0, sizeof(unsigned), s);
+    return f ? 1 : 0;
+}
 
 }  // namespace se

@@ -59,3 +59,50 @@ def test_batch_graph_matches_per_box_products(oracle_mod):
     got = ys[0].double().cpu().numpy()
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
     b.close()
+
+
+@pytest.mark.parametrize("ncomp,dtype", [(3, torch.float32), (12, torch.float64), (11, torch.float32)])
+def test_persistent_batch_matches_per_box_launches(ncomp, dtype):
+    """One persistent launch for every box (se_batch_apply mode 2) against the batch's
+    per-box launches: the same stage code on the same data, so the same products (to
+    FP32 rounding), on replays and with new inputs in the same buffers.  The boxes mix
+    8^3 and 8x8x16 spreading tiles (a 24^3 grid with P = 12 leaves no room for the
+    taller tiles), the real-space and the hybrid size modes, and uneven N."""
+    boxes = inputs.batch_boxes(seed=5, nbox=7, nmin=40, nmax=400)
+    ctxs, xs = [], []
+    rng = np.random.default_rng(2)
+    for k, cfg in enumerate(boxes):
+        sp = params.choose(cfg.L, cfg.N, 1e-6, M_max=64, a_eff=params.effective_radius(cfg.rad), precision=0)
+        c = api.Context()
+        if k == 0:
+            c.set_params(sp.xi, 24, 12, min(sp.rc, 0.45 * cfg.L))
+        else:
+            c.set_params(sp.xi, sp.M, sp.P, sp.rc)
+            c.set_option(api.SE_OPT_SHAPE_M, sp.m)
+        c.set_option(api.SE_OPT_SIZE_MODE, 0 if k == 1 else 1)
+        c.set_config(cfg.pos, cfg.rad, cfg.L)
+        xs.append(torch.tensor(rng.standard_normal((cfg.N, ncomp)), device="cuda", dtype=dtype))
+        ctxs.append(c)
+    ref = [torch.empty_like(x) for x in xs]
+    ys = [torch.empty_like(x) for x in xs]
+    b = api.Batch(ctxs, nstreams=4)
+    b.apply(xs, ref, use_graph=0)
+    torch.cuda.synchronize()
+
+    def close(a, r):
+        return float(torch.linalg.norm((a - r).double()) / torch.linalg.norm(r.double())) <= 1e-6
+
+    for rep in range(3):                  # prepare (eager step), then two persistent launches
+        for y in ys:
+            y.fill_(float("nan"))
+        b.apply(xs, ys, use_graph=api.Batch.PERSISTENT)
+        b.status()
+        for y, r in zip(ys, ref):
+            assert torch.isfinite(y).all() and close(y, r), rep
+    for x in xs:
+        x.mul_(-2.0)
+    b.apply(xs, ys, use_graph=api.Batch.PERSISTENT)
+    b.status()
+    for y, r in zip(ys, ref):
+        assert close(y, -2.0 * r)
+    b.close()
