@@ -76,7 +76,7 @@ def parse():
                     help="real-space sum beside the spread (0), beside the FFT chain (1), in line (2)")
     ap.add_argument("--fp64-solve-maxit", type=int, default=100,
                     help="iterations of the plain FP64 solve that are timed (it runs ~20x slower)")
-    ap.add_argument("--workload", choices=["mono_n200k", "batch64"], default="mono_n200k")
+    ap.add_argument("--workload", choices=["mono_n200k", "batch64", "brownian"], default="mono_n200k")
     ap.add_argument("--autotune", action="store_true", help="batch64: time candidate parameters per box")
     ap.add_argument("--streams", type=int, default=8, help="batch64: streams of the captured graph")
     ap.add_argument("--n", type=int, default=200000,
@@ -643,6 +643,51 @@ def run_batch(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+def run_brownian(args, rank, world, local):
+    """Far-field Brownian source M^{-1/2} Psi (F, T, S; Sec. 4.3) by the Swan-Brady IVP,
+    dtau = 0.1, on the log-normal suspension (N = 20000, phi = 0.4), FP32 products with
+    FP64 refinement, each of the 20 GMRES solves to 1e-6.  One step = one IVP."""
+    import torch
+    from paper_1506_08481_b300 import api, inputs, params
+
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = inputs.lognormal(seed=3, n=20000, phi=0.4)
+    sp = params.choose(cfg.L, cfg.N, 5e-7, M_max=128, a_eff=params.effective_radius(cfg.rad), precision=0)
+    ctx = api.Context(local)
+    ctx.set_params(sp.xi, sp.M, sp.P, sp.rc)
+    ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
+    ctx.set_option(api.SE_OPT_SIZE_MODE, 1)
+    ctx.set_option(api.SE_OPT_RESTART, 100)
+    ctx.set_config(cfg.pos, cfg.rad, cfg.L)
+    psi = torch.tensor(np.random.default_rng(7).standard_normal((cfg.N, 11)), device=dev, dtype=torch.float64)
+    x10, prods = ctx.brownian_ivp(psi, nsteps=10, rtol=1e-6, maxit=2000)          # warm-up (preconditioner)
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        x10, prods = ctx.brownian_ivp(psi, nsteps=10, rtol=1e-6, maxit=2000)
+    ms = job_time_ms(1e3 * (time.perf_counter() - t), world, dev) / steps
+    x20, prods20 = ctx.brownian_ivp(psi, nsteps=20, rtol=1e-6, maxit=2000)
+    disc = float(torch.linalg.norm(x10 - x20) / torch.linalg.norm(x20))
+    if rank == 0:
+        line = {"metric": "far-field Brownian IVPs M^-1/2 Psi per second (N=20000 log-normal, F,T,S)",
+                "value": job_rate(1, ms, world), "unit": "IVPs/s", "n_gpus": world, "steps": steps, "warmup": 1,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "brownian_lognormal_n20000_phi0.4", "N": cfg.N, "ncomp": 11, "dtau": 0.1,
+                           "solve_rtol": 1e-6, "params": {"xi": sp.xi, "M": sp.M, "P": sp.P, "rc": sp.rc}},
+                "products_per_ivp": prods, "products_per_ivp_dtau_0.05": prods20,
+                "rel_diff_dtau_0.1_vs_0.05": disc}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args)
@@ -650,6 +695,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batch64":
         run_batch(args, rank, world, local)
+    elif args.workload == "brownian":
+        run_brownian(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

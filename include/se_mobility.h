@@ -179,6 +179,23 @@ int se_real_space_apply_noalloc(int device, void *stream, int64_t N, double L, d
                                 double eta, const double *pos, const double *radius, int ncomp,
                                 const double *x, double *y);
 
+/* Far-field Brownian displacement source: x = M^{-1/2} c for the F, T, S block of the
+ * far-field grand mobility (Sec. 4.3, Eq. br-f-ff: F^B,ff and the Brownian stresslet
+ * fluctuation are (2kT/dt) M^{-1/2} Psi), by the initial value problem of Eq. ivp-1 marched
+ * with the explicit and implicit Euler half-steps of Eqs. ivp-forward/ivp-backward.
+ *   ncomp   : 3, 6 or 11 (the symmetric positive definite F, T, S prefix)
+ *   scale   : s > 0 with A = s M (the IVP is solved for A; x = sqrt(s) A^{-1/2} c); s <= 0
+ *             selects 6 pi eta <a>, which puts A's translational self blocks near I
+ *   nsteps  : number of steps, dtau = 1 / nsteps (the paper finds dtau = 0.1 adequate)
+ *   rtol, maxit : tolerance and product limit of each of the 2 nsteps GMRES solves
+ *             (shifted operators alpha I + beta M, block preconditioner of the shift;
+ *             products at the context's precision with FP64 refinement)
+ *   c, x    : FP64 DEVICE arrays [N][ncomp] (c is read, x is written; they may not alias)
+ *   products: if not NULL, receives the number of products used
+ * Returns SE_ERR_NOT_CONVERGED if a solve missed rtol (x is still written); synchronises. */
+int se_brownian_ivp(se_ctx *ctx, int ncomp, double scale, int nsteps, double rtol, int maxit,
+                    const double *c, double *x, int *products);
+
 /* Learned preconditioner correction (SE_PRECOND_LEARNED).  A small network (16 -> 64 ->
  * 64 -> 4, tanh, FP32) maps rotation- and permutation-invariant features of a sphere's
  * radius and of its neighbours inside rc to corrections of the isotropic parts of its

@@ -35,7 +35,7 @@ SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED, SE_PRECOND_SPECTRAL = 0, 
 
 # every entry point declared in include/se_mobility.h
 ABI_SYMBOLS = ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
-               "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_last_error",
+               "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_brownian_ivp", "se_last_error",
                "se_kernel_launches", "se_stage_times", "se_real_space_apply_noalloc",
                "se_set_learned_weights", "se_learned_features", "se_mlp_forward", "se_mlp_grad",
                "se_mlp_adam_step", "se_batch_create", "se_batch_apply", "se_batch_destroy",
@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.se_mobility_apply.argtypes = [p, i, p, p, i]
     lib.se_mobility_apply_host.argtypes = [p, i, p, p]
     lib.se_solve.argtypes = [p, i, p, p, i, d, i, i, ctypes.POINTER(i), ctypes.POINTER(d)]
+    lib.se_brownian_ivp.argtypes = [p, i, d, i, d, i, p, p, ctypes.POINTER(i)]
     lib.se_last_error.argtypes = [p]
     lib.se_last_error.restype = ctypes.c_char_p
     lib.se_kernel_launches.argtypes = [p]
@@ -93,7 +94,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("se_batch_create", "se_batch_apply", "se_batch_destroy", "se_batch_status"):
         getattr(lib, name).restype = i
     for name in ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
-                 "se_mobility_apply", "se_mobility_apply_host", "se_solve"):
+                 "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_brownian_ivp"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -251,6 +252,27 @@ class Context:
         return x, iters.value, relres.value
 
     solve = se_solve
+
+    # --- se_brownian_ivp
+    def se_brownian_ivp(self, c, nsteps: int = 10, rtol: float = 1e-8, maxit: int = 1000, scale: float = 0.0,
+                        ncomp: int | None = None, allow_not_converged: bool = False):
+        """x = M^{-1/2} c (FP64 CUDA tensor [N, ncomp], ncomp 3, 6 or 11) by the Swan-Brady
+        initial value problem with dtau = 1/nsteps; returns (x, products)."""
+        import torch
+        if ncomp is None:
+            ncomp = c.shape[-1]
+        c = c.to(torch.float64).contiguous()
+        x = torch.empty_like(c)
+        prods = ctypes.c_int(0)
+        rc = self.lib.se_brownian_ivp(self.h, int(ncomp), float(scale), int(nsteps), float(rtol), int(maxit),
+                                      ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.byref(prods))
+        if rc == SE_ERR_NOT_CONVERGED and allow_not_converged:
+            return x, prods.value
+        self._check(rc)
+        return x, prods.value
+
+    brownian_ivp = se_brownian_ivp
 
 
 # --- network kernels (stand-alone; device tensors)

@@ -140,8 +140,11 @@ static void free_config(se_ctx *c)
     }
     c->npairs = 0;
     dfree_t(c->b.pc_inv);
+    dfree_t(c->b.pc_C);
     dfree_t(c->b.kry);
     dfree_t(c->b.work64);
+    c->b.kry_n = 0;
+    c->b.kry_m = 0;
     dfree_t(c->b.red);
     dfree_t(c->b.stage);
     c->alloc_N = 0;

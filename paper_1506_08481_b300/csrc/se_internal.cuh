@@ -74,9 +74,12 @@ struct Buffers {
     double *stage = nullptr;     // [2][N][12]
     // solver
     double *pc_inv = nullptr;    // [N][nc][nc] inverse preconditioner blocks (caller order)
+    double *pc_C = nullptr;      // [3][12][12] fitted self-image block coefficients (C0, C1, C2)
     float *mlp_w = nullptr;      // learned correction network (packed parameters)
     double *kry = nullptr;       // Krylov basis [restart + 1][n] and preconditioned vectors [restart][n]
     double *work64 = nullptr;    // FP64 work vectors [5][n]
+    size_t kry_n = 0;            // n and restart the Krylov arrays were sized for
+    int kry_m = 0;
     double *red = nullptr;       // reduction scratch
 };
 
@@ -113,6 +116,7 @@ struct se_ctx {
     // preconditioner state
     bool pc_ready = false;
     int pc_ncomp = 0, pc_prec = -1, pc_kind = -1;
+    double pc_alpha = 0, pc_beta = 1;  // the blocks invert alpha I + beta M_ii
     bool have_mlp = false;
     int pc_fallbacks = 0;              // particles whose learned block fell back to the plain one
     // spectral correction (SE_PRECOND_SPECTRAL): a coarse forces-only context whose

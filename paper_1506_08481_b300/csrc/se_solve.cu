@@ -111,15 +111,17 @@ __global__ void block_apply_kernel(int N, int nc, const double *Binv, const doub
     }
 }
 
-// Block of particle with radius a: isolated-sphere self terms + C0 + a^2 C1 + a^4 C2,
-// inverted by Gauss-Jordan elimination with partial pivoting.  Sorted particle k is
-// stored at caller index perm[k].  Singular blocks fall back to the isolated inverse.
+// Block of particle with radius a: isolated-sphere self terms + C0 + a^2 C1 + a^4 C2
+// (the diagonal block M_ii), shifted to alpha I + beta M_ii (the diagonal block of the
+// operator alpha I + beta M; alpha = 0, beta = 1 for M itself), inverted by Gauss-Jordan
+// elimination with partial pivoting.  Sorted particle k is stored at caller index
+// perm[k].  Singular blocks fall back to the shifted isolated-sphere inverse.
 // `corr` (may be null, caller order [N][4]): learned dimensionless corrections of the
 // isotropic parts, each scaled by the isolated-sphere mobility of its block.  A learned
 // block that cannot be inverted falls back to the plain block (counted in *fallbacks).
 __global__ void block_build_kernel(int N, int nc, double eta, const double *rad, const int *perm,
-                                   const double *C /*[3][12][12]*/, const double *corr, double *Binv,
-                                   int *fallbacks)
+                                   const double *C /*[3][12][12]*/, const double *corr, double alpha,
+                                   double beta, double *Binv, int *fallbacks)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
@@ -142,6 +144,8 @@ retry:
                          : r < 11 ? 3.0 / (20 * pi * eta * a * a2) : 3.0 / (16 * pi * eta * a * a2);
         const double dc = use_corr ? d[r < 3 ? 0 : r < 6 ? 1 : r < 11 ? 2 : 3] : 0.0;
         A[r][r] += iso * (1.0 + dc);
+        for (int q = 0; q < nc; ++q) A[r][q] *= beta;
+        A[r][r] += alpha;
     }
     bool ok = true;
     for (int col = 0; col < nc && ok; ++col) {
@@ -178,9 +182,9 @@ retry:
         for (int q = 0; q < nc; ++q) {
             double v = A[r][nc + q];
             if (!ok || !isfinite(v)) {
-                const double iso = r < 3 ? 6 * pi * eta * a : r < 6 ? 8 * pi * eta * a * a2
-                                 : r < 11 ? 20 * pi * eta * a * a2 / 3 : 16 * pi * eta * a * a2 / 3;
-                v = r == q ? iso : 0.0;
+                const double mob = r < 3 ? 1.0 / (6 * pi * eta * a) : r < 6 ? 1.0 / (8 * pi * eta * a * a2)
+                                 : r < 11 ? 3.0 / (20 * pi * eta * a * a2) : 3.0 / (16 * pi * eta * a * a2);
+                v = r == q ? 1.0 / (alpha + beta * mob) : 0.0;
             }
             out[r * nc + q] = v;
         }
@@ -196,6 +200,8 @@ void convert_f2d(int n, const float *x, double *y, cudaStream_t s)
 static int grid_for(size_t n) { size_t g = (n + 255) / 256; return (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g)); }
 
 // ---------------------------------------------------------------- preconditioner
+
+static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double beta);
 
 static int build_precond(se_ctx *c, int ncomp, bool learned)
 {
@@ -278,47 +284,63 @@ static int build_precond(se_ctx *c, int ncomp, bool learned)
             }
         }
     }
-    double *dC = nullptr;
-    SE_CUDA_CHECK(c, cudaMalloc(&dC, C.size() * sizeof(double)));
-    SE_CUDA_CHECK(c, cudaMemcpyAsync(dC, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    // the fitted coefficients stay with the configuration: shifted blocks (alpha I +
+    // beta M_ii, the Brownian IVP's systems) are rebuilt from them without new products
+    if (!c->b.pc_C) SE_CUDA_CHECK(c, cudaMalloc(&c->b.pc_C, C.size() * sizeof(double)));
+    SE_CUDA_CHECK(c, cudaMemcpyAsync(c->b.pc_C, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    c->pc_ready = false;
+    return build_blocks(c, ncomp, learned, 0.0, 1.0);
+}
+
+// the inverse blocks of alpha I + beta M_ii from the fitted coefficients (learned:
+// with the network's corrections; only for alpha = 0, beta = 1)
+static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double beta)
+{
+    cudaStream_t s = c->stream;
+    const int N = (int)c->N;
     if (c->b.pc_inv) cudaFree(c->b.pc_inv);
     c->b.pc_inv = nullptr;
+    c->pc_ready = false;
     if (cudaMalloc(&c->b.pc_inv, (size_t)N * ncomp * ncomp * sizeof(double)) != cudaSuccess) {
-        cudaFree(dC);
+        cudaGetLastError();
         c->err = "preconditioner allocation failed";
         return SE_ERR_NOMEM;
     }
     double *corr = nullptr;
     int *dfb = nullptr;
-    if (cudaMalloc(&dfb, sizeof(int)) != cudaSuccess) { cudaFree(dC); return SE_ERR_NOMEM; }
+    if (cudaMalloc(&dfb, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return SE_ERR_NOMEM; }
     cudaMemsetAsync(dfb, 0, sizeof(int), s);
     if (learned) {
         if (cudaMalloc(&corr, (size_t)N * 4 * sizeof(double)) != cudaSuccess) {
-            cudaFree(dC);
+            cudaGetLastError();
             cudaFree(dfb);
             return SE_ERR_NOMEM;
         }
         const int r = learned_corrections(c, corr);
         if (r != SE_OK) {
-            cudaFree(dC);
             cudaFree(dfb);
             cudaFree(corr);
             return r;
         }
     }
-    block_build_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->eta, c->b.rad, c->b.perm, dC, corr, c->b.pc_inv,
-                                                       dfb);
+    block_build_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->eta, c->b.rad, c->b.perm, c->b.pc_C, corr, alpha,
+                                                       beta, c->b.pc_inv, dfb);
     c->launches++;
     int fb = 0;
     cudaMemcpyAsync(&fb, dfb, sizeof(int), cudaMemcpyDeviceToHost, s);
-    SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
-    cudaFree(dC);
+    const cudaError_t e = cudaStreamSynchronize(s);
     cudaFree(dfb);
     if (corr) cudaFree(corr);
+    if (e != cudaSuccess) {
+        c->err = std::string("preconditioner blocks: ") + cudaGetErrorString(e);
+        return SE_ERR_CUDA;
+    }
     c->pc_fallbacks = fb;
     c->pc_ready = true;
     c->pc_ncomp = ncomp;
     c->pc_kind = learned ? SE_PRECOND_LEARNED : SE_PRECOND_BLOCK;
+    c->pc_alpha = alpha;
+    c->pc_beta = beta;
     return SE_OK;
 }
 
@@ -644,29 +666,21 @@ static int spectral_apply(se_ctx *c, int ncomp, const double *v, double *z)
 
 using namespace se;
 
-// working-precision restart residuals are used while rel > kFp64Switch * rtol
+// working-precision restart residuals are used while rel > kFp64Switch * rtol and they
+// still fall by 2x per cycle
 constexpr double kFp64Switch = 30.0;
 
-extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype, double rtol, int maxit,
-                        int precond, int *iters, double *relres)
+// Krylov basis, preconditioned vectors, work vectors and reduction scratch for the
+// context's restart length and n unknowns (kept between solves of the same size)
+static int ensure_solver_work(se_ctx *c, size_t n)
 {
-    if (!c) return SE_ERR_ARG;
-    if (!b || !x) { c->err = "null b or x"; return SE_ERR_ARG; }
-    if (ncomp != 3 && ncomp != 6 && ncomp != 11 && ncomp != 12) { c->err = "ncomp must be 3, 6, 11 or 12"; return SE_ERR_ARG; }
-    if (dtype != SE_F32 && dtype != SE_F64) { c->err = "bad dtype"; return SE_ERR_ARG; }
-    if (!(rtol > 0) || maxit < 1) { c->err = "rtol must be > 0 and maxit >= 1"; return SE_ERR_ARG; }
-    if (precond < SE_PRECOND_NONE || precond > SE_PRECOND_SPECTRAL) { c->err = "bad preconditioner"; return SE_ERR_ARG; }
-    if (!c->have_config) { c->err = "se_set_config must be called first"; return SE_ERR_STATE; }
-    cudaSetDevice(c->device);
-    cudaStream_t s = c->stream;
     const int m = c->restart;
-    const size_t n = (size_t)c->N * ncomp;
-
-    // work space
+    if (c->b.kry && c->b.kry_n == n && c->b.kry_m == m) return SE_OK;
     if (c->b.kry) cudaFree(c->b.kry);
     if (c->b.work64) cudaFree(c->b.work64);
     if (c->b.red) cudaFree(c->b.red);
     c->b.kry = c->b.work64 = c->b.red = nullptr;
+    c->b.kry_n = 0;
     // flexible GMRES: Krylov basis V [m + 1][n] and the preconditioned vectors Z [m][n]
     if (cudaMalloc(&c->b.kry, (size_t)(2 * m + 1) * n * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->b.work64, 5 * n * sizeof(double)) != cudaSuccess ||
@@ -675,28 +689,48 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
         c->err = "solver allocation failed";
         return SE_ERR_NOMEM;
     }
+    c->b.kry_n = n;
+    c->b.kry_m = m;
+    return SE_OK;
+}
+
+// Right-preconditioned flexible GMRES(restart) on (alpha I + beta M) x = b, with M the
+// grand mobility of the ncomp-prefix; bd and xd are FP64 device arrays [N][ncomp] (xd:
+// initial guess in, solution out; neither may alias the work vectors).  The block
+// preconditioner inverts the blocks of alpha I + beta M_ii; the learned and spectral
+// corrections apply to M itself (alpha = 0, beta = 1) only, shifted systems take the
+// block preconditioner.
+static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double rtol, int maxit, int precond,
+                      double alpha, double beta, int *iters, double *relres)
+{
+    cudaStream_t s = c->stream;
+    const int m = c->restart;
+    const size_t n = (size_t)c->N * ncomp;
+    int rc = ensure_solver_work(c, n);
+    if (rc != SE_OK) return rc;
     double *V = c->b.kry, *Zb = c->b.kry + (size_t)(m + 1) * n;
-    double *bd = c->b.work64, *xd = bd + n, *r = xd + n, *w = r + n, *z = w + n;
+    double *r = c->b.work64, *w = r + n, *z = w + n;
     Gm gm{c, n, c->b.red, c->b.red + (size_t)kRedBlocks * (m + 1)};
     double *yd = gm.hd + (m + 1);
+    const bool shifted = !(alpha == 0.0 && beta == 1.0);
+    if (shifted && precond != SE_PRECOND_NONE) precond = SE_PRECOND_BLOCK;
 
-    if (dtype == SE_F64) {
-        SE_CUDA_CHECK(c, cudaMemcpyAsync(bd, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        SE_CUDA_CHECK(c, cudaMemcpyAsync(xd, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    } else {
-        convert_kernel<float, double><<<grid_for(n), 256, 0, s>>>(n, (const float *)b, bd);
-        convert_kernel<float, double><<<grid_for(n), 256, 0, s>>>(n, (const float *)x, xd);
-        c->launches += 2;
-    }
     // the learned correction needs trained weights; without them it is the plain block
     const int kind = precond == SE_PRECOND_LEARNED && c->have_mlp ? SE_PRECOND_LEARNED : SE_PRECOND_BLOCK;
-    if (precond != SE_PRECOND_NONE && (!c->pc_ready || c->pc_ncomp != ncomp || c->pc_kind != kind)) {
-        int rc = build_precond(c, ncomp, kind == SE_PRECOND_LEARNED);
-        if (rc != SE_OK) return rc;
-        free_spectral(c);
+    if (precond != SE_PRECOND_NONE) {
+        if (!c->pc_ready || c->pc_ncomp != ncomp) {
+            rc = build_precond(c, ncomp, kind == SE_PRECOND_LEARNED);
+            if (rc != SE_OK) return rc;
+            free_spectral(c);
+        }
+        if (c->pc_kind != kind || c->pc_alpha != alpha || c->pc_beta != beta) {
+            rc = build_blocks(c, ncomp, kind == SE_PRECOND_LEARNED, alpha, beta);
+            if (rc != SE_OK) return rc;
+            free_spectral(c);
+        }
     }
     if (precond == SE_PRECOND_SPECTRAL && !c->spc) {
-        int rc = build_spectral(c, ncomp, gm, z, w);
+        rc = build_spectral(c, ncomp, gm, z, w);
         if (rc != SE_OK) return rc;
     }
     auto Pinv = [&](const double *v, double *out) -> int {
@@ -710,9 +744,17 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
         }
         return SE_OK;
     };
+    // out = (alpha I + beta M) v at product precision prec
+    auto op = [&](const double *v, double *out, int prec) -> int {
+        const int e = se_apply_internal(c, ncomp, v, out, SE_F64, prec);
+        if (e != SE_OK || !shifted) return e;
+        axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, alpha, v, beta, out, out);
+        c->launches++;
+        return SE_OK;
+    };
 
     double bn2, xn2;
-    int rc = gm.dots(bd, 0, 1, bd, &bn2);
+    rc = gm.dots(bd, 0, 1, bd, &bn2);
     if (rc != SE_OK) return rc;
     if ((rc = gm.dots(xd, 0, 1, xd, &xn2)) != SE_OK) return rc;
     const double bnorm = std::sqrt(bn2);
@@ -730,6 +772,7 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
         // (an FP64 product), so each further cycle is a step of iterative refinement on
         // the FP64 residual, and convergence is decided by it.
         bool fp64_res = c->precision == 1;
+        double rel_wp = 1.0;                  // the previous working-precision restart residual
         for (;;) {
             bool exact = fp64_res;            // r is the FP64 residual (or b itself)
             if (x_zero) {
@@ -737,7 +780,7 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
                 x_zero = false;
                 exact = true;
             } else {
-                rc = se_apply_internal(c, ncomp, xd, w, SE_F64, fp64_res ? 1 : c->precision);
+                rc = op(xd, w, fp64_res ? 1 : c->precision);
                 if (rc != SE_OK) return rc;
                 axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, bd, -1.0, w, r);
                 c->launches++;
@@ -748,10 +791,14 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
             const double beta = std::sqrt(rn2);
             rel = beta / bnorm;
             if (!std::isfinite(rel)) { c->err = "non-finite residual"; return SE_ERR_NONFINITE; }
-            if (!exact && (rel <= kFp64Switch * rtol || prods >= maxit)) {
-                fp64_res = true;              // from here on the FP64 residual decides
+            // from here on the FP64 residual decides: near rtol, at maxit, or when the
+            // working-precision residual stopped falling (its rounding floor lies above
+            // rtol, so only refinement on the FP64 residual gets further)
+            if (!exact && (rel <= kFp64Switch * rtol || prods >= maxit || rel > 0.5 * rel_wp)) {
+                fp64_res = true;
                 continue;
             }
+            if (!exact) rel_wp = rel;
             if (rel <= rtol || prods >= maxit) break;
             axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0 / beta, r, 0.0, r, V);
             c->launches++;
@@ -761,7 +808,7 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
             for (int j = 0; j < m && prods < maxit; ++j) {
                 double *zj = Zb + (size_t)j * n;
                 if ((rc = Pinv(V + (size_t)j * n, zj)) != SE_OK) return rc;
-                rc = se_apply_internal(c, ncomp, zj, w, SE_F64, c->precision);
+                rc = op(zj, w, c->precision);
                 if (rc != SE_OK) return rc;
                 ++prods;
                 // classical Gram-Schmidt, twice
@@ -809,12 +856,6 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
             c->launches++;
         }
     }
-    if (dtype == SE_F64) {
-        SE_CUDA_CHECK(c, cudaMemcpyAsync(x, xd, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    } else {
-        convert_kernel<double, float><<<grid_for(n), 256, 0, s>>>(n, xd, (float *)x);
-        c->launches++;
-    }
     SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
     if (iters) *iters = prods;
     if (relres) *relres = rel;
@@ -823,4 +864,136 @@ extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype,
         return SE_ERR_NOT_CONVERGED;
     }
     return SE_OK;
+}
+
+extern "C" int se_solve(se_ctx *c, int ncomp, const void *b, void *x, int dtype, double rtol, int maxit,
+                        int precond, int *iters, double *relres)
+{
+    if (!c) return SE_ERR_ARG;
+    if (!b || !x) { c->err = "null b or x"; return SE_ERR_ARG; }
+    if (ncomp != 3 && ncomp != 6 && ncomp != 11 && ncomp != 12) { c->err = "ncomp must be 3, 6, 11 or 12"; return SE_ERR_ARG; }
+    if (dtype != SE_F32 && dtype != SE_F64) { c->err = "bad dtype"; return SE_ERR_ARG; }
+    if (!(rtol > 0) || maxit < 1) { c->err = "rtol must be > 0 and maxit >= 1"; return SE_ERR_ARG; }
+    if (precond < SE_PRECOND_NONE || precond > SE_PRECOND_SPECTRAL) { c->err = "bad preconditioner"; return SE_ERR_ARG; }
+    if (!c->have_config) { c->err = "se_set_config must be called first"; return SE_ERR_STATE; }
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const size_t n = (size_t)c->N * ncomp;
+    int rc = ensure_solver_work(c, n);
+    if (rc != SE_OK) return rc;
+    double *bd = c->b.work64 + 3 * n, *xd = bd + n;      // work vectors 3 and 4: b, x in FP64
+    if (dtype == SE_F64) {
+        SE_CUDA_CHECK(c, cudaMemcpyAsync(bd, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        SE_CUDA_CHECK(c, cudaMemcpyAsync(xd, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+        convert_kernel<float, double><<<grid_for(n), 256, 0, s>>>(n, (const float *)b, bd);
+        convert_kernel<float, double><<<grid_for(n), 256, 0, s>>>(n, (const float *)x, xd);
+        c->launches += 2;
+    }
+    rc = solve_core(c, ncomp, bd, xd, rtol, maxit, precond, 0.0, 1.0, iters, relres);
+    if (rc != SE_OK && rc != SE_ERR_NOT_CONVERGED) return rc;
+    if (dtype == SE_F64) {
+        SE_CUDA_CHECK(c, cudaMemcpyAsync(x, xd, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+        convert_kernel<double, float><<<grid_for(n), 256, 0, s>>>(n, xd, (float *)x);
+        c->launches++;
+    }
+    SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
+    return rc;
+}
+
+// ---------------------------------------------------------------- Brownian IVP
+//
+// x = M^{-1/2} c by the initial value problem of Sec. 4.3 (Eq. ivp-1): with A = s M
+// (s a scale that brings A's self blocks near the identity), x(tau) solves
+//   dx/dtau = -1/2 [tau I + (1 - tau) A]^{-1} (A - I) x,  x(0) = c,
+// and x(1) = A^{-1/2} c, so M^{-1/2} c = sqrt(s) x(1).  n steps of size dtau = 1/n, each
+// an explicit Euler half-step (Eq. ivp-forward) and an implicit one (Eq. ivp-backward):
+//   [tau_i I + (1 - tau_i) A] y = (A - I) x_i,            x_{i+1/2} = x_i - (dtau/4) y,
+//   [(tau_{i+1} - dtau/4) I + (1 - tau_{i+1} + dtau/4) A] x_{i+1}
+//                                = [tau_{i+1} I + (1 - tau_{i+1}) A] x_{i+1/2},
+// the second written with the operator multiplied through by tau_{i+1} I + (1 - tau_{i+1}) A.
+// Both systems are solved by the GMRES above (block preconditioner of the shifted
+// operator), the right-hand sides formed with one product each.
+extern "C" int se_brownian_ivp(se_ctx *c, int ncomp, double scale, int nsteps, double rtol, int maxit,
+                               const double *cvec, double *xout, int *products)
+{
+    if (!c) return SE_ERR_ARG;
+    if (!cvec || !xout) { c->err = "null c or x"; return SE_ERR_ARG; }
+    if (ncomp != 3 && ncomp != 6 && ncomp != 11) {
+        c->err = "ncomp must be 3, 6 or 11 (the F, T, S block is symmetric positive definite)";
+        return SE_ERR_ARG;
+    }
+    if (nsteps < 1 || nsteps > 10000 || !(rtol > 0) || maxit < 1) { c->err = "bad nsteps, rtol or maxit"; return SE_ERR_ARG; }
+    if (!c->have_config) { c->err = "se_set_config must be called first"; return SE_ERR_STATE; }
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const size_t n = (size_t)c->N * ncomp;
+    if (!(scale > 0)) {
+        // default: 6 pi eta <a>, so the translational self block of A is near the identity
+        std::vector<double> rad(c->N);
+        SE_CUDA_CHECK(c, cudaMemcpy(rad.data(), c->b.rad, c->N * sizeof(double), cudaMemcpyDeviceToHost));
+        double am = 0;
+        for (double a : rad) am += a;
+        scale = 6 * kPi * c->eta * am / (double)c->N;
+    }
+    double *xv = nullptr, *yv = nullptr, *tv = nullptr;
+    if (cudaMalloc(&xv, 3 * n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "IVP allocation failed";
+        return SE_ERR_NOMEM;
+    }
+    yv = xv + n;
+    tv = yv + n;
+    int total = 0, status = SE_OK;
+    auto fail = [&](int rc) {
+        cudaFree(xv);
+        if (products) *products = total;
+        return rc;
+    };
+    if (cudaMemcpyAsync(xv, cvec, n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(yv, 0, n * sizeof(double), s) != cudaSuccess) {
+        c->err = "IVP: copy of c failed";
+        return fail(SE_ERR_CUDA);
+    }
+    const double dt = 1.0 / nsteps;
+    for (int i = 0; i < nsteps; ++i) {
+        const double t0 = i * dt, t1 = (i + 1) * dt;
+        // forward half-step: t = (A - I) x, then [t0 I + (1 - t0) A] y = t
+        int rc = se_apply_internal(c, ncomp, xv, tv, SE_F64, c->precision);
+        if (rc != SE_OK) return fail(rc);
+        axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, -1.0, xv, scale, tv, tv);
+        c->launches++;
+        ++total;
+        int it = 0;
+        rc = solve_core(c, ncomp, tv, yv, rtol, maxit, SE_PRECOND_BLOCK, t0, (1 - t0) * scale, &it, nullptr);
+        total += it;
+        if (rc == SE_ERR_NOT_CONVERGED) status = rc;
+        else if (rc != SE_OK) return fail(rc);
+        axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, xv, -0.25 * dt, yv, xv);      // x_{i+1/2}
+        c->launches++;
+        // backward half-step: t = [t1 I + (1 - t1) A] x_{i+1/2}; x_{i+1} starts from x_{i+1/2}
+        rc = se_apply_internal(c, ncomp, xv, tv, SE_F64, c->precision);
+        if (rc != SE_OK) return fail(rc);
+        axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, t1, xv, (1 - t1) * scale, tv, tv);
+        c->launches++;
+        ++total;
+        rc = solve_core(c, ncomp, tv, xv, rtol, maxit, SE_PRECOND_BLOCK, t1 - 0.25 * dt, (1 - t1 + 0.25 * dt) * scale,
+                        &it, nullptr);
+        total += it;
+        if (rc == SE_ERR_NOT_CONVERGED) status = rc;
+        else if (rc != SE_OK) return fail(rc);
+    }
+    axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, std::sqrt(scale), xv, 0.0, xv, xout);
+    c->launches++;
+    const cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(xv);
+    if (e != cudaSuccess) {
+        c->err = std::string("IVP: ") + cudaGetErrorString(e);
+        if (products) *products = total;
+        return SE_ERR_CUDA;
+    }
+    if (products) *products = total;
+    if (status != SE_OK) c->err = "a GMRES solve of the IVP did not reach rtol within maxit products";
+    return status;
 }
