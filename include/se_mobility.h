@@ -196,6 +196,29 @@ int se_real_space_apply_noalloc(int device, void *stream, int64_t N, double L, d
 int se_brownian_ivp(se_ctx *ctx, int ncomp, double scale, int nsteps, double rtol, int maxit,
                     const double *c, double *x, int *products);
 
+/* Rigid spheres driven by forces and torques in the quiescent fluid (E = 0, Sec. 6.1):
+ * [U; Omega; 0] = M [F; T; S] with the stresslets S unknown, so (U, Omega) = mu (F, T)
+ * with mu = M_UF - M_US M_ES^{-1} M_EF, the inverse of the FU block of the far-field
+ * resistance M^{-1}.  Solved as one GMRES system for (U, Omega, S) (one product per
+ * iteration, block preconditioner of that system; the right-hand side M [F; T; 0] in
+ * FP64).
+ *   ft [N][6] (F, T), uw [N][6] (U, Omega), s [N][5] (S on the orthonormal basis; may be
+ *   NULL): FP64 DEVICE arrays, caller order; iters, relres as for se_solve.
+ * Returns SE_ERR_NOT_CONVERGED if rtol was missed (outputs still written); synchronises. */
+int se_rigid_solve(se_ctx *ctx, const double *ft, double *uw, double *s, double rtol, int maxit,
+                   int *iters, double *relres);
+
+/* Far-field short-time self-diffusivities by the matrix-free estimator of Sec. 6.1
+ * (Eq. dstr-def): for random (F, T) with zero mean and unit covariance, the average of
+ * (U, Omega) (F, T) over samples is diag(mu), mu as in se_rigid_solve.
+ *   fr [nsamples][N][6]: the samples (FP64 DEVICE, drawn by the caller), d [N][2]: per
+ *   particle the estimates of tr(mu_ii^tt)/3 and tr(mu_ii^rr)/3 (FP64 DEVICE, caller
+ *   order; times kT these are the particle's translational and rotational diffusivity,
+ *   to be averaged over a species by the caller); products: total products used.
+ * Returns SE_ERR_NOT_CONVERGED if a solve missed rtol; synchronises. */
+int se_far_field_diffusivity(se_ctx *ctx, int nsamples, const double *fr, double *d, double rtol, int maxit,
+                             int *products);
+
 /* Learned preconditioner correction (SE_PRECOND_LEARNED).  A small network (16 -> 64 ->
  * 64 -> 4, tanh, FP32) maps rotation- and permutation-invariant features of a sphere's
  * radius and of its neighbours inside rc to corrections of the isotropic parts of its

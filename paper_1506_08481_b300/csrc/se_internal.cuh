@@ -77,7 +77,7 @@ struct Buffers {
     double *pc_C = nullptr;      // [3][12][12] fitted self-image block coefficients (C0, C1, C2)
     float *mlp_w = nullptr;      // learned correction network (packed parameters)
     double *kry = nullptr;       // Krylov basis [restart + 1][n] and preconditioned vectors [restart][n]
-    double *work64 = nullptr;    // FP64 work vectors [5][n]
+    double *work64 = nullptr;    // FP64 work vectors [6][n]
     size_t kry_n = 0;            // n and restart the Krylov arrays were sized for
     int kry_m = 0;
     double *red = nullptr;       // reduction scratch
@@ -117,6 +117,7 @@ struct se_ctx {
     bool pc_ready = false;
     int pc_ncomp = 0, pc_prec = -1, pc_kind = -1;
     double pc_alpha = 0, pc_beta = 1;  // the blocks invert alpha I + beta M_ii
+    int pc_mixed = 0;                  // ... or the rigid-particle block (se_rigid_solve)
     bool have_mlp = false;
     int pc_fallbacks = 0;              // particles whose learned block fell back to the plain one
     // spectral correction (SE_PRECOND_SPECTRAL): a coarse forces-only context whose

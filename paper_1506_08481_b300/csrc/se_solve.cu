@@ -89,6 +89,21 @@ __global__ void axpby_kernel(size_t n, double a, const double *x, double b, cons
         out[e] = a * x[e] + b * y[e];
 }
 
+// the rigid-particle operator (11 components per particle): ms = v with the force and
+// torque slots zeroed; out -= the force and torque slots of v
+__global__ void mixed_mask_kernel(int N, const double *v, double *ms)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int c = 0; c < 11; ++c) ms[(size_t)i * 11 + c] = c < 6 ? 0.0 : v[(size_t)i * 11 + c];
+}
+__global__ void mixed_fix_kernel(int N, const double *v, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int c = 0; c < 6; ++c) out[(size_t)i * 11 + c] -= v[(size_t)i * 11 + c];
+}
+
 template <typename TI, typename TO>
 __global__ void convert_kernel(size_t n, const TI *x, TO *y)
 {
@@ -119,9 +134,11 @@ __global__ void block_apply_kernel(int N, int nc, const double *Binv, const doub
 // `corr` (may be null, caller order [N][4]): learned dimensionless corrections of the
 // isotropic parts, each scaled by the isolated-sphere mobility of its block.  A learned
 // block that cannot be inverted falls back to the plain block (counted in *fallbacks).
+// mixed = 1 (the rigid-particle system of se_rigid_solve, nc = 11): the columns of the
+// force and torque unknowns are replaced by -I (they hold U, Omega there).
 __global__ void block_build_kernel(int N, int nc, double eta, const double *rad, const int *perm,
                                    const double *C /*[3][12][12]*/, const double *corr, double alpha,
-                                   double beta, double *Binv, int *fallbacks)
+                                   double beta, int mixed, double *Binv, int *fallbacks)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
@@ -146,6 +163,8 @@ retry:
         A[r][r] += iso * (1.0 + dc);
         for (int q = 0; q < nc; ++q) A[r][q] *= beta;
         A[r][r] += alpha;
+        if (mixed)
+            for (int q = 0; q < 6; ++q) A[r][q] = r == q ? -1.0 : 0.0;
     }
     bool ok = true;
     for (int col = 0; col < nc && ok; ++col) {
@@ -184,7 +203,7 @@ retry:
             if (!ok || !isfinite(v)) {
                 const double mob = r < 3 ? 1.0 / (6 * pi * eta * a) : r < 6 ? 1.0 / (8 * pi * eta * a * a2)
                                  : r < 11 ? 3.0 / (20 * pi * eta * a * a2) : 3.0 / (16 * pi * eta * a * a2);
-                v = r == q ? 1.0 / (alpha + beta * mob) : 0.0;
+                v = r == q ? (mixed && r < 6 ? -1.0 : 1.0 / (alpha + beta * mob)) : 0.0;
             }
             out[r * nc + q] = v;
         }
@@ -201,7 +220,7 @@ static int grid_for(size_t n) { size_t g = (n + 255) / 256; return (int)(g > 409
 
 // ---------------------------------------------------------------- preconditioner
 
-static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double beta);
+static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double beta, int mixed = 0);
 
 static int build_precond(se_ctx *c, int ncomp, bool learned)
 {
@@ -294,7 +313,7 @@ static int build_precond(se_ctx *c, int ncomp, bool learned)
 
 // the inverse blocks of alpha I + beta M_ii from the fitted coefficients (learned:
 // with the network's corrections; only for alpha = 0, beta = 1)
-static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double beta)
+static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double beta, int mixed)
 {
     cudaStream_t s = c->stream;
     const int N = (int)c->N;
@@ -324,7 +343,7 @@ static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double
         }
     }
     block_build_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->eta, c->b.rad, c->b.perm, c->b.pc_C, corr, alpha,
-                                                       beta, c->b.pc_inv, dfb);
+                                                       beta, mixed, c->b.pc_inv, dfb);
     c->launches++;
     int fb = 0;
     cudaMemcpyAsync(&fb, dfb, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -341,6 +360,7 @@ static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double
     c->pc_kind = learned ? SE_PRECOND_LEARNED : SE_PRECOND_BLOCK;
     c->pc_alpha = alpha;
     c->pc_beta = beta;
+    c->pc_mixed = mixed;
     return SE_OK;
 }
 
@@ -683,7 +703,7 @@ static int ensure_solver_work(se_ctx *c, size_t n)
     c->b.kry_n = 0;
     // flexible GMRES: Krylov basis V [m + 1][n] and the preconditioned vectors Z [m][n]
     if (cudaMalloc(&c->b.kry, (size_t)(2 * m + 1) * n * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->b.work64, 5 * n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->b.work64, 6 * n * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->b.red, ((size_t)kRedBlocks * (m + 1) + 2 * (m + 1)) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         c->err = "solver allocation failed";
@@ -700,8 +720,12 @@ static int ensure_solver_work(se_ctx *c, size_t n)
 // preconditioner inverts the blocks of alpha I + beta M_ii; the learned and spectral
 // corrections apply to M itself (alpha = 0, beta = 1) only, shifted systems take the
 // block preconditioner.
+//
+// mixed = 1 (ncomp 11, alpha = 0, beta = 1): the rigid-particle system of se_rigid_solve,
+// K w = M (P_S w) - P_FT w, whose unknowns w hold (U, Omega) in the force and torque
+// slots and S in the stresslet slots (P_S, P_FT: the stresslet and force-torque parts).
 static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double rtol, int maxit, int precond,
-                      double alpha, double beta, int *iters, double *relres)
+                      double alpha, double beta, int *iters, double *relres, int mixed = 0)
 {
     cudaStream_t s = c->stream;
     const int m = c->restart;
@@ -713,7 +737,8 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
     Gm gm{c, n, c->b.red, c->b.red + (size_t)kRedBlocks * (m + 1)};
     double *yd = gm.hd + (m + 1);
     const bool shifted = !(alpha == 0.0 && beta == 1.0);
-    if (shifted && precond != SE_PRECOND_NONE) precond = SE_PRECOND_BLOCK;
+    if ((shifted || mixed) && precond != SE_PRECOND_NONE) precond = SE_PRECOND_BLOCK;
+    double *ms = c->b.work64 + 5 * n;     // the masked vector P_S v of the mixed operator
 
     // the learned correction needs trained weights; without them it is the plain block
     const int kind = precond == SE_PRECOND_LEARNED && c->have_mlp ? SE_PRECOND_LEARNED : SE_PRECOND_BLOCK;
@@ -723,8 +748,8 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
             if (rc != SE_OK) return rc;
             free_spectral(c);
         }
-        if (c->pc_kind != kind || c->pc_alpha != alpha || c->pc_beta != beta) {
-            rc = build_blocks(c, ncomp, kind == SE_PRECOND_LEARNED, alpha, beta);
+        if (c->pc_kind != kind || c->pc_alpha != alpha || c->pc_beta != beta || c->pc_mixed != mixed) {
+            rc = build_blocks(c, ncomp, kind == SE_PRECOND_LEARNED, alpha, beta, mixed);
             if (rc != SE_OK) return rc;
             free_spectral(c);
         }
@@ -746,6 +771,14 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
     };
     // out = (alpha I + beta M) v at product precision prec
     auto op = [&](const double *v, double *out, int prec) -> int {
+        if (mixed) {
+            mixed_mask_kernel<<<((int)c->N + 127) / 128, 128, 0, s>>>((int)c->N, v, ms);
+            const int e = se_apply_internal(c, ncomp, ms, out, SE_F64, prec);
+            if (e != SE_OK) return e;
+            mixed_fix_kernel<<<((int)c->N + 127) / 128, 128, 0, s>>>((int)c->N, v, out);
+            c->launches += 2;
+            return SE_OK;
+        }
         const int e = se_apply_internal(c, ncomp, v, out, SE_F64, prec);
         if (e != SE_OK || !shifted) return e;
         axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, alpha, v, beta, out, out);
@@ -995,5 +1028,145 @@ extern "C" int se_brownian_ivp(se_ctx *c, int ncomp, double scale, int nsteps, d
     }
     if (products) *products = total;
     if (status != SE_OK) c->err = "a GMRES solve of the IVP did not reach rtol within maxit products";
+    return status;
+}
+
+// ---------------------------------------------------------------- rigid particles and the
+// far-field self-diffusivities
+//
+// Force- and torque-driven rigid spheres in the quiescent fluid (E = 0): from the grand
+// mobility, [U; Omega; 0] = M [F; T; S] with S unknown, i.e. U = mu (F, T) with
+// mu = M_UF - M_US M_ES^{-1} M_EF, the inverse of the FU block of the far-field resistance
+// M^{-1} (Sec. 6.1, Eq. dstr-def: mu_ii are the diagonal blocks of R_FU^{-1}).  Written as
+// one system for w = (U, Omega, S): M (P_S w) - P_FT w = -M [F; T; 0].
+
+namespace se {
+namespace {
+
+// x11 = (F, T, 0) of particle i from ft [N][6]
+__global__ void embed_ft_kernel(int N, const double *ft, double *x11)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int c = 0; c < 11; ++c) x11[(size_t)i * 11 + c] = c < 6 ? ft[(size_t)i * 6 + c] : 0.0;
+}
+__global__ void split_w_kernel(int N, const double *w, double *uw, double *sv)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int c = 0; c < 6; ++c) uw[(size_t)i * 6 + c] = w[(size_t)i * 11 + c];
+    if (sv)
+        for (int c = 0; c < 5; ++c) sv[(size_t)i * 5 + c] = w[(size_t)i * 11 + 6 + c];
+}
+// d[i] += ((U . F) / 3, (Omega . T) / 3) of one sample
+__global__ void diffusivity_accum_kernel(int N, const double *ft, const double *uw, double *d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double t = 0, r = 0;
+    for (int c = 0; c < 3; ++c) {
+        t += uw[(size_t)i * 6 + c] * ft[(size_t)i * 6 + c];
+        r += uw[(size_t)i * 6 + 3 + c] * ft[(size_t)i * 6 + 3 + c];
+    }
+    d[2 * i] += t / 3.0;
+    d[2 * i + 1] += r / 3.0;
+}
+
+// one rigid-particle solve with device work arrays x11, w11 [N][11]
+int rigid_core(se_ctx *c, const double *ft, double *x11, double *w11, double rtol, int maxit, int *iters,
+               double *relres)
+{
+    cudaStream_t s = c->stream;
+    const int N = (int)c->N;
+    const size_t n = (size_t)N * 11;
+    embed_ft_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ft, x11);
+    c->launches++;
+    int rc = se_apply_internal(c, 11, x11, w11, SE_F64, 1);     // M [F; T; 0] in FP64
+    if (rc != SE_OK) return rc;
+    axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, -1.0, w11, 0.0, w11, x11);   // right-hand side
+    c->launches++;
+    SE_CUDA_CHECK(c, cudaMemsetAsync(w11, 0, n * sizeof(double), s));
+    return solve_core(c, 11, x11, w11, rtol, maxit, SE_PRECOND_BLOCK, 0.0, 1.0, iters, relres, 1);
+}
+
+}  // namespace
+}  // namespace se
+
+extern "C" int se_rigid_solve(se_ctx *c, const double *ft, double *uw, double *sv, double rtol, int maxit,
+                              int *iters, double *relres)
+{
+    if (!c) return SE_ERR_ARG;
+    if (!ft || !uw) { c->err = "null F or U"; return SE_ERR_ARG; }
+    if (!(rtol > 0) || maxit < 1) { c->err = "rtol must be > 0 and maxit >= 1"; return SE_ERR_ARG; }
+    if (!c->have_config) { c->err = "se_set_config must be called first"; return SE_ERR_STATE; }
+    cudaSetDevice(c->device);
+    const int N = (int)c->N;
+    const size_t n = (size_t)N * 11;
+    double *x11 = nullptr;
+    if (cudaMalloc(&x11, 2 * n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "rigid solve allocation failed";
+        return SE_ERR_NOMEM;
+    }
+    double *w11 = x11 + n;
+    int rc = rigid_core(c, ft, x11, w11, rtol, maxit, iters, relres);
+    if (rc == SE_OK || rc == SE_ERR_NOT_CONVERGED) {
+        split_w_kernel<<<(N + 127) / 128, 128, 0, c->stream>>>(N, w11, uw, sv);
+        c->launches++;
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            c->err = std::string("rigid solve: ") + cudaGetErrorString(e);
+            rc = SE_ERR_CUDA;
+        }
+    }
+    cudaFree(x11);
+    return rc;
+}
+
+extern "C" int se_far_field_diffusivity(se_ctx *c, int nsamples, const double *fr, double *d, double rtol,
+                                        int maxit, int *products)
+{
+    if (!c) return SE_ERR_ARG;
+    if (!fr || !d || nsamples < 1) { c->err = "null F^R or d, or nsamples < 1"; return SE_ERR_ARG; }
+    if (!(rtol > 0) || maxit < 1) { c->err = "rtol must be > 0 and maxit >= 1"; return SE_ERR_ARG; }
+    if (!c->have_config) { c->err = "se_set_config must be called first"; return SE_ERR_STATE; }
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int N = (int)c->N;
+    const size_t n = (size_t)N * 11;
+    double *x11 = nullptr;
+    if (cudaMalloc(&x11, (2 * n + (size_t)N * 6 + (size_t)N * 2) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "diffusivity allocation failed";
+        return SE_ERR_NOMEM;
+    }
+    double *w11 = x11 + n, *uw = w11 + n, *acc = uw + (size_t)N * 6;
+    int total = 0, status = SE_OK;
+    cudaMemsetAsync(acc, 0, (size_t)N * 2 * sizeof(double), s);
+    for (int k = 0; k < nsamples; ++k) {
+        const double *ft = fr + (size_t)k * N * 6;
+        int it = 0;
+        int rc = rigid_core(c, ft, x11, w11, rtol, maxit, &it, nullptr);
+        total += it + 1;
+        if (rc == SE_ERR_NOT_CONVERGED) status = rc;
+        else if (rc != SE_OK) {
+            cudaFree(x11);
+            if (products) *products = total;
+            return rc;
+        }
+        split_w_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, w11, uw, nullptr);
+        diffusivity_accum_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ft, uw, acc);
+        c->launches += 2;
+    }
+    axpby_kernel<<<grid_for((size_t)N * 2), 256, 0, s>>>((size_t)N * 2, 1.0 / nsamples, acc, 0.0, acc, d);
+    c->launches++;
+    const cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(x11);
+    if (products) *products = total;
+    if (e != cudaSuccess) {
+        c->err = std::string("diffusivity: ") + cudaGetErrorString(e);
+        return SE_ERR_CUDA;
+    }
+    if (status != SE_OK) c->err = "a rigid-particle solve did not reach rtol within maxit products";
     return status;
 }
