@@ -36,7 +36,9 @@ def _worker(rank, world, port, out):
 
 def test_replica_timing_over_two_gloo_ranks():
     world = 2
-    mgr = mp.Manager()
+    # a spawned manager: the test process may already run the oracle's OpenMP threads,
+    # and a fork of a multi-threaded process can deadlock
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     for rank in range(world):
