@@ -1,0 +1,69 @@
+"""Wave-space accuracy of the particle-size approaches (Sec. 3.2; the comparison of
+Sec. 6.1.1, Eq. err-E): e_inf,r(E) = max_i |E_i^SE - E_i^*| / |E_i^*| of the wave-space
+part alone (FP64) against the oracle's direct-Ewald wave-space part at the same xi, as a
+function of the support P at the best shape parameter m, M = 64, xi a_1 = 0.1, for the
+real-space and the hybrid approach, on a bidisperse suspension (radii 1 and 2).
+
+The paper finds the minimum error decaying like exp(-P pi/2) with the optimal m near
+sqrt(pi P), and e ~ 1e-4 reached at P = 15 (real-space approach) and 13 (hybrid).  The
+test checks the exponential decay, the location of the optimal m, and that the hybrid
+approach needs no larger P than the real-space one for a given error; it prints the
+table it measured."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_1506_08481_b300 import api, inputs  # noqa: E402
+
+
+def e_inf_r(y, ref):
+    """Eq. err-E on the strain-rate rows (5 components, orthonormal basis)."""
+    E, Es = y[:, 6:11], ref[:, 6:11]
+    return float(np.max(np.linalg.norm(E - Es, axis=1) / np.linalg.norm(Es, axis=1)))
+
+
+def test_wave_space_error_against_support(oracle_mod):
+    cfg = inputs.bidisperse(seed=1, n=100, phi=0.2)
+    xi = 0.1
+    x = np.random.default_rng(4).standard_normal((cfg.N, 12))
+    x[:, 11] = 0.0
+    ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x, xi=xi, tol=1e-15, parts=2)
+    Ps = [5, 7, 9, 11, 13, 15, 17, 19]
+    best = {}
+    for mode, name in ((1, "real-space"), (0, "hybrid")):
+        for P in Ps:
+            errs = []
+            for m in np.linspace(0.6, 1.6, 11) * math.sqrt(math.pi * P):
+                ctx = api.Context()
+                ctx.set_params(xi, 64, P, 0.45 * cfg.L)
+                ctx.set_option(api.SE_OPT_PRECISION, 1)
+                ctx.set_option(api.SE_OPT_SIZE_MODE, mode)
+                ctx.set_option(api.SE_OPT_PARTS, 2)
+                ctx.set_option(api.SE_OPT_SHAPE_M, float(m))
+                ctx.set_config(cfg.pos, cfg.rad, cfg.L)
+                y = ctx.apply(torch.tensor(x, device="cuda")).cpu().numpy()
+                errs.append((e_inf_r(y, ref), float(m)))
+                ctx.close()
+            best[(name, P)] = min(errs)
+    print("\n  P   real-space e (m)       hybrid e (m)      [m/sqrt(pi P) at the minimum]")
+    for P in Ps:
+        (er, mr), (eh, mh) = best[("real-space", P)], best[("hybrid", P)]
+        print(f"{P:3d}   {er:9.2e} ({mr:5.2f})   {eh:9.2e} ({mh:5.2f})   "
+              f"[{mr / math.sqrt(math.pi * P):.2f}, {mh / math.sqrt(math.pi * P):.2f}]")
+    need = {}
+    for name in ("real-space", "hybrid"):
+        e = [best[(name, P)][0] for P in Ps]
+        # exponential decay of the minimum error: a decade every few points of P
+        assert e[-1] < 1e-3 * e[0], (name, e)
+        # the optimal m sits near sqrt(pi P)
+        for P in Ps[2:]:
+            assert 0.6 < best[(name, P)][1] / math.sqrt(math.pi * P) < 1.6
+        need[name] = min((P for P in Ps if best[(name, P)][0] <= 1e-4), default=None)
+    print("P needed for e <= 1e-4:", need)
+    assert need["hybrid"] is not None and need["real-space"] is not None
+    assert need["hybrid"] <= need["real-space"]
