@@ -196,17 +196,24 @@ int se_real_space_apply_noalloc(int device, void *stream, int64_t N, double L, d
 int se_brownian_ivp(se_ctx *ctx, int ncomp, double scale, int nsteps, double rtol, int maxit,
                     const double *c, double *x, int *products);
 
-/* Rigid spheres driven by forces and torques in the quiescent fluid (E = 0, Sec. 6.1):
- * [U; Omega; 0] = M [F; T; S] with the stresslets S unknown, so (U, Omega) = mu (F, T)
- * with mu = M_UF - M_US M_ES^{-1} M_EF, the inverse of the FU block of the far-field
- * resistance M^{-1}.  Solved as one GMRES system for (U, Omega, S) (one product per
- * iteration, block preconditioner of that system; the right-hand side M [F; T; 0] in
- * FP64).
- *   ft [N][6] (F, T), uw [N][6] (U, Omega), s [N][5] (S on the orthonormal basis; may be
- *   NULL): FP64 DEVICE arrays, caller order; iters, relres as for se_solve.
+/* Rigid spheres driven by forces and torques and by an imposed strain rate E_inf
+ * (Sec. 6.1): [U; Omega; E_inf] = M [F; T; S] with the stresslets S unknown; for E_inf = 0,
+ * (U, Omega) = mu (F, T) with mu = M_UF - M_US M_ES^{-1} M_EF, the inverse of the FU block
+ * of the far-field resistance M^{-1}.  Solved as one GMRES system for (U, Omega, S) (one
+ * product per iteration, block preconditioner of that system; M [F; T; 0] in FP64).
+ *   ft [N][6] (F, T; may be NULL: force- and torque-free), uw [N][6] (U, Omega), s [N][5]
+ *   (S on the orthonormal basis; may be NULL): FP64 DEVICE arrays, caller order;
+ *   einf: 5 HOST doubles, the imposed strain rate on the orthonormal basis (NULL: 0);
+ *   iters, relres as for se_solve.
  * Returns SE_ERR_NOT_CONVERGED if rtol was missed (outputs still written); synchronises. */
-int se_rigid_solve(se_ctx *ctx, const double *ft, double *uw, double *s, double rtol, int maxit,
-                   int *iters, double *relres);
+int se_rigid_solve(se_ctx *ctx, const double *ft, const double *einf, double *uw, double *s, double rtol,
+                   int maxit, int *iters, double *relres);
+
+/* High-frequency shear viscosity eta_s / eta of the far-field suspension (the eta_s of
+ * Eq. dst-corr): force- and torque-free rigid spheres in each of the five orthonormal
+ * basis strains; eta_s / eta - 1 = sum_i S_i . e_k / (2 eta V), averaged over the five.
+ * products: total products used (may be NULL).  Synchronises. */
+int se_high_frequency_viscosity(se_ctx *ctx, double rtol, int maxit, double *eta_ratio, int *products);
 
 /* Far-field short-time self-diffusivities by the matrix-free estimator of Sec. 6.1
  * (Eq. dstr-def): for random (F, T) with zero mean and unit covariance, the average of

@@ -8,7 +8,9 @@ inverse of the F, T, S grand mobility M, and the rigid spheres' (U, Omega) follo
 averages (U^R, Omega^R)(F^R, T^R) over random (F^R, T^R) of unit covariance, which tends to
 diag(mu).  Everything here is dense numpy on the oracle's matrix (oracle.dense_matrix with
 ncomp = 11), written from those definitions; it shares no code with the CUDA path.
-Pinned in tests/test_diffusivity_oracle.py.
+The high-frequency shear viscosity (the eta_s of Eq. dst-corr) follows from the same
+resistance with forces and torques zero and a strain imposed.  Pinned in
+tests/test_diffusivity_oracle.py.
 """
 import numpy as np
 
@@ -42,6 +44,32 @@ def rigid_response(M11, ft_vec):
     uw = np.linalg.solve(R[np.ix_(ft, ft)], np.asarray(ft_vec, dtype=np.float64).reshape(-1))
     s = R[np.ix_(si, ft)] @ uw
     return uw.reshape(N, 6), s.reshape(N, 5)
+
+
+def rigid_response_strain(M11, e):
+    """(U, Omega) [N, 6] and S [N, 5] of force- and torque-free rigid spheres in the
+    imposed strain rate e (5 numbers on the orthonormal basis): with R = M11^{-1},
+    [F; S] = R [U; E] and F = 0 give R_FU U = -R_FE E, then S = R_SU U + R_SE E."""
+    M11 = np.asarray(M11, dtype=np.float64)
+    N = M11.shape[0] // NC
+    R = np.linalg.inv(M11)
+    ft, si = _ft_index(N), _s_index(N)
+    E = np.tile(np.asarray(e, dtype=np.float64), N)
+    uw = np.linalg.solve(R[np.ix_(ft, ft)], -R[np.ix_(ft, si)] @ E)
+    s = R[np.ix_(si, ft)] @ uw + R[np.ix_(si, si)] @ E
+    return uw.reshape(N, 6), s.reshape(N, 5)
+
+
+def viscosity_ratio(M11, L, eta=1.0):
+    """eta_s / eta: particle stress n <S> of force- and torque-free rigid spheres in each
+    orthonormal basis strain e_k, (sum_i S_i . e_k) / (2 eta V), averaged over k."""
+    acc = 0.0
+    for k in range(5):
+        e = np.zeros(5)
+        e[k] = 1.0
+        _, s = rigid_response_strain(M11, e)
+        acc += s[:, k].sum() / (2 * eta * L ** 3)
+    return 1.0 + acc / 5
 
 
 def diag_traces(mu):

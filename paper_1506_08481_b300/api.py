@@ -36,7 +36,7 @@ SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED, SE_PRECOND_SPECTRAL = 0, 
 # every entry point declared in include/se_mobility.h
 ABI_SYMBOLS = ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
                "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_brownian_ivp", "se_rigid_solve",
-               "se_far_field_diffusivity", "se_last_error",
+               "se_far_field_diffusivity", "se_high_frequency_viscosity", "se_last_error",
                "se_kernel_launches", "se_stage_times", "se_real_space_apply_noalloc",
                "se_set_learned_weights", "se_learned_features", "se_mlp_forward", "se_mlp_grad",
                "se_mlp_adam_step", "se_batch_create", "se_batch_apply", "se_batch_destroy",
@@ -70,7 +70,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.se_mobility_apply_host.argtypes = [p, i, p, p]
     lib.se_solve.argtypes = [p, i, p, p, i, d, i, i, ctypes.POINTER(i), ctypes.POINTER(d)]
     lib.se_brownian_ivp.argtypes = [p, i, d, i, d, i, p, p, ctypes.POINTER(i)]
-    lib.se_rigid_solve.argtypes = [p, p, p, p, d, i, ctypes.POINTER(i), ctypes.POINTER(d)]
+    lib.se_rigid_solve.argtypes = [p, p, p, p, p, d, i, ctypes.POINTER(i), ctypes.POINTER(d)]
+    lib.se_high_frequency_viscosity.argtypes = [p, d, i, ctypes.POINTER(d), ctypes.POINTER(i)]
     lib.se_far_field_diffusivity.argtypes = [p, i, p, p, d, i, ctypes.POINTER(i)]
     lib.se_last_error.argtypes = [p]
     lib.se_last_error.restype = ctypes.c_char_p
@@ -97,7 +98,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("se_batch_create", "se_batch_apply", "se_batch_destroy", "se_batch_status"):
         getattr(lib, name).restype = i
     for name in ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
-                 "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_brownian_ivp", "se_rigid_solve", "se_far_field_diffusivity"):
+                 "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_brownian_ivp", "se_rigid_solve", "se_far_field_diffusivity",
+                 "se_high_frequency_viscosity"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -278,18 +280,25 @@ class Context:
     brownian_ivp = se_brownian_ivp
 
     # --- se_rigid_solve / se_far_field_diffusivity
-    def se_rigid_solve(self, ft, rtol: float = 1e-8, maxit: int = 1000, allow_not_converged: bool = False):
-        """(U, Omega) [N, 6] and S [N, 5] of force- and torque-driven rigid spheres (E = 0)
-        for FP64 CUDA ft [N, 6]; returns (uw, s, iters, relres)."""
+    def se_rigid_solve(self, ft=None, einf=None, rtol: float = 1e-8, maxit: int = 1000,
+                       allow_not_converged: bool = False):
+        """(U, Omega) [N, 6] and S [N, 5] of rigid spheres under forces and torques ft
+        (FP64 CUDA [N, 6] or None) and the imposed strain einf (5 numbers on the
+        orthonormal basis or None); returns (uw, s, iters, relres)."""
         import torch
-        ft = ft.to(torch.float64).contiguous()
-        uw = torch.empty_like(ft)
-        sv = torch.empty(ft.shape[0], 5, device=ft.device, dtype=torch.float64)
+        N = int(self.N)
+        dev = torch.device("cuda", self.device)
+        if ft is not None:
+            ft = ft.to(torch.float64).contiguous()
+        uw = torch.empty(N, 6, device=dev, dtype=torch.float64)
+        sv = torch.empty(N, 5, device=dev, dtype=torch.float64)
+        e = (ctypes.c_double * 5)(*[float(v) for v in einf]) if einf is not None else None
         iters = ctypes.c_int(0)
         relres = ctypes.c_double(0.0)
-        rc = self.lib.se_rigid_solve(self.h, ctypes.c_void_p(ft.data_ptr()), ctypes.c_void_p(uw.data_ptr()),
-                                     ctypes.c_void_p(sv.data_ptr()), float(rtol), int(maxit), ctypes.byref(iters),
-                                     ctypes.byref(relres))
+        rc = self.lib.se_rigid_solve(self.h, ctypes.c_void_p(ft.data_ptr() if ft is not None else 0),
+                                     ctypes.cast(e, ctypes.c_void_p) if e is not None else None,
+                                     ctypes.c_void_p(uw.data_ptr()), ctypes.c_void_p(sv.data_ptr()), float(rtol),
+                                     int(maxit), ctypes.byref(iters), ctypes.byref(relres))
         if not (rc == SE_ERR_NOT_CONVERGED and allow_not_converged):
             self._check(rc)
         return uw, sv, iters.value, relres.value
@@ -310,6 +319,16 @@ class Context:
         return d, prods.value
 
     far_field_diffusivity = se_far_field_diffusivity
+
+    def se_high_frequency_viscosity(self, rtol: float = 1e-6, maxit: int = 1000):
+        """eta_s / eta of the far-field suspension; returns (ratio, products)."""
+        r = ctypes.c_double(0.0)
+        prods = ctypes.c_int(0)
+        self._check(self.lib.se_high_frequency_viscosity(self.h, float(rtol), int(maxit), ctypes.byref(r),
+                                                         ctypes.byref(prods)))
+        return r.value, prods.value
+
+    high_frequency_viscosity = se_high_frequency_viscosity
 
 
 # --- network kernels (stand-alone; device tensors)

@@ -1043,12 +1043,21 @@ extern "C" int se_brownian_ivp(se_ctx *c, int ncomp, double scale, int nsteps, d
 namespace se {
 namespace {
 
-// x11 = (F, T, 0) of particle i from ft [N][6]
+// x11 = (F, T, 0) of particle i from ft [N][6] (ft may be null: zero forces and torques)
 __global__ void embed_ft_kernel(int N, const double *ft, double *x11)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    for (int c = 0; c < 11; ++c) x11[(size_t)i * 11 + c] = c < 6 ? ft[(size_t)i * 6 + c] : 0.0;
+    for (int c = 0; c < 11; ++c) x11[(size_t)i * 11 + c] = c < 6 && ft ? ft[(size_t)i * 6 + c] : 0.0;
+}
+// the right-hand side of the rigid-particle system: out = (0, 0, E_inf) - w11 (w11 = M (F, T, 0))
+__global__ void rigid_rhs_kernel(int N, const double *w11, double e0, double e1, double e2, double e3, double e4,
+                                 double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double e[5] = {e0, e1, e2, e3, e4};
+    for (int c = 0; c < 11; ++c) out[(size_t)i * 11 + c] = (c < 6 ? 0.0 : e[c - 6]) - w11[(size_t)i * 11 + c];
 }
 __global__ void split_w_kernel(int N, const double *w, double *uw, double *sv)
 {
@@ -1072,18 +1081,21 @@ __global__ void diffusivity_accum_kernel(int N, const double *ft, const double *
     d[2 * i + 1] += r / 3.0;
 }
 
-// one rigid-particle solve with device work arrays x11, w11 [N][11]
-int rigid_core(se_ctx *c, const double *ft, double *x11, double *w11, double rtol, int maxit, int *iters,
-               double *relres)
+// one rigid-particle solve with device work arrays x11, w11 [N][11]; einf: the imposed
+// strain rate on the orthonormal basis (5 host doubles) or null
+int rigid_core(se_ctx *c, const double *ft, const double *einf, double *x11, double *w11, double rtol, int maxit,
+               int *iters, double *relres)
 {
     cudaStream_t s = c->stream;
     const int N = (int)c->N;
     const size_t n = (size_t)N * 11;
+    const double z[5] = {0, 0, 0, 0, 0};
+    const double *e = einf ? einf : z;
     embed_ft_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ft, x11);
     c->launches++;
     int rc = se_apply_internal(c, 11, x11, w11, SE_F64, 1);     // M [F; T; 0] in FP64
     if (rc != SE_OK) return rc;
-    axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, -1.0, w11, 0.0, w11, x11);   // right-hand side
+    rigid_rhs_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, w11, e[0], e[1], e[2], e[3], e[4], x11);
     c->launches++;
     SE_CUDA_CHECK(c, cudaMemsetAsync(w11, 0, n * sizeof(double), s));
     return solve_core(c, 11, x11, w11, rtol, maxit, SE_PRECOND_BLOCK, 0.0, 1.0, iters, relres, 1);
@@ -1092,11 +1104,11 @@ int rigid_core(se_ctx *c, const double *ft, double *x11, double *w11, double rto
 }  // namespace
 }  // namespace se
 
-extern "C" int se_rigid_solve(se_ctx *c, const double *ft, double *uw, double *sv, double rtol, int maxit,
-                              int *iters, double *relres)
+extern "C" int se_rigid_solve(se_ctx *c, const double *ft, const double *einf, double *uw, double *sv, double rtol,
+                              int maxit, int *iters, double *relres)
 {
     if (!c) return SE_ERR_ARG;
-    if (!ft || !uw) { c->err = "null F or U"; return SE_ERR_ARG; }
+    if (!uw) { c->err = "null U"; return SE_ERR_ARG; }
     if (!(rtol > 0) || maxit < 1) { c->err = "rtol must be > 0 and maxit >= 1"; return SE_ERR_ARG; }
     if (!c->have_config) { c->err = "se_set_config must be called first"; return SE_ERR_STATE; }
     cudaSetDevice(c->device);
@@ -1109,7 +1121,7 @@ extern "C" int se_rigid_solve(se_ctx *c, const double *ft, double *uw, double *s
         return SE_ERR_NOMEM;
     }
     double *w11 = x11 + n;
-    int rc = rigid_core(c, ft, x11, w11, rtol, maxit, iters, relres);
+    int rc = rigid_core(c, ft, einf, x11, w11, rtol, maxit, iters, relres);
     if (rc == SE_OK || rc == SE_ERR_NOT_CONVERGED) {
         split_w_kernel<<<(N + 127) / 128, 128, 0, c->stream>>>(N, w11, uw, sv);
         c->launches++;
@@ -1146,7 +1158,7 @@ extern "C" int se_far_field_diffusivity(se_ctx *c, int nsamples, const double *f
     for (int k = 0; k < nsamples; ++k) {
         const double *ft = fr + (size_t)k * N * 6;
         int it = 0;
-        int rc = rigid_core(c, ft, x11, w11, rtol, maxit, &it, nullptr);
+        int rc = rigid_core(c, ft, nullptr, x11, w11, rtol, maxit, &it, nullptr);
         total += it + 1;
         if (rc == SE_ERR_NOT_CONVERGED) status = rc;
         else if (rc != SE_OK) {
@@ -1167,6 +1179,59 @@ extern "C" int se_far_field_diffusivity(se_ctx *c, int nsamples, const double *f
         c->err = std::string("diffusivity: ") + cudaGetErrorString(e);
         return SE_ERR_CUDA;
     }
+    if (status != SE_OK) c->err = "a rigid-particle solve did not reach rtol within maxit products";
+    return status;
+}
+
+// High-frequency shear viscosity of the far-field suspension (the eta_s of Eq. dst-corr):
+// force- and torque-free rigid spheres in the imposed strain E_inf = e_k (each of the five
+// orthonormal basis tensors in turn); the particle stress is n <S>, so along e_k
+// eta_s / eta - 1 = (sum_i S_i . e_k) / (2 eta V), averaged over k (an isotropic
+// suspension gives five equal values).  The isolated sphere's S = (20/3) pi eta a^3 E_inf
+// gives Einstein's 1 + 5 phi / 2.
+extern "C" int se_high_frequency_viscosity(se_ctx *c, double rtol, int maxit, double *eta_ratio, int *products)
+{
+    if (!c || !eta_ratio) return SE_ERR_ARG;
+    if (!(rtol > 0) || maxit < 1) { c->err = "rtol must be > 0 and maxit >= 1"; return SE_ERR_ARG; }
+    if (!c->have_config) { c->err = "se_set_config must be called first"; return SE_ERR_STATE; }
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    const int N = (int)c->N;
+    const size_t n = (size_t)N * 11;
+    double *x11 = nullptr;
+    if (cudaMalloc(&x11, 2 * n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "viscosity allocation failed";
+        return SE_ERR_NOMEM;
+    }
+    double *w11 = x11 + n;
+    std::vector<double> h(n);
+    int total = 0, status = SE_OK;
+    double acc = 0;
+    for (int k = 0; k < 5; ++k) {
+        double e[5] = {0, 0, 0, 0, 0};
+        e[k] = 1.0;
+        int it = 0;
+        const int rc = rigid_core(c, nullptr, e, x11, w11, rtol, maxit, &it, nullptr);
+        total += it + 1;
+        if (rc == SE_ERR_NOT_CONVERGED) status = rc;
+        else if (rc != SE_OK) {
+            cudaFree(x11);
+            return rc;
+        }
+        if (cudaMemcpyAsync(h.data(), w11, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaFree(x11);
+            c->err = "viscosity: copy of the stresslets failed";
+            return SE_ERR_CUDA;
+        }
+        double sk = 0;
+        for (int i = 0; i < N; ++i) sk += h[(size_t)i * 11 + 6 + k];
+        acc += sk / (2.0 * c->eta * c->L * c->L * c->L);
+    }
+    cudaFree(x11);
+    *eta_ratio = 1.0 + acc / 5.0;
+    if (products) *products = total;
     if (status != SE_OK) c->err = "a rigid-particle solve did not reach rtol within maxit products";
     return status;
 }

@@ -56,3 +56,20 @@ def test_estimator_converges_to_the_diagonal(oracle_mod):
     # each estimate is a mean of 20000 quadratic forms: standard error ~ |mu_i| sqrt(2/3) / sqrt(20000)
     scale = np.abs(mu).max()
     assert np.abs(est - exact).max() < 6 * scale * math.sqrt(2 / 3) / math.sqrt(20000)
+
+
+def test_viscosity_dilute_limit_is_einstein(oracle_mod):
+    """A single sphere in a large periodic cell: eta_s / eta = 1 + 5 phi / 2 + O(phi^2)
+    (Einstein; the isolated rigid sphere's stresslet (20/3) pi eta a^3 E)."""
+    a = 1.0
+    for L in (20.0, 40.0):
+        M = oracle_mod.dense_matrix(np.array([[1.0, 2.0, 3.0]]), np.array([a]), L, ncomp=11, tol=1e-13)
+        phi = 4 * math.pi / 3 * a ** 3 / L ** 3
+        r = diffusivity.viscosity_ratio(M, L)
+        assert abs(r - 1 - 2.5 * phi) < 10 * phi ** 2, (L, r, phi)
+    # the five basis strains give the same value for a cubic lattice, and the
+    # rigid spheres do not move
+    M = oracle_mod.dense_matrix(np.array([[1.0, 2.0, 3.0]]), np.array([a]), 20.0, ncomp=11, tol=1e-13)
+    uw, s = diffusivity.rigid_response_strain(M, np.array([0.0, 0.0, 1.0, 0.0, 0.0]))
+    assert np.abs(uw).max() < 1e-12
+    np.testing.assert_allclose(s[0, 2], 20 * math.pi / 3 * a ** 3 * (1 + 0.0), rtol=2e-3)

@@ -82,3 +82,20 @@ def test_rigid_solve_fp32_products(oracle_mod):
     uw_or, _ = diffusivity.rigid_response(M, f)
     print(f"FP32 products: U {rel(uw.cpu().numpy(), uw_or):.2e}, {iters} products")
     assert rel(uw.cpu().numpy(), uw_or) <= 1e-5
+
+
+def test_imposed_strain_and_viscosity(poly12):
+    """Force- and torque-free rigid spheres in an imposed strain, and the high-frequency
+    viscosity eta_s / eta, against the oracle's resistance relations."""
+    cfg, M, mu = poly12
+    ctx = make(cfg, 1e-11, precision=1)
+    e = np.array([0.3, -0.2, 1.0, 0.1, 0.5])
+    uw, s, iters, relres = ctx.rigid_solve(None, einf=e, rtol=1e-12)
+    uw_or, s_or = diffusivity.rigid_response_strain(M, e)
+    print(f"imposed strain: U {rel(uw.cpu().numpy(), uw_or):.2e}, S {rel(s.cpu().numpy(), s_or):.2e}")
+    assert rel(s.cpu().numpy(), s_or) <= 1e-8
+    assert rel(uw.cpu().numpy(), uw_or) <= 1e-7
+    r, prods = ctx.high_frequency_viscosity(rtol=1e-12)
+    r_or = diffusivity.viscosity_ratio(M, cfg.L)
+    print(f"eta_s/eta {r:.12f} vs oracle {r_or:.12f}, {prods} products")
+    assert abs(r - r_or) <= 1e-9 * r_or
