@@ -58,6 +58,7 @@ typedef struct se_ctx se_ctx;
 #define SE_ERR_NOT_CONVERGED -7   /* GMRES reached maxit (x holds the last iterate) */
 #define SE_ERR_NOMEM         -8   /* device allocation failed */
 #define SE_ERR_TOO_LARGE     -9   /* problem larger than a fixed capacity (se_real_space_apply_noalloc) */
+#define SE_ERR_OVERLAP      -10   /* two spheres overlap, |x_ij| < (a_i + a_j)(1 - 1e-12), with |x_ij| < rc */
 
 /* dtypes of x / y */
 #define SE_F32 0
@@ -87,6 +88,12 @@ typedef struct se_ctx se_ctx;
 #define SE_OPT_SPREAD     12   /* spreading kernel: 0 = default (FP32: 8 x 8 x 16 tiles with packed FP32
                                   FMAs where the grid has room for them, else 8^3 tiles), 1 = 8^3
                                   tiles always; results agree to rounding */
+
+#define SE_OPT_OVERLAP_CHECK 13  /* 1 (default): se_set_config fails with SE_ERR_OVERLAP if two spheres within
+                                  the real-space cutoff overlap (touching is allowed; the far-field
+                                  interactions of overlapping spheres are not those of the paper, and
+                                  coincident centres make them infinite); 0: no check.  The check runs
+                                  with the pair-table build of the configuration's working precision */
 
 /* product stages reported by se_stage_times */
 #define SE_STAGE_PERMUTE   0   /* inputs into cell order */

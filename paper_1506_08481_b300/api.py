@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libse_b300.so")
 SE_OK = 0
 SE_ERR_ARG, SE_ERR_GRID, SE_ERR_CUTOFF, SE_ERR_CUDA = -1, -2, -3, -4
 SE_ERR_STATE, SE_ERR_NONFINITE, SE_ERR_NOT_CONVERGED, SE_ERR_NOMEM = -5, -6, -7, -8
-SE_ERR_TOO_LARGE = -9
+SE_ERR_TOO_LARGE, SE_ERR_OVERLAP = -9, -10
 SE_NOALLOC_MAX_N = 8192
 SE_F32, SE_F64 = 0, 1
 SE_OPT_PRECISION, SE_OPT_SIZE_MODE, SE_OPT_ETA, SE_OPT_SHAPE_M, SE_OPT_RESTART, SE_OPT_PARTS = 1, 2, 3, 4, 5, 6
@@ -28,6 +28,7 @@ SE_OPT_TIMING = 7
 SE_OPT_OVERLAP = 8
 SE_OPT_GATHER = 9
 SE_OPT_SPREAD = 12
+SE_OPT_OVERLAP_CHECK = 13
 SE_OPT_PC_THETA = 10
 SE_OPT_PC_KA = 11
 STAGES = ("permute", "real", "spread", "fft_x_fwd", "fft_y_fwd", "fft_z_scale", "fft_y_inv", "fft_x_inv", "gather")

@@ -211,6 +211,7 @@ static int ensure_support(se_ctx *c, int prec)
         // the stored pair table is an optimisation: without memory for it the
         // real-space kernel recomputes the pairs from the cell list
         const int r = prec == 1 ? build_pair_table<double>(c) : build_pair_table<float>(c);
+        if (r == SE_ERR_OVERLAP) return r;
         if (r != SE_OK) {
             cudaGetLastError();
             dfree(c->b.pair_x[prec]);
@@ -384,6 +385,10 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
     case SE_OPT_SPREAD:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "spread must be 0 or 1");
         c->spread = (int)value;
+        return SE_OK;
+    case SE_OPT_OVERLAP_CHECK:
+        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "overlap check must be 0 or 1");
+        c->overlap_check = (int)value;
         return SE_OK;
     case SE_OPT_TIMING:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "timing must be 0 or 1");

@@ -102,6 +102,7 @@ struct se_ctx {
     int overlap = 2;             // SE_OPT_OVERLAP
     int gather = 0;              // SE_OPT_GATHER
     int spread = 0;              // SE_OPT_SPREAD
+    int overlap_check = 1;       // SE_OPT_OVERLAP_CHECK
     int nsplit = 1;              // CTAs sharing a spreading tile (few tiles: small M)
     // configuration
     bool have_config = false;

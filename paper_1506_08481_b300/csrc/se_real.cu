@@ -422,24 +422,37 @@ __device__ __forceinline__ void for_neighbours(int i, const PairSearch &ps, cons
                                      y2 = min_image(pz - pos[3 * j + 2], ps.L);
                         if (!(y0 * y0 + y1 * y1 + y2 * y2 < ps.rc2)) continue;
                     }
-                    f(j);
+                    f(j, r2f, pj.w);
                 }
             }
 }
 
-__global__ void pos_f32_kernel(int N, const double *pos, float4 *pf)
+__global__ void pos_f32_kernel(int N, const double *pos, const double *rad, float4 *pf)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) pf[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], 0.f);
+    if (i < N) pf[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], (float)rad[i]);
 }
 
-__global__ void pair_count_kernel(int N, PairSearch ps, const int *cell_start, const double *pos, const float4 *pf,
-                                  int *count)
+// Counts the pairs of target i; with `overlap` set, also flags a pair inside rc whose
+// spheres overlap, |x| < (a_i + a_j)(1 - 1e-12) in FP64 (an FP32 prefilter with a 1e-4
+// margin picks the candidates; touching spheres are allowed).
+__global__ void pair_count_kernel(int N, PairSearch ps, const int *cell_start, const double *pos, const double *rad,
+                                  const float4 *pf, int *count, int *overlap)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int n = 0;
-    for_neighbours(i, ps, cell_start, pos, pf, [&](int) { ++n; });
+    const float ai = pf[i].w;
+    for_neighbours(i, ps, cell_start, pos, pf, [&](int j, float r2f, float aj) {
+        ++n;
+        const float sa = ai + aj;
+        if (overlap && r2f < sa * sa * 1.0001f) {
+            const double y0 = min_image(pos[3 * i] - pos[3 * j], ps.L), y1 = min_image(pos[3 * i + 1] - pos[3 * j + 1], ps.L),
+                         y2 = min_image(pos[3 * i + 2] - pos[3 * j + 2], ps.L);
+            const double s = (rad[i] + rad[j]) * (1.0 - 1e-12);
+            if (y0 * y0 + y1 * y1 + y2 * y2 < s * s) atomicExch(overlap, 1);
+        }
+    });
     count[i] = n;
 }
 
@@ -449,7 +462,7 @@ __global__ void pair_list_kernel(int N, PairSearch ps, const int *cell_start, co
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int k = off[i];
-    for_neighbours(i, ps, cell_start, pos, pf, [&](int j) { pj[k++] = j; });
+    for_neighbours(i, ps, cell_start, pos, pf, [&](int j, float, float) { pj[k++] = j; });
 }
 
 // One warp per target: the lanes take the target's pairs in turn, form the FP64
@@ -524,7 +537,7 @@ int build_pair_table(se_ctx *c)
             return SE_ERR_CUDA;
         };
         if (cudaMalloc(&c->b.pair_off, (N + 1) * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&count, N * sizeof(int)) != cudaSuccess || cudaMalloc(&pf, N * sizeof(float4)) != cudaSuccess)
+            cudaMalloc(&count, (N + 1) * sizeof(int)) != cudaSuccess || cudaMalloc(&pf, N * sizeof(float4)) != cudaSuccess)
             return fail();
         PairSearch ps;
         ps.L = c->L;
@@ -534,13 +547,22 @@ int build_pair_table(se_ctx *c)
         const double mrg = std::ldexp(c->L + c->rc, -20);
         ps.lo = (float)((c->rc - mrg) * (c->rc - mrg));
         ps.hi = (float)((c->rc + mrg) * (c->rc + mrg));
-        pos_f32_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, c->b.pos, pf);
-        pair_count_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ps, c->b.cell_start, c->b.pos, pf, count);
+        int *ovl = c->overlap_check ? count + N : nullptr;    // the flag after the counts
+        if (ovl) cudaMemsetAsync(ovl, 0, sizeof(int), s);
+        pos_f32_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, c->b.pos, c->b.rad, pf);
+        pair_count_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ps, c->b.cell_start, c->b.pos, c->b.rad, pf, count, ovl);
         c->launches += 2;
         launch_scan(c, N, count, c->b.pair_off, s);
-        int np = 0;
+        int np = 0, hov = 0;
         cudaMemcpyAsync(&np, c->b.pair_off + N, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (ovl) cudaMemcpyAsync(&hov, ovl, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (int rc = sync()) return rc;
+        if (hov) {
+            release();
+            drop_lists();
+            c->err = "two spheres overlap (|x_ij| < a_i + a_j) within the real-space cutoff";
+            return SE_ERR_OVERLAP;
+        }
         c->npairs = (size_t)np;
         if (cudaMalloc(&c->b.pair_j, (c->npairs + 1) * sizeof(int)) != cudaSuccess) return fail();
         pair_list_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ps, c->b.cell_start, c->b.pos, pf, c->b.pair_off,

@@ -286,3 +286,33 @@ def test_spread_variants_agree(small_poly, small_poly_ref, M, P, ncomp):
     assert rel(out[0], out[1]) <= 2e-6
     if M == 72 and ncomp == 12:
         assert rel(out[0], small_poly_ref) <= 1e-5
+
+
+def test_overlap_detection():
+    """se_set_config rejects overlapping spheres within rc (SE_ERR_OVERLAP), including
+    across the periodic boundary and coincident centres; touching spheres are accepted;
+    SE_OPT_OVERLAP_CHECK 0 turns the check off."""
+    L = 10.0
+    rad = np.array([1.0, 1.0, 0.5])
+    cases = {
+        "overlap": (np.array([[2.0, 2.0, 2.0], [3.9, 2.0, 2.0], [7.0, 7.0, 7.0]]), True),
+        "periodic": (np.array([[0.5, 5.0, 5.0], [9.0, 5.0, 5.0], [5.0, 1.0, 8.0]]), True),   # 1.5 apart
+        "coincident": (np.array([[4.0, 4.0, 4.0], [4.0, 4.0, 4.0], [8.0, 8.0, 8.0]]), True),
+        "touching": (np.array([[2.0, 2.0, 2.0], [4.0, 2.0, 2.0], [7.0, 7.0, 7.0]]), False),
+    }
+    for name, (pos, bad) in cases.items():
+        ctx = api.Context()
+        ctx.set_params(1.0, 32, 8, 4.0)
+        if bad:
+            with pytest.raises(api.SeError) as e:
+                ctx.set_config(pos, rad, L)
+            assert e.value.code == api.SE_ERR_OVERLAP, name
+        else:
+            ctx.set_config(pos, rad, L)
+            y = ctx.apply(torch.ones(3, 12, device="cuda", dtype=torch.float64))
+            assert torch.isfinite(y).all(), name
+    ctx = api.Context()
+    ctx.set_params(1.0, 32, 8, 4.0)
+    ctx.set_option(api.SE_OPT_OVERLAP_CHECK, 0)
+    ctx.set_config(cases["overlap"][0], rad, L)
+    assert torch.isfinite(ctx.apply(torch.ones(3, 12, device="cuda", dtype=torch.float64))).all()
