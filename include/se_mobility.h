@@ -65,7 +65,10 @@ typedef struct se_ctx se_ctx;
 #define SE_F64 1
 
 /* options for se_set_option */
-#define SE_OPT_PRECISION   1   /* compute precision of products: 0 = FP32 (default), 1 = FP64 */
+#define SE_OPT_PRECISION   1   /* compute precision of products: 0 = FP32 (default), 1 = FP64, 2 = FP64-
+                                  equivalent: spread and gather in double-float arithmetic (pairs of
+                                  FP32 numbers, ~2^-44 relative), the rest in FP64; same accuracy as 1
+                                  at a fraction of its time on B300's FP64 rate */
 #define SE_OPT_SIZE_MODE   2   /* particle-size terms: 0 = hybrid (default), 1 = real-space approach */
 #define SE_OPT_ETA         3   /* solvent viscosity (default 1) */
 #define SE_OPT_SHAPE_M     4   /* Gaussian shape parameter m of Eq. theta-param (default sqrt(pi P)) */
@@ -89,6 +92,8 @@ typedef struct se_ctx se_ctx;
                                   FMAs where the grid has room for them, else 8^3 tiles), 1 = 8^3
                                   tiles always; results agree to rounding */
 
+#define SE_OPT_RESIDUAL   14   /* precision of the solver's true residuals and right-hand-side products
+                                  when the products run in FP32: 2 (default, double-float) or 1 (FP64) */
 #define SE_OPT_OVERLAP_CHECK 13  /* 1 (default): se_set_config fails with SE_ERR_OVERLAP if two spheres within
                                   the real-space cutoff overlap (touching is allowed; the far-field
                                   interactions of overlapping spheres are not those of the paper, and

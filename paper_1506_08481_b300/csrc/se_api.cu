@@ -101,7 +101,7 @@ static void dfree_t(P *&p)
 
 static void free_grids(se_ctx *c)
 {
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < 3; ++q) {
         dfree(c->b.grid_f[q]);
         dfree(c->b.grid_part[q]);
         dfree(c->b.spec_f[q]);
@@ -122,7 +122,7 @@ static void free_config(se_ctx *c)
     dfree_t(c->b.tile_perm);
     dfree_t(c->b.tile_start);
     dfree_t(c->b.sup_base);
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < 3; ++q) {
         dfree(c->b.sup_s0[q]);
         dfree(c->b.sup_w[q]);
         dfree(c->b.self_c[q]);
@@ -133,7 +133,7 @@ static void free_config(se_ctx *c)
     }
     dfree_t(c->b.pair_off);
     dfree_t(c->b.pair_j);
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < 3; ++q) {
         dfree(c->b.pair_x[q]);
         dfree(c->b.pair_c[q]);
         c->pairs_ok[q] = false;
@@ -161,9 +161,44 @@ static void free_config(se_ctx *c)
         }                                                                             \
     } while (0)
 
+template <typename TI, typename TO>
+__global__ void cvt_kernel(size_t n, const TI *in, TO *out)
+{
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = (TO)in[e];
+}
+template <typename TI, typename TO>
+static void launch_cvt(se_ctx *c, size_t n, const void *in, void *out, cudaStream_t s)
+{
+    const size_t g = std::min<size_t>((n + 255) / 256, 8192);
+    cvt_kernel<TI, TO><<<(unsigned)std::max<size_t>(g, 1), 256, 0, s>>>(n, (const TI *)in, (TO *)out);
+    c->launches++;
+}
+
+static int ensure_grids(se_ctx *c, int prec);
+
+// the double-float (precision 2) grids: spread and gathered grids in double-float, the
+// spectra, twiddles and the FFT's own grids those of FP64
+static int ensure_grids_ff(se_ctx *c)
+{
+    int rc = ensure_grids(c, 1);
+    if (rc != SE_OK) return rc;
+    if (c->grid_M[2] == (size_t)c->M && c->b.grid_f[2]) return SE_OK;
+    dfree(c->b.grid_f[2]);
+    dfree(c->b.grid_part[2]);
+    dfree(c->b.grid_o[2]);
+    const size_t M = c->M;
+    SE_ALLOC(c, c->b.grid_f[2], M * M * M * 4 * sizeof(ff));
+    if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[2], (size_t)c->nsplit * M * M * M * 4 * sizeof(ff));
+    SE_ALLOC(c, c->b.grid_o[2], M * M * M * 8 * sizeof(ff));
+    c->grid_M[2] = c->M;
+    return SE_OK;
+}
+
 // grids for (M, precision prec)
 static int ensure_grids(se_ctx *c, int prec)
 {
+    if (prec == 2) return ensure_grids_ff(c);
     const size_t es = prec == 1 ? sizeof(double) : sizeof(float);
     if (c->grid_M[prec] == (size_t)c->M && c->b.grid_f[prec]) return SE_OK;
     dfree(c->b.grid_f[prec]);
@@ -190,9 +225,36 @@ static int ensure_grids(se_ctx *c, int prec)
     return SE_OK;
 }
 
+static int ensure_support(se_ctx *c, int prec);
+
+// double-float support: the FP64 tables (and the FP64 pair table of the real-space sum)
+// converted once per configuration
+static int ensure_support_ff(se_ctx *c)
+{
+    int rc = ensure_support(c, 1);
+    if (rc != SE_OK) return rc;
+    const size_t N = c->N;
+    if (!c->b.xs[2]) SE_ALLOC(c, c->b.xs[2], N * kNC * sizeof(ff));
+    if (!c->b.yreal[2]) SE_ALLOC(c, c->b.yreal[2], N * kNC * sizeof(ff));
+    if (!c->support_ok[2]) {
+        dfree(c->b.sup_w[2]);
+        if (!c->b.sup_s0[2]) SE_ALLOC(c, c->b.sup_s0[2], N * 3 * sizeof(ff));
+        if (!c->b.self_c[2]) SE_ALLOC(c, c->b.self_c[2], N * 4 * sizeof(ff));
+        SE_ALLOC(c, c->b.sup_w[2], N * 3 * c->P * sizeof(ff));
+        cudaStream_t s = c->stream;
+        launch_cvt<double, ff>(c, N * 3, c->b.sup_s0[1], c->b.sup_s0[2], s);
+        launch_cvt<double, ff>(c, N * 3 * c->P, c->b.sup_w[1], c->b.sup_w[2], s);
+        launch_cvt<double, ff>(c, N * 4, c->b.self_c[1], c->b.self_c[2], s);
+        SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
+        c->support_ok[2] = true;
+    }
+    return SE_OK;
+}
+
 // support tables and work vectors at precision prec
 static int ensure_support(se_ctx *c, int prec)
 {
+    if (prec == 2) return ensure_support_ff(c);
     if (c->alloc_N == 0 || !c->b.pos) {
         c->err = "se_set_config must be called first";
         return SE_ERR_STATE;
@@ -327,7 +389,8 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
     if (!c) return SE_ERR_ARG;
     switch (key) {
     case SE_OPT_PRECISION:
-        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "precision must be 0 (FP32) or 1 (FP64)");
+        if (value != 0 && value != 1 && value != 2)
+            return set_error(c, SE_ERR_ARG, "precision must be 0 (FP32), 1 (FP64) or 2 (FP64-equivalent double-float)");
         c->precision = (int)value;
         return SE_OK;
     case SE_OPT_SIZE_MODE:
@@ -340,7 +403,7 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         if (value != c->eta) {
             // the stored pair coefficients and the self coefficients carry 1/eta
             c->eta = value;
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < 3; ++q) {
                 dfree(c->b.pair_x[q]);
                 dfree(c->b.pair_c[q]);
                 c->pairs_ok[q] = false;
@@ -353,7 +416,7 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         if (!(value > 0)) return set_error(c, SE_ERR_ARG, "m must be positive");
         c->m_shape = value;
         c->m_user = true;
-        c->support_ok[0] = c->support_ok[1] = false;
+        c->support_ok[0] = c->support_ok[1] = c->support_ok[2] = false;
         c->pc_ready = false;
         return SE_OK;
     case SE_OPT_RESTART:
@@ -385,6 +448,10 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
     case SE_OPT_SPREAD:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "spread must be 0 or 1");
         c->spread = (int)value;
+        return SE_OK;
+    case SE_OPT_RESIDUAL:
+        if (value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "residual precision must be 1 or 2");
+        c->res_precision = (int)value;
         return SE_OK;
     case SE_OPT_OVERLAP_CHECK:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "overlap check must be 0 or 1");
@@ -487,6 +554,45 @@ static int apply_t(se_ctx *c, int ncomp, const TO *x, TO *y)
     return SE_OK;
 }
 
+// FP64-equivalent product (precision 2): the real-space sum, the FFT and the k-space
+// scaling in FP64, the spread and gather (the FP64-pipe-bound stages) in double-float
+template <typename TO>
+static int apply_ff(se_ctx *c, int ncomp, const TO *x, TO *y)
+{
+    cudaStream_t s = c->stream;
+    const size_t N = c->N;
+    double *xs1 = (double *)c->b.xs[1], *yr1 = (double *)c->b.yreal[1];
+    ff *xs2 = (ff *)c->b.xs[2], *yr2 = (ff *)c->b.yreal[2];
+    const int with_wave = (c->parts & 2) ? 1 : 0;
+    stage_mark(c, SE_STAGE_PERMUTE, s, false);
+    launch_permute_in<double, TO>(c, x, xs1, ncomp, s);
+    launch_cvt<double, ff>(c, N * kNC, xs1, xs2, s);
+    stage_mark(c, SE_STAGE_PERMUTE, s, true);
+    stage_mark(c, SE_STAGE_REAL, s, false);
+    if (c->parts & 1) launch_real<double>(c, xs1, yr1, s, ncomp);
+    else SE_CUDA_CHECK(c, cudaMemsetAsync(yr1, 0, N * kNC * sizeof(double), s));
+    launch_cvt<double, ff>(c, N * kNC, yr1, yr2, s);
+    stage_mark(c, SE_STAGE_REAL, s, true);
+    const size_t M3 = (size_t)c->M * c->M * c->M;
+    if (with_wave) {
+        launch_wave_spread<ff>(c, xs2, s, ncomp);
+        launch_cvt<ff, double>(c, M3 * 4, c->b.grid_f[2], c->b.grid_f[1], s);
+        launch_wave_fft<double>(c, s);
+        launch_cvt<double, ff>(c, M3 * (c->size_mode == 0 ? 8 : 4), c->b.grid_o[1], c->b.grid_o[2], s);
+    } else {
+        for (int st = SE_STAGE_SPREAD; st <= SE_STAGE_FFT_XI; ++st) {
+            stage_mark(c, st, s, false);
+            stage_mark(c, st, s, true);
+        }
+    }
+    stage_mark(c, SE_STAGE_GATHER, s, false);
+    launch_gather_combine<ff, TO>(c, xs2, yr2, y, ncomp, with_wave, s);
+    stage_mark(c, SE_STAGE_GATHER, s, true);
+    if (c->timing) c->tprod++;
+    SE_CUDA_CHECK(c, cudaGetLastError());
+    return SE_OK;
+}
+
 int se::se_apply_internal(se_ctx *c, int ncomp, const void *x, void *y, int dtype, int prec)
 {
     if (!c->have_config) return set_error(c, SE_ERR_STATE, "se_set_config must be called first");
@@ -494,6 +600,10 @@ int se::se_apply_internal(se_ctx *c, int ncomp, const void *x, void *y, int dtyp
     if (rc != SE_OK) return rc;
     rc = ensure_grids(c, prec);
     if (rc != SE_OK) return rc;
+    if (prec == 2) {
+        return dtype == SE_F64 ? apply_ff<double>(c, ncomp, (const double *)x, (double *)y)
+                               : apply_ff<float>(c, ncomp, (const float *)x, (float *)y);
+    }
     if (prec == 1) {
         return dtype == SE_F64 ? apply_t<double, double>(c, ncomp, (const double *)x, (double *)y)
                                : apply_t<double, float>(c, ncomp, (const float *)x, (float *)y);

@@ -1,0 +1,91 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two FP32 numbers
+// (|lo| <= ulp(hi) / 2 after normalisation), carrying about 44 significant bits.  The
+// products of the FP64-equivalent mode (SE_OPT_PRECISION 2) run their spread and gather
+// in it: B300's FP32 pipe issues many times the FMAs of its FP64 pipe, and a double-float
+// multiply-add costs about a dozen FP32 instructions.  The type `ff` carries the
+// arithmetic operators the templated spread, gather and combine code uses, so those
+// kernels are instantiated on it unchanged.
+//
+// Building blocks (exact transformations of FP32 arithmetic; Dekker 1971, Knuth's
+// TwoSum): fl(a b) + fma(a, b, -fl(a b)) = a b, and two_sum(a, b) = a + b exactly as s + e.
+// Products keep the cross terms a.hi b.lo + a.lo b.hi; sums add the low parts after
+// the exact sum of the high parts (the "sloppy" double-float sum: relative error
+// ~2^-44 of the larger operand).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace se {
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)   // |a| >= |b|
+{
+    s = a + b;
+    e = b - (s - a);
+}
+
+struct ff {
+    float hi, lo;
+    ff() = default;
+    __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}
+    __device__ ff(int v) : hi((float)v), lo((float)(v - (int)(float)v)) {}
+    __device__ ff(float v) : hi(v), lo(0.f) {}
+    __device__ ff(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __device__ explicit operator float() const { return hi + lo; }
+    __device__ explicit operator int() const { return (int)((double)hi + (double)lo); }
+};
+
+__device__ __forceinline__ ff ff_norm(float hi, float lo)
+{
+    ff r;
+    fast_two_sum(hi, lo, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ ff operator+(ff a, ff b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return ff_norm(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+__device__ __forceinline__ ff operator*(ff a, ff b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return ff_norm(p, e);
+}
+__device__ __forceinline__ ff operator/(ff a, ff b)
+{
+    // q1 = a/b to FP32, one correction step on the double-float remainder
+    const float q1 = a.hi / b.hi;
+    const ff r = a - b * ff(q1);
+    const float q2 = r.hi / b.hi;
+    return ff_norm(q1, q2);
+}
+__device__ __forceinline__ ff &operator+=(ff &a, ff b) { return a = a + b; }
+__device__ __forceinline__ ff &operator-=(ff &a, ff b) { return a = a - b; }
+__device__ __forceinline__ ff &operator*=(ff &a, ff b) { return a = a * b; }
+__device__ __forceinline__ bool operator==(ff a, ff b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator!=(ff a, ff b) { return !(a == b); }
+
+// warp exchange of any arithmetic type or of a double-float
+template <typename T>
+__device__ __forceinline__ T shfl_xor(unsigned mask, T v, int off) { return __shfl_xor_sync(mask, v, off); }
+__device__ __forceinline__ ff shfl_xor(unsigned mask, ff v, int off)
+{
+    return ff(__shfl_xor_sync(mask, v.hi, off), __shfl_xor_sync(mask, v.lo, off));
+}
+
+struct __align__(32) ff4 {
+    ff x, y, z, w;
+};
+
+}  // namespace se

@@ -7,7 +7,10 @@
 #include <string>
 #include <vector>
 
+#include <type_traits>
+
 #include "../../include/se_mobility.h"
+#include "se_ff.cuh"
 
 namespace se {
 
@@ -19,7 +22,11 @@ constexpr int kSMs = 148;        // streaming multiprocessors of a B300 (grid si
 template <typename T> struct C2;
 template <> struct C2<float> { using t = float2; };
 template <> struct C2<double> { using t = double2; };
-template <typename T> constexpr int pix() { return sizeof(T) == 8 ? 1 : 0; }
+// index of the per-precision buffers: FP32, FP64, double-float (SE_OPT_PRECISION 0, 1, 2)
+template <typename T> constexpr int pix()
+{
+    return std::is_same<T, float>::value ? 0 : (std::is_same<T, double>::value ? 1 : 2);
+}
 
 // radices of a mixed-radix Stockham FFT of length M = 2^a 3^b
 struct FftPlan {
@@ -53,23 +60,23 @@ struct Buffers {
     int *tile_start = nullptr;   // [ntile^3 + 1]
     int *sup_base = nullptr;     // [N][3] first support point (wrapped)
     // per compute precision (index 0: FP32, 1: FP64)
-    void *sup_s0[2] = {};        // [N][3] T: offset of the first support point from the particle
-    void *sup_w[2] = {};         // [N][3][P] T: Gaussian weights along each axis
-    void *self_c[2] = {};        // [N][4] T: self coefficients of U, Omega, E, E_tr (computed in FP64)
-    void *rel[2] = {};           // [N][4] T offset from the cell origin (3) and radius
-    void *xs[2] = {};            // [N][12] T inputs in cell order
-    void *yreal[2] = {};         // [N][12] T real-space result
-    void *grid_f[2] = {};        // [M^3][4] T spread grids
-    void *grid_part[2] = {};     // [nsplit][M^3][4] T partial spread grids (small grids only)
-    void *spec_f[2] = {};        // [M][M][Mh][4] complex T
-    void *spec_o[2] = {};        // [M][M][Mh][8] complex T
-    void *grid_o[2] = {};        // [M^3][8] T gathered grids
-    void *tw[2] = {};            // [M] complex T twiddles
+    void *sup_s0[3] = {};        // [N][3] T: offset of the first support point from the particle
+    void *sup_w[3] = {};         // [N][3][P] T: Gaussian weights along each axis
+    void *self_c[3] = {};        // [N][4] T: self coefficients of U, Omega, E, E_tr (computed in FP64)
+    void *rel[3] = {};           // [N][4] T offset from the cell origin (3) and radius
+    void *xs[3] = {};            // [N][12] T inputs in cell order
+    void *yreal[3] = {};         // [N][12] T real-space result
+    void *grid_f[3] = {};        // [M^3][4] T spread grids
+    void *grid_part[3] = {};     // [nsplit][M^3][4] T partial spread grids (small grids only)
+    void *spec_f[3] = {};        // [M][M][Mh][4] complex T
+    void *spec_o[3] = {};        // [M][M][Mh][8] complex T
+    void *grid_o[3] = {};        // [M^3][8] T gathered grids
+    void *tw[3] = {};            // [M] complex T twiddles
     // stored real-space pairs (Sec. 3.3): CSR over targets in cell order
     int *pair_off = nullptr;     // [N + 1]
     int *pair_j = nullptr;       // [npairs]
-    void *pair_x[2] = {};        // [3][npairs] T separations (SoA)
-    void *pair_c[2] = {};        // [19][npairs] T radial coefficients (SoA)
+    void *pair_x[3] = {};        // [3][npairs] T separations (SoA)
+    void *pair_c[3] = {};        // [19][npairs] T radial coefficients (SoA)
     // host-API staging (device side)
     double *stage = nullptr;     // [2][N][12]
     // solver
@@ -95,7 +102,8 @@ struct se_ctx {
     double xi = 0, rc = 0, m_shape = 0, eta = 1.0;
     bool m_user = false;
     int M = 0, P = 0;
-    int precision = 0;                 // 0 FP32, 1 FP64
+    int precision = 0;                 // 0 FP32, 1 FP64, 2 FP64-equivalent (double-float spread/gather)
+    int res_precision = 2;             // true residuals of the solver (SE_OPT_RESIDUAL): 1 FP64, 2 double-float
     int size_mode = 0;                 // 0 hybrid, 1 real-space approach
     int restart = 30;
     int parts = 7;
@@ -106,11 +114,11 @@ struct se_ctx {
     int nsplit = 1;              // CTAs sharing a spreading tile (few tiles: small M)
     // configuration
     bool have_config = false;
-    bool support_ok[2] = {false, false};
+    bool support_ok[3] = {false, false, false};
     bool tiles_ok = false;
-    bool pairs_ok[2] = {false, false};
+    bool pairs_ok[3] = {false, false, false};
     size_t npairs = 0;
-    size_t grid_M[2] = {0, 0};
+    size_t grid_M[3] = {0, 0, 0};
     int64_t N = 0;
     double L = 0;
     int nc = 1;

@@ -804,7 +804,10 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
         // against the residual itself.  Below that every restart uses the FP64 residual
         // (an FP64 product), so each further cycle is a step of iterative refinement on
         // the FP64 residual, and convergence is decided by it.
-        bool fp64_res = c->precision == 1;
+        bool fp64_res = c->precision >= 1;
+        // the precision of the "FP64" residual products: FP64 or double-float (the same
+        // accuracy; SE_OPT_RESIDUAL) when the Krylov products run in FP32
+        const int res_prec = c->precision == 0 ? c->res_precision : c->precision;
         double rel_wp = 1.0;                  // the previous working-precision restart residual
         for (;;) {
             bool exact = fp64_res;            // r is the FP64 residual (or b itself)
@@ -813,7 +816,7 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
                 x_zero = false;
                 exact = true;
             } else {
-                rc = op(xd, w, fp64_res ? 1 : c->precision);
+                rc = op(xd, w, fp64_res ? res_prec : c->precision);
                 if (rc != SE_OK) return rc;
                 axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0, bd, -1.0, w, r);
                 c->launches++;
@@ -1093,7 +1096,8 @@ int rigid_core(se_ctx *c, const double *ft, const double *einf, double *x11, dou
     const double *e = einf ? einf : z;
     embed_ft_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ft, x11);
     c->launches++;
-    int rc = se_apply_internal(c, 11, x11, w11, SE_F64, 1);     // M [F; T; 0] in FP64
+    // M [F; T; 0] at FP64 accuracy (FP64 or double-float products)
+    int rc = se_apply_internal(c, 11, x11, w11, SE_F64, c->precision == 0 ? c->res_precision : c->precision);
     if (rc != SE_OK) return rc;
     rigid_rhs_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, w11, e[0], e[1], e[2], e[3], e[4], x11);
     c->launches++;

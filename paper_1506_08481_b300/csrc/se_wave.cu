@@ -38,6 +38,7 @@ namespace {
 template <typename T> struct V4;
 template <> struct V4<float> { using t = float4; };
 template <> struct V4<double> { using t = double4_32a; };
+template <> struct V4<ff> { using t = ff4; };
 
 __device__ __forceinline__ int wrapi(int i, int M) { return i >= M ? i - M : (i < 0 ? i + M : i); }
 
@@ -1099,7 +1100,7 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
 #pragma unroll
         for (int cc = 0; cc < NA; ++cc) {
             T v = acc[cc] - cmp[cc];
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            for (int off = 16; off > 0; off >>= 1) v += shfl_xor(0xffffffffu, v, off);
             acc[cc] = v;
         }
     }
@@ -1593,8 +1594,8 @@ void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int nc
                                        c->b.rad, (const T *)c->b.self_c[pix<T>()], c->b.perm,
                                        (const T *)c->b.grid_o[pix<T>()], xs, yreal, y, ncomp, with_wave, with_self);
     };
-    const bool staged = c->gather == 2 || (c->gather == 0 && c->P <= kStagedMaxP);
-    if (with_wave && staged) {
+    const bool staged = !std::is_same<T, ff>::value && (c->gather == 2 || (c->gather == 0 && c->P <= kStagedMaxP));
+    if constexpr (!std::is_same<T, ff>::value) if (with_wave && staged) {
         // staged gather: one CTA per spreading bin (see gather_staged_kernel)
         const int CO = p.hybrid ? 8 : 4;
         StagedLayout<T> lay;
@@ -1650,6 +1651,9 @@ template void launch_gather_combine<float, float>(se_ctx *, const float *, const
 template void launch_gather_combine<float, double>(se_ctx *, const float *, const float *, double *, int, int, cudaStream_t);
 template void launch_gather_combine<double, float>(se_ctx *, const double *, const double *, float *, int, int, cudaStream_t);
 template void launch_gather_combine<double, double>(se_ctx *, const double *, const double *, double *, int, int, cudaStream_t);
+template void launch_wave_spread<ff>(se_ctx *, const ff *, cudaStream_t, int);
+template void launch_gather_combine<ff, float>(se_ctx *, const ff *, const ff *, float *, int, int, cudaStream_t);
+template void launch_gather_combine<ff, double>(se_ctx *, const ff *, const ff *, double *, int, int, cudaStream_t);
 
 }  // namespace se
 

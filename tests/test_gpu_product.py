@@ -316,3 +316,41 @@ def test_overlap_detection():
     ctx.set_option(api.SE_OPT_OVERLAP_CHECK, 0)
     ctx.set_config(cases["overlap"][0], rad, L)
     assert torch.isfinite(ctx.apply(torch.ones(3, 12, device="cuda", dtype=torch.float64))).all()
+
+
+@pytest.mark.parametrize("size_mode", [0, 1])
+@pytest.mark.parametrize("ncomp", [3, 12])
+def test_double_float_mode(small_poly, small_poly_ref, size_mode, ncomp):
+    """SE_OPT_PRECISION 2 (spread and gather in double-float, the rest in FP64) gives the
+    FP64 product to double-float rounding (~2^-44 per operation) and meets the FP64 parity
+    bound against the oracle; FP32 and FP64 inputs and outputs."""
+    cfg, x = small_poly
+    xx = x[:, :ncomp].copy()
+    c64 = make_ctx(1.0, 64, 24, 5.45, cfg, precision=1, size_mode=size_mode)
+    y64 = gpu_apply(c64, xx)
+    cff = make_ctx(1.0, 64, 24, 5.45, cfg, precision=2, size_mode=size_mode)
+    yff = gpu_apply(cff, xx)
+    assert rel(yff, y64) <= 1e-12
+    if ncomp == 12:
+        assert rel(yff, small_poly_ref) <= 1e-9
+    y32io = gpu_apply(cff, xx, dtype=torch.float32)
+    assert rel(y32io, y64) <= 2e-7
+
+
+def test_double_float_mode_large_grid(oracle_mod):
+    """Bidisperse N = 2000 at the parameters the error model picks for 1e-10 (FP64): the
+    double-float product equals the FP64 one to 1e-12 and meets 1e-9 against the oracle."""
+    cfg = inputs.bidisperse(seed=0)
+    x12 = inputs.moments(cfg.N, np.random.default_rng(5), 11)          # [N, 12], S_tr = 0
+    x = x12[:, :11].copy()
+    from paper_1506_08481_b300 import params
+    sp = params.choose(cfg.L, cfg.N, 3e-11, M_max=192, a_eff=params.effective_radius(cfg.rad), precision=1)
+    out = {}
+    for prec in (1, 2):
+        ctx = make_ctx(sp.xi, sp.M, sp.P, sp.rc, cfg, precision=prec)
+        ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
+        out[prec] = gpu_apply(ctx, x)
+    assert rel(out[2], out[1]) <= 1e-12
+    rows = np.random.default_rng(0).choice(cfg.N, 16, replace=False)
+    ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x12, rows=rows, tol=1e-13)[:, :11]
+    assert rel(out[2][rows], ref) <= 1e-9
