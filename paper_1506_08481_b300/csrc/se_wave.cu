@@ -40,6 +40,16 @@ template <> struct V4<float> { using t = float4; };
 template <> struct V4<double> { using t = double4_32a; };
 template <> struct V4<ff> { using t = ff4; };
 
+// CTAs of 256 threads per SM the gather is compiled for (register budget) and the
+// unrolling of its z-loop (loads in flight per lane)
+#ifndef SE_GATHER_MINB
+#define SE_GATHER_MINB 2
+#endif
+#ifndef SE_GATHER_UNROLL
+#define SE_GATHER_UNROLL 12
+#endif
+constexpr int kGatherUnroll = SE_GATHER_UNROLL;
+
 __device__ __forceinline__ int wrapi(int i, int M) { return i >= M ? i - M : (i < 0 ? i + M : i); }
 
 // S tensor (xx, yy, zz, xy, xz, yz) from coordinates on the orthonormal basis
@@ -1030,7 +1040,7 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
             // column moments: Z0..Z3 of v (and of v'' in the hybrid mode), Zp of p
             T z0[3] = {0, 0, 0}, z1[3] = {0, 0, 0}, z2[3] = {0, 0, 0}, z3[3] = {0, 0, 0}, zp = 0;
             if (act) {
-#pragma unroll 12
+#pragma unroll kGatherUnroll
                 for (int k = 0; k < P; ++k) {
                     const T4 w = Wz[k];
                     const T4 u0 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[k] * zs);
@@ -1109,7 +1119,7 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
 }
 
 template <typename T, typename TO, int CO, int NCOMP>
-__global__ void __launch_bounds__(256, 2) gather_kernel(SeParams p, int N, const int *order, const int *base,
+__global__ void __launch_bounds__(256, SE_GATHER_MINB) gather_kernel(SeParams p, int N, const int *order, const int *base,
                                                      const T *s0g, const T *wg, const double *rad, const T *selfc,
                                                      const int *perm, const T *grid, const T *xs, const T *yreal,
                                                      TO *y, int ncomp_out, int with_wave, int with_self)
