@@ -188,8 +188,8 @@ static int ensure_grids_ff(se_ctx *c)
     dfree(c->b.grid_part[2]);
     dfree(c->b.grid_o[2]);
     const size_t M = c->M;
-    SE_ALLOC(c, c->b.grid_f[2], M * M * M * 4 * sizeof(ff));
-    if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[2], (size_t)c->nsplit * M * M * M * 4 * sizeof(ff));
+    SE_ALLOC(c, c->b.grid_f[2], M * M * M * 8 * sizeof(ff));
+    if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[2], (size_t)c->nsplit * M * M * M * 8 * sizeof(ff));
     SE_ALLOC(c, c->b.grid_o[2], M * M * M * 8 * sizeof(ff));
     c->grid_M[2] = c->M;
     return SE_OK;
@@ -208,15 +208,16 @@ static int ensure_grids(se_ctx *c, int prec)
     dfree(c->b.grid_o[prec]);
     dfree(c->b.tw[prec]);
     const size_t M = c->M, Mh = M / 2 + 1;
-    SE_ALLOC(c, c->b.grid_f[prec], M * M * M * 4 * es);
+    // 8 components: the wave-space approach spreads 7 grids (4 otherwise)
+    SE_ALLOC(c, c->b.grid_f[prec], M * M * M * 8 * es);
     // With few spreading tiles (small M) several CTAs share a tile, each summing part
     // of its particles into its own partial grid: about two waves of CTAs on the SMs.
     {
         const size_t ntiles = (M / kTile) * (M / kTile) * (M / kTile);
         c->nsplit = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * kSMs * 11 + ntiles - 1) / ntiles));
-        if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[prec], (size_t)c->nsplit * M * M * M * 4 * es);
+        if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[prec], (size_t)c->nsplit * M * M * M * 8 * es);
     }
-    SE_ALLOC(c, c->b.spec_f[prec], M * M * Mh * 4 * 2 * es);
+    SE_ALLOC(c, c->b.spec_f[prec], M * M * Mh * 8 * 2 * es);
     SE_ALLOC(c, c->b.spec_o[prec], M * M * Mh * 8 * 2 * es);
     SE_ALLOC(c, c->b.grid_o[prec], M * M * M * 8 * es);
     SE_ALLOC(c, c->b.tw[prec], M * 2 * es);
@@ -394,7 +395,8 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         c->precision = (int)value;
         return SE_OK;
     case SE_OPT_SIZE_MODE:
-        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "size mode must be 0 (hybrid) or 1 (real-space)");
+        if (value != 0 && value != 1 && value != 2)
+            return set_error(c, SE_ERR_ARG, "size mode must be 0 (hybrid), 1 (real-space) or 2 (wave-space)");
         c->size_mode = (int)value;
         c->pc_ready = false;
         return SE_OK;
@@ -576,9 +578,9 @@ static int apply_ff(se_ctx *c, int ncomp, const TO *x, TO *y)
     const size_t M3 = (size_t)c->M * c->M * c->M;
     if (with_wave) {
         launch_wave_spread<ff>(c, xs2, s, ncomp);
-        launch_cvt<ff, double>(c, M3 * 4, c->b.grid_f[2], c->b.grid_f[1], s);
+        launch_cvt<ff, double>(c, M3 * (c->size_mode == 2 ? 8 : 4), c->b.grid_f[2], c->b.grid_f[1], s);
         launch_wave_fft<double>(c, s);
-        launch_cvt<double, ff>(c, M3 * (c->size_mode == 0 ? 8 : 4), c->b.grid_o[1], c->b.grid_o[2], s);
+        launch_cvt<double, ff>(c, M3 * (c->size_mode != 1 ? 8 : 4), c->b.grid_o[1], c->b.grid_o[2], s);
     } else {
         for (int st = SE_STAGE_SPREAD; st <= SE_STAGE_FFT_XI; ++st) {
             stage_mark(c, st, s, false);

@@ -23,7 +23,8 @@ SeParams make_params(const se_ctx *c)
     const double m = c->m_user ? c->m_shape : std::sqrt(kPi * c->P);
     p.alpha = 2.0 * m * m / ((double)c->P * c->P);
     p.kappa = c->L > 0 ? c->M / c->L : 0.0;
-    p.hybrid = c->size_mode == 0 ? 1 : 0;
+    p.hybrid = c->size_mode != 1 ? 1 : 0;
+    p.wsrc = c->size_mode == 2 ? 1 : 0;
     return p;
 }
 

@@ -42,7 +42,8 @@ struct SeParams {
     double L, xi, rc, eta;
     double alpha;                // Gaussian exp(-alpha s^2) in grid units, alpha = 2 m^2 / P^2
     double kappa;                // M / L  (d/dx = kappa d/ds)
-    int hybrid;                  // 1: hybrid size terms, 0: real-space approach
+    int hybrid;                  // 1: target Faxen terms in wave space (hybrid and wave-space approaches)
+    int wsrc;                    // 1: source Faxen terms in wave space too (wave-space approach)
 };
 
 // Cell list for the real-space sum (cells of side >= rc).
@@ -104,7 +105,7 @@ struct se_ctx {
     int M = 0, P = 0;
     int precision = 0;                 // 0 FP32, 1 FP64, 2 FP64-equivalent (double-float spread/gather)
     int res_precision = 2;             // true residuals of the solver (SE_OPT_RESIDUAL): 1 FP64, 2 double-float
-    int size_mode = 0;                 // 0 hybrid, 1 real-space approach
+    int size_mode = 0;                 // 0 hybrid, 1 real-space approach, 2 wave-space approach
     int restart = 30;
     int parts = 7;
     int overlap = 2;             // SE_OPT_OVERLAP

@@ -127,7 +127,12 @@ template <typename T> struct Spread8Smem {
 };
 
 // The tile's work for 64 threads (tid 0..63, sync() a barrier of those 64 threads).
-template <typename T, int NCOMP, bool SPLIT, typename Sync>
+// WS: the wave-space approach to the particle sizes (SE_OPT_SIZE_MODE 2): no Faxen
+// Laplacian in the spread; instead 8 grid components per point, H0 (3) = g [F - alpha
+// kappa (s x T) + 2 alpha kappa S.s], Ha (3) = g [(a^2/6) F + (a^2 alpha kappa / 5) S.s]
+// (whose transform enters with -k^2: the source Faxen operators (1 + a^2 Lap/6) and
+// (1 + a^2 Lap/10) in wave space), the source g S_tr and a zero; 13 FMAs per point.
+template <typename T, int NCOMP, bool SPLIT, typename Sync, bool WS = false>
 __device__ __forceinline__ void spread_body(int tile, int part, int tid, Sync sync, Spread8Smem<T> &sm, SeParams p,
                                             const int *tile_start, const int *tile_perm, const int *base,
                                             const T *s0g, const T *wg, const double *rad, const T *xs, T *grid,
@@ -146,7 +151,8 @@ __device__ __forceinline__ void spread_body(int tile, int part, int tid, Sync sy
     const int tx = tid & 7, ty = tid >> 3;
     const int nbin = (P - 1 + TT - 1) / TT + 1, nb3 = nbin * nbin * nbin;
     const T alpha = (T)p.alpha, kap = (T)p.kappa, akap = alpha * kap;
-    constexpr int NA = NCOMP >= 12 ? 4 : 3;
+    constexpr int NA = WS ? 7 : (NCOMP >= 12 ? 4 : 3);
+    constexpr int GC = WS ? 8 : 4;                // grid components per point
     T acc[TT][NA];
 #pragma unroll
     for (int z = 0; z < TT; ++z)
@@ -172,7 +178,7 @@ __device__ __forceinline__ void spread_body(int tile, int part, int tid, Sync sy
     // and writes the partial grid part
     int cbeg = 0, cstep = CH;
     if constexpr (SPLIT) {
-        grid += (size_t)part * M * M * M * 4;
+        grid += (size_t)part * M * M * M * GC;
         cbeg = part * CH;
         cstep = nsplit * CH;
     }
@@ -216,10 +222,16 @@ __device__ __forceinline__ void spread_body(int tile, int part, int tid, Sync sy
             const int zlo = max(0, -od[2]), zhi = min(TT, P - od[2]);
             const int halves = (zlo < TT / 2 && zhi > 0 ? 1 : 0) | (zhi > TT / 2 && zlo < TT ? 2 : 0);
             // offsets of the tile origin, Faxen coefficients, moments
-            sp[k][0] = T4{s0g[3 * i] + (T)od[0], s0g[3 * i + 1] + (T)od[1], 1 - a2k2 * alpha,
-                          (T)(2.0 / 3.0) * a2k2 * alpha * alpha};
-            sp[k][1] = T4{2 * kap * alpha * (1 - a2k2 * alpha), (T)0.8 * kap * a2k2 * alpha * alpha * alpha,
-                          ok ? (T)halves : (T)0, NCOMP >= 12 ? xi[11] : (T)0};
+            if constexpr (WS) {
+                const T a2 = a * a;
+                sp[k][0] = T4{s0g[3 * i] + (T)od[0], s0g[3 * i + 1] + (T)od[1], a2 / 6, (T)0.2 * a2 * alpha * kap};
+                sp[k][1] = T4{2 * kap * alpha, (T)0, ok ? (T)halves : (T)0, NCOMP >= 12 ? xi[11] : (T)0};
+            } else {
+                sp[k][0] = T4{s0g[3 * i] + (T)od[0], s0g[3 * i + 1] + (T)od[1], 1 - a2k2 * alpha,
+                              (T)(2.0 / 3.0) * a2k2 * alpha * alpha};
+                sp[k][1] = T4{2 * kap * alpha * (1 - a2k2 * alpha), (T)0.8 * kap * a2k2 * alpha * alpha * alpha,
+                              ok ? (T)halves : (T)0, NCOMP >= 12 ? xi[11] : (T)0};
+            }
             sp[k][2] = T4{xi[0], xi[1], xi[2], Tq[0]};
             sp[k][3] = T4{Tq[1], Tq[2], S[0], S[1]};
             sp[k][4] = T4{S[2], S[3], S[4], S[5]};
@@ -233,6 +245,65 @@ __device__ __forceinline__ void spread_body(int tile, int part, int tid, Sync sy
             if (gxy == (T)0 || halves == 0) continue;
             const T4 v0 = sp[k][0], v2 = sp[k][2];
             const T sx = v0.x + tx, sy = v0.y + ty;
+            if constexpr (WS) {
+                // h0[q][p], ha[q][p]: coefficients of s_z^p (p = 0, 1) of H0 and Ha (times g_xy)
+                T h0[3][2], ha[3][2];
+                const T F[3] = {v2.x, v2.y, v2.z};
+                const T c6 = v0.z, c5 = v0.w, ak2 = v1.x;     // a^2/6, a^2 alpha kappa/5, 2 alpha kappa
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    h0[q][0] = F[q];
+                    h0[q][1] = 0;
+                    ha[q][0] = c6 * F[q];
+                    ha[q][1] = 0;
+                }
+                if constexpr (NCOMP >= 6) {
+                    const T4 v3 = sp[k][3];
+                    const T T0 = v2.w, T1 = v3.x, T2 = v3.y;
+                    h0[0][0] -= akap * sy * T2;
+                    h0[1][0] += akap * sx * T2;
+                    h0[2][0] -= akap * (sx * T1 - sy * T0);
+                    h0[0][1] += akap * T1;
+                    h0[1][1] -= akap * T0;
+                    if constexpr (NCOMP >= 11) {
+                        const T4 v4 = sp[k][4];
+                        const T S[6] = {v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
+                        const T d0[3] = {S[0] * sx + S[3] * sy, S[3] * sx + S[1] * sy, S[4] * sx + S[5] * sy};
+                        const T d1[3] = {S[4], S[5], S[2]};
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            h0[q][0] += ak2 * d0[q];
+                            h0[q][1] += ak2 * d1[q];
+                            ha[q][0] += c5 * d0[q];
+                            ha[q][1] = c5 * d1[q];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        h0[q][e] *= gxy;
+                        ha[q][e] *= gxy;
+                    }
+                const T cs = NCOMP >= 12 ? gxy * v1.w : (T)0;
+                auto planes = [&](auto z0c) {
+                    constexpr int z0 = decltype(z0c)::value;
+#pragma unroll
+                    for (int z = z0; z < z0 + TT / 2; ++z) {
+                        const T4 W = swz[k][z ^ sw_z];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            acc[z][q] += h0[q][0] * W.x + h0[q][1] * W.y;
+                            acc[z][3 + q] += ha[q][0] * W.x + ha[q][1] * W.y;
+                        }
+                        if constexpr (NCOMP >= 12) acc[z][6] += cs * W.x;
+                    }
+                };
+                if (halves & 1) planes(std::integral_constant<int, 0>{});
+                if (halves & 2) planes(std::integral_constant<int, TT / 2>{});
+                continue;
+            }
             const T sxy2 = sx * sx + sy * sy;
             const T A1 = v0.w, a0 = v0.z + A1 * sxy2;
             // column coefficients c[alpha][p] of s_z^p (times g_xy)
@@ -296,25 +367,36 @@ __device__ __forceinline__ void spread_body(int tile, int part, int tid, Sync sy
     }
 #pragma unroll
     for (int z = 0; z < TT; ++z) {
-        const size_t gi = (((size_t)(t0[2] + z) * M + (t0[1] + ty)) * M + (t0[0] + tx)) * 4;
+        const size_t gi = (((size_t)(t0[2] + z) * M + (t0[1] + ty)) * M + (t0[0] + tx)) * GC;
         T4 v;
         v.x = acc[z][0];
         v.y = acc[z][1];
         v.z = acc[z][2];
-        v.w = NCOMP >= 12 ? acc[z][NA - 1] : (T)0;
-        *reinterpret_cast<T4 *>(grid + gi) = v;
+        if constexpr (WS) {
+            v.w = acc[z][3];
+            *reinterpret_cast<T4 *>(grid + gi) = v;
+            v.x = acc[z][4];
+            v.y = acc[z][5];
+            v.z = NCOMP >= 12 ? acc[z][6] : (T)0;
+            v.w = (T)0;
+            *reinterpret_cast<T4 *>(grid + gi + 4) = v;
+        } else {
+            v.w = NCOMP >= 12 ? acc[z][NA - 1] : (T)0;
+            *reinterpret_cast<T4 *>(grid + gi) = v;
+        }
     }
 }
 
-template <typename T, int NCOMP, bool SPLIT>
+template <typename T, int NCOMP, bool SPLIT, bool WS = false>
 __global__ void __launch_bounds__(64, sizeof(T) == 4 ? 11 : 6) spread_kernel(SeParams p, const int *tile_start,
                                                     const int *tile_perm, const int *base,
                                                     const T *s0g, const T *wg, const double *rad,
                                                     const T *xs, T *grid, int nsplit)
 {
     __shared__ Spread8Smem<T> sm;
-    spread_body<T, NCOMP, SPLIT>(blockIdx.x, blockIdx.y, threadIdx.x, [] { __syncthreads(); }, sm, p, tile_start,
-                                 tile_perm, base, s0g, wg, rad, xs, grid, nsplit);
+    auto sync = [] { __syncthreads(); };
+    spread_body<T, NCOMP, SPLIT, decltype(sync), WS>(blockIdx.x, blockIdx.y, threadIdx.x, sync, sm, p, tile_start,
+                                                     tile_perm, base, s0g, wg, rad, xs, grid, nsplit);
 }
 
 // ---- FP32 spreading over 8 x 8 x 16 tiles with packed FMAs
@@ -619,51 +701,46 @@ __device__ __forceinline__ void fft_smem(unsigned char *sm, int M, int NLB, T2 *
 // persistent batched kernel runs the same code; each __global__ wrapper passes its
 // blockIdx and dynamic shared memory.
 
-// x pass, forward: each grid row (y, z) carries 4 real series packed as two complex
-// lines (H0 + i H1, H2 + i H3); after the transform the four half spectra
-// q = 0..M/2 are separated using Z(-q) = conj(Z(q)) of real data.
-template <typename T>
+// x pass, forward: each grid row (y, z) carries CF real series (4, or 8 in the
+// wave-space approach) packed as CF/2 complex lines (H0 + i H1, H2 + i H3, ...); after
+// the transform the half spectra q = 0..M/2 are separated using Z(-q) = conj(Z(q)) of
+// real data.
+template <typename T, int CF = 4>
 __device__ __forceinline__ void fft_x_fwd_body(int bx, unsigned char *sm, const FftPlan &plan,
                                                const typename C2<T>::t *twg, const T *grid, typename C2<T>::t *spec)
 {
     using T2 = typename C2<T>::t;
-    constexpr int NL = fft_nl<T>(), NR = NL / 2;          // complex lines, grid rows
+    constexpr int NL = fft_nl<T>(), NCL = CF / 2, NR = NL / NCL;   // complex lines, per row, grid rows
+    constexpr int CPE = sizeof(T) == 4 ? 2 : 1, NCH = NCL / CPE;     // complex per 16-byte copy, copies per point
     const int M = plan.M, Mh = M / 2 + 1;
     T2 *tw, *A, *B;
     fft_smem(sm, M, NL, tw, A, B);
     for (int e = threadIdx.x; e < M; e += blockDim.x) tw[e] = twg[e];
     const size_t row0 = (size_t)bx * NR;
-    if constexpr (sizeof(T) == 4) {
-        // one float4 (H0..H3) of row r at x -> lines 2r, 2r + 1 at element x
-        for (int e = threadIdx.x; e < NR * M; e += blockDim.x) {
-            const int r = e % NR, x = e / NR;
-            cp_async16(A + x * NL + 2 * r, grid + ((row0 + r) * M + x) * 4);
-        }
-    } else {
-        for (int e = threadIdx.x; e < 2 * NR * M; e += blockDim.x) {
-            const int h = e & 1, r = (e >> 1) % NR, x = (e >> 1) / NR;
-            cp_async16(A + x * NL + 2 * r + h, grid + ((row0 + r) * M + x) * 4 + 2 * h);
-        }
+    // copy h of row r at x (CPE complex lines) -> lines NCL r + CPE h .. at element x
+    for (int e = threadIdx.x; e < NCH * NR * M; e += blockDim.x) {
+        const int h = e % NCH, r = (e / NCH) % NR, x = e / NCH / NR;
+        cp_async16(A + x * NL + NCL * r + CPE * h, grid + ((row0 + r) * M + x) * CF + 2 * CPE * h);
     }
     cp_async_wait_all();
     __syncthreads();
     const T2 *Z = fft_run_dir<NL, false>(A, B, plan, tw);
-    for (int e = threadIdx.x; e < NR * Mh * 2; e += blockDim.x) {
-        const int h = e & 1, r = (e >> 1) % NR, q = (e >> 1) / NR;
-        const T2 z = Z[q * NL + 2 * r + h];
-        const T2 zm = Z[(q == 0 ? 0 : M - q) * NL + 2 * r + h];
-        T2 *o = spec + ((row0 + r) * Mh + q) * 4 + 2 * h;
+    for (int e = threadIdx.x; e < NR * Mh * NCL; e += blockDim.x) {
+        const int h = e % NCL, r = (e / NCL) % NR, q = (e / NCL) / NR;
+        const T2 z = Z[q * NL + NCL * r + h];
+        const T2 zm = Z[(q == 0 ? 0 : M - q) * NL + NCL * r + h];
+        T2 *o = spec + ((row0 + r) * Mh + q) * CF + 2 * h;
         o[0] = T2{(T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y)};
         o[1] = T2{(T)0.5 * (z.y + zm.y), (T)-0.5 * (z.x - zm.x)};
     }
 }
 
-template <typename T>
+template <typename T, int CF = 4>
 __global__ void __launch_bounds__(kFftThreads, 4) fft_x_fwd(FftPlan plan, const typename C2<T>::t *twg,
                                                             const T *grid, typename C2<T>::t *spec)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fft_x_fwd_body<T>(blockIdx.x, smraw, plan, twg, grid, spec);
+    fft_x_fwd_body<T, CF>(blockIdx.x, smraw, plan, twg, grid, spec);
 }
 
 // y pass (forward or inverse) in place on half spectra [z][y][q][C]: a CTA takes the
@@ -709,13 +786,16 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_y(FftPlan plan, const type
 // q0.. of one y row (LB = 4 for FP32 and 2 for FP64 while the buffers fit in shared
 // memory); input lines q * 4 + c, output lines q * CO + c (the component order of the
 // arrays in HBM).
-template <typename T, int CO, int LB>
+// CI = 8 (the wave-space approach): the input spectra are H0 (3), Ha (3), H_src, 0 and
+// the force density is H = H0 - k^2 Ha (the source Faxen operators in wave space).
+template <typename T, int CO, int LB, int CI = 4>
 __device__ __forceinline__ void fft_z_scale_body(int bx, int by, unsigned char *sm, const FftPlan &plan,
                                                  const typename C2<T>::t *twg, const typename C2<T>::t *specf,
                                                  typename C2<T>::t *speco, T cnorm, T twopiL, T i4x2, T ecoef)
 {
     using T2 = typename C2<T>::t;
-    constexpr int NLI = 4 * LB, NLO = LB * CO, CPE = sizeof(T) == 4 ? 2 : 1;
+    constexpr int NLI = CI * LB, NLO = LB * CO, CPE = sizeof(T) == 4 ? 2 : 1;
+    static_assert(NLI <= NLO, "the output line buffers hold the input lines");
     const int M = plan.M, Mh = M / 2 + 1;
     T2 *tw, *A, *B;
     fft_smem(sm, M, NLO, tw, A, B);
@@ -726,7 +806,7 @@ __device__ __forceinline__ void fft_z_scale_body(int bx, int by, unsigned char *
     for (int e = threadIdx.x; e < (NLI / CPE) * M; e += blockDim.x) {
         const int k = e % (NLI / CPE), z = e / (NLI / CPE);
         T2 *d = A + z * NLI + k * CPE;
-        if (k * CPE < nq * 4) cp_async16(d, specf + ((size_t)z * zs + (size_t)y * Mh + q0) * 4 + k * CPE);
+        if (k * CPE < nq * CI) cp_async16(d, specf + ((size_t)z * zs + (size_t)y * Mh + q0) * CI + k * CPE);
         else
             for (int u = 0; u < CPE; ++u) d[u] = T2{0, 0};
     }
@@ -754,8 +834,14 @@ __device__ __forceinline__ void fft_z_scale_body(int bx, int by, unsigned char *
             else E = exp(ex) * cnorm;
             const T ik2 = 1 / k2;
             const T Phi = E * (1 + k2 * i4x2) * ik2;
-            const T2 *h = X + z * NLI + q * 4;
-            const T2 H0 = h[0], H1 = h[1], H2 = h[2], Hs = h[3];
+            const T2 *h = X + z * NLI + q * CI;
+            T2 H0 = h[0], H1 = h[1], H2 = h[2], Hs = h[3];
+            if constexpr (CI == 8) {
+                H0 = T2{h[0].x - k2 * h[3].x, h[0].y - k2 * h[3].y};
+                H1 = T2{h[1].x - k2 * h[4].x, h[1].y - k2 * h[4].y};
+                H2 = T2{h[2].x - k2 * h[5].x, h[2].y - k2 * h[5].y};
+                Hs = h[6];
+            }
             const T2 kH = T2{kx * H0.x + ky * H1.x + kz * H2.x, kx * H0.y + ky * H1.y + kz * H2.y};
             const T2 pr = T2{kH.x * ik2, kH.y * ik2};
             // This FFT's forward transform carries exp(-i q.n), so Hhat(q) holds the moments'
@@ -788,14 +874,15 @@ __device__ __forceinline__ void fft_z_scale_body(int bx, int by, unsigned char *
     }
 }
 
-template <typename T, int CO, int LB>
+template <typename T, int CO, int LB, int CI = 4>
 __global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, const typename C2<T>::t *twg,
                                                               const typename C2<T>::t *specf,
                                                               typename C2<T>::t *speco, T cnorm, T twopiL, T i4x2,
                                                               T ecoef)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    fft_z_scale_body<T, CO, LB>(blockIdx.x, blockIdx.y, smraw, plan, twg, specf, speco, cnorm, twopiL, i4x2, ecoef);
+    fft_z_scale_body<T, CO, LB, CI>(blockIdx.x, blockIdx.y, smraw, plan, twg, specf, speco, cnorm, twopiL, i4x2,
+                                    ecoef);
 }
 
 // z pass with a tabulated radial kernel in place of the Ewald one (the coarse spectral
@@ -1455,7 +1542,7 @@ template <typename T>
 static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_t s, int ncomp)
 {
     if constexpr (std::is_same<T, float>::value) {
-        if (use_spread16(c, p, true)) {
+        if (!p.wsrc && use_spread16(c, p, true)) {
             launch_spread16(c, p, xs, s, ncomp);
             return;
         }
@@ -1467,26 +1554,32 @@ static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_
                                               (const T *)c->b.sup_s0[pix<T>()], (const T *)c->b.sup_w[pix<T>()],
                                               c->b.rad, xs, out, ns);
     };
+    auto pick = [&](auto split, auto ws) {
+        constexpr bool SP = decltype(split)::value, WS = decltype(ws)::value;
+        if (ncomp <= 3) args(spread_kernel<T, 3, SP, WS>);
+        else if (ncomp <= 6) args(spread_kernel<T, 6, SP, WS>);
+        else if (ncomp <= 11) args(spread_kernel<T, 11, SP, WS>);
+        else args(spread_kernel<T, 12, SP, WS>);
+    };
+    using yes = std::true_type;
+    using no = std::false_type;
     if (ns > 1) {
-        if (ncomp <= 3) args(spread_kernel<T, 3, true>);
-        else if (ncomp <= 6) args(spread_kernel<T, 6, true>);
-        else if (ncomp <= 11) args(spread_kernel<T, 11, true>);
-        else args(spread_kernel<T, 12, true>);
+        if (p.wsrc) pick(yes{}, yes{});
+        else pick(yes{}, no{});
     } else {
-        if (ncomp <= 3) args(spread_kernel<T, 3, false>);
-        else if (ncomp <= 6) args(spread_kernel<T, 6, false>);
-        else if (ncomp <= 11) args(spread_kernel<T, 11, false>);
-        else args(spread_kernel<T, 12, false>);
+        if (p.wsrc) pick(no{}, yes{});
+        else pick(no{}, no{});
     }
     c->launches++;
     if (ns > 1) {
-        const size_t n4 = (size_t)p.M * p.M * p.M;
+        // sum over the parts in units of 4 components
+        const size_t n4 = (size_t)p.M * p.M * p.M * (p.wsrc ? 2 : 1);
         sum_parts_kernel<T><<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(n4, ns, out, (T *)c->b.grid_f[pix<T>()]);
         c->launches++;
     }
 }
 
-template <typename T, int CO, int LB>
+template <typename T, int CO, int LB, int CI = 4>
 static void launch_z(se_ctx *c, const SeParams &p, const typename C2<T>::t *tw, const typename C2<T>::t *sf,
                      typename C2<T>::t *so, T cnorm, cudaStream_t s)
 {
@@ -1496,20 +1589,20 @@ static void launch_z(se_ctx *c, const SeParams &p, const typename C2<T>::t *tw, 
     // k = 2 pi q / L; net exponent -k^2/(4 xi^2) + 2 pi^2 q^2/(alpha M^2) (see the file header)
     const T twopiL = (T)(2.0 * kPi / p.L), i4x2 = (T)(0.25 / (p.xi * p.xi));
     const T ecoef = (T)(2.0 * kPi * kPi / (p.alpha * (double)M * M));
-    cudaFuncSetAttribute(fft_z_scale<T, CO, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fft_z_scale<T, CO, LB><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, smem, s>>>(c->plan, tw, sf, so, cnorm, twopiL,
-                                                                                 i4x2, ecoef);
+    cudaFuncSetAttribute(fft_z_scale<T, CO, LB, CI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fft_z_scale<T, CO, LB, CI><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, smem, s>>>(c->plan, tw, sf, so, cnorm,
+                                                                                     twopiL, i4x2, ecoef);
 }
 
-template <typename T, int CO>
+template <typename T, int CO, int CI = 4>
 static void launch_z_fit(se_ctx *c, const SeParams &p, const typename C2<T>::t *tw, const typename C2<T>::t *sf,
                          typename C2<T>::t *so, T cnorm, cudaStream_t s)
 {
     using T2 = typename C2<T>::t;
     constexpr int LB0 = fft_nl<T>() / 4;
-    if (fft_smem_bytes<T2>(c->M, CO * LB0) <= kSmemMax) launch_z<T, CO, LB0>(c, p, tw, sf, so, cnorm, s);
-    else if (fft_smem_bytes<T2>(c->M, CO * 2) <= kSmemMax) launch_z<T, CO, 2>(c, p, tw, sf, so, cnorm, s);
-    else launch_z<T, CO, 1>(c, p, tw, sf, so, cnorm, s);
+    if (fft_smem_bytes<T2>(c->M, CO * LB0) <= kSmemMax) launch_z<T, CO, LB0, CI>(c, p, tw, sf, so, cnorm, s);
+    else if (fft_smem_bytes<T2>(c->M, CO * 2) <= kSmemMax) launch_z<T, CO, 2, CI>(c, p, tw, sf, so, cnorm, s);
+    else launch_z<T, CO, 1, CI>(c, p, tw, sf, so, cnorm, s);
 }
 
 template <typename T, int C, bool INV>
@@ -1545,13 +1638,20 @@ void launch_wave_fft(se_ctx *c, cudaStream_t s)
     const size_t smem = fft_smem_bytes<T2>(M, NL);
 
     stage_mark(c, SE_STAGE_FFT_XF, s, false);
-    cudaFuncSetAttribute(fft_x_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fft_x_fwd<T><<<M * M / (NL / 2), kFftThreads, smem, s>>>(c->plan, tw, (const T *)c->b.grid_f[pix<T>()], sf);
+    if (p.wsrc) {
+        cudaFuncSetAttribute(fft_x_fwd<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fft_x_fwd<T, 8><<<M * M / (NL / 4), kFftThreads, smem, s>>>(c->plan, tw, (const T *)c->b.grid_f[pix<T>()],
+                                                                     sf);
+    } else {
+        cudaFuncSetAttribute(fft_x_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fft_x_fwd<T><<<M * M / (NL / 2), kFftThreads, smem, s>>>(c->plan, tw, (const T *)c->b.grid_f[pix<T>()], sf);
+    }
     c->launches++;
     stage_mark(c, SE_STAGE_FFT_XF, s, true);
 
     stage_mark(c, SE_STAGE_FFT_YF, s, false);
-    launch_y<T, 4, false>(c, tw, sf, s);
+    if (p.wsrc) launch_y<T, 8, false>(c, tw, sf, s);
+    else launch_y<T, 4, false>(c, tw, sf, s);
     c->launches++;
     stage_mark(c, SE_STAGE_FFT_YF, s, true);
 
@@ -1566,7 +1666,8 @@ void launch_wave_fft(se_ctx *c, cudaStream_t s)
         cudaFuncSetAttribute(fft_z_table<T, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm);
         fft_z_table<T, LB><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, zsm, s>>>(
             c->plan, tw, sf, so, (const T *)c->ktab[pix<T>()], c->ktab_n, (T)c->ktab_kmax, cn, twopiL, ecoef);
-    } else if (CO == 8) launch_z_fit<T, 8>(c, p, tw, sf, so, cnorm, s);
+    } else if (p.wsrc) launch_z_fit<T, 8, 8>(c, p, tw, sf, so, cnorm, s);
+    else if (CO == 8) launch_z_fit<T, 8>(c, p, tw, sf, so, cnorm, s);
     else launch_z_fit<T, 4>(c, p, tw, sf, so, cnorm, s);
     c->launches++;
     stage_mark(c, SE_STAGE_FFT_Z, s, true);
@@ -1913,9 +2014,9 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
         se_ctx *c = box[b];
         const int with_real = (c->parts & 1) ? 1 : 0, with_wave = (c->parts & 2) ? 1 : 0;
         if (c->precision != 0 || !c->support_ok[0] || !c->b.grid_f[0] || (with_real && !c->pairs_ok[0]) ||
-            c->ktab_on) {
-            err = "box " + std::to_string(b) + ": the persistent batch needs FP32 products with the stored pair "
-                  "table (run the batch once without it first)";
+            c->ktab_on || c->size_mode == 2) {
+            err = "box " + std::to_string(b) + ": the persistent batch needs FP32 products, the stored pair "
+                  "table (run the batch once without it first) and the real-space or hybrid size approach";
             return SE_ERR_STATE;
         }
         const SeParams p = make_params(c);

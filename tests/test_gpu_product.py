@@ -75,7 +75,7 @@ def test_mono_n100_forces_fp64_parity(oracle_mod):
     assert rel(gpu_apply(ctx, x[:, :3]), ref) <= 1e-9
 
 
-@pytest.mark.parametrize("size_mode", [0, 1])
+@pytest.mark.parametrize("size_mode", [0, 1, 2])
 def test_all_components_fp64(small_poly, small_poly_ref, size_mode):
     cfg, x = small_poly
     ctx = make_ctx(1.0, 64, 24, 5.45, cfg, precision=1, size_mode=size_mode)
@@ -84,7 +84,7 @@ def test_all_components_fp64(small_poly, small_poly_ref, size_mode):
         assert rel(y[:, sl], small_poly_ref[:, sl]) <= 1e-9, sl
 
 
-@pytest.mark.parametrize("size_mode", [0, 1])
+@pytest.mark.parametrize("size_mode", [0, 1, 2])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_all_components_fp32(small_poly, small_poly_ref, size_mode, dtype):
     cfg, x = small_poly
@@ -318,7 +318,7 @@ def test_overlap_detection():
     assert torch.isfinite(ctx.apply(torch.ones(3, 12, device="cuda", dtype=torch.float64))).all()
 
 
-@pytest.mark.parametrize("size_mode", [0, 1])
+@pytest.mark.parametrize("size_mode", [0, 1, 2])
 @pytest.mark.parametrize("ncomp", [3, 12])
 def test_double_float_mode(small_poly, small_poly_ref, size_mode, ncomp):
     """SE_OPT_PRECISION 2 (spread and gather in double-float, the rest in FP64) gives the
@@ -354,3 +354,21 @@ def test_double_float_mode_large_grid(oracle_mod):
     rows = np.random.default_rng(0).choice(cfg.N, 16, replace=False)
     ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x12, rows=rows, tol=1e-13)[:, :11]
     assert rel(out[2][rows], ref) <= 1e-9
+
+
+
+@pytest.mark.parametrize("ncomp", [3, 6, 11, 12])
+def test_wave_space_approach_ncomp_and_split(small_poly, small_poly_ref, ncomp):
+    """SE_OPT_SIZE_MODE 2 (source and target Faxen operators in wave space) for every
+    ncomp prefix, on a grid whose spreading tiles are split over several CTAs (M = 48)
+    and one that is not (M = 144): equal to the hybrid approach to their method errors,
+    and to the FP64 oracle to 1e-9."""
+    cfg, x = small_poly
+    for M, P in ((144, 24), (48, 20)):          # tiles not split / split over CTAs
+        ctx = make_ctx(1.0, M, P, 5.45, cfg, precision=1, size_mode=2)
+        y = gpu_apply(ctx, x[:, :ncomp].copy())
+        ctx2 = make_ctx(1.0, M, P, 5.45, cfg, precision=1, size_mode=0)
+        y0 = gpu_apply(ctx2, x[:, :ncomp].copy())
+        assert rel(y, y0) <= 1e-7, (M, P)
+        if ncomp == 12 and M == 144:
+            assert rel(y, small_poly_ref) <= 1e-9

@@ -2,12 +2,13 @@
 Sec. 6.1.1, Eq. err-E): e_inf,r(E) = max_i |E_i^SE - E_i^*| / |E_i^*| of the wave-space
 part alone (FP64) against the oracle's direct-Ewald wave-space part at the same xi, as a
 function of the support P at the best shape parameter m, M = 64, xi a_1 = 0.1, for the
-real-space and the hybrid approach, on a bidisperse suspension (radii 1 and 2).
+real-space, the hybrid and the wave-space approach, on a bidisperse suspension (radii
+1 and 2).
 
 The paper finds the minimum error decaying like exp(-P pi/2) with the optimal m near
-sqrt(pi P), and e ~ 1e-4 reached at P = 15 (real-space approach) and 13 (hybrid).  The
-test checks the exponential decay, the location of the optimal m, and that the hybrid
-approach needs no larger P than the real-space one for a given error; it prints the
+sqrt(pi P), and e ~ 1e-4 reached at P = 15 (real-space approach), 13 (hybrid) and 9
+(wave-space).  The test checks the exponential decay, the location of the optimal m,
+and the order of the three approaches in the P a given error needs; it prints the
 table it measured."""
 import math
 
@@ -35,7 +36,7 @@ def test_wave_space_error_against_support(oracle_mod):
     ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x, xi=xi, tol=1e-15, parts=2)
     Ps = [5, 7, 9, 11, 13, 15, 17, 19]
     best = {}
-    for mode, name in ((1, "real-space"), (0, "hybrid")):
+    for mode, name in ((1, "real-space"), (0, "hybrid"), (2, "wave-space")):
         for P in Ps:
             errs = []
             for m in np.linspace(0.6, 1.6, 11) * math.sqrt(math.pi * P):
@@ -50,13 +51,12 @@ def test_wave_space_error_against_support(oracle_mod):
                 errs.append((e_inf_r(y, ref), float(m)))
                 ctx.close()
             best[(name, P)] = min(errs)
-    print("\n  P   real-space e (m)       hybrid e (m)      [m/sqrt(pi P) at the minimum]")
+    print("\n  P   real-space e (m)       hybrid e (m)       wave-space e (m)")
     for P in Ps:
-        (er, mr), (eh, mh) = best[("real-space", P)], best[("hybrid", P)]
-        print(f"{P:3d}   {er:9.2e} ({mr:5.2f})   {eh:9.2e} ({mh:5.2f})   "
-              f"[{mr / math.sqrt(math.pi * P):.2f}, {mh / math.sqrt(math.pi * P):.2f}]")
+        (er, mr), (eh, mh), (ew, mw) = best[("real-space", P)], best[("hybrid", P)], best[("wave-space", P)]
+        print(f"{P:3d}   {er:9.2e} ({mr:5.2f})   {eh:9.2e} ({mh:5.2f})   {ew:9.2e} ({mw:5.2f})")
     need = {}
-    for name in ("real-space", "hybrid"):
+    for name in ("real-space", "hybrid", "wave-space"):
         e = [best[(name, P)][0] for P in Ps]
         # exponential decay of the minimum error: a decade every few points of P
         assert e[-1] < 1e-3 * e[0], (name, e)
@@ -65,5 +65,5 @@ def test_wave_space_error_against_support(oracle_mod):
             assert 0.6 < best[(name, P)][1] / math.sqrt(math.pi * P) < 1.6
         need[name] = min((P for P in Ps if best[(name, P)][0] <= 1e-4), default=None)
     print("P needed for e <= 1e-4:", need)
-    assert need["hybrid"] is not None and need["real-space"] is not None
-    assert need["hybrid"] <= need["real-space"]
+    assert all(v is not None for v in need.values())
+    assert need["wave-space"] <= need["hybrid"] <= need["real-space"]
