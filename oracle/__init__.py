@@ -11,7 +11,8 @@ ctypes and picks the Ewald parameter xi and the cutoffs for a requested accuracy
 the result does not depend on xi.
 
 Parity status of each function (pins live in ``tests/test_oracle_pins.py``):
-  mobility()      pinned: xi-independence, isolated-sphere limit, Hasimoto
+  mobility()      pinned: xi-independence (also on sheared lattices), identity of
+                  the lattices at strain gamma and gamma - 1, isolated-sphere limit, Hasimoto
                   simple-cubic drag (Sec. 6.1, Eq. dst-corr), Eq. uf-self,
                   symmetry and positive definiteness of the F,T,S block,
                   free-space limits, compressible-term special cases.
@@ -55,6 +56,8 @@ def _load():
         p = ctypes.c_void_p
         lib.se_oracle_mobility.argtypes = [l, d, p, p, p, p, l, p, d, d, d, i, d]
         lib.se_oracle_mobility.restype = i
+        lib.se_oracle_mobility_sheared.argtypes = [l, d, d, p, p, p, p, l, p, d, d, d, i, d]
+        lib.se_oracle_mobility_sheared.restype = i
         lib.se_oracle_pair_block.argtypes = [p, d, d, d, i, d, p]
         lib.se_oracle_pair_block.restype = i
         lib.se_oracle_stresslet_basis.argtypes = [p]
@@ -104,10 +107,11 @@ def choose_xi(N: int, L: float, nrows: int, tol: float) -> float:
 
 
 def mobility(pos, rad, L, x, rows=None, xi=None, tol=1e-13, parts=PARTS_ALL,
-             eta=1.0, rc=None, kc=None):
+             eta=1.0, rc=None, kc=None, gamma=0.0):
     """y = M_inf . x for the listed target rows (all particles if rows is None).
 
     pos [N,3], rad [N], x [N,12] = [F, T, S(5 on the orthonormal basis), S_tr].
+    gamma: strain of the sheared lattice a2 = (gamma L, L, 0) (0: the cubic box).
     Returns y [nrows, 12] = [U, Omega, E(5), E_tr].
     """
     lib = _load()
@@ -128,9 +132,9 @@ def mobility(pos, rad, L, x, rows=None, xi=None, tol=1e-13, parts=PARTS_ALL,
     rc = rc0 if rc is None else rc
     kc = kc0 if kc is None else kc
     y = np.zeros((nrows, NCOMP))
-    rc_ = lib.se_oracle_mobility(N, float(L), _ptr(pos), _ptr(rad), _ptr(x), _ptr(rows),
-                                 nrows, _ptr(y), float(xi), float(rc), float(kc), int(parts),
-                                 float(eta))
+    rc_ = lib.se_oracle_mobility_sheared(N, float(L), float(gamma), _ptr(pos), _ptr(rad), _ptr(x), _ptr(rows),
+                                         nrows, _ptr(y), float(xi), float(rc), float(kc), int(parts),
+                                         float(eta))
     if rc_ != 0:
         raise RuntimeError(f"se_oracle_mobility failed with code {rc_}")
     return y

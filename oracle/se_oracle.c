@@ -470,9 +470,16 @@ static void wave_target_add(const double *k, double k2, double ai, cplx phase,
 
 /* ---------------- public entry points ---------------- */
 
-static void minimum_shift(double *d, double L)
+/* Minimum image for the lattice a1 = (L, 0, 0), a2 = (gamma L, L, 0), a3 = (0, 0, L)
+ * (a cubic box sheared by the strain gamma in x along y, Sec. 3.2; gamma = 0: the cube):
+ * first the multiple of a2 that brings d_y into [-L/2, L/2), then a1 and a3. */
+static void minimum_shift(double *d, double L, double gamma)
 {
-    for (int a = 0; a < 3; a++) d[a] -= L * floor(d[a] / L + 0.5);
+    const double ny = floor(d[1] / L + 0.5);
+    d[1] -= ny * L;
+    d[0] -= ny * gamma * L;
+    d[0] -= L * floor(d[0] / L + 0.5);
+    d[2] -= L * floor(d[2] / L + 0.5);
 }
 
 /*
@@ -490,18 +497,34 @@ static void minimum_shift(double *d, double L)
  *   eta           : viscosity
  * Returns 0 on success, negative on bad arguments.
  */
+int se_oracle_mobility_sheared(long N, double L, double gamma, const double *pos, const double *rad,
+                               const double *x, const long *rows, long nrows, double *y, double xi, double rc,
+                               double kc, int parts, double eta);
+
 int se_oracle_mobility(long N, double L, const double *pos, const double *rad, const double *x,
                        const long *rows, long nrows, double *y, double xi, double rc, double kc,
                        int parts, double eta)
 {
-    if (N <= 0 || L <= 0 || xi <= 0 || !pos || !rad || !x || !y) return -1;
+    return se_oracle_mobility_sheared(N, L, 0.0, pos, rad, x, rows, nrows, y, xi, rc, kc, parts, eta);
+}
+
+/*
+ * The same on the sheared lattice a1 = (L, 0, 0), a2 = (gamma L, L, 0), a3 = (0, 0, L):
+ * real-space images d + p1 a1 + p2 a2 + p3 a3, wave vectors k = (2 pi / L)(q1, q2 - gamma q1, q3)
+ * (the reciprocal lattice), cell volume L^3.
+ */
+int se_oracle_mobility_sheared(long N, double L, double gamma, const double *pos, const double *rad,
+                               const double *x, const long *rows, long nrows, double *y, double xi, double rc,
+                               double kc, int parts, double eta)
+{
+    if (N <= 0 || L <= 0 || xi <= 0 || !pos || !rad || !x || !y || !(fabs(gamma) <= 1.0)) return -1;
     if (!rows) nrows = N;
     memset(y, 0, sizeof(double) * nrows * NC);
     const double V = L * L * L;
 
     /* real space: all images with |x| < rc, excluding (i = j, p = 0) */
     if (parts & 1) {
-        int pmax = (int)ceil(rc / L) + 1;
+        int pmax = (int)ceil(rc / L) + 2;
 #pragma omp parallel for schedule(dynamic, 1)
         for (long ii = 0; ii < nrows; ii++) {
             long i = rows ? rows[ii] : ii;
@@ -510,11 +533,11 @@ int se_oracle_mobility(long N, double L, const double *pos, const double *rad, c
             gens_t g;
             for (long j = 0; j < N; j++) {
                 double d0[3] = { pos[3 * i] - pos[3 * j], pos[3 * i + 1] - pos[3 * j + 1], pos[3 * i + 2] - pos[3 * j + 2] };
-                minimum_shift(d0, L);
+                minimum_shift(d0, L, gamma);
                 for (int px = -pmax; px <= pmax; px++)
                     for (int py = -pmax; py <= pmax; py++)
                         for (int pz = -pmax; pz <= pmax; pz++) {
-                            double d[3] = { d0[0] + px * L, d0[1] + py * L, d0[2] + pz * L };
+                            double d[3] = { d0[0] + px * L + py * gamma * L, d0[1] + py * L, d0[2] + pz * L };
                             double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                             if (r2 >= rc * rc) continue;
                             if (i == j && px == 0 && py == 0 && pz == 0) continue;
@@ -528,10 +551,12 @@ int se_oracle_mobility(long N, double L, const double *pos, const double *rad, c
         }
     }
 
-    /* wave space: half space of integer vectors q != 0 with |k| < kc, k = 2 pi q / L */
+    /* wave space: half space of integer vectors q != 0 with |k| < kc,
+     * k = (2 pi / L)(q1, q2 - gamma q1, q3) */
     if (parts & 2) {
         int qmax = (int)floor(kc * L / (2 * PI));
-        int ncol = (2 * qmax + 1) * (2 * qmax + 1);
+        int qmy = qmax + (int)ceil(fabs(gamma) * qmax);
+        int ncol = (2 * qmax + 1) * (2 * qmy + 1);
         int nthreads = 1;
 #ifdef _OPENMP
         nthreads = omp_get_max_threads();
@@ -548,8 +573,9 @@ int se_oracle_mobility(long N, double L, const double *pos, const double *rad, c
             cplx *sf = (cplx *)malloc(sizeof(cplx) * (size_t)(qmax + 1) * NSF);
 #pragma omp for schedule(dynamic, 1)
             for (int col = 0; col < ncol; col++) {
-                int qx = col % (2 * qmax + 1) - qmax, qy = col / (2 * qmax + 1) - qmax;
-                double kxy2 = (2 * PI / L) * (2 * PI / L) * (double)(qx * qx + qy * qy);
+                int qx = col % (2 * qmax + 1) - qmax, qy = col / (2 * qmax + 1) - qmy;
+                const double ky_q = qy - gamma * qx;       /* k_y L / (2 pi) */
+                double kxy2 = (2 * PI / L) * (2 * PI / L) * ((double)(qx * qx) + ky_q * ky_q);
                 if (kxy2 >= kc * kc) continue;
                 int qz0 = (qy > 0 || (qy == 0 && qx > 0)) ? 0 : 1;
                 int qz1 = (int)floor(sqrt(fmax(0.0, kc * kc - kxy2)) * L / (2 * PI));
@@ -559,7 +585,7 @@ int se_oracle_mobility(long N, double L, const double *pos, const double *rad, c
                 memset(sf, 0, sizeof(cplx) * (size_t)nq * NSF);
                 /* structure factors of raw moments, exp(i k.r_j) by recurrence along qz */
                 for (long j = 0; j < N; j++) {
-                    double th = 2 * PI / L * (qx * pos[3 * j] + qy * pos[3 * j + 1] + qz0 * pos[3 * j + 2]);
+                    double th = 2 * PI / L * (qx * pos[3 * j] + ky_q * pos[3 * j + 1] + qz0 * pos[3 * j + 2]);
                     cplx ph = { cos(th), sin(th) };
                     double tz = 2 * PI / L * pos[3 * j + 2];
                     cplx st = { cos(tz), sin(tz) };
@@ -581,19 +607,19 @@ int se_oracle_mobility(long N, double L, const double *pos, const double *rad, c
                     int nb = nq - iq0 < 64 ? nq - iq0 : 64;
                     for (int b = 0; b < nb; b++) {
                         int qz = qz0 + iq0 + b;
-                        double k[3] = { 2 * PI * qx / L, 2 * PI * qy / L, 2 * PI * qz / L };
+                        double k[3] = { 2 * PI * qx / L, 2 * PI * ky_q / L, 2 * PI * qz / L };
                         double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
                         wave_source_symbols(k, k2, xi, V, eta, sf + (size_t)(iq0 + b) * NSF, vh[b], &phh[b]);
                     }
                     for (long ii = 0; ii < nrows; ii++) {
                         long i = rows ? rows[ii] : ii;
                         int qz = qz0 + iq0;
-                        double th = -2 * PI / L * (qx * pos[3 * i] + qy * pos[3 * i + 1] + qz * pos[3 * i + 2]);
+                        double th = -2 * PI / L * (qx * pos[3 * i] + ky_q * pos[3 * i + 1] + qz * pos[3 * i + 2]);
                         cplx ph = { cos(th), sin(th) };
                         double tz = -2 * PI / L * pos[3 * i + 2];
                         cplx st = { cos(tz), sin(tz) };
                         for (int b = 0; b < nb; b++) {
-                            double k[3] = { 2 * PI * qx / L, 2 * PI * qy / L, 2 * PI * (qz + b) / L };
+                            double k[3] = { 2 * PI * qx / L, 2 * PI * ky_q / L, 2 * PI * (qz + b) / L };
                             double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
                             wave_target_add(k, k2, rad[i], ph, vh[b], phh[b], eta, myacc + ii * NC);
                             ph = cmul(ph, st);

@@ -293,3 +293,38 @@ def test_compressible_one_way_coupling(oracle_mod):
     X[:, 3:6] = rng.standard_normal((5, 3))
     y = oracle_mod.mobility(pos, rad, L, X)
     assert np.abs(y[:, 11]).max() < 1e-15                        # E_tr <- T
+
+
+@pytest.mark.parametrize("gamma", [0.3, -0.5])
+def test_sheared_lattice_xi_independence(oracle_mod, gamma):
+    """On the sheared lattice a2 = (gamma L, L, 0) (Sec. 3.2) the split into real-space
+    images and reciprocal-lattice waves leaves the sum independent of xi."""
+    from paper_1506_08481_b300 import inputs
+    rng = np.random.default_rng(3)
+    rad = rng.uniform(0.6, 1.0, 6)
+    L = 8.0
+    pos = inputs.positions_rsa(rad, L, rng)
+    x = rng.standard_normal((6, 12))
+    ys = [oracle_mod.mobility(pos, rad, L, x, xi=xi, tol=1e-13, gamma=gamma) for xi in (0.5, 0.9, 1.4)]
+    for y in ys[1:]:
+        assert np.abs(y - ys[0]).max() <= 1e-12 * np.abs(ys[0]).max()
+
+
+def test_sheared_lattice_periodic_in_the_strain(oracle_mod):
+    """Strains gamma and gamma - 1 give the same lattice (a2 - a1), hence the same
+    mobility; gamma = 0 is another lattice and another mobility; the F, T, S block stays
+    symmetric positive definite."""
+    from paper_1506_08481_b300 import inputs
+    rng = np.random.default_rng(4)
+    rad = rng.uniform(0.6, 1.0, 5)
+    L = 7.5
+    pos = inputs.positions_rsa(rad, L, rng)
+    x = rng.standard_normal((5, 12))
+    y1 = oracle_mod.mobility(pos, rad, L, x, tol=1e-13, gamma=0.2)
+    y2 = oracle_mod.mobility(pos, rad, L, x, tol=1e-13, gamma=-0.8)
+    y0 = oracle_mod.mobility(pos, rad, L, x, tol=1e-13, gamma=0.0)
+    assert np.abs(y1 - y2).max() <= 1e-12 * np.abs(y1).max()
+    assert np.abs(y1 - y0).max() > 1e-4 * np.abs(y1).max()
+    A = oracle_mod.dense_matrix(pos, rad, L, ncomp=11, tol=1e-12, gamma=0.4)
+    assert np.abs(A - A.T).max() <= 1e-10 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
