@@ -30,6 +30,7 @@ SE_OPT_GATHER = 9
 SE_OPT_SPREAD = 12
 SE_OPT_OVERLAP_CHECK = 13
 SE_OPT_RESIDUAL = 14
+SE_OPT_SHEAR = 15
 SE_OPT_PC_THETA = 10
 SE_OPT_PC_KA = 11
 STAGES = ("permute", "real", "spread", "fft_x_fwd", "fft_y_fwd", "fft_z_scale", "fft_y_inv", "fft_x_inv", "gather")

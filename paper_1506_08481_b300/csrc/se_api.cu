@@ -275,6 +275,7 @@ static int ensure_support(se_ctx *c, int prec)
         // real-space kernel recomputes the pairs from the cell list
         const int r = prec == 1 ? build_pair_table<double>(c) : build_pair_table<float>(c);
         if (r == SE_ERR_OVERLAP) return r;
+        if (r != SE_OK && c->shear != 0) return r;      // the cell-list fallback is for the cube only
         if (r != SE_OK) {
             cudaGetLastError();
             dfree(c->b.pair_x[prec]);
@@ -455,6 +456,14 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         if (value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "residual precision must be 1 or 2");
         c->res_precision = (int)value;
         return SE_OK;
+    case SE_OPT_SHEAR:
+        if (!(std::fabs(value) <= 0.5)) return set_error(c, SE_ERR_ARG, "shear strain must be in [-0.5, 0.5]");
+        if (value != c->shear) {
+            c->shear = value;
+            c->have_config = false;        // the configuration must be set again
+            c->pc_ready = false;
+        }
+        return SE_OK;
     case SE_OPT_OVERLAP_CHECK:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "overlap check must be 0 or 1");
         c->overlap_check = (int)value;
@@ -475,12 +484,15 @@ extern "C" int se_set_config(se_ctx *c, int64_t N, double L, const double *pos, 
     if (!c->have_params) return set_error(c, SE_ERR_STATE, "se_set_params must be called first");
     if (!(L > 0) || !std::isfinite(L)) return set_error(c, SE_ERR_ARG, "L must be positive");
     if (c->rc >= 0.5 * L) return set_error(c, SE_ERR_CUTOFF, "rc must be smaller than L/2");
+    if (c->shear != 0 && c->size_mode != 2)
+        return set_error(c, SE_ERR_ARG, "a sheared cell needs the wave-space size approach (SE_OPT_SIZE_MODE 2)");
     cudaSetDevice(c->device);
     SE_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
     free_config(c);
     c->N = N;
     c->L = L;
-    int nc = (int)std::floor(L / c->rc);
+    // cells uniform in the fractional coordinates: the rc ball reaches (1 + |gamma|) rc along t_x
+    int nc = (int)std::floor(L / ((1 + std::fabs(c->shear)) * c->rc));
     if (nc < 3) nc = 1;
     if (nc > 256) nc = 256;
     c->nc = nc;

@@ -25,27 +25,39 @@ SeParams make_params(const se_ctx *c)
     p.kappa = c->L > 0 ? c->M / c->L : 0.0;
     p.hybrid = c->size_mode != 1 ? 1 : 0;
     p.wsrc = c->size_mode == 2 ? 1 : 0;
+    p.gamma = c->shear;
     return p;
 }
 
 namespace {
 
-__global__ void wrap_key_kernel(int N, double L, int nc, const double *pos_in, const double *rad_in,
+// Wraps positions into the periodic cell and keys them by real-space cell.  The cell is
+// spanned by a1 = (L, 0, 0), a2 = (gamma L, L, 0), a3 = (0, 0, L) (gamma = 0: the cube);
+// in the fractional coordinates L t = (x - gamma y, y, z) it is [0, L)^3, and the cells
+// and the Spectral Ewald grid are uniform in t.  The stored position is x = L B t.
+__global__ void wrap_key_kernel(int N, double L, double gamma, int nc, const double *pos_in, const double *rad_in,
                                 double *posw, int *key, int *bad)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int k[3];
     bool ok = isfinite(rad_in[i]) && rad_in[i] > 0;
+    double v[3];
     for (int d = 0; d < 3; ++d) {
-        double v = pos_in[3 * i + d];
-        ok = ok && isfinite(v);
-        v = ok ? v - L * floor(v / L) : 0.0;
-        if (v >= L) v -= L;                    // rounding of the wrap
-        int kk = (int)(v / (L / nc));
-        k[d] = kk >= nc ? nc - 1 : kk;
-        posw[3 * i + d] = v;
+        v[d] = pos_in[3 * i + d];
+        ok = ok && isfinite(v[d]);
     }
+    if (!ok) v[0] = v[1] = v[2] = 0.0;
+    double t[3] = {v[0] - gamma * v[1], v[1], v[2]};      // L t
+    for (int d = 0; d < 3; ++d) {
+        t[d] -= L * floor(t[d] / L);
+        if (t[d] >= L) t[d] -= L;                  // rounding of the wrap
+        int kk = (int)(t[d] / (L / nc));
+        k[d] = kk >= nc ? nc - 1 : kk;
+    }
+    posw[3 * i] = t[0] + gamma * t[1];
+    posw[3 * i + 1] = t[1];
+    posw[3 * i + 2] = t[2];
     key[i] = (k[2] * nc + k[1]) * nc + k[0];
     if (!ok) atomicExch(bad, 1);
 }
@@ -176,7 +188,7 @@ int build_cells(se_ctx *c, const double *pos_in, const double *rad_in)
     SE_CUDA_CHECK(c, cudaMalloc(&count, sizeof(int) * (ncell + 1)));
     SE_CUDA_CHECK(c, cudaMalloc(&bad, sizeof(int)));
     SE_CUDA_CHECK(c, cudaMemsetAsync(bad, 0, sizeof(int), s));
-    wrap_key_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, c->L, nc, pos_in, rad_in, posw, key, bad);
+    wrap_key_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, c->L, c->shear, nc, pos_in, rad_in, posw, key, bad);
     c->launches++;
     int rc = counting_sort(c, N, ncell, key, count, c->b.cell_start, c->b.perm, true);
     if (rc == SE_OK) {

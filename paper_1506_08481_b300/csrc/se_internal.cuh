@@ -44,6 +44,7 @@ struct SeParams {
     double kappa;                // M / L  (d/dx = kappa d/ds)
     int hybrid;                  // 1: target Faxen terms in wave space (hybrid and wave-space approaches)
     int wsrc;                    // 1: source Faxen terms in wave space too (wave-space approach)
+    double gamma;                // strain of the sheared cell a2 = (gamma L, L, 0)
 };
 
 // Cell list for the real-space sum (cells of side >= rc).
@@ -112,6 +113,7 @@ struct se_ctx {
     int gather = 0;              // SE_OPT_GATHER
     int spread = 0;              // SE_OPT_SPREAD
     int overlap_check = 1;       // SE_OPT_OVERLAP_CHECK
+    double shear = 0.0;          // SE_OPT_SHEAR: strain gamma of the periodic cell
     int nsplit = 1;              // CTAs sharing a spreading tile (few tiles: small M)
     // configuration
     bool have_config = false;

@@ -380,20 +380,26 @@ __device__ __forceinline__ void pair_coefficients(double r2, double ai2, double 
 // taken in FP32 where that is safe: with positions in [0, L) rounded to FP32, each
 // component of the FP32 separation is within 5 * 2^-24 L of the exact one and the FP32
 // |x|^2 within 2^-22 |x|^2 of its value, so |x_f32| differs from |x| by less than
-// mrg = 2^-20 (L + rc).  Below (rc - mrg)^2 the pair is surely inside, at or above
+// mrg = 2^-20 (L (1 + 2 |gamma|) + rc) (the sheared cell adds the rounding of the
+// gamma L shift).  Below (rc - mrg)^2 the pair is surely inside, at or above
 // (rc + mrg)^2 surely outside; only the thin band between repeats the FP64 test.
-__device__ __forceinline__ double min_image(double d, double L)
+// Minimum image on the cell a1 = (L, 0, 0), a2 = (g L, L, 0), a3 = (0, 0, L) (|g| <= 1/2):
+// the separation (positions in the wrapped cell, so each component is below (1 + |g|) L)
+// is shifted by a2 until |y| <= L/2, then by a1 (at most twice) and a3.  For g = 0 it is the
+// per-component wrap of the cube.
+template <typename R>
+__device__ __forceinline__ void min_image3(R &x, R &y, R &z, R L, R g)
 {
-    return d > 0.5 * L ? d - L : (d < -0.5 * L ? d + L : d);
-}
-__device__ __forceinline__ float min_image_f(float d, float L)
-{
-    return d > 0.5f * L ? d - L : (d < -0.5f * L ? d + L : d);
+    const R h = (R)0.5 * L;
+    if (y > h) { y -= L; x -= g * L; } else if (y < -h) { y += L; x += g * L; }
+    x = x > h ? x - L : (x < -h ? x + L : x);
+    x = x > h ? x - L : (x < -h ? x + L : x);
+    z = z > h ? z - L : (z < -h ? z + L : z);
 }
 
 struct PairSearch {
-    double L, rc2;
-    float Lf, lo, hi;          // FP32 box and the band (rc -+ mrg)^2
+    double L, rc2, gamma;
+    float Lf, gf, lo, hi;      // FP32 box and strain, and the band (rc -+ mrg)^2
     int nc;
 };
 
@@ -404,7 +410,9 @@ __device__ __forceinline__ void for_neighbours(int i, const PairSearch &ps, cons
     const int nc = ps.nc;
     const double w = ps.L / nc;
     const double px = pos[3 * i], py = pos[3 * i + 1], pz = pos[3 * i + 2];
-    const int cx = min(nc - 1, (int)(px / w)), cy = min(nc - 1, (int)(py / w)), cz = min(nc - 1, (int)(pz / w));
+    // cells of the fractional coordinates L t = (x - gamma y, y, z)
+    const int cx = max(0, min(nc - 1, (int)((px - ps.gamma * py) / w))), cy = min(nc - 1, (int)(py / w)),
+              cz = min(nc - 1, (int)(pz / w));
     const float4 pi = pf[i];
     const int span = nc >= 3 ? 1 : 0;
     for (int dz = -span; dz <= span; ++dz)
@@ -413,13 +421,13 @@ __device__ __forceinline__ void for_neighbours(int i, const PairSearch &ps, cons
                 const int nb = (((cz + dz + nc) % nc) * nc + (cy + dy + nc) % nc) * nc + (cx + dx + nc) % nc;
                 for (int j = cell_start[nb]; j < cell_start[nb + 1]; ++j) {
                     const float4 pj = pf[j];
-                    const float x0 = min_image_f(pi.x - pj.x, ps.Lf), x1 = min_image_f(pi.y - pj.y, ps.Lf),
-                                x2 = min_image_f(pi.z - pj.z, ps.Lf);
+                    float x0 = pi.x - pj.x, x1 = pi.y - pj.y, x2 = pi.z - pj.z;
+                    min_image3(x0, x1, x2, ps.Lf, ps.gf);
                     const float r2f = x0 * x0 + x1 * x1 + x2 * x2;
                     if (r2f >= ps.hi || j == i) continue;
                     if (r2f >= ps.lo) {
-                        const double y0 = min_image(px - pos[3 * j], ps.L), y1 = min_image(py - pos[3 * j + 1], ps.L),
-                                     y2 = min_image(pz - pos[3 * j + 2], ps.L);
+                        double y0 = px - pos[3 * j], y1 = py - pos[3 * j + 1], y2 = pz - pos[3 * j + 2];
+                        min_image3(y0, y1, y2, ps.L, ps.gamma);
                         if (!(y0 * y0 + y1 * y1 + y2 * y2 < ps.rc2)) continue;
                     }
                     f(j, r2f, pj.w);
@@ -447,8 +455,8 @@ __global__ void pair_count_kernel(int N, PairSearch ps, const int *cell_start, c
         ++n;
         const float sa = ai + aj;
         if (overlap && r2f < sa * sa * 1.0001f) {
-            const double y0 = min_image(pos[3 * i] - pos[3 * j], ps.L), y1 = min_image(pos[3 * i + 1] - pos[3 * j + 1], ps.L),
-                         y2 = min_image(pos[3 * i + 2] - pos[3 * j + 2], ps.L);
+            double y0 = pos[3 * i] - pos[3 * j], y1 = pos[3 * i + 1] - pos[3 * j + 1], y2 = pos[3 * i + 2] - pos[3 * j + 2];
+            min_image3(y0, y1, y2, ps.L, ps.gamma);
             const double s = (rad[i] + rad[j]) * (1.0 - 1e-12);
             if (y0 * y0 + y1 * y1 + y2 * y2 < s * s) atomicExch(overlap, 1);
         }
@@ -468,7 +476,8 @@ __global__ void pair_list_kernel(int N, PairSearch ps, const int *cell_start, co
 // One warp per target: the lanes take the target's pairs in turn, form the FP64
 // separation and the radial coefficients and store them (coalesced SoA rows).
 template <typename T>
-__global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double xi, double eta, const double *pos,
+__global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double gamma, double xi, double eta,
+                                                        const double *pos,
                                                         const double *rad, const int *off, size_t np, const int *pj,
                                                         T *px, T *pc)
 {
@@ -479,8 +488,8 @@ __global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double 
     const int ke = off[i + 1];
     for (int k = off[i] + lane; k < ke; k += 32) {
         const int j = pj[k];
-        const double x0 = min_image(p0 - pos[3 * j], L), x1 = min_image(p1 - pos[3 * j + 1], L),
-                     x2 = min_image(p2 - pos[3 * j + 2], L);
+        double x0 = p0 - pos[3 * j], x1 = p1 - pos[3 * j + 1], x2 = p2 - pos[3 * j + 2];
+        min_image3(x0, x1, x2, L, gamma);
         double cf[kNPC];
         pair_coefficients(x0 * x0 + x1 * x1 + x2 * x2, ai2, rad[j] * rad[j], xi, eta, cf);
         px[k] = (T)x0;
@@ -542,9 +551,13 @@ int build_pair_table(se_ctx *c)
         PairSearch ps;
         ps.L = c->L;
         ps.rc2 = c->rc * c->rc;
+        ps.gamma = c->shear;
         ps.nc = c->nc;
         ps.Lf = (float)c->L;
-        const double mrg = std::ldexp(c->L + c->rc, -20);
+        ps.gf = (float)c->shear;
+        // FP32 separations: within 5 2^-24 L of the exact ones per component, plus the
+        // rounding of the shear shift gamma L
+        const double mrg = std::ldexp(c->L * (1 + 2 * std::fabs(c->shear)) + c->rc, -20);
         ps.lo = (float)((c->rc - mrg) * (c->rc - mrg));
         ps.hi = (float)((c->rc + mrg) * (c->rc + mrg));
         int *ovl = c->overlap_check ? count + N : nullptr;    // the flag after the counts
@@ -581,8 +594,9 @@ int build_pair_table(se_ctx *c)
         c->err = "pair table allocation failed";
         return SE_ERR_NOMEM;
     }
-    pair_fill_kernel<T><<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->xi, c->eta, c->b.pos, c->b.rad, c->b.pair_off, np,
-                                                    c->b.pair_j, (T *)c->b.pair_x[q], (T *)c->b.pair_c[q]);
+    pair_fill_kernel<T><<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->shear, c->xi, c->eta, c->b.pos, c->b.rad,
+                                                    c->b.pair_off, np, c->b.pair_j, (T *)c->b.pair_x[q],
+                                                    (T *)c->b.pair_c[q]);
     c->launches++;
     SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
     c->pairs_ok[q] = true;

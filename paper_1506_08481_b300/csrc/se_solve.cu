@@ -243,6 +243,7 @@ static int build_precond(se_ctx *c, int ncomp, bool learned)
     rc = se_set_params(sc, c->xi, c->M, c->P, c->rc);
     if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_PRECISION, 1);
     if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_SIZE_MODE, c->size_mode);
+    if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_SHEAR, c->shear);
     if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_ETA, c->eta);
     if (rc == SE_OK && c->m_user) rc = se_set_option(sc, SE_OPT_SHAPE_M, c->m_shape);
     if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_PARTS, 2);   // wave space only (no real-space neighbours)
@@ -738,6 +739,8 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
     double *yd = gm.hd + (m + 1);
     const bool shifted = !(alpha == 0.0 && beta == 1.0);
     if ((shifted || mixed) && precond != SE_PRECOND_NONE) precond = SE_PRECOND_BLOCK;
+    // the spectral correction's plane waves are those of the cube
+    if (precond == SE_PRECOND_SPECTRAL && c->shear != 0) precond = SE_PRECOND_BLOCK;
     double *ms = c->b.work64 + 5 * n;     // the masked vector P_S v of the mixed operator
 
     // the learned correction needs trained weights; without them it is the plain block

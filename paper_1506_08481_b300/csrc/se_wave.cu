@@ -79,7 +79,8 @@ __global__ void support_kernel(int N, SeParams p, const double *pos, const doubl
     if (i >= N) return;
     const int M = p.M, P = p.P;
     for (int d = 0; d < 3; ++d) {
-        double u = pos[3 * i + d] * p.kappa;
+        // grid units of the fractional coordinate: u = M t, L t = (x - gamma y, y, z)
+        double u = (pos[3 * i + d] - (d == 0 ? p.gamma * pos[3 * i + 1] : 0.0)) * p.kappa;
         int b = (int)floor(u - 0.5 * P) + 1;
         double s0 = b - u;                       // in (-P/2, -P/2 + 1]
         int ic = (int)floor(-s0 + 0.5);          // index of the point nearest the particle
@@ -244,7 +245,10 @@ __device__ __forceinline__ void spread_body(int tile, int part, int tid, Sync sy
             const int halves = (int)v1.z;
             if (gxy == (T)0 || halves == 0) continue;
             const T4 v0 = sp[k][0], v2 = sp[k][2];
-            const T sx = v0.x + tx, sy = v0.y + ty;
+            const T sx = v0.x + tx, sy0 = v0.y + ty;
+            // the physical gradient of the window is -2 alpha kappa (sx, sy - gamma sx, sz) g in
+            // the sheared cell (grid units of the fractional coordinates); gamma = 0 otherwise
+            const T sy = WS ? sy0 - (T)p.gamma * sx : sy0;
             if constexpr (WS) {
                 // h0[q][p], ha[q][p]: coefficients of s_z^p (p = 0, 1) of H0 and Ha (times g_xy)
                 T h0[3][2], ha[3][2];
@@ -791,7 +795,8 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_y(FftPlan plan, const type
 template <typename T, int CO, int LB, int CI = 4>
 __device__ __forceinline__ void fft_z_scale_body(int bx, int by, unsigned char *sm, const FftPlan &plan,
                                                  const typename C2<T>::t *twg, const typename C2<T>::t *specf,
-                                                 typename C2<T>::t *speco, T cnorm, T twopiL, T i4x2, T ecoef)
+                                                 typename C2<T>::t *speco, T cnorm, T twopiL, T i4x2, T ecoef,
+                                                 T gam = (T)0)
 {
     using T2 = typename C2<T>::t;
     constexpr int NLI = CI * LB, NLO = LB * CO, CPE = sizeof(T) == 4 ? 2 : 1;
@@ -825,7 +830,8 @@ __device__ __forceinline__ void fft_z_scale_body(int bx, int by, unsigned char *
         const bool zero = q >= nq || (qx == 0 && ys == 0 && zsn == 0) || 2 * qx == M || 2 * ys == M ||
                           2 * zsn == M;
         if (!zero) {
-            const T kx = twopiL * qx, ky = twopiL * ys, kz = twopiL * zsn;
+            // k = (2 pi / L)(q1, q2 - gamma q1, q3): the reciprocal lattice of the sheared cell
+            const T kx = twopiL * qx, ky = twopiL * ((T)ys - gam * (T)qx), kz = twopiL * zsn;
             const T k2 = kx * kx + ky * ky + kz * kz;
             const T q2 = (T)(qx * qx + ys * ys + zsn * zsn);
             const T ex = -k2 * i4x2 + ecoef * q2;
@@ -878,11 +884,11 @@ template <typename T, int CO, int LB, int CI = 4>
 __global__ void __launch_bounds__(kFftThreads, 4) fft_z_scale(FftPlan plan, const typename C2<T>::t *twg,
                                                               const typename C2<T>::t *specf,
                                                               typename C2<T>::t *speco, T cnorm, T twopiL, T i4x2,
-                                                              T ecoef)
+                                                              T ecoef, T gam)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     fft_z_scale_body<T, CO, LB, CI>(blockIdx.x, blockIdx.y, smraw, plan, twg, specf, speco, cnorm, twopiL, i4x2,
-                                    ecoef);
+                                    ecoef, gam);
 }
 
 // z pass with a tabulated radial kernel in place of the Ewald one (the coarse spectral
@@ -1154,7 +1160,9 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
                 }
             }
             const T gxy = act ? wx[cx] * wy[cy] : (T)0;
-            const T sx = sx0 + cx, sy = sy0 + cy, sxy2 = sx * sx + sy * sy;
+            // sheared cell: the physical direction of the window gradient (sx, sy - gamma sx, sz)
+            const T sx = sx0 + cx, sy = sy0 + cy - (CO == 8 ? (T)p.gamma * (sx0 + cx) : (T)0),
+                    sxy2 = sx * sx + sy * sy;
             T col[NA];
             if constexpr (CO == 8) {
                 // U = sum g (v + a^2/6 v''); Omega ~ sum g s x v; E ~ sum g sym(s (x) (v + a^2/10 v''))
@@ -1591,7 +1599,8 @@ static void launch_z(se_ctx *c, const SeParams &p, const typename C2<T>::t *tw, 
     const T ecoef = (T)(2.0 * kPi * kPi / (p.alpha * (double)M * M));
     cudaFuncSetAttribute(fft_z_scale<T, CO, LB, CI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     fft_z_scale<T, CO, LB, CI><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, smem, s>>>(c->plan, tw, sf, so, cnorm,
-                                                                                     twopiL, i4x2, ecoef);
+                                                                                     twopiL, i4x2, ecoef,
+                                                                                     (T)p.gamma);
 }
 
 template <typename T, int CO, int CI = 4>
@@ -1705,7 +1714,8 @@ void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int nc
                                        c->b.rad, (const T *)c->b.self_c[pix<T>()], c->b.perm,
                                        (const T *)c->b.grid_o[pix<T>()], xs, yreal, y, ncomp, with_wave, with_self);
     };
-    const bool staged = !std::is_same<T, ff>::value && (c->gather == 2 || (c->gather == 0 && c->P <= kStagedMaxP));
+    const bool staged = !std::is_same<T, ff>::value && c->shear == 0 &&
+                        (c->gather == 2 || (c->gather == 0 && c->P <= kStagedMaxP));
     if constexpr (!std::is_same<T, ff>::value) if (with_wave && staged) {
         // staged gather: one CTA per spreading bin (see gather_staged_kernel)
         const int CO = p.hybrid ? 8 : 4;

@@ -76,6 +76,36 @@ def _pair_dist(pos, pairs, L):
     return np.sqrt(np.sum(dx * dx, axis=1))
 
 
+def positions_rsa_sheared(rad: np.ndarray, L: float, gamma: float, rng: np.random.Generator,
+                          max_tries: int = 5000) -> np.ndarray:
+    """Random sequential addition (largest first, brute force: small N) in the periodic
+    cell a1 = (L, 0, 0), a2 = (gamma L, L, 0), a3 = (0, 0, L): no sphere overlaps another
+    or any periodic image of it (Lees-Edwards minimum image)."""
+    n = rad.shape[0]
+    order = np.argsort(-rad, kind="stable")
+    pos = np.zeros((n, 3))
+    placed: list[int] = []
+    for idx in order:
+        for _ in range(max_tries):
+            t = rng.uniform(0.0, 1.0, 3)
+            p = L * np.array([t[0] + gamma * t[1], t[1], t[2]])
+            if placed:
+                d = p - pos[placed]
+                ny = np.round(d[:, 1] / L)
+                d[:, 1] -= ny * L
+                d[:, 0] -= ny * gamma * L
+                d[:, 0] -= L * np.round(d[:, 0] / L)
+                d[:, 2] -= L * np.round(d[:, 2] / L)
+                if np.any(np.sum(d * d, axis=1) < (rad[idx] + rad[placed]) ** 2):
+                    continue
+            pos[idx] = p
+            placed.append(idx)
+            break
+        else:
+            raise RuntimeError("random sequential addition did not place every sphere")
+    return pos
+
+
 def positions_rsa(rad: np.ndarray, L: float, rng: np.random.Generator, max_tries: int = 2000) -> np.ndarray:
     """Random sequential addition (largest first), each sphere uniform in the box
     and rejected while it overlaps an already placed one."""
