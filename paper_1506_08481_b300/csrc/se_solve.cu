@@ -850,13 +850,21 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
                 rc = op(zj, w, c->precision);
                 if (rc != SE_OK) return rc;
                 ++prods;
-                // classical Gram-Schmidt, twice
+                // classical Gram-Schmidt with selective reorthogonalisation (Daniel, Gragg,
+                // Kaufman & Stewart 1976): a second pass only when the first one cancelled,
+                // |w - V h|^2 < |w|^2 / 2 with |w|^2 = |h|^2 + |w - V h|^2
                 if ((rc = gm.dots(V, n, j + 1, w, h.data())) != SE_OK) return rc;
                 if ((rc = gm.axpy_multi(V, n, j + 1, h.data(), w)) != SE_OK) return rc;
-                if ((rc = gm.dots(V, n, j + 1, w, h2.data())) != SE_OK) return rc;
-                if ((rc = gm.axpy_multi(V, n, j + 1, h2.data(), w)) != SE_OK) return rc;
                 double wn2;
                 if ((rc = gm.dots(w, 0, 1, w, &wn2)) != SE_OK) return rc;
+                double hn2 = 0;
+                for (int i = 0; i <= j; ++i) hn2 += h[i] * h[i];
+                std::fill(h2.begin(), h2.begin() + (j + 1), 0.0);
+                if (wn2 < 0.5 * (hn2 + wn2)) {
+                    if ((rc = gm.dots(V, n, j + 1, w, h2.data())) != SE_OK) return rc;
+                    if ((rc = gm.axpy_multi(V, n, j + 1, h2.data(), w)) != SE_OK) return rc;
+                    if ((rc = gm.dots(w, 0, 1, w, &wn2)) != SE_OK) return rc;
+                }
                 const double hn = std::sqrt(wn2);
                 for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i] + h2[i];
                 H[(size_t)(j + 1) * m + j] = hn;
