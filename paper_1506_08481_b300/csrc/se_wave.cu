@@ -433,20 +433,26 @@ __device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
 
 constexpr int kTz = 16;    // planes per tile of spread16_kernel
 
-struct Spread16Smem {
-    float sxy[64][2 * kTile];   // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
-    float4 swz[64][kTz];        // unit 2 zp + h: (W_2zp, W_2zp+1) of e = 2h, 2h + 1; at unit ^ (k & 7)
-    float4 sp[64][5];
+// particles staged per chunk (the CTA's 64 threads stage up to CH of them at a time)
+#ifndef SE_SPREAD16_CH
+#define SE_SPREAD16_CH 64
+#endif
+
+template <int CH = SE_SPREAD16_CH> struct Spread16SmemT {
+    float sxy[CH][2 * kTile];   // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
+    float4 swz[CH][kTz];        // unit 2 zp + h: (W_2zp, W_2zp+1) of e = 2h, 2h + 1; at unit ^ (k & 7)
+    float4 sp[CH][5];
     int bin_beg[6 * 6 * 7], bin_off[6 * 6 * 7 + 1];
 };
+using Spread16Smem = Spread16SmemT<>;
 
-template <int NCOMP, bool SPLIT, typename Sync>
-__device__ __forceinline__ void spread16_body(int tile, int part, int tid, Sync sync, Spread16Smem &sm, SeParams p,
+template <int NCOMP, bool SPLIT, typename Sync, int CH = SE_SPREAD16_CH>
+__device__ __forceinline__ void spread16_body(int tile, int part, int tid, Sync sync, Spread16SmemT<CH> &sm, SeParams p,
                                               const int *tile_start, const int *tile_perm, const int *base,
                                               const float *s0g, const float *wg, const double *rad, const float *xs,
                                               float *grid, int nsplit)
 {
-    constexpr int TT = kTile, TZ = kTz, CH = 64;
+    constexpr int TT = kTile, TZ = kTz, NT = 64;      // threads
     auto &sxy = sm.sxy;
     auto &swz = sm.swz;
     auto &sp = sm.sp;
@@ -468,7 +474,7 @@ __device__ __forceinline__ void spread16_body(int tile, int part, int tid, Sync 
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc2[z][c] = 0ull;
 
-    for (int bb = tid; bb < nb3; bb += CH) {
+    for (int bb = tid; bb < nb3; bb += NT) {
         const int bx = bb % nbin, by = (bb / nbin) % nbin, bz = bb / (nbin * nbin);
         const int bin = (wrapi(bztop - bz, nt) * nt + wrapi(by0 - by, nt)) * nt + wrapi(bx0 - bx, nt);
         bin_beg[bb] = tile_start[bin];
@@ -635,8 +641,12 @@ __device__ __forceinline__ void spread16_body(int tile, int part, int tid, Sync 
     }
 }
 
+#ifndef SE_SPREAD16_MINB
+#define SE_SPREAD16_MINB 8
+#endif
+
 template <int NCOMP, bool SPLIT>
-__global__ void __launch_bounds__(64, 8) spread16_kernel(SeParams p, const int *tile_start, const int *tile_perm,
+__global__ void __launch_bounds__(64, SE_SPREAD16_MINB) spread16_kernel(SeParams p, const int *tile_start, const int *tile_perm,
                                                          const int *base, const float *s0g, const float *wg,
                                                          const double *rad, const float *xs, float *grid, int nsplit)
 {
