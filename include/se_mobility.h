@@ -96,7 +96,8 @@ typedef struct se_ctx se_ctx;
                                   when the products run in FP32: 2 (default, double-float) or 1 (FP64) */
 #define SE_OPT_SHEAR      15   /* strain gamma in [-0.5, 0.5] of the periodic cell a1 = (L, 0, 0), a2 = (gamma L,
                                   L, 0), a3 = (0, 0, L) (a cube sheared in x along y, Sec. 3.2; default 0).
-                                  Needs SE_OPT_SIZE_MODE 2; se_set_config must follow; the spectral
+                                  Needs SE_OPT_SIZE_MODE 2 (set first; SE_ERR_ARG otherwise, also for a
+                                  later change of the size mode); se_set_config must follow; the spectral
                                   preconditioner falls back to the block one; positions may be given
                                   in any periodic image */
 #define SE_OPT_OVERLAP_CHECK 13  /* 1 (default): se_set_config fails with SE_ERR_OVERLAP if two spheres within

@@ -398,6 +398,8 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
     case SE_OPT_SIZE_MODE:
         if (value != 0 && value != 1 && value != 2)
             return set_error(c, SE_ERR_ARG, "size mode must be 0 (hybrid), 1 (real-space) or 2 (wave-space)");
+        if (c->shear != 0 && value != 2)
+            return set_error(c, SE_ERR_ARG, "a sheared cell needs the wave-space size approach (SE_OPT_SIZE_MODE 2)");
         c->size_mode = (int)value;
         c->pc_ready = false;
         return SE_OK;
@@ -458,6 +460,8 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         return SE_OK;
     case SE_OPT_SHEAR:
         if (!(std::fabs(value) <= 0.5)) return set_error(c, SE_ERR_ARG, "shear strain must be in [-0.5, 0.5]");
+        if (value != 0 && c->size_mode != 2)
+            return set_error(c, SE_ERR_ARG, "a sheared cell needs the wave-space size approach (SE_OPT_SIZE_MODE 2)");
         if (value != c->shear) {
             c->shear = value;
             c->have_config = false;        // the configuration must be set again

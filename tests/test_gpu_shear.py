@@ -120,6 +120,12 @@ def test_shear_needs_the_wave_space_approach(poly):
     cfg, _ = poly
     c = api.Context()
     c.set_params(1.0, 64, 24, 5.45)
+    with pytest.raises(api.SeError):
+        c.set_option(api.SE_OPT_SHEAR, 0.2)              # size approach 0 (hybrid)
+    c.set_option(api.SE_OPT_SIZE_MODE, 2)
     c.set_option(api.SE_OPT_SHEAR, 0.2)
     with pytest.raises(api.SeError):
-        c.set_config(cfg.pos, cfg.rad, cfg.L)
+        c.set_option(api.SE_OPT_SIZE_MODE, 1)
+    with pytest.raises(api.SeError):
+        c.set_option(api.SE_OPT_SHEAR, 0.7)              # outside [-1/2, 1/2]
+    c.set_config(cfg.pos, cfg.rad, cfg.L)
