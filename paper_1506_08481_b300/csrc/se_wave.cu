@@ -45,6 +45,9 @@ template <> struct V4<ff> { using t = ff4; };
 #ifndef SE_GATHER_MINB
 #define SE_GATHER_MINB 2
 #endif
+#ifndef SE_GATHER_NCL
+#define SE_GATHER_NCL 2         // columns per lane of the FP32 4-component gather
+#endif
 #ifndef SE_GATHER_UNROLL
 #define SE_GATHER_UNROLL 12
 #endif
@@ -1135,82 +1138,106 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
         const T B1 = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
         const T c6 = a * a / 6, c10 = a * a / 10;
         const size_t zs = (size_t)M * M * CO;
-        for (int it = 0; it < P * P; it += 32) {
-            const int c = it + lane;
-            const bool act = c < P * P;
-            const int cy = act ? c / P : 0, cx = act ? c - cy * P : 0;
-            const T *gp = grid + ((size_t)wrapi(by + cy, M) * M + wrapi(bx + cx, M)) * CO;
+        // FP32 4-component grids: each lane takes two columns at a time, so that one read of
+        // a plane's W and offset (shared memory, the same for every lane) serves two points
+        constexpr int NCL = (std::is_same<T, float>::value && CO == 4) ? SE_GATHER_NCL : 1;
+        constexpr int kUnr = kGatherUnroll;
+        for (int it = 0; it < P * P; it += 32 * NCL) {
+            int cxa[NCL], cya[NCL];
+            bool acta[NCL];
+            const T *gpa[NCL];
             // column moments: Z0..Z3 of v (and of v'' in the hybrid mode), Zp of p
-            T z0[3] = {0, 0, 0}, z1[3] = {0, 0, 0}, z2[3] = {0, 0, 0}, z3[3] = {0, 0, 0}, zp = 0;
-            if (act) {
-#pragma unroll kGatherUnroll
+            T z0[NCL][3], z1[NCL][3], z2[NCL][3], z3[NCL][3], zp[NCL];
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < NCL; ++j) {
+                const int c = it + 32 * j + lane;
+                acta[j] = c < P * P;
+                any |= acta[j];
+                cya[j] = acta[j] ? c / P : 0;
+                cxa[j] = acta[j] ? c - cya[j] * P : 0;
+                gpa[j] = grid + ((size_t)wrapi(by + cya[j], M) * M + wrapi(bx + cxa[j], M)) * CO;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) z0[j][q] = z1[j][q] = z2[j][q] = z3[j][q] = 0;
+                zp[j] = 0;
+            }
+            if (any) {
+#pragma unroll kUnr
                 for (int k = 0; k < P; ++k) {
                     const T4 w = Wz[k];
-                    const T4 u0 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[k] * zs);
-                    if constexpr (CO == 8) {
-                        const T4 u1 = *reinterpret_cast<const T4 *>(gp + (size_t)Zi[k] * zs + 4);
-                        // u0 = (v0 v1 v2 v''0), u1 = (v''1 v''2 p -): z0 = sum g v, z1 = sum g v'',
-                        // z2 = sum g s_z v, z3 = sum g s_z v''
-                        z0[0] += w.x * u0.x; z0[1] += w.x * u0.y; z0[2] += w.x * u0.z;
-                        z1[0] += w.x * u0.w; z1[1] += w.x * u1.x; z1[2] += w.x * u1.y;
-                        if constexpr (NCOMP >= 6) {
-                            z2[0] += w.y * u0.x; z2[1] += w.y * u0.y; z2[2] += w.y * u0.z;
-                            if constexpr (NCOMP >= 11) { z3[0] += w.y * u0.w; z3[1] += w.y * u1.x; z3[2] += w.y * u1.y; }
+                    const size_t off = (size_t)Zi[k] * zs;
+#pragma unroll
+                    for (int j = 0; j < NCL; ++j) {
+                        const T4 u0 = *reinterpret_cast<const T4 *>(gpa[j] + off);
+                        if constexpr (CO == 8) {
+                            const T4 u1 = *reinterpret_cast<const T4 *>(gpa[j] + off + 4);
+                            // u0 = (v0 v1 v2 v''0), u1 = (v''1 v''2 p -): z0 = sum g v, z1 = sum g v'',
+                            // z2 = sum g s_z v, z3 = sum g s_z v''
+                            z0[j][0] += w.x * u0.x; z0[j][1] += w.x * u0.y; z0[j][2] += w.x * u0.z;
+                            z1[j][0] += w.x * u0.w; z1[j][1] += w.x * u1.x; z1[j][2] += w.x * u1.y;
+                            if constexpr (NCOMP >= 6) {
+                                z2[j][0] += w.y * u0.x; z2[j][1] += w.y * u0.y; z2[j][2] += w.y * u0.z;
+                                if constexpr (NCOMP >= 11) { z3[j][0] += w.y * u0.w; z3[j][1] += w.y * u1.x; z3[j][2] += w.y * u1.y; }
+                            }
+                            if constexpr (NCOMP >= 12) zp[j] += w.x * u1.z;
+                        } else {
+                            z0[j][0] += w.x * u0.x; z0[j][1] += w.x * u0.y; z0[j][2] += w.x * u0.z;
+                            z2[j][0] += w.z * u0.x; z2[j][1] += w.z * u0.y; z2[j][2] += w.z * u0.z;
+                            if constexpr (NCOMP >= 6) {
+                                z1[j][0] += w.y * u0.x; z1[j][1] += w.y * u0.y; z1[j][2] += w.y * u0.z;
+                                if constexpr (NCOMP >= 11) { z3[j][0] += w.w * u0.x; z3[j][1] += w.w * u0.y; z3[j][2] += w.w * u0.z; }
+                            }
+                            if constexpr (NCOMP >= 12) zp[j] += w.x * u0.w;
                         }
-                        if constexpr (NCOMP >= 12) zp += w.x * u1.z;
-                    } else {
-                        z0[0] += w.x * u0.x; z0[1] += w.x * u0.y; z0[2] += w.x * u0.z;
-                        z2[0] += w.z * u0.x; z2[1] += w.z * u0.y; z2[2] += w.z * u0.z;
-                        if constexpr (NCOMP >= 6) {
-                            z1[0] += w.y * u0.x; z1[1] += w.y * u0.y; z1[2] += w.y * u0.z;
-                            if constexpr (NCOMP >= 11) { z3[0] += w.w * u0.x; z3[1] += w.w * u0.y; z3[2] += w.w * u0.z; }
-                        }
-                        if constexpr (NCOMP >= 12) zp += w.x * u0.w;
                     }
                 }
             }
-            const T gxy = act ? wx[cx] * wy[cy] : (T)0;
-            // sheared cell: the physical direction of the window gradient (sx, sy - gamma sx, sz)
-            const T sx = sx0 + cx, sy = sy0 + cy - (CO == 8 ? (T)p.gamma * (sx0 + cx) : (T)0),
-                    sxy2 = sx * sx + sy * sy;
-            T col[NA];
-            if constexpr (CO == 8) {
-                // U = sum g (v + a^2/6 v''); Omega ~ sum g s x v; E ~ sum g sym(s (x) (v + a^2/10 v''))
-                col[0] = gxy * (z0[0] + c6 * z1[0]);
-                col[1] = gxy * (z0[1] + c6 * z1[1]);
-                col[2] = gxy * (z0[2] + c6 * z1[2]);
-                col[3] = gxy * (sy * z0[2] - z2[1]);
-                col[4] = gxy * (z2[0] - sx * z0[2]);
-                col[5] = gxy * (sx * z0[1] - sy * z0[0]);
-                const T Q0 = z0[0] + c10 * z1[0], Q1 = z0[1] + c10 * z1[1], Q2 = z0[2] + c10 * z1[2];
-                const T R0 = z2[0] + c10 * z3[0], R1 = z2[1] + c10 * z3[1], R2 = z2[2] + c10 * z3[2];
-                col[6] = gxy * sx * Q0;
-                col[7] = gxy * sy * Q1;
-                col[8] = gxy * R2;
-                col[9] = gxy * (sx * Q1 + sy * Q0);
-                col[10] = gxy * (sx * Q2 + R0);
-                col[11] = gxy * (sy * Q2 + R1);
-            } else {
-                // z0 = sum g v, z1 = sum g s_z v, z2 = sum g s_z^2 v, z3 = sum g s_z^3 v
-                const T a0 = A0 + A1 * sxy2, b0 = B0 + B1 * sxy2;
-                col[0] = gxy * (a0 * z0[0] + A1 * z2[0]);
-                col[1] = gxy * (a0 * z0[1] + A1 * z2[1]);
-                col[2] = gxy * (a0 * z0[2] + A1 * z2[2]);
-                col[3] = gxy * (sy * z0[2] - z1[1]);
-                col[4] = gxy * (z1[0] - sx * z0[2]);
-                col[5] = gxy * (sx * z0[1] - sy * z0[0]);
-                const T Q0 = b0 * z0[0] + B1 * z2[0], Q1 = b0 * z0[1] + B1 * z2[1], Q2 = b0 * z0[2] + B1 * z2[2];
-                const T R0 = b0 * z1[0] + B1 * z3[0], R1 = b0 * z1[1] + B1 * z3[1], R2 = b0 * z1[2] + B1 * z3[2];
-                col[6] = gxy * sx * Q0;
-                col[7] = gxy * sy * Q1;
-                col[8] = gxy * R2;
-                col[9] = gxy * (sx * Q1 + sy * Q0);
-                col[10] = gxy * (sx * Q2 + R0);
-                col[11] = gxy * (sy * Q2 + R1);
-            }
-            col[12] = gxy * zp;
 #pragma unroll
-            for (int cc = 0; cc < NA; ++cc) kahan_add(acc[cc], cmp[cc], col[cc]);
+            for (int j = 0; j < NCL; ++j) {
+                const int cx = cxa[j], cy = cya[j];
+                const T gxy = acta[j] ? wx[cx] * wy[cy] : (T)0;
+                // sheared cell: the physical direction of the window gradient (sx, sy - gamma sx, sz)
+                const T sx = sx0 + cx, sy = sy0 + cy - (CO == 8 ? (T)p.gamma * (sx0 + cx) : (T)0),
+                        sxy2 = sx * sx + sy * sy;
+                T col[NA];
+                if constexpr (CO == 8) {
+                    // U = sum g (v + a^2/6 v''); Omega ~ sum g s x v; E ~ sum g sym(s (x) (v + a^2/10 v''))
+                    col[0] = gxy * (z0[j][0] + c6 * z1[j][0]);
+                    col[1] = gxy * (z0[j][1] + c6 * z1[j][1]);
+                    col[2] = gxy * (z0[j][2] + c6 * z1[j][2]);
+                    col[3] = gxy * (sy * z0[j][2] - z2[j][1]);
+                    col[4] = gxy * (z2[j][0] - sx * z0[j][2]);
+                    col[5] = gxy * (sx * z0[j][1] - sy * z0[j][0]);
+                    const T Q0 = z0[j][0] + c10 * z1[j][0], Q1 = z0[j][1] + c10 * z1[j][1], Q2 = z0[j][2] + c10 * z1[j][2];
+                    const T R0 = z2[j][0] + c10 * z3[j][0], R1 = z2[j][1] + c10 * z3[j][1], R2 = z2[j][2] + c10 * z3[j][2];
+                    col[6] = gxy * sx * Q0;
+                    col[7] = gxy * sy * Q1;
+                    col[8] = gxy * R2;
+                    col[9] = gxy * (sx * Q1 + sy * Q0);
+                    col[10] = gxy * (sx * Q2 + R0);
+                    col[11] = gxy * (sy * Q2 + R1);
+                } else {
+                    // z0 = sum g v, z1 = sum g s_z v, z2 = sum g s_z^2 v, z3 = sum g s_z^3 v
+                    const T a0 = A0 + A1 * sxy2, b0 = B0 + B1 * sxy2;
+                    col[0] = gxy * (a0 * z0[j][0] + A1 * z2[j][0]);
+                    col[1] = gxy * (a0 * z0[j][1] + A1 * z2[j][1]);
+                    col[2] = gxy * (a0 * z0[j][2] + A1 * z2[j][2]);
+                    col[3] = gxy * (sy * z0[j][2] - z1[j][1]);
+                    col[4] = gxy * (z1[j][0] - sx * z0[j][2]);
+                    col[5] = gxy * (sx * z0[j][1] - sy * z0[j][0]);
+                    const T Q0 = b0 * z0[j][0] + B1 * z2[j][0], Q1 = b0 * z0[j][1] + B1 * z2[j][1], Q2 = b0 * z0[j][2] + B1 * z2[j][2];
+                    const T R0 = b0 * z1[j][0] + B1 * z3[j][0], R1 = b0 * z1[j][1] + B1 * z3[j][1], R2 = b0 * z1[j][2] + B1 * z3[j][2];
+                    col[6] = gxy * sx * Q0;
+                    col[7] = gxy * sy * Q1;
+                    col[8] = gxy * R2;
+                    col[9] = gxy * (sx * Q1 + sy * Q0);
+                    col[10] = gxy * (sx * Q2 + R0);
+                    col[11] = gxy * (sy * Q2 + R1);
+                }
+                col[12] = gxy * zp[j];
+#pragma unroll
+                for (int cc = 0; cc < NA; ++cc) kahan_add(acc[cc], cmp[cc], col[cc]);
+            }
         }
 #pragma unroll
         for (int cc = 0; cc < NA; ++cc) {
