@@ -438,13 +438,13 @@ constexpr int kTz = 16;    // planes per tile of spread16_kernel
 
 // particles staged per chunk (the CTA's 64 threads stage up to CH of them at a time)
 #ifndef SE_SPREAD16_CH
-#define SE_SPREAD16_CH 64
+#define SE_SPREAD16_CH 60
 #endif
 
 template <int CH = SE_SPREAD16_CH> struct Spread16SmemT {
     float sxy[CH][2 * kTile];   // window weights x(8) y(8), entry e at e ^ ((k >> 1) & 15)
     float4 swz[CH][kTz];        // unit 2 zp + h: (W_2zp, W_2zp+1) of e = 2h, 2h + 1; at unit ^ (k & 7)
-    float4 sp[CH][5];
+    float4 sp[CH][7];           // per-particle coefficients of the column polynomials (below)
     int bin_beg[6 * 6 * 7], bin_off[6 * 6 * 7 + 1];
 };
 using Spread16Smem = Spread16SmemT<>;
@@ -549,53 +549,80 @@ __device__ __forceinline__ void spread16_body(int tile, int part, int tid, Sync 
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq)
                 if (zlo < 4 * qq + 4 && zhi > 4 * qq) quarters |= 1 << qq;
-            sp[k][0] = make_float4(s0g[3 * i] + (float)od[0], s0g[3 * i + 1] + (float)od[1], 1 - a2k2 * alpha,
-                                   (2.0f / 3.0f) * a2k2 * alpha * alpha);
-            sp[k][1] = make_float4(2 * kap * alpha * (1 - a2k2 * alpha), 0.8f * kap * a2k2 * alpha * alpha * alpha,
+            // Column coefficients of the real-space approach (s = (sx, sy) the column's
+            // offset, r2 = sx^2 + sy^2, k = alpha kappa):
+            //   c_q0 = a0 F_q + b0 (S s)_q + k (s x T)-term,  c_q1 = k T-term + b0 (S_xz, S_yz, S_zz)_q,
+            //   c_q2 = A1 F_q + B1 (S s)_q,  c_q3 = B1 (S_xz, S_yz, S_zz)_q,
+            // a0 = A0 + A1 r2, b0 = B0 + B1 r2 (the Faxen weights of the force and stresslet
+            // terms, which cancel near r2 = -A0/A1 and -B0/B1: formed per column as scalars
+            // before they multiply the moments).  Products of particle constants that do
+            // not cancel (k T, A1 F, B1 S) are formed here once.
+            const float A0 = 1 - a2k2 * alpha, A1 = (2.0f / 3.0f) * a2k2 * alpha * alpha;
+            const float B0 = 2 * kap * alpha * (1 - a2k2 * alpha), B1 = 0.8f * kap * a2k2 * alpha * alpha * alpha;
+            sp[k][0] = make_float4(s0g[3 * i] + (float)od[0], s0g[3 * i + 1] + (float)od[1],
                                    ok ? (float)quarters : 0.f, NCOMP >= 12 ? xi[11] : 0.f);
-            sp[k][2] = make_float4(xi[0], xi[1], xi[2], Tq[0]);
-            sp[k][3] = make_float4(Tq[1], Tq[2], S[0], S[1]);
+            sp[k][1] = make_float4(A0, A1, B0, B1);
+            sp[k][2] = make_float4(xi[0], xi[1], xi[2], akap * Tq[0]);
+            sp[k][3] = make_float4(akap * Tq[1], akap * Tq[2], S[0], S[1]);
             sp[k][4] = make_float4(S[2], S[3], S[4], S[5]);
+            sp[k][5] = make_float4(A1 * xi[0], A1 * xi[1], A1 * xi[2], B1 * S[4]);
+            sp[k][6] = make_float4(B1 * S[5], B1 * S[2], 0.f, 0.f);
         }
         sync();
         for (int k = 0; k < cnt; ++k) {
             const int sw_xy = (k >> 1) & 15, sw_z = k & 7;
             const float gxy = sxy[k][tx ^ sw_xy] * sxy[k][(TT + ty) ^ sw_xy];
-            const float4 v1 = sp[k][1];
-            const int quarters = (int)v1.z;
+            const float4 v0 = sp[k][0];
+            const int quarters = (int)v0.z;
             if (gxy == 0.f || quarters == 0) continue;
-            const float4 v0 = sp[k][0], v2 = sp[k][2];
             const float sx = v0.x + tx, sy = v0.y + ty;
-            const float sxy2 = sx * sx + sy * sy;
-            const float A1 = v0.w, a0 = v0.z + A1 * sxy2;
-            float c[3][4];
+            const float r2 = sx * sx + sy * sy;
+            const float4 v1 = sp[k][1], v2 = sp[k][2], v5 = sp[k][5];
+            const float a0 = v1.x + v1.y * r2;
             const float F[3] = {v2.x, v2.y, v2.z};
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                c[q][0] = a0 * F[q];
-                c[q][1] = 0;
-                c[q][2] = A1 * F[q];
-                c[q][3] = 0;
-            }
+            float c[3][4];
             if constexpr (NCOMP >= 6) {
                 const float4 v3 = sp[k][3];
-                const float T0 = v2.w, T1 = v3.x, T2 = v3.y;
-                c[0][0] -= akap * sy * T2;
-                c[1][0] += akap * sx * T2;
-                c[2][0] -= akap * (sx * T1 - sy * T0);
-                c[0][1] += akap * T1;
-                c[1][1] -= akap * T0;
+                const float kT0 = v2.w, kT1 = v3.x, kT2 = v3.y;
+                // k (s x T)-terms of the velocity coefficients and k T-terms of the first moments
+                const float t[3] = {-kT2 * sy, kT2 * sx, kT0 * sy - kT1 * sx};
+                const float nk[3] = {kT1, -kT0, 0.f};
                 if constexpr (NCOMP >= 11) {
-                    const float4 v4 = sp[k][4];
-                    const float S[6] = {v3.z, v3.w, v4.x, v4.y, v4.z, v4.w};
-                    const float B1 = v1.y, b0 = v1.x + B1 * sxy2;
-                    const float d00 = S[0] * sx + S[3] * sy, d01 = S[3] * sx + S[1] * sy, d02 = S[4] * sx + S[5] * sy;
-                    const float d10 = S[4], d11 = S[5], d12 = S[2];
-                    c[0][0] += b0 * d00; c[1][0] += b0 * d01; c[2][0] += b0 * d02;
-                    c[0][1] += b0 * d10; c[1][1] += b0 * d11; c[2][1] += b0 * d12;
-                    c[0][2] += B1 * d00; c[1][2] += B1 * d01; c[2][2] += B1 * d02;
-                    c[0][3] = B1 * d10; c[1][3] = B1 * d11; c[2][3] = B1 * d12;
+                    const float4 v4 = sp[k][4], v6 = sp[k][6];
+                    const float b0 = v1.z + v1.w * r2;
+                    const float S0 = v3.z, S1 = v3.w, S2 = v4.x, S3 = v4.y, S4 = v4.z, S5 = v4.w;
+                    const float d[3] = {S0 * sx + S3 * sy, S3 * sx + S1 * sy, S4 * sx + S5 * sy};
+                    const float Sp[3] = {S4, S5, S2}, B1Sp[3] = {v5.w, v6.x, v6.y};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        c[q][0] = a0 * F[q] + (b0 * d[q] + t[q]);
+                        c[q][1] = nk[q] + b0 * Sp[q];
+                        c[q][3] = B1Sp[q];
+                    }
+                    c[0][2] = v5.x + v1.w * d[0];
+                    c[1][2] = v5.y + v1.w * d[1];
+                    c[2][2] = v5.z + v1.w * d[2];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        c[q][0] = a0 * F[q] + t[q];
+                        c[q][1] = nk[q];
+                        c[q][3] = 0;
+                    }
+                    c[0][2] = v5.x;
+                    c[1][2] = v5.y;
+                    c[2][2] = v5.z;
                 }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    c[q][0] = a0 * F[q];
+                    c[q][1] = 0;
+                    c[q][3] = 0;
+                }
+                c[0][2] = v5.x;
+                c[1][2] = v5.y;
+                c[2][2] = v5.z;
             }
             constexpr int NE = NCOMP >= 11 ? 4 : (NCOMP >= 6 ? 3 : 2);
             constexpr int ES[4] = {0, 2, 1, 3};       // the terms present: 0, 2 (F); 1 (T); 3 (S)
@@ -607,7 +634,7 @@ __device__ __forceinline__ void spread16_body(int tile, int part, int tid, Sync 
                     const float v = c[q][e] * gxy;
                     cc[q][e] = pack2(v, v);
                 }
-            const float csv = NCOMP >= 12 ? gxy * v1.w : 0.f;
+            const float csv = NCOMP >= 12 ? gxy * v0.w : 0.f;
             const u64 cs = pack2(csv, csv);
             auto quarter = [&](auto q0c) {
                 constexpr int zq = decltype(q0c)::value;
@@ -1100,7 +1127,7 @@ __device__ __forceinline__ void combine_write(const SeParams &p, const T (&acc)[
 // U(3), s x v (3), sym(s (x) w) (6: xx yy zz, xy xz yz doubled), p (1) once per column.
 // Column contributions are Kahan-compensated across the P^2 / 32 columns of a lane.
 // The work of warp w_ (particle order[w_]); Wz and Zi: the warp's 32-entry tables.
-template <typename T, typename TO, int CO, int NCOMP>
+template <typename T, typename TO, int CO, int NCOMP, int NCL = 1>
 __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t *Wz, int *Zi, const SeParams &p,
                                             int N, const int *order, const int *base, const T *s0g, const T *wg,
                                             const double *rad, const T *selfc, const int *perm, const T *grid,
@@ -1138,9 +1165,10 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
         const T B1 = (T)0.8 * kap * a2k2 * alpha * alpha * alpha;
         const T c6 = a * a / 6, c10 = a * a / 10;
         const size_t zs = (size_t)M * M * CO;
-        // FP32 4-component grids: each lane takes two columns at a time, so that one read of
-        // a plane's W and offset (shared memory, the same for every lane) serves two points
-        constexpr int NCL = (std::is_same<T, float>::value && CO == 4) ? SE_GATHER_NCL : 1;
+        // NCL = 2 (FP32, 4-component grids, P^2 close to a multiple of 64): each lane takes two
+        // columns at a time, so that one read of a plane's W and offset (shared memory, the
+        // same for every lane) serves two points.  A lane's columns are summed in the order
+        // c = lane, lane + 32, ... either way.
         constexpr int kUnr = kGatherUnroll;
         for (int it = 0; it < P * P; it += 32 * NCL) {
             int cxa[NCL], cya[NCL];
@@ -1197,8 +1225,7 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
                 const int cx = cxa[j], cy = cya[j];
                 const T gxy = acta[j] ? wx[cx] * wy[cy] : (T)0;
                 // sheared cell: the physical direction of the window gradient (sx, sy - gamma sx, sz)
-                const T sx = sx0 + cx, sy = sy0 + cy - (CO == 8 ? (T)p.gamma * (sx0 + cx) : (T)0),
-                        sxy2 = sx * sx + sy * sy;
+                const T sx = sx0 + cx, sy = sy0 + cy - (CO == 8 ? (T)p.gamma * (sx0 + cx) : (T)0);
                 T col[NA];
                 if constexpr (CO == 8) {
                     // U = sum g (v + a^2/6 v''); Omega ~ sum g s x v; E ~ sum g sym(s (x) (v + a^2/10 v''))
@@ -1218,6 +1245,7 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
                     col[11] = gxy * (sy * Q2 + R1);
                 } else {
                     // z0 = sum g v, z1 = sum g s_z v, z2 = sum g s_z^2 v, z3 = sum g s_z^3 v
+                    const T sxy2 = sx * sx + sy * sy;
                     const T a0 = A0 + A1 * sxy2, b0 = B0 + B1 * sxy2;
                     col[0] = gxy * (a0 * z0[j][0] + A1 * z2[j][0]);
                     col[1] = gxy * (a0 * z0[j][1] + A1 * z2[j][1]);
@@ -1250,7 +1278,7 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
     combine_write<T, TO, CO>(p, acc, i, selfc, perm, xs, yreal, y, ncomp_out, with_self);
 }
 
-template <typename T, typename TO, int CO, int NCOMP>
+template <typename T, typename TO, int CO, int NCOMP, int NCL = 1>
 __global__ void __launch_bounds__(256, SE_GATHER_MINB) gather_kernel(SeParams p, int N, const int *order, const int *base,
                                                      const T *s0g, const T *wg, const double *rad, const T *selfc,
                                                      const int *perm, const T *grid, const T *xs, const T *yreal,
@@ -1261,7 +1289,7 @@ __global__ void __launch_bounds__(256, SE_GATHER_MINB) gather_kernel(SeParams p,
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     // particles in spreading-bin order (supports starting in the same 8^3 tile are
     // taken by neighbouring warps, so their grid reads share L1 lines)
-    gather_body<T, TO, CO, NCOMP>(blockIdx.x * (blockDim.x >> 5) + wl, lane, Wz[wl], Zi[wl], p, N, order, base, s0g,
+    gather_body<T, TO, CO, NCOMP, NCL>(blockIdx.x * (blockDim.x >> 5) + wl, lane, Wz[wl], Zi[wl], p, N, order, base, s0g,
                                   wg, rad, selfc, perm, grid, xs, yreal, y, ncomp_out, with_wave, with_self);
 }
 
@@ -1791,6 +1819,18 @@ void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int nc
         else if (ncomp <= 11) go(gather_kernel<T, TO, 8, 11>);
         else go(gather_kernel<T, TO, 8, 12>);
     } else {
+        // FP32: two support columns per lane where few column slots of the last 64-column
+        // chunk stay idle
+        if constexpr (std::is_same<T, float>::value && SE_GATHER_NCL == 2) {
+            if ((c->P * c->P) % 64 == 0 || (c->P * c->P) % 64 > 32) {
+                if (ncomp <= 3) go(gather_kernel<T, TO, 4, 3, 2>);
+                else if (ncomp <= 6) go(gather_kernel<T, TO, 4, 6, 2>);
+                else if (ncomp <= 11) go(gather_kernel<T, TO, 4, 11, 2>);
+                else go(gather_kernel<T, TO, 4, 12, 2>);
+                c->launches++;
+                return;
+            }
+        }
         if (ncomp <= 3) go(gather_kernel<T, TO, 4, 3>);
         else if (ncomp <= 6) go(gather_kernel<T, TO, 4, 6>);
         else if (ncomp <= 11) go(gather_kernel<T, TO, 4, 11>);
