@@ -146,7 +146,8 @@ int se_set_option(se_ctx *ctx, int key, double value);
 
 /* Particle configuration: N spheres, box side L; pos [N][3] and radius [N] are FP64
  * DEVICE arrays (positions anywhere, wrapped into the box).  Builds the cell list,
- * the spreading bins and (lazily) the preconditioner.  Fails with SE_ERR_CUTOFF when
+ * the spreading bins and (lazily) the preconditioner.  Fails with SE_ERR_ARG unless
+ * 1 <= N <= 2^28 (an empty configuration included) or for null pointers, SE_ERR_CUTOFF when
  * rc >= L/2 and SE_ERR_NONFINITE for non-finite or non-positive data.  The arrays are
  * copied; the caller may free them afterwards.  Synchronises the stream. */
 int se_set_config(se_ctx *ctx, int64_t N, double L, const double *pos, const double *radius);

@@ -76,6 +76,28 @@ __device__ __forceinline__ ff &operator*=(ff &a, ff b) { return a = a * b; }
 __device__ __forceinline__ bool operator==(ff a, ff b) { return a.hi == b.hi && a.lo == b.lo; }
 __device__ __forceinline__ bool operator!=(ff a, ff b) { return !(a == b); }
 
+// Multiply-add loops.  lazy_madd(acc, a, b) is acc += a b; on double-floats the product's
+// high part joins the accumulator's high part by an exact TwoSum and every error term (the
+// TwoSum's, the product's rounding and its cross terms) collects in the low part, which is
+// left unnormalised until lazy_finish(acc): about a dozen FP32 instructions per term
+// instead of the two normalisations of a separate multiply and add.  A loop of n terms
+// leaves |lo| up to about n ulp(hi), so it is finished after tens of terms, not thousands.
+template <typename T>
+__device__ __forceinline__ void lazy_madd(T &acc, T a, T b) { acc += a * b; }
+__device__ __forceinline__ void lazy_madd(ff &acc, ff a, ff b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    float s, err;
+    two_sum(acc.hi, p, s, err);
+    acc.hi = s;
+    acc.lo += err + e;
+}
+template <typename T>
+__device__ __forceinline__ void lazy_finish(T &) {}
+__device__ __forceinline__ void lazy_finish(ff &acc) { acc = ff_norm(acc.hi, acc.lo); }
+
 // warp exchange of any arithmetic type or of a double-float
 template <typename T>
 __device__ __forceinline__ T shfl_xor(unsigned mask, T v, int off) { return __shfl_xor_sync(mask, v, off); }

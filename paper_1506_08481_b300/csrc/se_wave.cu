@@ -357,7 +357,14 @@ __device__ __forceinline__ void spread_body(int tile, int part, int tid, Sync sy
                     const T4 W = swz[k][z ^ sw_z];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
-                        if constexpr (NCOMP >= 11)
+                        if constexpr (std::is_same<T, ff>::value) {
+                            // double-floats: the column's terms into the plane's sum with one normalisation
+                            lazy_madd(acc[z][q], c[q][0], W.x);
+                            if constexpr (NCOMP >= 6) lazy_madd(acc[z][q], c[q][1], W.y);
+                            lazy_madd(acc[z][q], c[q][2], W.z);
+                            if constexpr (NCOMP >= 11) lazy_madd(acc[z][q], c[q][3], W.w);
+                            lazy_finish(acc[z][q]);
+                        } else if constexpr (NCOMP >= 11)
                             acc[z][q] += c[q][0] * W.x + c[q][1] * W.y + c[q][2] * W.z + c[q][3] * W.w;
                         else if constexpr (NCOMP >= 6)
                             acc[z][q] += c[q][0] * W.x + c[q][1] * W.y + c[q][2] * W.z;
@@ -1201,23 +1208,35 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
                             const T4 u1 = *reinterpret_cast<const T4 *>(gpa[j] + off + 4);
                             // u0 = (v0 v1 v2 v''0), u1 = (v''1 v''2 p -): z0 = sum g v, z1 = sum g v'',
                             // z2 = sum g s_z v, z3 = sum g s_z v''
-                            z0[j][0] += w.x * u0.x; z0[j][1] += w.x * u0.y; z0[j][2] += w.x * u0.z;
-                            z1[j][0] += w.x * u0.w; z1[j][1] += w.x * u1.x; z1[j][2] += w.x * u1.y;
+                            lazy_madd(z0[j][0], w.x, u0.x); lazy_madd(z0[j][1], w.x, u0.y); lazy_madd(z0[j][2], w.x, u0.z);
+                            lazy_madd(z1[j][0], w.x, u0.w); lazy_madd(z1[j][1], w.x, u1.x); lazy_madd(z1[j][2], w.x, u1.y);
                             if constexpr (NCOMP >= 6) {
-                                z2[j][0] += w.y * u0.x; z2[j][1] += w.y * u0.y; z2[j][2] += w.y * u0.z;
-                                if constexpr (NCOMP >= 11) { z3[j][0] += w.y * u0.w; z3[j][1] += w.y * u1.x; z3[j][2] += w.y * u1.y; }
+                                lazy_madd(z2[j][0], w.y, u0.x); lazy_madd(z2[j][1], w.y, u0.y); lazy_madd(z2[j][2], w.y, u0.z);
+                                if constexpr (NCOMP >= 11) { lazy_madd(z3[j][0], w.y, u0.w); lazy_madd(z3[j][1], w.y, u1.x); lazy_madd(z3[j][2], w.y, u1.y); }
                             }
-                            if constexpr (NCOMP >= 12) zp[j] += w.x * u1.z;
+                            if constexpr (NCOMP >= 12) lazy_madd(zp[j], w.x, u1.z);
                         } else {
-                            z0[j][0] += w.x * u0.x; z0[j][1] += w.x * u0.y; z0[j][2] += w.x * u0.z;
-                            z2[j][0] += w.z * u0.x; z2[j][1] += w.z * u0.y; z2[j][2] += w.z * u0.z;
+                            lazy_madd(z0[j][0], w.x, u0.x); lazy_madd(z0[j][1], w.x, u0.y); lazy_madd(z0[j][2], w.x, u0.z);
+                            lazy_madd(z2[j][0], w.z, u0.x); lazy_madd(z2[j][1], w.z, u0.y); lazy_madd(z2[j][2], w.z, u0.z);
                             if constexpr (NCOMP >= 6) {
-                                z1[j][0] += w.y * u0.x; z1[j][1] += w.y * u0.y; z1[j][2] += w.y * u0.z;
-                                if constexpr (NCOMP >= 11) { z3[j][0] += w.w * u0.x; z3[j][1] += w.w * u0.y; z3[j][2] += w.w * u0.z; }
+                                lazy_madd(z1[j][0], w.y, u0.x); lazy_madd(z1[j][1], w.y, u0.y); lazy_madd(z1[j][2], w.y, u0.z);
+                                if constexpr (NCOMP >= 11) { lazy_madd(z3[j][0], w.w, u0.x); lazy_madd(z3[j][1], w.w, u0.y); lazy_madd(z3[j][2], w.w, u0.z); }
                             }
-                            if constexpr (NCOMP >= 12) zp[j] += w.x * u0.w;
+                            if constexpr (NCOMP >= 12) lazy_madd(zp[j], w.x, u0.w);
                         }
                     }
+                }
+                // double-floats: normalise the column sums once, after the z-loop
+#pragma unroll
+                for (int j = 0; j < NCL; ++j) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        lazy_finish(z0[j][q]);
+                        lazy_finish(z1[j][q]);
+                        lazy_finish(z2[j][q]);
+                        lazy_finish(z3[j][q]);
+                    }
+                    lazy_finish(zp[j]);
                 }
             }
 #pragma unroll

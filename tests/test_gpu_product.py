@@ -168,6 +168,9 @@ def test_error_codes():
     assert _raw_apply(ctx, 3, z, z.clone(), api.SE_F64) == api.SE_ERR_STATE   # before params/config
     ctx.set_params(1.0, 32, 12, 4.0)
     with pytest.raises(api.SeError) as e:
+        ctx.set_config(np.zeros((0, 3)), np.ones(0), 10.0)                    # empty configuration
+    assert e.value.code == api.SE_ERR_ARG
+    with pytest.raises(api.SeError) as e:
         ctx.set_config(np.zeros((2, 3)), np.ones(2), 7.9)                     # rc >= L/2
     assert e.value.code == api.SE_ERR_CUTOFF
     pos = np.array([[1.0, 1.0, 1.0], [np.nan, 2.0, 2.0]])
