@@ -572,8 +572,9 @@ static int apply_t(se_ctx *c, int ncomp, const TO *x, TO *y)
     return SE_OK;
 }
 
-// FP64-equivalent product (precision 2): the real-space sum, the FFT and the k-space
-// scaling in FP64, the spread and gather (the FP64-pipe-bound stages) in double-float
+// FP64-equivalent product (precision 2): the FFT and the k-space scaling in FP64, the
+// real-space sum (from the FP64 pair table), the spread and the gather (the stages bound
+// by B300's FP64 pipe) in double-float
 template <typename TO>
 static int apply_ff(se_ctx *c, int ncomp, const TO *x, TO *y)
 {
@@ -587,9 +588,11 @@ static int apply_ff(se_ctx *c, int ncomp, const TO *x, TO *y)
     launch_cvt<double, ff>(c, N * kNC, xs1, xs2, s);
     stage_mark(c, SE_STAGE_PERMUTE, s, true);
     stage_mark(c, SE_STAGE_REAL, s, false);
-    if (c->parts & 1) launch_real<double>(c, xs1, yr1, s, ncomp);
-    else SE_CUDA_CHECK(c, cudaMemsetAsync(yr1, 0, N * kNC * sizeof(double), s));
-    launch_cvt<double, ff>(c, N * kNC, yr1, yr2, s);
+    if (!(c->parts & 1) || !launch_real_ff(c, xs2, yr2, s, ncomp)) {
+        if (c->parts & 1) launch_real<double>(c, xs1, yr1, s, ncomp);
+        else SE_CUDA_CHECK(c, cudaMemsetAsync(yr1, 0, N * kNC * sizeof(double), s));
+        launch_cvt<double, ff>(c, N * kNC, yr1, yr2, s);
+    }
     stage_mark(c, SE_STAGE_REAL, s, true);
     const size_t M3 = (size_t)c->M * c->M * c->M;
     if (with_wave) {

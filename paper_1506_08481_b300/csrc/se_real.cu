@@ -501,12 +501,12 @@ __global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double 
 }
 
 // One warp per target (real_table_body).
-template <typename T, int NCOMP>
+template <typename T, int NCOMP, typename TL = T>
 __global__ void __launch_bounds__(256) real_table_kernel(int N, const int *off, size_t np, const int *pj,
-                                                         const T *px, const T *pc, const T *xs, T *yreal)
+                                                         const TL *px, const TL *pc, const T *xs, T *yreal)
 {
-    real_table_body<T, NCOMP>(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), threadIdx.x & 31, N, off, np, pj,
-                              px, pc, xs, yreal);
+    real_table_body<T, NCOMP, TL>(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), threadIdx.x & 31, N, off, np,
+                                  pj, px, pc, xs, yreal);
 }
 
 }  // namespace
@@ -642,6 +642,27 @@ void launch_real(se_ctx *c, const T *xs, T *yreal, cudaStream_t s, int ncomp)
     else if (ncomp <= 11) go(real_kernel<T, 11>);
     else go(real_kernel<T, 12>);
     c->launches++;
+}
+
+// The FP64-equivalent product's real-space sum: the FP64 pair table contracted in
+// double-float arithmetic (B300's FP32 pipe issues many times the FMAs of its FP64 pipe).
+// Returns false, launching nothing, when there is no FP64 table (the caller then runs the
+// FP64 cell-list kernel).
+bool launch_real_ff(se_ctx *c, const ff *xs, ff *yreal, cudaStream_t s, int ncomp)
+{
+    if (!c->pairs_ok[1]) return false;
+    const int N = (int)c->N, wpb = 8;
+    auto go = [&](auto kern) {
+        kern<<<(N + wpb - 1) / wpb, wpb * 32, 0, s>>>(N, c->b.pair_off, c->npairs, c->b.pair_j,
+                                                      (const double *)c->b.pair_x[1], (const double *)c->b.pair_c[1],
+                                                      xs, yreal);
+    };
+    if (ncomp <= 3) go(real_table_kernel<ff, 3, double>);
+    else if (ncomp <= 6) go(real_table_kernel<ff, 6, double>);
+    else if (ncomp <= 11) go(real_table_kernel<ff, 11, double>);
+    else go(real_table_kernel<ff, 12, double>);
+    c->launches++;
+    return true;
 }
 
 template void setup_rel<float>(se_ctx *, cudaStream_t);

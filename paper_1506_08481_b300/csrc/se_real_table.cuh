@@ -9,10 +9,11 @@
 
 namespace se {
 
-// target i, lane 0..31 of its warp
-template <typename T, int NCOMP>
+// target i, lane 0..31 of its warp; the table is stored at precision TL and read into T
+// (the FP64-equivalent product contracts the FP64 table in double-float arithmetic)
+template <typename T, int NCOMP, typename TL = T>
 __device__ __forceinline__ void real_table_body(int i, int lane, int N, const int *off, size_t np, const int *pj,
-                                                const T *px, const T *pc, const T *xs, T *yreal)
+                                                const TL *px, const TL *pc, const T *xs, T *yreal)
 {
     if (i >= N) return;
     T a[13];
@@ -21,12 +22,12 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
     const int k1 = off[i + 1];
     for (int k = off[i] + lane; k < k1; k += 32) {
         const int j = pj[k];
-        const T x0 = px[k], x1 = px[np + k], x2 = px[2 * np + k];
+        const T x0 = T(px[k]), x1 = T(px[np + k]), x2 = T(px[2 * np + k]);
         const T *xj = xs + (size_t)j * kNC;
         const T F0 = xj[0], F1 = xj[1], F2 = xj[2];
         const T xF = x0 * F0 + x1 * F1 + x2 * F2;
         {
-            const T aF = pc[k], bF = pc[np + k] * xF;
+            const T aF = T(pc[k]), bF = T(pc[np + k]) * xF;
             a[0] += aF * F0 - bF * x0;
             a[1] += aF * F1 - bF * x1;
             a[2] += aF * F2 - bF * x2;
@@ -34,14 +35,14 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
         if constexpr (NCOMP >= 6) {
             const T T0 = xj[3], T1 = xj[4], T2 = xj[5];
             const T xT0 = x1 * T2 - x2 * T1, xT1 = x2 * T0 - x0 * T2, xT2 = x0 * T1 - x1 * T0;
-            const T uT = pc[2 * np + k], oF = pc[3 * np + k];
+            const T uT = T(pc[2 * np + k]), oF = T(pc[3 * np + k]);
             a[0] += uT * xT0;
             a[1] += uT * xT1;
             a[2] += uT * xT2;
             a[3] += oF * (x1 * F2 - x2 * F1);
             a[4] += oF * (x2 * F0 - x0 * F2);
             a[5] += oF * (x0 * F1 - x1 * F0);
-            const T oTa = pc[4 * np + k] * (x0 * T0 + x1 * T1 + x2 * T2), oTb = pc[5 * np + k];
+            const T oTa = T(pc[4 * np + k]) * (x0 * T0 + x1 * T1 + x2 * T2), oTb = T(pc[5 * np + k]);
             a[3] += oTa * x0 - oTb * T0;
             a[4] += oTa * x1 - oTb * T1;
             a[5] += oTa * x2 - oTb * T2;
@@ -53,20 +54,20 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
                         Sx2 = Sxz * x0 + Syz * x1 + Szz * x2;
                 const T xSx = x0 * Sx0 + x1 * Sx1 + x2 * Sx2;
                 {   // U <- S
-                    const T ua = pc[6 * np + k], ub = pc[7 * np + k] * xSx;
+                    const T ua = T(pc[6 * np + k]), ub = T(pc[7 * np + k]) * xSx;
                     a[0] += ua * Sx0 + ub * x0;
                     a[1] += ua * Sx1 + ub * x1;
                     a[2] += ua * Sx2 + ub * x2;
                 }
                 {   // Om <- S
-                    const T o = pc[8 * np + k];
+                    const T o = T(pc[8 * np + k]);
                     a[3] += o * (x1 * Sx2 - x2 * Sx1);
                     a[4] += o * (x2 * Sx0 - x0 * Sx2);
                     a[5] += o * (x0 * Sx1 - x1 * Sx0);
                 }
                 // E (symmetric tensor xx yy zz xy xz yz) <- F, T, S
-                const T ea = pc[9 * np + k], eb = pc[10 * np + k] * xF, et = pc[11 * np + k];
-                const T sa = pc[12 * np + k], sb = pc[13 * np + k], sc = pc[14 * np + k] * xSx;
+                const T ea = T(pc[9 * np + k]), eb = T(pc[10 * np + k]) * xF, et = T(pc[11 * np + k]);
+                const T sa = T(pc[12 * np + k]), sb = T(pc[13 * np + k]), sc = T(pc[14 * np + k]) * xSx;
                 a[6] += ea * x0 * F0 + eb * x0 * x0 + et * x0 * xT0 + sa * Sxx + sb * x0 * Sx0 + sc * x0 * x0;
                 a[7] += ea * x1 * F1 + eb * x1 * x1 + et * x1 * xT1 + sa * Syy + sb * x1 * Sx1 + sc * x1 * x1;
                 a[8] += ea * x2 * F2 + eb * x2 * x2 + et * x2 * xT2 + sa * Szz + sb * x2 * Sx2 + sc * x2 * x2;
@@ -78,7 +79,7 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
                          eb * x1 * x2 + sa * Syz + sc * x1 * x2;
                 if constexpr (NCOMP >= 12) {
                     const T Str = xj[11];
-                    const T uq = pc[15 * np + k] * Str, eq = pc[16 * np + k] * Str;
+                    const T uq = T(pc[15 * np + k]) * Str, eq = T(pc[16 * np + k]) * Str;
                     a[0] += uq * x0;
                     a[1] += uq * x1;
                     a[2] += uq * x2;
@@ -88,14 +89,14 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
                     a[9] += eq * x0 * x1;
                     a[10] += eq * x0 * x2;
                     a[11] += eq * x1 * x2;
-                    a[12] += pc[17 * np + k] * xF + pc[18 * np + k] * xSx;
+                    a[12] += T(pc[17 * np + k]) * xF + T(pc[18 * np + k]) * xSx;
                 }
             }
         }
     }
 #pragma unroll
     for (int c = 0; c < 13; ++c)
-        for (int o = 16; o > 0; o >>= 1) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+        for (int o = 16; o > 0; o >>= 1) a[c] += shfl_xor(0xffffffffu, a[c], o);
     if (lane == 0) {
         T *yo = yreal + (size_t)i * kNC;
         yo[0] = a[0];
