@@ -228,7 +228,7 @@ static int ensure_grids(se_ctx *c, int prec)
 
 static int ensure_support(se_ctx *c, int prec);
 
-// double-float support: the FP64 tables (and the FP64 pair table of the real-space sum)
+// double-float support: the FP64 tables and the FP64 pair table of the real-space sum
 // converted once per configuration
 static int ensure_support_ff(se_ctx *c)
 {
@@ -249,7 +249,7 @@ static int ensure_support_ff(se_ctx *c)
         SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
         c->support_ok[2] = true;
     }
-    return SE_OK;
+    return build_pair_table_ff(c);
 }
 
 // support tables and work vectors at precision prec

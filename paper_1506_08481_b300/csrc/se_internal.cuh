@@ -175,6 +175,7 @@ void setup_rel(se_ctx *c, cudaStream_t s);
 template <typename T>
 int build_pair_table(se_ctx *c);
 bool launch_real_ff(se_ctx *c, const ff *xs, ff *yreal, cudaStream_t s, int ncomp);
+int build_pair_table_ff(se_ctx *c);
 // se_learned.cu: per-particle learned corrections [N][4] (caller order)
 int learned_corrections(se_ctx *c, double *d_dev);
 // se_solve.cu

@@ -644,23 +644,57 @@ void launch_real(se_ctx *c, const T *xs, T *yreal, cudaStream_t s, int ncomp)
     c->launches++;
 }
 
-// The FP64-equivalent product's real-space sum: the FP64 pair table contracted in
-// double-float arithmetic (B300's FP32 pipe issues many times the FMAs of its FP64 pipe).
-// Returns false, launching nothing, when there is no FP64 table (the caller then runs the
-// FP64 cell-list kernel).
+namespace {
+__global__ void d2ff_kernel(size_t n, const double *in, ff *out)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        out[k] = ff(in[k]);
+}
+}  // namespace
+
+// The FP64 pair table as double-floats (once per configuration, beside the FP64 one), so
+// that the double-float real-space sum reads no FP64 values.  Without memory for it the
+// sum converts the FP64 table as it reads it.
+int build_pair_table_ff(se_ctx *c)
+{
+    if (!c->pairs_ok[1] || c->pairs_ok[2]) return SE_OK;
+    const size_t np = c->npairs, nx = 3 * np + 1, nc = (size_t)kNPC * np + 1;
+    if (cudaMalloc(&c->b.pair_x[2], nx * sizeof(ff)) != cudaSuccess ||
+        cudaMalloc(&c->b.pair_c[2], nc * sizeof(ff)) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->b.pair_x[2]) cudaFree(c->b.pair_x[2]);
+        c->b.pair_x[2] = nullptr;
+        return SE_OK;
+    }
+    cudaStream_t s = c->stream;
+    d2ff_kernel<<<4 * kSMs, 256, 0, s>>>(nx, (const double *)c->b.pair_x[1], (ff *)c->b.pair_x[2]);
+    d2ff_kernel<<<4 * kSMs, 256, 0, s>>>(nc, (const double *)c->b.pair_c[1], (ff *)c->b.pair_c[2]);
+    c->launches += 2;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SE_ERR_CUDA;
+    c->pairs_ok[2] = true;
+    return SE_OK;
+}
+
+// The FP64-equivalent product's real-space sum: the pair table contracted in double-float
+// arithmetic (B300's FP32 pipe issues many times the FMAs of its FP64 pipe), from the
+// double-float table, else from the FP64 one.  Returns false, launching nothing, when
+// there is neither (the caller then runs the FP64 cell-list kernel).
 bool launch_real_ff(se_ctx *c, const ff *xs, ff *yreal, cudaStream_t s, int ncomp)
 {
-    if (!c->pairs_ok[1]) return false;
+    if (!c->pairs_ok[1] && !c->pairs_ok[2]) return false;
     const int N = (int)c->N, wpb = 8;
-    auto go = [&](auto kern) {
-        kern<<<(N + wpb - 1) / wpb, wpb * 32, 0, s>>>(N, c->b.pair_off, c->npairs, c->b.pair_j,
-                                                      (const double *)c->b.pair_x[1], (const double *)c->b.pair_c[1],
-                                                      xs, yreal);
+    auto go = [&](auto kern, const auto *px, const auto *pc) {
+        kern<<<(N + wpb - 1) / wpb, wpb * 32, 0, s>>>(N, c->b.pair_off, c->npairs, c->b.pair_j, px, pc, xs, yreal);
     };
-    if (ncomp <= 3) go(real_table_kernel<ff, 3, double>);
-    else if (ncomp <= 6) go(real_table_kernel<ff, 6, double>);
-    else if (ncomp <= 11) go(real_table_kernel<ff, 11, double>);
-    else go(real_table_kernel<ff, 12, double>);
+    auto pick = [&](const auto *px, const auto *pc) {
+        using TL = std::remove_cv_t<std::remove_pointer_t<decltype(px)>>;
+        if (ncomp <= 3) go(real_table_kernel<ff, 3, TL>, px, pc);
+        else if (ncomp <= 6) go(real_table_kernel<ff, 6, TL>, px, pc);
+        else if (ncomp <= 11) go(real_table_kernel<ff, 11, TL>, px, pc);
+        else go(real_table_kernel<ff, 12, TL>, px, pc);
+    };
+    if (c->pairs_ok[2]) pick((const ff *)c->b.pair_x[2], (const ff *)c->b.pair_c[2]);
+    else pick((const double *)c->b.pair_x[1], (const double *)c->b.pair_c[1]);
     c->launches++;
     return true;
 }
