@@ -66,9 +66,10 @@ typedef struct se_ctx se_ctx;
 
 /* options for se_set_option */
 #define SE_OPT_PRECISION   1   /* compute precision of products: 0 = FP32 (default), 1 = FP64, 2 = FP64-
-                                  equivalent: spread and gather in double-float arithmetic (pairs of
-                                  FP32 numbers, ~2^-44 relative), the rest in FP64; same accuracy as 1
-                                  at a fraction of its time on B300's FP64 rate */
+                                  equivalent: real-space sum, spread and gather in double-float
+                                  arithmetic (pairs of FP32 numbers, ~2^-44 relative), the FFT and
+                                  k-space scaling in FP64; same accuracy as 1 at a fraction of its
+                                  time on B300's FP64 rate */
 #define SE_OPT_SIZE_MODE   2   /* particle-size terms: 0 = hybrid (default), 1 = real-space approach */
 #define SE_OPT_ETA         3   /* solvent viscosity (default 1) */
 #define SE_OPT_SHAPE_M     4   /* Gaussian shape parameter m of Eq. theta-param (default sqrt(pi P)) */

@@ -124,9 +124,16 @@ def test_ncomp_prefixes_agree(small_poly):
 
 
 def test_host_buffer_entry_point(small_poly):
+    """se_mobility_apply_host with pageable and with page-locked host buffers, for all 12
+    components and a 3-component prefix."""
     cfg, x = small_poly
     ctx = make_ctx(0.9, 48, 16, 5.4, cfg, precision=1)
     np.testing.assert_allclose(ctx.apply_host(x), gpu_apply(ctx, x), rtol=0, atol=1e-15)
+    for nc in (12, 3):
+        xp = torch.from_numpy(x[:, :nc].copy()).pin_memory()
+        yp = torch.full_like(xp, float("nan")).pin_memory()
+        out = ctx.apply_host(xp.numpy(), yp.numpy())
+        np.testing.assert_allclose(out, gpu_apply(ctx, x[:, :nc].copy()), rtol=0, atol=1e-15)
 
 
 @pytest.mark.parametrize("N,M", [(1, 24), (33, 72), (65, 40)])
