@@ -1297,14 +1297,17 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
     combine_write<T, TO, CO>(p, acc, i, selfc, perm, xs, yreal, y, ncomp_out, with_self);
 }
 
+#ifndef SE_GATHER_WPB
+#define SE_GATHER_WPB 8
+#endif
 template <typename T, typename TO, int CO, int NCOMP, int NCL = 1>
-__global__ void __launch_bounds__(256, SE_GATHER_MINB) gather_kernel(SeParams p, int N, const int *order, const int *base,
+__global__ void __launch_bounds__(32 * SE_GATHER_WPB, SE_GATHER_MINB) gather_kernel(SeParams p, int N, const int *order, const int *base,
                                                      const T *s0g, const T *wg, const double *rad, const T *selfc,
                                                      const int *perm, const T *grid, const T *xs, const T *yreal,
                                                      TO *y, int ncomp_out, int with_wave, int with_self)
 {
-    __shared__ typename V4<T>::t Wz[8][32];
-    __shared__ int Zi[8][32];
+    __shared__ typename V4<T>::t Wz[SE_GATHER_WPB][32];
+    __shared__ int Zi[SE_GATHER_WPB][32];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     // particles in spreading-bin order (supports starting in the same 8^3 tile are
     // taken by neighbouring warps, so their grid reads share L1 lines)
@@ -1789,7 +1792,7 @@ void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int nc
 {
     const SeParams p = make_params(c);
     const int N = (int)c->N;
-    const int wpb = 8;
+    const int wpb = SE_GATHER_WPB;
     dim3 grid((N + wpb - 1) / wpb);
     const int with_self = (c->parts & 4) ? 1 : 0;
     auto go = [&](auto kern) {
