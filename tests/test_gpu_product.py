@@ -352,6 +352,24 @@ def test_double_float_mode(small_poly, small_poly_ref, size_mode, ncomp):
     assert rel(y32io, y64) <= 2e-7
 
 
+@pytest.mark.parametrize("ncomp", [3, 6, 11, 12])
+def test_double_float_real_space_part(oracle_mod, small_poly, ncomp):
+    """The real-space sum of SE_OPT_PRECISION 2 (the pair table contracted in double-float
+    arithmetic) alone: equal to the FP64 real-space sum to double-float rounding and, in the
+    U, Omega, E rows, to the oracle's real-space part (same xi, rc) to its FP64 parity bound,
+    for every prefix.  (E_tr splits the harmonic pressure Faxen term differently.)"""
+    cfg, x = small_poly
+    xx = x[:, :ncomp].copy()
+    y64 = gpu_apply(make_ctx(0.9, 48, 16, 5.4, cfg, precision=1, parts=1), xx)
+    yff = gpu_apply(make_ctx(0.9, 48, 16, 5.4, cfg, precision=2, parts=1), xx)
+    assert rel(yff, y64) <= 1e-12
+    x12 = np.zeros((cfg.N, 12))
+    x12[:, :ncomp] = xx
+    nr = min(ncomp, 11)
+    ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x12, xi=0.9, rc=5.4, kc=1.0, parts=1)[:, :nr]
+    assert rel(yff[:, :nr], ref) <= 1e-12
+
+
 def test_double_float_mode_large_grid(oracle_mod):
     """Bidisperse N = 2000 at the parameters the error model picks for 1e-10 (FP64): the
     double-float product equals the FP64 one to 1e-12 and meets 1e-9 against the oracle."""
