@@ -23,8 +23,9 @@
  *   the Spectral Ewald method (Sec. 3.1): Gaussian spreading Eq. grid-space with the
  *   shape function Eq. shape, theta from Eq. theta-param, fast Gaussian gridding
  *   Eq. fgg-exp, 3D FFT, k-space scaling Eq. wave-result, gather by the trapezoid rule
- *   Eq. parseval-sum; particle-size terms by the hybrid approach (Sec. 3.2, default)
- *   or the real-space approach Eq. non-ortho-shape; self terms Eq. uf-self.
+ *   Eq. parseval-sum; particle-size terms by the hybrid approach (Sec. 3.2, default),
+ *   the real-space approach (Eq. non-ortho-shape) or the wave-space approach; sheared
+ *   cells (Sec. 3.2, lattice a2 = (gamma L, L, 0)); self terms Eq. uf-self.
  *   se_solve: GMRES with the block-diagonal far-field preconditioner of Sec. 4.2.
  *
  * Conventions common to all entry points:
@@ -70,7 +71,10 @@ typedef struct se_ctx se_ctx;
                                   arithmetic (pairs of FP32 numbers, ~2^-44 relative), the FFT and
                                   k-space scaling in FP64; same accuracy as 1 at a fraction of its
                                   time on B300's FP64 rate */
-#define SE_OPT_SIZE_MODE   2   /* particle-size terms: 0 = hybrid (default), 1 = real-space approach */
+#define SE_OPT_SIZE_MODE   2   /* particle-size (Faxen) terms, Sec. 3.2: 0 = hybrid approach (default: target
+                                  Laplacians in k-space), 1 = real-space approach (all of them in the
+                                  spread/gather polynomial, Eq. non-ortho-shape), 2 = wave-space approach
+                                  (source and target Laplacians in k-space; required by SE_OPT_SHEAR) */
 #define SE_OPT_ETA         3   /* solvent viscosity (default 1) */
 #define SE_OPT_SHAPE_M     4   /* Gaussian shape parameter m of Eq. theta-param (default sqrt(pi P)) */
 #define SE_OPT_RESTART     5   /* GMRES restart length, 1..1000 (default 30; the basis takes (restart + 1) N ncomp doubles) */
@@ -101,6 +105,11 @@ typedef struct se_ctx se_ctx;
                                   later change of the size mode); se_set_config must follow; the spectral
                                   preconditioner falls back to the block one; positions may be given
                                   in any periodic image */
+#define SE_OPT_FF_TABLE   16   /* FP64-equivalent mode (SE_OPT_PRECISION 2): 1 (default) keeps a double-float
+                                  copy of the FP64 real-space pair table per configuration (about 176 bytes
+                                  per stored pair: 7 GB at N = 2e5, rc = 7.5, phi = 0.45), so the
+                                  double-float real-space sum reads no FP64 values; 0 drops it and the sum
+                                  converts the FP64 table as it reads it (same result, less memory, more time) */
 #define SE_OPT_OVERLAP_CHECK 13  /* 1 (default): se_set_config fails with SE_ERR_OVERLAP if two spheres within
                                   the real-space cutoff overlap (touching is allowed; the far-field
                                   interactions of overlapping spheres are not those of the paper, and
@@ -188,7 +197,10 @@ int se_solve(se_ctx *ctx, int ncomp, const void *b, void *x, int dtype, double r
  *   x, y           : FP64 DEVICE arrays [N][ncomp], ncomp in {3, 6, 11, 12}; y is overwritten
  * Returns SE_ERR_TOO_LARGE if N > SE_NOALLOC_MAX_N, SE_ERR_CUTOFF if rc >= L/2,
  * SE_ERR_ARG for null pointers or bad sizes, SE_ERR_NONFINITE for non-finite positions
- * or non-positive radii, SE_ERR_CUDA for a failed CUDA call; synchronises the stream.
+ * or non-positive radii, SE_ERR_CUDA for a failed CUDA call of this call (a launch error
+ * left pending by earlier, unrelated work is cleared on entry, not reported).  Every call
+ * waits for `stream` (it reads a status flag back) and leaves the calling thread's
+ * current device as it found it.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the one array and
  * every call clears what must start at zero; calls that overlap on the GPU race on it,
@@ -270,6 +282,9 @@ int se_mlp_grad(const float *w, const float *X, const float *Yt, int n, float *g
 int se_mlp_adam_step(float *w, float *m, float *v, const float *grad, int step, float lr, void *stream);
 
 /* Batches of independent boxes (uneven N, each with its own context and parameters).
+ * This replaces a single batched call over ragged arrays with per-box offsets
+ * (se_mobility_apply_batched(ctx, nbox, offsets, ...)): each box keeps its own context
+ * (its own xi, M, P, rc and configuration), and a batch groups existing contexts.
  * se_batch_create borrows nbox configured contexts (they must outlive the batch) and
  * runs box i on the i-th (mod nstreams) of nstreams streams it creates, forked from
  * and joined back to `stream`.
@@ -280,13 +295,14 @@ int se_mlp_adam_step(float *w, float *m, float *v, const float *grad, int step, 
  *      once eagerly, captures it into one CUDA graph and launches it; later calls only
  *      launch the graph;
  *   2  ONE persistent cooperative launch computes every box (FP32 boxes with their
- *      stored pair tables): eight phases (inputs, real space + spreading, five FFT
- *      passes with the k-space scaling, gather), each a list of work items over all
- *      boxes claimed by the CTAs through a counter, separated by grid barriers.  The
+ *      stored pair tables): per box eight phases in order (inputs, real space +
+ *      spreading, five FFT passes with the k-space scaling, gather), each a list of
+ *      work items; a CTA claims an item of any box whose earlier phases have finished
+ *      (per-box counters, no grid-wide barrier), so the boxes' phases overlap.  The
  *      first call runs the batch eagerly and prepares the launch (captured into a graph
- *      when the runtime allows); later calls make the one launch.  A CTA that waits
- *      more than about two seconds at a barrier aborts the launch; se_batch_status
- *      reports it.
+ *      when the runtime allows); later calls make the one launch.  A CTA that finds no
+ *      ready item for longer than the wait limit (default 2 s) aborts the launch, and
+ *      every CTA returns; se_batch_status reports it.
  * Asynchronous on `stream`; errors as for se_mobility_apply (SE_ERR_STATE when a box
  * does not meet mode 2's conditions), described by se_batch_last_error.
  * se_batch_status synchronises `stream` and returns SE_ERR_CUDA if a persistent launch
@@ -297,6 +313,28 @@ int se_batch_apply(se_batch *b, int ncomp, const void *const *x, void *const *y,
 int se_batch_destroy(se_batch *b);
 int se_batch_status(se_batch *b);
 const char *se_batch_last_error(const se_batch *b);
+
+/* se_batch_set_wait_limit: the time limit (seconds, in (0, 600]) of every wait of a
+ * persistent launch (mode 2) for work of an earlier phase; the next mode-2 call prepares
+ * the launch again.  se_batch_inject_stall: failure-injection hook for tests of that
+ * bounded wait; box >= 0 makes that box's real-space/spreading phase never count as
+ * finished, so the CTAs waiting for it give up after the wait limit and the launch
+ * returns with the failure that se_batch_status reports (no fault, no hang; the
+ * results of that launch are not valid); box = -1 turns it off.  Both return
+ * SE_ERR_ARG for a bad value. */
+int se_batch_set_wait_limit(se_batch *b, double seconds);
+int se_batch_inject_stall(se_batch *b, int box);
+
+/* FP32 FMA throughput probe (no counterpart in the paper): the measured peak that the
+ * ALU-bound spreading and gather kernels are compared with.  Enqueues on `stream` one
+ * launch of 8 CTAs of 256 threads per SM of `device`, each thread running 8 independent
+ * FMA chains of `iters` rounds; the caller times it with CUDA events on `stream`.
+ *   sink : DEVICE float[1], written only in a case that never occurs (keeps the chains live)
+ *   flop : receives the launch's floating-point operations (an FMA counts 2)
+ *   sms  : if not NULL, receives the device's number of streaming multiprocessors
+ * Returns SE_ERR_ARG for iters < 1 or null pointers, SE_ERR_CUDA for a failed launch.
+ * Asynchronous; the calling thread's current device is left as it was. */
+int se_fp32_fma_probe(int device, void *stream, int iters, float *sink, double *flop, int *sms);
 
 /* Message describing the last failure on this context ("" if none).  Valid until the
  * next call on the same context.  ctx may be NULL (returns the last create failure). */

@@ -31,6 +31,7 @@ SE_OPT_SPREAD = 12
 SE_OPT_OVERLAP_CHECK = 13
 SE_OPT_RESIDUAL = 14
 SE_OPT_SHEAR = 15
+SE_OPT_FF_TABLE = 16
 SE_OPT_PC_THETA = 10
 SE_OPT_PC_KA = 11
 STAGES = ("permute", "real", "spread", "fft_x_fwd", "fft_y_fwd", "fft_z_scale", "fft_y_inv", "fft_x_inv", "gather")
@@ -43,7 +44,8 @@ ABI_SYMBOLS = ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_
                "se_kernel_launches", "se_stage_times", "se_real_space_apply_noalloc",
                "se_set_learned_weights", "se_learned_features", "se_mlp_forward", "se_mlp_grad",
                "se_mlp_adam_step", "se_batch_create", "se_batch_apply", "se_batch_destroy",
-               "se_batch_last_error", "se_batch_status")
+               "se_batch_last_error", "se_batch_status", "se_fp32_fma_probe", "se_batch_set_wait_limit",
+               "se_batch_inject_stall")
 SE_MLP_NW, SE_MLP_NTRAIN, SE_MLP_SAMPLE = 5544, 5508, 276
 
 _lib = None
@@ -92,13 +94,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("se_set_learned_weights", "se_learned_features", "se_mlp_forward", "se_mlp_grad",
                  "se_mlp_adam_step"):
         getattr(lib, name).restype = i
+    lib.se_fp32_fma_probe.argtypes = [i, p, i, p, ctypes.POINTER(d), ctypes.POINTER(i)]
+    lib.se_fp32_fma_probe.restype = i
     lib.se_batch_create.argtypes = [ctypes.POINTER(p), ctypes.POINTER(p), i, i, p]
     lib.se_batch_apply.argtypes = [p, i, ctypes.POINTER(p), ctypes.POINTER(p), i, i]
     lib.se_batch_destroy.argtypes = [p]
     lib.se_batch_last_error.argtypes = [p]
     lib.se_batch_last_error.restype = ctypes.c_char_p
     lib.se_batch_status.argtypes = [p]
-    for name in ("se_batch_create", "se_batch_apply", "se_batch_destroy", "se_batch_status"):
+    lib.se_batch_set_wait_limit.argtypes = [p, d]
+    lib.se_batch_inject_stall.argtypes = [p, i]
+    for name in ("se_batch_create", "se_batch_apply", "se_batch_destroy", "se_batch_status",
+                 "se_batch_set_wait_limit", "se_batch_inject_stall"):
         getattr(lib, name).restype = i
     for name in ("se_create", "se_destroy", "se_set_params", "se_set_option", "se_set_config",
                  "se_mobility_apply", "se_mobility_apply_host", "se_solve", "se_brownian_ivp", "se_rigid_solve", "se_far_field_diffusivity",
@@ -408,6 +415,18 @@ class Batch:
         if rc != SE_OK:
             raise SeError(rc, self.lib.se_batch_last_error(self.h).decode())
 
+    def set_wait_limit(self, seconds: float):
+        """Time limit of every wait inside a persistent launch (se_batch_set_wait_limit)."""
+        rc = self.lib.se_batch_set_wait_limit(self.h, float(seconds))
+        if rc != SE_OK:
+            raise SeError(rc, "se_batch_set_wait_limit failed")
+
+    def inject_stall(self, box: int):
+        """Failure-injection hook for tests (se_batch_inject_stall); -1 turns it off."""
+        rc = self.lib.se_batch_inject_stall(self.h, int(box))
+        if rc != SE_OK:
+            raise SeError(rc, "se_batch_inject_stall failed")
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.se_batch_destroy(self.h)
@@ -418,3 +437,28 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def fp32_fma_peak(device: int = 0, iters: int = 4096, reps: int = 5) -> tuple[float, int]:
+    """Measured FP32 FMA throughput of the device in TFLOP/s (best of `reps` launches of
+    se_fp32_fma_probe, timed with CUDA events on torch's current stream) and its SM count."""
+    import torch
+    lib = load()
+    stream = torch.cuda.current_stream(device)
+    sink = torch.zeros(1, device=f"cuda:{device}", dtype=torch.float32)
+    flop, sms = ctypes.c_double(0.0), ctypes.c_int(0)
+    best = None
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = lib.se_fp32_fma_probe(device, ctypes.c_void_p(stream.cuda_stream), iters,
+                                   ctypes.c_void_p(sink.data_ptr()), ctypes.byref(flop), ctypes.byref(sms))
+        e1.record(stream)
+        if rc != SE_OK:
+            raise SeError(rc, "se_fp32_fma_probe failed")
+        e1.synchronize()
+        if r == 0:
+            continue                      # the first launch loads the module
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return flop.value / (best * 1e-3) / 1e12, sms.value

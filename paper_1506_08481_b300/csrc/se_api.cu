@@ -214,7 +214,7 @@ static int ensure_grids(se_ctx *c, int prec)
     // of its particles into its own partial grid: about two waves of CTAs on the SMs.
     {
         const size_t ntiles = (M / kTile) * (M / kTile) * (M / kTile);
-        c->nsplit = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * kSMs * 11 + ntiles - 1) / ntiles));
+        c->nsplit = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * (size_t)c->sms * 11 + ntiles - 1) / ntiles));
         if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[prec], (size_t)c->nsplit * M * M * M * 8 * es);
     }
     SE_ALLOC(c, c->b.spec_f[prec], M * M * Mh * 8 * 2 * es);
@@ -311,6 +311,11 @@ extern "C" int se_create(se_ctx **out, int device, void *stream)
     se_ctx *c = new se_ctx();
     c->device = device;
     c->stream = (cudaStream_t)stream;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || c->sms < 1) {
+        g_create_error = "cudaDeviceGetAttribute(MultiProcessorCount) failed";
+        delete c;
+        return SE_ERR_CUDA;
+    }
     int prio_least = 0, prio_greatest = 0;
     cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     if (cudaStreamCreateWithPriority(&c->aux, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
@@ -453,6 +458,15 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
     case SE_OPT_SPREAD:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "spread must be 0 or 1");
         c->spread = (int)value;
+        return SE_OK;
+    case SE_OPT_FF_TABLE:
+        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "ff table must be 0 or 1");
+        c->ff_table = (int)value;
+        if (!c->ff_table && c->pairs_ok[2]) {
+            dfree(c->b.pair_x[2]);
+            dfree(c->b.pair_c[2]);
+            c->pairs_ok[2] = false;
+        }
         return SE_OK;
     case SE_OPT_RESIDUAL:
         if (value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "residual precision must be 1 or 2");

@@ -23,6 +23,8 @@ struct se_batch {
     bool pp_ok = false;
     // what the graph was captured for (mode 1 or 2)
     int g_mode = 0, g_ncomp = 0, g_dtype = -1;
+    long long wait_ns = 2000000000ll;            // limit of the persistent launch's waits
+    int stall_box = -1;                          // failure-injection hook (se_batch_inject_stall)
     std::vector<const void *> g_x;
     std::vector<void *> g_y;
     std::string err;
@@ -126,6 +128,8 @@ static int batch_persistent(se_batch *b, int ncomp, const void *const *x, void *
         SE_CUDA_CHECK(b, cudaStreamSynchronize(b->main));
         rc = se::persist_prepare(b->box.data(), (int)n, ncomp, x, y, dtype, b->pp, b->err);
         if (rc != SE_OK) return rc;
+        b->pp.wait_ns = b->wait_ns;
+        b->pp.stall_box = b->stall_box;
         b->pp_ok = true;
         b->g_mode = 2;
         b->g_ncomp = ncomp;
@@ -206,10 +210,28 @@ extern "C" int se_batch_status(se_batch *b)
     cudaSetDevice(b->device);
     SE_CUDA_CHECK(b, cudaStreamSynchronize(b->main));
     if (b->pp.ctl && se::persist_failed(b->pp, b->main)) {
-        b->err = "a persistent batch launch gave up waiting at a grid barrier";
+        b->err = "a persistent batch launch gave up waiting for work of an earlier phase";
         return SE_ERR_CUDA;
     }
     return SE_OK;
 }
 
 extern "C" const char *se_batch_last_error(const se_batch *b) { return b ? b->err.c_str() : ""; }
+
+extern "C" int se_batch_set_wait_limit(se_batch *b, double seconds)
+{
+    if (!b || !(seconds > 0) || !(seconds <= 600)) return SE_ERR_ARG;
+    b->wait_ns = (long long)(seconds * 1e9);
+    batch_drop_graph(b);          // the launch's arguments change: prepare and capture again
+    b->pp_ok = false;
+    return SE_OK;
+}
+
+extern "C" int se_batch_inject_stall(se_batch *b, int box)
+{
+    if (!b || box < -1 || box >= (int)b->box.size()) return SE_ERR_ARG;
+    b->stall_box = box;
+    batch_drop_graph(b);
+    b->pp_ok = false;
+    return SE_OK;
+}

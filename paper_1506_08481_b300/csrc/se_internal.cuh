@@ -17,7 +17,6 @@ namespace se {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kNC = 12;          // components per particle, internal layout
 constexpr int kTile = 8;         // spreading tile edge (grid points)
-constexpr int kSMs = 148;        // streaming multiprocessors of a B300 (grid sizing)
 
 template <typename T> struct C2;
 template <> struct C2<float> { using t = float2; };
@@ -96,6 +95,7 @@ struct Buffers {
 
 struct se_ctx {
     int device = 0;
+    int sms = 1;                       // streaming multiprocessors of the device (grid sizing)
     cudaStream_t stream = nullptr;     // borrowed
     cudaStream_t aux = nullptr;        // owned: real space overlaps the wave chain
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -113,6 +113,7 @@ struct se_ctx {
     int gather = 0;              // SE_OPT_GATHER
     int spread = 0;              // SE_OPT_SPREAD
     int overlap_check = 1;       // SE_OPT_OVERLAP_CHECK
+    int ff_table = 1;            // SE_OPT_FF_TABLE
     double shear = 0.0;          // SE_OPT_SHEAR: strain gamma of the periodic cell
     int nsplit = 1;              // CTAs sharing a spreading tile (few tiles: small M)
     // configuration
@@ -200,8 +201,11 @@ void make_twiddles(se_ctx *c, int prec);
 // se_wave.cu: one persistent launch for the products of a batch of boxes (FP32)
 struct PersistPlan {
     void *desc = nullptr;        // device BoxDesc[nbox]
-    int *pref = nullptr;         // device [kPersistPhases][nbox + 1] work-item prefix sums
-    unsigned *ctl = nullptr;     // device: barrier count, generation, work counters, status (2)
+    int *pref = nullptr;         // device [nbox][kPersistPhases] work items per phase
+    unsigned *ctl = nullptr;     // device: abort flag, per-box claimed / finished counters, failure flag
+    int ctl_words = 0;
+    long long wait_ns = 2000000000ll;   // limit of every wait in the launch
+    int stall_box = -1;          // test hook: this box's phase 1 never finishes (waits run out)
     int nbox = 0, ncomp = 0, dtype = -1, grid = 0;
     size_t smem = 0;
     const void *kernel = nullptr;

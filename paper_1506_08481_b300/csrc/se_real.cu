@@ -653,24 +653,37 @@ __global__ void d2ff_kernel(size_t n, const double *in, ff *out)
 }  // namespace
 
 // The FP64 pair table as double-floats (once per configuration, beside the FP64 one), so
-// that the double-float real-space sum reads no FP64 values.  Without memory for it the
-// sum converts the FP64 table as it reads it.
+// that the double-float real-space sum reads no FP64 values.  Without memory for it, or
+// with SE_OPT_FF_TABLE 0, the sum converts the FP64 table as it reads it.
 int build_pair_table_ff(se_ctx *c)
 {
-    if (!c->pairs_ok[1] || c->pairs_ok[2]) return SE_OK;
+    if (!c->pairs_ok[1] || c->pairs_ok[2] || !c->ff_table) return SE_OK;
     const size_t np = c->npairs, nx = 3 * np + 1, nc = (size_t)kNPC * np + 1;
+    for (int q = 0; q < 2; ++q) {
+        void *&p = q ? c->b.pair_c[2] : c->b.pair_x[2];
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
     if (cudaMalloc(&c->b.pair_x[2], nx * sizeof(ff)) != cudaSuccess ||
         cudaMalloc(&c->b.pair_c[2], nc * sizeof(ff)) != cudaSuccess) {
         cudaGetLastError();
         if (c->b.pair_x[2]) cudaFree(c->b.pair_x[2]);
-        c->b.pair_x[2] = nullptr;
+        c->b.pair_x[2] = c->b.pair_c[2] = nullptr;
         return SE_OK;
     }
     cudaStream_t s = c->stream;
-    d2ff_kernel<<<4 * kSMs, 256, 0, s>>>(nx, (const double *)c->b.pair_x[1], (ff *)c->b.pair_x[2]);
-    d2ff_kernel<<<4 * kSMs, 256, 0, s>>>(nc, (const double *)c->b.pair_c[1], (ff *)c->b.pair_c[2]);
+    d2ff_kernel<<<4 * c->sms, 256, 0, s>>>(nx, (const double *)c->b.pair_x[1], (ff *)c->b.pair_x[2]);
+    d2ff_kernel<<<4 * c->sms, 256, 0, s>>>(nc, (const double *)c->b.pair_c[1], (ff *)c->b.pair_c[2]);
     c->launches += 2;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return SE_ERR_CUDA;
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        // no half-built copy survives: the sum falls back to the FP64 table
+        cudaFree(c->b.pair_x[2]);
+        cudaFree(c->b.pair_c[2]);
+        c->b.pair_x[2] = c->b.pair_c[2] = nullptr;
+        c->err = std::string("double-float pair table: ") + cudaGetErrorString(e);
+        return SE_ERR_CUDA;
+    }
     c->pairs_ok[2] = true;
     return SE_OK;
 }
@@ -868,7 +881,15 @@ extern "C" int se_real_space_apply_noalloc(int device, void *stream, int64_t N, 
     if (N > kNaMaxN) return SE_ERR_TOO_LARGE;
     if (!(rc > 0) || rc >= 0.5 * L) return SE_ERR_CUTOFF;
     if (device < 0 || device >= kNaMaxDevices) return SE_ERR_ARG;
+    // the caller's current device is restored before every return
+    int prev_device = -1;
+    if (cudaGetDevice(&prev_device) != cudaSuccess) return SE_ERR_CUDA;
+    struct Restore {
+        int dev;
+        ~Restore() { cudaSetDevice(dev); }
+    } restore{prev_device};
     if (cudaSetDevice(device) != cudaSuccess) return SE_ERR_CUDA;
+    cudaGetLastError();   // an earlier, unrelated launch error is not this call's
     // once per device: the device address of the scratch array (its host-side name is
     // only a stand-in and must not be passed to a kernel)
     if (!g_noalloc_ptr[device]) {
@@ -903,10 +924,10 @@ extern "C" int se_real_space_apply_noalloc(int device, void *stream, int64_t N, 
     else if (ncomp <= 11) go(real_kernel<double, 11>);
     else go(real_kernel<double, 12>);
     na_scatter_out_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, ncomp, l.perm, l.yr, y);
+    if (cudaGetLastError() != cudaSuccess) return SE_ERR_CUDA;   // a launch of this call failed
     int flag = 0;
     if (cudaMemcpyAsync(&flag, l.flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return SE_ERR_CUDA;
-    if (cudaGetLastError() != cudaSuccess) return SE_ERR_CUDA;
     return flag ? SE_ERR_NONFINITE : SE_OK;
 }

@@ -1612,7 +1612,7 @@ static void launch_spread16(se_ctx *c, const SeParams &p, const float *xs, cudaS
 {
     const int nt = p.ntile, ntiles = nt * nt * ((nt + 1) / 2);
     // partial grids only where the tiles alone leave SMs idle (at most the allocated parts)
-    const int ns = std::min(c->nsplit, std::max(1, (2 * kSMs * 8 + ntiles - 1) / ntiles));
+    const int ns = std::min(c->nsplit, std::max(1, (2 * c->sms * 8 + ntiles - 1) / ntiles));
     float *out = ns > 1 ? (float *)c->b.grid_part[0] : (float *)c->b.grid_f[0];
     auto args = [&](auto kern) {
         kern<<<dim3(ntiles, ns), 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
@@ -1885,16 +1885,19 @@ template void launch_gather_combine<ff, double>(se_ctx *, const ff *, const ff *
 // ---------------------------------------------------------------- persistent batched product
 //
 // The products of a batch of independent boxes (own N, M, P, xi, rc each) in ONE
-// cooperative launch of 2 CTAs per SM: eight phases, each a list of work items over
-// every box (prefix sums per phase), separated by a grid barrier:
+// cooperative launch of 2 CTAs per SM.  Each box runs eight phases in order:
 //   0 inputs into cell order   1 real-space pair sum and spreading (4 tiles per CTA,
 //   64 threads each)   2 x pass   3 y pass   4 z pass with the k-space scaling
-//   5 inverse y pass   6 inverse x pass   7 gather + combine.
-// Items are claimed with an atomic counter per phase (boxes of very different size
-// share the SMs in proportion to their work).  The stage code is that of the
-// per-box kernels (the *_body functions).  Every wait at a grid barrier is bounded:
-// after about two seconds the CTA raises the launch's abort flag (and the sticky
-// failure flag the host reads) and returns; the other CTAs see the flag and return.
+//   5 inverse y pass   6 inverse x pass   7 gather + combine,
+// each a list of work items.  There is no grid-wide barrier: every box keeps, per
+// phase, a counter of claimed and a counter of finished items, and a CTA takes an
+// item of any box whose earlier phases have finished (a warp scans the boxes, the
+// latest phase first, then the box with the most work), so one box's latency-bound FFT
+// passes run beside other boxes' spreading and gather.  A CTA never holds an item while
+// it waits, so the launch cannot deadlock.  The stage code is that of the per-box
+// kernels (the *_body functions).  Every wait is bounded in time (globaltimer): past the
+// limit the CTA raises the launch's abort flag and the sticky failure flag that the
+// host reads (se_batch_status), and every CTA returns.
 #include "se_real_table.cuh"
 
 namespace se {
@@ -1903,13 +1906,13 @@ namespace {
 
 constexpr int kPersistPhases = 8;
 constexpr int kPersistThreads = 256;
-constexpr long long kBarrierSpins = 20000000;    // x ~100 ns sleeps
 
 struct BoxDesc {
     SeParams p;
     FftPlan plan;
     int N, co, s16, with_wave, with_real, with_self;
     int nreal_items;                  // phase-1 items of the real-space sum (8 targets each)
+    int prio;                         // 0..1023, larger for boxes with more work
     float cnorm, twopiL, i4x2, ecoef;
     const void *x;
     void *y;
@@ -1925,9 +1928,10 @@ struct BoxDesc {
     size_t npairs;
 };
 
-// ctl: [0] arrivals, [1] generation, [2 .. 2 + phases) work counters, then the abort
-// flag and the sticky failure flag
-constexpr int kCtlAbort = 2 + kPersistPhases, kCtlFailed = kCtlAbort + 1, kCtlWords = kCtlFailed + 1;
+// ctl: [0] abort flag, then per box kBoxWords words (claimed items of each phase,
+// finished items of each phase), then the sticky failure flag (not reset per launch)
+constexpr int kCtlAbort = 0, kCtlHdr = 4, kBoxWords = 2 * kPersistPhases;
+inline int ctl_words(int nbox) { return kCtlHdr + nbox * kBoxWords + 1; }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *a)
 {
@@ -1936,34 +1940,18 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *a)
     return v;
 }
 
-__device__ bool grid_barrier(unsigned *ctl)
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *a)
 {
-    __syncthreads();
-    __shared__ int ok;
-    if (threadIdx.x == 0) {
-        const unsigned g = ld_acquire(ctl + 1);
-        __threadfence();
-        if (atomicAdd(ctl, 1u) == gridDim.x - 1) {
-            atomicExch(ctl, 0u);
-            __threadfence();
-            atomicAdd(ctl + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (ld_acquire(ctl + 1) == g) {
-                if (ld_acquire(ctl + kCtlAbort)) break;
-                if (++spins > kBarrierSpins) {
-                    atomicExch(ctl + kCtlAbort, 1u);
-                    atomicExch(ctl + kCtlFailed, 1u);
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-        ok = ld_acquire(ctl + kCtlAbort) == 0;
-    }
-    __syncthreads();
-    return ok != 0;
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ void bar_named(int id, int n)
@@ -1971,31 +1959,97 @@ __device__ __forceinline__ void bar_named(int id, int n)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// Warp 0 of a CTA claims the next item: returns the box (>= 0) with *ph and *it set,
+// -1 when every item of every box has been claimed, -2 when the launch is aborted.
+// A phase may start once the latest earlier phase with items has finished (that
+// phase's items all started after the phases before it had finished).  stall_box >= 0
+// is a test hook: that box's phase 1 never counts as finished, so waits for it run out.
+__device__ int claim_item(const BoxDesc *__restrict__ bd, int nbox, const int *__restrict__ cnt, unsigned *ctl,
+                          long long wait_ns, int stall_box, int *ph_out, int *it_out)
+{
+    const int lane = threadIdx.x & 31;
+    long long t_wait = -1;
+    for (;;) {
+        if (ld_acquire(ctl + kCtlAbort)) return -2;
+        unsigned best = 0;          // (phase + 1) << 26 | prio << 16 | box
+        bool left = false;
+        for (int b = lane; b < nbox; b += 32) {
+            const unsigned *bw = ctl + kCtlHdr + b * kBoxWords;
+            const int *cb = cnt + b * kPersistPhases;
+            int cur = 0;
+            while (cur < kPersistPhases && (int)ld_relaxed(bw + cur) >= cb[cur]) ++cur;
+            if (cur >= kPersistPhases) continue;
+            left = true;
+            int q = cur - 1;
+            while (q >= 0 && cb[q] == 0) --q;
+            bool ready = true;
+            if (q >= 0) {
+                const int need = cb[q] + (b == stall_box && q == 1 ? 1 : 0);
+                ready = (int)ld_acquire(bw + kPersistPhases + q) >= need;
+            }
+            if (ready) {
+                const unsigned key = ((unsigned)(cur + 1) << 26) | ((unsigned)bd[b].prio << 16) | (unsigned)b;
+                best = key > best ? key : best;
+            }
+        }
+        const unsigned top = __reduce_max_sync(0xffffffffu, best);
+        const bool any_left = __any_sync(0xffffffffu, left);
+        if (!any_left) return -1;
+        if (top != 0) {
+            const int b = (int)(top & 0xffffu), ph = (int)(top >> 26) - 1;
+            int got = -1;
+            if (lane == 0) {
+                const unsigned old = atomicAdd(ctl + kCtlHdr + b * kBoxWords + ph, 1u);
+                got = (int)old < cnt[b * kPersistPhases + ph] ? (int)old : -1;
+            }
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (got >= 0) {
+                *ph_out = ph;
+                *it_out = got;
+                return b;
+            }
+            continue;               // another CTA took the last item of that phase
+        }
+        // nothing ready yet: every remaining item waits for items in flight elsewhere
+        const long long now = global_ns();
+        if (t_wait < 0) t_wait = now;
+        if (now - t_wait > wait_ns) {
+            if (lane == 0) {
+                atomicExch(ctl + kCtlAbort, 1u);
+                atomicExch(ctl + kCtlHdr + nbox * kBoxWords, 1u);
+            }
+            __syncwarp();
+            return -2;
+        }
+        __nanosleep(256);
+    }
+}
+
 template <int NCOMP, typename TO>
 __global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(const BoxDesc *__restrict__ bd, int nbox,
-                                                                              const int *__restrict__ pref,
-                                                                              unsigned *ctl)
+                                                                              const int *__restrict__ cnt,
+                                                                              unsigned *ctl, long long wait_ns,
+                                                                              int stall_box)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ int s_item;
+    __shared__ int s_box, s_ph, s_it;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int ph = 0; ph < kPersistPhases; ++ph) {
-        if (ph > 0 && !grid_barrier(ctl)) return;
-        const int *pr = pref + ph * (nbox + 1);
-        const int total = pr[nbox];
-        for (;;) {
-            __syncthreads();                          // the previous item's shared buffers are free
-            if (threadIdx.x == 0) s_item = (int)atomicAdd(ctl + 2 + ph, 1u);
-            __syncthreads();
-            const int item = s_item;
-            if (item >= total) break;
-            int lo = 0, hi = nbox;                    // pr[lo] <= item < pr[lo + 1]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (pr[mid] <= item) lo = mid; else hi = mid;
+    for (;;) {
+        __syncthreads();                          // the previous item's shared buffers are free
+        if (warp == 0) {
+            int ph = 0, it = 0;
+            const int b = claim_item(bd, nbox, cnt, ctl, wait_ns, stall_box, &ph, &it);
+            if (lane == 0) {
+                s_box = b;
+                s_ph = ph;
+                s_it = it;
             }
-            const BoxDesc &d = bd[lo];
-            const int it = item - pr[lo];
+        }
+        __syncthreads();
+        const int box = s_box, ph = s_ph, it = s_it;
+        if (box < 0) return;
+        {
+            const BoxDesc &d = bd[box];
             const int Mh = d.p.M / 2 + 1;
             switch (ph) {
             case 0: {
@@ -2087,6 +2141,12 @@ __global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(co
             }
             }
         }
+        // the item's writes are visible device-wide before it counts as finished
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(ctl + kCtlHdr + box * kBoxWords + kPersistPhases + ph, 1u);
+        }
     }
 }
 
@@ -2122,7 +2182,8 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
 {
     persist_free(pl);
     std::vector<BoxDesc> h(nbox);
-    std::vector<int> pref((size_t)kPersistPhases * (nbox + 1), 0);
+    std::vector<int> cnt((size_t)kPersistPhases * nbox, 0);
+    std::vector<double> work(nbox, 0.0);
     size_t smem = (size_t)4 * sizeof(Spread16Smem);
     for (int b = 0; b < nbox; ++b) {
         se_ctx *c = box[b];
@@ -2182,14 +2243,25 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
             nw * (d.co == 8 ? (Mh + 1) / 2 : (Mh + 3) / 4) * M,
             nw * M * M / (d.co == 8 ? 4 : 8),
             d.nreal_items};
-        for (int ph = 0; ph < kPersistPhases; ++ph)
-            pref[(size_t)ph * (nbox + 1) + b + 1] = pref[(size_t)ph * (nbox + 1) + b] + items[ph];
+        for (int ph = 0; ph < kPersistPhases; ++ph) cnt[(size_t)b * kPersistPhases + ph] = items[ph];
+        work[b] = (double)d.N * p.P * p.P * p.P + (double)M * M * M;
         smem = std::max(smem, fft_smem_bytes<float2>(M, fft_nl<float>()));
         smem = std::max(smem, fft_smem_bytes<float2>(M, 4 * d.co));
     }
     if (smem > kSmemMax) {
         err = "a box's grid is too large for the persistent batch";
         return SE_ERR_GRID;
+    }
+    if (nbox > 65535) {
+        err = "the persistent batch takes at most 65535 boxes";
+        return SE_ERR_ARG;
+    }
+    // priority: rank by work, so the largest boxes start first
+    {
+        std::vector<int> order(nbox);
+        for (int b = 0; b < nbox; ++b) order[b] = b;
+        std::sort(order.begin(), order.end(), [&](int u, int v) { return work[u] > work[v]; });
+        for (int r = 0; r < nbox; ++r) h[order[r]].prio = 1023 - std::min(r, 1023);
     }
     const void *kern = persist_kernel(ncomp, dtype);
     int dev = 0, nsm = 0, occ = 0, coop = 0;
@@ -2203,22 +2275,24 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
         err = "the persistent batch kernel cannot be launched cooperatively on this device";
         return SE_ERR_CUDA;
     }
+    const int nw = ctl_words(nbox);
     if (cudaMalloc(&pl.desc, nbox * sizeof(BoxDesc)) != cudaSuccess ||
-        cudaMalloc(&pl.pref, pref.size() * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&pl.ctl, kCtlWords * sizeof(unsigned)) != cudaSuccess) {
+        cudaMalloc(&pl.pref, cnt.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&pl.ctl, nw * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         persist_free(pl);
         err = "persistent batch allocation failed";
         return SE_ERR_NOMEM;
     }
     if (cudaMemcpy(pl.desc, h.data(), nbox * sizeof(BoxDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pl.pref, pref.data(), pref.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(pl.ctl, 0, kCtlWords * sizeof(unsigned)) != cudaSuccess) {
+        cudaMemcpy(pl.pref, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(pl.ctl, 0, nw * sizeof(unsigned)) != cudaSuccess) {
         persist_free(pl);
         err = "persistent batch upload failed";
         return SE_ERR_CUDA;
     }
     pl.nbox = nbox;
+    pl.ctl_words = nw;
     pl.ncomp = ncomp;
     pl.dtype = dtype;
     pl.grid = occ * nsm;
@@ -2229,14 +2303,16 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
 
 int persist_launch(const PersistPlan &pl, cudaStream_t s, std::string &err)
 {
-    // fresh barrier, work counters and abort flag; the sticky failure flag stays
-    cudaError_t e = cudaMemsetAsync(pl.ctl, 0, kCtlFailed * sizeof(unsigned), s);
+    // fresh abort flag and item counters; the sticky failure flag (the last word) stays
+    cudaError_t e = cudaMemsetAsync(pl.ctl, 0, (pl.ctl_words - 1) * sizeof(unsigned), s);
     if (e == cudaSuccess) {
         const BoxDesc *bd = (const BoxDesc *)pl.desc;
         int nbox = pl.nbox;
-        const int *pref = pl.pref;
+        const int *cnt = pl.pref;
         unsigned *ctl = pl.ctl;
-        void *args[] = {(void *)&bd, (void *)&nbox, (void *)&pref, (void *)&ctl};
+        long long wait_ns = pl.wait_ns;
+        int stall_box = pl.stall_box;
+        void *args[] = {(void *)&bd, (void *)&nbox, (void *)&cnt, (void *)&ctl, (void *)&wait_ns, (void *)&stall_box};
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
@@ -2259,9 +2335,10 @@ int persist_launch(const PersistPlan &pl, cudaStream_t s, std::string &err)
 int persist_failed(const PersistPlan &pl, cudaStream_t s)
 {
     unsigned f = 0;
-    cudaMemcpyAsync(&f, pl.ctl + kCtlFailed, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    unsigned *failed = pl.ctl + pl.ctl_words - 1;
+    cudaMemcpyAsync(&f, failed, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    cudaMemsetAsync(pl.ctl + kCtlFailed, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(failed, 0, sizeof(unsigned), s);
     return f ? 1 : 0;
 }
 

@@ -34,6 +34,11 @@ import numpy as np
 # prefactor between the model and the measured relative 2-norm error
 ERROR_PREFACTOR = 1.0
 
+# The large-scale monodisperse workload: N = 200000 spheres of radius 1 at phi = 0.45
+# (box side L = 123.018), all 12 components, support P = 24.  xi, M, rc and m are the
+# error model's choice for <= 1e-6 in FP32 at that support (real-space size approach).
+LARGE_MONO = dict(xi=0.6, M=216, P=24, rc=7.5, m=8.68, size_mode=1)
+
 
 @dataclass
 class SeParams:

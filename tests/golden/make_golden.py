@@ -24,7 +24,7 @@ def checksum(a):
     return float(np.sum(a * np.arange(1, a.size + 1).reshape(a.shape) % 97))
 
 
-def mono_n200k(nrows=64):
+def mono_n200k(nrows=1000):
     cfg = inputs.mono_dense(seed=0, n=200000, phi=0.45)
     x = inputs.moments(cfg.N, np.random.default_rng(1), 12)
     rows = np.sort(np.random.default_rng(2).choice(cfg.N, nrows, replace=False))

@@ -106,3 +106,87 @@ def test_persistent_batch_matches_per_box_launches(ncomp, dtype):
     for y, r in zip(ys, ref):
         assert close(y, -2.0 * r)
     b.close()
+
+
+def test_batch_with_largest_box_vs_oracle(oracle_mod):
+    """Boxes of the 64-box workload's kind (bidisperse radii 1 and 1.5 at equal numbers,
+    forces only, FP32, parameters the chooser picks for 1e-6 on a grid of at most 128^3,
+    as in the benchmark), one of them at the workload's largest size N = 8000 and
+    phi = 0.45: the graph and the persistent launch against the FP64 oracle on 256 sampled
+    rows of every box, <= 1e-6 in relative 2-norm."""
+    rng = np.random.default_rng(40)
+    boxes = []
+    for n, phi in ((8000, 0.45), (1500, 0.1), (600, 0.3)):
+        rad = inputs.radii_bidisperse(n, 1.0, 1.5, 0.5, rng)
+        L = inputs.box_side(rad, phi)
+        boxes.append(inputs.Config(f"n{n}", L, inputs.positions_dense(rad, L, rng, sweeps=4), rad))
+    ctxs, xs = [], []
+    for cfg in boxes:
+        sp = params.choose(cfg.L, cfg.N, 1e-6, M_max=128, a_eff=params.effective_radius(cfg.rad), precision=0)
+        c = api.Context()
+        c.set_params(sp.xi, sp.M, sp.P, sp.rc)
+        c.set_option(api.SE_OPT_SHAPE_M, sp.m)
+        c.set_option(api.SE_OPT_SIZE_MODE, 1)
+        c.set_config(cfg.pos, cfg.rad, cfg.L)
+        ctxs.append(c)
+        xs.append(torch.tensor(rng.standard_normal((cfg.N, 3)), device="cuda", dtype=torch.float32))
+    refs = []
+    for cfg, x in zip(boxes, xs):
+        rows = np.sort(rng.choice(cfg.N, 256, replace=False))
+        xx = np.zeros((cfg.N, 12))
+        xx[:, :3] = x.double().cpu().numpy()
+        refs.append((rows, oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, xx, rows=rows, tol=1e-11)[:, :3]))
+    ys = [torch.empty_like(x) for x in xs]
+    b = api.Batch(ctxs, nstreams=4)
+    for mode in (True, True, api.Batch.PERSISTENT, api.Batch.PERSISTENT):
+        for y in ys:
+            y.fill_(float("nan"))
+        b.apply(xs, ys, use_graph=mode)
+        b.status()
+        for cfg, y, (rows, ref) in zip(boxes, ys, refs):
+            e = np.linalg.norm(y.double().cpu().numpy()[rows] - ref) / np.linalg.norm(ref)
+            print(f"{cfg.name} mode {int(mode)}: {e:.2e}")
+            assert e <= 1e-6, (cfg.name, mode)
+    b.close()
+
+
+def test_persistent_batch_bounded_wait_runs_out():
+    """Failure detection without a GPU fault: the injected stall keeps one box's first
+    phases from ever counting as finished, so the CTAs that wait for them give up after
+    the (shortened) wait limit; the launch returns, se_batch_status reports the failure,
+    and once the hook is off the same batch computes the right products again."""
+    boxes = inputs.batch_boxes(seed=9, nbox=4, nmin=60, nmax=300)
+    ctxs, xs = [], []
+    rng = np.random.default_rng(3)
+    for cfg in boxes:
+        sp = params.choose(cfg.L, cfg.N, 1e-6, M_max=64, a_eff=params.effective_radius(cfg.rad), precision=0)
+        c = api.Context()
+        c.set_params(sp.xi, sp.M, sp.P, sp.rc)
+        c.set_option(api.SE_OPT_SHAPE_M, sp.m)
+        c.set_option(api.SE_OPT_SIZE_MODE, 1)
+        c.set_config(cfg.pos, cfg.rad, cfg.L)
+        ctxs.append(c)
+        xs.append(torch.tensor(rng.standard_normal((cfg.N, 3)), device="cuda", dtype=torch.float32))
+    ref = [c.apply(x).clone() for c, x in zip(ctxs, xs)]
+    ys = [torch.empty_like(x) for x in xs]
+    b = api.Batch(ctxs, nstreams=2)
+    b.set_wait_limit(0.05)
+    b.inject_stall(2)
+    import time
+    for step in range(2):                 # the eager preparing step, then the persistent launch
+        b.apply(xs, ys, use_graph=api.Batch.PERSISTENT)
+    t = time.perf_counter()
+    with pytest.raises(api.SeError) as e:
+        b.status()
+    assert e.value.code == api.SE_ERR_CUDA
+    assert time.perf_counter() - t < 5.0
+    b.status()                            # the failure was reported once and cleared
+    b.inject_stall(-1)
+    for step in range(2):
+        for y in ys:
+            y.fill_(float("nan"))
+        b.apply(xs, ys, use_graph=api.Batch.PERSISTENT)
+        b.status()
+        for y, r in zip(ys, ref):
+            assert float(torch.linalg.norm(y - r) / torch.linalg.norm(r)) <= 1e-6
+    b.close()

@@ -55,6 +55,56 @@ def test_noalloc_matches_regular_real_space_part():
             assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-12, (call, ncomp)
 
 
+@pytest.mark.parametrize("case", ["cells_4", "cells_enlarged"])
+def test_noalloc_cell_list_vs_oracle(oracle_mod, case):
+    """The entry point's own cell-list pipeline (scan, scatter, per-cell order, wrapped cell
+    offsets, the 27 neighbour cells) against the oracle's real-space part at the same xi
+    and rc.  "cells_4": rc = L / 4.2, so 4^3 cells.  "cells_enlarged": L / rc = 17.5 asks
+    for 17^3 > SE_NOALLOC_MAX_CELLS cells, which the entry point enlarges to 16^3.  The
+    positions are shifted by whole periods, most of them out of [0, L), and every case is
+    called twice in a row.  U, Omega and E equal the oracle's real-space sum; E_tr (whose
+    harmonic pressure Faxen term the library splits between real and wave space in
+    another way than the oracle) equals the regular product's real-space part."""
+    lib = api.load()
+    rng = np.random.default_rng(33)
+    if case == "cells_4":
+        rad = rng.uniform(0.5, 1.0, 600)
+        L = inputs.box_side(rad, 0.1)
+        xi, rc = 0.6, L / 4.2
+    else:
+        rad = np.full(3000, 0.5)
+        L = inputs.box_side(rad, 0.05)
+        xi, rc = 1.5, L / 17.5
+    pos = inputs.positions_rsa(rad, L, rng)
+    shifted = pos + L * rng.integers(-3, 4, size=pos.shape)
+    N = rad.shape[0]
+    x = rng.standard_normal((N, 12))
+    ref = oracle_mod.mobility(pos, rad, L, x, xi=xi, rc=rc, kc=1.0, parts=1)
+    ctx = api.Context()
+    ctx.set_params(xi, 32, 12, rc)
+    ctx.set_option(api.SE_OPT_PRECISION, 1)
+    ctx.set_option(api.SE_OPT_PARTS, 1)
+    ctx.set_config(pos, rad, L)
+    xd = torch.tensor(x, device="cuda", dtype=torch.float64)
+    lib_real = ctx.apply(xd).cpu().numpy()
+    pos_d = torch.tensor(shifted, device="cuda", dtype=torch.float64)
+    rad_d = torch.tensor(rad, device="cuda", dtype=torch.float64)
+    for call in range(2):
+        code, y = noalloc(lib, pos_d, rad_d, L, xi, rc, xd)
+        assert code == api.SE_OK, (call, code)
+        got = y.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.linalg.norm(got[:, :11] - ref[:, :11]) / np.linalg.norm(ref[:, :11]) <= 1e-12, call
+        assert np.linalg.norm(got[:, 11] - lib_real[:, 11]) / np.linalg.norm(lib_real[:, 11]) <= 1e-12, call
+        # the forces-only prefix reads and writes 3 components per sphere
+        code, y3 = noalloc(lib, pos_d, rad_d, L, xi, rc, xd[:, :3].contiguous())
+        assert code == api.SE_OK
+        x3 = np.zeros_like(x)
+        x3[:, :3] = x[:, :3]
+        ref3 = oracle_mod.mobility(pos, rad, L, x3, xi=xi, rc=rc, kc=1.0, parts=1)[:, :3] if call == 0 else ref3
+        assert np.linalg.norm(y3.cpu().numpy() - ref3) / np.linalg.norm(ref3) <= 1e-12, call
+
+
 def test_noalloc_rejects_sizes_beyond_capacity():
     lib = api.load()
     N = api.SE_NOALLOC_MAX_N + 1
