@@ -1940,13 +1940,6 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *a)
     return v;
 }
 
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned *a)
-{
-    unsigned v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ long long global_ns()
 {
     long long t;
@@ -1961,13 +1954,28 @@ __device__ __forceinline__ void bar_named(int id, int n)
 
 // Warp 0 of a CTA claims the next item: returns the box (>= 0) with *ph and *it set,
 // -1 when every item of every box has been claimed, -2 when the launch is aborted.
-// A phase may start once the latest earlier phase with items has finished (that
-// phase's items all started after the phases before it had finished).  stall_box >= 0
-// is a test hook: that box's phase 1 never counts as finished, so waits for it run out.
+// A CTA keeps taking items of the (box, phase) it took last while that phase has
+// unclaimed items (one atomic per item); only then does the warp scan the boxes.  A
+// phase may start once the latest earlier phase with items has finished (that phase's
+// items all started after the phases before it had finished).  stall_box >= 0 is a
+// test hook: that box's phase 1 never counts as finished, so waits for it run out.
 __device__ int claim_item(const BoxDesc *__restrict__ bd, int nbox, const int *__restrict__ cnt, unsigned *ctl,
-                          long long wait_ns, int stall_box, int *ph_out, int *it_out)
+                          long long wait_ns, int stall_box, int last_box, int last_ph, int *ph_out, int *it_out)
 {
     const int lane = threadIdx.x & 31;
+    if (last_box >= 0) {
+        int got = -1;
+        if (lane == 0) {
+            const unsigned old = atomicAdd(ctl + kCtlHdr + last_box * kBoxWords + last_ph, 1u);
+            got = (int)old < cnt[last_box * kPersistPhases + last_ph] ? (int)old : -1;
+        }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got >= 0) {
+            *ph_out = last_ph;
+            *it_out = got;
+            return last_box;
+        }
+    }
     long long t_wait = -1;
     for (;;) {
         if (ld_acquire(ctl + kCtlAbort)) return -2;
@@ -1976,22 +1984,30 @@ __device__ int claim_item(const BoxDesc *__restrict__ bd, int nbox, const int *_
         for (int b = lane; b < nbox; b += 32) {
             const unsigned *bw = ctl + kCtlHdr + b * kBoxWords;
             const int *cb = cnt + b * kPersistPhases;
+            // the box's claimed and finished counters in four 16-byte loads
+            unsigned w[kBoxWords];
+#pragma unroll
+            for (int v = 0; v < kBoxWords / 4; ++v)
+                asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(w[4 * v]), "=r"(w[4 * v + 1]), "=r"(w[4 * v + 2]), "=r"(w[4 * v + 3])
+                             : "l"(bw + 4 * v)
+                             : "memory");
             int cur = 0;
-            while (cur < kPersistPhases && (int)ld_relaxed(bw + cur) >= cb[cur]) ++cur;
+            while (cur < kPersistPhases && (int)w[cur] >= cb[cur]) ++cur;
             if (cur >= kPersistPhases) continue;
             left = true;
             int q = cur - 1;
             while (q >= 0 && cb[q] == 0) --q;
-            bool ready = true;
-            if (q >= 0) {
-                const int need = cb[q] + (b == stall_box && q == 1 ? 1 : 0);
-                ready = (int)ld_acquire(bw + kPersistPhases + q) >= need;
-            }
+            const bool ready = q < 0 || (int)w[kPersistPhases + q] >= cb[q] + (b == stall_box && q == 1 ? 1 : 0);
             if (ready) {
                 const unsigned key = ((unsigned)(cur + 1) << 26) | ((unsigned)bd[b].prio << 16) | (unsigned)b;
                 best = key > best ? key : best;
             }
         }
+        // the finished counts were read relaxed: a lane that saw a finished phase fences
+        // (acquire side of the producers' fence + atomic), and the CTA barrier after the
+        // claim orders that before every thread's reads of the item's inputs
+        if (best != 0) __threadfence();
         const unsigned top = __reduce_max_sync(0xffffffffu, best);
         const bool any_left = __any_sync(0xffffffffu, left);
         if (!any_left) return -1;
@@ -2034,11 +2050,12 @@ __global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(co
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_box, s_ph, s_it;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int last_box = -1, last_ph = 0;
     for (;;) {
         __syncthreads();                          // the previous item's shared buffers are free
         if (warp == 0) {
             int ph = 0, it = 0;
-            const int b = claim_item(bd, nbox, cnt, ctl, wait_ns, stall_box, &ph, &it);
+            const int b = claim_item(bd, nbox, cnt, ctl, wait_ns, stall_box, last_box, last_ph, &ph, &it);
             if (lane == 0) {
                 s_box = b;
                 s_ph = ph;
@@ -2048,6 +2065,8 @@ __global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(co
         __syncthreads();
         const int box = s_box, ph = s_ph, it = s_it;
         if (box < 0) return;
+        last_box = box;
+        last_ph = ph;
         {
             const BoxDesc &d = bd[box];
             const int Mh = d.p.M / 2 + 1;

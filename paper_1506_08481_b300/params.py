@@ -35,9 +35,13 @@ import numpy as np
 ERROR_PREFACTOR = 1.0
 
 # The large-scale monodisperse workload: N = 200000 spheres of radius 1 at phi = 0.45
-# (box side L = 123.018), all 12 components, support P = 24.  xi, M, rc and m are the
-# error model's choice for <= 1e-6 in FP32 at that support (real-space size approach).
-LARGE_MONO = dict(xi=0.6, M=216, P=24, rc=7.5, m=8.68, size_mode=1)
+# (box side L = 123.018), all 12 components, support P = 24, real-space size approach.
+# The FP32 rounding of the wave-space part grows with the sharpness of the window on
+# the grid, kappa sqrt(alpha) ~ M m / (L P) (the gather's derivative weights amplify the
+# grid's rounding noise; measured: E block 1.2e-6 at M = 216, m = 8.68, 6.8e-7 at M = 144,
+# m = 8), so the grid is the coarsest that resolves the wave-space sum at this support:
+# xi = 0.45 (the method error, FP64, ~1e-7), rc = 10 for the real-space truncation.
+LARGE_MONO = dict(xi=0.45, M=144, P=24, rc=10.0, m=8.0, size_mode=1)
 
 
 @dataclass

@@ -1,10 +1,10 @@
 """The large-scale workload that the benchmark times, against the FP64 direct-Ewald oracle.
 
 N = 200000 spheres of radius 1 at phi = 0.45 (box side 123.018), all 12 components
-i.i.d. N(0, 1), support P = 24, grid M = 216, xi = 0.6, rc = 7.5, m = 8.68, real-space
-size approach, FP32 products with the default kernels (8 x 8 x 16 spreading tiles with
-packed FMAs, two support columns per gather lane): the exact launch configuration of the
-benchmark.  Expected values are 1000 random output rows of the oracle product, stored in
+i.i.d. N(0, 1), support P = 24, and the grid, splitting and cutoff of
+paper_1506_08481_b300.params.LARGE_MONO (real-space size approach), FP32 products with the
+default kernels (8 x 8 x 16 spreading tiles with packed FMAs, two support columns per
+gather lane): the exact launch configuration of the benchmark.  Expected values are 1000 random output rows of the oracle product, stored in
 tests/golden/mono_n200k_rows.npz by tests/golden/make_golden.py (oracle only); the stored
 checksums confirm that the seeded generators rebuilt the same positions and moments.
 
@@ -73,7 +73,7 @@ def test_large_fp32_product_vs_oracle_rows(large):
     cfg, x, rows, ref, ctx = large
     assert len(rows) == 1000
     y = ctx.apply(torch.tensor(x, device="cuda", dtype=torch.float32)).double().cpu().numpy()[rows]
-    errs = report("FP32, N=2e5, P=24, M=216:", y, ref)
+    errs = report("FP32, N=2e5, P=24:", y, ref)
     assert rel(y, ref) <= 1e-6
     for k, (r2, _) in errs.items():
         assert r2 <= 1e-6, k
@@ -96,7 +96,7 @@ def test_large_fp64_and_double_float_vs_oracle_rows(large):
     finally:
         ctx.set_option(api.SE_OPT_PRECISION, 0)
     for prec, tag in ((1, "FP64"), (2, "double-float")):
-        errs = report(f"{tag}, N=2e5, P=24, M=216:", out[prec], ref)
+        errs = report(f"{tag}, N=2e5, P=24:", out[prec], ref)
         assert rel(out[prec], ref) <= 2e-7, tag
         for k, (r2, _) in errs.items():
             assert r2 <= 5e-7, (tag, k)
