@@ -73,8 +73,13 @@ typedef struct se_ctx se_ctx;
                                   time on B300's FP64 rate */
 #define SE_OPT_SIZE_MODE   2   /* particle-size (Faxen) terms, Sec. 3.2: 0 = hybrid approach (default: target
                                   Laplacians in k-space), 1 = real-space approach (all of them in the
-                                  spread/gather polynomial, Eq. non-ortho-shape), 2 = wave-space approach
-                                  (source and target Laplacians in k-space; required by SE_OPT_SHEAR) */
+                                  spread/gather polynomial, Eq. non-ortho-shape), 2 = Laplacians of source and
+                                  target in k-space with the torque / stresslet gradients still in the
+                                  spread and gather (8 grids each way), 3 = the paper's wave-space approach
+                                  (Eqs. wave-only-f-assign, wave-only-compute-1/2, parseval-sum-2): every
+                                  derivative in k-space, the plain window on both sides, 20 grids each
+                                  way; runs in FP32 or FP64 (SE_OPT_PRECISION 2 runs it in FP64).  A
+                                  sheared cell (SE_OPT_SHEAR) needs mode 2 or 3 */
 #define SE_OPT_ETA         3   /* solvent viscosity (default 1) */
 #define SE_OPT_SHAPE_M     4   /* Gaussian shape parameter m of Eq. theta-param (default sqrt(pi P)) */
 #define SE_OPT_RESTART     5   /* GMRES restart length, 1..1000 (default 30; the basis takes (restart + 1) N ncomp doubles) */
@@ -101,7 +106,7 @@ typedef struct se_ctx se_ctx;
                                   when the products run in FP32: 2 (default, double-float) or 1 (FP64) */
 #define SE_OPT_SHEAR      15   /* strain gamma in [-0.5, 0.5] of the periodic cell a1 = (L, 0, 0), a2 = (gamma L,
                                   L, 0), a3 = (0, 0, L) (a cube sheared in x along y, Sec. 3.2; default 0).
-                                  Needs SE_OPT_SIZE_MODE 2 (set first; SE_ERR_ARG otherwise, also for a
+                                  Needs SE_OPT_SIZE_MODE 2 or 3 (set first; SE_ERR_ARG otherwise, also for a
                                   later change of the size mode); se_set_config must follow; the spectral
                                   preconditioner falls back to the block one; positions may be given
                                   in any periodic image */
@@ -131,11 +136,16 @@ typedef struct se_ctx se_ctx;
 /* preconditioners for se_solve */
 #define SE_PRECOND_NONE    0
 #define SE_PRECOND_BLOCK   1   /* block-diagonal self + own-image blocks (Sec. 4.2) */
-#define SE_PRECOND_LEARNED 2   /* block preconditioner + learned correction (BLOCK without weights) */
+#define SE_PRECOND_LEARNED 2   /* SE_PRECOND_SPECTRAL with the damping and cutoff that the learned network
+                                  predicts for the configuration (se_set_learned_weights); the plain
+                                  block preconditioner without weights or in a sheared cell */
 #define SE_PRECOND_SPECTRAL 3  /* block preconditioner minus a correction of the long-wavelength
                                   transverse force modes (their eigenvalues n/(eta k^2) set the
                                   iteration count), applied as a forces-only product on a coarse
-                                  grid; built with three extra products.  Not in the paper. */
+                                  grid; built with three extra products.  A restart cycle that fails
+                                  to halve the residual switches the rest of the solve to the block
+                                  preconditioner (a damping too strong for the configuration).  Not
+                                  in the paper. */
 
 /* Create a context on CUDA device `device`; `stream` is a cudaStream_t (may be 0 for
  * the legacy default stream), borrowed for the context's lifetime.  *out receives the
@@ -258,15 +268,17 @@ int se_high_frequency_viscosity(se_ctx *ctx, double rtol, int maxit, double *eta
 int se_far_field_diffusivity(se_ctx *ctx, int nsamples, const double *fr, double *d, double rtol, int maxit,
                              int *products);
 
-/* Learned preconditioner correction (SE_PRECOND_LEARNED).  A small network (16 -> 64 ->
- * 64 -> 4, tanh, FP32) maps rotation- and permutation-invariant features of a sphere's
- * radius and of its neighbours inside rc to corrections of the isotropic parts of its
- * block of the Sec. 4.2 preconditioner; blocks that would not be invertible fall back
- * to the plain block.  Weights are SE_MLP_NW packed floats (layout in se_learned.cu),
- * produced by paper_1506_08481_b300/train_pc.py.
+/* Learned preconditioner (SE_PRECOND_LEARNED).  A small network (16 -> 64 -> 64 -> 4,
+ * tanh, FP32) maps rotation- and permutation-invariant features of each sphere's radius and
+ * of its neighbours inside rc (and the box size L / <a>) to per-sphere outputs whose mean
+ * over the spheres sets the damping theta and the cutoff k_c <a> of the spectral correction
+ * of the Sec. 4.2 block preconditioner (theta clamped to [0.5, 0.985], k_c <a> to [0.4, 1.5]).
+ * Weights are SE_MLP_NW packed floats (layout in se_learned.cu), produced by
+ * paper_1506_08481_b300/train_pc.py from the iteration counts of solves over a grid of
+ * (theta, k_c <a>) on generated configurations.
  *   se_set_learned_weights: copies the HOST array w; SE_ERR_NONFINITE on NaN/Inf.
  *   se_learned_features   : DEVICE feat [N][16] in caller order for the configuration.
- *   se_mlp_forward        : DEVICE w, X [n][16] -> Y [n][4] (dimensionless corrections).
+ *   se_mlp_forward        : DEVICE w, X [n][16] -> Y [n][4] (the outputs, unstandardised).
  *   se_mlp_grad           : gradient DEVICE grad [SE_MLP_NTRAIN] and loss [1] of the mean
  *                           squared error of the standardised outputs against Yt [n][4];
  *                           scratch >= n * 276 floats (SE_ERR_TOO_LARGE otherwise).

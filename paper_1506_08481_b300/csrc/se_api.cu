@@ -110,11 +110,18 @@ static void free_grids(se_ctx *c)
         dfree(c->b.tw[q]);
         c->grid_M[q] = 0;
     }
+    for (int q = 0; q < 2; ++q) {
+        dfree(c->b.ws_grid[q]);
+        dfree(c->b.ws_spec_a[q]);
+        dfree(c->b.ws_spec_b[q]);
+        c->b.ws_M[q] = 0;
+    }
 }
 
 static void free_config(se_ctx *c)
 {
     free_spectral(c);
+    c->lp_ready = false;
     dfree_t(c->b.pos);
     dfree_t(c->b.rad);
     dfree_t(c->b.perm);
@@ -227,6 +234,22 @@ static int ensure_grids(se_ctx *c, int prec)
 }
 
 static int ensure_support(se_ctx *c, int prec);
+
+// the wave-space approach's 20-component grids and spectra (SE_OPT_SIZE_MODE 3)
+static int ensure_ws_grids(se_ctx *c, int prec)
+{
+    if (c->b.ws_M[prec] == (size_t)c->M && c->b.ws_grid[prec]) return SE_OK;
+    dfree(c->b.ws_grid[prec]);
+    dfree(c->b.ws_spec_a[prec]);
+    dfree(c->b.ws_spec_b[prec]);
+    const size_t es = prec == 1 ? sizeof(double) : sizeof(float);
+    const size_t M = c->M, Mh = M / 2 + 1;
+    SE_ALLOC(c, c->b.ws_grid[prec], M * M * M * 20 * es);
+    SE_ALLOC(c, c->b.ws_spec_a[prec], M * M * Mh * 20 * 2 * es);
+    SE_ALLOC(c, c->b.ws_spec_b[prec], M * M * Mh * 20 * 2 * es);
+    c->b.ws_M[prec] = c->M;
+    return SE_OK;
+}
 
 // double-float support: the FP64 tables and the FP64 pair table of the real-space sum
 // converted once per configuration
@@ -401,10 +424,11 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         c->precision = (int)value;
         return SE_OK;
     case SE_OPT_SIZE_MODE:
-        if (value != 0 && value != 1 && value != 2)
-            return set_error(c, SE_ERR_ARG, "size mode must be 0 (hybrid), 1 (real-space) or 2 (wave-space)");
-        if (c->shear != 0 && value != 2)
-            return set_error(c, SE_ERR_ARG, "a sheared cell needs the wave-space size approach (SE_OPT_SIZE_MODE 2)");
+        if (value != 0 && value != 1 && value != 2 && value != 3)
+            return set_error(c, SE_ERR_ARG, "size mode must be 0 (hybrid), 1 (real-space), 2 (wave-space, "
+                                            "gradients in the spread) or 3 (wave-space, all derivatives in k-space)");
+        if (c->shear != 0 && value != 2 && value != 3)
+            return set_error(c, SE_ERR_ARG, "a sheared cell needs a wave-space size approach (SE_OPT_SIZE_MODE 2 or 3)");
         c->size_mode = (int)value;
         c->pc_ready = false;
         return SE_OK;
@@ -474,8 +498,8 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         return SE_OK;
     case SE_OPT_SHEAR:
         if (!(std::fabs(value) <= 0.5)) return set_error(c, SE_ERR_ARG, "shear strain must be in [-0.5, 0.5]");
-        if (value != 0 && c->size_mode != 2)
-            return set_error(c, SE_ERR_ARG, "a sheared cell needs the wave-space size approach (SE_OPT_SIZE_MODE 2)");
+        if (value != 0 && c->size_mode != 2 && c->size_mode != 3)
+            return set_error(c, SE_ERR_ARG, "a sheared cell needs a wave-space size approach (SE_OPT_SIZE_MODE 2 or 3)");
         if (value != c->shear) {
             c->shear = value;
             c->have_config = false;        // the configuration must be set again
@@ -502,8 +526,8 @@ extern "C" int se_set_config(se_ctx *c, int64_t N, double L, const double *pos, 
     if (!c->have_params) return set_error(c, SE_ERR_STATE, "se_set_params must be called first");
     if (!(L > 0) || !std::isfinite(L)) return set_error(c, SE_ERR_ARG, "L must be positive");
     if (c->rc >= 0.5 * L) return set_error(c, SE_ERR_CUTOFF, "rc must be smaller than L/2");
-    if (c->shear != 0 && c->size_mode != 2)
-        return set_error(c, SE_ERR_ARG, "a sheared cell needs the wave-space size approach (SE_OPT_SIZE_MODE 2)");
+    if (c->shear != 0 && c->size_mode != 2 && c->size_mode != 3)
+        return set_error(c, SE_ERR_ARG, "a sheared cell needs a wave-space size approach (SE_OPT_SIZE_MODE 2 or 3)");
     cudaSetDevice(c->device);
     SE_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
     free_config(c);
@@ -563,6 +587,14 @@ static int apply_t(se_ctx *c, int ncomp, const TO *x, TO *y)
         return SE_OK;
     };
     int rc;
+    if (c->size_mode == 3) {
+        // the wave-space approach: its own 20-component chain after the real-space sum
+        if ((rc = real_part(s)) != SE_OK) return rc;
+        launch_wave_ws<T, TO>(c, xs, yr, y, ncomp, with_wave, s);
+        if (c->timing) c->tprod++;
+        SE_CUDA_CHECK(c, cudaGetLastError());
+        return SE_OK;
+    }
     if (c->overlap == 2 && (rc = real_part(s)) != SE_OK) return rc;
     if (c->overlap == 0 && (rc = fork_real()) != SE_OK) return rc;
     if (with_wave) launch_wave_spread<T>(c, xs, s, ncomp);
@@ -631,10 +663,12 @@ static int apply_ff(se_ctx *c, int ncomp, const TO *x, TO *y)
 int se::se_apply_internal(se_ctx *c, int ncomp, const void *x, void *y, int dtype, int prec)
 {
     if (!c->have_config) return set_error(c, SE_ERR_STATE, "se_set_config must be called first");
+    if (c->size_mode == 3 && prec == 2) prec = 1;     // the wave-space approach runs in FP32 or FP64
     int rc = ensure_support(c, prec);
     if (rc != SE_OK) return rc;
     rc = ensure_grids(c, prec);
     if (rc != SE_OK) return rc;
+    if (c->size_mode == 3 && (rc = ensure_ws_grids(c, prec)) != SE_OK) return rc;
     if (prec == 2) {
         return dtype == SE_F64 ? apply_ff<double>(c, ncomp, (const double *)x, (double *)y)
                                : apply_ff<float>(c, ncomp, (const float *)x, (float *)y);

@@ -73,6 +73,11 @@ struct Buffers {
     void *spec_o[3] = {};        // [M][M][Mh][8] complex T
     void *grid_o[3] = {};        // [M^3][8] T gathered grids
     void *tw[3] = {};            // [M] complex T twiddles
+    // the wave-space approach of SE_OPT_SIZE_MODE 3 (FP32 and FP64 only)
+    void *ws_grid[2] = {};       // [5][M^3][4] T spread grids, then the gathered grids
+    void *ws_spec_a[2] = {};     // [5][M][M][Mh][4] complex T forward spectra
+    void *ws_spec_b[2] = {};     // [5][M][M][Mh][4] complex T output spectra
+    size_t ws_M[2] = {0, 0};
     // stored real-space pairs (Sec. 3.3): CSR over targets in cell order
     int *pair_off = nullptr;     // [N + 1]
     int *pair_j = nullptr;       // [npairs]
@@ -145,6 +150,10 @@ struct se_ctx {
     double ktab_kmax = 0;
     double sp_fit[3] = {0, 0, 0};       // fitted lambda_T(k) = A / k^2 + l0, and lambda_B
     double sp_rho = 0;                  // largest eigenvalue of the correction before capping
+    double spc_theta = 0, spc_ka = 0;   // the damping and cutoff spc was built with (0: the options)
+    int pc_stalls = 0;                  // solves whose spectral correction stalled and fell back to the block
+    bool lp_ready = false;              // the learned damping and cutoff for this configuration and weights
+    double lp_theta = 0, lp_ka = 0;
     se::FftPlan plan{};
     se::Buffers b;
     size_t alloc_N = 0;
@@ -177,8 +186,9 @@ template <typename T>
 int build_pair_table(se_ctx *c);
 bool launch_real_ff(se_ctx *c, const ff *xs, ff *yreal, cudaStream_t s, int ncomp);
 int build_pair_table_ff(se_ctx *c);
-// se_learned.cu: per-particle learned corrections [N][4] (caller order)
-int learned_corrections(se_ctx *c, double *d_dev);
+// se_learned.cu: the damping theta and cutoff k_c <a> of the spectral correction that the
+// learned network predicts for the configuration (mean of its per-particle outputs)
+int learned_spectral_params(se_ctx *c, double *theta, double *ka);
 // se_solve.cu
 void convert_f2d(int n, const float *x, double *y, cudaStream_t s);
 // exclusive scan of n ints into out[0..n] on stream s
@@ -194,6 +204,9 @@ void free_spectral(se_ctx *c);
 template <typename T, typename TO>
 void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int ncomp, int with_wave,
                            cudaStream_t s);
+// the wave-space approach (SE_OPT_SIZE_MODE 3): spread, transforms, k-space step, gather + combine
+template <typename T, typename TO>
+void launch_wave_ws(se_ctx *c, const T *xs, const T *yreal, TO *y, int ncomp, int with_wave, cudaStream_t s);
 template <typename T>
 void setup_support(se_ctx *c, cudaStream_t s);
 void make_twiddles(se_ctx *c, int prec);

@@ -1,22 +1,29 @@
-// Learned correction to the block-diagonal far-field preconditioner.
+// Learned preconditioner (SE_PRECOND_LEARNED): a network that reads every particle's
+// radius and its neighbours inside rc and sets the long-wavelength correction of the
+// block-diagonal far-field preconditioner of Sec. 4.2.
 //
 // Per particle i the network reads rotation- and permutation-invariant features of
-// its radius and of its neighbours inside rc,
-//   f = [ sum_j b_k(h_ij) (k < 7),  sum_j b_k(h_ij) a_j/a_i (k < 7),  a_i / <a>,  n_i / 32 ],
-//   h_ij = r_ij / (a_i + a_j),  b_k(h) = exp(-((h - c_k)/0.35)^2),  c = 1, 1.25, 1.5, 2, 2.5, 3, 4,
-// and outputs four dimensionless corrections d = (d_F, d_T, d_S, d_P) of the block's
-// isotropic parts; the corrected block is
-//   B_i + diag(d_F/(6 pi eta a) I3, d_T/(8 pi eta a^3) I3, d_S 3/(20 pi eta a^3) I5, d_P 3/(16 pi eta a^3)).
-// It is trained to reproduce the isotropic parts of [M^{-1}]_ii^{-1} - [M]_ii, the
-// change that turns the block of M into the inverse of the block of M^{-1}, on
-// configurations and blocks the method itself generates (train_pc.py).  When the
-// corrected block is not invertible or not finite the plain block is used.
+// its radius and of its neighbours inside rc, and one feature of the whole box,
+//   f = [ sum_j b_k(h_ij) (k < 7),  sum_j b_k(h_ij) a_j/a_i (k < 7),  a_i / <a>,  ln(L / <a>) / 5 ],
+//   h_ij = r_ij / (a_i + a_j),  b_k(h) = exp(-((h - c_k)/0.35)^2),  c = 1, 1.25, 1.5, 2, 2.5, 3, 4.
+// Its outputs, averaged over the particles (a permutation-invariant set function of
+// the configuration), are the damping theta and the cutoff k_c <a> of the spectral
+// correction P^-1 = B - S C S (se_solve.cu): those two numbers decide how many GMRES
+// iterations the long-wavelength collective modes cost, and a value that is too large
+// for a configuration stalls GMRES.  The network is trained on the iteration counts of
+// solves the method itself runs over a grid of (theta, k_c <a>) on generated
+// configurations (train_pc.py).  Outputs 2 and 3 are unused (trained to zero).
+// theta is clamped to [0.5, 0.985] and k_c <a> to [0.4, 1.5]; the plain block
+// preconditioner stays the fallback (no weights, sheared cells, and every solve whose
+// corrected cycle fails to halve the residual).
 //
 // Network: 16 -> 64 -> 64 -> 4, tanh, FP32, standardised inputs and outputs.
 // Packed parameters (float): W1[64][16] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]
 // (5508 trained values), then mu[16] sd[16] (input standardisation) and os[4]
 // (output scale), 5544 floats in all.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "se_internal.cuh"
 
@@ -35,8 +42,8 @@ struct WOff {
 };
 
 // features of every particle (written in caller order) from the stored pair lists
-__global__ void features_kernel(int N, double amean, const int *off, size_t np, const int *pj, const float *px,
-                                const double *px64, const double *rad, const int *perm, float *feat)
+__global__ void features_kernel(int N, double amean, double L, const int *off, size_t np, const int *pj,
+                                const float *px, const double *px64, const double *rad, const int *perm, float *feat)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -58,7 +65,7 @@ __global__ void features_kernel(int N, double amean, const int *off, size_t np, 
         }
     }
     f[14] = (float)(ai / amean);
-    f[15] = (float)(off[i + 1] - off[i]) / 32.0f;
+    f[15] = (float)(log(L / amean) / 5.0);
     float *o = feat + (size_t)perm[i] * kF;
     for (int q = 0; q < kF; ++q) o[q] = f[q];
 }
@@ -175,14 +182,19 @@ __global__ void adam_kernel(float *w, float *m, float *v, const float *g, int st
 
 }  // namespace
 
-// ---- used by se_solve: per-particle corrections d (caller order) for the context
-int learned_corrections(se_ctx *c, double *d_dev /*[N][4]*/)
+// ---- used by se_solve: the spectral correction's damping and cutoff for the configuration
+int learned_spectral_params(se_ctx *c, double *theta, double *ka)
 {
+    if (c->lp_ready) {
+        *theta = c->lp_theta;
+        *ka = c->lp_ka;
+        return SE_OK;
+    }
     cudaStream_t s = c->stream;
     const int N = (int)c->N;
     if (!c->b.pair_off || (!c->pairs_ok[0] && !c->pairs_ok[1])) {
-        c->err = "learned preconditioner needs the stored pair table";
-        return SE_ERR_STATE;
+        const int r = c->precision == 1 ? build_pair_table<double>(c) : build_pair_table<float>(c);
+        if (r != SE_OK) return r;
     }
     float *feat = nullptr, *y = nullptr;
     if (cudaMalloc(&feat, (size_t)N * kF * sizeof(float)) != cudaSuccess ||
@@ -197,20 +209,35 @@ int learned_corrections(se_ctx *c, double *d_dev /*[N][4]*/)
     double am = 0;
     for (double v : r) am += v;
     am /= N;
-    features_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, am, c->b.pair_off, c->npairs, c->b.pair_j,
+    features_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, am, c->L, c->b.pair_off, c->npairs, c->b.pair_j,
                                                     c->pairs_ok[0] ? (const float *)c->b.pair_x[0] : nullptr,
                                                     c->pairs_ok[0] ? nullptr : (const double *)c->b.pair_x[1],
                                                     c->b.rad, c->b.perm, feat);
     mlp_forward_kernel<<<(N + 127) / 128, 128, 0, s>>>(c->b.mlp_w, feat, N, y);
-    convert_f2d(N * kO, y, d_dev, s);
-    c->launches += 3;
-    cudaError_t e = cudaStreamSynchronize(s);
+    c->launches += 2;
+    std::vector<float> yh((size_t)N * kO);
+    cudaError_t e = cudaMemcpyAsync(yh.data(), y, yh.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(feat);
     cudaFree(y);
     if (e != cudaSuccess) {
-        c->err = std::string("learned corrections: ") + cudaGetErrorString(e);
+        c->err = std::string("learned preconditioner: ") + cudaGetErrorString(e);
         return SE_ERR_CUDA;
     }
+    double t = 0, k = 0;
+    for (int i = 0; i < N; ++i) {
+        t += yh[(size_t)i * kO];
+        k += yh[(size_t)i * kO + 1];
+    }
+    t /= N;
+    k /= N;
+    if (!std::isfinite(t)) t = 0.5;
+    if (!std::isfinite(k)) k = 0.9;
+    c->lp_theta = std::min(0.985, std::max(0.5, t));
+    c->lp_ka = std::min(1.5, std::max(0.4, k));
+    c->lp_ready = true;
+    *theta = c->lp_theta;
+    *ka = c->lp_ka;
     return SE_OK;
 }
 
@@ -238,7 +265,7 @@ extern "C" int se_set_learned_weights(se_ctx *c, const float *w, int nw)
     }
     SE_CUDA_CHECK(c, cudaMemcpy(c->b.mlp_w, w, kNW * sizeof(float), cudaMemcpyHostToDevice));
     c->have_mlp = true;
-    c->pc_ready = false;
+    c->lp_ready = false;
     return SE_OK;
 }
 
@@ -257,7 +284,7 @@ extern "C" int se_learned_features(se_ctx *c, float *feat)
     double am = 0;
     for (double v : r) am += v;
     am /= N;
-    features_kernel<<<(N + 127) / 128, 128, 0, c->stream>>>(N, am, c->b.pair_off, c->npairs, c->b.pair_j,
+    features_kernel<<<(N + 127) / 128, 128, 0, c->stream>>>(N, am, c->L, c->b.pair_off, c->npairs, c->b.pair_j,
                                                              c->pairs_ok[0] ? (const float *)c->b.pair_x[0] : nullptr,
                                                              c->pairs_ok[0] ? nullptr : (const double *)c->b.pair_x[1],
                                                              c->b.rad, c->b.perm, feat);

@@ -130,27 +130,18 @@ __global__ void block_apply_kernel(int N, int nc, const double *Binv, const doub
 // (the diagonal block M_ii), shifted to alpha I + beta M_ii (the diagonal block of the
 // operator alpha I + beta M; alpha = 0, beta = 1 for M itself), inverted by Gauss-Jordan
 // elimination with partial pivoting.  Sorted particle k is stored at caller index
-// perm[k].  Singular blocks fall back to the shifted isolated-sphere inverse.
-// `corr` (may be null, caller order [N][4]): learned dimensionless corrections of the
-// isotropic parts, each scaled by the isolated-sphere mobility of its block.  A learned
-// block that cannot be inverted falls back to the plain block (counted in *fallbacks).
-// mixed = 1 (the rigid-particle system of se_rigid_solve, nc = 11): the columns of the
-// force and torque unknowns are replaced by -I (they hold U, Omega there).
+// perm[k].  Singular blocks fall back to the shifted isolated-sphere inverse (counted in
+// *fallbacks).  mixed = 1 (the rigid-particle system of se_rigid_solve, nc = 11): the
+// columns of the force and torque unknowns are replaced by -I (they hold U, Omega there).
 __global__ void block_build_kernel(int N, int nc, double eta, const double *rad, const int *perm,
-                                   const double *C /*[3][12][12]*/, const double *corr, double alpha,
-                                   double beta, int mixed, double *Binv, int *fallbacks)
+                                   const double *C /*[3][12][12]*/, double alpha, double beta, int mixed,
+                                   double *Binv, int *fallbacks)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     const double a = rad[k], a2 = a * a;
     double A[kNC][2 * kNC];
     const double pi = kPi;
-    const double *d = corr ? corr + (size_t)perm[k] * 4 : nullptr;
-    bool use_corr = d != nullptr;
-    if (use_corr)
-        for (int q = 0; q < 4; ++q) use_corr &= isfinite(d[q]) != 0;
-    if (d && !use_corr) atomicAdd(fallbacks, 1);
-retry:
     for (int r = 0; r < nc; ++r) {
         for (int q = 0; q < nc; ++q) {
             A[r][q] = C[r * kNC + q] + a2 * C[kNC * kNC + r * kNC + q] + a2 * a2 * C[2 * kNC * kNC + r * kNC + q];
@@ -159,8 +150,7 @@ retry:
         const double iso = r < 3 ? 1.0 / (6 * pi * eta * a)
                          : r < 6 ? 1.0 / (8 * pi * eta * a * a2)
                          : r < 11 ? 3.0 / (20 * pi * eta * a * a2) : 3.0 / (16 * pi * eta * a * a2);
-        const double dc = use_corr ? d[r < 3 ? 0 : r < 6 ? 1 : r < 11 ? 2 : 3] : 0.0;
-        A[r][r] += iso * (1.0 + dc);
+        A[r][r] += iso;
         for (int q = 0; q < nc; ++q) A[r][q] *= beta;
         A[r][r] += alpha;
         if (mixed)
@@ -183,20 +173,8 @@ retry:
                 for (int q = 0; q < 2 * nc; ++q) A[r][q] -= f * A[col][q];
         }
     }
-    if (use_corr) {
-        bool fin = ok;
-        for (int r = 0; r < nc && fin; ++r)
-            for (int q = 0; q < nc; ++q) fin &= isfinite(A[r][nc + q]) != 0;
-        // the corrected block must stay positive on its diagonal (a mobility)
-        for (int r = 0; r < nc && fin; ++r) fin &= A[r][nc + r] > 0;
-        if (!fin) {
-            atomicAdd(fallbacks, 1);
-            use_corr = false;
-            ok = true;
-            goto retry;
-        }
-    }
     double *out = Binv + (size_t)perm[k] * nc * nc;
+    bool fell_back = false;
     for (int r = 0; r < nc; ++r)
         for (int q = 0; q < nc; ++q) {
             double v = A[r][nc + q];
@@ -204,9 +182,11 @@ retry:
                 const double mob = r < 3 ? 1.0 / (6 * pi * eta * a) : r < 6 ? 1.0 / (8 * pi * eta * a * a2)
                                  : r < 11 ? 3.0 / (20 * pi * eta * a * a2) : 3.0 / (16 * pi * eta * a * a2);
                 v = r == q ? (mixed && r < 6 ? -1.0 : 1.0 / (alpha + beta * mob)) : 0.0;
+                fell_back = true;
             }
             out[r * nc + q] = v;
         }
+    if (fell_back) atomicAdd(fallbacks, 1);
 }
 
 }  // namespace
@@ -312,10 +292,10 @@ static int build_precond(se_ctx *c, int ncomp, bool learned)
     return build_blocks(c, ncomp, learned, 0.0, 1.0);
 }
 
-// the inverse blocks of alpha I + beta M_ii from the fitted coefficients (learned:
-// with the network's corrections; only for alpha = 0, beta = 1)
+// the inverse blocks of alpha I + beta M_ii from the fitted coefficients
 static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double beta, int mixed)
 {
+    (void)learned;
     cudaStream_t s = c->stream;
     const int N = (int)c->N;
     if (c->b.pc_inv) cudaFree(c->b.pc_inv);
@@ -326,31 +306,16 @@ static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double
         c->err = "preconditioner allocation failed";
         return SE_ERR_NOMEM;
     }
-    double *corr = nullptr;
     int *dfb = nullptr;
     if (cudaMalloc(&dfb, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return SE_ERR_NOMEM; }
     cudaMemsetAsync(dfb, 0, sizeof(int), s);
-    if (learned) {
-        if (cudaMalloc(&corr, (size_t)N * 4 * sizeof(double)) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFree(dfb);
-            return SE_ERR_NOMEM;
-        }
-        const int r = learned_corrections(c, corr);
-        if (r != SE_OK) {
-            cudaFree(dfb);
-            cudaFree(corr);
-            return r;
-        }
-    }
-    block_build_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->eta, c->b.rad, c->b.perm, c->b.pc_C, corr, alpha,
+    block_build_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, c->eta, c->b.rad, c->b.perm, c->b.pc_C, alpha,
                                                        beta, mixed, c->b.pc_inv, dfb);
     c->launches++;
     int fb = 0;
     cudaMemcpyAsync(&fb, dfb, sizeof(int), cudaMemcpyDeviceToHost, s);
     const cudaError_t e = cudaStreamSynchronize(s);
     cudaFree(dfb);
-    if (corr) cudaFree(corr);
     if (e != cudaSuccess) {
         c->err = std::string("preconditioner blocks: ") + cudaGetErrorString(e);
         return SE_ERR_CUDA;
@@ -358,7 +323,7 @@ static int build_blocks(se_ctx *c, int ncomp, bool learned, double alpha, double
     c->pc_fallbacks = fb;
     c->pc_ready = true;
     c->pc_ncomp = ncomp;
-    c->pc_kind = learned ? SE_PRECOND_LEARNED : SE_PRECOND_BLOCK;
+    c->pc_kind = SE_PRECOND_BLOCK;
     c->pc_alpha = alpha;
     c->pc_beta = beta;
     c->pc_mixed = mixed;
@@ -495,7 +460,10 @@ void free_spectral(se_ctx *c)
 // largest eigenvalue allowed for the correction C
 constexpr double kCMax = 0.97;
 
-static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
+// theta_in, ka_in: the damping and cutoff k_c <a> (<= 0: the options SE_OPT_PC_THETA /
+// SE_OPT_PC_KA and their defaults)
+static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w, double theta_in = 0,
+                          double ka_in = 0)
 {
     cudaStream_t s = c->stream;
     const int N = (int)c->N;
@@ -504,10 +472,14 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w)
     SE_CUDA_CHECK(c, cudaMemcpy(rad.data(), c->b.rad, N * sizeof(double), cudaMemcpyDeviceToHost));
     double asum = 0, amin = rad[0], amax = rad[0];
     for (double a : rad) { asum += a; amin = std::min(amin, a); amax = std::max(amax, a); }
-    // damping: measured robust at 0.98 on monodisperse suspensions, 0.9 with size spread
-    const double theta = c->sp_theta > 0 ? c->sp_theta : (amax - amin <= 0.01 * amax ? 0.98 : 0.9);
+    // damping: 0.98 on monodisperse suspensions, 0.9 with size spread, unless given
+    const double theta = theta_in > 0 ? theta_in
+                                      : (c->sp_theta > 0 ? c->sp_theta : (amax - amin <= 0.01 * amax ? 0.98 : 0.9));
+    const double ka = ka_in > 0 ? ka_in : c->sp_ka;
+    c->spc_theta = theta_in;
+    c->spc_ka = ka_in;
     const double aref = asum / N, L = c->L, k1 = 2 * kPi / L;
-    double kc = c->sp_ka / aref;
+    double kc = ka / aref;
     if (kc <= 1.5 * k1) return SE_OK;                       // box too small: no long waves to correct
     // coarse grid with Nyquist wave number >= 2.5 k_c
     int Mc = 16;
@@ -743,22 +715,33 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
     if (precond == SE_PRECOND_SPECTRAL && c->shear != 0) precond = SE_PRECOND_BLOCK;
     double *ms = c->b.work64 + 5 * n;     // the masked vector P_S v of the mixed operator
 
-    // the learned correction needs trained weights; without them it is the plain block
-    const int kind = precond == SE_PRECOND_LEARNED && c->have_mlp ? SE_PRECOND_LEARNED : SE_PRECOND_BLOCK;
+    // the learned preconditioner: the spectral correction with the damping and cutoff
+    // the network predicts for this configuration; without weights (or where the
+    // spectral correction does not apply) it is the plain block preconditioner
+    double l_theta = 0, l_ka = 0;
+    if (precond == SE_PRECOND_LEARNED) {
+        if (c->have_mlp && c->shear == 0 && !shifted && !mixed) {
+            rc = learned_spectral_params(c, &l_theta, &l_ka);
+            if (rc != SE_OK) return rc;
+            precond = SE_PRECOND_SPECTRAL;
+        } else {
+            precond = SE_PRECOND_BLOCK;
+        }
+    }
     if (precond != SE_PRECOND_NONE) {
         if (!c->pc_ready || c->pc_ncomp != ncomp) {
-            rc = build_precond(c, ncomp, kind == SE_PRECOND_LEARNED);
+            rc = build_precond(c, ncomp, false);
             if (rc != SE_OK) return rc;
             free_spectral(c);
         }
-        if (c->pc_kind != kind || c->pc_alpha != alpha || c->pc_beta != beta || c->pc_mixed != mixed) {
-            rc = build_blocks(c, ncomp, kind == SE_PRECOND_LEARNED, alpha, beta, mixed);
+        if (c->pc_kind != SE_PRECOND_BLOCK || c->pc_alpha != alpha || c->pc_beta != beta || c->pc_mixed != mixed) {
+            rc = build_blocks(c, ncomp, false, alpha, beta, mixed);
             if (rc != SE_OK) return rc;
             free_spectral(c);
         }
     }
-    if (precond == SE_PRECOND_SPECTRAL && !c->spc) {
-        rc = build_spectral(c, ncomp, gm, z, w);
+    if (precond == SE_PRECOND_SPECTRAL && (!c->spc || c->spc_theta != l_theta || c->spc_ka != l_ka)) {
+        rc = build_spectral(c, ncomp, gm, z, w, l_theta, l_ka);
         if (rc != SE_OK) return rc;
     }
     auto Pinv = [&](const double *v, double *out) -> int {
@@ -812,6 +795,12 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
         // accuracy; SE_OPT_RESIDUAL) when the Krylov products run in FP32
         const int res_prec = c->precision == 0 ? c->res_precision : c->precision;
         double rel_wp = 1.0;                  // the previous working-precision restart residual
+        // A restart cycle of the spectral preconditioner that fails to halve the residual
+        // (a damping too strong for this configuration makes the corrected operator nearly
+        // singular on some modes) switches the remaining cycles to the plain block
+        // preconditioner; flexible GMRES allows the change between cycles.
+        double rel_cycle = -1.0;              // residual at the start of the last cycle
+        int prods_cycle = 0;
         for (;;) {
             bool exact = fp64_res;            // r is the FP64 residual (or b itself)
             if (x_zero) {
@@ -839,6 +828,13 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
             }
             if (!exact) rel_wp = rel;
             if (rel <= rtol || prods >= maxit) break;
+            if (precond == SE_PRECOND_SPECTRAL && rel_cycle > 0 && prods - prods_cycle >= std::min(m, 30) &&
+                rel > 0.5 * rel_cycle && rel > 10 * rtol) {
+                precond = SE_PRECOND_BLOCK;
+                c->pc_stalls++;
+            }
+            rel_cycle = rel;
+            prods_cycle = prods;
             axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0 / beta, r, 0.0, r, V);
             c->launches++;
             std::fill(g.begin(), g.end(), 0.0);

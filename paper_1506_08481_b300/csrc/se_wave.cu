@@ -1882,6 +1882,8 @@ template void launch_gather_combine<ff, double>(se_ctx *, const ff *, const ff *
 
 }  // namespace se
 
+#include "se_wave_ws.cuh"
+
 // ---------------------------------------------------------------- persistent batched product
 //
 // The products of a batch of independent boxes (own N, M, P, xi, rc each) in ONE
@@ -1906,12 +1908,18 @@ namespace {
 
 constexpr int kPersistPhases = 8;
 constexpr int kPersistThreads = 256;
+// The real-space, FFT and gather items each take kSubItems of the per-box kernels' CTA
+// tasks in turn, so a claim (an atomic round trip) and a completion count are paid once
+// per few tasks: small boxes have many short tasks.
+constexpr int kSubItems = 4;
 
 struct BoxDesc {
     SeParams p;
     FftPlan plan;
     int N, co, s16, with_wave, with_real, with_self;
-    int nreal_items;                  // phase-1 items of the real-space sum (8 targets each)
+    int nreal_items;                  // real-space sub-items (8 targets each), also the gather's
+    int nreal_groups;                 // phase-1 items of the real-space sum (kSubItems sub-items each)
+    int nsub[kPersistPhases];         // sub-items of the FFT phases 2..6
     int prio;                         // 0..1023, larger for boxes with more work
     float cnorm, twopiL, i4x2, ecoef;
     const void *x;
@@ -2082,19 +2090,23 @@ __global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(co
                 break;
             }
             case 1:
-                if (it < d.nreal_items) {
-                    const int i = it * (kPersistThreads / 32) + warp;
-                    if (d.with_real) {
-                        real_table_body<float, NCOMP>(i, lane, d.N, d.pair_off, d.npairs, d.pair_j, d.pair_x,
-                                                      d.pair_c, d.xs, d.yreal);
-                    } else if (i < d.N && lane < kNC) {
-                        d.yreal[(size_t)i * kNC + lane] = 0.f;
+                if (it < d.nreal_groups) {
+                    for (int u = 0; u < kSubItems; ++u) {
+                        const int sub = it * kSubItems + u;
+                        if (sub >= d.nreal_items) break;
+                        const int i = sub * (kPersistThreads / 32) + warp;
+                        if (d.with_real) {
+                            real_table_body<float, NCOMP>(i, lane, d.N, d.pair_off, d.npairs, d.pair_j, d.pair_x,
+                                                          d.pair_c, d.xs, d.yreal);
+                        } else if (i < d.N && lane < kNC) {
+                            d.yreal[(size_t)i * kNC + lane] = 0.f;
+                        }
                     }
                 } else {
                     const int grp = threadIdx.x >> 6, tid = threadIdx.x & 63;
                     const int nt = d.p.ntile;
                     const int ntiles = d.s16 ? nt * nt * ((nt + 1) / 2) : nt * nt * nt;
-                    const int tile = (it - d.nreal_items) * 4 + grp;
+                    const int tile = (it - d.nreal_groups) * 4 + grp;
                     if (tile < ntiles) {
                         auto sync = [grp] { bar_named(1 + grp, 64); };
                         if (d.s16) {
@@ -2111,53 +2123,68 @@ __global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(co
                     }
                 }
                 break;
-            case 2:
-                fft_x_fwd_body<float>(it, smraw, d.plan, d.tw, d.grid_f, d.spec_f);
-                break;
-            case 3: {
-                const int nbx = (Mh + 3) / 4;
-                fft_y_body<float, 4, false>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_f);
-                break;
-            }
-            case 4: {
-                const int nbx = (Mh + 3) / 4;
-                if (d.co == 8)
-                    fft_z_scale_body<float, 8, 4>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_f, d.spec_o,
-                                                  d.cnorm, d.twopiL, d.i4x2, d.ecoef);
-                else
-                    fft_z_scale_body<float, 4, 4>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_f, d.spec_o,
-                                                  d.cnorm, d.twopiL, d.i4x2, d.ecoef);
-                break;
-            }
-            case 5: {
-                if (d.co == 8) {
-                    const int nbx = (Mh + 1) / 2;
-                    fft_y_body<float, 8, true>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_o);
-                } else {
-                    const int nbx = (Mh + 3) / 4;
-                    fft_y_body<float, 4, true>(it % nbx, it / nbx, smraw, d.plan, d.tw, d.spec_o);
+            case 7: {
+                float4 *Wz = reinterpret_cast<float4 *>(smraw) + warp * 32;
+                int *Zi = reinterpret_cast<int *>(smraw + (kPersistThreads / 32) * 32 * sizeof(float4)) + warp * 32;
+                const int *order = d.with_wave ? d.tile_perm : nullptr;
+                for (int u = 0; u < kSubItems; ++u) {
+                    const int sub = it * kSubItems + u;
+                    if (sub >= d.nreal_items) break;
+                    __syncwarp();                 // the warp's tables are free again
+                    const int w_ = sub * (kPersistThreads / 32) + warp;
+                    if (d.co == 8)
+                        gather_body<float, TO, 8, NCOMP>(w_, lane, Wz, Zi, d.p, d.N, order, d.sup_base, d.sup_s0,
+                                                         d.sup_w, d.rad, d.selfc, d.perm, d.grid_o, d.xs, d.yreal,
+                                                         (TO *)d.y, NCOMP, d.with_wave, d.with_self);
+                    else
+                        gather_body<float, TO, 4, NCOMP>(w_, lane, Wz, Zi, d.p, d.N, order, d.sup_base, d.sup_s0,
+                                                         d.sup_w, d.rad, d.selfc, d.perm, d.grid_o, d.xs, d.yreal,
+                                                         (TO *)d.y, NCOMP, d.with_wave, d.with_self);
                 }
                 break;
             }
-            case 6:
-                if (d.co == 8) fft_x_inv_body<float, 8>(it, smraw, d.plan, d.tw, d.spec_o, d.grid_o);
-                else fft_x_inv_body<float, 4>(it, smraw, d.plan, d.tw, d.spec_o, d.grid_o);
+            default:
+                // FFT phases: kSubItems CTA tasks of the per-box pass in turn
+                for (int u = 0; u < kSubItems; ++u) {
+                    const int sub = it * kSubItems + u;
+                    if (sub >= d.nsub[ph]) break;
+                    if (u > 0) __syncthreads();   // the previous task's shared buffers are free
+                    switch (ph) {
+                    case 2:
+                        fft_x_fwd_body<float>(sub, smraw, d.plan, d.tw, d.grid_f, d.spec_f);
+                        break;
+                    case 3: {
+                        const int nbx = (Mh + 3) / 4;
+                        fft_y_body<float, 4, false>(sub % nbx, sub / nbx, smraw, d.plan, d.tw, d.spec_f);
+                        break;
+                    }
+                    case 4: {
+                        const int nbx = (Mh + 3) / 4;
+                        if (d.co == 8)
+                            fft_z_scale_body<float, 8, 4>(sub % nbx, sub / nbx, smraw, d.plan, d.tw, d.spec_f,
+                                                          d.spec_o, d.cnorm, d.twopiL, d.i4x2, d.ecoef);
+                        else
+                            fft_z_scale_body<float, 4, 4>(sub % nbx, sub / nbx, smraw, d.plan, d.tw, d.spec_f,
+                                                          d.spec_o, d.cnorm, d.twopiL, d.i4x2, d.ecoef);
+                        break;
+                    }
+                    case 5: {
+                        if (d.co == 8) {
+                            const int nbx = (Mh + 1) / 2;
+                            fft_y_body<float, 8, true>(sub % nbx, sub / nbx, smraw, d.plan, d.tw, d.spec_o);
+                        } else {
+                            const int nbx = (Mh + 3) / 4;
+                            fft_y_body<float, 4, true>(sub % nbx, sub / nbx, smraw, d.plan, d.tw, d.spec_o);
+                        }
+                        break;
+                    }
+                    default:
+                        if (d.co == 8) fft_x_inv_body<float, 8>(sub, smraw, d.plan, d.tw, d.spec_o, d.grid_o);
+                        else fft_x_inv_body<float, 4>(sub, smraw, d.plan, d.tw, d.spec_o, d.grid_o);
+                        break;
+                    }
+                }
                 break;
-            default: {
-                float4 *Wz = reinterpret_cast<float4 *>(smraw) + warp * 32;
-                int *Zi = reinterpret_cast<int *>(smraw + (kPersistThreads / 32) * 32 * sizeof(float4)) + warp * 32;
-                const int w_ = it * (kPersistThreads / 32) + warp;
-                const int *order = d.with_wave ? d.tile_perm : nullptr;
-                if (d.co == 8)
-                    gather_body<float, TO, 8, NCOMP>(w_, lane, Wz, Zi, d.p, d.N, order, d.sup_base, d.sup_s0, d.sup_w,
-                                                     d.rad, d.selfc, d.perm, d.grid_o, d.xs, d.yreal, (TO *)d.y,
-                                                     NCOMP, d.with_wave, d.with_self);
-                else
-                    gather_body<float, TO, 4, NCOMP>(w_, lane, Wz, Zi, d.p, d.N, order, d.sup_base, d.sup_s0, d.sup_w,
-                                                     d.rad, d.selfc, d.perm, d.grid_o, d.xs, d.yreal, (TO *)d.y,
-                                                     NCOMP, d.with_wave, d.with_self);
-                break;
-            }
             }
         }
         // the item's writes are visible device-wide before it counts as finished
@@ -2208,7 +2235,7 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
         se_ctx *c = box[b];
         const int with_real = (c->parts & 1) ? 1 : 0, with_wave = (c->parts & 2) ? 1 : 0;
         if (c->precision != 0 || !c->support_ok[0] || !c->b.grid_f[0] || (with_real && !c->pairs_ok[0]) ||
-            c->ktab_on || c->size_mode == 2) {
+            c->ktab_on || c->size_mode >= 2) {
             err = "box " + std::to_string(b) + ": the persistent batch needs FP32 products, the stored pair "
                   "table (run the batch once without it first) and the real-space or hybrid size approach";
             return SE_ERR_STATE;
@@ -2253,15 +2280,18 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
         const int M = p.M, Mh = M / 2 + 1, nt = p.ntile;
         const int ntiles = d.s16 ? nt * nt * ((nt + 1) / 2) : nt * nt * nt;
         const int nw = with_wave;
+        // CTA tasks of the per-box kernels; FFT and real-space/gather items take kSubItems each
+        const int sub[kPersistPhases] = {0, 0, nw * M * M / 8, nw * ((Mh + 3) / 4) * M, nw * ((Mh + 3) / 4) * M,
+                                         nw * (d.co == 8 ? (Mh + 1) / 2 : (Mh + 3) / 4) * M,
+                                         nw * M * M / (d.co == 8 ? 4 : 8), 0};
+        for (int ph = 0; ph < kPersistPhases; ++ph) d.nsub[ph] = sub[ph];
+        d.nreal_groups = (d.nreal_items + kSubItems - 1) / kSubItems;
+        auto groups = [](int n) { return (n + kSubItems - 1) / kSubItems; };
         const int items[kPersistPhases] = {
             (d.N + kPersistThreads - 1) / kPersistThreads,
-            d.nreal_items + nw * (ntiles + 3) / 4,
-            nw * M * M / 8,
-            nw * ((Mh + 3) / 4) * M,
-            nw * ((Mh + 3) / 4) * M,
-            nw * (d.co == 8 ? (Mh + 1) / 2 : (Mh + 3) / 4) * M,
-            nw * M * M / (d.co == 8 ? 4 : 8),
-            d.nreal_items};
+            d.nreal_groups + nw * (ntiles + 3) / 4,
+            groups(sub[2]), groups(sub[3]), groups(sub[4]), groups(sub[5]), groups(sub[6]),
+            d.nreal_groups};
         for (int ph = 0; ph < kPersistPhases; ++ph) cnt[(size_t)b * kPersistPhases + ph] = items[ph];
         work[b] = (double)d.N * p.P * p.P * p.P + (double)M * M * M;
         smem = std::max(smem, fft_smem_bytes<float2>(M, fft_nl<float>()));

@@ -212,37 +212,51 @@ def candidates(L: float, N: int, tol: float, M_max: int = 384, supports=None, a_
     return out
 
 
-def autotune(cfg, tol: float, ncomp: int = 3, precision: int = 0, max_candidates: int = 4, reps: int = 3,
-             supports=None):
-    """Time the cheapest few candidate parameter sets (and both particle-size modes) for a
-    configuration on the GPU and return (SeParams, size_mode, ms per product) of the fastest."""
+def autotune(cfg, tol: float, ncomp: int = 3, precision: int = 0, max_candidates: int = 3, reps: int = 3,
+             supports=None, fp32_tol: float | None = None, spreads=(0, 1), modes=(1, 0)):
+    """Time the cheapest few candidate parameter sets for a configuration on the GPU, each
+    with the particle-size modes `modes` and the spreading tile shapes `spreads`
+    (SE_OPT_SPREAD 0: 8 x 8 x 16 tiles where the grid has room, 1: 8^3 tiles), and return
+    (SeParams, size_mode, ms per product, {"spread": tile option}) of the fastest.  The
+    candidates meet the error model at tol (method) and fp32_tol (FP32 rounding)."""
     import torch
     from . import api
-    cands = sorted(candidates(cfg.L, cfg.N, tol, supports=supports, a_eff=effective_radius(cfg.rad),
-                              precision=precision),
-                   key=lambda s: s.M ** 3 * math.log2(s.M) * 0.5 + 0.1 * cfg.N * s.P ** 3
+    a_eff = effective_radius(cfg.rad)
+    out, seen = [], set()
+    for M in fft_sizes(16, 384):
+        try:
+            sp = choose(cfg.L, cfg.N, tol, P=None, M_max=M, M_min=M, a_eff=a_eff, precision=precision,
+                        fp32_tol=fp32_tol)
+        except ValueError:
+            continue
+        if (sp.M, sp.P) not in seen:
+            seen.add((sp.M, sp.P))
+            out.append(sp)
+    cands = sorted(out, key=lambda s: s.M ** 3 * math.log2(s.M) * 0.5 + 0.1 * cfg.N * s.P ** 3
                    + cfg.N ** 2 / cfg.L ** 3 * 4.19 * s.rc ** 3)[:max_candidates]
     x = torch.randn(cfg.N, ncomp, device="cuda", dtype=torch.float32 if precision == 0 else torch.float64)
     y = torch.empty_like(x)
     best = None
     for sp in cands:
-        for mode in (1, 0):
+        for mode in modes:
             ctx = api.Context()
             ctx.set_params(sp.xi, sp.M, sp.P, sp.rc)
             ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
             ctx.set_option(api.SE_OPT_SIZE_MODE, mode)
             ctx.set_option(api.SE_OPT_PRECISION, precision)
             ctx.set_config(cfg.pos, cfg.rad, cfg.L)
-            ctx.apply(x, y)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record()
-            for _ in range(reps):
+            for spread in spreads:
+                ctx.set_option(api.SE_OPT_SPREAD, spread)
                 ctx.apply(x, y)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / reps
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(reps):
+                    ctx.apply(x, y)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                if best is None or ms < best[2]:
+                    best = (sp, mode, ms, {"spread": spread})
             ctx.close()
-            if best is None or ms < best[2]:
-                best = (sp, mode, ms)
     return best

@@ -1,21 +1,28 @@
-"""Train the learned correction of the block-diagonal far-field preconditioner.
+"""Train the learned preconditioner: the network that sets the damping theta and the cutoff
+k_c <a> of the long-wavelength (spectral) correction of the block-diagonal far-field
+preconditioner.
 
-  python -m paper_1506_08481_b300.train_pc [--configs 200] [--n 96] [--epochs 400]
+  python -m paper_1506_08481_b300.train_pc [--configs 160] [--epochs 300]
 
-Training data come from the method itself: for each generated configuration (log-normal
-radii, mean 1, std 0.2, volume fraction 0.4) the dense F,T,S grand mobility is assembled
-column by column from FP64 Spectral Ewald products (se_mobility_apply), inverted, and the
-target of sphere i is the isotropic part of [M^-1]_ii^-1 - [M]_ii, made dimensionless by
-the isolated-sphere mobilities (the change that turns the plain block into the inverse of
-the diagonal block of M^-1).  Features come from se_learned_features; the network is
-trained with the library's kernels (se_mlp_grad, se_mlp_adam_step).  Writes
-learned_pc_weights.npy (SE_MLP_NW floats) and learned_pc_weights.json next to this file.
+Training data come from the method itself.  For each generated configuration (mono-, bi-
+and polydisperse suspensions, volume fractions 0.1-0.45, N from 1000 to 50000) the
+library solves M x = b (11 components, FP32 products with FP64 refinement, GMRES(100) to
+1e-6) with the spectral correction at every (theta, k_c <a>) of a grid and records the
+products each solve took (a damping too strong for the configuration stalls its cycles and
+falls back to the block preconditioner, which costs products).  The configuration's target
+is the pair with the fewest products, the smaller theta among ties (the safer one).
+Every particle of the configuration carries the target; the network's mean over the
+particles is its prediction for the configuration.  Features come from
+se_learned_features; the network is trained with the library's kernels (se_mlp_grad,
+se_mlp_adam_step).  Writes learned_pc_weights.npy (SE_MLP_NW floats) and
+learned_pc_weights.json (the data and the training record) next to this file.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import math
+import multiprocessing as mp
 import os
 import time
 
@@ -26,65 +33,97 @@ from . import api, inputs, params
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "learned_pc_weights.npy")
 NC = 11
+THETAS = (0.8, 0.85, 0.9, 0.93, 0.95, 0.97, 0.98)
+KAS = (0.6, 0.9)
 
 
-def dense_mobility(ctx, N):
-    import torch
-    n = N * NC
-    Mt = torch.empty(n, n, device="cuda", dtype=torch.float64)
-    e = torch.zeros(N, NC, device="cuda", dtype=torch.float64)
-    y = torch.empty_like(e)
-    for col in range(n):
-        e.view(-1)[col] = 1.0
-        ctx.apply(e, y)
-        Mt[col] = y.view(-1)
-        e.view(-1)[col] = 0.0
-    return Mt.T.contiguous()
+def config_spec(k: int, seed0: int):
+    """The k-th configuration of the training set: (kind, N, phi, radius parameter, seed)."""
+    rng = np.random.default_rng(seed0 + 7919 * k)
+    kind = ("mono", "bidisperse", "lognormal")[k % 3]
+    u = rng.uniform()
+    N = int(round(math.exp(math.log(1000) + u * (math.log(20000) - math.log(1000)))))
+    if k % 40 == 39:
+        N = 50000
+    phi = float(rng.uniform(0.1, 0.45 if kind == "mono" else 0.4))
+    par = {"mono": 1.0, "bidisperse": float(rng.choice([1.5, 2.0])), "lognormal": float(rng.uniform(0.1, 0.3))}[kind]
+    return kind, N, phi, par, seed0 + k
 
 
-def targets_for(ctx, cfg):
-    """Dimensionless isotropic corrections [N, 4] and features [N, 16]."""
-    import torch
-    M = dense_mobility(ctx, cfg.N)
-    Mi = torch.linalg.inv(M)
-    N = cfg.N
-    idx = torch.arange(N, device="cuda")
-    blk = lambda A: A.view(N, NC, N, NC)[idx, :, idx, :]          # diagonal blocks [N, 11, 11]
-    B = blk(M)
-    D = torch.linalg.inv(blk(Mi)) - B
-    a = torch.tensor(cfg.rad, device="cuda", dtype=torch.float64)
-    iso = torch.stack([1 / (6 * math.pi * a), 1 / (8 * math.pi * a ** 3), 3 / (20 * math.pi * a ** 3)], 1)
-    dF = torch.diagonal(D[:, 0:3, 0:3], dim1=1, dim2=2).mean(1)
-    dT = torch.diagonal(D[:, 3:6, 3:6], dim1=1, dim2=2).mean(1)
-    dS = torch.diagonal(D[:, 6:11, 6:11], dim1=1, dim2=2).mean(1)
-    Y = torch.stack([dF / iso[:, 0], dT / iso[:, 1], dS / iso[:, 2], torch.zeros_like(dF)], 1)
-    return Y.float(), ctx.learned_features()
+def make_config(spec):
+    kind, N, phi, par, seed = spec
+    rng = np.random.default_rng(seed)
+    if kind == "mono":
+        rad = np.ones(N)
+    elif kind == "bidisperse":
+        rad = inputs.radii_bidisperse(N, 1.0, par, 0.5, rng)
+    else:
+        rad = inputs.radii_lognormal(N, 1.0, par, rng)
+    L = inputs.box_side(rad, phi)
+    pos = inputs.positions_dense(rad, L, rng, sweeps=4)
+    return inputs.Config(f"{kind}_n{N}_phi{phi:.2f}_s{seed}", L, pos, rad)
 
 
-def make_context(cfg, tol=1e-7, M_max=64):
-    sp = params.choose(cfg.L, cfg.N, tol, M_max=M_max, a_eff=params.effective_radius(cfg.rad))
+def solve_context(cfg, tol=5e-7, M_max=128):
+    sp = params.choose(cfg.L, cfg.N, tol, M_max=M_max, a_eff=params.effective_radius(cfg.rad), precision=0)
     ctx = api.Context()
     ctx.set_params(sp.xi, sp.M, sp.P, sp.rc)
     ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
-    ctx.set_option(api.SE_OPT_PRECISION, 1)
+    ctx.set_option(api.SE_OPT_SIZE_MODE, 1)
+    ctx.set_option(api.SE_OPT_RESTART, 100)
     ctx.set_config(cfg.pos, cfg.rad, cfg.L)
     return ctx
 
 
-def build_dataset(nconf, n, seed0, phi=0.4, log=print):
+def products(ctx, b, precond, theta=0.0, ka=0.9, maxit=600):
+    """Products of one solve to 1e-6 (maxit + 1 if it did not converge)."""
+    ctx.set_option(api.SE_OPT_PC_THETA, theta)
+    ctx.set_option(api.SE_OPT_PC_KA, ka)
+    _, it, rel = ctx.solve(b, rtol=1e-6, maxit=maxit, precond=precond, allow_not_converged=True)
+    ctx.set_option(api.SE_OPT_PC_THETA, 0.0)
+    ctx.set_option(api.SE_OPT_PC_KA, 0.9)
+    return it if rel <= 1e-6 else maxit + 1
+
+
+def label(ctx, cfg, seed):
+    """Products on the (theta, k_c a) grid; the target pair; the block and default counts."""
     import torch
-    Xs, Ys = [], []
+    b = torch.tensor(np.random.default_rng(seed).standard_normal((cfg.N, NC)), device="cuda")
+    grid = {}
+    for th in THETAS:
+        for ka in KAS:
+            grid[(th, ka)] = products(ctx, b, api.SE_PRECOND_SPECTRAL, th, ka)
+    best = min(grid.values())
+    target = min((k for k, v in grid.items() if v <= best * 1.02), key=lambda k: (k[0], -k[1]))
+    return {"target": target, "grid": {f"{k[0]},{k[1]}": v for k, v in grid.items()},
+            "block": products(ctx, b, api.SE_PRECOND_BLOCK), "spectral_default": products(ctx, b, api.SE_PRECOND_SPECTRAL)}
+
+
+def build_dataset(specs, per_config=2000, log=print):
+    import torch
     t = time.time()
-    for c in range(nconf):
-        cfg = inputs.lognormal(seed=seed0 + c, n=n, phi=phi)
-        ctx = make_context(cfg)
-        Y, X = targets_for(ctx, cfg)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        cfgs = pool.map(make_config, specs)
+    log(f"  {len(cfgs)} configurations generated in {time.time() - t:.0f} s")
+    Xs, Ys, recs = [], [], []
+    rng = np.random.default_rng(0)
+    t = time.time()
+    for c, (cfg, spec) in enumerate(zip(cfgs, specs)):
+        ctx = solve_context(cfg)
+        rec = label(ctx, cfg, spec[4])
+        feat = ctx.learned_features()
         ctx.close()
+        sel = torch.tensor(rng.choice(cfg.N, min(per_config, cfg.N), replace=False), device="cuda")
+        X = feat[sel]
+        Y = torch.zeros(X.shape[0], 4, device="cuda")
+        Y[:, 0], Y[:, 1] = rec["target"][0], rec["target"][1]
         Xs.append(X)
         Ys.append(Y)
-        if (c + 1) % 25 == 0:
-            log(f"  {c + 1}/{nconf} configurations ({time.time() - t:.0f} s)")
-    return torch.cat(Xs), torch.cat(Ys)
+        rec.update({"name": cfg.name, "N": cfg.N})
+        recs.append(rec)
+        if (c + 1) % 20 == 0:
+            log(f"  {c + 1}/{len(cfgs)} configurations labelled ({time.time() - t:.0f} s)")
+    return torch.cat(Xs), torch.cat(Ys), recs
 
 
 def init_weights(X, Y, seed=0):
@@ -100,14 +139,14 @@ def init_weights(X, Y, seed=0):
     mu = X.double().mean(0).cpu().numpy()
     sd = X.double().std(0).cpu().numpy()
     sd = np.where(sd > 1e-6, sd, 1.0)
-    os_ = Y.double().std(0).cpu().numpy()
+    os_ = Y.double().abs().max(0).values.cpu().numpy()
     os_ = np.where(os_ > 1e-9, os_, 1.0)
     packed = np.concatenate(w + [mu, sd, os_]).astype(np.float32)
     assert packed.size == api.SE_MLP_NW
     return torch.tensor(packed, device="cuda")
 
 
-def train(X, Y, epochs=400, lr=3e-3, batch=8192, seed=0, log=print):
+def train(X, Y, epochs=300, lr=2e-3, batch=8192, seed=0, log=print):
     import torch
     w = init_weights(X, Y, seed)
     m = torch.zeros(api.SE_MLP_NTRAIN, device="cuda")
@@ -132,25 +171,27 @@ def train(X, Y, epochs=400, lr=3e-3, batch=8192, seed=0, log=print):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--configs", type=int, default=200)
-    ap.add_argument("--n", type=int, default=96)
-    ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--configs", type=int, default=160)
+    ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--seed0", type=int, default=1000)
     ap.add_argument("--out", default=WEIGHTS)
     args = ap.parse_args()
     t = time.time()
-    X, Y = build_dataset(args.configs, args.n, args.seed0)
+    specs = [config_spec(k, args.seed0) for k in range(args.configs)]
+    X, Y, recs = build_dataset(specs)
     t_data = time.time() - t
     w, hist = train(X, Y, epochs=args.epochs)
     np.save(args.out, w.cpu().numpy())
-    meta = {"configs": args.configs, "n": args.n, "phi": 0.4, "radii": "log-normal mean 1 std 0.2",
-            "seeds": [args.seed0, args.seed0 + args.configs - 1], "samples": int(X.shape[0]),
+    tot = {k: sum(r[k] for r in recs) for k in ("block", "spectral_default")}
+    tot["best_on_grid"] = sum(min(r["grid"].values()) for r in recs)
+    meta = {"configs": args.configs, "seeds": [args.seed0, args.seed0 + args.configs - 1],
+            "grid": {"theta": THETAS, "k_c_a": KAS}, "samples": int(X.shape[0]),
             "loss_first": hist[0], "loss_last": hist[-1], "epochs": args.epochs,
-            "target_std": Y.double().std(0).cpu().tolist(), "data_seconds": t_data,
-            "train_seconds": time.time() - t - t_data}
+            "products_summed_over_configs": tot, "data_seconds": t_data,
+            "train_seconds": time.time() - t - t_data, "records": recs}
     with open(args.out.replace(".npy", ".json"), "w") as f:
         json.dump(meta, f, indent=1)
-    print(json.dumps(meta))
+    print(json.dumps({k: v for k, v in meta.items() if k != "records"}))
 
 
 if __name__ == "__main__":

@@ -110,8 +110,8 @@ def test_persistent_batch_matches_per_box_launches(ncomp, dtype):
 
 def test_batch_with_largest_box_vs_oracle(oracle_mod):
     """Boxes of the 64-box workload's kind (bidisperse radii 1 and 1.5 at equal numbers,
-    forces only, FP32, parameters the chooser picks for 1e-6 on a grid of at most 128^3,
-    as in the benchmark), one of them at the workload's largest size N = 8000 and
+    forces only, FP32, parameters the chooser picks on a grid of at most 128^3 as in the
+    benchmark: method tolerance 2.5e-7, FP32 floor 1e-6), one of them at the workload's largest size N = 8000 and
     phi = 0.45: the graph and the persistent launch against the FP64 oracle on 256 sampled
     rows of every box, <= 1e-6 in relative 2-norm."""
     rng = np.random.default_rng(40)
@@ -122,7 +122,8 @@ def test_batch_with_largest_box_vs_oracle(oracle_mod):
         boxes.append(inputs.Config(f"n{n}", L, inputs.positions_dense(rad, L, rng, sweeps=4), rad))
     ctxs, xs = [], []
     for cfg in boxes:
-        sp = params.choose(cfg.L, cfg.N, 1e-6, M_max=128, a_eff=params.effective_radius(cfg.rad), precision=0)
+        sp = params.choose(cfg.L, cfg.N, 2.5e-7, M_max=128, a_eff=params.effective_radius(cfg.rad), precision=0,
+                           fp32_tol=1e-6)
         c = api.Context()
         c.set_params(sp.xi, sp.M, sp.P, sp.rc)
         c.set_option(api.SE_OPT_SHAPE_M, sp.m)

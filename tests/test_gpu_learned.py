@@ -1,6 +1,7 @@
-"""Learned correction of the block-diagonal preconditioner: the hand-written network
-kernels against the FP64 reference network (oracle/mlp.py), training, fallbacks, and
-what the trained network gains over the plain block preconditioner."""
+"""Learned preconditioner: the hand-written network kernels against the FP64 reference
+network (oracle/mlp.py), training, fallbacks, and what the trained network (the damping
+and cutoff of the spectral correction of the block-diagonal preconditioner) gains over
+the method without it."""
 import os
 
 import numpy as np
@@ -58,12 +59,14 @@ def test_adam_training_reduces_the_loss():
     assert float(loss.item()) < 0.2 * l0
 
 
-def _solve_ctx(cfg):
-    sp = params.choose(cfg.L, cfg.N, 1e-8, M_max=96, a_eff=params.effective_radius(cfg.rad))
+def _solve_ctx(cfg, precision=1, tol=1e-8, M_max=96):
+    sp = params.choose(cfg.L, cfg.N, tol, M_max=M_max, a_eff=params.effective_radius(cfg.rad),
+                       precision=precision)
     ctx = api.Context()
     ctx.set_params(sp.xi, sp.M, sp.P, sp.rc)
     ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
-    ctx.set_option(api.SE_OPT_PRECISION, 1)
+    ctx.set_option(api.SE_OPT_PRECISION, precision)
+    ctx.set_option(api.SE_OPT_SIZE_MODE, 1)
     ctx.set_option(api.SE_OPT_RESTART, 100)
     ctx.set_config(cfg.pos, cfg.rad, cfg.L)
     return ctx
@@ -78,46 +81,70 @@ def test_without_weights_learned_is_the_block_preconditioner():
     assert i1 == i2 and torch.equal(x1, x2)
 
 
-def test_bad_weights_are_rejected_or_fall_back():
-    cfg = inputs.lognormal(seed=8, n=300, phi=0.3)
-    ctx = _solve_ctx(cfg)
+def test_bad_weights_are_rejected_or_clamped():
+    """Non-finite weights are rejected; weights whose outputs lie far outside the useful
+    range give the clamped damping and cutoff, and the solve still converges (a correction
+    that stalls falls back to the block preconditioner)."""
+    cfg = inputs.mono_dense(seed=8, n=2000, phi=0.45)
+    ctx = _solve_ctx(cfg, precision=0, tol=5e-7, M_max=64)
     w = random_weights(np.random.default_rng(3))
     bad = w.copy()
     bad[5] = np.nan
     with pytest.raises(api.SeError) as e:
         ctx.set_learned_weights(bad)
     assert e.value.code == api.SE_ERR_NONFINITE
-    # corrections that would make every block negative fall back to the plain block
-    w[ref.NTRAIN - 4:ref.NTRAIN] = -50.0          # b3
-    w[:ref.NTRAIN - 4] *= 0.0
-    ctx.set_learned_weights(w)
     b = torch.tensor(np.random.default_rng(4).standard_normal((cfg.N, 11)), device="cuda")
-    x1, i1, _ = ctx.solve(b, rtol=1e-8, maxit=400, precond=api.SE_PRECOND_BLOCK)
-    x2, i2, r2 = ctx.solve(b, rtol=1e-8, maxit=400, precond=api.SE_PRECOND_LEARNED)
-    assert r2 <= 1e-8 and i1 == i2
+    xb, ib, rb = ctx.solve(b, rtol=1e-6, maxit=800, precond=api.SE_PRECOND_BLOCK)
+    for big in (-50.0, 50.0):
+        w2 = w.copy()
+        w2[:ref.NTRAIN] = 0.0
+        w2[ref.NTRAIN - 4:ref.NTRAIN - 2] = big          # b3 of outputs 0 and 1
+        ctx.set_learned_weights(w2)
+        xl, il, rl = ctx.solve(b, rtol=1e-6, maxit=800, precond=api.SE_PRECOND_LEARNED)
+        assert rl <= 1e-6, big
+
+
+# Held-out configurations, seeds disjoint from training (train_pc.py uses 1000..1159):
+# the kinds the network is trained on, including two on which the fixed default damping
+# of the spectral correction stalls (monodisperse phi = 0.45 at N = 20000, bidisperse).
+HELD_OUT = [("lognormal", 4000, 0.4, 5001), ("mono", 20000, 0.45, 5002), ("bidisperse", 4000, 0.3, 5003),
+            ("mono", 3000, 0.2, 5004)]
+
+
+def _held_out(kind, n, phi, seed):
+    if kind == "lognormal":
+        return inputs.lognormal(seed=seed, n=n, phi=phi)
+    if kind == "mono":
+        return inputs.mono_dense(seed=seed, n=n, phi=phi)
+    return inputs.bidisperse(seed=seed, n=n, phi=phi)
 
 
 @pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained weights in the package")
 def test_trained_network_gain_on_held_out_configurations():
-    """Held-out log-normal configurations (seeds disjoint from training): the learned
-    preconditioner needs no more products than the plain block one, and both solutions
-    agree (the network only changes the iteration count)."""
+    """What the trained network gains over the method without it.  On every held-out
+    configuration the learned preconditioner (the spectral correction with the network's
+    damping and cutoff) needs fewer products than the plain block-diagonal preconditioner
+    it corrects, and at least 1.5x fewer summed over the set; it never needs more than the
+    spectral correction with the fixed default damping and cutoff (+3%), and every solve
+    meets the tolerance (the network only changes the iteration count)."""
     w = np.load(WEIGHTS)
-    gains = []
-    for seed in (5001, 5002, 5003):
-        cfg = inputs.lognormal(seed=seed, n=600, phi=0.4)
-        ctx = _solve_ctx(cfg)
+    tot = {"block": 0, "learned": 0, "spectral": 0}
+    for kind, n, phi, seed in HELD_OUT:
+        cfg = _held_out(kind, n, phi, seed)
+        ctx = _solve_ctx(cfg, precision=0, tol=5e-7, M_max=128)
         b = torch.tensor(np.random.default_rng(seed).standard_normal((cfg.N, 11)), device="cuda")
-        xb, ib, rb = ctx.solve(b, rtol=1e-8, maxit=800, precond=api.SE_PRECOND_BLOCK)
+        xb, ib, rb = ctx.solve(b, rtol=1e-6, maxit=1500, precond=api.SE_PRECOND_BLOCK)
+        xs, is_, rs = ctx.solve(b, rtol=1e-6, maxit=1500, precond=api.SE_PRECOND_SPECTRAL)
         ctx.set_learned_weights(w)
-        xl, il, rl = ctx.solve(b, rtol=1e-8, maxit=800, precond=api.SE_PRECOND_LEARNED)
-        assert rb <= 1e-8 and rl <= 1e-8
-        assert float(torch.linalg.norm(xl - xb) / torch.linalg.norm(xb)) <= 1e-6
-        gains.append(ib / il)
-    # The gain is small by construction: with the exact diagonal blocks of the inverse
-    # (the network's training target) GMRES saves 2-6% of the products on these
-    # configurations, because the iteration count is set by the long-wavelength
-    # collective modes that no per-particle block reaches.  The test records the gain
-    # and requires that the learned correction costs no more than 15%.
-    print("iterations block/learned:", gains)
-    assert min(gains) >= 0.85
+        xl, il, rl = ctx.solve(b, rtol=1e-6, maxit=1500, precond=api.SE_PRECOND_LEARNED)
+        # every solve meets the tolerance on its FP64-equivalent residual: the network
+        # changes how many products the solution takes, not the system that is solved
+        assert rb <= 1e-6 and rl <= 1e-6 and rs <= 1e-6
+        print(f"{kind} N={n} phi={phi}: products block {ib}, spectral default {is_}, learned {il}")
+        assert il < ib, (kind, n)
+        assert il <= 1.03 * is_ + 2, (kind, n)
+        tot["block"] += ib
+        tot["learned"] += il
+        tot["spectral"] += is_
+    print("summed products:", tot)
+    assert tot["block"] >= 1.5 * tot["learned"]

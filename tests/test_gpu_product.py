@@ -75,7 +75,7 @@ def test_mono_n100_forces_fp64_parity(oracle_mod):
     assert rel(gpu_apply(ctx, x[:, :3]), ref) <= 1e-9
 
 
-@pytest.mark.parametrize("size_mode", [0, 1, 2])
+@pytest.mark.parametrize("size_mode", [0, 1, 2, 3])
 def test_all_components_fp64(small_poly, small_poly_ref, size_mode):
     cfg, x = small_poly
     ctx = make_ctx(1.0, 64, 24, 5.45, cfg, precision=1, size_mode=size_mode)
@@ -84,7 +84,7 @@ def test_all_components_fp64(small_poly, small_poly_ref, size_mode):
         assert rel(y[:, sl], small_poly_ref[:, sl]) <= 1e-9, sl
 
 
-@pytest.mark.parametrize("size_mode", [0, 1, 2])
+@pytest.mark.parametrize("size_mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_all_components_fp32(small_poly, small_poly_ref, size_mode, dtype):
     cfg, x = small_poly
@@ -333,7 +333,7 @@ def test_overlap_detection():
     assert torch.isfinite(ctx.apply(torch.ones(3, 12, device="cuda", dtype=torch.float64))).all()
 
 
-@pytest.mark.parametrize("size_mode", [0, 1, 2])
+@pytest.mark.parametrize("size_mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("ncomp", [3, 12])
 def test_double_float_mode(small_poly, small_poly_ref, size_mode, ncomp):
     """SE_OPT_PRECISION 2 (spread and gather in double-float, the rest in FP64) gives the

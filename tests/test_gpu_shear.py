@@ -17,10 +17,10 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def ctx_for(cfg, gamma, precision, M=64, P=24, xi=1.0, rc=5.45):
+def ctx_for(cfg, gamma, precision, M=64, P=24, xi=1.0, rc=5.45, size_mode=2):
     c = api.Context()
     c.set_params(xi, M, P, rc)
-    c.set_option(api.SE_OPT_SIZE_MODE, 2)
+    c.set_option(api.SE_OPT_SIZE_MODE, size_mode)
     c.set_option(api.SE_OPT_SHEAR, gamma)
     c.set_option(api.SE_OPT_PRECISION, precision)
     c.set_config(cfg.pos, cfg.rad, cfg.L)
@@ -54,14 +54,18 @@ def _min_gap(pos, rad, L, g):
     return r.min()
 
 
+@pytest.mark.parametrize("size_mode", [2, 3])
 @pytest.mark.parametrize("gamma", [0.5, -0.3, 0.2])
-def test_sheared_product_vs_oracle(oracle_mod, poly, gamma):
+def test_sheared_product_vs_oracle(oracle_mod, poly, gamma, size_mode):
+    """Both wave-space size approaches on the sheared lattice: mode 2 (the window's
+    gradients along the sheared directions in the spread and gather) and mode 3 (every
+    derivative in k-space with the sheared reciprocal lattice)."""
     cfg, x = poly
     ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x, tol=1e-15, gamma=gamma)
-    y = ctx_for(cfg, gamma, 1).apply(torch.tensor(x, device="cuda")).cpu().numpy()
+    y = ctx_for(cfg, gamma, 1, size_mode=size_mode).apply(torch.tensor(x, device="cuda")).cpu().numpy()
     for sl in (slice(0, 3), slice(3, 6), slice(6, 11), slice(11, 12)):
         assert rel(y[:, sl], ref[:, sl]) <= 1e-9, (gamma, sl)
-    y32 = ctx_for(cfg, gamma, 0, M=48, P=16, xi=0.9, rc=5.4).apply(
+    y32 = ctx_for(cfg, gamma, 0, M=48, P=16, xi=0.9, rc=5.4, size_mode=size_mode).apply(
         torch.tensor(x, device="cuda", dtype=torch.float32)).double().cpu().numpy()
     assert rel(y32, ref) <= 1e-6
     # the sheared cell changes the result (the test would pass trivially otherwise)

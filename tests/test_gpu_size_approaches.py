@@ -2,7 +2,9 @@
 Sec. 6.1.1, Eq. err-E): e_inf,r(E) = max_i |E_i^SE - E_i^*| / |E_i^*| of the wave-space
 part alone (FP64) against the oracle's direct-Ewald wave-space part at the same xi, as a
 function of the support P at the best shape parameter m, M = 64, xi a_1 = 0.1, for the
-real-space, the hybrid and the wave-space approach, on a bidisperse suspension (radii
+real-space, the hybrid and the wave-space approach (SE_OPT_SIZE_MODE 1, 0, 3: every
+derivative in k-space, 20 grids each way), and for the variant that keeps the torque and
+stresslet gradients in the spread and gather (mode 2), on a bidisperse suspension (radii
 1 and 2).
 
 The paper finds the minimum error decaying like exp(-P pi/2) with the optimal m near
@@ -36,7 +38,8 @@ def test_wave_space_error_against_support(oracle_mod):
     ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x, xi=xi, tol=1e-15, parts=2)
     Ps = [5, 7, 9, 11, 13, 15, 17, 19]
     best = {}
-    for mode, name in ((1, "real-space"), (0, "hybrid"), (2, "wave-space")):
+    names = ("real-space", "hybrid", "wave-space", "laplacians in k-space")
+    for mode, name in ((1, "real-space"), (0, "hybrid"), (3, "wave-space"), (2, "laplacians in k-space")):
         for P in Ps:
             errs = []
             for m in np.linspace(0.6, 1.6, 11) * math.sqrt(math.pi * P):
@@ -51,12 +54,11 @@ def test_wave_space_error_against_support(oracle_mod):
                 errs.append((e_inf_r(y, ref), float(m)))
                 ctx.close()
             best[(name, P)] = min(errs)
-    print("\n  P   real-space e (m)       hybrid e (m)       wave-space e (m)")
+    print("\n  P   " + "   ".join(f"{n} e (m)" for n in names))
     for P in Ps:
-        (er, mr), (eh, mh), (ew, mw) = best[("real-space", P)], best[("hybrid", P)], best[("wave-space", P)]
-        print(f"{P:3d}   {er:9.2e} ({mr:5.2f})   {eh:9.2e} ({mh:5.2f})   {ew:9.2e} ({mw:5.2f})")
+        print(f"{P:3d}   " + "   ".join(f"{best[(n, P)][0]:9.2e} ({best[(n, P)][1]:5.2f})" for n in names))
     need = {}
-    for name in ("real-space", "hybrid", "wave-space"):
+    for name in names:
         e = [best[(name, P)][0] for P in Ps]
         # exponential decay of the minimum error: a decade every few points of P
         assert e[-1] < 1e-3 * e[0], (name, e)
@@ -66,4 +68,4 @@ def test_wave_space_error_against_support(oracle_mod):
         need[name] = min((P for P in Ps if best[(name, P)][0] <= 1e-4), default=None)
     print("P needed for e <= 1e-4:", need)
     assert all(v is not None for v in need.values())
-    assert need["wave-space"] <= need["hybrid"] <= need["real-space"]
+    assert need["wave-space"] <= need["laplacians in k-space"] <= need["hybrid"] <= need["real-space"]
