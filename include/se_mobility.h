@@ -89,9 +89,10 @@ typedef struct se_ctx se_ctx;
                                   beside the spread, 1 = beside the FFT chain, 2 = in line before the
                                   spread (default: the spread and gather fill every SM, so running
                                   beside them only slows them); results are identical */
-#define SE_OPT_PC_THETA   10   /* damping theta of the spectral correction, in [0, 1]; 0 (default) = 0.98 for
-                                  monodisperse suspensions, 0.9 otherwise (larger values stalled GMRES on a
-                                  log-normal suspension) */
+#define SE_OPT_PC_THETA   10   /* damping theta of the spectral correction, in [0, 1]; 0 (default) = 0.9, the
+                                  best single value over generated mono-, bi- and polydisperse suspensions
+                                  (the best per configuration ranges from 0.8 to 0.98, which the learned
+                                  preconditioner predicts; too large a value stalls the corrected cycles) */
 #define SE_OPT_PC_KA      11   /* cutoff k_c a of the spectral correction, a the mean radius (default 0.9) */
 #define SE_OPT_GATHER      9   /* gather kernel: 0 = default (currently 1), 1 = one warp per particle
                                   reading the grid through L2, 2 = one CTA per spreading bin staging

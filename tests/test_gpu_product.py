@@ -352,16 +352,21 @@ def test_double_float_mode(small_poly, small_poly_ref, size_mode, ncomp):
     assert rel(y32io, y64) <= 2e-7
 
 
+@pytest.mark.parametrize("ff_table", [1, 0])
 @pytest.mark.parametrize("ncomp", [3, 6, 11, 12])
-def test_double_float_real_space_part(oracle_mod, small_poly, ncomp):
+def test_double_float_real_space_part(oracle_mod, small_poly, ncomp, ff_table):
     """The real-space sum of SE_OPT_PRECISION 2 (the pair table contracted in double-float
-    arithmetic) alone: equal to the FP64 real-space sum to double-float rounding and, in the
-    U, Omega, E rows, to the oracle's real-space part (same xi, rc) to its FP64 parity bound,
-    for every prefix.  (E_tr splits the harmonic pressure Faxen term differently.)"""
+    arithmetic) alone, reading the double-float copy of the pair table (SE_OPT_FF_TABLE 1)
+    or converting the FP64 table as it reads it (0): equal to the FP64 real-space sum to
+    double-float rounding and, in the U, Omega, E rows, to the oracle's real-space part
+    (same xi, rc) to its FP64 parity bound, for every prefix.  (E_tr splits the harmonic
+    pressure Faxen term differently.)"""
     cfg, x = small_poly
     xx = x[:, :ncomp].copy()
     y64 = gpu_apply(make_ctx(0.9, 48, 16, 5.4, cfg, precision=1, parts=1), xx)
-    yff = gpu_apply(make_ctx(0.9, 48, 16, 5.4, cfg, precision=2, parts=1), xx)
+    cff = make_ctx(0.9, 48, 16, 5.4, cfg, precision=2, parts=1)
+    cff.set_option(api.SE_OPT_FF_TABLE, ff_table)
+    yff = gpu_apply(cff, xx)
     assert rel(yff, y64) <= 1e-12
     x12 = np.zeros((cfg.N, 12))
     x12[:, :ncomp] = xx

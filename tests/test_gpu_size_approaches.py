@@ -10,8 +10,8 @@ stresslet gradients in the spread and gather (mode 2), on a bidisperse suspensio
 The paper finds the minimum error decaying like exp(-P pi/2) with the optimal m near
 sqrt(pi P), and e ~ 1e-4 reached at P = 15 (real-space approach), 13 (hybrid) and 9
 (wave-space).  The test checks the exponential decay, the location of the optimal m,
-and the order of the three approaches in the P a given error needs; it prints the
-table it measured."""
+the order of the approaches in the P a given error needs and the paper's P for 1e-4; it
+prints the table it measured."""
 import math
 
 import numpy as np
@@ -69,3 +69,5 @@ def test_wave_space_error_against_support(oracle_mod):
     print("P needed for e <= 1e-4:", need)
     assert all(v is not None for v in need.values())
     assert need["wave-space"] <= need["laplacians in k-space"] <= need["hybrid"] <= need["real-space"]
+    # the paper's supports for 1e-4 (Sec. 6.1.1): 15, 13 and 9
+    assert need["real-space"] <= 15 and need["hybrid"] <= 13 and need["wave-space"] <= 9
