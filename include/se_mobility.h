@@ -94,6 +94,10 @@ typedef struct se_ctx se_ctx;
                                   (the best per configuration ranges from 0.8 to 0.98, which the learned
                                   preconditioner predicts; too large a value stalls the corrected cycles) */
 #define SE_OPT_PC_KA      11   /* cutoff k_c a of the spectral correction, a the mean radius (default 0.9) */
+#define SE_OPT_PC_CMAX    17   /* cap in [0.5, 0.99] of the largest eigenvalue of the spectral correction C
+                                  (default 0.97): where the estimate of |C| (48 Lanczos steps, times 1.01)
+                                  passes it, C is scaled down to it, which keeps the preconditioner positive
+                                  definite */
 #define SE_OPT_GATHER      9   /* gather kernel: 0 = default (currently 1), 1 = one warp per particle
                                   reading the grid through L2, 2 = one CTA per spreading bin staging
                                   the bin's support window in shared memory (slower on B300 at P = 14
@@ -137,9 +141,9 @@ typedef struct se_ctx se_ctx;
 /* preconditioners for se_solve */
 #define SE_PRECOND_NONE    0
 #define SE_PRECOND_BLOCK   1   /* block-diagonal self + own-image blocks (Sec. 4.2) */
-#define SE_PRECOND_LEARNED 2   /* SE_PRECOND_SPECTRAL with the damping and cutoff that the learned network
-                                  predicts for the configuration (se_set_learned_weights); the plain
-                                  block preconditioner without weights or in a sheared cell */
+#define SE_PRECOND_LEARNED 2   /* SE_PRECOND_SPECTRAL with the damping, cutoff and norm cap that the learned
+                                  network predicts for the configuration (se_set_learned_weights); the
+                                  plain block preconditioner without weights or in a sheared cell */
 #define SE_PRECOND_SPECTRAL 3  /* block preconditioner minus a correction of the long-wavelength
                                   transverse force modes (their eigenvalues n/(eta k^2) set the
                                   iteration count), applied as a forces-only product on a coarse
@@ -272,11 +276,12 @@ int se_far_field_diffusivity(se_ctx *ctx, int nsamples, const double *fr, double
 /* Learned preconditioner (SE_PRECOND_LEARNED).  A small network (16 -> 64 -> 64 -> 4,
  * tanh, FP32) maps rotation- and permutation-invariant features of each sphere's radius and
  * of its neighbours inside rc (and the box size L / <a>) to per-sphere outputs whose mean
- * over the spheres sets the damping theta and the cutoff k_c <a> of the spectral correction
- * of the Sec. 4.2 block preconditioner (theta clamped to [0.5, 0.985], k_c <a> to [0.4, 1.5]).
+ * over the spheres sets the damping theta, the cutoff k_c <a> and the norm cap c_max of the
+ * spectral correction of the Sec. 4.2 block preconditioner (clamped to [0.5, 0.985],
+ * [0.4, 1.5] and [0.85, 0.985]).
  * Weights are SE_MLP_NW packed floats (layout in se_learned.cu), produced by
  * paper_1506_08481_b300/train_pc.py from the iteration counts of solves over a grid of
- * (theta, k_c <a>) on generated configurations.
+ * (theta, k_c <a>, c_max) on generated configurations.
  *   se_set_learned_weights: copies the HOST array w; SE_ERR_NONFINITE on NaN/Inf.
  *   se_learned_features   : DEVICE feat [N][16] in caller order for the configuration.
  *   se_mlp_forward        : DEVICE w, X [n][16] -> Y [n][4] (the outputs, unstandardised).

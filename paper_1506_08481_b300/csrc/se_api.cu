@@ -122,6 +122,7 @@ static void free_config(se_ctx *c)
 {
     free_spectral(c);
     c->lp_ready = false;
+    c->sp_theta_cap = 1.0;
     dfree_t(c->b.pos);
     dfree_t(c->b.rad);
     dfree_t(c->b.perm);
@@ -469,6 +470,12 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         if (!(value >= 0 && value <= 1)) return set_error(c, SE_ERR_ARG, "theta must be in [0, 1]");
         if (value != c->sp_theta) free_spectral(c);
         c->sp_theta = value;
+        c->sp_theta_cap = 1.0;
+        return SE_OK;
+    case SE_OPT_PC_CMAX:
+        if (!(value >= 0.5 && value <= 0.99)) return set_error(c, SE_ERR_ARG, "c_max must be in [0.5, 0.99]");
+        if (value != c->sp_cmax) free_spectral(c);
+        c->sp_cmax = value;
         return SE_OK;
     case SE_OPT_PC_KA:
         if (!(value > 0 && value <= 3)) return set_error(c, SE_ERR_ARG, "k_c a must be in (0, 3]");

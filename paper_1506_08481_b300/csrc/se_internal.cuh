@@ -150,10 +150,14 @@ struct se_ctx {
     double ktab_kmax = 0;
     double sp_fit[3] = {0, 0, 0};       // fitted lambda_T(k) = A / k^2 + l0, and lambda_B
     double sp_rho = 0;                  // largest eigenvalue of the correction before capping
-    double spc_theta = 0, spc_ka = 0;   // the damping and cutoff spc was built with (0: the options)
+    double sp_cmax = 0.97;              // cap of the largest eigenvalue of the correction (SE_OPT_PC_CMAX)
+    double sp_cmax_used = 0.97;
+    double spc_theta = 0, spc_ka = 0, spc_cmax = 0;   // what spc was requested with (0: the options)
+    double sp_theta_used = 0;           // the damping spc was built with
+    double sp_theta_cap = 1.0;          // at most this damping on this configuration (lowered by stalls)
     int pc_stalls = 0;                  // solves whose spectral correction stalled and fell back to the block
     bool lp_ready = false;              // the learned damping and cutoff for this configuration and weights
-    double lp_theta = 0, lp_ka = 0;
+    double lp_theta = 0, lp_ka = 0, lp_cmax = 0;
     se::FftPlan plan{};
     se::Buffers b;
     size_t alloc_N = 0;
@@ -188,7 +192,7 @@ bool launch_real_ff(se_ctx *c, const ff *xs, ff *yreal, cudaStream_t s, int ncom
 int build_pair_table_ff(se_ctx *c);
 // se_learned.cu: the damping theta and cutoff k_c <a> of the spectral correction that the
 // learned network predicts for the configuration (mean of its per-particle outputs)
-int learned_spectral_params(se_ctx *c, double *theta, double *ka);
+int learned_spectral_params(se_ctx *c, double *theta, double *ka, double *cmax);
 // se_solve.cu
 void convert_f2d(int n, const float *x, double *y, cudaStream_t s);
 // exclusive scan of n ints into out[0..n] on stream s

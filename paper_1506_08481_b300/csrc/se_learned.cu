@@ -7,15 +7,15 @@
 //   f = [ sum_j b_k(h_ij) (k < 7),  sum_j b_k(h_ij) a_j/a_i (k < 7),  a_i / <a>,  ln(L / <a>) / 5 ],
 //   h_ij = r_ij / (a_i + a_j),  b_k(h) = exp(-((h - c_k)/0.35)^2),  c = 1, 1.25, 1.5, 2, 2.5, 3, 4.
 // Its outputs, averaged over the particles (a permutation-invariant set function of
-// the configuration), are the damping theta and the cutoff k_c <a> of the spectral
-// correction P^-1 = B - S C S (se_solve.cu): those two numbers decide how many GMRES
-// iterations the long-wavelength collective modes cost, and a value that is too large
-// for a configuration stalls GMRES.  The network is trained on the iteration counts of
-// solves the method itself runs over a grid of (theta, k_c <a>) on generated
-// configurations (train_pc.py).  Outputs 2 and 3 are unused (trained to zero).
-// theta is clamped to [0.5, 0.985] and k_c <a> to [0.4, 1.5]; the plain block
-// preconditioner stays the fallback (no weights, sheared cells, and every solve whose
-// corrected cycle fails to halve the residual).
+// the configuration), are the damping theta, the cutoff k_c <a> and the norm cap c_max of
+// the spectral correction P^-1 = B - S C S (se_solve.cu): they decide how far the
+// long-wavelength collective modes, which set the GMRES iteration count, are corrected.
+// The network is trained on the iteration counts of solves the method itself runs over
+// a grid of (theta, k_c <a>, c_max) on generated configurations (train_pc.py).  Output 3
+// is unused (trained to zero).  theta is clamped to [0.5, 0.985], k_c <a> to [0.4, 1.5]
+// and c_max to [0.85, 0.985]; the plain block preconditioner stays the fallback (no
+// weights, sheared cells), and a corrected cycle that fails to halve the residual is
+// retried with less damping.
 //
 // Network: 16 -> 64 -> 64 -> 4, tanh, FP32, standardised inputs and outputs.
 // Packed parameters (float): W1[64][16] b1[64] W2[64][64] b2[64] W3[4][64] b3[4]
@@ -183,11 +183,12 @@ __global__ void adam_kernel(float *w, float *m, float *v, const float *g, int st
 }  // namespace
 
 // ---- used by se_solve: the spectral correction's damping and cutoff for the configuration
-int learned_spectral_params(se_ctx *c, double *theta, double *ka)
+int learned_spectral_params(se_ctx *c, double *theta, double *ka, double *cmax)
 {
     if (c->lp_ready) {
         *theta = c->lp_theta;
         *ka = c->lp_ka;
+        *cmax = c->lp_cmax;
         return SE_OK;
     }
     cudaStream_t s = c->stream;
@@ -224,20 +225,25 @@ int learned_spectral_params(se_ctx *c, double *theta, double *ka)
         c->err = std::string("learned preconditioner: ") + cudaGetErrorString(e);
         return SE_ERR_CUDA;
     }
-    double t = 0, k = 0;
+    double t = 0, k = 0, m = 0;
     for (int i = 0; i < N; ++i) {
         t += yh[(size_t)i * kO];
         k += yh[(size_t)i * kO + 1];
+        m += yh[(size_t)i * kO + 2];
     }
     t /= N;
     k /= N;
+    m /= N;
     if (!std::isfinite(t)) t = 0.5;
     if (!std::isfinite(k)) k = 0.9;
+    if (!std::isfinite(m)) m = 0.85;
     c->lp_theta = std::min(0.985, std::max(0.5, t));
     c->lp_ka = std::min(1.5, std::max(0.4, k));
+    c->lp_cmax = std::min(0.985, std::max(0.85, m));
     c->lp_ready = true;
     *theta = c->lp_theta;
     *ka = c->lp_ka;
+    *cmax = c->lp_cmax;
     return SE_OK;
 }
 

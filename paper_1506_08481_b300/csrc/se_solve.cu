@@ -457,13 +457,13 @@ void free_spectral(se_ctx *c)
     c->sp_f = c->sp_u = c->sp_s = nullptr;
 }
 
-// largest eigenvalue allowed for the correction C
-constexpr double kCMax = 0.97;
+// Lanczos steps of the estimate of the largest eigenvalue of the correction C
+constexpr int kLanczos = 48;
 
-// theta_in, ka_in: the damping and cutoff k_c <a> (<= 0: the options SE_OPT_PC_THETA /
-// SE_OPT_PC_KA and their defaults)
+// theta_in, ka_in, cmax_in: the damping, the cutoff k_c <a> and the cap of the largest
+// eigenvalue of C (<= 0: the options SE_OPT_PC_THETA / _KA / _CMAX and their defaults)
 static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w, double theta_in = 0,
-                          double ka_in = 0)
+                          double ka_in = 0, double cmax_in = 0)
 {
     cudaStream_t s = c->stream;
     const int N = (int)c->N;
@@ -473,11 +473,15 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w, do
     double asum = 0;
     for (double a : rad) asum += a;
     // damping: 0.9 unless given (the best single value over 160 generated mono-, bi- and
-    // polydisperse configurations; the best per configuration ranges from 0.8 to 0.98)
-    const double theta = theta_in > 0 ? theta_in : (c->sp_theta > 0 ? c->sp_theta : 0.9);
+    // polydisperse configurations; the best per configuration ranges from 0.8 to 0.98),
+    // at most the cap left by earlier stalls on this configuration
+    const double theta = std::min(c->sp_theta_cap, theta_in > 0 ? theta_in : (c->sp_theta > 0 ? c->sp_theta : 0.9));
+    c->sp_theta_used = theta;
     const double ka = ka_in > 0 ? ka_in : c->sp_ka;
+    c->sp_cmax_used = cmax_in > 0 ? cmax_in : c->sp_cmax;
     c->spc_theta = theta_in;
     c->spc_ka = ka_in;
+    c->spc_cmax = cmax_in;
     const double aref = asum / N, L = c->L, k1 = 2 * kPi / L;
     double kc = ka / aref;
     if (kc <= 1.5 * k1) return SE_OK;                       // box too small: no long waves to correct
@@ -599,27 +603,73 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w, do
         sc->ktab_kmax = kc;
         sc->ktab_on = true;
         // On particle positions the plane waves are only nearly orthogonal, so |C| can
-        // exceed max h.  Power iteration on C (symmetric, positive semi-definite): if its
-        // largest eigenvalue passes kCMax the table is scaled down to kCMax, which keeps
-        // I - C, and P^-1, positive definite.
+        // exceed max h (measured up to 1.11 at theta 0.98): C is symmetric positive
+        // semi-definite, and its largest eigenvalue is estimated by kLanczos steps of
+        // Lanczos (the largest Ritz value of the tridiagonal matrix, by Sturm bisection)
+        // times 1.01; if that passes the cap c_max the table is scaled down to c_max,
+        // which keeps I - C, and P^-1, positive definite.  (A 12-step power iteration
+        // underestimated |C| by up to 10%: corrected cycles stalled on an indefinite P^-1.)
         const size_t n3 = 3 * (size_t)N;
         Gm g3{c, n3, gm.part, gm.hd};
-        hash_fill_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(n3, 12345u, c->sp_f);
-        double rho = 0;
-        for (int it = 0; it < 12 && rc == SE_OK; ++it) {
-            rc = se_apply_internal(sc, 3, c->sp_f, c->sp_u, SE_F64, 0);
-            double ff = 0, fu = 0, uu = 0;
-            if (rc == SE_OK) rc = g3.dots(c->sp_f, 0, 1, c->sp_f, &ff);
-            if (rc == SE_OK) rc = g3.dots(c->sp_f, 0, 1, c->sp_u, &fu);
-            if (rc == SE_OK) rc = g3.dots(c->sp_u, 0, 1, c->sp_u, &uu);
-            if (rc != SE_OK || !(uu > 0)) break;
-            rho = fu / ff;
-            axpby_kernel<<<grid_for(n3), 256, 0, s>>>(n3, 1.0 / std::sqrt(uu), c->sp_u, 0.0, c->sp_u, c->sp_f);
+        double *vp = z, *v = c->sp_f, *wv = c->sp_u;
+        hash_fill_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(n3, 12345u, v);
+        SE_CUDA_CHECK(c, cudaMemsetAsync(vp, 0, n3 * sizeof(double), s));
+        c->launches++;
+        std::vector<double> al, be;           // diagonal alpha_j and off-diagonal beta_{j+1}
+        double vv = 0;
+        if ((rc = g3.dots(v, 0, 1, v, &vv)) == SE_OK && vv > 0) {
+            axpby_kernel<<<grid_for(n3), 256, 0, s>>>(n3, 1.0 / std::sqrt(vv), v, 0.0, v, v);
             c->launches++;
         }
+        double bprev = 0;
+        for (int j = 0; j < kLanczos && rc == SE_OK; ++j) {
+            rc = se_apply_internal(sc, 3, v, wv, SE_F64, 0);
+            double a = 0, ww = 0;
+            if (rc == SE_OK) rc = g3.dots(v, 0, 1, wv, &a);
+            if (rc != SE_OK) break;
+            axpby_kernel<<<grid_for(n3), 256, 0, s>>>(n3, -a, v, 1.0, wv, wv);
+            axpby_kernel<<<grid_for(n3), 256, 0, s>>>(n3, -bprev, vp, 1.0, wv, wv);
+            c->launches += 2;
+            al.push_back(a);
+            if ((rc = g3.dots(wv, 0, 1, wv, &ww)) != SE_OK) break;
+            const double b = std::sqrt(std::max(ww, 0.0));
+            if (!(b > 1e-12 * std::fabs(a)) || j + 1 == kLanczos) break;
+            be.push_back(b);
+            axpby_kernel<<<grid_for(n3), 256, 0, s>>>(n3, 1.0, v, 0.0, v, vp);
+            axpby_kernel<<<grid_for(n3), 256, 0, s>>>(n3, 1.0 / b, wv, 0.0, wv, v);
+            c->launches += 2;
+            bprev = b;
+        }
+        // the largest eigenvalue of the tridiagonal matrix: bisection on the Sturm count
+        double rho = 0;
+        if (rc == SE_OK && !al.empty()) {
+            const int K = (int)al.size();
+            double lo = 1e300, hi = -1e300;
+            for (int i = 0; i < K; ++i) {
+                const double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < K ? std::fabs(be[i]) : 0.0);
+                lo = std::min(lo, al[i] - r);
+                hi = std::max(hi, al[i] + r);
+            }
+            auto below = [&](double x) {      // eigenvalues smaller than x
+                int cnt = 0;
+                double d = 1.0;
+                for (int i = 0; i < K; ++i) {
+                    const double b2 = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
+                    d = al[i] - x - (i > 0 ? b2 / (d != 0.0 ? d : 1e-300) : 0.0);
+                    if (d < 0) ++cnt;
+                }
+                return cnt;
+            };
+            for (int it = 0; it < 100; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (below(mid) >= K) hi = mid; else lo = mid;
+            }
+            rho = 1.01 * hi;
+        }
         c->sp_rho = rho;
-        if (rc == SE_OK && rho > kCMax) {
-            for (float &v : tab) v = (float)(v * (kCMax / rho));
+        const double cmax = c->sp_cmax_used;
+        if (rc == SE_OK && rho > cmax) {
+            for (float &v : tab) v = (float)(v * (cmax / rho));
             cudaMemcpyAsync(sc->ktab[0], tab.data(), ntab * sizeof(float), cudaMemcpyHostToDevice, s);
         }
         c->launches += sc->launches;
@@ -662,6 +712,8 @@ using namespace se;
 // working-precision restart residuals are used while rel > kFp64Switch * rtol and they
 // still fall by 2x per cycle
 constexpr double kFp64Switch = 30.0;
+// products after which a cycle of the spectral correction must have halved the residual
+constexpr int kStallIts = 30;
 
 // Krylov basis, preconditioned vectors, work vectors and reduction scratch for the
 // context's restart length and n unknowns (kept between solves of the same size)
@@ -718,10 +770,10 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
     // the learned preconditioner: the spectral correction with the damping and cutoff
     // the network predicts for this configuration; without weights (or where the
     // spectral correction does not apply) it is the plain block preconditioner
-    double l_theta = 0, l_ka = 0;
+    double l_theta = 0, l_ka = 0, l_cmax = 0;
     if (precond == SE_PRECOND_LEARNED) {
         if (c->have_mlp && c->shear == 0 && !shifted && !mixed) {
-            rc = learned_spectral_params(c, &l_theta, &l_ka);
+            rc = learned_spectral_params(c, &l_theta, &l_ka, &l_cmax);
             if (rc != SE_OK) return rc;
             precond = SE_PRECOND_SPECTRAL;
         } else {
@@ -740,8 +792,9 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
             free_spectral(c);
         }
     }
-    if (precond == SE_PRECOND_SPECTRAL && (!c->spc || c->spc_theta != l_theta || c->spc_ka != l_ka)) {
-        rc = build_spectral(c, ncomp, gm, z, w, l_theta, l_ka);
+    if (precond == SE_PRECOND_SPECTRAL &&
+        (!c->spc || c->spc_theta != l_theta || c->spc_ka != l_ka || c->spc_cmax != l_cmax)) {
+        rc = build_spectral(c, ncomp, gm, z, w, l_theta, l_ka, l_cmax);
         if (rc != SE_OK) return rc;
     }
     auto Pinv = [&](const double *v, double *out) -> int {
@@ -801,6 +854,20 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
         // preconditioner; flexible GMRES allows the change between cycles.
         double rel_cycle = -1.0;              // residual at the start of the last cycle
         int prods_cycle = 0;
+        bool stalled = false;                 // the last cycle was cut short by a stall
+        // A stall (the spectral correction's damping too strong for this configuration):
+        // lower the damping by 0.05 for the rest of this solve and the next solves on the
+        // configuration, and rebuild the correction; below 0.6 use the block preconditioner.
+        auto relax_damping = [&]() -> int {
+            c->pc_stalls++;
+            const double th = c->sp_theta_used - 0.05;
+            if (th < 0.6 || !c->spc) {
+                precond = SE_PRECOND_BLOCK;
+                return SE_OK;
+            }
+            c->sp_theta_cap = th;
+            return build_spectral(c, ncomp, gm, z, w, l_theta, l_ka, l_cmax);
+        };
         for (;;) {
             bool exact = fp64_res;            // r is the FP64 residual (or b itself)
             if (x_zero) {
@@ -828,11 +895,11 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
             }
             if (!exact) rel_wp = rel;
             if (rel <= rtol || prods >= maxit) break;
-            if (precond == SE_PRECOND_SPECTRAL && rel_cycle > 0 && prods - prods_cycle >= std::min(m, 30) &&
-                rel > 0.5 * rel_cycle && rel > 10 * rtol) {
-                precond = SE_PRECOND_BLOCK;
-                c->pc_stalls++;
+            if (precond == SE_PRECOND_SPECTRAL && rel > 10 * rtol &&
+                (stalled || (rel_cycle > 0 && prods - prods_cycle >= std::min(m, kStallIts) && rel > 0.5 * rel_cycle))) {
+                if ((rc = relax_damping()) != SE_OK) return rc;
             }
+            stalled = false;
             rel_cycle = rel;
             prods_cycle = prods;
             axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, 1.0 / beta, r, 0.0, r, V);
@@ -884,6 +951,13 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
                     c->launches++;
                 }
                 if (std::fabs(g[j + 1]) <= 0.3 * rtol * bnorm || hn == 0.0) break;
+                // a spectral cycle that has not halved the residual after kStallIts products
+                // is cut short (the correction is rebuilt with less damping at the restart)
+                if (precond == SE_PRECOND_SPECTRAL && j + 1 == kStallIts && j + 1 < m &&
+                    std::fabs(g[j + 1]) > 0.5 * beta && std::fabs(g[j + 1]) > 10 * rtol * bnorm) {
+                    stalled = true;
+                    break;
+                }
             }
             // y = H^{-1} g (upper triangular), x += Z y (flexible GMRES: the stored
             // preconditioned vectors, so an FP32-rounded preconditioner stays consistent)

@@ -1912,6 +1912,12 @@ constexpr int kPersistThreads = 256;
 // tasks in turn, so a claim (an atomic round trip) and a completion count are paid once
 // per few tasks: small boxes have many short tasks.
 constexpr int kSubItems = 4;
+// Particles staged per chunk by the persistent kernel's spreading groups: fewer than the
+// standalone kernel's, so four groups' staging leaves L1 room for the gather's grid reads
+// (two CTAs per SM).
+constexpr int kPersistCH = 32;
+constexpr size_t kGroupSmem = sizeof(Spread16SmemT<kPersistCH>) > sizeof(Spread8Smem<float>)
+                                  ? sizeof(Spread16SmemT<kPersistCH>) : sizeof(Spread8Smem<float>);
 
 struct BoxDesc {
     SeParams p;
@@ -2110,12 +2116,13 @@ __global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(co
                     if (tile < ntiles) {
                         auto sync = [grp] { bar_named(1 + grp, 64); };
                         if (d.s16) {
-                            Spread16Smem &sm = reinterpret_cast<Spread16Smem *>(smraw)[grp];
-                            spread16_body<NCOMP, false>(tile, 0, tid, sync, sm, d.p, d.tile_start, d.tile_perm,
-                                                        d.sup_base, d.sup_s0, d.sup_w, d.rad, d.xs, d.grid_f, 1);
+                            auto &sm = *reinterpret_cast<Spread16SmemT<kPersistCH> *>(smraw + (size_t)grp * kGroupSmem);
+                            spread16_body<NCOMP, false, decltype(sync), kPersistCH>(
+                                tile, 0, tid, sync, sm, d.p, d.tile_start, d.tile_perm, d.sup_base, d.sup_s0, d.sup_w,
+                                d.rad, d.xs, d.grid_f, 1);
                         } else {
                             Spread8Smem<float> &sm = *reinterpret_cast<Spread8Smem<float> *>(
-                                smraw + (size_t)grp * sizeof(Spread16Smem));
+                                smraw + (size_t)grp * kGroupSmem);
                             spread_body<float, NCOMP, false>(tile, 0, tid, sync, sm, d.p, d.tile_start, d.tile_perm,
                                                              d.sup_base, d.sup_s0, d.sup_w, d.rad, d.xs, d.grid_f,
                                                              1);
@@ -2230,7 +2237,7 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
     std::vector<BoxDesc> h(nbox);
     std::vector<int> cnt((size_t)kPersistPhases * nbox, 0);
     std::vector<double> work(nbox, 0.0);
-    size_t smem = (size_t)4 * sizeof(Spread16Smem);
+    size_t smem = (size_t)4 * kGroupSmem;
     for (int b = 0; b < nbox; ++b) {
         se_ctx *c = box[b];
         const int with_real = (c->parts & 1) ? 1 : 0, with_wave = (c->parts & 2) ? 1 : 0;

@@ -1,18 +1,17 @@
-"""Train the learned preconditioner: the network that sets the damping theta and the cutoff
-k_c <a> of the long-wavelength (spectral) correction of the block-diagonal far-field
-preconditioner.
+"""Train the learned preconditioner: the network that sets the damping theta, the cutoff
+k_c <a> and the norm cap c_max of the long-wavelength (spectral) correction of the
+block-diagonal far-field preconditioner.
 
   python -m paper_1506_08481_b300.train_pc [--configs 160] [--epochs 300]
 
 Training data come from the method itself.  For each generated configuration (mono-, bi-
 and polydisperse suspensions, volume fractions 0.1-0.45, N from 1000 to 50000) the
 library solves M x = b (11 components, FP32 products with FP64 refinement, GMRES(100) to
-1e-6) with the spectral correction at every (theta, k_c <a>) of a grid and records the
-products each solve took (a damping too strong for the configuration stalls its cycles and
-falls back to the block preconditioner, which costs products).  The configuration's target
-is the pair with the fewest products, the smaller theta among ties (the safer one).
-Every particle of the configuration carries the target; the network's mean over the
-particles is its prediction for the configuration.  Features come from
+1e-6) with the spectral correction at every (theta, k_c <a>, c_max) of a grid and records
+the products each solve took.  The configuration's target is the grid point with the
+fewest products; among those within 2% of it, the smallest c_max and theta (the safer
+correction).  Every particle of the configuration carries the target; the network's mean
+over the particles is its prediction for the configuration.  Features come from
 se_learned_features; the network is trained with the library's kernels (se_mlp_grad,
 se_mlp_adam_step).  Writes learned_pc_weights.npy (SE_MLP_NW floats) and
 learned_pc_weights.json (the data and the training record) next to this file.
@@ -33,8 +32,9 @@ from . import api, inputs, params
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "learned_pc_weights.npy")
 NC = 11
-THETAS = (0.8, 0.85, 0.9, 0.93, 0.95, 0.97, 0.98)
-KAS = (0.6, 0.9)
+THETAS = (0.9, 0.98)
+KAS = (0.6, 0.9, 1.2)
+CMAXS = (0.9, 0.95, 0.97, 0.985)
 
 
 def config_spec(k: int, seed0: int):
@@ -75,31 +75,41 @@ def solve_context(cfg, tol=5e-7, M_max=128):
     return ctx
 
 
-def products(ctx, b, precond, theta=0.0, ka=0.9, maxit=600):
+def products(ctx, b, precond, theta=0.0, ka=0.9, cmax=0.97, maxit=600):
     """Products of one solve to 1e-6 (maxit + 1 if it did not converge)."""
     ctx.set_option(api.SE_OPT_PC_THETA, theta)
     ctx.set_option(api.SE_OPT_PC_KA, ka)
+    ctx.set_option(api.SE_OPT_PC_CMAX, cmax)
     _, it, rel = ctx.solve(b, rtol=1e-6, maxit=maxit, precond=precond, allow_not_converged=True)
     ctx.set_option(api.SE_OPT_PC_THETA, 0.0)
     ctx.set_option(api.SE_OPT_PC_KA, 0.9)
+    ctx.set_option(api.SE_OPT_PC_CMAX, 0.97)
     return it if rel <= 1e-6 else maxit + 1
 
 
 def label(ctx, cfg, seed):
-    """Products on the (theta, k_c a) grid; the target pair; the block and default counts."""
+    """Products on the (theta, k_c a, c_max) grid; the target; the block and default counts."""
     import torch
     b = torch.tensor(np.random.default_rng(seed).standard_normal((cfg.N, NC)), device="cuda")
     grid = {}
     for th in THETAS:
         for ka in KAS:
-            grid[(th, ka)] = products(ctx, b, api.SE_PRECOND_SPECTRAL, th, ka)
-    best = min(grid.values())
-    target = min((k for k, v in grid.items() if v <= best * 1.02), key=lambda k: (k[0], -k[1]))
-    return {"target": target, "grid": {f"{k[0]},{k[1]}": v for k, v in grid.items()},
+            for cm in CMAXS:
+                grid[(th, ka, cm)] = products(ctx, b, api.SE_PRECOND_SPECTRAL, th, ka, cm)
+    return {"target": target_of(grid), "grid": {",".join(str(v) for v in k): p for k, p in grid.items()},
             "block": products(ctx, b, api.SE_PRECOND_BLOCK), "spectral_default": products(ctx, b, api.SE_PRECOND_SPECTRAL)}
 
 
-def build_dataset(specs, per_config=2000, log=print):
+def target_of(grid):
+    """The grid point with the fewest products; among those within 2% of it, the smallest
+    c_max, then the smallest theta."""
+    best = min(grid.values())
+    return min((k for k, v in grid.items() if v <= 1.02 * best), key=lambda k: (k[2], k[0], grid[k]))
+
+
+def build_dataset(specs, per_config=2000, labels=None, log=print):
+    """Features and targets of every configuration; labels: records of an earlier run (their
+    product grids are reused, only the features are computed again)."""
     import torch
     t = time.time()
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
@@ -108,15 +118,21 @@ def build_dataset(specs, per_config=2000, log=print):
     Xs, Ys, recs = [], [], []
     rng = np.random.default_rng(0)
     t = time.time()
+    old = {r["name"]: r for r in labels} if labels else {}
     for c, (cfg, spec) in enumerate(zip(cfgs, specs)):
         ctx = solve_context(cfg)
-        rec = label(ctx, cfg, spec[4])
+        if cfg.name in old:
+            rec = dict(old[cfg.name])
+            grid = {tuple(float(v) for v in k.split(",")): p for k, p in rec["grid"].items()}
+            rec["target"] = target_of(grid)
+        else:
+            rec = label(ctx, cfg, spec[4])
         feat = ctx.learned_features()
         ctx.close()
         sel = torch.tensor(rng.choice(cfg.N, min(per_config, cfg.N), replace=False), device="cuda")
         X = feat[sel]
         Y = torch.zeros(X.shape[0], 4, device="cuda")
-        Y[:, 0], Y[:, 1] = rec["target"][0], rec["target"][1]
+        Y[:, 0], Y[:, 1], Y[:, 2] = rec["target"][0], rec["target"][1], rec["target"][2]
         Xs.append(X)
         Ys.append(Y)
         rec.update({"name": cfg.name, "N": cfg.N})
@@ -175,17 +191,23 @@ def main():
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--seed0", type=int, default=1000)
     ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--labels-from", default=None,
+                    help="a learned_pc_weights.json of an earlier run: reuse its product grids")
     args = ap.parse_args()
     t = time.time()
     specs = [config_spec(k, args.seed0) for k in range(args.configs)]
-    X, Y, recs = build_dataset(specs)
+    labels = None
+    if args.labels_from:
+        with open(args.labels_from) as f:
+            labels = json.load(f)["records"]
+    X, Y, recs = build_dataset(specs, labels=labels)
     t_data = time.time() - t
     w, hist = train(X, Y, epochs=args.epochs)
     np.save(args.out, w.cpu().numpy())
     tot = {k: sum(r[k] for r in recs) for k in ("block", "spectral_default")}
     tot["best_on_grid"] = sum(min(r["grid"].values()) for r in recs)
     meta = {"configs": args.configs, "seeds": [args.seed0, args.seed0 + args.configs - 1],
-            "grid": {"theta": THETAS, "k_c_a": KAS}, "samples": int(X.shape[0]),
+            "grid": {"theta": THETAS, "k_c_a": KAS, "c_max": CMAXS}, "samples": int(X.shape[0]),
             "loss_first": hist[0], "loss_last": hist[-1], "epochs": args.epochs,
             "products_summed_over_configs": tot, "data_seconds": t_data,
             "train_seconds": time.time() - t - t_data, "records": recs}
