@@ -223,6 +223,9 @@ static int ensure_grids(se_ctx *c, int prec)
     {
         const size_t ntiles = (M / kTile) * (M / kTile) * (M / kTile);
         c->nsplit = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * (size_t)c->sms * 11 + ntiles - 1) / ntiles));
+        // the FP32 16-plane tiles may split too, to fill the last wave of CTAs
+        const int nt = (int)(M / kTile);
+        if (prec == 0) c->nsplit = std::max(c->nsplit, spread16_split(c->sms, nt * nt * ((nt + 1) / 2), 4));
         if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[prec], (size_t)c->nsplit * M * M * M * 8 * es);
     }
     SE_ALLOC(c, c->b.spec_f[prec], M * M * Mh * 8 * 2 * es);

@@ -201,6 +201,8 @@ void launch_scan(se_ctx *c, int n, const int *in, int *out, cudaStream_t s);
 // se_wave.cu
 template <typename T>
 void launch_wave_spread(se_ctx *c, const T *xs, cudaStream_t s, int ncomp);
+// CTAs per 16-plane spreading tile (partial grids) for ntiles tiles, at most maxparts
+int spread16_split(int sms, int ntiles, int maxparts);
 template <typename T>
 void launch_wave_fft(se_ctx *c, cudaStream_t s);
 // releases the spectral-correction sub-context (se_solve.cu)

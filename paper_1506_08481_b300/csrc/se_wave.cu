@@ -1600,6 +1600,25 @@ void setup_support(se_ctx *c, cudaStream_t s)
     cudaFree(de3);
 }
 
+// CTAs sharing a 16-plane tile (each sums every ns-th chunk of its particles into its own
+// partial grid): at least two waves of CTAs on the SMs, and, where the tiles fill the last
+// wave poorly (M = 144: 2916 tiles on 1184 CTA slots, 2.46 waves), as many parts as bring
+// the wave efficiency to the best of 1..maxparts (+2% per extra part)
+int spread16_split(int sms, int ntiles, int maxparts)
+{
+    const int slots = sms * SE_SPREAD16_MINB;
+    int ns = std::min(maxparts, std::max(1, (2 * sms * 8 + ntiles - 1) / ntiles));
+    double best = 0;
+    for (int q = ns; q <= maxparts; ++q) {
+        const double w = (double)ntiles * q / slots, eff = w / std::ceil(w);
+        if (eff > best + 0.02) {
+            best = eff;
+            ns = q;
+        }
+    }
+    return std::max(1, ns);
+}
+
 // whether spread16_kernel applies: FP32, and the nbin + 1 z-bins of a 16-plane tile
 // are distinct bins of the grid
 static bool use_spread16(const se_ctx *c, const SeParams &p, bool fp32)
@@ -1611,8 +1630,7 @@ static bool use_spread16(const se_ctx *c, const SeParams &p, bool fp32)
 static void launch_spread16(se_ctx *c, const SeParams &p, const float *xs, cudaStream_t s, int ncomp)
 {
     const int nt = p.ntile, ntiles = nt * nt * ((nt + 1) / 2);
-    // partial grids only where the tiles alone leave SMs idle (at most the allocated parts)
-    const int ns = std::min(c->nsplit, std::max(1, (2 * c->sms * 8 + ntiles - 1) / ntiles));
+    const int ns = spread16_split(c->sms, ntiles, c->nsplit);
     float *out = ns > 1 ? (float *)c->b.grid_part[0] : (float *)c->b.grid_f[0];
     auto args = [&](auto kern) {
         kern<<<dim3(ntiles, ns), 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
@@ -1647,7 +1665,9 @@ static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_
             return;
         }
     }
-    const int nt = p.ntile, ntiles = nt * nt * nt, ns = c->nsplit;
+    // 8^3 tiles: partial grids only where the tiles alone leave SMs idle (about two waves)
+    const int nt = p.ntile, ntiles = nt * nt * nt;
+    const int ns = std::min(c->nsplit, std::max(1, (2 * c->sms * 11 + ntiles - 1) / ntiles));
     T *out = ns > 1 ? (T *)c->b.grid_part[pix<T>()] : (T *)c->b.grid_f[pix<T>()];
     auto args = [&](auto kern) {
         kern<<<dim3(ntiles, ns), 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
