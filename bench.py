@@ -48,13 +48,14 @@ FLOPS_PER_COLUMN = {"spread": 75.0, "gather": 72.0}
 # bytes of one stored real-space pair in FP32 (index 4 + separation 12 + 19 coefficients)
 PAIR_BYTES = 92
 
-# DRAM bytes (read + write) per launch from one ncu capture of the half-size case
-# (N = 100000, M = 192, the command in profiles/kernels_mono_n100000_P24.md), scaled to a
-# launch of the measured workload by grid points (M^3) or stored pairs.  A kernel changed
-# since that capture has no entry (its traffic is reported as null).
-NCU_CAPTURE = {"N": 100000, "M": 192, "npairs": 18740004}
-NCU_DRAM_BYTES = {"spread": 106e6, "gather": 180e6, "fft_x_fwd": 182e6, "fft_y_fwd": 174e6,
-                  "fft_z_scale": 186e6, "fft_y_inv": 174e6, "fft_x_inv": 179e6, "real": 1821e6}
+# DRAM bytes (read + write) per launch from one ncu capture of this workload (one product's launches,
+# the command in profiles/dram_mono_n200000_P24.md); the spread stage is spread16_kernel plus
+# sum_parts_kernel.  Other sizes scale them by grid points (M^3), stored pairs or particles.  A kernel
+# changed since that capture has no entry (its traffic is reported as null).
+NCU_CAPTURE = {"N": 200000, "M": 144, "npairs": 88237670}
+NCU_DRAM_BYTES = {"permute": 13.0e6, "real": 8724.4e6, "spread": 385.7e6, "fft_x_fwd": 50.4e6,
+                  "fft_y_fwd": 48.6e6, "fft_z_scale": 54.7e6, "fft_y_inv": 48.7e6, "fft_x_inv": 50.1e6,
+                  "gather": 149.1e6}
 
 
 def parse():
@@ -193,13 +194,15 @@ def count_pairs(cfg, rc):
     return int(t.count_neighbors(t, rc)) - cfg.N
 
 
-def ncu_traffic(stage, M, npairs):
+def ncu_traffic(stage, M, npairs, N):
     """Scaled DRAM bytes per launch from the ncu capture, or None."""
     b = NCU_DRAM_BYTES.get(stage)
     if b is None:
         return None
     if stage == "real":
         return b * npairs / NCU_CAPTURE["npairs"]
+    if stage == "permute":
+        return b * N / NCU_CAPTURE["N"]
     return b * (M / NCU_CAPTURE["M"]) ** 3
 
 
@@ -211,13 +214,13 @@ def roofline_entry(stage, ms, N, M, P, CO, npairs, peaks, peak_kind):
         peak = peaks["fp32_fma_tflops"]
         achieved = units / t / 1e12
         return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "ms": ms, "traffic": ncu_traffic(stage, M, npairs),
+                "frac": achieved / peak, "ms": ms, "traffic": ncu_traffic(stage, M, npairs, N),
                 "peak_source": (f"measured: FP32 FMA probe on {peaks['sms']} SMs (8 independent FMA chains per "
                                 f"thread, 8 CTAs of 256 threads per SM, best of 5 launches, CUDA events)")}
     peak = peaks.get("hbm_gbs", 6400.0)
     achieved = units / t / 1e9
     return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "ms": ms, "traffic": ncu_traffic(stage, M, npairs),
+            "frac": achieved / peak, "ms": ms, "traffic": ncu_traffic(stage, M, npairs, N),
             "algorithmic_bytes": units, "peak_source": f"hbm_gbs ({peak_kind})"}
 
 
@@ -575,7 +578,8 @@ def run_ours(args, rank, world, local):
     kernels["real"]["note"] = "timed alone (real-space part only); overlapped with spread/FFT in the product"
     dom = max((k for k in per_prod if k not in ("real", "permute")), key=lambda k: per_prod[k])
     roof = dict(kernels[dom])
-    roof["traffic_source"] = ("ncu DRAM bytes of the N=100000 capture scaled by grid points or pairs"
+    roof["traffic_source"] = ("ncu DRAM bytes per launch of this workload's capture (scaled by grid points, "
+                              "pairs or particles at other sizes)"
                               if roof["traffic"] is not None else "kernel changed since the last capture")
 
     workload = WORKLOAD if args.n == 200000 else WORKLOAD.replace("n200000", f"n{args.n}")

@@ -318,16 +318,22 @@ namespace {
 // The coefficients are evaluated in FP64 and stored at the compute precision.
 constexpr int kNPC = 19;
 
-__device__ __forceinline__ void pair_coefficients(double r2, double ai2, double aj2, double xi, double eta,
-                                                  double *cf)
+// constants of pair_coefficients (per configuration): xi, xi^2, 1/(xi sqrt(pi)), 1/(8 pi eta)
+struct PairConst {
+    double xi, x2, exn, c8;
+};
+
+// The B_n need one FP64 division (1/r^2), a square root and the two special functions;
+// the Faxen factors a^2/6, a^2/10 and their products are multiplications by constants.
+__device__ __forceinline__ void pair_coefficients(double r2, double ai2, double aj2, const PairConst &k, double *cf)
 {
-    const double r = sqrt(r2), ir2 = 1.0 / r2, x2 = xi * xi;
-    const double ex = exp(-x2 * r2) / (xi * sqrt(kPi));
+    const double r = sqrt(r2), ir2 = 1.0 / r2;
+    const double ex = exp(-k.x2 * r2) * k.exn;
     double B[8];
-    B[0] = erfc(xi * r) / r;
+    B[0] = erfc(k.xi * r) * (r * ir2);
     double pw = 1.0;
     for (int n = 1; n < 8; ++n) {
-        pw *= 2 * x2;
+        pw *= 2 * k.x2;
         B[n] = ((2 * n - 1) * B[n - 1] + pw * ex) * ir2;
     }
     const double s1 = B[0], s2 = -B[1], s3 = B[2], s4 = -B[3], s5 = B[4], s6 = -B[5], s7 = B[6], s8 = -B[7];
@@ -336,42 +342,44 @@ __device__ __forceinline__ void pair_coefficients(double r2, double ai2, double 
     const double m1 = 5 * l2 + r2 * l3, m2 = 7 * l3 + r2 * l4, m3 = 9 * l4 + r2 * l5, m4 = 11 * l5 + r2 * l6;
     const double p1 = -B[1], p2 = B[2], p3 = -B[3], p4 = B[4];
     const double q1 = 5 * p2 + r2 * p3, q2 = 7 * p3 + r2 * p4;
-    const double c8 = 1.0 / (8 * kPi * eta), c16 = 0.5 * c8, c32 = 0.25 * c8;
+    const double c8 = k.c8, c16 = 0.5 * c8, c32 = 0.25 * c8;
+    constexpr double i6 = 1.0 / 6, i10 = 0.1;
+    const double ai6 = ai2 * i6, aj6 = aj2 * i6, ai10 = ai2 * i10, aj10 = aj2 * i10;
     {
-        const double c1 = (ai2 + aj2) / 6, cc = ai2 * aj2 / 36;
+        const double c1 = ai6 + aj6, cc = ai6 * aj6;                 // (a_i^2 + a_j^2)/6, a_i^2 a_j^2/36
         const double G1 = s1 + c1 * l1 + cc * m1, G2 = s2 + c1 * l2 + cc * m2;
         cf[0] = c8 * (2 * G1 + r2 * G2);
         cf[1] = c8 * G2;
     }
-    cf[2] = c16 * (l1 + ai2 / 6 * m1);
-    cf[3] = c16 * (l1 + aj2 / 6 * m1);
+    cf[2] = c16 * (l1 + ai6 * m1);
+    cf[3] = c16 * (l1 + aj6 * m1);
     cf[4] = c32 * l2;
     cf[5] = c32 * (2 * l1 + r2 * l2);
     {
-        const double c1 = ai2 / 6 + aj2 / 10, cc = ai2 * aj2 / 60;
+        const double c1 = ai6 + aj10, cc = ai6 * aj10;               // a_i^2/6 + a_j^2/10, a_i^2 a_j^2/60
         const double G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
         cf[6] = -c8 * (3 * G2 + r2 * G3);
         cf[7] = c8 * G3;
     }
-    cf[8] = -c16 * (l2 + aj2 / 10 * m2);
+    cf[8] = -c16 * (l2 + aj10 * m2);
     {
-        const double c1 = ai2 / 10 + aj2 / 6, cc = ai2 * aj2 / 60;
+        const double c1 = ai10 + aj6, cc = ai10 * aj6;
         const double G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
         cf[9] = c8 * (3 * G2 + r2 * G3);
         cf[10] = -c8 * G3;
     }
-    cf[11] = c16 * (l2 + ai2 / 10 * m2);
+    cf[11] = c16 * (l2 + ai10 * m2);
     {
-        const double c1 = (ai2 + aj2) / 10, cc = ai2 * aj2 / 100;
+        const double c1 = ai10 + aj10, cc = ai10 * aj10;             // (a_i^2 + a_j^2)/10, a_i^2 a_j^2/100
         const double G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3, G4 = s4 + c1 * l4 + cc * m4;
         cf[12] = -c8 * (3 * G2 + r2 * G3);
         cf[13] = -c8 * (3 * G3 + r2 * G4);
         cf[14] = c8 * G4;
     }
-    cf[15] = -c16 * (p1 + ai2 / 6 * q1);
-    cf[16] = -c16 * (p2 + ai2 / 10 * q2);
-    cf[17] = -3 * c16 * (p1 + aj2 / 6 * q1);
-    cf[18] = 3 * c16 * (p2 + aj2 / 10 * q2);
+    cf[15] = -c16 * (p1 + ai6 * q1);
+    cf[16] = -c16 * (p2 + ai10 * q2);
+    cf[17] = -3 * c16 * (p1 + aj6 * q1);
+    cf[18] = 3 * c16 * (p2 + aj10 * q2);
 }
 
 // Neighbour search for target i (cell order): calls f(j) for every j != i with
@@ -476,7 +484,7 @@ __global__ void pair_list_kernel(int N, PairSearch ps, const int *cell_start, co
 // One warp per target: the lanes take the target's pairs in turn, form the FP64
 // separation and the radial coefficients and store them (coalesced SoA rows).
 template <typename T>
-__global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double gamma, double xi, double eta,
+__global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double gamma, PairConst pk,
                                                         const double *pos,
                                                         const double *rad, const int *off, size_t np, const int *pj,
                                                         T *px, T *pc)
@@ -491,7 +499,7 @@ __global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double 
         double x0 = p0 - pos[3 * j], x1 = p1 - pos[3 * j + 1], x2 = p2 - pos[3 * j + 2];
         min_image3(x0, x1, x2, L, gamma);
         double cf[kNPC];
-        pair_coefficients(x0 * x0 + x1 * x1 + x2 * x2, ai2, rad[j] * rad[j], xi, eta, cf);
+        pair_coefficients(x0 * x0 + x1 * x1 + x2 * x2, ai2, rad[j] * rad[j], pk, cf);
         px[k] = (T)x0;
         px[np + k] = (T)x1;
         px[2 * np + k] = (T)x2;
@@ -594,7 +602,8 @@ int build_pair_table(se_ctx *c)
         c->err = "pair table allocation failed";
         return SE_ERR_NOMEM;
     }
-    pair_fill_kernel<T><<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->shear, c->xi, c->eta, c->b.pos, c->b.rad,
+    const PairConst pk{c->xi, c->xi * c->xi, 1.0 / (c->xi * std::sqrt(kPi)), 1.0 / (8 * kPi * c->eta)};
+    pair_fill_kernel<T><<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->shear, pk, c->b.pos, c->b.rad,
                                                     c->b.pair_off, np, c->b.pair_j, (T *)c->b.pair_x[q],
                                                     (T *)c->b.pair_c[q]);
     c->launches++;

@@ -244,6 +244,33 @@ def test_gather_variants_agree(small_poly, small_poly_ref, size_mode):
     assert rel(out[2], out[1]) <= 1e-13
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_real_space_placement_identical(oracle_mod, precision):
+    """The real-space sum in line or on the second stream beside the spread or the FFT
+    chain computes every target's sum in the same order: the products are bitwise
+    identical (each placement twice), and they match the oracle."""
+    from paper_1506_08481_b300 import params
+    cfg = inputs.bidisperse(seed=3, n=3000, phi=0.3)
+    x = inputs.moments(cfg.N, np.random.default_rng(4), 12)
+    sp = params.choose(cfg.L, cfg.N, 2.5e-7, a_eff=params.effective_radius(cfg.rad), precision=precision,
+                       fp32_tol=1e-6 if precision == 0 else None)
+    ctx = make_ctx(sp.xi, sp.M, sp.P, sp.rc, cfg, precision=precision, size_mode=1)
+    ctx.set_option(api.SE_OPT_SHAPE_M, sp.m)
+    dt = torch.float32 if precision == 0 else torch.float64
+    outs = []
+    for overlap in (2, 0, 1, 2):
+        ctx.set_option(api.SE_OPT_OVERLAP, overlap)
+        outs.append(gpu_apply(ctx, x, dt))
+        outs.append(gpu_apply(ctx, x, dt))
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    rows = np.random.default_rng(5).choice(cfg.N, 12, replace=False)
+    ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x, rows=rows, tol=1e-12)
+    assert rel(outs[0][rows], ref) <= 1e-6
+    with pytest.raises(api.SeError):
+        ctx.set_option(api.SE_OPT_OVERLAP, 3)
+
+
 @pytest.mark.parametrize("precision", [1, 0])
 def test_cutoff_boundary_pairs(oracle_mod, precision):
     """Pairs at |x| = rc (1 +- delta), delta from 1e-13 to 1e-2, along axes, diagonals and
