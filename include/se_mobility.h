@@ -120,6 +120,12 @@ typedef struct se_ctx se_ctx;
                                   per stored pair: 7 GB at N = 2e5, rc = 7.5, phi = 0.45), so the
                                   double-float real-space sum reads no FP64 values; 0 drops it and the sum
                                   converts the FP64 table as it reads it (same result, less memory, more time) */
+#define SE_OPT_PAIR_FILL  18   /* evaluation of the FP32 real-space pair table's radial coefficients (once per
+                                  configuration): 0 (default) = double-float arithmetic on the FP32 pipe
+                                  (erfc through a table of Chebyshev interpolants of erfc(x) exp(x^2), exp by
+                                  argument reduction and its Taylor series), with FP64 for pairs closer than
+                                  0.1 or with xi r > 8.5; 1 = FP64 for every pair.  Both give the coefficients
+                                  to within an FP32 rounding; changing it re-evaluates the table */
 #define SE_OPT_OVERLAP_CHECK 13  /* 1 (default): se_set_config fails with SE_ERR_OVERLAP if two spheres within
                                   the real-space cutoff overlap (touching is allowed; the far-field
                                   interactions of overlapping spheres are not those of the paper, and

@@ -35,6 +35,7 @@ SE_OPT_FF_TABLE = 16
 SE_OPT_PC_THETA = 10
 SE_OPT_PC_KA = 11
 SE_OPT_PC_CMAX = 17
+SE_OPT_PAIR_FILL = 18
 STAGES = ("permute", "real", "spread", "fft_x_fwd", "fft_y_fwd", "fft_z_scale", "fft_y_inv", "fft_x_inv", "gather")
 SE_PRECOND_NONE, SE_PRECOND_BLOCK, SE_PRECOND_LEARNED, SE_PRECOND_SPECTRAL = 0, 1, 2, 3
 

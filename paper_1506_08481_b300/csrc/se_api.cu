@@ -516,6 +516,15 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
             c->pc_ready = false;
         }
         return SE_OK;
+    case SE_OPT_PAIR_FILL:
+        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "pair fill must be 0 or 1");
+        if ((int)value != c->pair_fill_fp64) {
+            c->pair_fill_fp64 = (int)value;
+            dfree(c->b.pair_x[0]);          // the FP32 table is evaluated again when next needed
+            dfree(c->b.pair_c[0]);
+            c->pairs_ok[0] = false;
+        }
+        return SE_OK;
     case SE_OPT_OVERLAP_CHECK:
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "overlap check must be 0 or 1");
         c->overlap_check = (int)value;

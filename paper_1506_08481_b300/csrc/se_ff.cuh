@@ -106,6 +106,46 @@ __device__ __forceinline__ ff shfl_xor(unsigned mask, ff v, int off)
     return ff(__shfl_xor_sync(mask, v.hi, off), __shfl_xor_sync(mask, v.lo, off));
 }
 
+// Square root of a double-float: one Newton step from the FP32 root, r = s + (a - s^2) / (2 s),
+// with s^2 formed exactly (two-product); relative error about 2^-44.
+__device__ __forceinline__ ff ff_sqrt(ff a)
+{
+    const float s = sqrtf(a.hi);
+    const float p = s * s, e = fmaf(s, s, -p);
+    const ff d = a - ff(p, e);
+    return ff_norm(s, d.hi / (2.0f * s));
+}
+
+// exp(t) of a double-float argument, -87 < t <= 0 (results stay normal FP32 numbers): the
+// textbook argument reduction t = k ln 2 + u, |u| <= ln2 / 2, with ln 2 = L1 + L2 split so that
+// k L1 is exact (L1 = 2839 / 4096 has 12 significant bits, |k| < 2^7), exp(u) by its Taylor
+// series to degree 11 in double-float Horner form (truncation 6e-15 relative at |u| = ln2 / 2),
+// then the exact scaling by 2^k.
+__device__ __forceinline__ ff ff_exp(ff t)
+{
+    // 1/n! as double-floats, n = 0..11
+    constexpr float c[12][2] = {{1.0f, 0.0f},
+                                {1.0f, 0.0f},
+                                {0.5f, 0.0f},
+                                {0.1666666716337204f, -4.967053879312289e-09f},
+                                {0.0416666679084301f, -1.2417634698280722e-09f},
+                                {0.008333333767950535f, -4.34617203337595e-10f},
+                                {0.0013888889225199819f, -3.3631094437103215e-11f},
+                                {0.00019841270113829523f, -2.725596874933456e-12f},
+                                {2.4801587642286904e-05f, -3.40699609366682e-13f},
+                                {2.7557318844628753e-06f, 3.793571224297229e-14f},
+                                {2.755731998149713e-07f, -7.575112209051195e-15f},
+                                {2.5052107943679403e-08f, 4.4176230446483665e-16f}};
+    constexpr float L1 = 0.693115234375f, L2h = 3.194618329871446e-05f, L2l = 1.6465949697480609e-12f;
+    const float k = rintf(t.hi * 1.44269504088896341f);
+    const ff u = (t - ff(k * L1, 0.f)) - ff(k) * ff(L2h, L2l);
+    ff q(c[11][0], c[11][1]);
+#pragma unroll
+    for (int n = 10; n >= 0; --n) q = q * u + ff(c[n][0], c[n][1]);
+    const int ki = (int)k;
+    return ff(ldexpf(q.hi, ki), ldexpf(q.lo, ki));
+}
+
 struct __align__(32) ff4 {
     ff x, y, z, w;
 };

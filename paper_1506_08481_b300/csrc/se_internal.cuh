@@ -118,6 +118,7 @@ struct se_ctx {
     int gather = 0;              // SE_OPT_GATHER
     int spread = 0;              // SE_OPT_SPREAD
     int overlap_check = 1;       // SE_OPT_OVERLAP_CHECK
+    int pair_fill_fp64 = 0;      // SE_OPT_PAIR_FILL
     int ff_table = 1;            // SE_OPT_FF_TABLE
     double shear = 0.0;          // SE_OPT_SHEAR: strain gamma of the periodic cell
     int nsplit = 1;              // CTAs sharing a spreading tile (few tiles: small M)

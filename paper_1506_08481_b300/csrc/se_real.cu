@@ -31,6 +31,9 @@
 // E rows are accumulated as a symmetric tensor and projected on the orthonormal
 // traceless basis at the end.
 #include <cmath>
+#include <type_traits>
+#include <vector>
+#include <algorithm>
 
 #include "se_internal.cuh"
 #include "se_real_table.cuh"
@@ -323,31 +326,34 @@ struct PairConst {
     double xi, x2, exn, c8;
 };
 
-// The B_n need one FP64 division (1/r^2), a square root and the two special functions;
-// the Faxen factors a^2/6, a^2/10 and their products are multiplications by constants.
-__device__ __forceinline__ void pair_coefficients(double r2, double ai2, double aj2, const PairConst &k, double *cf)
+// The 19 coefficients from B_0 = erfc(xi r)/r and ex = exp(-xi^2 r^2)/(xi sqrt(pi)) by the
+// recurrence above, in arithmetic R (FP64, or double-float for the FP32 table): the Laplacians
+// of psi cancel (a float64 evaluation loses up to 14 bits against a 50-digit one), so R carries
+// more than the stored precision.  tx2 = 2 xi^2; i6, i10 = 1/6, 1/10; c8 = 1/(8 pi eta).
+template <typename R>
+__device__ __forceinline__ void pair_coefficients_B(const R r2, const R ir2, const R B0, const R ex, const R ai2,
+                                                    const R aj2, const R tx2, const R c8, const R i6, const R i10,
+                                                    R *cf)
 {
-    const double r = sqrt(r2), ir2 = 1.0 / r2;
-    const double ex = exp(-k.x2 * r2) * k.exn;
-    double B[8];
-    B[0] = erfc(k.xi * r) * (r * ir2);
-    double pw = 1.0;
+    R B[8];
+    B[0] = B0;
+    R pw = tx2;
+#pragma unroll
     for (int n = 1; n < 8; ++n) {
-        pw *= 2 * k.x2;
         B[n] = ((2 * n - 1) * B[n - 1] + pw * ex) * ir2;
+        pw = pw * tx2;
     }
-    const double s1 = B[0], s2 = -B[1], s3 = B[2], s4 = -B[3], s5 = B[4], s6 = -B[5], s7 = B[6], s8 = -B[7];
-    const double l1 = 5 * s2 + r2 * s3, l2 = 7 * s3 + r2 * s4, l3 = 9 * s4 + r2 * s5, l4 = 11 * s5 + r2 * s6,
-                 l5 = 13 * s6 + r2 * s7, l6 = 15 * s7 + r2 * s8;
-    const double m1 = 5 * l2 + r2 * l3, m2 = 7 * l3 + r2 * l4, m3 = 9 * l4 + r2 * l5, m4 = 11 * l5 + r2 * l6;
-    const double p1 = -B[1], p2 = B[2], p3 = -B[3], p4 = B[4];
-    const double q1 = 5 * p2 + r2 * p3, q2 = 7 * p3 + r2 * p4;
-    const double c8 = k.c8, c16 = 0.5 * c8, c32 = 0.25 * c8;
-    constexpr double i6 = 1.0 / 6, i10 = 0.1;
-    const double ai6 = ai2 * i6, aj6 = aj2 * i6, ai10 = ai2 * i10, aj10 = aj2 * i10;
+    const R s1 = B[0], s2 = -B[1], s3 = B[2], s4 = -B[3], s5 = B[4], s6 = -B[5], s7 = B[6], s8 = -B[7];
+    const R l1 = 5 * s2 + r2 * s3, l2 = 7 * s3 + r2 * s4, l3 = 9 * s4 + r2 * s5, l4 = 11 * s5 + r2 * s6,
+            l5 = 13 * s6 + r2 * s7, l6 = 15 * s7 + r2 * s8;
+    const R m1 = 5 * l2 + r2 * l3, m2 = 7 * l3 + r2 * l4, m3 = 9 * l4 + r2 * l5, m4 = 11 * l5 + r2 * l6;
+    const R p1 = -B[1], p2 = B[2], p3 = -B[3], p4 = B[4];
+    const R q1 = 5 * p2 + r2 * p3, q2 = 7 * p3 + r2 * p4;
+    const R c16 = c8 * R(0.5f), c32 = c8 * R(0.25f);
+    const R ai6 = ai2 * i6, aj6 = aj2 * i6, ai10 = ai2 * i10, aj10 = aj2 * i10;
     {
-        const double c1 = ai6 + aj6, cc = ai6 * aj6;                 // (a_i^2 + a_j^2)/6, a_i^2 a_j^2/36
-        const double G1 = s1 + c1 * l1 + cc * m1, G2 = s2 + c1 * l2 + cc * m2;
+        const R c1 = ai6 + aj6, cc = ai6 * aj6;                      // (a_i^2 + a_j^2)/6, a_i^2 a_j^2/36
+        const R G1 = s1 + c1 * l1 + cc * m1, G2 = s2 + c1 * l2 + cc * m2;
         cf[0] = c8 * (2 * G1 + r2 * G2);
         cf[1] = c8 * G2;
     }
@@ -356,22 +362,22 @@ __device__ __forceinline__ void pair_coefficients(double r2, double ai2, double 
     cf[4] = c32 * l2;
     cf[5] = c32 * (2 * l1 + r2 * l2);
     {
-        const double c1 = ai6 + aj10, cc = ai6 * aj10;               // a_i^2/6 + a_j^2/10, a_i^2 a_j^2/60
-        const double G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
+        const R c1 = ai6 + aj10, cc = ai6 * aj10;                    // a_i^2/6 + a_j^2/10, a_i^2 a_j^2/60
+        const R G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
         cf[6] = -c8 * (3 * G2 + r2 * G3);
         cf[7] = c8 * G3;
     }
     cf[8] = -c16 * (l2 + aj10 * m2);
     {
-        const double c1 = ai10 + aj6, cc = ai10 * aj6;
-        const double G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
+        const R c1 = ai10 + aj6, cc = ai10 * aj6;
+        const R G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3;
         cf[9] = c8 * (3 * G2 + r2 * G3);
         cf[10] = -c8 * G3;
     }
     cf[11] = c16 * (l2 + ai10 * m2);
     {
-        const double c1 = ai10 + aj10, cc = ai10 * aj10;             // (a_i^2 + a_j^2)/10, a_i^2 a_j^2/100
-        const double G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3, G4 = s4 + c1 * l4 + cc * m4;
+        const R c1 = ai10 + aj10, cc = ai10 * aj10;                  // (a_i^2 + a_j^2)/10, a_i^2 a_j^2/100
+        const R G2 = s2 + c1 * l2 + cc * m2, G3 = s3 + c1 * l3 + cc * m3, G4 = s4 + c1 * l4 + cc * m4;
         cf[12] = -c8 * (3 * G2 + r2 * G3);
         cf[13] = -c8 * (3 * G3 + r2 * G4);
         cf[14] = c8 * G4;
@@ -380,6 +386,53 @@ __device__ __forceinline__ void pair_coefficients(double r2, double ai2, double 
     cf[16] = -c16 * (p2 + ai10 * q2);
     cf[17] = -3 * c16 * (p1 + aj6 * q1);
     cf[18] = 3 * c16 * (p2 + aj10 * q2);
+}
+
+// FP64 evaluation: one FP64 division (1/r^2), a square root and the two special functions.
+__device__ __forceinline__ void pair_coefficients(double r2, double ai2, double aj2, const PairConst &k, double *cf)
+{
+    const double r = sqrt(r2), ir2 = 1.0 / r2;
+    const double ex = exp(-k.x2 * r2) * k.exn;
+    const double B0 = erfc(k.xi * r) * (r * ir2);
+    pair_coefficients_B<double>(r2, ir2, B0, ex, ai2, aj2, 2 * k.x2, k.c8, 1.0 / 6, 0.1, cf);
+}
+
+// ---- double-float evaluation for the FP32 table (B300's FP32 pipe issues tens of times the
+// operations of its FP64 pipe).  erfc(x) = erfcx(x) exp(-x^2), with the scaled complementary error
+// function erfcx from a table of Chebyshev interpolants (kErfcxDeg + 1 points per interval of width
+// 1/4 on [0, xi rc], built on the host from the C library's long-double erfc and exp and stored as
+// double-float coefficients of the monomials in t = 8 x - (2 j + 1) in [-1, 1]; interpolation error
+// below 1e-14 relative) and exp(-x^2) from ff_exp.  Pairs outside the range where the double-float
+// values stay normal FP32 numbers (r < 0.1, where B_7 ~ r^-15 grows large; xi r > kFfXmax, where
+// exp(-x^2) approaches the FP32 underflow) take the FP64 evaluation.
+constexpr int kErfcxDeg = 9;
+constexpr double kFfXmax = 8.5, kFfR2min = 0.01;
+
+struct PairConstFF {
+    ff xi, x2, exn, tx2, c8, i6, i10;
+};
+
+__device__ __forceinline__ ff erfcx_ff(ff x, const float2 *tab, int nint)
+{
+    const int j = max(0, min(nint - 1, (int)(x.hi * 4.0f)));
+    const ff t = ff(8.0f * x.hi, 8.0f * x.lo) - ff((float)(2 * j + 1), 0.f);
+    const float2 *c = tab + j * (kErfcxDeg + 1);
+    ff q(c[kErfcxDeg].x, c[kErfcxDeg].y);
+#pragma unroll
+    for (int m = kErfcxDeg - 1; m >= 0; --m) q = q * t + ff(c[m].x, c[m].y);
+    return q;
+}
+
+__device__ __forceinline__ void pair_coefficients_ff(double r2d, double ai2d, double aj2d, const PairConstFF &k,
+                                                     const float2 *tab, int nint, float *cf)
+{
+    const ff r2 = ff(r2d), r = ff_sqrt(r2), ir2 = ff(1) / r2;
+    const ff e2 = ff_exp(-(k.x2 * r2));                 // exp(-xi^2 r^2)
+    const ff B0 = erfcx_ff(k.xi * r, tab, nint) * e2 * (r * ir2);
+    ff c[kNPC];
+    pair_coefficients_B<ff>(r2, ir2, B0, e2 * k.exn, ff(ai2d), ff(aj2d), k.tx2, k.c8, k.i6, k.i10, c);
+#pragma unroll
+    for (int q = 0; q < kNPC; ++q) cf[q] = c[q].hi + c[q].lo;
 }
 
 // Neighbour search for target i (cell order): calls f(j) for every j != i with
@@ -508,6 +561,41 @@ __global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double 
     }
 }
 
+// The FP32 table with the coefficients in double-float arithmetic where its range allows
+// (pair_coefficients_ff), in FP64 elsewhere; the separation is formed in FP64 as above.
+__global__ void __launch_bounds__(256) pair_fill_ff_kernel(int N, double L, double gamma, PairConst pk,
+                                                           PairConstFF pkf, const float2 *etab, int nint,
+                                                           double r2_ff_max, const double *pos, const double *rad,
+                                                           const int *off, size_t np, const int *pj, float *px,
+                                                           float *pc)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= N) return;
+    const double p0 = pos[3 * i], p1 = pos[3 * i + 1], p2 = pos[3 * i + 2], ai2 = rad[i] * rad[i];
+    const int ke = off[i + 1];
+    for (int k = off[i] + lane; k < ke; k += 32) {
+        const int j = pj[k];
+        double x0 = p0 - pos[3 * j], x1 = p1 - pos[3 * j + 1], x2 = p2 - pos[3 * j + 2];
+        min_image3(x0, x1, x2, L, gamma);
+        const double r2 = x0 * x0 + x1 * x1 + x2 * x2, aj2 = rad[j] * rad[j];
+        float cf[kNPC];
+        if (r2 >= kFfR2min && r2 <= r2_ff_max) {
+            pair_coefficients_ff(r2, ai2, aj2, pkf, etab, nint, cf);
+        } else {
+            double cd[kNPC];
+            pair_coefficients(r2, ai2, aj2, pk, cd);
+#pragma unroll
+            for (int q = 0; q < kNPC; ++q) cf[q] = (float)cd[q];
+        }
+        px[k] = (float)x0;
+        px[np + k] = (float)x1;
+        px[2 * np + k] = (float)x2;
+#pragma unroll
+        for (int q = 0; q < kNPC; ++q) pc[q * np + k] = cf[q];
+    }
+}
+
 // One warp per target (real_table_body).
 template <typename T, int NCOMP, typename TL = T>
 __global__ void __launch_bounds__(256) real_table_kernel(int N, const int *off, size_t np, const int *pj,
@@ -518,6 +606,55 @@ __global__ void __launch_bounds__(256) real_table_kernel(int N, const int *off, 
 }
 
 }  // namespace
+
+// Chebyshev interpolants of erfcx(x) = erfc(x) exp(x^2) on the intervals [j/4, (j+1)/4] covering
+// [0, xmax]: values at the kErfcxDeg + 1 Chebyshev points of each interval from the C library's
+// long-double erfc and exp, Chebyshev coefficients by the discrete cosine sums, converted to the
+// monomial basis of t in [-1, 1] (T_{m+1} = 2 t T_m - T_{m-1}) and stored as double-floats.
+static std::vector<float2> erfcx_table(double xmax, int &nint)
+{
+    constexpr int n = kErfcxDeg + 1;
+    nint = std::max(1, (int)std::ceil(xmax * 4));
+    std::vector<float2> tab((size_t)nint * n);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int j = 0; j < nint; ++j) {
+        long double f[n], cheb[n], mono[n] = {}, Tprev[n] = {}, Tcur[n] = {}, Tnext[n];
+        for (int k = 0; k < n; ++k) {
+            const long double th = pi * (k + 0.5L) / n;
+            const long double x = (j + (std::cos(th) + 1) / 2) / 4.0L;
+            f[k] = std::erfc(x) * std::exp(x * x);
+        }
+        for (int m = 0; m < n; ++m) {
+            long double acc = 0;
+            for (int k = 0; k < n; ++k) acc += f[k] * std::cos(m * pi * (k + 0.5L) / n);
+            cheb[m] = 2 * acc / n;
+        }
+        cheb[0] /= 2;
+        Tprev[0] = 1;                                   // T_0
+        Tcur[1] = 1;                                    // T_1
+        mono[0] = cheb[0];
+        for (int m = 1; m < n; ++m) {
+            for (int d = 0; d < n; ++d) mono[d] += cheb[m] * Tcur[d];
+            for (int d = 0; d < n; ++d) Tnext[d] = (d > 0 ? 2 * Tcur[d - 1] : 0) - Tprev[d];
+            for (int d = 0; d < n; ++d) {
+                Tprev[d] = Tcur[d];
+                Tcur[d] = Tnext[d];
+            }
+        }
+        for (int d = 0; d < n; ++d) {
+            const float hi = (float)mono[d];
+            tab[(size_t)j * n + d] = make_float2(hi, (float)(mono[d] - (long double)hi));
+        }
+    }
+    return tab;
+}
+
+static PairConstFF ff_constants(const PairConst &k)
+{
+    auto split = [](double d) { const float h = (float)d; return ff(h, (float)(d - (double)h)); };
+    return PairConstFF{split(k.xi), split(k.x2), split(k.exn), split(2 * k.x2), split(k.c8), split(1.0 / 6),
+                       split(0.1)};
+}
 
 // neighbour lists (precision independent) and coefficients at precision T
 template <typename T>
@@ -603,11 +740,38 @@ int build_pair_table(se_ctx *c)
         return SE_ERR_NOMEM;
     }
     const PairConst pk{c->xi, c->xi * c->xi, 1.0 / (c->xi * std::sqrt(kPi)), 1.0 / (8 * kPi * c->eta)};
-    pair_fill_kernel<T><<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->shear, pk, c->b.pos, c->b.rad,
-                                                    c->b.pair_off, np, c->b.pair_j, (T *)c->b.pair_x[q],
-                                                    (T *)c->b.pair_c[q]);
+    float2 *etab = nullptr;
+    int nint = 0;
+    if (std::is_same<T, float>::value && !c->pair_fill_fp64) {
+        // erfcx table on [0, min(xi rc, kFfXmax)] (the pairs beyond take the FP64 evaluation)
+        const double xmax = std::min(c->xi * c->rc * (1 + 1e-6), kFfXmax);
+        const std::vector<float2> h = erfcx_table(xmax, nint);
+        if (cudaMalloc(&etab, h.size() * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            etab = nullptr;           // the FP64 evaluation below
+        } else if (cudaMemcpyAsync(etab, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice, s) !=
+                   cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(etab);
+            etab = nullptr;
+        }
+    }
+    if (etab) {
+        const double xm = nint * 0.25 < kFfXmax ? nint * 0.25 : kFfXmax;    // table end
+        const double r2max = (xm / c->xi) * (xm / c->xi);
+        const PairConstFF pkf = ff_constants(pk);
+        pair_fill_ff_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->shear, pk, pkf, etab, nint, r2max, c->b.pos,
+                                                         c->b.rad, c->b.pair_off, np, c->b.pair_j,
+                                                         (float *)c->b.pair_x[q], (float *)c->b.pair_c[q]);
+    } else {
+        pair_fill_kernel<T><<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->shear, pk, c->b.pos, c->b.rad,
+                                                        c->b.pair_off, np, c->b.pair_j, (T *)c->b.pair_x[q],
+                                                        (T *)c->b.pair_c[q]);
+    }
     c->launches++;
-    SE_CUDA_CHECK(c, cudaStreamSynchronize(s));
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (etab) cudaFree(etab);
+    SE_CUDA_CHECK(c, e);
     c->pairs_ok[q] = true;
     return SE_OK;
 }

@@ -271,6 +271,48 @@ def test_real_space_placement_identical(oracle_mod, precision):
         ctx.set_option(api.SE_OPT_OVERLAP, 3)
 
 
+def _fill_case(case):
+    rng = np.random.default_rng({"poly": 21, "close": 22, "wide": 23}[case])
+    if case == "poly":
+        rad = rng.uniform(0.3, 1.0, 500)
+        L = inputs.box_side(rad, 0.3)
+        return inputs.Config(case, L, inputs.positions_rsa(rad, L, rng), rad), 0.7, min(7.0, 0.49 * L)
+    if case == "close":
+        # pairs at separation 0.085 (spheres of radius 0.04 nearly touching): r < 0.1
+        L, n = 4.0, 150
+        c = inputs.positions_rsa(np.full(n, 0.2), L, rng)
+        d = rng.standard_normal((n, 3))
+        d *= 0.085 / np.linalg.norm(d, axis=1, keepdims=True)
+        pos = np.concatenate([c, c + d])
+        return inputs.Config(case, L, pos, np.full(2 * n, 0.04)), 3.0, 1.5
+    rad = np.full(200, 0.5)
+    L = 12.0
+    return inputs.Config(case, L, inputs.positions_rsa(rad, L, rng), rad), 2.0, 5.0      # xi rc = 10
+
+
+@pytest.mark.parametrize("case", ["poly", "close", "wide"])
+def test_pair_fill_double_float(oracle_mod, case):
+    """The FP32 pair table's radial coefficients evaluated in double-float arithmetic
+    (SE_OPT_PAIR_FILL 0, the default) and in FP64 (1) round to the same FP32 numbers but for
+    rare last-bit differences: the FP32 real-space products agree to 2e-8 relative, and both
+    match the oracle's real-space sum to FP32 accuracy.  'close' has pairs closer than 0.1 and
+    'wide' has xi r up to 10, both beyond the double-float range (those pairs take FP64)."""
+    cfg, xi, rc = _fill_case(case)
+    x = inputs.moments(cfg.N, np.random.default_rng(5), 12)
+    ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x, xi=xi, rc=rc, kc=1.0, parts=1)
+    ctx = make_ctx(xi, 32, 12, rc, cfg, precision=0, parts=1)
+    y_ff = gpu_apply(ctx, x, torch.float32)
+    ctx.set_option(api.SE_OPT_PAIR_FILL, 1)
+    y_64 = gpu_apply(ctx, x, torch.float32)
+    ctx.set_option(api.SE_OPT_PAIR_FILL, 0)
+    assert np.array_equal(gpu_apply(ctx, x, torch.float32), y_ff)
+    assert rel(y_ff, y_64) <= 2e-8
+    assert rel(y_ff[:, :11], ref[:, :11]) <= 5e-7
+    assert rel(y_64[:, :11], ref[:, :11]) <= 5e-7
+    with pytest.raises(api.SeError):
+        ctx.set_option(api.SE_OPT_PAIR_FILL, 2)
+
+
 @pytest.mark.parametrize("precision", [1, 0])
 def test_cutoff_boundary_pairs(oracle_mod, precision):
     """Pairs at |x| = rc (1 +- delta), delta from 1e-13 to 1e-2, along axes, diagonals and
