@@ -118,7 +118,9 @@ static void free_grids(se_ctx *c)
     }
 }
 
-static void free_config(se_ctx *c)
+// keep_pairs: the pair table's buffers stay allocated for the next configuration (set_config
+// overwrites them in place), only the table's validity is dropped
+static void free_config(se_ctx *c, bool keep_pairs = false)
 {
     free_spectral(c);
     c->lp_ready = false;
@@ -139,11 +141,19 @@ static void free_config(se_ctx *c)
         dfree(c->b.rel[q]);
         c->support_ok[q] = false;
     }
-    dfree_t(c->b.pair_off);
-    dfree_t(c->b.pair_j);
+    c->lists_ok = false;
+    if (!keep_pairs) {
+        dfree_t(c->b.pair_off);
+        dfree_t(c->b.pair_j);
+        c->pair_off_n = 0;
+        c->pairj_cap = 0;
+    }
     for (int q = 0; q < 3; ++q) {
-        dfree(c->b.pair_x[q]);
-        dfree(c->b.pair_c[q]);
+        if (!keep_pairs || q == 2) {
+            dfree(c->b.pair_x[q]);
+            dfree(c->b.pair_c[q]);
+            c->pair_cap[q] = 0;
+        }
         c->pairs_ok[q] = false;
     }
     c->npairs = 0;
@@ -307,6 +317,7 @@ static int ensure_support(se_ctx *c, int prec)
             cudaGetLastError();
             dfree(c->b.pair_x[prec]);
             dfree(c->b.pair_c[prec]);
+            c->pair_cap[prec] = 0;
             c->err.clear();
         }
     }
@@ -444,6 +455,7 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
             for (int q = 0; q < 3; ++q) {
                 dfree(c->b.pair_x[q]);
                 dfree(c->b.pair_c[q]);
+                c->pair_cap[q] = 0;
                 c->pairs_ok[q] = false;
                 c->support_ok[q] = false;
             }
@@ -520,9 +532,7 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "pair fill must be 0 or 1");
         if ((int)value != c->pair_fill_fp64) {
             c->pair_fill_fp64 = (int)value;
-            dfree(c->b.pair_x[0]);          // the FP32 table is evaluated again when next needed
-            dfree(c->b.pair_c[0]);
-            c->pairs_ok[0] = false;
+            c->pairs_ok[0] = false;         // the FP32 table is evaluated again when next needed
         }
         return SE_OK;
     case SE_OPT_OVERLAP_CHECK:
@@ -548,8 +558,10 @@ extern "C" int se_set_config(se_ctx *c, int64_t N, double L, const double *pos, 
     if (c->shear != 0 && c->size_mode != 2 && c->size_mode != 3)
         return set_error(c, SE_ERR_ARG, "a sheared cell needs a wave-space size approach (SE_OPT_SIZE_MODE 2 or 3)");
     cudaSetDevice(c->device);
-    SE_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
-    free_config(c);
+    // the pair table is overwritten in place: work of this context in flight on any stream
+    // (its own two, a batch's stream pool or graph) must finish first, as a cudaFree would wait
+    SE_CUDA_CHECK(c, cudaDeviceSynchronize());
+    free_config(c, true);
     c->N = N;
     c->L = L;
     // cells uniform in the fractional coordinates: the rc ball reaches (1 + |gamma|) rc along t_x

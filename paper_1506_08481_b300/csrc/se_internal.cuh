@@ -128,6 +128,12 @@ struct se_ctx {
     bool tiles_ok = false;
     bool pairs_ok[3] = {false, false, false};
     size_t npairs = 0;
+    // the pair table's buffers outlive a configuration: set_config overwrites them in place
+    // (same N for the offsets, the neighbour indices and coefficients while they fit)
+    bool lists_ok = false;       // neighbour lists of the current configuration built
+    int64_t pair_off_n = 0;      // N of the allocated offsets
+    size_t pairj_cap = 0;        // allocated neighbour indices
+    size_t pair_cap[3] = {};     // pairs the coefficient buffers of precision q hold (0, 1)
     size_t grid_M[3] = {0, 0, 0};
     int64_t N = 0;
     double L = 0;

@@ -662,7 +662,7 @@ int build_pair_table(se_ctx *c)
 {
     cudaStream_t s = c->stream;
     const int N = (int)c->N;
-    if (!c->b.pair_off) {
+    if (!c->lists_ok) {
         int *count = nullptr;
         float4 *pf = nullptr;
         auto release = [&]() {
@@ -674,6 +674,8 @@ int build_pair_table(se_ctx *c)
             if (c->b.pair_j) cudaFree(c->b.pair_j);
             c->b.pair_off = nullptr;
             c->b.pair_j = nullptr;
+            c->pair_off_n = 0;
+            c->pairj_cap = 0;
         };
         auto fail = [&]() {
             cudaGetLastError();
@@ -690,8 +692,17 @@ int build_pair_table(se_ctx *c)
             c->err = std::string("pair table build: ") + cudaGetErrorString(e);
             return SE_ERR_CUDA;
         };
-        if (cudaMalloc(&c->b.pair_off, (N + 1) * sizeof(int)) != cudaSuccess ||
-            cudaMalloc(&count, (N + 1) * sizeof(int)) != cudaSuccess || cudaMalloc(&pf, N * sizeof(float4)) != cudaSuccess)
+        // the previous configuration's buffers are overwritten in place when they fit
+        if (c->b.pair_off && c->pair_off_n != N) {
+            cudaFree(c->b.pair_off);
+            c->b.pair_off = nullptr;
+            c->pair_off_n = 0;
+        }
+        if (!c->b.pair_off) {
+            if (cudaMalloc(&c->b.pair_off, (N + 1) * sizeof(int)) != cudaSuccess) return fail();
+            c->pair_off_n = N;
+        }
+        if (cudaMalloc(&count, (N + 1) * sizeof(int)) != cudaSuccess || cudaMalloc(&pf, N * sizeof(float4)) != cudaSuccess)
             return fail();
         PairSearch ps;
         ps.L = c->L;
@@ -722,22 +733,39 @@ int build_pair_table(se_ctx *c)
             return SE_ERR_OVERLAP;
         }
         c->npairs = (size_t)np;
-        if (cudaMalloc(&c->b.pair_j, (c->npairs + 1) * sizeof(int)) != cudaSuccess) return fail();
+        if (c->npairs + 1 > c->pairj_cap) {
+            if (c->b.pair_j) cudaFree(c->b.pair_j);
+            c->b.pair_j = nullptr;
+            c->pairj_cap = 0;
+            const size_t cap = c->npairs + 1 + c->npairs / 16;      // room for the next configurations
+            if (cudaMalloc(&c->b.pair_j, cap * sizeof(int)) != cudaSuccess) return fail();
+            c->pairj_cap = cap;
+        }
         pair_list_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ps, c->b.cell_start, c->b.pos, pf, c->b.pair_off,
                                                          c->b.pair_j);
         c->launches++;
         if (int rc = sync()) return rc;
         release();
+        c->lists_ok = true;
     }
     const int q = pix<T>();
     const size_t np = c->npairs;
-    if (cudaMalloc(&c->b.pair_x[q], (3 * np + 1) * sizeof(T)) != cudaSuccess ||
-        cudaMalloc(&c->b.pair_c[q], ((size_t)kNPC * np + 1) * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
+    if (c->pair_cap[q] < np) {
         if (c->b.pair_x[q]) cudaFree(c->b.pair_x[q]);
-        c->b.pair_x[q] = nullptr;
-        c->err = "pair table allocation failed";
-        return SE_ERR_NOMEM;
+        if (c->b.pair_c[q]) cudaFree(c->b.pair_c[q]);
+        c->b.pair_x[q] = c->b.pair_c[q] = nullptr;
+        c->pair_cap[q] = 0;
+        const size_t cap = np + np / 16;                           // room for the next configurations
+        if (cudaMalloc(&c->b.pair_x[q], (3 * cap + 1) * sizeof(T)) != cudaSuccess ||
+            cudaMalloc(&c->b.pair_c[q], ((size_t)kNPC * cap + 1) * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            if (c->b.pair_x[q]) cudaFree(c->b.pair_x[q]);
+            if (c->b.pair_c[q]) cudaFree(c->b.pair_c[q]);
+            c->b.pair_x[q] = c->b.pair_c[q] = nullptr;
+            c->err = "pair table allocation failed";
+            return SE_ERR_NOMEM;
+        }
+        c->pair_cap[q] = cap;
     }
     const PairConst pk{c->xi, c->xi * c->xi, 1.0 / (c->xi * std::sqrt(kPi)), 1.0 / (8 * kPi * c->eta)};
     float2 *etab = nullptr;

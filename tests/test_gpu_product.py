@@ -313,6 +313,32 @@ def test_pair_fill_double_float(oracle_mod, case):
         ctx.set_option(api.SE_OPT_PAIR_FILL, 2)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_config_reuses_pair_buffers(precision):
+    """set_config overwrites the previous configuration's pair table in place while it fits
+    (same N, no more pairs than the buffers hold) and reallocates otherwise: a context
+    taken through configurations A (phi 0.2), B (new positions), C (phi 0.35: more pairs
+    than A's buffers hold), D (fewer particles) and A again gives, after each, the product
+    of a fresh context on that configuration, bit for bit."""
+    rng = np.random.default_rng(31)
+    rad = rng.uniform(0.6, 1.0, 1500)
+    def cfg(phi, n=1500, seed=0):
+        r = rad[:n]
+        L = inputs.box_side(r, phi)
+        return inputs.Config(f"c{phi}_{n}_{seed}", L, inputs.positions_rsa(r, L, np.random.default_rng(seed)), r)
+    cfgs = [cfg(0.2), cfg(0.2, seed=1), cfg(0.35), cfg(0.2, n=900), cfg(0.2)]
+    dt = torch.float32 if precision == 0 else torch.float64
+    xi, M, P = 0.9, 48, 16
+    reused = make_ctx(xi, M, P, 5.0, cfgs[0], precision=precision, size_mode=1)
+    for c in cfgs:
+        x = inputs.moments(c.N, np.random.default_rng(c.N), 12)
+        reused.set_config(c.pos, c.rad, c.L)
+        y = gpu_apply(reused, x, dt)
+        fresh = make_ctx(xi, M, P, 5.0, c, precision=precision, size_mode=1)
+        assert np.array_equal(y, gpu_apply(fresh, x, dt)), c.name
+        fresh.close()
+
+
 @pytest.mark.parametrize("precision", [1, 0])
 def test_cutoff_boundary_pairs(oracle_mod, precision):
     """Pairs at |x| = rc (1 +- delta), delta from 1e-13 to 1e-2, along axes, diagonals and
