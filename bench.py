@@ -47,13 +47,16 @@ FLOPS_PER_POINT = {"spread": 26.0, "gather": 26.0}
 FLOPS_PER_COLUMN = {"spread": 75.0, "gather": 72.0}
 # bytes of one stored real-space pair in FP32 (index 4 + separation 12 + 19 coefficients)
 PAIR_BYTES = 92
+# a monodisperse configuration's table stores 13 of the 19 coefficients (the others follow
+# from a_i = a_j): 68 bytes per pair
+PAIR_BYTES_MONO = 68
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (one product's launches,
 # the command in profiles/dram_mono_n200000_P24.md); the spread stage is spread16_kernel plus
 # sum_parts_kernel.  Other sizes scale them by grid points (M^3), stored pairs or particles.  A kernel
 # changed since that capture has no entry (its traffic is reported as null).
 NCU_CAPTURE = {"N": 200000, "M": 144, "npairs": 88237670}
-NCU_DRAM_BYTES = {"permute": 13.0e6, "real": 8724.4e6, "spread": 385.7e6, "fft_x_fwd": 50.4e6,
+NCU_DRAM_BYTES = {"permute": 13.0e6, "spread": 385.7e6, "fft_x_fwd": 50.4e6,
                   "fft_y_fwd": 48.6e6, "fft_z_scale": 54.7e6, "fft_y_inv": 48.7e6, "fft_x_inv": 50.1e6,
                   "gather": 149.1e6}
 
@@ -170,14 +173,14 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def stage_algorithmic(stage: str, N: int, M: int, P: int, CO: int, npairs: int = 0):
+def stage_algorithmic(stage: str, N: int, M: int, P: int, CO: int, npairs: int = 0, mono: bool = True):
     """(bound, units per launch, unit) of one launch of a stage (FP32 grids)."""
     Mh = M // 2 + 1
     if stage in ("spread", "gather"):
         return "alu", N * P ** 3 * FLOPS_PER_POINT[stage] + N * P ** 2 * FLOPS_PER_COLUMN[stage], "flop"
     if stage == "real":
         # the stored pair table streamed once, moments read and results written once
-        return "hbm", npairs * PAIR_BYTES + N * 12 * 4 * 2, "byte"
+        return "hbm", npairs * (PAIR_BYTES_MONO if mono else PAIR_BYTES) + N * 12 * 4 * 2, "byte"
     if stage == "permute":
         return "hbm", N * 12 * 4 * 2, "byte"
     # FFT passes: one read and one write of the arrays they stream (bytes)

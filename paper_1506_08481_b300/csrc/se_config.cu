@@ -59,7 +59,10 @@ __global__ void wrap_key_kernel(int N, double L, double gamma, int nc, const dou
     posw[3 * i + 1] = t[1];
     posw[3 * i + 2] = t[2];
     key[i] = (k[2] * nc + k[1]) * nc + k[0];
-    if (!ok) atomicExch(bad, 1);
+    if (!ok) atomicOr(bad, 1);
+    // bit 2: a radius differs from the first one (the configuration is not monodisperse)
+    const unsigned act = __activemask();
+    if (__ballot_sync(act, rad_in[i] != rad_in[0]) && (int)(threadIdx.x & 31) == __ffs(act) - 1) atomicOr(bad, 2);
 }
 
 __global__ void histogram_kernel(int N, const int *key, int *count)
@@ -207,10 +210,11 @@ int build_cells(se_ctx *c, const double *pos_in, const double *rad_in)
         c->err = std::string("cell list: ") + cudaGetErrorString(e);
         return SE_ERR_CUDA;
     }
-    if (hbad) {
+    if (hbad & 1) {
         c->err = "non-finite position or non-positive radius";
         return SE_ERR_NONFINITE;
     }
+    c->mono = (hbad & 2) == 0;
     return SE_OK;
 }
 

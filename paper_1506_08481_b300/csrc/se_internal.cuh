@@ -134,6 +134,8 @@ struct se_ctx {
     int64_t pair_off_n = 0;      // N of the allocated offsets
     size_t pairj_cap = 0;        // allocated neighbour indices
     size_t pair_cap[3] = {};     // pairs the coefficient buffers of precision q hold (0, 1)
+    bool mono = false;           // every radius of the configuration equal
+    bool pair_mono[3] = {};      // table q stores the 13 coefficients of a monodisperse configuration
     size_t grid_M[3] = {0, 0, 0};
     int64_t N = 0;
     double L = 0;

@@ -534,13 +534,28 @@ __global__ void pair_list_kernel(int N, PairSearch ps, const int *cell_start, co
     for_neighbours(i, ps, cell_start, pos, pf, [&](int j, float, float) { pj[k++] = j; });
 }
 
+// the coefficients of pair k in the SoA table: all 19, or the 13 stored slots of a monodisperse
+// table (mono_slot)
+template <typename T, typename C>
+__device__ __forceinline__ void store_coefficients(T *pc, size_t np, int k, const C *cf, int mono)
+{
+    if (mono) {
+#pragma unroll
+        for (int q = 0; q < kNPC; ++q)
+            if (mono_slot(q) >= 0) pc[(size_t)mono_slot(q) * np + k] = (T)cf[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < kNPC; ++q) pc[(size_t)q * np + k] = (T)cf[q];
+    }
+}
+
 // One warp per target: the lanes take the target's pairs in turn, form the FP64
 // separation and the radial coefficients and store them (coalesced SoA rows).
 template <typename T>
 __global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double gamma, PairConst pk,
                                                         const double *pos,
                                                         const double *rad, const int *off, size_t np, const int *pj,
-                                                        T *px, T *pc)
+                                                        T *px, T *pc, int mono)
 {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -556,8 +571,7 @@ __global__ void __launch_bounds__(256) pair_fill_kernel(int N, double L, double 
         px[k] = (T)x0;
         px[np + k] = (T)x1;
         px[2 * np + k] = (T)x2;
-#pragma unroll
-        for (int q = 0; q < kNPC; ++q) pc[q * np + k] = (T)cf[q];
+        store_coefficients(pc, np, k, cf, mono);
     }
 }
 
@@ -567,7 +581,7 @@ __global__ void __launch_bounds__(256) pair_fill_ff_kernel(int N, double L, doub
                                                            PairConstFF pkf, const float2 *etab, int nint,
                                                            double r2_ff_max, const double *pos, const double *rad,
                                                            const int *off, size_t np, const int *pj, float *px,
-                                                           float *pc)
+                                                           float *pc, int mono)
 {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -591,18 +605,17 @@ __global__ void __launch_bounds__(256) pair_fill_ff_kernel(int N, double L, doub
         px[k] = (float)x0;
         px[np + k] = (float)x1;
         px[2 * np + k] = (float)x2;
-#pragma unroll
-        for (int q = 0; q < kNPC; ++q) pc[q * np + k] = cf[q];
+        store_coefficients(pc, np, k, cf, mono);
     }
 }
 
 // One warp per target (real_table_body).
-template <typename T, int NCOMP, typename TL = T>
+template <typename T, int NCOMP, typename TL = T, bool MONO = false>
 __global__ void __launch_bounds__(256) real_table_kernel(int N, const int *off, size_t np, const int *pj,
                                                          const TL *px, const TL *pc, const T *xs, T *yreal)
 {
-    real_table_body<T, NCOMP, TL>(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), threadIdx.x & 31, N, off, np,
-                                  pj, px, pc, xs, yreal);
+    real_table_body<T, NCOMP, TL, MONO>(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), threadIdx.x & 31, N, off,
+                                        np, pj, px, pc, xs, yreal);
 }
 
 }  // namespace
@@ -768,6 +781,8 @@ int build_pair_table(se_ctx *c)
         c->pair_cap[q] = cap;
     }
     const PairConst pk{c->xi, c->xi * c->xi, 1.0 / (c->xi * std::sqrt(kPi)), 1.0 / (8 * kPi * c->eta)};
+    // monodisperse FP32 tables store 13 of the 19 coefficients (mono_slot)
+    const int mono = std::is_same<T, float>::value && c->mono ? 1 : 0;
     float2 *etab = nullptr;
     int nint = 0;
     if (std::is_same<T, float>::value && !c->pair_fill_fp64) {
@@ -790,16 +805,17 @@ int build_pair_table(se_ctx *c)
         const PairConstFF pkf = ff_constants(pk);
         pair_fill_ff_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->shear, pk, pkf, etab, nint, r2max, c->b.pos,
                                                          c->b.rad, c->b.pair_off, np, c->b.pair_j,
-                                                         (float *)c->b.pair_x[q], (float *)c->b.pair_c[q]);
+                                                         (float *)c->b.pair_x[q], (float *)c->b.pair_c[q], mono);
     } else {
         pair_fill_kernel<T><<<(N + 7) / 8, 256, 0, s>>>(N, c->L, c->shear, pk, c->b.pos, c->b.rad,
                                                         c->b.pair_off, np, c->b.pair_j, (T *)c->b.pair_x[q],
-                                                        (T *)c->b.pair_c[q]);
+                                                        (T *)c->b.pair_c[q], mono);
     }
     c->launches++;
     const cudaError_t e = cudaStreamSynchronize(s);
     if (etab) cudaFree(etab);
     SE_CUDA_CHECK(c, e);
+    c->pair_mono[q] = mono != 0;
     c->pairs_ok[q] = true;
     return SE_OK;
 }
@@ -827,10 +843,17 @@ void launch_real(se_ctx *c, const T *xs, T *yreal, cudaStream_t s, int ncomp)
                                                           (const T *)c->b.pair_x[q], (const T *)c->b.pair_c[q],
                                                           xs, yreal);
         };
-        if (ncomp <= 3) go(real_table_kernel<T, 3>);
-        else if (ncomp <= 6) go(real_table_kernel<T, 6>);
-        else if (ncomp <= 11) go(real_table_kernel<T, 11>);
-        else go(real_table_kernel<T, 12>);
+        if (c->pair_mono[q]) {
+            if (ncomp <= 3) go(real_table_kernel<T, 3, T, true>);
+            else if (ncomp <= 6) go(real_table_kernel<T, 6, T, true>);
+            else if (ncomp <= 11) go(real_table_kernel<T, 11, T, true>);
+            else go(real_table_kernel<T, 12, T, true>);
+        } else {
+            if (ncomp <= 3) go(real_table_kernel<T, 3>);
+            else if (ncomp <= 6) go(real_table_kernel<T, 6>);
+            else if (ncomp <= 11) go(real_table_kernel<T, 11>);
+            else go(real_table_kernel<T, 12>);
+        }
         c->launches++;
         return;
     }

@@ -9,9 +9,19 @@
 
 namespace se {
 
+// Monodisperse tables (every radius equal) store 13 of the 19 coefficients: with a_i = a_j
+// the Faxen factors of source and target coincide, so c3 = c2, c9 = -c6, c10 = -c7,
+// c11 = -c8, c17 = 3 c15 and c18 = -3 c16.  mono_slot(q): the stored slot of c_q, -1 for the
+// derived ones.
+__host__ __device__ constexpr int mono_slot(int q)
+{
+    return q <= 2 ? q : q == 3 ? -1 : q <= 8 ? q - 1 : q <= 11 ? -1 : q <= 16 ? q - 4 : -1;
+}
+
 // target i, lane 0..31 of its warp; the table is stored at precision TL and read into T
-// (the FP64-equivalent product contracts the FP64 table in double-float arithmetic)
-template <typename T, int NCOMP, typename TL = T>
+// (the FP64-equivalent product contracts the FP64 table in double-float arithmetic);
+// MONO: the table holds the 13 stored slots of a monodisperse configuration.
+template <typename T, int NCOMP, typename TL = T, bool MONO = false>
 __device__ __forceinline__ void real_table_body(int i, int lane, int N, const int *off, size_t np, const int *pj,
                                                 const TL *px, const TL *pc, const T *xs, T *yreal)
 {
@@ -20,6 +30,8 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
 #pragma unroll
     for (int c = 0; c < 13; ++c) a[c] = 0;
     const int k1 = off[i + 1];
+    // coefficient q of pair k (slot q, or its monodisperse slot)
+    auto C = [&](int q, int k) -> T { return T(pc[(size_t)(MONO ? mono_slot(q) : q) * np + k]); };
     for (int k = off[i] + lane; k < k1; k += 32) {
         const int j = pj[k];
         const T x0 = T(px[k]), x1 = T(px[np + k]), x2 = T(px[2 * np + k]);
@@ -27,7 +39,7 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
         const T F0 = xj[0], F1 = xj[1], F2 = xj[2];
         const T xF = x0 * F0 + x1 * F1 + x2 * F2;
         {
-            const T aF = T(pc[k]), bF = T(pc[np + k]) * xF;
+            const T aF = C(0, k), bF = C(1, k) * xF;
             a[0] += aF * F0 - bF * x0;
             a[1] += aF * F1 - bF * x1;
             a[2] += aF * F2 - bF * x2;
@@ -35,14 +47,16 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
         if constexpr (NCOMP >= 6) {
             const T T0 = xj[3], T1 = xj[4], T2 = xj[5];
             const T xT0 = x1 * T2 - x2 * T1, xT1 = x2 * T0 - x0 * T2, xT2 = x0 * T1 - x1 * T0;
-            const T uT = T(pc[2 * np + k]), oF = T(pc[3 * np + k]);
+            const T uT = C(2, k);
+            T oF;
+            if constexpr (MONO) oF = uT; else oF = C(3, k);
             a[0] += uT * xT0;
             a[1] += uT * xT1;
             a[2] += uT * xT2;
             a[3] += oF * (x1 * F2 - x2 * F1);
             a[4] += oF * (x2 * F0 - x0 * F2);
             a[5] += oF * (x0 * F1 - x1 * F0);
-            const T oTa = T(pc[4 * np + k]) * (x0 * T0 + x1 * T1 + x2 * T2), oTb = T(pc[5 * np + k]);
+            const T oTa = C(4, k) * (x0 * T0 + x1 * T1 + x2 * T2), oTb = C(5, k);
             a[3] += oTa * x0 - oTb * T0;
             a[4] += oTa * x1 - oTb * T1;
             a[5] += oTa * x2 - oTb * T2;
@@ -54,20 +68,30 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
                         Sx2 = Sxz * x0 + Syz * x1 + Szz * x2;
                 const T xSx = x0 * Sx0 + x1 * Sx1 + x2 * Sx2;
                 {   // U <- S
-                    const T ua = T(pc[6 * np + k]), ub = T(pc[7 * np + k]) * xSx;
+                    const T c6 = C(6, k), c7 = C(7, k);
+                    const T ua = c6, ub = c7 * xSx;
                     a[0] += ua * Sx0 + ub * x0;
                     a[1] += ua * Sx1 + ub * x1;
                     a[2] += ua * Sx2 + ub * x2;
                 }
                 {   // Om <- S
-                    const T o = T(pc[8 * np + k]);
+                    const T o = C(8, k);
                     a[3] += o * (x1 * Sx2 - x2 * Sx1);
                     a[4] += o * (x2 * Sx0 - x0 * Sx2);
                     a[5] += o * (x0 * Sx1 - x1 * Sx0);
                 }
                 // E (symmetric tensor xx yy zz xy xz yz) <- F, T, S
-                const T ea = T(pc[9 * np + k]), eb = T(pc[10 * np + k]) * xF, et = T(pc[11 * np + k]);
-                const T sa = T(pc[12 * np + k]), sb = T(pc[13 * np + k]), sc = T(pc[14 * np + k]) * xSx;
+                T ea, eb, et;
+                if constexpr (MONO) {
+                    ea = -C(6, k);
+                    eb = -C(7, k) * xF;
+                    et = -C(8, k);
+                } else {
+                    ea = C(9, k);
+                    eb = C(10, k) * xF;
+                    et = C(11, k);
+                }
+                const T sa = C(12, k), sb = C(13, k), sc = C(14, k) * xSx;
                 a[6] += ea * x0 * F0 + eb * x0 * x0 + et * x0 * xT0 + sa * Sxx + sb * x0 * Sx0 + sc * x0 * x0;
                 a[7] += ea * x1 * F1 + eb * x1 * x1 + et * x1 * xT1 + sa * Syy + sb * x1 * Sx1 + sc * x1 * x1;
                 a[8] += ea * x2 * F2 + eb * x2 * x2 + et * x2 * xT2 + sa * Szz + sb * x2 * Sx2 + sc * x2 * x2;
@@ -79,7 +103,8 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
                          eb * x1 * x2 + sa * Syz + sc * x1 * x2;
                 if constexpr (NCOMP >= 12) {
                     const T Str = xj[11];
-                    const T uq = T(pc[15 * np + k]) * Str, eq = T(pc[16 * np + k]) * Str;
+                    const T c15 = C(15, k), c16 = C(16, k);
+                    const T uq = c15 * Str, eq = c16 * Str;
                     a[0] += uq * x0;
                     a[1] += uq * x1;
                     a[2] += uq * x2;
@@ -89,7 +114,8 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
                     a[9] += eq * x0 * x1;
                     a[10] += eq * x0 * x2;
                     a[11] += eq * x1 * x2;
-                    a[12] += T(pc[17 * np + k]) * xF + T(pc[18 * np + k]) * xSx;
+                    if constexpr (MONO) a[12] += 3 * c15 * xF - 3 * c16 * xSx;
+                    else a[12] += C(17, k) * xF + C(18, k) * xSx;
                 }
             }
         }

@@ -1960,6 +1960,7 @@ struct BoxDesc {
     const int *pair_off, *pair_j;
     const float *pair_x, *pair_c;
     size_t npairs;
+    int pair_mono;                    // the FP32 table stores the 13 monodisperse coefficients
 };
 
 // ctl: [0] abort flag, then per box kBoxWords words (claimed items of each phase,
@@ -2122,8 +2123,12 @@ __global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(co
                         if (sub >= d.nreal_items) break;
                         const int i = sub * (kPersistThreads / 32) + warp;
                         if (d.with_real) {
-                            real_table_body<float, NCOMP>(i, lane, d.N, d.pair_off, d.npairs, d.pair_j, d.pair_x,
-                                                          d.pair_c, d.xs, d.yreal);
+                            if (d.pair_mono)
+                                real_table_body<float, NCOMP, float, true>(i, lane, d.N, d.pair_off, d.npairs,
+                                                                           d.pair_j, d.pair_x, d.pair_c, d.xs, d.yreal);
+                            else
+                                real_table_body<float, NCOMP>(i, lane, d.N, d.pair_off, d.npairs, d.pair_j, d.pair_x,
+                                                              d.pair_c, d.xs, d.yreal);
                         } else if (i < d.N && lane < kNC) {
                             d.yreal[(size_t)i * kNC + lane] = 0.f;
                         }
@@ -2303,6 +2308,7 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
         d.pair_j = c->b.pair_j;
         d.pair_x = (const float *)c->b.pair_x[0];
         d.pair_c = (const float *)c->b.pair_c[0];
+        d.pair_mono = c->pair_mono[0] ? 1 : 0;
         d.npairs = c->npairs;
         const int M = p.M, Mh = M / 2 + 1, nt = p.ntile;
         const int ntiles = d.s16 ? nt * nt * ((nt + 1) / 2) : nt * nt * nt;

@@ -313,6 +313,32 @@ def test_pair_fill_double_float(oracle_mod, case):
         ctx.set_option(api.SE_OPT_PAIR_FILL, 2)
 
 
+def test_monodisperse_pair_table(oracle_mod):
+    """Equal radii: the FP32 table stores 13 of the 19 coefficients and derives the others
+    (c3 = c2, c9..c11 = -c6..-c8, c17 = 3 c15, c18 = -3 c16).  Against the 19-coefficient
+    table of the same spheres (one radius moved by one part in 1e15, which makes the
+    configuration polydisperse), the real-space and full FP32 products agree to FP32
+    rounding (the derived coefficients differ from separately rounded ones by up to 1.5 ulp;
+    a wrong slot or sign would differ at order one), and the real-space part matches the
+    oracle."""
+    rng = np.random.default_rng(41)
+    rad = np.full(1200, 1.0)
+    L = inputs.box_side(rad, 0.25)
+    cfg = inputs.Config("mono", L, inputs.positions_rsa(rad, L, rng), rad)
+    rad2 = rad.copy()
+    rad2[7] *= 1 + 1e-15
+    cfg2 = inputs.Config("mono_perturbed", L, cfg.pos, rad2)
+    x = inputs.moments(cfg.N, np.random.default_rng(6), 12)
+    xi, rc = 0.8, 5.5
+    ref = oracle_mod.mobility(cfg.pos, cfg.rad, cfg.L, x, xi=xi, rc=rc, kc=1.0, parts=1)
+    for parts, tol in ((1, 2e-7), (7, 2e-7)):
+        y = gpu_apply(make_ctx(xi, 48, 16, rc, cfg, precision=0, size_mode=1, parts=parts), x, torch.float32)
+        y2 = gpu_apply(make_ctx(xi, 48, 16, rc, cfg2, precision=0, size_mode=1, parts=parts), x, torch.float32)
+        assert rel(y, y2) <= tol
+        if parts == 1:
+            assert rel(y[:, :11], ref[:, :11]) <= 5e-7
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_set_config_reuses_pair_buffers(precision):
     """set_config overwrites the previous configuration's pair table in place while it fits
