@@ -1197,10 +1197,8 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
                 zp[j] = 0;
             }
             if (any) {
-#pragma unroll kUnr
-                for (int k = 0; k < P; ++k) {
+                auto plane = [&](int k, size_t off) {
                     const T4 w = Wz[k];
-                    const size_t off = (size_t)Zi[k] * zs;
 #pragma unroll
                     for (int j = 0; j < NCL; ++j) {
                         const T4 u0 = *reinterpret_cast<const T4 *>(gpa[j] + off);
@@ -1225,6 +1223,16 @@ __device__ __forceinline__ void gather_body(int w_, int lane, typename V4<T>::t 
                             if constexpr (NCOMP >= 12) lazy_madd(zp[j], w.x, u0.w);
                         }
                     }
+                };
+                if (bz + P <= M) {
+                    // the support does not wrap in z: the plane offsets follow from bz (no
+                    // offset-table read per plane)
+                    const size_t off0 = (size_t)bz * zs;
+#pragma unroll kUnr
+                    for (int k = 0; k < P; ++k) plane(k, off0 + (size_t)k * zs);
+                } else {
+#pragma unroll kUnr
+                    for (int k = 0; k < P; ++k) plane(k, (size_t)Zi[k] * zs);
                 }
                 // double-floats: normalise the column sums once, after the z-loop
 #pragma unroll
