@@ -1939,7 +1939,7 @@ constexpr int kPersistThreads = 256;
 // The real-space, FFT and gather items each take kSubItems of the per-box kernels' CTA
 // tasks in turn, so a claim (an atomic round trip) and a completion count are paid once
 // per few tasks: small boxes have many short tasks.
-constexpr int kSubItems = 4;
+constexpr int kSubItems = 8;
 // Particles staged per chunk by the persistent kernel's spreading groups: fewer than the
 // standalone kernel's, so four groups' staging leaves L1 room for the gather's grid reads
 // (two CTAs per SM).
