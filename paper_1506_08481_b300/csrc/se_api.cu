@@ -207,7 +207,11 @@ static int ensure_grids_ff(se_ctx *c)
     dfree(c->b.grid_o[2]);
     const size_t M = c->M;
     SE_ALLOC(c, c->b.grid_f[2], M * M * M * 8 * sizeof(ff));
-    if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[2], (size_t)c->nsplit * M * M * M * 8 * sizeof(ff));
+    {
+        const size_t ntiles = (M / kTile) * (M / kTile) * (M / kTile);
+        c->nsplit[2] = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * (size_t)c->sms * 11 + ntiles - 1) / ntiles));
+        if (c->nsplit[2] > 1) SE_ALLOC(c, c->b.grid_part[2], (size_t)c->nsplit[2] * M * M * M * 8 * sizeof(ff));
+    }
     SE_ALLOC(c, c->b.grid_o[2], M * M * M * 8 * sizeof(ff));
     c->grid_M[2] = c->M;
     return SE_OK;
@@ -232,11 +236,12 @@ static int ensure_grids(se_ctx *c, int prec)
     // of its particles into its own partial grid: about two waves of CTAs on the SMs.
     {
         const size_t ntiles = (M / kTile) * (M / kTile) * (M / kTile);
-        c->nsplit = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * (size_t)c->sms * 11 + ntiles - 1) / ntiles));
+        int ns = (int)std::min<size_t>(16, std::max<size_t>(1, (2 * (size_t)c->sms * 11 + ntiles - 1) / ntiles));
         // the FP32 16-plane tiles may split too, to fill the last wave of CTAs
         const int nt = (int)(M / kTile);
-        if (prec == 0) c->nsplit = std::max(c->nsplit, spread16_split(c->sms, nt * nt * ((nt + 1) / 2), 4));
-        if (c->nsplit > 1) SE_ALLOC(c, c->b.grid_part[prec], (size_t)c->nsplit * M * M * M * 8 * es);
+        if (prec == 0) ns = std::max(ns, spread16_split(c->sms, nt * nt * ((nt + 1) / 2), 4));
+        c->nsplit[prec] = ns;
+        if (ns > 1) SE_ALLOC(c, c->b.grid_part[prec], (size_t)ns * M * M * M * 8 * es);
     }
     SE_ALLOC(c, c->b.spec_f[prec], M * M * Mh * 8 * 2 * es);
     SE_ALLOC(c, c->b.spec_o[prec], M * M * Mh * 8 * 2 * es);

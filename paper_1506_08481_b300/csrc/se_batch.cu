@@ -93,13 +93,12 @@ static int batch_enqueue(se_batch *b, cudaStream_t root, int ncomp, const void *
     for (size_t i = 0; i < b->box.size(); ++i) {
         se_ctx *c = b->box[i];
         cudaStream_t own = c->stream;
-        const int ns = c->nsplit;
         // the boxes run concurrently, so no box splits its spreading tiles over CTAs
         c->stream = b->streams[i % b->streams.size()];
-        c->nsplit = 1;
+        c->split_cap = 1;
         const int rc = se::se_apply_internal(c, ncomp, x[i], y[i], dtype, c->precision);
         c->stream = own;
-        c->nsplit = ns;
+        c->split_cap = 16;
         if (rc != SE_OK) {
             b->err = "box " + std::to_string(i) + ": " + c->err;
             return rc;

@@ -121,7 +121,8 @@ struct se_ctx {
     int pair_fill_fp64 = 0;      // SE_OPT_PAIR_FILL
     int ff_table = 1;            // SE_OPT_FF_TABLE
     double shear = 0.0;          // SE_OPT_SHEAR: strain gamma of the periodic cell
-    int nsplit = 1;              // CTAs sharing a spreading tile (few tiles: small M)
+    int nsplit[3] = {1, 1, 1};   // partial spread grids allocated per precision (CTAs sharing a tile)
+    int split_cap = 16;          // upper bound on the parts a launch uses (1 while boxes run concurrently)
     // configuration
     bool have_config = false;
     bool support_ok[3] = {false, false, false};

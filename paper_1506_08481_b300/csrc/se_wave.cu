@@ -1638,7 +1638,7 @@ static bool use_spread16(const se_ctx *c, const SeParams &p, bool fp32)
 static void launch_spread16(se_ctx *c, const SeParams &p, const float *xs, cudaStream_t s, int ncomp)
 {
     const int nt = p.ntile, ntiles = nt * nt * ((nt + 1) / 2);
-    const int ns = spread16_split(c->sms, ntiles, c->nsplit);
+    const int ns = spread16_split(c->sms, ntiles, std::min(c->nsplit[0], c->split_cap));
     float *out = ns > 1 ? (float *)c->b.grid_part[0] : (float *)c->b.grid_f[0];
     auto args = [&](auto kern) {
         kern<<<dim3(ntiles, ns), 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
@@ -1675,7 +1675,7 @@ static void launch_spread(se_ctx *c, const SeParams &p, const T *xs, cudaStream_
     }
     // 8^3 tiles: partial grids only where the tiles alone leave SMs idle (about two waves)
     const int nt = p.ntile, ntiles = nt * nt * nt;
-    const int ns = std::min(c->nsplit, std::max(1, (2 * c->sms * 11 + ntiles - 1) / ntiles));
+    const int ns = std::min(std::min(c->nsplit[pix<T>()], c->split_cap), std::max(1, (2 * c->sms * 11 + ntiles - 1) / ntiles));
     T *out = ns > 1 ? (T *)c->b.grid_part[pix<T>()] : (T *)c->b.grid_f[pix<T>()];
     auto args = [&](auto kern) {
         kern<<<dim3(ntiles, ns), 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
@@ -1876,11 +1876,12 @@ void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int nc
     } else {
         // FP32: two support columns per lane where few column slots of the last 64-column
         // chunk stay idle
+        // (ncomp 6 and 11 take the 12-component kernel, which writes only the caller's
+        // components: measured at N = 2e5, P = 24 it runs 3.04 ms against 3.24 and 3.84 ms
+        // for the 6- and 11-component instantiations, whose compiled z-loops schedule worse)
         if constexpr (std::is_same<T, float>::value && SE_GATHER_NCL == 2) {
             if ((c->P * c->P) % 64 == 0 || (c->P * c->P) % 64 > 32) {
                 if (ncomp <= 3) go(gather_kernel<T, TO, 4, 3, 2>);
-                else if (ncomp <= 6) go(gather_kernel<T, TO, 4, 6, 2>);
-                else if (ncomp <= 11) go(gather_kernel<T, TO, 4, 11, 2>);
                 else go(gather_kernel<T, TO, 4, 12, 2>);
                 c->launches++;
                 return;
