@@ -103,9 +103,10 @@ typedef struct se_ctx se_ctx;
                                   the bin's support window in shared memory (slower on B300 at P = 14
                                   and 24); results agree to rounding */
 
-#define SE_OPT_SPREAD     12   /* spreading kernel: 0 = default (FP32: 8 x 8 x 16 tiles with packed FP32
-                                  FMAs where the grid has room for them, else 8^3 tiles), 1 = 8^3
-                                  tiles always; results agree to rounding */
+#define SE_OPT_SPREAD     12   /* spreading kernel: 0 = default (FP32: 8 x 4 x 16 blocks of one warp with
+                                  packed FP32 FMAs where the grid has room for them, else 8^3 tiles),
+                                  1 = 8^3 tiles always, 2 = 8 x 8 x 16 tiles of two warps (FP32); results
+                                  agree to rounding */
 
 #define SE_OPT_RESIDUAL   14   /* precision of the solver's true residuals and right-hand-side products
                                   when the products run in FP32: 2 (default, double-float) or 1 (FP64) */

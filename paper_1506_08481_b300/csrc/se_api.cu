@@ -507,7 +507,7 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         c->gather = (int)value;
         return SE_OK;
     case SE_OPT_SPREAD:
-        if (value != 0 && value != 1) return set_error(c, SE_ERR_ARG, "spread must be 0 or 1");
+        if (value != 0 && value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "spread must be 0, 1 or 2");
         c->spread = (int)value;
         return SE_OK;
     case SE_OPT_FF_TABLE:

@@ -456,6 +456,96 @@ template <int CH = SE_SPREAD16_CH> struct Spread16SmemT {
 };
 using Spread16Smem = Spread16SmemT<>;
 
+// The update of one particle's 16-plane column at lane column (tx, ty): the 13 column
+// coefficients (gxy: the column's x-y weight; v0: the particle's first staged row), then the
+// plane pairs of the quarters the support reaches, in packed FMAs.  Shared by the two-warp and
+// the one-warp spreading blocks.
+template <int NCOMP, typename SP, typename SWZ>
+__device__ __forceinline__ void spread16_column(int k, int sw_z, float gxy, float4 v0, int tx, int ty, SP &sp,
+                                                SWZ &swz, u64 (&acc2)[kTz / 2][4])
+{
+    const int quarters = (int)v0.z;
+    const float sx = v0.x + tx, sy = v0.y + ty;
+    const float r2 = sx * sx + sy * sy;
+    const float4 v1 = sp[k][1], v2 = sp[k][2], v5 = sp[k][5];
+    const float a0 = v1.x + v1.y * r2;
+    const float F[3] = {v2.x, v2.y, v2.z};
+    float c[3][4];
+    if constexpr (NCOMP >= 6) {
+        const float4 v3 = sp[k][3];
+        const float kT0 = v2.w, kT1 = v3.x, kT2 = v3.y;
+        // k (s x T)-terms of the velocity coefficients and k T-terms of the first moments
+        const float t[3] = {-kT2 * sy, kT2 * sx, kT0 * sy - kT1 * sx};
+        const float nk[3] = {kT1, -kT0, 0.f};
+        if constexpr (NCOMP >= 11) {
+            const float4 v4 = sp[k][4], v6 = sp[k][6];
+            const float b0 = v1.z + v1.w * r2;
+            const float S0 = v3.z, S1 = v3.w, S2 = v4.x, S3 = v4.y, S4 = v4.z, S5 = v4.w;
+            const float d[3] = {S0 * sx + S3 * sy, S3 * sx + S1 * sy, S4 * sx + S5 * sy};
+            const float Sp[3] = {S4, S5, S2}, B1Sp[3] = {v5.w, v6.x, v6.y};
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                c[q][0] = a0 * F[q] + (b0 * d[q] + t[q]);
+                c[q][1] = nk[q] + b0 * Sp[q];
+                c[q][3] = B1Sp[q];
+            }
+            c[0][2] = v5.x + v1.w * d[0];
+            c[1][2] = v5.y + v1.w * d[1];
+            c[2][2] = v5.z + v1.w * d[2];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                c[q][0] = a0 * F[q] + t[q];
+                c[q][1] = nk[q];
+                c[q][3] = 0;
+            }
+            c[0][2] = v5.x;
+            c[1][2] = v5.y;
+            c[2][2] = v5.z;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            c[q][0] = a0 * F[q];
+            c[q][1] = 0;
+            c[q][3] = 0;
+        }
+        c[0][2] = v5.x;
+        c[1][2] = v5.y;
+        c[2][2] = v5.z;
+    }
+    constexpr int NE = NCOMP >= 11 ? 4 : (NCOMP >= 6 ? 3 : 2);
+    constexpr int ES[4] = {0, 2, 1, 3};       // the terms present: 0, 2 (F); 1 (T); 3 (S)
+    u64 cc[3][4];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float v = c[q][e] * gxy;
+            cc[q][e] = pack2(v, v);
+        }
+    const float csv = NCOMP >= 12 ? gxy * v0.w : 0.f;
+    const u64 cs = pack2(csv, csv);
+    auto quarter = [&](auto q0c) {
+        constexpr int zq = decltype(q0c)::value;
+#pragma unroll
+        for (int zp = 2 * zq; zp < 2 * zq + 2; ++zp) {
+            const ulonglong2 wa = *reinterpret_cast<const ulonglong2 *>(&swz[k][(2 * zp) ^ sw_z]);
+            const ulonglong2 wb = *reinterpret_cast<const ulonglong2 *>(&swz[k][(2 * zp + 1) ^ sw_z]);
+            const u64 Wp[4] = {wa.x, wa.y, wb.x, wb.y};
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int j = 0; j < NE; ++j) acc2[zp][q] = ffma2(cc[q][ES[j]], Wp[ES[j]], acc2[zp][q]);
+            if constexpr (NCOMP >= 12) acc2[zp][3] = ffma2(cs, Wp[0], acc2[zp][3]);
+        }
+    };
+    if (quarters & 1) quarter(std::integral_constant<int, 0>{});
+    if (quarters & 2) quarter(std::integral_constant<int, 1>{});
+    if (quarters & 4) quarter(std::integral_constant<int, 2>{});
+    if (quarters & 8) quarter(std::integral_constant<int, 3>{});
+}
+
 template <int NCOMP, bool SPLIT, typename Sync, int CH = SE_SPREAD16_CH>
 __device__ __forceinline__ void spread16_body(int tile, int part, int tid, Sync sync, Spread16SmemT<CH> &sm, SeParams p,
                                               const int *tile_start, const int *tile_perm, const int *base,
@@ -582,85 +672,7 @@ __device__ __forceinline__ void spread16_body(int tile, int part, int tid, Sync 
             const float4 v0 = sp[k][0];
             const int quarters = (int)v0.z;
             if (gxy == 0.f || quarters == 0) continue;
-            const float sx = v0.x + tx, sy = v0.y + ty;
-            const float r2 = sx * sx + sy * sy;
-            const float4 v1 = sp[k][1], v2 = sp[k][2], v5 = sp[k][5];
-            const float a0 = v1.x + v1.y * r2;
-            const float F[3] = {v2.x, v2.y, v2.z};
-            float c[3][4];
-            if constexpr (NCOMP >= 6) {
-                const float4 v3 = sp[k][3];
-                const float kT0 = v2.w, kT1 = v3.x, kT2 = v3.y;
-                // k (s x T)-terms of the velocity coefficients and k T-terms of the first moments
-                const float t[3] = {-kT2 * sy, kT2 * sx, kT0 * sy - kT1 * sx};
-                const float nk[3] = {kT1, -kT0, 0.f};
-                if constexpr (NCOMP >= 11) {
-                    const float4 v4 = sp[k][4], v6 = sp[k][6];
-                    const float b0 = v1.z + v1.w * r2;
-                    const float S0 = v3.z, S1 = v3.w, S2 = v4.x, S3 = v4.y, S4 = v4.z, S5 = v4.w;
-                    const float d[3] = {S0 * sx + S3 * sy, S3 * sx + S1 * sy, S4 * sx + S5 * sy};
-                    const float Sp[3] = {S4, S5, S2}, B1Sp[3] = {v5.w, v6.x, v6.y};
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        c[q][0] = a0 * F[q] + (b0 * d[q] + t[q]);
-                        c[q][1] = nk[q] + b0 * Sp[q];
-                        c[q][3] = B1Sp[q];
-                    }
-                    c[0][2] = v5.x + v1.w * d[0];
-                    c[1][2] = v5.y + v1.w * d[1];
-                    c[2][2] = v5.z + v1.w * d[2];
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        c[q][0] = a0 * F[q] + t[q];
-                        c[q][1] = nk[q];
-                        c[q][3] = 0;
-                    }
-                    c[0][2] = v5.x;
-                    c[1][2] = v5.y;
-                    c[2][2] = v5.z;
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    c[q][0] = a0 * F[q];
-                    c[q][1] = 0;
-                    c[q][3] = 0;
-                }
-                c[0][2] = v5.x;
-                c[1][2] = v5.y;
-                c[2][2] = v5.z;
-            }
-            constexpr int NE = NCOMP >= 11 ? 4 : (NCOMP >= 6 ? 3 : 2);
-            constexpr int ES[4] = {0, 2, 1, 3};       // the terms present: 0, 2 (F); 1 (T); 3 (S)
-            u64 cc[3][4];
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float v = c[q][e] * gxy;
-                    cc[q][e] = pack2(v, v);
-                }
-            const float csv = NCOMP >= 12 ? gxy * v0.w : 0.f;
-            const u64 cs = pack2(csv, csv);
-            auto quarter = [&](auto q0c) {
-                constexpr int zq = decltype(q0c)::value;
-#pragma unroll
-                for (int zp = 2 * zq; zp < 2 * zq + 2; ++zp) {
-                    const ulonglong2 wa = *reinterpret_cast<const ulonglong2 *>(&swz[k][(2 * zp) ^ sw_z]);
-                    const ulonglong2 wb = *reinterpret_cast<const ulonglong2 *>(&swz[k][(2 * zp + 1) ^ sw_z]);
-                    const u64 Wp[4] = {wa.x, wa.y, wb.x, wb.y};
-#pragma unroll
-                    for (int q = 0; q < 3; ++q)
-#pragma unroll
-                        for (int j = 0; j < NE; ++j) acc2[zp][q] = ffma2(cc[q][ES[j]], Wp[ES[j]], acc2[zp][q]);
-                    if constexpr (NCOMP >= 12) acc2[zp][3] = ffma2(cs, Wp[0], acc2[zp][3]);
-                }
-            };
-            if (quarters & 1) quarter(std::integral_constant<int, 0>{});
-            if (quarters & 2) quarter(std::integral_constant<int, 1>{});
-            if (quarters & 4) quarter(std::integral_constant<int, 2>{});
-            if (quarters & 8) quarter(std::integral_constant<int, 3>{});
+            spread16_column<NCOMP>(k, sw_z, gxy, v0, tx, ty, sp, swz, acc2);
         }
     }
 #pragma unroll
@@ -691,6 +703,8 @@ __global__ void __launch_bounds__(64, SE_SPREAD16_MINB) spread16_kernel(SeParams
     spread16_body<NCOMP, SPLIT>(blockIdx.x, blockIdx.y, threadIdx.x, [] { __syncthreads(); }, sm, p, tile_start,
                                 tile_perm, base, s0g, wg, rad, xs, grid, nsplit);
 }
+
+#include "se_spread16w.cuh"
 
 // Self coefficients of particle i (FP64, once per configuration): the isolated sphere
 // (Eqs. faxen-f/t/s/p: 1/(6 pi eta a), 1/(8 pi eta a^3), 3/(20 pi eta a^3),
@@ -1632,14 +1646,41 @@ int spread16_split(int sms, int ntiles, int maxparts)
 static bool use_spread16(const se_ctx *c, const SeParams &p, bool fp32)
 {
     const int nbin = (p.P - 1 + kTile - 1) / kTile + 1;
-    return fp32 && c->spread == 0 && nbin + 1 <= p.ntile;
+    return fp32 && (c->spread == 0 || c->spread == 2) && nbin + 1 <= p.ntile;
 }
 
 static void launch_spread16(se_ctx *c, const SeParams &p, const float *xs, cudaStream_t s, int ncomp)
 {
     const int nt = p.ntile, ntiles = nt * nt * ((nt + 1) / 2);
+    // the one-warp 8 x 4 x 16 blocks (default) are twice as many as the two-warp tiles at twice
+    // the CTAs per SM, so the wave arithmetic of the split is the same
     const int ns = spread16_split(c->sms, ntiles, std::min(c->nsplit[0], c->split_cap));
     float *out = ns > 1 ? (float *)c->b.grid_part[0] : (float *)c->b.grid_f[0];
+    if (c->spread == 0) {
+        auto argw = [&](auto kern) {
+            kern<<<dim3(2 * ntiles, ns), 32, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
+                                                      (const float *)c->b.sup_s0[0], (const float *)c->b.sup_w[0],
+                                                      c->b.rad, xs, out, ns);
+        };
+        if (ns > 1) {
+            if (ncomp <= 3) argw(spread16w_kernel<3, true>);
+            else if (ncomp <= 6) argw(spread16w_kernel<6, true>);
+            else if (ncomp <= 11) argw(spread16w_kernel<11, true>);
+            else argw(spread16w_kernel<12, true>);
+        } else {
+            if (ncomp <= 3) argw(spread16w_kernel<3, false>);
+            else if (ncomp <= 6) argw(spread16w_kernel<6, false>);
+            else if (ncomp <= 11) argw(spread16w_kernel<11, false>);
+            else argw(spread16w_kernel<12, false>);
+        }
+        c->launches++;
+        if (ns > 1) {
+            const size_t n4 = (size_t)p.M * p.M * p.M;
+            sum_parts_kernel<float><<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(n4, ns, out, (float *)c->b.grid_f[0]);
+            c->launches++;
+        }
+        return;
+    }
     auto args = [&](auto kern) {
         kern<<<dim3(ntiles, ns), 64, 0, s>>>(p, c->b.tile_start, c->b.tile_perm, c->b.sup_base,
                                               (const float *)c->b.sup_s0[0], (const float *)c->b.sup_w[0], c->b.rad,

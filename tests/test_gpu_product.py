@@ -403,14 +403,15 @@ def test_cutoff_boundary_pairs(oracle_mod, precision):
 @pytest.mark.parametrize("M,P", [(216, 24), (72, 24), (48, 16), (48, 32), (24, 8), (24, 12)])
 @pytest.mark.parametrize("ncomp", [3, 6, 11, 12])
 def test_spread_variants_agree(small_poly, small_poly_ref, M, P, ncomp):
-    """FP32 spreading over 8 x 8 x 16 tiles with packed FMAs (the default where the grid
-    has room for it: M = 72 and 216 leave a last tile of 8 planes, M = 48 and 24 split the
-    tiles' particles over partial grids, M = 24 with P = 12 falls back) against 8^3 tiles
-    (SE_OPT_SPREAD 1): the same terms in another order, so they agree to FP32 rounding."""
+    """FP32 spreading over one-warp 8 x 4 x 16 blocks with packed FMAs (the default where the
+    grid has room for it: M = 72 and 216 leave a last tile of 8 planes, M = 48 and 24 split the
+    tiles' particles over partial grids, M = 24 with P = 12 falls back) and over two-warp
+    8 x 8 x 16 tiles (SE_OPT_SPREAD 2) against 8^3 tiles (SE_OPT_SPREAD 1): the same terms in
+    another order, so they agree to FP32 rounding."""
     cfg, x = small_poly
     x = x[:, :ncomp].copy()
     out = {}
-    for s in (0, 1):
+    for s in (0, 1, 2):
         ctx = make_ctx(0.9, M, P, 5.4, cfg, precision=0)
         ctx.set_option(api.SE_OPT_SPREAD, s)
         out[s] = gpu_apply(ctx, x, dtype=torch.float32)
@@ -420,6 +421,7 @@ def test_spread_variants_agree(small_poly, small_poly_ref, M, P, ncomp):
     # about 100 for the largest sphere at M = 216 in this box of 11 (both are then ~3e-6 from FP64).
     amp = max(1.0, (cfg.rad.max() * M / cfg.L) ** 2 * 2 * np.pi / P)
     assert rel(out[0], out[1]) <= max(2e-6, 2.0 ** -24 * amp)
+    assert rel(out[2], out[1]) <= max(2e-6, 2.0 ** -24 * amp)
     if M == 72 and ncomp == 12:
         assert rel(out[0], small_poly_ref) <= 1e-5
 
