@@ -56,7 +56,7 @@ PAIR_BYTES_MONO = 68
 # sum_parts_kernel.  Other sizes scale them by grid points (M^3), stored pairs or particles.  A kernel
 # changed since that capture has no entry (its traffic is reported as null).
 NCU_CAPTURE = {"N": 200000, "M": 144, "npairs": 88237670}
-NCU_DRAM_BYTES = {"permute": 13.0e6, "real": 6438.7e6, "spread": 381.8e6, "fft_x_fwd": 50.6e6,
+NCU_DRAM_BYTES = {"permute": 13.0e6, "real": 6438.7e6, "fft_x_fwd": 50.6e6,
                   "fft_y_fwd": 48.5e6, "fft_z_scale": 54.0e6, "fft_y_inv": 48.5e6, "fft_x_inv": 49.4e6,
                   "gather": 149.5e6}
 
