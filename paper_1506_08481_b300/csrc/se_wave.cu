@@ -1982,12 +1982,9 @@ constexpr int kPersistThreads = 256;
 // tasks in turn, so a claim (an atomic round trip) and a completion count are paid once
 // per few tasks: small boxes have many short tasks.
 constexpr int kSubItems = 8;
-// Particles staged per chunk by the persistent kernel's spreading groups: fewer than the
-// standalone kernel's, so four groups' staging leaves L1 room for the gather's grid reads
-// (two CTAs per SM).
-constexpr int kPersistCH = 32;
-constexpr size_t kGroupSmem = sizeof(Spread16SmemT<kPersistCH>) > sizeof(Spread8Smem<float>)
-                                  ? sizeof(Spread16SmemT<kPersistCH>) : sizeof(Spread8Smem<float>);
+// Shared memory of one 64-thread group spreading 8^3 tiles (the 16-plane tiles are spread by
+// the CTA's eight warps, each with a Spread16wSmem).
+constexpr size_t kGroupSmem = sizeof(Spread8Smem<float>);
 
 struct BoxDesc {
     SeParams p;
@@ -2187,15 +2184,20 @@ __global__ void __launch_bounds__(kPersistThreads, 2) batch_persistent_kernel(co
                     const int grp = threadIdx.x >> 6, tid = threadIdx.x & 63;
                     const int nt = d.p.ntile;
                     const int ntiles = d.s16 ? nt * nt * ((nt + 1) / 2) : nt * nt * nt;
+                    if (d.s16) {
+                        // 16-plane tiles: eight one-warp 8 x 4 x 16 blocks per item (spread16w_body)
+                        const int blk = (it - d.nreal_groups) * 8 + warp;
+                        if (blk < 2 * ntiles) {
+                            auto &smw = *reinterpret_cast<Spread16wSmem *>(smraw + (size_t)warp * sizeof(Spread16wSmem));
+                            spread16w_body<NCOMP, false>(blk, 0, lane, smw, d.p, d.tile_start, d.tile_perm, d.sup_base,
+                                                         d.sup_s0, d.sup_w, d.rad, d.xs, d.grid_f, 1);
+                        }
+                        break;
+                    }
                     const int tile = (it - d.nreal_groups) * 4 + grp;
                     if (tile < ntiles) {
                         auto sync = [grp] { bar_named(1 + grp, 64); };
-                        if (d.s16) {
-                            auto &sm = *reinterpret_cast<Spread16SmemT<kPersistCH> *>(smraw + (size_t)grp * kGroupSmem);
-                            spread16_body<NCOMP, false, decltype(sync), kPersistCH>(
-                                tile, 0, tid, sync, sm, d.p, d.tile_start, d.tile_perm, d.sup_base, d.sup_s0, d.sup_w,
-                                d.rad, d.xs, d.grid_f, 1);
-                        } else {
+                        {
                             Spread8Smem<float> &sm = *reinterpret_cast<Spread8Smem<float> *>(
                                 smraw + (size_t)grp * kGroupSmem);
                             spread_body<float, NCOMP, false>(tile, 0, tid, sync, sm, d.p, d.tile_start, d.tile_perm,
@@ -2312,7 +2314,7 @@ int persist_prepare(se_ctx *const *box, int nbox, int ncomp, const void *const *
     std::vector<BoxDesc> h(nbox);
     std::vector<int> cnt((size_t)kPersistPhases * nbox, 0);
     std::vector<double> work(nbox, 0.0);
-    size_t smem = (size_t)4 * kGroupSmem;
+    size_t smem = std::max((size_t)4 * kGroupSmem, (size_t)(kPersistThreads / 32) * sizeof(Spread16wSmem));
     for (int b = 0; b < nbox; ++b) {
         se_ctx *c = box[b];
         const int with_real = (c->parts & 1) ? 1 : 0, with_wave = (c->parts & 2) ? 1 : 0;
