@@ -52,11 +52,11 @@ PAIR_BYTES = 92
 PAIR_BYTES_MONO = 68
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (one product's launches,
-# the command in profiles/dram_mono_n200000_P24.md); the spread stage is spread16_kernel plus
+# the command in profiles/dram_mono_n200000_P24.md); the spread stage is spread16w_kernel plus
 # sum_parts_kernel.  Other sizes scale them by grid points (M^3), stored pairs or particles.  A kernel
 # changed since that capture has no entry (its traffic is reported as null).
 NCU_CAPTURE = {"N": 200000, "M": 144, "npairs": 88237670}
-NCU_DRAM_BYTES = {"permute": 13.0e6, "real": 6438.7e6, "fft_x_fwd": 50.6e6,
+NCU_DRAM_BYTES = {"permute": 13.0e6, "real": 6438.9e6, "spread": 374.6e6, "fft_x_fwd": 50.6e6,
                   "fft_y_fwd": 48.5e6, "fft_z_scale": 54.0e6, "fft_y_inv": 48.5e6, "fft_x_inv": 49.4e6,
                   "gather": 149.5e6}
 

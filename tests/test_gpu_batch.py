@@ -67,8 +67,12 @@ def test_persistent_batch_matches_per_box_launches(ncomp, dtype):
     per-box launches: the same stage code on the same data, so the same products (to
     FP32 rounding), on replays and with new inputs in the same buffers.  The boxes mix
     8^3 and 8x8x16 spreading tiles (a 24^3 grid with P = 12 leaves no room for the
-    taller tiles), the real-space and the hybrid size modes, and uneven N."""
+    taller tiles), the real-space and the hybrid size modes, uneven N, and a monodisperse box
+    (its pair table stores 13 of the 19 coefficients)."""
     boxes = inputs.batch_boxes(seed=5, nbox=7, nmin=40, nmax=400)
+    rad = np.ones(300)
+    L = inputs.box_side(rad, 0.2)
+    boxes[2] = inputs.Config("mono_n300", L, inputs.positions_rsa(rad, L, np.random.default_rng(8)), rad)
     ctxs, xs = [], []
     rng = np.random.default_rng(2)
     for k, cfg in enumerate(boxes):
