@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the GMRES solves (and the batch measurement)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU product and solve")
     ap.add_argument("--solve-maxit", type=int, default=800)
@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="batch64: the error model's parameters instead of timing candidates per box")
     ap.add_argument("--streams", type=int, default=8, help="batch64: streams of the captured graph")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="default workload: skip the 64-box batch measurement carried in its line (--no-solve "
+                         "skips it too: both are the line's secondary measurements)")
     ap.add_argument("--n", type=int, default=200000,
                     help="spheres (N-sweep of the large-scale configuration at the same phi and grid density)")
     return ap.parse_args()
@@ -585,6 +588,16 @@ def run_ours(args, rank, world, local):
                               "pairs or particles at other sizes)"
                               if roof["traffic"] is not None else "kernel changed since the last capture")
 
+    # the 64-box batch (graph, persistent launch, per-box loop), as --workload batch64 measures it
+    batch = None
+    if not (args.no_batch or args.no_solve):
+        bl = measure_batch(args, rank, world, local, dev)
+        if rank == 0:
+            batch = {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step", "graph_of_per_box_launches",
+                                        "persistent_launch", "per_box_launch_loop")}
+            batch["boxes"], batch["N_total"] = 64, bl["config"]["N_total"]
+            batch["launch"] = bl["config"]["launch"]
+
     workload = WORKLOAD if args.n == 200000 else WORKLOAD.replace("n200000", f"n{args.n}")
     if rank == 0:
         cpu = None
@@ -609,7 +622,8 @@ def run_ours(args, rank, world, local):
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e, "unit": "products/s", "h2d_bytes_per_step": int(x64.nbytes),
                         "d2h_bytes_per_step": int(y64.nbytes)},
-                "gpu_launches": int(launches), "clocks": clk, "fp64_product": fp64, "tuned_product": tuned, "solve": solve}
+                "gpu_launches": int(launches), "clocks": clk, "fp64_product": fp64, "tuned_product": tuned, "solve": solve,
+                "batch64": batch}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -621,13 +635,24 @@ def run_batch(args, rank, world, local):
     forces only, FP32, per-box parameters for 1e-6; one step = one product of every box.
     The captured graph (boxes concurrent on 8 streams) against a per-box launch loop."""
     import torch
-    from paper_1506_08481_b300 import api, inputs, params
 
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    line = measure_batch(args, rank, world, local, dev)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_batch(args, rank, world, local, dev):
+    """The 64-box measurement of run_batch; returns its JSON line (a dict)."""
+    import torch
+    from paper_1506_08481_b300 import api, inputs, params
+
     boxes = inputs.batch_boxes(seed=0)
     rng = np.random.default_rng(1)
     ctxs, xs, ys, chosen = [], [], [], []
@@ -693,6 +718,7 @@ def run_batch(args, rank, world, local):
     ntot = sum(c.N for c in boxes)
     best = "graph" if ms_graph <= ms_pers else "persistent"
     ms_best = min(ms_graph, ms_pers)
+    line = None
     if rank == 0:
         line = {"metric": "aggregate box products/s, 64 uneven boxes (forces only)", "value": job_rate(64, ms_best, world),
                 "unit": "box products/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -715,11 +741,9 @@ def run_batch(args, rank, world, local):
                 "persistent_speedup": ms_loop / ms_pers,
                 "gpu_launches_setup_and_eager": sum(c.kernel_launches() for c in ctxs) - launches0,
                 "clocks": clk}
-        print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return line
 
 
 def run_brownian(args, rank, world, local):

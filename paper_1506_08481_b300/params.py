@@ -213,10 +213,11 @@ def candidates(L: float, N: int, tol: float, M_max: int = 384, supports=None, a_
 
 
 def autotune(cfg, tol: float, ncomp: int = 3, precision: int = 0, max_candidates: int = 3, reps: int = 3,
-             supports=None, fp32_tol: float | None = None, spreads=(0, 1), modes=(1, 0)):
+             supports=None, fp32_tol: float | None = None, spreads=(0, 1, 2), modes=(1, 0)):
     """Time the cheapest few candidate parameter sets for a configuration on the GPU, each
     with the particle-size modes `modes` and the spreading tile shapes `spreads`
-    (SE_OPT_SPREAD 0: 8 x 8 x 16 tiles where the grid has room, 1: 8^3 tiles), and return
+    (SE_OPT_SPREAD 0: one-warp 8 x 4 x 16 blocks where the grid has room, 1: 8^3 tiles, 2: two-warp
+    8 x 8 x 16 tiles), and return
     (SeParams, size_mode, ms per product, {"spread": tile option}) of the fastest.  The
     candidates meet the error model at tol (method) and fp32_tol (FP32 rounding)."""
     import torch
