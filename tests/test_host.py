@@ -30,6 +30,19 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_binding_constants_match_the_header():
+    """Every option, precision, preconditioner, stage and error code the header defines has
+    the same value in the binding (the binding passes them through as plain integers)."""
+    src = open(os.path.join(ROOT, "include", "se_mobility.h")).read()
+    defs = dict((k, int(v)) for k, v in re.findall(r"^#define\s+(SE_[A-Z0-9_]+)\s+(-?\d+)\b", src, re.M))
+    assert len(defs) > 30
+    missing = [k for k in defs if k.startswith("SE_OPT_") and not hasattr(api, k)]
+    assert not missing, missing
+    for k, v in defs.items():
+        if hasattr(api, k):
+            assert getattr(api, k) == v, k
+
+
 def test_theta_parameterisation_edge_value():
     """Eq. theta-param: with theta = (2 pi P xi/(M m))^2 the Gaussian of Eq. shape has the
     value exp(-m^2/2) at |t| = P/(2M); in grid units exp(-alpha s^2), alpha = 2 m^2/P^2."""
