@@ -181,7 +181,13 @@ int se_set_option(se_ctx *ctx, int key, double value);
  * the spreading bins and (lazily) the preconditioner.  Fails with SE_ERR_ARG unless
  * 1 <= N <= 2^28 (an empty configuration included) or for null pointers, SE_ERR_CUTOFF when
  * rc >= L/2 and SE_ERR_NONFINITE for non-finite or non-positive data.  The arrays are
- * copied; the caller may free them afterwards.  Synchronises the stream. */
+ * copied; the caller may free them afterwards.  Synchronises the device (work of this
+ * context still in flight on any stream finishes first): the real-space pair table of the
+ * previous configuration is overwritten in place while it fits (same N for its offsets; up
+ * to 6% more pairs than the largest earlier table), so a sequence of configurations of one
+ * N allocates and frees nothing after the first; its buffers are returned by se_destroy.
+ * Equal radii are detected on the device and make the FP32 table store 13 of the 19
+ * coefficients per pair. */
 int se_set_config(se_ctx *ctx, int64_t N, double L, const double *pos, const double *radius);
 
 /* y = M_inf . x.  x, y: DEVICE arrays [N][ncomp] of dtype SE_F32 or SE_F64 (both the
