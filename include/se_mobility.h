@@ -114,8 +114,8 @@ typedef struct se_ctx se_ctx;
                                   L, 0), a3 = (0, 0, L) (a cube sheared in x along y, Sec. 3.2; default 0).
                                   Needs SE_OPT_SIZE_MODE 2 or 3 (set first; SE_ERR_ARG otherwise, also for a
                                   later change of the size mode); se_set_config must follow; the spectral
-                                  preconditioner falls back to the block one; positions may be given
-                                  in any periodic image */
+                                  and learned preconditioners take the plane waves of the sheared
+                                  reciprocal lattice; positions may be given in any periodic image */
 #define SE_OPT_FF_TABLE   16   /* FP64-equivalent mode (SE_OPT_PRECISION 2): 1 (default) keeps a double-float
                                   copy of the FP64 real-space pair table per configuration (about 176 bytes
                                   per stored pair: 7 GB at N = 2e5, rc = 7.5, phi = 0.45), so the

@@ -447,7 +447,7 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         if (value != 0 && value != 1 && value != 2 && value != 3)
             return set_error(c, SE_ERR_ARG, "size mode must be 0 (hybrid), 1 (real-space), 2 (wave-space, "
                                             "gradients in the spread) or 3 (wave-space, all derivatives in k-space)");
-        if (c->shear != 0 && value != 2 && value != 3)
+        if (c->shear != 0 && value != 2 && value != 3 && !c->point_forces)
             return set_error(c, SE_ERR_ARG, "a sheared cell needs a wave-space size approach (SE_OPT_SIZE_MODE 2 or 3)");
         c->size_mode = (int)value;
         c->pc_ready = false;
@@ -525,7 +525,7 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         return SE_OK;
     case SE_OPT_SHEAR:
         if (!(std::fabs(value) <= 0.5)) return set_error(c, SE_ERR_ARG, "shear strain must be in [-0.5, 0.5]");
-        if (value != 0 && c->size_mode != 2 && c->size_mode != 3)
+        if (value != 0 && c->size_mode != 2 && c->size_mode != 3 && !c->point_forces)
             return set_error(c, SE_ERR_ARG, "a sheared cell needs a wave-space size approach (SE_OPT_SIZE_MODE 2 or 3)");
         if (value != c->shear) {
             c->shear = value;
@@ -560,7 +560,7 @@ extern "C" int se_set_config(se_ctx *c, int64_t N, double L, const double *pos, 
     if (!c->have_params) return set_error(c, SE_ERR_STATE, "se_set_params must be called first");
     if (!(L > 0) || !std::isfinite(L)) return set_error(c, SE_ERR_ARG, "L must be positive");
     if (c->rc >= 0.5 * L) return set_error(c, SE_ERR_CUTOFF, "rc must be smaller than L/2");
-    if (c->shear != 0 && c->size_mode != 2 && c->size_mode != 3)
+    if (c->shear != 0 && c->size_mode != 2 && c->size_mode != 3 && !c->point_forces)
         return set_error(c, SE_ERR_ARG, "a sheared cell needs a wave-space size approach (SE_OPT_SIZE_MODE 2 or 3)");
     cudaSetDevice(c->device);
     // the pair table is overwritten in place: work of this context in flight on any stream

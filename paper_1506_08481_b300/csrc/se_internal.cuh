@@ -136,6 +136,10 @@ struct se_ctx {
     size_t pairj_cap = 0;        // allocated neighbour indices
     size_t pair_cap[3] = {};     // pairs the coefficient buffers of precision q hold (0, 1)
     bool mono = false;           // every radius of the configuration equal
+    // internal contexts of point forces only (the spectral correction's coarse product: radii
+    // negligible, wave part): no window gradient enters, so a sheared cell runs with the
+    // real-space size approach
+    bool point_forces = false;
     bool pair_mono[3] = {};      // table q stores the 13 coefficients of a monodisperse configuration
     size_t grid_M[3] = {0, 0, 0};
     int64_t N = 0;

@@ -507,6 +507,7 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w, do
     for (int t = 0; t < 3 && rc == SE_OK; ++t) {
         // modes with |n|^2 = target (nearest populated shell above it), at most 64
         std::vector<double> md;
+        double k2sum = 0;
         int r2 = targets[t];
         for (; md.empty() && r2 < targets[t] + 64; ++r2) {
             const int R = (int)std::ceil(std::sqrt((double)r2));
@@ -514,8 +515,10 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w, do
                 for (int b2 = -R; b2 <= R && md.size() < 9 * 64; ++b2)
                     for (int cc = -R; cc <= R && md.size() < 9 * 64; ++cc) {
                         if (a * a + b2 * b2 + cc * cc != r2) continue;
-                        const double kv[3] = {k1 * a, k1 * b2, k1 * cc};
+                        // the reciprocal lattice of the (sheared) cell: k = k1 (a, b - gamma a, c)
+                        const double kv[3] = {k1 * a, k1 * (b2 - c->shear * a), k1 * cc};
                         const double kn = std::sqrt(kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2]);
+                        k2sum += kn * kn;
                         double ar[3], ai[3];
                         for (int d = 0; d < 3; ++d) { ar[d] = gauss(); ai[d] = gauss(); }
                         double pr = 0, pi_ = 0;
@@ -524,8 +527,8 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w, do
                         md.insert(md.end(), {kv[0], kv[1], kv[2], ar[0], ar[1], ar[2], ai[0], ai[1], ai[2]});
                     }
         }
-        kk[t] = k1 * std::sqrt((double)(r2 - 1));
         const int nm = (int)(md.size() / 9);
+        kk[t] = std::sqrt(k2sum / std::max(nm, 1));     // the shell's rms |k| (k1 sqrt(n^2) in the cube)
         cudaMemcpyAsync(modes_d, md.data(), md.size() * sizeof(double), cudaMemcpyHostToDevice, s);
         probe_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, ncomp, nm, posc, modes_d, z);
         c->launches++;
@@ -577,9 +580,11 @@ static int build_spectral(se_ctx *c, int ncomp, Gm &gm, double *z, double *w, do
     if (rc != SE_OK) { cudaFree(posc); c->err = "spectral preconditioner: se_create failed"; return rc; }
     c->spc = sc;
     const int Pc = 8;
+    sc->point_forces = true;                     // radii 1e-6 <a>: a sheared cell keeps size mode 1
     if (rc == SE_OK) rc = se_set_params(sc, 1.0, Mc, Pc, std::min(0.25 * L, 1.0));
     if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_PRECISION, 0);
     if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_SIZE_MODE, 1);
+    if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_SHEAR, c->shear);
     if (rc == SE_OK) rc = se_set_option(sc, SE_OPT_PARTS, 2);
     double *rtiny = nullptr;
     if (rc == SE_OK && cudaMalloc(&rtiny, (size_t)N * sizeof(double)) != cudaSuccess) rc = SE_ERR_NOMEM;
@@ -763,8 +768,6 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
     double *yd = gm.hd + (m + 1);
     const bool shifted = !(alpha == 0.0 && beta == 1.0);
     if ((shifted || mixed) && precond != SE_PRECOND_NONE) precond = SE_PRECOND_BLOCK;
-    // the spectral correction's plane waves are those of the cube
-    if (precond == SE_PRECOND_SPECTRAL && c->shear != 0) precond = SE_PRECOND_BLOCK;
     double *ms = c->b.work64 + 5 * n;     // the masked vector P_S v of the mixed operator
 
     // the learned preconditioner: the spectral correction with the damping and cutoff
@@ -772,7 +775,7 @@ static int solve_core(se_ctx *c, int ncomp, const double *bd, double *xd, double
     // spectral correction does not apply) it is the plain block preconditioner
     double l_theta = 0, l_ka = 0, l_cmax = 0;
     if (precond == SE_PRECOND_LEARNED) {
-        if (c->have_mlp && c->shear == 0 && !shifted && !mixed) {
+        if (c->have_mlp && !shifted && !mixed) {
             rc = learned_spectral_params(c, &l_theta, &l_ka, &l_cmax);
             if (rc != SE_OK) return rc;
             precond = SE_PRECOND_SPECTRAL;

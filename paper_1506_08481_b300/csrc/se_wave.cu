@@ -961,7 +961,7 @@ template <typename T, int LB>
 __global__ void __launch_bounds__(kFftThreads, 4) fft_z_table(FftPlan plan, const typename C2<T>::t *twg,
                                                               const typename C2<T>::t *specf,
                                                               typename C2<T>::t *speco, const T *tab, int ntab,
-                                                              T kmax, T cnorm, T twopiL, T ecoef)
+                                                              T kmax, T cnorm, T twopiL, T ecoef, T gam)
 {
     using T2 = typename C2<T>::t;
     constexpr int NLI = 4 * LB, CO = 4, NLO = LB * CO, CPE = sizeof(T) == 4 ? 2 : 1;
@@ -992,7 +992,8 @@ __global__ void __launch_bounds__(kFftThreads, 4) fft_z_table(FftPlan plan, cons
         T2 o[CO];
 #pragma unroll
         for (int c = 0; c < CO; ++c) o[c] = T2{0, 0};
-        const T kx = twopiL * qx, ky = twopiL * ys, kz = twopiL * zsn;
+        // k = (2 pi / L)(q1, q2 - gamma q1, q3) (the sheared cell's reciprocal lattice)
+        const T kx = twopiL * qx, ky = twopiL * ((T)ys - gam * (T)qx), kz = twopiL * zsn;
         const T k2 = kx * kx + ky * ky + kz * kz;
         const bool zero = q >= nq || (qx == 0 && ys == 0 && zsn == 0) || 2 * qx == M || 2 * ys == M ||
                           2 * zsn == M || k2 > kmax * kmax;
@@ -1835,7 +1836,8 @@ void launch_wave_fft(se_ctx *c, cudaStream_t s)
         const T cn = (T)pow(p.alpha / kPi, 3.0);
         cudaFuncSetAttribute(fft_z_table<T, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm);
         fft_z_table<T, LB><<<dim3((Mh + LB - 1) / LB, M), kFftThreads, zsm, s>>>(
-            c->plan, tw, sf, so, (const T *)c->ktab[pix<T>()], c->ktab_n, (T)c->ktab_kmax, cn, twopiL, ecoef);
+            c->plan, tw, sf, so, (const T *)c->ktab[pix<T>()], c->ktab_n, (T)c->ktab_kmax, cn, twopiL, ecoef,
+            (T)p.gamma);
     } else if (p.wsrc) launch_z_fit<T, 8, 8>(c, p, tw, sf, so, cnorm, s);
     else if (CO == 8) launch_z_fit<T, 8>(c, p, tw, sf, so, cnorm, s);
     else launch_z_fit<T, 4>(c, p, tw, sf, so, cnorm, s);

@@ -2,7 +2,7 @@
 a3 = (0, 0, L) of Sec. 3.2, with the wave-space size approach) against the FP64 oracle on
 the same lattice (oracle.mobility(..., gamma)): the product in FP64 (<= 1e-9) and FP32
 (<= 1e-6), the identity of strains 1/2 and -1/2 (the same lattice), positions given in
-any periodic image, and a block-preconditioned solve."""
+any periodic image, and block-preconditioned, spectral and learned solves."""
 import numpy as np
 import pytest
 
@@ -118,6 +118,46 @@ def test_sheared_solve(oracle_mod):
     assert relres <= 1e-11
     assert rel(x.cpu().numpy().reshape(-1), x_or) <= 1e-7
     print(f"sheared solve: {iters} products")
+
+
+def test_sheared_spectral_and_learned_solves():
+    """The long-wavelength (spectral) correction of the block preconditioner on a sheared cell:
+    its plane waves are those of the sheared reciprocal lattice, k = (2 pi / L)(q1, q2 - gamma q1,
+    q3), in the probes and in the coarse correction product.  At gamma = 0.3 (N = 2000, radii
+    0.8-1.2, phi = 0.3, FP32 products with double-float residuals): the spectral and learned
+    solves reach the tolerance with fewer products than the block one and agree with its
+    solution to the conditioning of the residual tolerance."""
+    import os
+    from paper_1506_08481_b300 import params
+    rng = np.random.default_rng(31)
+    g = 0.3
+    rad = rng.uniform(0.8, 1.2, 2000)
+    L = inputs.box_side(rad, 0.3)
+    cfg = inputs.Config("sheared_n2000", L, inputs.positions_rsa_sheared(rad, L, g, rng), rad)
+    sp = params.choose(cfg.L, cfg.N, 1e-6, M_max=96, a_eff=params.effective_radius(cfg.rad), precision=0)
+    c = api.Context()
+    c.set_params(sp.xi, sp.M, sp.P, sp.rc)
+    c.set_option(api.SE_OPT_SHAPE_M, sp.m)
+    c.set_option(api.SE_OPT_SIZE_MODE, 2)
+    c.set_option(api.SE_OPT_SHEAR, g)
+    c.set_option(api.SE_OPT_PRECISION, 0)
+    c.set_option(api.SE_OPT_RESTART, 100)
+    c.set_config(cfg.pos, cfg.rad, cfg.L)
+    w = os.path.join(os.path.dirname(api.__file__), "learned_pc_weights.npy")
+    c.set_learned_weights(np.load(w))
+    b = torch.tensor(np.random.default_rng(6).standard_normal((cfg.N, 11)), device="cuda")
+    out = {}
+    for pc in (api.SE_PRECOND_BLOCK, api.SE_PRECOND_SPECTRAL, api.SE_PRECOND_LEARNED):
+        x, iters, relres = c.solve(b, rtol=1e-6, maxit=800, precond=pc)
+        assert relres <= 1e-6
+        out[pc] = (x.cpu().numpy(), iters)
+    xb, ib = out[api.SE_PRECOND_BLOCK]
+    print("sheared solves (block, spectral, learned):", ib, out[api.SE_PRECOND_SPECTRAL][1],
+          out[api.SE_PRECOND_LEARNED][1])
+    for pc in (api.SE_PRECOND_SPECTRAL, api.SE_PRECOND_LEARNED):
+        x, it = out[pc]
+        assert it <= 0.8 * ib
+        assert rel(x, xb) <= 3e-4
 
 
 def test_shear_needs_the_wave_space_approach(poly):
