@@ -1983,7 +1983,7 @@ constexpr int kPersistThreads = 256;
 // The real-space, FFT and gather items each take kSubItems of the per-box kernels' CTA
 // tasks in turn, so a claim (an atomic round trip) and a completion count are paid once
 // per few tasks: small boxes have many short tasks.
-constexpr int kSubItems = 8;
+constexpr int kSubItems = 16;
 // Shared memory of one 64-thread group spreading 8^3 tiles (the 16-plane tiles are spread by
 // the CTA's eight warps, each with a Spread16wSmem).
 constexpr size_t kGroupSmem = sizeof(Spread8Smem<float>);
