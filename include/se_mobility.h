@@ -87,8 +87,12 @@ typedef struct se_ctx se_ctx;
 #define SE_OPT_TIMING      7   /* 1: record CUDA events around every stage of each product (default 0) */
 #define SE_OPT_OVERLAP     8   /* where the real-space sum runs: 0 = on a second, high-priority stream
                                   beside the spread, 1 = beside the FFT chain, 2 = in line before the
-                                  spread (default: the spread and gather fill every SM, so running
-                                  beside them only slows them); results are identical */
+                                  spread (the spread and gather fill every SM, so running beside them
+                                  only slows them), 3 (default) = inside the gather kernel, each warp
+                                  summing its particle's stored pairs before gathering, where that
+                                  kernel applies (FP32, stored pair table, 11 or 12 moment components,
+                                  SE_OPT_SIZE_MODE 1, unstaged gather), else as 2; results are
+                                  identical */
 #define SE_OPT_PC_THETA   10   /* damping theta of the spectral correction, in [0, 1]; 0 (default) = 0.9, the
                                   best single value over generated mono-, bi- and polydisperse suspensions
                                   (the best per configuration ranges from 0.8 to 0.98, which the learned

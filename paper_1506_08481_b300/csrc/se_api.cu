@@ -483,7 +483,8 @@ extern "C" int se_set_option(se_ctx *c, int key, double value)
         c->parts = (int)value;
         return SE_OK;
     case SE_OPT_OVERLAP:
-        if (value != 0 && value != 1 && value != 2) return set_error(c, SE_ERR_ARG, "overlap must be 0, 1 or 2");
+        if (value != 0 && value != 1 && value != 2 && value != 3)
+            return set_error(c, SE_ERR_ARG, "overlap must be 0, 1, 2 or 3");
         c->overlap = (int)value;
         return SE_OK;
     case SE_OPT_PC_THETA:
@@ -605,8 +606,10 @@ static int apply_t(se_ctx *c, int ncomp, const TO *x, TO *y)
     launch_permute_in<T, TO>(c, x, xs, ncomp, s);
     stage_mark(c, SE_STAGE_PERMUTE, s, true);
     const int with_wave = (c->parts & 2) ? 1 : 0;
-    // the real-space sum runs in line before the spread (overlap 2, the default), or on
-    // the auxiliary high-priority stream beside the spread (0) or the FFT chain (1)
+    // the real-space sum runs inside the gather kernel where fused_real_gather applies
+    // (overlap 3, the default), else in line before the spread (2, and 3 where the fused
+    // kernel does not apply), or on the auxiliary high-priority stream beside the spread (0)
+    // or the FFT chain (1)
     auto real_part = [&](cudaStream_t rs) -> int {
         stage_mark(c, SE_STAGE_REAL, rs, false);
         if (c->parts & 1) launch_real<T>(c, xs, yr, rs, ncomp);
@@ -631,7 +634,11 @@ static int apply_t(se_ctx *c, int ncomp, const TO *x, TO *y)
         SE_CUDA_CHECK(c, cudaGetLastError());
         return SE_OK;
     }
-    if (c->overlap == 2 && (rc = real_part(s)) != SE_OK) return rc;
+    const bool fused = std::is_same<T, float>::value && fused_real_gather(c, ncomp, with_wave);
+    if (fused) {
+        stage_mark(c, SE_STAGE_REAL, s, false);
+        stage_mark(c, SE_STAGE_REAL, s, true);
+    } else if (c->overlap >= 2 && (rc = real_part(s)) != SE_OK) return rc;
     if (c->overlap == 0 && (rc = fork_real()) != SE_OK) return rc;
     if (with_wave) launch_wave_spread<T>(c, xs, s, ncomp);
     else {
@@ -645,7 +652,7 @@ static int apply_t(se_ctx *c, int ncomp, const TO *x, TO *y)
             stage_mark(c, st, s, false);
             stage_mark(c, st, s, true);
         }
-    if (c->overlap != 2) SE_CUDA_CHECK(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+    if (c->overlap <= 1) SE_CUDA_CHECK(c, cudaStreamWaitEvent(s, c->ev_join, 0));
     stage_mark(c, SE_STAGE_GATHER, s, false);
     launch_gather_combine<T, TO>(c, xs, yr, y, ncomp, with_wave, s);
     stage_mark(c, SE_STAGE_GATHER, s, true);

@@ -114,7 +114,7 @@ struct se_ctx {
     int size_mode = 0;                 // 0 hybrid, 1 real-space approach, 2 wave-space approach
     int restart = 30;
     int parts = 7;
-    int overlap = 2;             // SE_OPT_OVERLAP
+    int overlap = 3;             // SE_OPT_OVERLAP
     int gather = 0;              // SE_OPT_GATHER
     int spread = 0;              // SE_OPT_SPREAD
     int overlap_check = 1;       // SE_OPT_OVERLAP_CHECK
@@ -221,6 +221,7 @@ template <typename T>
 void launch_wave_fft(se_ctx *c, cudaStream_t s);
 // releases the spectral-correction sub-context (se_solve.cu)
 void free_spectral(se_ctx *c);
+bool fused_real_gather(const se_ctx *c, int ncomp, int with_wave);
 template <typename T, typename TO>
 void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int ncomp, int with_wave,
                            cudaStream_t s);

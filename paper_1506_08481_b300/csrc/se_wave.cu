@@ -29,6 +29,7 @@
 
 #include "se_fft.cuh"
 #include "se_internal.cuh"
+#include "se_real_table.cuh"
 
 namespace se {
 
@@ -1343,6 +1344,28 @@ __global__ void __launch_bounds__(32 * WPB, SE_GATHER_MINB * SE_GATHER_WPB / WPB
                                   wg, rad, selfc, perm, grid, xs, yreal, y, ncomp_out, with_wave, with_self);
 }
 
+// The FP32 gather (4 components, NCL columns per lane) with the real-space pair sum of its
+// particle in front of it: the warp first sums its target's stored pairs
+// (real_table_body_fused) into yreal, then gathers and combines.  In a launch of its own the
+// pair-table stream runs at the HBM bound while the gather's short dependent z-loops wait on
+// latency; in one kernel the table loads of some warps fill the memory pipe while others
+// gather.  yreal is written and read back by the warp's lane 0, so no other thread's order
+// matters.
+template <typename TO, bool MONO, int NCL>
+__global__ void __launch_bounds__(32 * SE_GATHER_WPB, SE_GATHER_MINB) gather_real_kernel(
+    SeParams p, int N, const int *order, const int *base, const float *s0g, const float *wg, const double *rad,
+    const float *selfc, const int *perm, const float *grid, const float *xs, float *yreal, TO *y, int ncomp_out,
+    int with_wave, int with_self, const int *pair_off, size_t np, const int *pj, const float *px, const float *pc)
+{
+    __shared__ float4 Wz[SE_GATHER_WPB][32];
+    __shared__ int Zi[SE_GATHER_WPB][32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int w = blockIdx.x * SE_GATHER_WPB + wl;
+    if (w < N) real_table_body_fused<MONO>(order[w], lane, N, pair_off, np, pj, px, pc, xs, yreal);
+    gather_body<float, TO, 4, 12, NCL>(w, lane, Wz[wl], Zi[wl], p, N, order, base, s0g, wg, rad, selfc, perm, grid, xs,
+                                     yreal, y, ncomp_out, with_wave, with_self);
+}
+
 // ---------------------------------------------------------------- staged gather
 //
 // The particles whose support starts in one kTile^3 tile (a spreading bin) share a
@@ -1862,6 +1885,17 @@ void launch_wave_fft(se_ctx *c, cudaStream_t s)
     stage_mark(c, SE_STAGE_FFT_XI, s, true);
 }
 
+// Whether the FP32 product runs the real-space sum inside the gather (gather_real_kernel):
+// SE_OPT_OVERLAP 3, both parts on, the stored FP32 pair table, F T S (S_tr) moments (for F or
+// F T the in-line sum reads fewer coefficient rows than the 12-component one), the
+// real-space size approach (4-component gather) and no staged gather.
+bool fused_real_gather(const se_ctx *c, int ncomp, int with_wave)
+{
+    const bool staged = c->shear == 0 && (c->gather == 2 || (c->gather == 0 && c->P <= kStagedMaxP));
+    return c->overlap == 3 && (c->parts & 1) && with_wave && ncomp > 6 && c->pairs_ok[0] && c->size_mode == 1 &&
+           !staged;
+}
+
 template <typename T, typename TO>
 void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int ncomp, int with_wave,
                            cudaStream_t s)
@@ -1922,6 +1956,29 @@ void launch_gather_combine(se_ctx *c, const T *xs, const T *yreal, TO *y, int nc
         // (ncomp 6 and 11 take the 12-component kernel, which writes only the caller's
         // components: measured at N = 2e5, P = 24 it runs 3.04 ms against 3.24 and 3.84 ms
         // for the 6- and 11-component instantiations, whose compiled z-loops schedule worse)
+        if constexpr (std::is_same<T, float>::value) {
+            if (fused_real_gather(c, ncomp, with_wave)) {
+                // the gather's columns per lane as for the unfused kernel below
+                const bool ncl2 = SE_GATHER_NCL == 2 && ((c->P * c->P) % 64 == 0 || (c->P * c->P) % 64 > 32);
+                auto fr = [&](auto kern) {
+                    kern<<<grid, wpb * 32, 0, s>>>(p, N, c->b.tile_perm, c->b.sup_base, (const T *)c->b.sup_s0[0],
+                                                   (const T *)c->b.sup_w[0], c->b.rad, (const T *)c->b.self_c[0],
+                                                   c->b.perm, (const T *)c->b.grid_o[0], xs, const_cast<T *>(yreal),
+                                                   y, ncomp, with_wave, with_self, c->b.pair_off, c->npairs,
+                                                   c->b.pair_j,
+                                                   (const T *)c->b.pair_x[0], (const T *)c->b.pair_c[0]);
+                };
+                if (ncl2) {
+                    if (c->pair_mono[0]) fr(gather_real_kernel<TO, true, 2>);
+                    else fr(gather_real_kernel<TO, false, 2>);
+                } else {
+                    if (c->pair_mono[0]) fr(gather_real_kernel<TO, true, 1>);
+                    else fr(gather_real_kernel<TO, false, 1>);
+                }
+                c->launches++;
+                return;
+            }
+        }
         if constexpr (std::is_same<T, float>::value && SE_GATHER_NCL == 2) {
             if ((c->P * c->P) % 64 == 0 || (c->P * c->P) % 64 > 32) {
                 if (ncomp <= 3) go(gather_kernel<T, TO, 4, 3, 2>);
