@@ -58,7 +58,7 @@ PAIR_BYTES_MONO = 68
 NCU_CAPTURE = {"N": 200000, "M": 144, "npairs": 88237670}
 NCU_DRAM_BYTES = {"permute": 13.0e6, "real": 6438.9e6, "spread": 374.6e6, "fft_x_fwd": 50.6e6,
                   "fft_y_fwd": 48.5e6, "fft_z_scale": 54.0e6, "fft_y_inv": 48.5e6, "fft_x_inv": 49.4e6,
-                  "gather": 149.5e6}
+                  "gather": 149.5e6, "gather_real": 6861.7e6}
 
 
 def parse():
@@ -206,7 +206,7 @@ def ncu_traffic(stage, M, npairs, N):
     b = NCU_DRAM_BYTES.get(stage)
     if b is None:
         return None
-    if stage == "real":
+    if stage in ("real", "gather_real"):      # the fused kernel's bytes are the pair table's, to 98%
         return b * npairs / NCU_CAPTURE["npairs"]
     if stage == "permute":
         return b * N / NCU_CAPTURE["N"]
@@ -239,7 +239,7 @@ def fused_entry(ms, N, M, P, CO, npairs, peaks, peak_kind):
     r = roofline_entry("real", ms, N, M, P, CO, npairs, peaks, peak_kind)
     e = dict(g if g["frac"] >= r["frac"] else r)
     e["kernel"] = "gather_real"
-    e["traffic"] = None
+    e["traffic"] = ncu_traffic("gather_real", M, npairs, N)
     e["alu_frac"], e["hbm_frac"] = g["frac"], r["frac"]
     e["algorithmic_flops"] = g["achieved"] * 1e12 * ms * 1e-3
     e["algorithmic_bytes"] = r["algorithmic_bytes"]
