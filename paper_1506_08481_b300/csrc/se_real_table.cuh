@@ -143,11 +143,17 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
 
 
 // The same sum for one target inside the gather kernel (FP32, F T S S_tr): there only a few of
-// the SM's warps stream the table at a time, so each lane keeps two pairs in flight (both
-// pairs' values loaded before either is contracted), and the table is read with streaming
-// loads (evict-first) so that it does not push the gather's grid points out of L1.  The
+// the SM's warps stream the table at a time, so each lane keeps fused_pairs() pairs in flight
+// (all their values loaded before any is contracted), and the table is read with streaming
+// loads (evict-first) so that it does not push the gather's grid points out of L1.  Measured
+// per product at N = 2e5, P = 24 (8.33 ms with the sum in a kernel of its own): plain loads, 1
+// pair 8.98 ms, 2 pairs 8.69 ms; evict-first loads, 2 pairs 8.01 ms, 3 pairs 7.94 ms, 4 pairs
+// 8.13 ms (the registers of four pairs spill).  A pair of the 19-coefficient table holds six
+// registers more: on a bidisperse box (N = 1e5, P = 24) 3 pairs took 3.83 ms against 3.76 ms for
+// 2, so that table keeps 2.  The
 // arithmetic is that of real_table_body<float, 12, float, MONO>, pair by pair in the same
 // order, so the result is the same.
+template <bool MONO> constexpr int fused_pairs() { return MONO ? 3 : 2; }
 template <bool MONO>
 __device__ __forceinline__ void real_table_body_fused(int i, int lane, int N, const int *off, size_t np,
                                                       const int *pj, const float *px, const float *pc,
@@ -261,12 +267,13 @@ __device__ __forceinline__ void real_table_body_fused(int i, int lane, int N, co
         if constexpr (MONO) a[12] += 3 * c15 * xF - 3 * c16 * xSx;
         else a[12] += C(d, 17) * xF + C(d, 18) * xSx;
     };
-    for (int k = k0; k < k1; k += 64) {
-        PD d0, d1;
-        load(k, true, d0);
-        load(k + 32, k + 32 < k1, d1);
-        acc(d0);
-        acc(d1);
+    constexpr int U = fused_pairs<MONO>();
+    for (int k = k0; k < k1; k += 32 * U) {
+        PD d[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load(k + 32 * u, k + 32 * u < k1, d[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc(d[u]);
     }
 #pragma unroll
     for (int c = 0; c < 13; ++c)
