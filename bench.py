@@ -58,7 +58,7 @@ PAIR_BYTES_MONO = 68
 NCU_CAPTURE = {"N": 200000, "M": 144, "npairs": 88237670}
 NCU_DRAM_BYTES = {"permute": 13.0e6, "real": 6438.9e6, "spread": 374.6e6, "fft_x_fwd": 50.6e6,
                   "fft_y_fwd": 48.5e6, "fft_z_scale": 54.0e6, "fft_y_inv": 48.5e6, "fft_x_inv": 49.4e6,
-                  "gather": 149.5e6, "gather_real": 6861.7e6}
+                  "gather": 149.5e6, "gather_real": 7028.7e6}
 
 
 def parse():
