@@ -233,8 +233,8 @@ int se_solve(se_ctx *ctx, int ncomp, const void *b, void *x, int dtype, double r
  * left pending by earlier, unrelated work is cleared on entry, not reported).  Every call
  * waits for `stream` (it reads a status flag back) and leaves the calling thread's
  * current device as it found it.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the one array and
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress).
+ * All calls share the one array and
  * every call clears what must start at zero; calls that overlap on the GPU race on it,
  * so the caller must not run two at once. */
 #define SE_NOALLOC_MAX_N     8192
