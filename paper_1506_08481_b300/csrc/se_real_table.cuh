@@ -150,9 +150,8 @@ __device__ __forceinline__ void real_table_body(int i, int lane, int N, const in
 // pair 8.98 ms, 2 pairs 8.69 ms; evict-first loads, 2 pairs 8.01 ms, 3 pairs 7.94 ms, 4 pairs
 // 8.13 ms (the registers of four pairs spill).  A pair of the 19-coefficient table holds six
 // registers more: on a bidisperse box (N = 1e5, P = 24) 3 pairs took 3.83 ms against 3.76 ms for
-// 2, so that table keeps 2.  The
-// arithmetic is that of real_table_body<float, 12, float, MONO>, pair by pair in the same
-// order, so the result is the same.
+// 2, so that table keeps 2.  The arithmetic is that of real_table_body<float, 12, float, MONO>,
+// pair by pair in the same order (a masked pair adds exact zeros), so the result is the same.
 template <bool MONO> constexpr int fused_pairs() { return MONO ? 3 : 2; }
 template <bool MONO>
 __device__ __forceinline__ void real_table_body_fused(int i, int lane, int N, const int *off, size_t np,
